@@ -1,0 +1,283 @@
+"""FP64 CPU oracle (ctypes binding of ``open_cf_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
+leg of ``bench.py`` are the only users.  The product library never imports
+this package, and this package imports nothing from the product.
+
+Every function takes and returns numpy arrays; floating point is FP64 except
+``select_f32`` (Algorithm 2 evaluated in FP32 so that the chosen index can be
+compared bit-exactly with a kernel that decides in FP32).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "open_cf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+OK, NOT_SPD, EMPTY_ROW, FALLBACK_USED = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+_d = ctypes.POINTER(ctypes.c_double)
+_f = ctypes.POINTER(ctypes.c_float)
+_i64 = ctypes.POINTER(ctypes.c_int64)
+_i32 = ctypes.POINTER(ctypes.c_int32)
+_I64, _I32, _D, _F = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_float
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        sig = {
+            "orc_num_threads": (ctypes.c_int, []),
+            "orc_set_num_threads": (None, [ctypes.c_int]),
+            "orc_cholesky": (ctypes.c_int, [ctypes.c_int, _d, _d]),
+            "orc_chol_solve": (None, [ctypes.c_int, _d, _d, _d]),
+            "orc_normal_equations": (None, [ctypes.c_int, _D, _I64, _i32, _d, _d, _d, _d]),
+            "orc_row_solve": (ctypes.c_int, [ctypes.c_int, _D, _I64, _i32, _d, _d, _d]),
+            "orc_half_step": (None, [_I64, _i64, _i32, _d, _d, ctypes.c_int, _D, _d, _i32]),
+            "orc_transpose": (None, [_I64, _I64, _i64, _i32, _d, _i64, _i32, _d]),
+            "orc_objective": (_D, [_I64, _I64, _i64, _i32, _d, _d, _d, ctypes.c_int, _D]),
+            "orc_row_rmse": (None, [_I64, _i64, _i32, _d, _d, _d, ctypes.c_int, _d]),
+            "orc_normal_residual": (_D, [ctypes.c_int, _D, _I64, _i32, _d, _d, _d]),
+            "orc_als": (None, [_I64, _I64, _i64, _i32, _d, ctypes.c_int, _D, ctypes.c_int,
+                               _d, _d, _d, _i32, _i32]),
+            "orc_als_dense": (None, [_I64, _I64, _d, ctypes.c_int, _D, ctypes.c_int, _d, _d,
+                                     _d]),
+            "orc_predict": (None, [_I64, _I64, ctypes.c_int, _d, _d, _d]),
+            "orc_select_f64": (None, [_I64, _I64, _d, _I32, _d, _d, _D, _I64, _i32, _d]),
+            "orc_select_f32": (None, [_I64, _I64, _f, _I32, _f, _f, _F, _I64, _i32, _f]),
+            "orc_mlp_forward": (None, [_I64] + [ctypes.c_int] * 4 + [_d] * 10),
+            "orc_mlp_loss_grad": (_D, [_I64] + [ctypes.c_int] * 4 + [_d] * 15),
+            "orc_adam": (None, [_I64, _d, _d, _d, _d, _I64, _D, _D, _D, _D]),
+            "orc_mlp_features": (None, [_I64, _i64, _i32, _d, _I32, _I32, _d, _d,
+                                        ctypes.c_int, _d]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    lib().orc_set_num_threads(int(t))
+
+
+def cholesky(A):
+    A = _c(A, np.float64)
+    k = A.shape[0]
+    L = np.zeros((k, k))
+    st = lib().orc_cholesky(k, _p(A, _d), _p(L, _d))
+    return L, st
+
+
+def chol_solve(L, b):
+    L = _c(L, np.float64); b = _c(b, np.float64)
+    x = np.zeros_like(b)
+    lib().orc_chol_solve(L.shape[0], _p(L, _d), _p(b, _d), _p(x, _d))
+    return x
+
+
+def normal_equations(F, idx, val, lam):
+    F = _c(F, np.float64); idx = _c(idx, np.int32); val = _c(val, np.float64)
+    k = F.shape[1]
+    A = np.zeros((k, k)); b = np.zeros(k)
+    lib().orc_normal_equations(k, lam, len(idx), _p(idx, _i32), _p(val, _d), _p(F, _d),
+                               _p(A, _d), _p(b, _d))
+    return A, b
+
+
+def row_solve(F, idx, val, lam):
+    F = _c(F, np.float64); idx = _c(idx, np.int32); val = _c(val, np.float64)
+    u = np.zeros(F.shape[1])
+    st = lib().orc_row_solve(F.shape[1], lam, len(idx), _p(idx, _i32), _p(val, _d), _p(F, _d),
+                             _p(u, _d))
+    return u, st
+
+
+def half_step(row_ptr, col, val, F, lam):
+    """Solve every CSR row against the fixed other factor F; returns (out, status)."""
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    F = _c(F, np.float64)
+    m = len(row_ptr) - 1
+    k = F.shape[1]
+    out = np.zeros((m, k)); st = np.zeros(m, dtype=np.int32)
+    lib().orc_half_step(m, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d), _p(F, _d), k, lam,
+                        _p(out, _d), _p(st, _i32))
+    return out, st
+
+
+def transpose(row_ptr, col, val, n):
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    m = len(row_ptr) - 1
+    nnz = int(row_ptr[-1])
+    cptr = np.zeros(n + 1, dtype=np.int64)
+    cidx = np.zeros(max(nnz, 1), dtype=np.int32)
+    cval = np.zeros(max(nnz, 1))
+    lib().orc_transpose(m, n, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d), _p(cptr, _i64),
+                        _p(cidx, _i32), _p(cval, _d))
+    return cptr, cidx[:nnz], cval[:nnz]
+
+
+def objective(row_ptr, col, val, U, V, lam):
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    U = _c(U, np.float64); V = _c(V, np.float64)
+    return float(lib().orc_objective(len(row_ptr) - 1, V.shape[0], _p(row_ptr, _i64),
+                                     _p(col, _i32), _p(val, _d), _p(U, _d), _p(V, _d),
+                                     U.shape[1], lam))
+
+
+def row_rmse(row_ptr, col, val, U, V):
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    U = _c(U, np.float64); V = _c(V, np.float64)
+    out = np.zeros(len(row_ptr) - 1)
+    lib().orc_row_rmse(len(row_ptr) - 1, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d),
+                       _p(U, _d), _p(V, _d), U.shape[1], _p(out, _d))
+    return out
+
+
+def normal_residual(F, idx, val, lam, u):
+    F = _c(F, np.float64); idx = _c(idx, np.int32); val = _c(val, np.float64)
+    u = _c(u, np.float64)
+    return float(lib().orc_normal_residual(F.shape[1], lam, len(idx), _p(idx, _i32),
+                                           _p(val, _d), _p(F, _d), _p(u, _d)))
+
+
+def als(row_ptr, col, val, n, V0, lam, sweeps, history=False):
+    """ALS from V0; returns (U, V, J_hist or None, row_status, col_status)."""
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    V = np.array(V0, dtype=np.float64, copy=True, order="C")
+    m = len(row_ptr) - 1
+    k = V.shape[1]
+    U = np.zeros((m, k))
+    J = np.zeros(2 * sweeps) if history else None
+    rs = np.zeros(m, dtype=np.int32); cs = np.zeros(n, dtype=np.int32)
+    lib().orc_als(m, n, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d), k, lam, sweeps,
+                  _p(U, _d), _p(V, _d), _p(J, _d) if history else None, _p(rs, _i32),
+                  _p(cs, _i32))
+    return U, V, J, rs, cs
+
+
+def als_dense(P, V0, lam, sweeps, history=False):
+    P = _c(P, np.float64)
+    V = np.array(V0, dtype=np.float64, copy=True, order="C")
+    m, n = P.shape
+    k = V.shape[1]
+    U = np.zeros((m, k))
+    J = np.zeros(2 * sweeps) if history else None
+    lib().orc_als_dense(m, n, _p(P, _d), k, lam, sweeps, _p(U, _d), _p(V, _d),
+                        _p(J, _d) if history else None)
+    return U, V, J
+
+
+def predict(U, V):
+    U = _c(U, np.float64); V = _c(V, np.float64)
+    T = np.zeros((U.shape[0], V.shape[0]))
+    lib().orc_predict(U.shape[0], V.shape[0], U.shape[1], _p(U, _d), _p(V, _d), _p(T, _d))
+    return T
+
+
+def baseline_index(cpu_caps, gpu_caps):
+    """Index of the (max CPU cap, max GPU cap) setting, CPU-major."""
+    return int(np.argmax(cpu_caps)) * len(gpu_caps) + int(np.argmax(gpu_caps))
+
+
+def select_f64(T, cpu_caps, gpu_caps, gamma, base=None):
+    T = _c(T, np.float64)
+    cpu = _c(cpu_caps, np.float64); gpu = _c(gpu_caps, np.float64)
+    base = baseline_index(cpu, gpu) if base is None or base < 0 else int(base)
+    m, n = T.shape
+    best = np.zeros(m, dtype=np.int32); sav = np.zeros(m)
+    lib().orc_select_f64(m, n, _p(T, _d), len(gpu), _p(cpu, _d), _p(gpu, _d), gamma, base,
+                         _p(best, _i32), _p(sav, _d))
+    return best, sav
+
+
+def select_f32(T, cpu_caps, gpu_caps, gamma, base=None):
+    T = _c(T, np.float32)
+    cpu = _c(cpu_caps, np.float32); gpu = _c(gpu_caps, np.float32)
+    base = baseline_index(cpu, gpu) if base is None or base < 0 else int(base)
+    m, n = T.shape
+    best = np.zeros(m, dtype=np.int32); sav = np.zeros(m, dtype=np.float32)
+    lib().orc_select_f32(m, n, _p(T, _f), len(gpu), _p(cpu, _f), _p(gpu, _f),
+                         np.float32(gamma), base, _p(best, _i32), _p(sav, _f))
+    return best, sav
+
+
+def mlp_forward(X, params):
+    """params = [W1, b1, W2, b2, W3, b3] with W [in, out]; returns (Z1, Z2, Y)."""
+    X = _c(X, np.float64)
+    P = [_c(p, np.float64) for p in params]
+    B, din = X.shape
+    h1, h2, dout = P[0].shape[1], P[2].shape[1], P[4].shape[1]
+    Z1 = np.zeros((B, h1)); Z2 = np.zeros((B, h2)); Y = np.zeros((B, dout))
+    lib().orc_mlp_forward(B, din, h1, h2, dout, _p(X, _d), *[_p(p, _d) for p in P],
+                          _p(Z1, _d), _p(Z2, _d), _p(Y, _d))
+    return Z1, Z2, Y
+
+
+def mlp_loss_grad(X, params, Ytgt, G):
+    X = _c(X, np.float64)
+    P = [_c(p, np.float64) for p in params]
+    Ytgt = _c(Ytgt, np.float64); G = _c(G, np.float64)
+    B, din = X.shape
+    h1, h2, dout = P[0].shape[1], P[2].shape[1], P[4].shape[1]
+    grads = [np.zeros_like(p) for p in P]
+    L = lib().orc_mlp_loss_grad(B, din, h1, h2, dout, _p(X, _d), *[_p(p, _d) for p in P],
+                                _p(Ytgt, _d), _p(G, _d), *[_p(g, _d) for g in grads])
+    return float(L), grads
+
+
+def adam(theta, g, m1, m2, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam step on flat FP64 arrays."""
+    for a in (theta, g, m1, m2):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    lib().orc_adam(theta.size, _p(theta, _d), _p(g, _d), _p(m1, _d), _p(m2, _d), int(t), lr,
+                   beta1, beta2, eps)
+
+
+def mlp_features(row_ptr, col, val, cpu_caps, gpu_caps, s_in=16):
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    cpu = _c(cpu_caps, np.float64); gpu = _c(gpu_caps, np.float64)
+    m = len(row_ptr) - 1
+    X = np.zeros((m, 3 * s_in))
+    lib().orc_mlp_features(m, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d), len(cpu), len(gpu),
+                           _p(cpu, _d), _p(gpu, _d), s_in, _p(X, _d))
+    return X

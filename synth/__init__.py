@@ -1,0 +1,402 @@
+"""Seeded synthetic inputs for the OPEN online-phase completion path.
+
+This module only *generates inputs*: performance matrices, observation masks,
+initial factors, held-out samples and cap grids.  It holds none of the
+method's arithmetic (no Gram, no solve, no selection), so both the CUDA path
+and the FP64 oracle can be fed from it without sharing any method code.
+
+The paper's matrices come from profiling real applications under CPU/GPU
+power caps (Sec. "Putting it all together", Eq. 1; Sec. "Online Performance
+Prediction"); none of that data exists here.  The recipes below stand in for
+it, with the shapes of the paper's problem: rows are applications, columns are
+(CPU cap, GPU cap) settings in CPU-major order ``j = c_idx * n_gpu + g_idx``,
+the offline block is dense, and each new application contributes a handful of
+online-profiled entries.
+
+Readings of unstated details (also listed in the design doc):
+  * noise ``N(0, 0.01)`` is a standard deviation of 0.01, added after
+    normalisation, never clipped;
+  * the exp-transformed matrix is normalised by its global min and max;
+  * a "rank-r ground truth" is ``U V^T / max|U V^T|`` so it stays exactly
+    rank r;
+  * CPU caps are ``linspace(120, 270, n_cpu)`` W and GPU caps
+    ``linspace(100, 250, n_gpu)`` W (the paper enumerates no grid);
+  * random draws of the method itself (the initial V of ALS, the initial MLP
+    weights) are generated here and passed in as inputs.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+NOISE_STD = 0.01
+
+
+def cap_grid(n_cpu: int, n_gpu: int):
+    """CPU and GPU cap values in watts (ascending)."""
+    return (np.linspace(120.0, 270.0, n_cpu), np.linspace(100.0, 250.0, n_gpu))
+
+
+@dataclasses.dataclass
+class CompletionProblem:
+    """One sparse completion problem in CSR form plus what scores it."""
+    m: int
+    n: int
+    k: int
+    lam: float
+    sweeps: int
+    row_ptr: np.ndarray          # int64[m+1]
+    col: np.ndarray              # int32[nnz], strictly increasing per row
+    val: np.ndarray              # float64[nnz] observed (noisy) values
+    V0: np.ndarray               # float64[n, k] initial V of ALS
+    n_cpu: int = 1
+    n_gpu: int = 1
+    heldout_rows: Optional[np.ndarray] = None   # int64
+    heldout_cols: Optional[np.ndarray] = None   # int64
+    heldout_truth: Optional[np.ndarray] = None  # float64, noiseless
+    truth: Optional[np.ndarray] = None          # dense noiseless truth when small
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def caps(self):
+        return cap_grid(self.n_cpu, self.n_gpu)
+
+
+def csr_from_positions(pos: np.ndarray, m: int, n: int):
+    """CSR (row_ptr, col) of sorted flattened positions ``i * n + j``."""
+    rows = pos // n
+    cols = (pos - rows * n).astype(np.int32)
+    counts = np.bincount(rows, minlength=m).astype(np.int64)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return row_ptr, cols, rows
+
+
+def bernoulli_positions(rng: np.random.Generator, total: int, p: float) -> np.ndarray:
+    """Sorted positions of an i.i.d. Bernoulli(p) mask over ``total`` cells.
+
+    Successive gaps of a Bernoulli process are Geometric(p), so drawing gaps
+    gives the same distribution as drawing every cell, at O(p * total) cost.
+    """
+    if p >= 1.0:
+        return np.arange(total, dtype=np.int64)
+    est = int(p * total + 8.0 * math.sqrt(p * total + 1.0) + 64)
+    chunks = []
+    last = -1
+    while True:
+        gaps = rng.geometric(p, size=est).astype(np.int64)
+        pos = last + np.cumsum(gaps)
+        chunks.append(pos)
+        last = int(pos[-1])
+        if last >= total:
+            break
+    pos = np.concatenate(chunks)
+    return pos[pos < total]
+
+
+def sample_unobserved(rng, m, n, observed_pos, count):
+    """Seeded sample of ``count`` distinct unobserved cells (rows, cols)."""
+    count = int(min(count, m * n - len(observed_pos)))
+    picked = np.empty(0, dtype=np.int64)
+    while len(picked) < count:
+        cand = rng.integers(0, m * n, size=2 * (count - len(picked)) + 16)
+        cand = np.unique(cand)
+        cand = cand[~np.isin(cand, observed_pos, assume_unique=False)]
+        cand = cand[~np.isin(cand, picked)]
+        picked = np.concatenate([picked, cand])
+    picked = np.sort(picked[:count])
+    rows = picked // n
+    return rows, picked - rows * n
+
+
+def init_factor(rng, n, k, scale=0.1):
+    """Initial V of ALS: ``scale * N(0, 1)`` entries (n x k)."""
+    return scale * rng.standard_normal((n, k))
+
+
+# ---------------------------------------------------------------------------
+# Workload 1: 64 apps x 120 settings (8 CPU x 15 GPU caps), exp-transformed
+# rank-4 truth, 48 fully observed offline rows + 16 new rows with 6 entries.
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class OfflineOnlineProblem:
+    offline: np.ndarray          # dense [m_off, n] noisy offline block
+    new: CompletionProblem       # CSR of the new rows (row indices local)
+    joint: CompletionProblem     # CSR of all rows (offline + new)
+    truth: np.ndarray            # dense noiseless truth [m, n]
+    m_off: int
+
+
+def make_small_offline_online(seed: int = 0, m: int = 64, m_off: int = 48,
+                              n_cpu: int = 8, n_gpu: int = 15, rank: int = 4,
+                              k: int = 8, lam: float = 0.1, sweeps: int = 20,
+                              obs_per_new_row: int = 6) -> OfflineOnlineProblem:
+    rng = np.random.default_rng(seed)
+    n = n_cpu * n_gpu
+    Ut = rng.standard_normal((m, rank)) / 2.0
+    Vt = rng.standard_normal((n, rank)) / 2.0
+    T0 = np.exp(Ut @ Vt.T)
+    truth = (T0 - T0.min()) / (T0.max() - T0.min())
+    noisy = truth + rng.normal(0.0, NOISE_STD, size=(m, n))
+    offline = noisy[:m_off].copy()
+    new_cols = [np.sort(rng.choice(n, size=obs_per_new_row, replace=False))
+                for _ in range(m - m_off)]
+    V0 = init_factor(rng, n, k)
+
+    def build(rows_cols):
+        ptr = [0]
+        cols, vals = [], []
+        for i, cs in rows_cols:
+            cols.append(np.asarray(cs, dtype=np.int32))
+            vals.append(noisy[i, cs])
+            ptr.append(ptr[-1] + len(cs))
+        return (np.asarray(ptr, dtype=np.int64), np.concatenate(cols).astype(np.int32),
+                np.concatenate(vals).astype(np.float64))
+
+    new_rc = [(m_off + t, c) for t, c in enumerate(new_cols)]
+    p_new, c_new, v_new = build(new_rc)
+    all_rc = [(i, np.arange(n)) for i in range(m_off)] + new_rc
+    p_all, c_all, v_all = build(all_rc)
+    # held-out: every unobserved entry of the new rows
+    hr, hc = [], []
+    for t, cs in enumerate(new_cols):
+        un = np.setdiff1d(np.arange(n), cs)
+        hr.append(np.full(len(un), t, dtype=np.int64))
+        hc.append(un.astype(np.int64))
+    hr = np.concatenate(hr)
+    hc = np.concatenate(hc)
+    new = CompletionProblem(m - m_off, n, k, lam, sweeps, p_new, c_new, v_new, V0.copy(),
+                            n_cpu, n_gpu, hr, hc, truth[m_off + hr, hc], truth[m_off:].copy())
+    joint = CompletionProblem(m, n, k, lam, sweeps, p_all, c_all, v_all, V0.copy(),
+                              n_cpu, n_gpu, hr + m_off, hc, truth[m_off + hr, hc], truth.copy())
+    return OfflineOnlineProblem(offline, new, joint, truth, m_off)
+
+
+# ---------------------------------------------------------------------------
+# Workload 2 (and the generic sparse recipe): rank-r truth U V^T / max|U V^T|,
+# U, V ~ N(0,1)/2, Bernoulli(density) mask, N(0, 0.01) noise.
+# ---------------------------------------------------------------------------
+def make_sparse_problem(seed: int = 0, m: int = 4096, n_cpu: int = 16, n_gpu: int = 64,
+                        rank: int = 16, density: float = 0.05, k: int = 16,
+                        lam: float = 0.05, sweeps: int = 15, n_heldout: int = 1 << 17,
+                        keep_truth: bool = False, rng=None) -> CompletionProblem:
+    rng = np.random.default_rng(seed) if rng is None else rng
+    n = n_cpu * n_gpu
+    Ut = rng.standard_normal((m, rank)) / 2.0
+    Vt = rng.standard_normal((n, rank)) / 2.0
+    M = Ut @ Vt.T
+    scale = float(np.abs(M).max())
+    truth = M / scale
+    pos = bernoulli_positions(rng, m * n, density)
+    row_ptr, col, rows = csr_from_positions(pos, m, n)
+    val = truth.ravel()[pos] + rng.normal(0.0, NOISE_STD, size=len(pos))
+    V0 = init_factor(rng, n, k)
+    hr, hc = sample_unobserved(rng, m, n, pos, n_heldout)
+    return CompletionProblem(m, n, k, lam, sweeps, row_ptr, col, val.astype(np.float64), V0,
+                             n_cpu, n_gpu, hr, hc, truth[hr, hc],
+                             truth if keep_truth else None)
+
+
+def make_c2(seed: int = 0, **kw) -> CompletionProblem:
+    """4096 apps x 1024 settings (16 x 64 caps), rank 16, 5 % observed, k=16,
+    lambda=0.05, 15 sweeps."""
+    return make_sparse_problem(seed=seed, **kw)
+
+
+# ---------------------------------------------------------------------------
+# Workload 3: many independent problems of uneven size.
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class BatchedProblems:
+    problems: List[CompletionProblem]
+
+    def __len__(self):
+        return len(self.problems)
+
+    def concat(self):
+        """Concatenated CSR/V0 arrays with per-problem offsets (int64)."""
+        P = len(self.problems)
+        m = np.array([p.m for p in self.problems], dtype=np.int64)
+        n = np.array([p.n for p in self.problems], dtype=np.int64)
+        k = np.array([p.k for p in self.problems], dtype=np.int32)
+        nnz = np.array([p.nnz for p in self.problems], dtype=np.int64)
+        row_off = np.zeros(P + 1, dtype=np.int64); np.cumsum(m, out=row_off[1:])
+        col_off = np.zeros(P + 1, dtype=np.int64); np.cumsum(n, out=col_off[1:])
+        nnz_off = np.zeros(P + 1, dtype=np.int64); np.cumsum(nnz, out=nnz_off[1:])
+        uf = np.zeros(P + 1, dtype=np.int64); np.cumsum(m * k, out=uf[1:])
+        vf = np.zeros(P + 1, dtype=np.int64); np.cumsum(n * k, out=vf[1:])
+        # row_ptr of each problem is local (starts at 0); concatenated row_ptr
+        # holds global nnz offsets and has sum(m) + 1 entries.
+        row_ptr = np.zeros(int(row_off[-1]) + 1, dtype=np.int64)
+        for t, p in enumerate(self.problems):
+            row_ptr[row_off[t]:row_off[t + 1] + 1] = p.row_ptr + nnz_off[t]
+        col = np.concatenate([p.col for p in self.problems]).astype(np.int32)
+        val = np.concatenate([p.val for p in self.problems])
+        V0 = np.concatenate([p.V0.ravel() for p in self.problems])
+        return dict(m=m, n=n, k=k, row_off=row_off, col_off=col_off, nnz_off=nnz_off,
+                    u_off=uf, v_off=vf, row_ptr=row_ptr, col=col, val=val, V0=V0)
+
+
+def make_batched(seed: int = 0, n_problems: int = 10000, m_range=(32, 512),
+                 n_range=(64, 1024), density_range=(0.02, 0.20), rank_range=(8, 32),
+                 lam: float = 0.05, sweeps: int = 15, n_heldout: int = 64) -> BatchedProblems:
+    """Apps, settings and density log-uniform over their ranges, rank uniform
+    over the integers, solver k equal to the rank.  Settings counts are
+    factored into a CPU x GPU grid only nominally (n_cpu=1)."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    lm = np.log(m_range); ln = np.log(n_range); ld = np.log(density_range)
+    for _ in range(n_problems):
+        m = int(round(math.exp(rng.uniform(lm[0], lm[1]))))
+        n = int(round(math.exp(rng.uniform(ln[0], ln[1]))))
+        d = float(math.exp(rng.uniform(ld[0], ld[1])))
+        r = int(rng.integers(rank_range[0], rank_range[1] + 1))
+        probs.append(make_sparse_problem(m=m, n_cpu=1, n_gpu=n, rank=r, density=d, k=r,
+                                         lam=lam, sweeps=sweeps, n_heldout=n_heldout,
+                                         rng=rng))
+    return BatchedProblems(probs)
+
+
+# ---------------------------------------------------------------------------
+# Workloads 4 and 5 are too large for numpy on the host; they are drawn with
+# torch (CPU or CUDA device) from a seeded generator.  Only inputs are made.
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def torch_bernoulli_csr(gen, m: int, n: int, p: float, device):
+    """CSR of an i.i.d. Bernoulli(p) mask over m x n via geometric gaps
+    (inverse-CDF draws), entirely on ``device``."""
+    torch = _torch()
+    total = m * n
+    est = int(p * total + 8.0 * math.sqrt(p * total + 1.0) + 64)
+    logq = math.log1p(-p)
+    chunks = []
+    last = -1
+    while True:
+        u = torch.rand(est, generator=gen, device=device, dtype=torch.float64)
+        gaps = torch.floor(torch.log1p(-u) / logq).to(torch.int64) + 1
+        pos = last + torch.cumsum(gaps, 0)
+        chunks.append(pos)
+        last = int(pos[-1].item())
+        if last >= total:
+            break
+    pos = torch.cat(chunks)
+    pos = pos[pos < total]
+    rows = torch.div(pos, n, rounding_mode="floor")
+    cols = (pos - rows * n).to(torch.int32)
+    counts = torch.bincount(rows, minlength=m)
+    row_ptr = torch.zeros(m + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    return row_ptr, cols, rows
+
+
+@dataclasses.dataclass
+class LargeSparseProblem:
+    m: int
+    n: int
+    k: int
+    lam: float
+    n_cpu: int
+    n_gpu: int
+    row_ptr: object   # torch int64 [m+1]
+    col: object       # torch int32 [nnz]
+    val: object       # torch float32 [nnz]
+    Ut: object        # torch float32 [m, rank]  (ground-truth factors)
+    Vt: object        # torch float32 [n, rank]
+    scale: float
+    V: object         # torch float32 [n, k]  fixed V for the fold-in
+
+
+def make_large_foldin(seed: int = 0, m: int = 1 << 20, n_cpu: int = 64, n_gpu: int = 64,
+                      rank: int = 32, k: int = 32, density: float = 0.01, lam: float = 0.05,
+                      device="cuda") -> LargeSparseProblem:
+    """1M apps x 4096 settings (64 x 64 caps), 1 % observed, k=32.  The fixed
+    V of the fold-in is the ground-truth V plus 1 % noise (a stand-in for an
+    offline fit), so the fold-in works on a realistic, well-posed V."""
+    torch = _torch()
+    n = n_cpu * n_gpu
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    Ut = torch.randn(m, rank, generator=gen, device=device) / 2.0
+    Vt = torch.randn(n, rank, generator=gen, device=device) / 2.0
+    scale = 0.0
+    step = max(1, (1 << 26) // n)
+    for s in range(0, m, step):
+        scale = max(scale, float((Ut[s:s + step] @ Vt.T).abs().max().item()))
+    row_ptr, col, rows = torch_bernoulli_csr(gen, m, n, density, device)
+    nnz = col.numel()
+    val = torch.empty(nnz, dtype=torch.float32, device=device)
+    step = 1 << 24
+    for s in range(0, nnz, step):
+        r = rows[s:s + step]
+        c = col[s:s + step].to(torch.int64)
+        val[s:s + step] = (Ut[r] * Vt[c]).sum(1) / scale
+    val += NOISE_STD * torch.randn(nnz, generator=gen, device=device)
+    V = (Vt[:, :k] if rank >= k else torch.nn.functional.pad(Vt, (0, k - rank)))
+    V = (V + 0.01 * torch.randn(V.shape, generator=gen, device=device)).contiguous()
+    del rows
+    return LargeSparseProblem(m, n, k, lam, n_cpu, n_gpu, row_ptr, col, val, Ut, Vt, scale, V)
+
+
+@dataclasses.dataclass
+class LearnedWorkload:
+    n: int
+    n_cpu: int
+    n_gpu: int
+    k: int
+    lam: float
+    s_obs: int
+    scale: float
+    Vt: object        # ground-truth setting factors [n, rank] (torch)
+    offline: object   # dense noisy offline block [m_off, n] (torch float32)
+    gen: object       # torch generator for app draws
+    device: object
+    rank: int
+
+    def draw_apps(self, count: int):
+        """``count`` new apps: full noisy rows [count, n], noiseless rows, and
+        ``s_obs`` distinct observed settings per app (sorted, int32)."""
+        torch = _torch()
+        Ua = torch.randn(count, self.rank, generator=self.gen, device=self.device) / 2.0
+        clean = (Ua @ self.Vt.T) / self.scale
+        noisy = clean + NOISE_STD * torch.randn(clean.shape, generator=self.gen,
+                                                device=self.device)
+        keys = torch.rand(count, self.n, generator=self.gen, device=self.device)
+        obs = torch.topk(keys, self.s_obs, dim=1).indices.sort(dim=1).values.to(torch.int32)
+        return noisy, clean, obs
+
+
+def make_learned(seed: int = 0, n_cpu: int = 64, n_gpu: int = 64, rank: int = 32, k: int = 32,
+                 lam: float = 0.05, m_off: int = 4096, s_obs: int = 16,
+                 device="cuda") -> LearnedWorkload:
+    """Fixed 4096-setting V from a dense 4096-app offline block of the same
+    generative model (rank-32 truth U V^T / max|U V^T| plus noise)."""
+    torch = _torch()
+    n = n_cpu * n_gpu
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    Vt = torch.randn(n, rank, generator=gen, device=device) / 2.0
+    Uo = torch.randn(m_off, rank, generator=gen, device=device) / 2.0
+    M = Uo @ Vt.T
+    scale = float(M.abs().max().item())
+    offline = M / scale + NOISE_STD * torch.randn(M.shape, generator=gen, device=device)
+    return LearnedWorkload(n, n_cpu, n_gpu, k, lam, s_obs, scale, Vt, offline.contiguous(),
+                           gen, device, rank)
+
+
+def mlp_init(rng: np.random.Generator, sizes=(48, 256, 256, 32)):
+    """LeCun-normal initial weights (the SELU recommendation of Klambauer et
+    al. 2017) and zero biases; W_l is stored [in, out] row-major."""
+    params = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        params.append(rng.standard_normal((a, b)) / math.sqrt(a))
+        params.append(np.zeros(b))
+    return params
