@@ -1,0 +1,189 @@
+/*
+ * open_cf.h -- C ABI of the B300 engine for the collaborative-filtering step
+ * of OPEN's online phase (Zheng, Lan, Wu, Taylor, Papka: "Coordinated Power
+ * Management on Heterogeneous Systems", arXiv 2508.07605).
+ *
+ * The paper's problem (Sec. "Putting it all together", Eq. 1; Sec. "Online
+ * Performance Prediction"): a dense offline performance matrix P with one row
+ * per profiled application and one column per (CPU cap, GPU cap) setting; a
+ * new application is profiled online under a few settings, which appends a
+ * sparse row; collaborative filtering fills in the rest of the row; and
+ * Algorithm 2 picks the most energy-efficient setting within a loss bound.
+ *
+ * This library does the filling-in by regularised matrix factorisation
+ * P ~ U V^T fitted with alternating least squares (the model of the
+ * Netflix-prize work the paper cites for collaborative filtering, Sec.
+ * "Collaborative Filtering Model"):
+ *     J(U,V) = sum_{(i,j) observed} (R_ij - u_i . v_j)^2 + lambda (|U|_F^2 + |V|_F^2),
+ * each half-step solving, per row i,
+ *     (sum_{j in Omega_i} v_j v_j^T + lambda I) u_i = sum_{j in Omega_i} R_ij v_j.
+ *
+ * Conventions shared by every call
+ *  - Settings are indexed CPU-major: j = c_idx * n_gpu_caps + g_idx.
+ *  - Matrix entries are normalised runtimes (lower is faster).
+ *  - Every array argument is a DEVICE pointer on cfg.device unless its name
+ *    ends in _host.  The caller owns all arrays; nothing is retained after a
+ *    call returns.  Arrays are C-contiguous (row-major).
+ *  - "real" below means double when the handle's precision is OPEN_CF_FP64
+ *    and float otherwise (OPEN_CF_FP32, OPEN_CF_BF16_GRAM).
+ *  - Sparse inputs are CSR: row_ptr int64[m+1] with row_ptr[0] = 0,
+ *    non-decreasing, row_ptr[m] = nnz; col int32[nnz] strictly increasing
+ *    within a row, each in [0, n); val real[nnz], finite.  Kernels bounds-check
+ *    row_ptr against nnz and col against n and mark offending rows with
+ *    OPEN_CF_ROW_BAD_INPUT instead of reading out of bounds;
+ *    open_cf_validate_csr checks every stated property.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  A return of OPEN_CF_OK means the work is enqueued.  Argument
+ *    errors are detected synchronously on the host and leave the handle
+ *    unchanged.
+ *  - A handle may be used by one host thread at a time.
+ *  - There is no CPU fallback: every computation runs in this library's CUDA
+ *    kernels for sm_103a.
+ */
+#ifndef OPEN_CF_H
+#define OPEN_CF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define OPEN_CF_OK 0
+#define OPEN_CF_INVALID_ARG (-1)
+#define OPEN_CF_NOT_FITTED (-2)   /* no V set or fitted yet */
+#define OPEN_CF_CUDA_ERROR (-3)
+#define OPEN_CF_OUT_OF_MEMORY (-4)
+#define OPEN_CF_UNSUPPORTED (-5)  /* k > OPEN_CF_MAX_K, device not sm_103 */
+#define OPEN_CF_TIMEOUT (-6)
+
+/* Per-row status codes written to status arrays. */
+#define OPEN_CF_ROW_OK 0
+#define OPEN_CF_ROW_NOT_SPD 1        /* a Cholesky pivot was not > 0; u = 0 */
+#define OPEN_CF_ROW_EMPTY 2          /* no observation; u = 0 */
+#define OPEN_CF_ROW_FALLBACK_USED 3  /* learned factor rejected, ALS used */
+#define OPEN_CF_ROW_BAD_INPUT 4      /* row_ptr / col out of range; u = 0 */
+
+#define OPEN_CF_MAX_K 32
+
+typedef struct open_cf open_cf_t; /* opaque: owns V, workspaces, CUDA graphs */
+
+typedef enum {
+    OPEN_CF_FP64 = 0,      /* FP64 values, factors, Gram and Cholesky */
+    OPEN_CF_FP32 = 1,      /* FP32 values, factors, Gram and Cholesky */
+    OPEN_CF_BF16_GRAM = 2  /* FP32 values and factors; Gram from BF16 copies of
+                              the factors on tensor cores, FP32 accumulation */
+} open_cf_precision;
+
+typedef struct {
+    int32_t k;                 /* latent rank, 1..OPEN_CF_MAX_K */
+    double lambda;             /* ridge regulariser, > 0 */
+    int32_t sweeps;            /* ALS sweeps of a fit (U-half then V-half), >= 0 */
+    uint64_t seed;             /* reserved: random draws are passed in as inputs */
+    open_cf_precision precision;
+    int32_t cholesky_fp64;     /* 1: k x k factorisation in FP64 (FP32/BF16 modes) */
+    int32_t n_cpu_caps;        /* cap grid for Algorithm 2; 0 = no grid */
+    int32_t n_gpu_caps;
+    const double *cpu_caps_w_host; /* n_cpu_caps watts, copied at create */
+    const double *gpu_caps_w_host; /* n_gpu_caps watts, copied at create */
+    int32_t device;            /* CUDA device ordinal */
+    float mlp_fallback_threshold; /* observed-entry RMSE above which the learned
+                                     factor is replaced by the ALS solve */
+} open_cf_config;
+
+/* Create a handle.  Copies cfg and the cap grids.  Fails with
+ * OPEN_CF_UNSUPPORTED if the device is not compute capability 10.3 or k is out
+ * of range, OPEN_CF_INVALID_ARG for lambda <= 0 or a malformed cap grid. */
+int open_cf_create(const open_cf_config *cfg, open_cf_t **out);
+
+/* Release the handle and every device buffer it owns (synchronises the
+ * device first).  NULL is ignored. */
+void open_cf_destroy(open_cf_t *h);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next
+ * call on the handle. */
+const char *open_cf_last_error(const open_cf_t *h);
+
+/* Set the handle's V (n x k real): the initial V of the next fit (the random
+ * draw of ALS's initialisation is passed in), or the fixed V of a fold-in.
+ * If a cap grid was given, n must equal n_cpu_caps * n_gpu_caps. */
+int open_cf_set_V(open_cf_t *h, const void *V, int64_t n, void *stream);
+
+/* Copy the handle's current V (n x k real) out. */
+int open_cf_get_V(open_cf_t *h, void *V_out, void *stream);
+
+/* Offline fit on the dense offline block (Eq. 1; every entry observed):
+ * P is m_off x n real with leading dimension ld >= n.  Runs cfg.sweeps ALS
+ * sweeps from the V set by open_cf_set_V, keeps the fitted V (and the block,
+ * for later joint refits) in the handle, and writes the offline factors to
+ * U_out (m_off x k real, may be NULL).  J_hist (2 * sweeps doubles, may be
+ * NULL) receives J after every half-step. */
+int open_cf_fit_offline(open_cf_t *h, const void *P, int64_t m_off, int64_t n, int64_t ld,
+                        void *U_out, double *J_hist, void *stream);
+
+/* Sparse fit (extension): ALS sweeps on a CSR matrix of m rows and n columns
+ * from the handle's V.  The CSC copy of the matrix is built on the device by
+ * a stable counting sort.  U_out: m x k real (may be NULL); row_status and
+ * col_status (int32, may be NULL) receive the codes of the last sweep;
+ * J_hist as for open_cf_fit_offline. */
+int open_cf_fit_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                    const int32_t *col, const void *val, void *U_out, int32_t *row_status,
+                    int32_t *col_status, double *J_hist, void *stream);
+
+/* Online completion (Sec. "Online Performance Prediction"): m_new new
+ * applications, each with its few online-profiled entries as a CSR row.
+ * joint = 0 (fold-in): every row is one independent ridge solve against the
+ *   handle's fixed V; writes U_out (m_new x k real) and status (may be NULL).
+ * joint = 1: re-runs cfg.sweeps sweeps over the offline block of the last
+ *   open_cf_fit_offline plus the new rows, starting from the current V, and
+ *   updates V; U_out receives the factors of the new rows. */
+int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_t *row_ptr,
+                          const int32_t *col, const void *val, void *U_out, int32_t *status,
+                          int32_t joint, void *stream);
+
+/* Reconstruction and Algorithm 2 (energy-efficient power-cap selection) on
+ * the predicted rows T = U V^T, U m x k real.  T_out (m x n real) may be NULL,
+ * in which case the dense prediction never leaves the chip; best (int32[m])
+ * and saving (float[m]) may be NULL.  Per row, with t the predicted runtimes:
+ *   p_j = t_base / t_j, valid if t_j > 0 and 1 - p_j <= gamma,
+ *   E_j = (c_j + g_j) / p_j, saving_j = (E_base - E_j) / E_base,
+ *   E_base = C_b + G_b, best = argmax saving (ties: smaller c + g, then smaller j).
+ * The selection is evaluated in FP32 in exactly that operation order.
+ * baseline_setting = -1 selects (max CPU cap, max GPU cap).  A row whose
+ * baseline runtime is not > 0 gets best = -1 and saving = 0.  Needs a cap grid
+ * when best or saving is requested. */
+int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t *best,
+                    float *saving, float gamma, int32_t baseline_setting, void *stream);
+
+/* Algorithm 2 alone on a given dense matrix T (m x n float, ld >= n), as in
+ * open_cf_predict. */
+int open_cf_select(open_cf_t *h, const float *T, int64_t m, int64_t ld, int32_t *best,
+                   float *saving, float gamma, int32_t baseline_setting, void *stream);
+
+/* Objective J(U, V) of the CSR matrix against the given U (m x k real) and the
+ * handle's V, accumulated in FP64 in a fixed order: J_out (one double) and
+ * row_rmse (float[m], may be NULL: RMSE over each row's observed entries). */
+int open_cf_objective(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                      const int32_t *col, const void *val, const void *U, double *J_out,
+                      float *row_rmse, void *stream);
+
+/* CSR -> CSC by a stable counting sort on the device (entries of a column in
+ * increasing row order): col_ptr int64[n+1], row_idx int32[nnz], cval real[nnz].
+ * Uses handle-owned scratch of n * nb int32 counters (nb <= 4096 row blocks). */
+int open_cf_csr_to_csc(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                       const int32_t *col, const void *val, int64_t *col_ptr, int32_t *row_idx,
+                       void *cval, void *stream);
+
+/* Check every stated CSR property on the device; synchronises `stream` and
+ * writes 0 (valid) or the first failed check to *result_host:
+ * 1 row_ptr, 2 column range, 3 column order/duplicate, 4 non-finite value. */
+int open_cf_validate_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                         const int32_t *col, const void *val, int32_t *result_host,
+                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPEN_CF_H */

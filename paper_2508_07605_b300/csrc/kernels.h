@@ -1,0 +1,84 @@
+// Internal launcher declarations shared by the engine (open_cf.cu) and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ocf {
+
+// One ALS half-step over the rows of a CSR matrix against a fixed factor F.
+template <typename TV> struct SolveArgs {
+    int64_t m;            // number of systems (rows)
+    int64_t nnz;          // entries of the CSR arrays (bounds for row_ptr)
+    const int64_t *ptr;   // row_ptr [m+1]
+    const int32_t *idx;   // column indices [nnz]
+    const TV *val;        // observed values [nnz]
+    const TV *F;          // other factor, n_other rows of KP elements (zero padded)
+    int64_t n_other;
+    TV *out;              // output rows: out[i * ldo + q], q < kout
+    int64_t ldo;
+    int kout;
+    int32_t *status;      // per-row status or null
+    double lambda;
+};
+
+template <typename TV, typename TC>
+cudaError_t launch_row_solve(const SolveArgs<TV> &a, int KP, cudaStream_t st);
+
+// CSR -> CSC stable counting sort.  Scratch: cnt int32[n * nb] and tot
+// int64[n]; nb = number of row blocks (see csc_blocks).
+int64_t csc_blocks(int64_t m, int64_t n, int64_t nnz);
+template <typename TV>
+cudaError_t launch_csr_to_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *ptr,
+                              const int32_t *idx, const TV *val, int64_t *cptr, int32_t *ridx,
+                              TV *cval, int32_t *cnt, int64_t *tot, int64_t nb, cudaStream_t st);
+cudaError_t prepare_csr_to_csc(int64_t n_max);
+
+// Reconstruction T = U V^T fused with Algorithm 2.
+template <typename TV> struct PredictArgs {
+    int64_t m, n;
+    int KP, k;
+    const TV *U;          // m rows, stride ldu
+    int64_t ldu;
+    const TV *V;          // n rows of KP (padded)
+    const float *cg;      // [n] c_j + g_j in FP32 (null: no selection)
+    int64_t base;         // baseline setting
+    float Ebase;          // C_b + G_b in FP32
+    float gamma;
+    TV *T;                // [m, n] or null
+    int32_t *best;        // [m] or null
+    float *saving;        // [m] or null
+};
+template <typename TV> cudaError_t launch_predict_select(const PredictArgs<TV> &a, cudaStream_t st);
+
+// Algorithm 2 on a given dense FP32 matrix.
+cudaError_t launch_select(int64_t m, int64_t n, const float *T, int64_t ld, const float *cg,
+                          int64_t base, float Ebase, float gamma, int32_t *best, float *saving,
+                          cudaStream_t st);
+
+// Objective J and per-row observed RMSE.  part: double[2 * parts] scratch.
+int64_t objective_parts(int64_t m);
+template <typename TV>
+cudaError_t launch_objective(int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
+                             const TV *val, const TV *U, int64_t ldu, int k, const TV *V,
+                             int64_t n, int KP, double lambda, double *part, double *J_out,
+                             float *row_rmse, cudaStream_t st);
+
+// Layout helpers.
+template <typename TV>
+cudaError_t launch_pack_rows(const TV *src, int64_t rows, int64_t lds, int k, TV *dst, int KP,
+                             cudaStream_t st);                    // [rows,k] -> [rows,KP]
+template <typename TV>
+cudaError_t launch_unpack_rows(const TV *src, int64_t rows, int KP, int k, TV *dst,
+                               cudaStream_t st);                  // [rows,KP] -> [rows,k]
+cudaError_t launch_to_bf16(const float *src, int64_t count, void *dst, cudaStream_t st);
+template <typename TV>
+cudaError_t launch_dense_to_csr(const TV *P, int64_t m, int64_t n, int64_t ld, int64_t *ptr,
+                                int32_t *idx, TV *val, cudaStream_t st);
+template <typename TV>
+cudaError_t launch_validate_csr(int64_t m, int64_t n, int64_t nnz, const int64_t *ptr,
+                                const int32_t *idx, const TV *val, int32_t *flag,
+                                cudaStream_t st);
+
+}  // namespace ocf
