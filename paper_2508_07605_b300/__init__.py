@@ -1,0 +1,249 @@
+"""Python binding of ``libopen_cf.so`` (see include/open_cf.h).
+
+Argument marshalling only: tensors are checked for device, dtype and layout,
+their ``data_ptr()`` and the current CUDA stream are passed to the C ABI, and
+outputs are allocated with torch.  Every computation runs in the library's
+CUDA kernels; if the library cannot be loaded the import fails loudly -- there
+is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import buildlib as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+OK, INVALID_ARG, NOT_FITTED, CUDA_ERROR, OUT_OF_MEMORY, UNSUPPORTED, TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+ROW_OK, ROW_NOT_SPD, ROW_EMPTY, ROW_FALLBACK_USED, ROW_BAD_INPUT = 0, 1, 2, 3, 4
+FP64, FP32, BF16_GRAM = 0, 1, 2
+_PRECISION = {"fp64": FP64, "fp32": FP32, "bf16_gram": BF16_GRAM}
+MAX_K = 32
+
+
+class OpenCFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"open_cf error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("lambda_", ctypes.c_double), ("sweeps", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
+                ("cholesky_fp64", ctypes.c_int32), ("n_cpu_caps", ctypes.c_int32),
+                ("n_gpu_caps", ctypes.c_int32),
+                ("cpu_caps_w_host", ctypes.POINTER(ctypes.c_double)),
+                ("gpu_caps_w_host", ctypes.POINTER(ctypes.c_double)),
+                ("device", ctypes.c_int32), ("mlp_fallback_threshold", ctypes.c_float)]
+
+
+_V, _I64, _I32, _F, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_double
+
+_SIGNATURES = {
+    "open_cf_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(_V)]),
+    "open_cf_destroy": (None, [_V]),
+    "open_cf_last_error": (ctypes.c_char_p, [_V]),
+    "open_cf_set_V": (ctypes.c_int, [_V, _V, _I64, _V]),
+    "open_cf_get_V": (ctypes.c_int, [_V, _V, _V]),
+    "open_cf_fit_offline": (ctypes.c_int, [_V, _V, _I64, _I64, _I64, _V, _V, _V]),
+    "open_cf_fit_csr": (ctypes.c_int, [_V, _I64, _I64, _I64, _V, _V, _V, _V, _V, _V, _V, _V]),
+    "open_cf_complete_rows": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _I32, _V]),
+    "open_cf_predict": (ctypes.c_int, [_V, _V, _I64, _V, _V, _V, _F, _I32, _V]),
+    "open_cf_select": (ctypes.c_int, [_V, _V, _I64, _I64, _V, _V, _F, _I32, _V]),
+    "open_cf_objective": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
+    "open_cf_csr_to_csc": (ctypes.c_int, [_V, _I64, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
+    "open_cf_validate_csr": (ctypes.c_int, [_V, _I64, _I64, _I64, _V, _V, _V,
+                                            ctypes.POINTER(_I32), _V]),
+}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    return _build.build(force=force)
+
+
+def lib():
+    """Load libopen_cf.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if not _build.up_to_date():
+            _build.build()
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGNATURES)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class OpenCF:
+    """Handle of the completion engine (open_cf_create / open_cf_destroy)."""
+
+    def __init__(self, k: int, lam: float, sweeps: int = 15, precision: str = "fp32",
+                 cholesky_fp64: bool = False, cpu_caps=None, gpu_caps=None, device: int = 0,
+                 mlp_fallback_threshold: float = 0.02):
+        self._h = ctypes.c_void_p(0)
+        self.k, self.lam, self.sweeps = int(k), float(lam), int(sweeps)
+        self.precision = precision
+        self.device = torch.device("cuda", device)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        cpu = [] if cpu_caps is None else [float(c) for c in cpu_caps]
+        gpu = [] if gpu_caps is None else [float(g) for g in gpu_caps]
+        self._cpu = (ctypes.c_double * max(1, len(cpu)))(*cpu)
+        self._gpu = (ctypes.c_double * max(1, len(gpu)))(*gpu)
+        self.n_cpu, self.n_gpu = len(cpu), len(gpu)
+        cfg = Config(self.k, self.lam, self.sweeps, 0, _PRECISION[precision], int(cholesky_fp64),
+                     len(cpu), len(gpu), ctypes.cast(self._cpu, ctypes.POINTER(ctypes.c_double)),
+                     ctypes.cast(self._gpu, ctypes.POINTER(ctypes.c_double)), device,
+                     float(mlp_fallback_threshold))
+        rc = lib().open_cf_create(ctypes.byref(cfg), ctypes.byref(self._h))
+        if rc != OK:
+            raise OpenCFError(rc, "open_cf_create failed")
+        self.n = None
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().open_cf_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers ---------------------------------------------------------
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _check(self, rc):
+        if rc != OK:
+            raise OpenCFError(rc, lib().open_cf_last_error(self._h).decode())
+
+    def _real(self, t, name):
+        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor on {self.device}")
+        return t
+
+    def _csr(self, row_ptr, col, val):
+        if row_ptr.dtype != torch.int64 or col.dtype != torch.int32:
+            raise ValueError("row_ptr must be int64 and col int32")
+        for t, nm in ((row_ptr, "row_ptr"), (col, "col")):
+            if t.device != self.device or not t.is_contiguous():
+                raise ValueError(f"{nm} must be contiguous on {self.device}")
+        self._real(val, "val")
+        return row_ptr.numel() - 1, col.numel()
+
+    def _empty(self, *shape, dtype=None):
+        return torch.empty(*shape, dtype=dtype or self.dtype, device=self.device)
+
+    # -- API ---------------------------------------------------------------
+    def last_error(self) -> str:
+        return lib().open_cf_last_error(self._h).decode()
+
+    def set_V(self, V):
+        self._real(V, "V")
+        if V.dim() != 2 or V.shape[1] != self.k:
+            raise ValueError("V must be [n, k]")
+        self._check(lib().open_cf_set_V(self._h, _ptr(V), V.shape[0], self._stream()))
+        self.n = V.shape[0]
+
+    def get_V(self):
+        out = self._empty(self.n, self.k)
+        self._check(lib().open_cf_get_V(self._h, _ptr(out), self._stream()))
+        return out
+
+    def fit_offline(self, P, J_hist: bool = False):
+        self._real(P, "P")
+        m, n = P.shape
+        U = self._empty(m, self.k)
+        J = self._empty(2 * self.sweeps, dtype=torch.float64) if J_hist else None
+        self._check(lib().open_cf_fit_offline(self._h, _ptr(P), m, n, P.stride(0), _ptr(U),
+                                              _ptr(J), self._stream()))
+        return (U, J) if J_hist else U
+
+    def fit_csr(self, row_ptr, col, val, n: int, J_hist: bool = False, status: bool = False):
+        m, nnz = self._csr(row_ptr, col, val)
+        U = self._empty(m, self.k)
+        J = self._empty(2 * self.sweeps, dtype=torch.float64) if J_hist else None
+        rs = self._empty(m, dtype=torch.int32) if status else None
+        cs = self._empty(n, dtype=torch.int32) if status else None
+        self._check(lib().open_cf_fit_csr(self._h, m, n, nnz, _ptr(row_ptr), _ptr(col), _ptr(val),
+                                          _ptr(U), _ptr(rs), _ptr(cs), _ptr(J), self._stream()))
+        out = [U]
+        if J_hist:
+            out.append(J)
+        if status:
+            out += [rs, cs]
+        return out[0] if len(out) == 1 else tuple(out)
+
+    def complete_rows(self, row_ptr, col, val, joint: bool = False):
+        m, nnz = self._csr(row_ptr, col, val)
+        U = self._empty(m, self.k)
+        st = self._empty(m, dtype=torch.int32)
+        self._check(lib().open_cf_complete_rows(self._h, m, nnz, _ptr(row_ptr), _ptr(col),
+                                                _ptr(val), _ptr(U), _ptr(st), int(joint),
+                                                self._stream()))
+        return U, st
+
+    def predict(self, U, gamma: float = 0.05, baseline: int = -1, want_T: bool = True,
+                want_select: bool = True):
+        self._real(U, "U")
+        m = U.shape[0]
+        T = self._empty(m, self.n) if want_T else None
+        best = self._empty(m, dtype=torch.int32) if want_select else None
+        sav = self._empty(m, dtype=torch.float32) if want_select else None
+        self._check(lib().open_cf_predict(self._h, _ptr(U), m, _ptr(T), _ptr(best), _ptr(sav),
+                                          float(gamma), int(baseline), self._stream()))
+        return T, best, sav
+
+    def select(self, T, gamma: float = 0.05, baseline: int = -1):
+        if T.dtype != torch.float32 or T.device != self.device or T.stride(1) != 1:
+            raise ValueError("T must be float32 on the device with unit column stride")
+        m = T.shape[0]
+        best = self._empty(m, dtype=torch.int32)
+        sav = self._empty(m, dtype=torch.float32)
+        self._check(lib().open_cf_select(self._h, _ptr(T), m, T.stride(0), _ptr(best), _ptr(sav),
+                                         float(gamma), int(baseline), self._stream()))
+        return best, sav
+
+    def objective(self, row_ptr, col, val, U, row_rmse: bool = False):
+        m, nnz = self._csr(row_ptr, col, val)
+        self._real(U, "U")
+        J = self._empty(1, dtype=torch.float64)
+        rr = self._empty(m, dtype=torch.float32) if row_rmse else None
+        self._check(lib().open_cf_objective(self._h, m, nnz, _ptr(row_ptr), _ptr(col), _ptr(val),
+                                            _ptr(U), _ptr(J), _ptr(rr), self._stream()))
+        return (J, rr) if row_rmse else J
+
+    def csr_to_csc(self, row_ptr, col, val, n: int):
+        m, nnz = self._csr(row_ptr, col, val)
+        cptr = self._empty(n + 1, dtype=torch.int64)
+        ridx = self._empty(max(nnz, 1), dtype=torch.int32)
+        cval = self._empty(max(nnz, 1))
+        self._check(lib().open_cf_csr_to_csc(self._h, m, n, nnz, _ptr(row_ptr), _ptr(col),
+                                             _ptr(val), _ptr(cptr), _ptr(ridx), _ptr(cval),
+                                             self._stream()))
+        return cptr, ridx[:nnz], cval[:nnz]
+
+    def validate_csr(self, row_ptr, col, val, n: int) -> int:
+        m, nnz = self._csr(row_ptr, col, val)
+        res = ctypes.c_int32(-1)
+        self._check(lib().open_cf_validate_csr(self._h, m, n, nnz, _ptr(row_ptr), _ptr(col),
+                                               _ptr(val), ctypes.byref(res), self._stream()))
+        return int(res.value)

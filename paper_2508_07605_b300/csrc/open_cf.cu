@@ -1,0 +1,612 @@
+// Engine behind the open_cf C ABI: the handle owns V, the cap grid, the CSC
+// copy and every workspace, validates arguments on the host, and enqueues the
+// kernels on the caller's stream.  A fit (CSC build + all ALS sweeps + unpack)
+// is captured once into a CUDA graph per argument set and replayed, so a
+// 15-sweep fit costs one graph launch instead of ~35 kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "open_cf.h"
+
+using namespace ocf;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct GraphEntry {
+    std::vector<int64_t> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct open_cf {
+    open_cf_config cfg{};
+    std::vector<double> cpu_caps, gpu_caps;
+    int device = 0;
+    int k = 0, KP = 8;
+    bool f64 = false;
+    size_t esz = 4;           // element size of "real"
+    int64_t n = -1;           // settings (rows of V)
+    bool V_set = false;
+    Buf V, Vb16, cg;          // V: n x KP real; Vb16: BF16 copy; cg: n floats
+    int64_t base_default = -1;
+    // offline block kept for joint refits (CSR of the dense block)
+    Buf off_ptr, off_idx, off_val;
+    int64_t m_off = 0, nnz_off = 0;
+    // workspaces
+    Buf U_w, csc_ptr, csc_idx, csc_val, cnt, tot, part, flag, j_ptr, j_idx, j_val, Ub16;
+    uint64_t generation = 0;  // bumps whenever a workspace moves
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(open_cf_t *h, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    return code;
+}
+
+int cuda_fail(open_cf_t *h, cudaError_t e, const char *where) {
+    cudaGetLastError();  // clear the sticky-free error state of the runtime
+    return fail(h, e == cudaErrorMemoryAllocation ? OPEN_CF_OUT_OF_MEMORY : OPEN_CF_CUDA_ERROR,
+                "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(h, expr)                                             \
+    do {                                                        \
+        cudaError_t e_ = (expr);                                \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #expr); \
+    } while (0)
+
+cudaError_t ensure(open_cf_t *h, Buf &b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return cudaSuccess;
+    size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+    if (b.p) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return e;
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) return e;
+    b.bytes = want;
+    h->generation++;
+    return cudaSuccess;
+}
+
+void free_buf(Buf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Run `enqueue` on `stream` through a cached CUDA graph keyed by `key`.
+template <typename F>
+int run_graph(open_cf_t *h, std::vector<int64_t> key, cudaStream_t stream, F &&enqueue) {
+    key.push_back((int64_t)h->generation);
+    for (auto &g : h->graphs)
+        if (g.key == key) {
+            CK(h, cudaGraphLaunch(g.exec, stream));
+            return OPEN_CF_OK;
+        }
+    if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue(h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "enqueue during capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    if (h->graphs.size() >= 16) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back(GraphEntry{std::move(key), exec});
+    CK(h, cudaGraphLaunch(exec, stream));
+    return OPEN_CF_OK;
+}
+
+// One ALS half-step with the handle's precision.
+template <typename TV>
+cudaError_t half_step(open_cf_t *h, const SolveArgs<TV> &a, cudaStream_t st) {
+    if constexpr (sizeof(TV) == 8) {
+        return launch_row_solve<double, double>(a, h->KP, st);
+    } else {
+        if (h->cfg.cholesky_fp64) return launch_row_solve<float, double>(a, h->KP, st);
+        return launch_row_solve<float, float>(a, h->KP, st);
+    }
+}
+
+int check_csr_args(open_cf_t *h, int64_t m, int64_t nnz, const void *ptr, const void *idx,
+                   const void *val) {
+    if (m < 0 || nnz < 0) return fail(h, OPEN_CF_INVALID_ARG, "negative m or nnz");
+    if (m > 0 && !ptr) return fail(h, OPEN_CF_INVALID_ARG, "row_ptr is NULL");
+    if (nnz > 0 && (!idx || !val)) return fail(h, OPEN_CF_INVALID_ARG, "col or val is NULL");
+    if (nnz > INT64_C(0x7fffffff) * 64) return fail(h, OPEN_CF_UNSUPPORTED, "nnz too large");
+    return OPEN_CF_OK;
+}
+
+// ALS sweeps on a CSR matrix (rows m, columns n == h->n) starting from h->V.
+template <typename TV>
+int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
+               const TV *val, TV *U_out, int64_t u_row0, int64_t u_rows, int32_t *row_status,
+               int32_t *col_status, double *J_hist, cudaStream_t stream) {
+    const int64_t n = h->n;
+    const int KP = h->KP;
+    const int64_t nb = csc_blocks(m, n, nnz);
+    CK(h, ensure(h, h->U_w, sizeof(TV) * std::max<int64_t>(m, 1) * KP));
+    CK(h, ensure(h, h->csc_ptr, sizeof(int64_t) * (n + 1)));
+    CK(h, ensure(h, h->csc_idx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    CK(h, ensure(h, h->csc_val, sizeof(TV) * std::max<int64_t>(nnz, 1)));
+    CK(h, ensure(h, h->cnt, sizeof(int32_t) * n * nb));
+    CK(h, ensure(h, h->tot, sizeof(int64_t) * n));
+    CK(h, ensure(h, h->part, sizeof(double) * 2 * objective_parts(std::max<int64_t>(m, n))));
+    TV *Uw = (TV *)h->U_w.p;
+    TV *V = (TV *)h->V.p;
+    int64_t *cptr = (int64_t *)h->csc_ptr.p;
+    int32_t *cidx = (int32_t *)h->csc_idx.p;
+    TV *cval = (TV *)h->csc_val.p;
+    const int sweeps = h->cfg.sweeps;
+    const int k = h->k;
+    const double lam = h->cfg.lambda;
+    auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(Uw, 0, sizeof(TV) * m * KP, st);
+        if (e != cudaSuccess) return e;
+        e = launch_csr_to_csc<TV>(m, n, nnz, ptr, idx, val, cptr, cidx, cval, (int32_t *)h->cnt.p,
+                                  (int64_t *)h->tot.p, nb, st);
+        if (e != cudaSuccess) return e;
+        for (int s = 0; s < sweeps; ++s) {
+            SolveArgs<TV> ua{m, nnz, ptr, idx, val, V, n, Uw, KP, KP, row_status, lam};
+            if ((e = half_step<TV>(h, ua, st)) != cudaSuccess) return e;
+            if (J_hist &&
+                (e = launch_objective<TV>(m, nnz, ptr, idx, val, Uw, KP, k, V, n, KP, lam,
+                                          (double *)h->part.p, J_hist + 2 * s, nullptr, st)) !=
+                    cudaSuccess)
+                return e;
+            SolveArgs<TV> va{n, nnz, cptr, cidx, cval, Uw, m, V, KP, KP, col_status, lam};
+            if ((e = half_step<TV>(h, va, st)) != cudaSuccess) return e;
+            if (J_hist &&
+                (e = launch_objective<TV>(m, nnz, ptr, idx, val, Uw, KP, k, V, n, KP, lam,
+                                          (double *)h->part.p, J_hist + 2 * s + 1, nullptr,
+                                          st)) != cudaSuccess)
+                return e;
+        }
+        if (U_out && u_rows > 0)
+            return launch_unpack_rows<TV>(Uw + u_row0 * KP, u_rows, KP, k, U_out, st);
+        return cudaSuccess;
+    };
+    std::vector<int64_t> key = {1,
+                                m,
+                                nnz,
+                                (int64_t)ptr,
+                                (int64_t)idx,
+                                (int64_t)val,
+                                (int64_t)U_out,
+                                u_row0,
+                                u_rows,
+                                (int64_t)row_status,
+                                (int64_t)col_status,
+                                (int64_t)J_hist};
+    return run_graph(h, key, stream, enqueue);
+}
+
+template <typename TV> TV *as(const void *p) { return (TV *)p; }
+
+}  // namespace
+
+extern "C" {
+
+int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
+    if (!cfg || !out) return OPEN_CF_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->k < 1 || cfg->k > OPEN_CF_MAX_K) return OPEN_CF_UNSUPPORTED;
+    if (!(cfg->lambda > 0.0) || !std::isfinite(cfg->lambda)) return OPEN_CF_INVALID_ARG;
+    if (cfg->sweeps < 0) return OPEN_CF_INVALID_ARG;
+    if (cfg->precision != OPEN_CF_FP64 && cfg->precision != OPEN_CF_FP32 &&
+        cfg->precision != OPEN_CF_BF16_GRAM)
+        return OPEN_CF_INVALID_ARG;
+    if (cfg->precision == OPEN_CF_BF16_GRAM) return OPEN_CF_UNSUPPORTED;
+    if (cfg->n_cpu_caps < 0 || cfg->n_gpu_caps < 0 ||
+        ((cfg->n_cpu_caps > 0) != (cfg->n_gpu_caps > 0)))
+        return OPEN_CF_INVALID_ARG;
+    if (cfg->n_cpu_caps > 0 && (!cfg->cpu_caps_w_host || !cfg->gpu_caps_w_host))
+        return OPEN_CF_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return OPEN_CF_UNSUPPORTED;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, cfg->device) != cudaSuccess) return OPEN_CF_CUDA_ERROR;
+    if (!(prop.major == 10 && prop.minor == 3)) return OPEN_CF_UNSUPPORTED;
+
+    open_cf_t *h = new open_cf();
+    h->cfg = *cfg;
+    h->device = cfg->device;
+    h->k = cfg->k;
+    h->KP = padded_k(cfg->k);
+    h->f64 = cfg->precision == OPEN_CF_FP64;
+    h->esz = h->f64 ? 8 : 4;
+    if (cfg->n_cpu_caps > 0) {
+        h->cpu_caps.assign(cfg->cpu_caps_w_host, cfg->cpu_caps_w_host + cfg->n_cpu_caps);
+        h->gpu_caps.assign(cfg->gpu_caps_w_host, cfg->gpu_caps_w_host + cfg->n_gpu_caps);
+        for (double c : h->cpu_caps)
+            if (!std::isfinite(c)) { delete h; return OPEN_CF_INVALID_ARG; }
+        for (double g : h->gpu_caps)
+            if (!std::isfinite(g)) { delete h; return OPEN_CF_INVALID_ARG; }
+        h->cfg.cpu_caps_w_host = nullptr;
+        h->cfg.gpu_caps_w_host = nullptr;
+        const int64_t ci = std::max_element(h->cpu_caps.begin(), h->cpu_caps.end()) -
+                           h->cpu_caps.begin();
+        const int64_t gi = std::max_element(h->gpu_caps.begin(), h->gpu_caps.end()) -
+                           h->gpu_caps.begin();
+        h->base_default = ci * cfg->n_gpu_caps + gi;
+    }
+    DeviceGuard g(h->device);
+    if (prepare_csr_to_csc(50000) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return OPEN_CF_CUDA_ERROR;
+    }
+    *out = h;
+    return OPEN_CF_OK;
+}
+
+void open_cf_destroy(open_cf_t *h) {
+    if (!h) return;
+    {
+        DeviceGuard g(h->device);
+        cudaDeviceSynchronize();
+        for (auto &ge : h->graphs) cudaGraphExecDestroy(ge.exec);
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+        for (Buf *b : {&h->V, &h->Vb16, &h->cg, &h->off_ptr, &h->off_idx, &h->off_val, &h->U_w,
+                       &h->csc_ptr, &h->csc_idx, &h->csc_val, &h->cnt, &h->tot, &h->part,
+                       &h->flag, &h->j_ptr, &h->j_idx, &h->j_val, &h->Ub16})
+            free_buf(*b);
+    }
+    delete h;
+}
+
+const char *open_cf_last_error(const open_cf_t *h) { return h ? h->err.c_str() : ""; }
+
+int open_cf_set_V(open_cf_t *h, const void *V, int64_t n, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!V || n <= 0) return fail(h, OPEN_CF_INVALID_ARG, "V is NULL or n <= 0");
+    if (n > 50000) return fail(h, OPEN_CF_UNSUPPORTED, "n = %lld settings exceeds 50000",
+                               (long long)n);
+    if (!h->cpu_caps.empty() && n != (int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size())
+        return fail(h, OPEN_CF_INVALID_ARG, "n = %lld != n_cpu_caps * n_gpu_caps", (long long)n);
+    DeviceGuard g(h->device);
+    CK(h, ensure(h, h->V, h->esz * n * h->KP));
+    cudaStream_t st = S(stream);
+    if (h->f64)
+        CK(h, launch_pack_rows<double>(as<double>(V), n, h->k, h->k, (double *)h->V.p, h->KP, st));
+    else
+        CK(h, launch_pack_rows<float>(as<float>(V), n, h->k, h->k, (float *)h->V.p, h->KP, st));
+    if (!h->cpu_caps.empty() && h->n != n) {
+        std::vector<float> cg(n);
+        const int ng = (int)h->gpu_caps.size();
+        for (int64_t j = 0; j < n; ++j)
+            cg[j] = (float)h->cpu_caps[j / ng] + (float)h->gpu_caps[j % ng];
+        CK(h, ensure(h, h->cg, sizeof(float) * n));
+        CK(h, cudaMemcpyAsync(h->cg.p, cg.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+        CK(h, cudaStreamSynchronize(st));  // host vector goes out of scope
+    }
+    h->n = n;
+    h->V_set = true;
+    return OPEN_CF_OK;
+}
+
+int open_cf_get_V(open_cf_t *h, void *V_out, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "V was never set");
+    if (!V_out) return fail(h, OPEN_CF_INVALID_ARG, "V_out is NULL");
+    DeviceGuard g(h->device);
+    if (h->f64)
+        CK(h, launch_unpack_rows<double>((double *)h->V.p, h->n, h->KP, h->k, (double *)V_out,
+                                         S(stream)));
+    else
+        CK(h, launch_unpack_rows<float>((float *)h->V.p, h->n, h->KP, h->k, (float *)V_out,
+                                        S(stream)));
+    return OPEN_CF_OK;
+}
+
+int open_cf_fit_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                    const int32_t *col, const void *val, void *U_out, int32_t *row_status,
+                    int32_t *col_status, double *J_hist, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "set the initial V before a fit");
+    if (n != h->n) return fail(h, OPEN_CF_INVALID_ARG, "n = %lld but V has %lld rows",
+                               (long long)n, (long long)h->n);
+    DeviceGuard g(h->device);
+    if (h->f64)
+        return fit_sweeps<double>(h, m, nnz, row_ptr, col, as<double>(val), (double *)U_out, 0,
+                                  m, row_status, col_status, J_hist, S(stream));
+    return fit_sweeps<float>(h, m, nnz, row_ptr, col, as<float>(val), (float *)U_out, 0, m,
+                             row_status, col_status, J_hist, S(stream));
+}
+
+int open_cf_fit_offline(open_cf_t *h, const void *P, int64_t m_off, int64_t n, int64_t ld,
+                        void *U_out, double *J_hist, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!P || m_off <= 0 || n <= 0 || ld < n)
+        return fail(h, OPEN_CF_INVALID_ARG, "bad dense block (P, m_off, n, ld)");
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "set the initial V before a fit");
+    if (n != h->n) return fail(h, OPEN_CF_INVALID_ARG, "n = %lld but V has %lld rows",
+                               (long long)n, (long long)h->n);
+    if (m_off * n > INT64_C(0x7fffffff) * 8)
+        return fail(h, OPEN_CF_UNSUPPORTED, "dense block too large");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const int64_t nnz = m_off * n;
+    CK(h, ensure(h, h->off_ptr, sizeof(int64_t) * (m_off + 1)));
+    CK(h, ensure(h, h->off_idx, sizeof(int32_t) * nnz));
+    CK(h, ensure(h, h->off_val, h->esz * nnz));
+    h->m_off = 0;
+    if (h->f64)
+        CK(h, launch_dense_to_csr<double>(as<double>(P), m_off, n, ld, (int64_t *)h->off_ptr.p,
+                                          (int32_t *)h->off_idx.p, (double *)h->off_val.p, st));
+    else
+        CK(h, launch_dense_to_csr<float>(as<float>(P), m_off, n, ld, (int64_t *)h->off_ptr.p,
+                                         (int32_t *)h->off_idx.p, (float *)h->off_val.p, st));
+    int rc;
+    if (h->f64)
+        rc = fit_sweeps<double>(h, m_off, nnz, (int64_t *)h->off_ptr.p, (int32_t *)h->off_idx.p,
+                                (double *)h->off_val.p, (double *)U_out, 0, m_off, nullptr,
+                                nullptr, J_hist, st);
+    else
+        rc = fit_sweeps<float>(h, m_off, nnz, (int64_t *)h->off_ptr.p, (int32_t *)h->off_idx.p,
+                               (float *)h->off_val.p, (float *)U_out, 0, m_off, nullptr, nullptr,
+                               J_hist, st);
+    if (rc == OPEN_CF_OK) {
+        h->m_off = m_off;
+        h->nnz_off = nnz;
+    }
+    return rc;
+}
+
+namespace {
+__global__ void k_offset_copy(const int64_t *__restrict__ src, int64_t count, int64_t add,
+                              int64_t *__restrict__ dst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[e] + add;
+}
+}  // namespace
+
+int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_t *row_ptr,
+                          const int32_t *col, const void *val, void *U_out, int32_t *status,
+                          int32_t joint, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = check_csr_args(h, m_new, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: fit or set V first");
+    if (m_new > 0 && !U_out) return fail(h, OPEN_CF_INVALID_ARG, "U_out is NULL");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    if (!joint) {
+        if (h->f64) {
+            SolveArgs<double> a{m_new, nnz, row_ptr, col, as<double>(val), (double *)h->V.p,
+                                h->n, (double *)U_out, h->k, h->k, status, h->cfg.lambda};
+            CK(h, half_step<double>(h, a, st));
+        } else {
+            SolveArgs<float> a{m_new, nnz, row_ptr, col, as<float>(val), (float *)h->V.p,
+                               h->n, (float *)U_out, h->k, h->k, status, h->cfg.lambda};
+            CK(h, half_step<float>(h, a, st));
+        }
+        return OPEN_CF_OK;
+    }
+    // joint: [offline block ; new rows] as one CSR in handle workspaces
+    const int64_t m = h->m_off + m_new, nz = h->nnz_off + nnz;
+    CK(h, ensure(h, h->j_ptr, sizeof(int64_t) * (m + 1)));
+    CK(h, ensure(h, h->j_idx, sizeof(int32_t) * std::max<int64_t>(nz, 1)));
+    CK(h, ensure(h, h->j_val, h->esz * std::max<int64_t>(nz, 1)));
+    int64_t *jp = (int64_t *)h->j_ptr.p;
+    if (h->m_off > 0) {
+        CK(h, cudaMemcpyAsync(jp, h->off_ptr.p, sizeof(int64_t) * h->m_off,
+                              cudaMemcpyDeviceToDevice, st));
+        CK(h, cudaMemcpyAsync(h->j_idx.p, h->off_idx.p, sizeof(int32_t) * h->nnz_off,
+                              cudaMemcpyDeviceToDevice, st));
+        CK(h, cudaMemcpyAsync(h->j_val.p, h->off_val.p, h->esz * h->nnz_off,
+                              cudaMemcpyDeviceToDevice, st));
+    }
+    k_offset_copy<<<(unsigned)std::min<int64_t>((m_new + 256) / 256 + 1, 4096), 256, 0, st>>>(
+        row_ptr, m_new + 1, h->nnz_off, jp + h->m_off);
+    CK(h, cudaGetLastError());
+    if (nnz > 0) {
+        CK(h, cudaMemcpyAsync((int32_t *)h->j_idx.p + h->nnz_off, col, sizeof(int32_t) * nnz,
+                              cudaMemcpyDeviceToDevice, st));
+        CK(h, cudaMemcpyAsync((char *)h->j_val.p + h->esz * h->nnz_off, val, h->esz * nnz,
+                              cudaMemcpyDeviceToDevice, st));
+    }
+    if (status && m_new > 0) CK(h, cudaMemsetAsync(status, 0, sizeof(int32_t) * m_new, st));
+    if (h->f64)
+        return fit_sweeps<double>(h, m, nz, jp, (int32_t *)h->j_idx.p, (double *)h->j_val.p,
+                                  (double *)U_out, h->m_off, m_new, nullptr, nullptr, nullptr,
+                                  st);
+    return fit_sweeps<float>(h, m, nz, jp, (int32_t *)h->j_idx.p, (float *)h->j_val.p,
+                             (float *)U_out, h->m_off, m_new, nullptr, nullptr, nullptr, st);
+}
+
+int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t *best,
+                    float *saving, float gamma, int32_t baseline_setting, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: fit or set V first");
+    if (m < 0 || (m > 0 && !U)) return fail(h, OPEN_CF_INVALID_ARG, "bad U or m");
+    const bool sel = best || saving;
+    if (sel && h->cpu_caps.empty())
+        return fail(h, OPEN_CF_INVALID_ARG, "selection needs a cap grid");
+    if (!std::isfinite(gamma)) return fail(h, OPEN_CF_INVALID_ARG, "gamma is not finite");
+    int64_t base = baseline_setting < 0 ? h->base_default : baseline_setting;
+    if (sel && (base < 0 || base >= h->n))
+        return fail(h, OPEN_CF_INVALID_ARG, "baseline setting out of range");
+    float Eb = 0.0f;
+    if (sel) {
+        const int ng = (int)h->gpu_caps.size();
+        Eb = (float)h->cpu_caps[base / ng] + (float)h->gpu_caps[base % ng];
+    }
+    DeviceGuard g(h->device);
+    if (h->f64) {
+        PredictArgs<double> a{m, h->n, h->KP, h->k, as<double>(U), h->k, (double *)h->V.p,
+                              sel ? (float *)h->cg.p : nullptr, base, Eb, gamma,
+                              (double *)T_out, best, saving};
+        CK(h, launch_predict_select<double>(a, S(stream)));
+    } else {
+        PredictArgs<float> a{m, h->n, h->KP, h->k, as<float>(U), h->k, (float *)h->V.p,
+                             sel ? (float *)h->cg.p : nullptr, base, Eb, gamma, (float *)T_out,
+                             best, saving};
+        CK(h, launch_predict_select<float>(a, S(stream)));
+    }
+    return OPEN_CF_OK;
+}
+
+int open_cf_select(open_cf_t *h, const float *T, int64_t m, int64_t ld, int32_t *best,
+                   float *saving, float gamma, int32_t baseline_setting, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (h->cpu_caps.empty()) return fail(h, OPEN_CF_INVALID_ARG, "selection needs a cap grid");
+    const int64_t n = (int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size();
+    if (m < 0 || (m > 0 && !T) || ld < n) return fail(h, OPEN_CF_INVALID_ARG, "bad T, m or ld");
+    if (!std::isfinite(gamma)) return fail(h, OPEN_CF_INVALID_ARG, "gamma is not finite");
+    int64_t base = baseline_setting < 0 ? h->base_default : baseline_setting;
+    if (base < 0 || base >= n) return fail(h, OPEN_CF_INVALID_ARG, "baseline out of range");
+    DeviceGuard g(h->device);
+    if (h->n != n) {
+        std::vector<float> cg(n);
+        const int ng = (int)h->gpu_caps.size();
+        for (int64_t j = 0; j < n; ++j)
+            cg[j] = (float)h->cpu_caps[j / ng] + (float)h->gpu_caps[j % ng];
+        CK(h, ensure(h, h->cg, sizeof(float) * n));
+        CK(h, cudaMemcpy(h->cg.p, cg.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+    }
+    const int ng = (int)h->gpu_caps.size();
+    const float Eb = (float)h->cpu_caps[base / ng] + (float)h->gpu_caps[base % ng];
+    CK(h, launch_select(m, n, T, ld, (float *)h->cg.p, base, Eb, gamma, best, saving,
+                        S(stream)));
+    return OPEN_CF_OK;
+}
+
+int open_cf_objective(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                      const int32_t *col, const void *val, const void *U, double *J_out,
+                      float *row_rmse, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: fit or set V first");
+    if (!J_out || (m > 0 && !U)) return fail(h, OPEN_CF_INVALID_ARG, "J_out or U is NULL");
+    DeviceGuard g(h->device);
+    CK(h, ensure(h, h->part, sizeof(double) * 2 * objective_parts(std::max<int64_t>(m, 1))));
+    if (h->f64)
+        CK(h, launch_objective<double>(m, nnz, row_ptr, col, as<double>(val), as<double>(U), h->k,
+                                       h->k, (double *)h->V.p, h->n, h->KP, h->cfg.lambda,
+                                       (double *)h->part.p, J_out, row_rmse, S(stream)));
+    else
+        CK(h, launch_objective<float>(m, nnz, row_ptr, col, as<float>(val), as<float>(U), h->k,
+                                      h->k, (float *)h->V.p, h->n, h->KP, h->cfg.lambda,
+                                      (double *)h->part.p, J_out, row_rmse, S(stream)));
+    return OPEN_CF_OK;
+}
+
+int open_cf_csr_to_csc(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                       const int32_t *col, const void *val, int64_t *col_ptr, int32_t *row_idx,
+                       void *cval, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (n <= 0 || !col_ptr || (nnz > 0 && (!row_idx || !cval)))
+        return fail(h, OPEN_CF_INVALID_ARG, "bad n or output arrays");
+    if (n > 50000) return fail(h, OPEN_CF_UNSUPPORTED, "n exceeds 50000 columns");
+    DeviceGuard g(h->device);
+    const int64_t nb = csc_blocks(m, n, nnz);
+    CK(h, ensure(h, h->cnt, sizeof(int32_t) * n * nb));
+    CK(h, ensure(h, h->tot, sizeof(int64_t) * n));
+    if (h->f64)
+        CK(h, launch_csr_to_csc<double>(m, n, nnz, row_ptr, col, as<double>(val), col_ptr, row_idx,
+                                        (double *)cval, (int32_t *)h->cnt.p,
+                                        (int64_t *)h->tot.p, nb, S(stream)));
+    else
+        CK(h, launch_csr_to_csc<float>(m, n, nnz, row_ptr, col, as<float>(val), col_ptr, row_idx,
+                                       (float *)cval, (int32_t *)h->cnt.p, (int64_t *)h->tot.p,
+                                       nb, S(stream)));
+    return OPEN_CF_OK;
+}
+
+int open_cf_validate_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                         const int32_t *col, const void *val, int32_t *result_host,
+                         void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (!result_host || n <= 0) return fail(h, OPEN_CF_INVALID_ARG, "bad result pointer or n");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    CK(h, ensure(h, h->flag, sizeof(int32_t)));
+    CK(h, cudaMemsetAsync(h->flag.p, 0x7f, sizeof(int32_t), st));
+    if (h->f64)
+        CK(h, launch_validate_csr<double>(m, n, nnz, row_ptr, col, as<double>(val),
+                                          (int32_t *)h->flag.p, st));
+    else
+        CK(h, launch_validate_csr<float>(m, n, nnz, row_ptr, col, as<float>(val),
+                                         (int32_t *)h->flag.p, st));
+    int32_t f = 0;
+    CK(h, cudaMemcpyAsync(&f, h->flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    *result_host = (f == 0x7f7f7f7f) ? 0 : f;
+    return OPEN_CF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,38 @@
+"""Helpers shared by the GPU parity tests: device copies of synthetic inputs
+and the error measures the tolerances are stated in."""
+import numpy as np
+import torch
+
+DEV = torch.device("cuda", 0)
+
+# Tolerances (per-row relative 2-norm error against the FP64 oracle fed the
+# identical inputs).  FP32: the gate the method's FP32 path is held to;
+# FP64: rounding of a k x k Cholesky with modest condition numbers.
+TOL_FP32 = 1e-5
+TOL_FP64 = 1e-12
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device=DEV, dtype=dtype)
+
+
+def csr_dev(row_ptr, col, val, dtype):
+    return dev(row_ptr, torch.int64), dev(col, torch.int32), dev(val, dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def row_rel_err(gpu, ref, floor=1e-30):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    num = np.linalg.norm(gpu - ref, axis=1)
+    den = np.maximum(np.linalg.norm(ref, axis=1), floor)
+    return num / den
+
+
+def rounded(a, dtype):
+    """The values a kernel of the given precision actually sees, as FP64."""
+    return np.asarray(a, dtype=np.float32 if dtype == torch.float32 else np.float64).astype(
+        np.float64)
