@@ -34,6 +34,7 @@ cudaError_t launch_csr_to_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *
                               const int32_t *idx, const TV *val, int64_t *cptr, int32_t *ridx,
                               TV *cval, int32_t *cnt, int64_t *tot, int64_t nb, cudaStream_t st);
 cudaError_t prepare_csr_to_csc(int64_t n_max);
+cudaError_t prepare_row_solve();
 
 // Reconstruction T = U V^T fused with Algorithm 2.
 template <typename TV> struct PredictArgs {

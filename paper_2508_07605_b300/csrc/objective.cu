@@ -13,8 +13,8 @@ namespace ocf {
 constexpr int OBJ_WARPS = 8;
 
 int64_t objective_parts(int64_t m) {
-    int64_t g = (m + 63) / 64;
-    if (g > NUM_SMS_HINT * 8) g = NUM_SMS_HINT * 8;
+    int64_t g = (m + 7) / 8;
+    if (g > NUM_SMS_HINT * 16) g = NUM_SMS_HINT * 16;
     if (g < 1) g = 1;
     return g;
 }

@@ -286,7 +286,7 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
         h->base_default = ci * cfg->n_gpu_caps + gi;
     }
     DeviceGuard g(h->device);
-    if (prepare_csr_to_csc(50000) != cudaSuccess) {
+    if (prepare_csr_to_csc(50000) != cudaSuccess || prepare_row_solve() != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return OPEN_CF_CUDA_ERROR;

@@ -55,7 +55,7 @@ __device__ __forceinline__ Cand shfl_cand(const Cand &c, int off) {
     return o;
 }
 
-constexpr int BM = 64, BN = 64, PT = 256;
+constexpr int PT = 256;
 
 template <typename TV>
 __device__ __forceinline__ void load4(const TV *p, TV (&x)[4]) {
@@ -72,14 +72,21 @@ __device__ __forceinline__ void load4(const TV *p, TV (&x)[4]) {
 // T[i][j] = sum_p U[i][p] V[j][p] as one FMA chain in p order (in TV), then
 // the selection on float(T).  The baseline runtime uses the identical chain so
 // that t_b equals T[i][base] bit for bit and the baseline's loss is exactly 0.
-template <typename TV, int KP>
+// Tile: BM rows x BN settings per step, 256 threads as TY x TX with TY = BM/4
+// (each thread a 4 x 4 micro-tile); BM = 16 keeps enough CTAs in flight when
+// there are few rows, BM = 64 reuses each V tile over more rows when there
+// are many.
+template <typename TV, int KP, int BM>
 __global__ void __launch_bounds__(PT) k_predict_select(PredictArgs<TV> a) {
+    constexpr int TY = BM / 4, TX = PT / TY, BN = 4 * TX;
+    constexpr int WPR = TX > 32 ? TX / 32 : 1;       // warps sharing one row group
     __shared__ __align__(16) TV Us[KP][BM];
     __shared__ __align__(16) TV Vs[KP][BN + 4];
     __shared__ float cgs[BN];
     __shared__ float tbs[BM];
+    __shared__ Cand xw[TY][WPR][4];
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;       // 16 x 16 threads
+    const int tx = tid % TX, ty = tid / TX;
     const bool sel = a.cg != nullptr;
     const int64_t row_tiles = (a.m + BM - 1) / BM;
     const bool vec_store = sizeof(TV) == 4 && (a.n & 3) == 0 &&
@@ -114,7 +121,8 @@ __global__ void __launch_bounds__(PT) k_predict_select(PredictArgs<TV> a) {
                 const int64_t j = c0 + jj;
                 Vs[p][jj] = (j < a.n) ? a.V[j * KP + p] : TV(0);
             }
-            if (sel && tid < BN) cgs[tid] = (c0 + tid < a.n) ? a.cg[c0 + tid] : 0.0f;
+            if (sel)
+                for (int e = tid; e < BN; e += PT) cgs[e] = (c0 + e < a.n) ? a.cg[c0 + e] : 0.0f;
             __syncthreads();
             TV acc[4][4];
 #pragma unroll
@@ -159,34 +167,58 @@ __global__ void __launch_bounds__(PT) k_predict_select(PredictArgs<TV> a) {
             }
         }
         if (sel) {
+            constexpr int LANES = TX < 32 ? TX : 32;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
 #pragma unroll
-                for (int off = 1; off < 16; off <<= 1) {
+                for (int off = 1; off < LANES; off <<= 1) {
                     const Cand o = shfl_cand(best[r], off);
                     if (better(o, best[r])) best[r] = o;
                 }
-                const int64_t i = r0 + ty * 4 + r;
-                if (tx == 0 && i < a.m) {
-                    if (a.best) a.best[i] = best[r].j;
-                    if (a.saving) a.saving[i] = best[r].j >= 0 ? best[r].sv : 0.0f;
+            }
+            if constexpr (WPR > 1) {
+                const int wr = (tid % TX) / 32;
+                if ((tid & 31) == 0)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) xw[ty][wr][r] = best[r];
+                __syncthreads();
+                if (tx == 0)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        for (int w = 1; w < WPR; ++w)
+                            if (better(xw[ty][w][r], best[r])) best[r] = xw[ty][w][r];
+            }
+            if (tx == 0) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int64_t i = r0 + ty * 4 + r;
+                    if (i < a.m) {
+                        if (a.best) a.best[i] = best[r].j;
+                        if (a.saving) a.saving[i] = best[r].j >= 0 ? best[r].sv : 0.0f;
+                    }
                 }
             }
         }
     }
 }
 
-template <typename TV> cudaError_t launch_predict_select(const PredictArgs<TV> &a, cudaStream_t st) {
-    if (a.m <= 0 || a.n <= 0) return cudaSuccess;
+template <typename TV, int BM>
+static cudaError_t launch_bm(const PredictArgs<TV> &a, cudaStream_t st) {
     int64_t blocks = (a.m + BM - 1) / BM;
     if (blocks > NUM_SMS_HINT * 16) blocks = NUM_SMS_HINT * 16;
     switch (a.KP) {
-        case 8: k_predict_select<TV, 8><<<(unsigned)blocks, PT, 0, st>>>(a); break;
-        case 16: k_predict_select<TV, 16><<<(unsigned)blocks, PT, 0, st>>>(a); break;
-        case 32: k_predict_select<TV, 32><<<(unsigned)blocks, PT, 0, st>>>(a); break;
+        case 8: k_predict_select<TV, 8, BM><<<(unsigned)blocks, PT, 0, st>>>(a); break;
+        case 16: k_predict_select<TV, 16, BM><<<(unsigned)blocks, PT, 0, st>>>(a); break;
+        case 32: k_predict_select<TV, 32, BM><<<(unsigned)blocks, PT, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <typename TV> cudaError_t launch_predict_select(const PredictArgs<TV> &a, cudaStream_t st) {
+    if (a.m <= 0 || a.n <= 0) return cudaSuccess;
+    if (sizeof(TV) == 4 && (a.m + 63) / 64 < 2 * NUM_SMS_HINT) return launch_bm<TV, 16>(a, st);
+    return launch_bm<TV, 64>(a, st);
 }
 
 template cudaError_t launch_predict_select<float>(const PredictArgs<float> &, cudaStream_t);

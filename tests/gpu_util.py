@@ -36,3 +36,28 @@ def rounded(a, dtype):
     """The values a kernel of the given precision actually sees, as FP64."""
     return np.asarray(a, dtype=np.float32 if dtype == torch.float32 else np.float64).astype(
         np.float64)
+
+
+def solve_err(gpu, ref, F, ptr, col, val, lam):
+    """Per-row error of ridge solves, scaled by what FP32 rounding can reach.
+
+    Dividing by |u_ref| alone overstates the error when the right-hand side
+    sum b = sum_t r_t f_t cancels (u tiny next to its terms): its rounding
+    error is ~eps * sum_t |r_t| |f_t|, carried through A^{-1}.  The scale is
+    max(|u_ref|, |A^{-1}|_2 * |sum_t |r_t| |f_t||)."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    out = np.zeros(len(ref))
+    k = F.shape[1]
+    for i in range(len(ref)):
+        c = col[ptr[i]:ptr[i + 1]]
+        r = val[ptr[i]:ptr[i + 1]]
+        if len(c) == 0:
+            out[i] = np.linalg.norm(gpu[i])
+            continue
+        A = F[c].T @ F[c] + lam * np.eye(k)
+        babs = (np.abs(r)[:, None] * np.abs(F[c])).sum(0)
+        scale = max(np.linalg.norm(ref[i]), np.linalg.norm(np.linalg.inv(A), 2) *
+                    np.linalg.norm(babs))
+        out[i] = np.linalg.norm(gpu[i] - ref[i]) / max(scale, 1e-300)
+    return out
