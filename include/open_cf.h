@@ -182,6 +182,37 @@ int open_cf_validate_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const 
                          const int32_t *col, const void *val, int32_t *result_host,
                          void *stream);
 
+/* Allocation-free CSR -> CSC (no counterpart in the paper; a service of this
+ * library).  Some callers cannot allocate device memory: their host framework
+ * owns every device allocation through its own pool and forbids direct
+ * cudaMalloc, their latency path cannot absorb the device-wide
+ * synchronisation of cudaMalloc/cudaFree, or they run under a fixed memory
+ * budget set at start-up.  This call performs the same stable counting sort as
+ * open_cf_csr_to_csc on FP32 values, needs no handle and allocates nothing:
+ * its scratch (column totals and per-row-block column counters) is one
+ * file-scope device array of OPEN_CF_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading this library holds until the process exits.  The caller still
+ * provides every input and output (device pointers on the current device):
+ * row_ptr int64[m+1], col int32[nnz], val float[nnz]; col_ptr int64[n+1],
+ * row_idx int32[nnz], cval float[nnz].
+ *  - The first call on a device looks up the array's device address and sets
+ *    the kernels' shared-memory limit; make that first call before any stream
+ *    capture begins.
+ *  - All calls share the one array, so calls whose work overlaps on the GPU
+ *    (different streams, or different host threads) race and corrupt each
+ *    other's results; serialise them.  Each call overwrites every counter it
+ *    reads, so nothing has to be cleared between calls.
+ *  - n > OPEN_CF_NOALLOC_MAX_COLUMNS returns OPEN_CF_UNSUPPORTED (the column
+ *    totals plus one block of counters no longer fit the array); the outputs
+ *    are then left untouched.  Bad sizes or NULL pointers return
+ *    OPEN_CF_INVALID_ARG; a CUDA failure returns OPEN_CF_CUDA_ERROR.
+ * Work is enqueued on `stream` (NULL = legacy default stream). */
+#define OPEN_CF_NOALLOC_SCRATCH_BYTES (256 * 1024)
+#define OPEN_CF_NOALLOC_MAX_COLUMNS 21824 /* largest n with 8n (rounded up to 256) + 4n <= 256 KiB */
+int open_cf_csr_to_csc_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                               const int32_t *col, const float *val, int64_t *col_ptr,
+                               int32_t *row_idx, float *cval, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

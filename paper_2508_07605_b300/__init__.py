@@ -58,6 +58,7 @@ _SIGNATURES = {
     "open_cf_csr_to_csc": (ctypes.c_int, [_V, _I64, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
     "open_cf_validate_csr": (ctypes.c_int, [_V, _I64, _I64, _I64, _V, _V, _V,
                                             ctypes.POINTER(_I32), _V]),
+    "open_cf_csr_to_csc_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
 }
 
 _lib = None
