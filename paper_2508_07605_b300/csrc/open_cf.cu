@@ -155,6 +155,7 @@ cudaError_t half_step(open_cf_t *h, const SolveArgs<TV> &a, cudaStream_t st) {
     if constexpr (sizeof(TV) == 8) {
         return launch_row_solve<double, double>(a, h->KP, st);
     } else {
+        if (h->KP >= 16) return launch_row_solve_tc(a, h->KP, h->cfg.cholesky_fp64 != 0, st);
         if (h->cfg.cholesky_fp64) return launch_row_solve<float, double>(a, h->KP, st);
         return launch_row_solve<float, float>(a, h->KP, st);
     }
@@ -286,7 +287,8 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
         h->base_default = ci * cfg->n_gpu_caps + gi;
     }
     DeviceGuard g(h->device);
-    if (prepare_csr_to_csc(50000) != cudaSuccess || prepare_row_solve() != cudaSuccess) {
+    if (prepare_csr_to_csc(50000) != cudaSuccess || prepare_row_solve() != cudaSuccess ||
+        prepare_row_solve_tc() != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return OPEN_CF_CUDA_ERROR;

@@ -1,0 +1,342 @@
+// Tensor-core masked Gram + Cholesky row solve (one ALS half-step), FP32 path.
+//
+// Same computation as k_row_solve (row_solve.cu): for every row i of a CSR
+// matrix with F the fixed other factor,
+//     A_i = sum_{j in Omega_i} f_j f_j^T + lambda I,   b_i = sum_{j in Omega_i} R_ij f_j,
+// then A_i = L L^T, L y = b_i, L^T x_i = y  (the per-row ridge solve of ALS;
+// Sec. "Collaborative Filtering Model" and "Online Performance Prediction").
+//
+// The Gram and the right-hand side are small dense contractions over the
+// row's observations: with the staged factor rows S (obs x KP),
+// A_i = S^T S and b_i = S^T r.  They run on the tensor cores with
+// mma.sync.m16n8k8 TF32 in the 3-pass split form (x = hi + lo, both TF32;
+// S^T S ~ hi^T hi + hi^T lo + lo^T hi, FP32 accumulation), which keeps FP32
+// accuracy (the dropped lo^T lo term is ~2^-22 relative).  The A and B
+// fragments of S^T S come from the same staged tile, so each 8-observation
+// step costs 4 (KP=16) or 8 (KP=32) shared loads plus 9 or 24 MMAs; only
+// the lower-triangle 16x8 blocks are formed.
+//
+// Mapping: KP in {16, 32}.  With WPS = 1 a warp forms the Grams of SPW =
+// 32/KP systems one after another with all 32 lanes, then factorises them in
+// parallel, one KP-lane segment per system (lane q owns row q of A).  With
+// WPS = 4 a CTA of 4 warps splits one long row's observations, sums the
+// partial Grams in a fixed order through shared memory, and warp 0 solves.
+// Staging: lane t loads observation t's factor row (16-byte loads) into a
+// padded tile (stride KP+8 floats: the fragment loads are conflict-free).
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ocf {
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+template <int KP, typename TC> struct alignas(16) TcSmem {
+    static constexpr int SPW = 32 / KP;
+    static constexpr int LD = KP + 8;
+    float stage[32][LD];
+    float sr[32];
+    struct alignas(16) Seg {
+        union {
+            float G[KP][KP + 1];   // Gram (lower triangle), then
+            TC L[KP][KP + 1];      // the Cholesky factor of the same system
+        };
+        float b[KP];
+        TC col[2][KP];
+        TC dinv[KP];
+    } seg[SPW];
+};
+
+template <int KP> struct Blocks {
+    static constexpr int MB = KP / 16;
+    // lower-triangle 16x8 blocks (mb, nb): nb <= 2*mb + 1
+    static constexpr int NBLK = (KP == 16) ? 2 : 6;
+    __device__ static constexpr int mb_of(int t) { return KP == 16 ? 0 : (t < 2 ? 0 : 1); }
+    __device__ static constexpr int nb_of(int t) { return KP == 16 ? t : (t < 2 ? t : t - 2); }
+};
+
+template <int KP, typename TC, int WPS>
+__global__ void __launch_bounds__(WPS == 1 ? (sizeof(TC) == 8 && KP == 32 ? 128 : 256) : 32 * WPS)
+k_row_solve_tc(SolveArgs<float> a) {
+    constexpr int WARPS = (WPS == 1) ? ((sizeof(TC) == 8 && KP == 32) ? 4 : 8) : WPS;
+    constexpr int SPW = (WPS == 1) ? 32 / KP : 1;   // systems per warp
+    constexpr int MB = Blocks<KP>::MB;
+    constexpr int NBLK = Blocks<KP>::NBLK;
+    using WS = TcSmem<KP, TC>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WS *smem = reinterpret_cast<WS *>(smem_raw);
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gid = lane >> 2, tid4 = lane & 3;
+    const int g = lane / KP, q = lane % KP;
+    WS &W = smem[warp];
+    const int64_t sys0 = (WPS == 1) ? ((int64_t)blockIdx.x * WARPS + warp) * SPW
+                                    : (int64_t)blockIdx.x;
+    const int64_t sys_stride = (WPS == 1) ? (int64_t)gridDim.x * WARPS * SPW
+                                          : (int64_t)gridDim.x;
+
+    for (int64_t base = sys0; base < a.m; base += sys_stride) {
+        bool bad_s[SPW];
+        int64_t s_s[SPW];
+        // ---------------- Gram phase: whole warp per system -----------------
+#pragma unroll
+        for (int si = 0; si < SPW; ++si) {
+            const int64_t i = base + si;
+            int64_t beg = 0, end = 0;
+            bool bad = false;
+            if (i < a.m) bad = !row_bounds(a.ptr, i, a.nnz, beg, end);
+            const int64_t s = end - beg;
+            float d[NBLK][4], dr[MB][4];
+#pragma unroll
+            for (int t = 0; t < NBLK; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) d[t][e] = 0.0f;
+#pragma unroll
+            for (int mb = 0; mb < MB; ++mb)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dr[mb][e] = 0.0f;
+
+            const int wsub = (WPS == 1) ? 0 : warp;
+            for (int64_t c0 = (int64_t)wsub * 32; c0 < s; c0 += 32 * WPS) {
+                const int64_t t = c0 + lane;
+                float4 *dst = reinterpret_cast<float4 *>(&W.stage[lane][0]);
+                if (t < s) {
+                    int32_t j = __ldg(a.idx + beg + t);
+                    float r = __ldg(a.val + beg + t);
+                    if (j < 0 || (int64_t)j >= a.n_other) {
+                        bad = true;
+                        j = 0;
+                        r = 0.0f;
+                    }
+                    const float4 *src = reinterpret_cast<const float4 *>(a.F + (int64_t)j * KP);
+#pragma unroll
+                    for (int e4 = 0; e4 < KP / 4; ++e4) dst[e4] = __ldg(src + e4);
+                    W.sr[lane] = r;
+                } else {
+#pragma unroll
+                    for (int e4 = 0; e4 < KP / 4; ++e4) dst[e4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    W.sr[lane] = 0.0f;
+                }
+                __syncwarp();
+                const int nks = (int)((min((int64_t)32, s - c0) + 7) / 8);
+                for (int ks = 0; ks < nks; ++ks) {
+                    const int k0 = ks * 8;
+                    uint32_t ah[MB][4], al[MB][4];
+#pragma unroll
+                    for (int mb = 0; mb < MB; ++mb) {
+                        split_tf32(W.stage[k0 + tid4][mb * 16 + gid], ah[mb][0], al[mb][0]);
+                        split_tf32(W.stage[k0 + tid4][mb * 16 + gid + 8], ah[mb][1], al[mb][1]);
+                        split_tf32(W.stage[k0 + tid4 + 4][mb * 16 + gid], ah[mb][2], al[mb][2]);
+                        split_tf32(W.stage[k0 + tid4 + 4][mb * 16 + gid + 8], ah[mb][3],
+                                   al[mb][3]);
+                    }
+                    uint32_t rh0, rl0, rh1, rl1;
+                    split_tf32(gid == 0 ? W.sr[k0 + tid4] : 0.0f, rh0, rl0);
+                    split_tf32(gid == 0 ? W.sr[k0 + tid4 + 4] : 0.0f, rh1, rl1);
+#pragma unroll
+                    for (int tb = 0; tb < NBLK; ++tb) {
+                        const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
+                        const int src_mb = nb >> 1, h = nb & 1;
+                        const uint32_t bh0 = ah[src_mb][h], bh1 = ah[src_mb][2 + h];
+                        const uint32_t bl0 = al[src_mb][h], bl1 = al[src_mb][2 + h];
+                        mma_tf32(d[tb], al[mb], bh0, bh1);
+                        mma_tf32(d[tb], ah[mb], bl0, bl1);
+                        mma_tf32(d[tb], ah[mb], bh0, bh1);
+                    }
+#pragma unroll
+                    for (int mb = 0; mb < MB; ++mb) {
+                        mma_tf32(dr[mb], al[mb], rh0, rh1);
+                        mma_tf32(dr[mb], ah[mb], rl0, rl1);
+                        mma_tf32(dr[mb], ah[mb], rh0, rh1);
+                    }
+                }
+                __syncwarp();
+            }
+            // fragments -> shared Gram (lower-triangle blocks) and RHS
+            float (*G)[KP + 1] = W.seg[si].G;
+#pragma unroll
+            for (int tb = 0; tb < NBLK; ++tb) {
+                const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
+                const int r0 = mb * 16 + gid, c = nb * 8 + 2 * tid4;
+                G[r0][c] = d[tb][0];
+                G[r0][c + 1] = d[tb][1];
+                G[r0 + 8][c] = d[tb][2];
+                G[r0 + 8][c + 1] = d[tb][3];
+            }
+            if (tid4 == 0) {
+#pragma unroll
+                for (int mb = 0; mb < MB; ++mb) {
+                    W.seg[si].b[mb * 16 + gid] = dr[mb][0];
+                    W.seg[si].b[mb * 16 + gid + 8] = dr[mb][2];
+                }
+            }
+            bad_s[si] = __any_sync(FULL, bad) != 0;
+            s_s[si] = s;
+        }
+        if constexpr (WPS > 1) {
+            bad_s[0] = __syncthreads_or(bad_s[0]) != 0;
+        } else {
+            __syncwarp();
+        }
+
+        // ---------------- solve phase: one KP-lane segment per system --------
+        const int slot = (WPS == 1) ? g : 0;
+        bool bad = false;
+        int64_t s = 0;
+#pragma unroll
+        for (int si = 0; si < SPW; ++si)
+            if (si == slot) {
+                bad = bad_s[si];
+                s = s_s[si];
+            }
+        if (WPS == 1 || warp == 0) {
+            auto &S = W.seg[slot];
+            const bool writer = (WPS == 1) || g == 0;
+            TC A[KP];
+            TC bt;
+            if constexpr (WPS > 1) {
+#pragma unroll
+                for (int e = 0; e < KP; ++e) A[e] = TC(smem[0].seg[0].G[q][e]);
+                bt = TC(smem[0].seg[0].b[q]);
+                for (int w = 1; w < WPS; ++w) {
+#pragma unroll
+                    for (int e = 0; e < KP; ++e) A[e] += TC(smem[w].seg[0].G[q][e]);
+                    bt += TC(smem[w].seg[0].b[q]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < KP; ++e) A[e] = TC(S.G[q][e]);
+                bt = TC(S.b[q]);
+            }
+#pragma unroll
+            for (int e = 0; e < KP; ++e)
+                if (e == q) A[e] += TC(a.lambda);
+            __syncwarp();   // every lane has read G before L overwrites it
+
+            bool fail = false;
+#pragma unroll
+            for (int p = 0; p < KP; ++p) {
+                TC piv = __shfl_sync(FULL, A[p], p, KP);
+                if (!(piv > TC(0))) {
+                    fail = true;
+                    piv = TC(1);
+                }
+                const TC inv = rsq(piv);
+                const TC l = (q == p) ? piv * inv : A[p] * inv;
+                A[p] = l;
+                TC *cb = S.col[p & 1];
+                if (writer) cb[q] = l;
+                if (writer && q == 0) S.dinv[p] = inv;
+                __syncwarp();
+#pragma unroll
+                for (int r = p + 1; r < KP; ++r) A[r] = my_fma(-l, cb[r], A[r]);
+            }
+            TC y = bt, yq = TC(0);
+#pragma unroll
+            for (int p = 0; p < KP; ++p) {
+                const TC yp = __shfl_sync(FULL, y, p, KP) * S.dinv[p];
+                if (q == p) yq = yp;
+                if (q > p) y = my_fma(-A[p], yp, y);
+            }
+            if (writer) {
+#pragma unroll
+                for (int e = 0; e < KP; ++e) S.L[q][e] = A[e];
+            }
+            __syncwarp();
+            TC x = yq, xq = TC(0);
+#pragma unroll
+            for (int p = KP - 1; p >= 0; --p) {
+                const TC xp = __shfl_sync(FULL, x, p, KP) * S.dinv[p];
+                if (q == p) xq = xp;
+                if (q < p) x = my_fma(-S.L[p][q], xp, x);
+            }
+            const int64_t i = base + slot;
+            if (writer && i < a.m) {
+                int32_t st = ST_OK;
+                if (bad) st = ST_BAD;
+                else if (s == 0) st = ST_EMPTY;
+                else if (fail) st = ST_NOT_SPD;
+                if (st != ST_OK) xq = TC(0);
+                if (q < a.kout) a.out[i * a.ldo + q] = (float)xq;
+                if (a.status && q == 0) a.status[i] = st;
+            }
+            __syncwarp();
+        }
+        if constexpr (WPS > 1) __syncthreads();
+    }
+}
+
+template <int KP, typename TC, int WPS> static size_t tc_smem_bytes() {
+    constexpr int WARPS = (WPS == 1) ? ((sizeof(TC) == 8 && KP == 32) ? 4 : 8) : WPS;
+    return sizeof(TcSmem<KP, TC>) * WARPS;
+}
+
+template <int KP, typename TC, int WPS> static cudaError_t tc_attr() {
+    return cudaFuncSetAttribute(k_row_solve_tc<KP, TC, WPS>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem_bytes<KP, TC, WPS>());
+}
+
+cudaError_t prepare_row_solve_tc() {
+    cudaError_t e;
+    if ((e = tc_attr<16, float, 1>()) != cudaSuccess) return e;
+    if ((e = tc_attr<32, float, 1>()) != cudaSuccess) return e;
+    if ((e = tc_attr<16, float, 4>()) != cudaSuccess) return e;
+    if ((e = tc_attr<32, float, 4>()) != cudaSuccess) return e;
+    if ((e = tc_attr<16, double, 1>()) != cudaSuccess) return e;
+    if ((e = tc_attr<32, double, 1>()) != cudaSuccess) return e;
+    if ((e = tc_attr<16, double, 4>()) != cudaSuccess) return e;
+    return tc_attr<32, double, 4>();
+}
+
+constexpr int64_t LONG_ROW_TC = 96;
+
+template <int KP, typename TC>
+static cudaError_t launch_tc_kp(const SolveArgs<float> &a, cudaStream_t st) {
+    if (a.nnz >= LONG_ROW_TC * a.m) {
+        int64_t blocks = a.m;
+        if (blocks > NUM_SMS_HINT * 64) blocks = NUM_SMS_HINT * 64;
+        k_row_solve_tc<KP, TC, 4><<<(unsigned)blocks, 128, tc_smem_bytes<KP, TC, 4>(), st>>>(a);
+    } else {
+        constexpr int WARPS = (sizeof(TC) == 8 && KP == 32) ? 4 : 8;
+        const int64_t per = (int64_t)WARPS * (32 / KP);
+        int64_t blocks = (a.m + per - 1) / per;
+        if (blocks > NUM_SMS_HINT * 32) blocks = NUM_SMS_HINT * 32;
+        k_row_solve_tc<KP, TC, 1>
+            <<<(unsigned)blocks, WARPS * 32, tc_smem_bytes<KP, TC, 1>(), st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp64,
+                                cudaStream_t st) {
+    if (a.m <= 0) return cudaSuccess;
+    if (KP == 16) return chol_fp64 ? launch_tc_kp<16, double>(a, st) : launch_tc_kp<16, float>(a, st);
+    if (KP == 32) return chol_fp64 ? launch_tc_kp<32, double>(a, st) : launch_tc_kp<32, float>(a, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ocf
