@@ -36,6 +36,12 @@ cudaError_t launch_csr_to_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *
 cudaError_t prepare_csr_to_csc(int64_t n_max);
 cudaError_t prepare_row_solve();
 
+// FP32 path with the Gram and RHS on tensor cores (3-pass TF32 mma.sync),
+// KP in {16, 32}.
+cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp64,
+                                cudaStream_t st);
+cudaError_t prepare_row_solve_tc();
+
 // Reconstruction T = U V^T fused with Algorithm 2.
 template <typename TV> struct PredictArgs {
     int64_t m, n;
