@@ -26,13 +26,19 @@ template <typename TV> struct SolveArgs {
 template <typename TV, typename TC>
 cudaError_t launch_row_solve(const SolveArgs<TV> &a, int KP, cudaStream_t st);
 
-// CSR -> CSC stable counting sort.  Scratch: cnt int32[n * nb] and tot
-// int64[n]; nb = number of row blocks (see csc_blocks).
-int64_t csc_blocks(int64_t m, int64_t n, int64_t nnz);
+// CSR -> CSC stable counting sort.  Rows are cut into nb blocks of rb rows
+// (rb a multiple of 32).  Scratch: cnt int32[n * nb] and tot int64[n].
+// nb_cap > 0 bounds nb (and so the scratch); 0 = no bound.
+struct CscPlan {
+    int64_t rb, nb;
+};
+CscPlan csc_plan(int64_t m, int64_t n, int64_t nnz, int64_t nb_cap);
+constexpr int64_t CSC_MAX_N = 25000;   // two 4-byte shared counters per column
 template <typename TV>
 cudaError_t launch_csr_to_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *ptr,
                               const int32_t *idx, const TV *val, int64_t *cptr, int32_t *ridx,
-                              TV *cval, int32_t *cnt, int64_t *tot, int64_t nb, cudaStream_t st);
+                              TV *cval, int32_t *cnt, int64_t *tot, CscPlan plan,
+                              cudaStream_t st);
 cudaError_t prepare_csr_to_csc(int64_t n_max);
 cudaError_t prepare_row_solve();
 
@@ -64,7 +70,7 @@ cudaError_t launch_select(int64_t m, int64_t n, const float *T, int64_t ld, cons
                           int64_t base, float Ebase, float gamma, int32_t *best, float *saving,
                           cudaStream_t st);
 
-// Objective J and per-row observed RMSE.  part: double[2 * parts] scratch.
+// Objective J and per-row observed RMSE.  part: double[3 * objective_parts(max(m, n))].
 int64_t objective_parts(int64_t m);
 template <typename TV>
 cudaError_t launch_objective(int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,

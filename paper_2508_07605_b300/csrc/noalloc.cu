@@ -40,7 +40,7 @@ int setup_device(int dev, void **scratch) {
             cudaGetLastError();
             return OPEN_CF_CUDA_ERROR;
         }
-        e = ocf::prepare_csr_to_csc(50000);   // the same limit a handle sets
+        e = ocf::prepare_csr_to_csc(ocf::CSC_MAX_N);   // the same limit a handle sets
         if (e != cudaSuccess) {
             cudaGetLastError();
             return OPEN_CF_CUDA_ERROR;
@@ -78,12 +78,11 @@ extern "C" int open_cf_csr_to_csc_noalloc(int64_t m, int64_t n, int64_t nnz,
     int32_t *cnt = reinterpret_cast<int32_t *>(static_cast<unsigned char *>(scratch) + tot_bytes);
     const int64_t max_nb = (int64_t)((kScratchBytes - tot_bytes) / (sizeof(int32_t) * (size_t)n));
     if (max_nb < 1) return OPEN_CF_UNSUPPORTED;
-    int64_t nb = ocf::csc_blocks(m, n, nnz);
-    if (nb > max_nb) nb = max_nb;
+    const ocf::CscPlan plan = ocf::csc_plan(m, n, nnz, max_nb);
     // Every counter and total the kernels read is written earlier in the same
     // call, so nothing left from a previous call needs clearing.
     cudaError_t e = ocf::launch_csr_to_csc<float>(m, n, nnz, row_ptr, col, val, col_ptr, row_idx,
-                                                  cval, cnt, tot, nb,
+                                                  cval, cnt, tot, plan,
                                                   reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         cudaGetLastError();

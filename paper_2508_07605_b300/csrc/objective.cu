@@ -25,37 +25,49 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <typename TV>
+// Per CTA: a fixed contiguous range of rows (one warp per row, lanes over the
+// row's entries, u held in registers, v_j read as 16-byte vectors) and a fixed
+// slice of V's rows for |V|^2.  part[3b .. 3b+2] = (SSE, |U|^2, |V|^2) of CTA b.
+template <typename TV, int KP>
 __global__ void __launch_bounds__(OBJ_WARPS * 32)
 k_objective_rows(int64_t m, int64_t nnz, const int64_t *__restrict__ ptr,
                  const int32_t *__restrict__ idx, const TV *__restrict__ val,
                  const TV *__restrict__ U, int64_t ldu, int k, const TV *__restrict__ V,
-                 int64_t n, int KP, double *__restrict__ part, float *__restrict__ row_rmse) {
-    __shared__ double ws[OBJ_WARPS][2];
+                 int64_t n, double *__restrict__ part, float *__restrict__ row_rmse) {
+    using VT = typename Vec4<TV>::type;
+    constexpr int VN = Vec4<TV>::N;
+    __shared__ double ws[OBJ_WARPS][3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t G = gridDim.x;
     const int64_t per = (m + G - 1) / G;
     const int64_t r0 = blockIdx.x * per, r1 = min(m, r0 + per);
-    double sse_w = 0.0, nu_w = 0.0;
+    double sse_w = 0.0, nu_w = 0.0, nv_w = 0.0;
     for (int64_t i = r0 + warp; i < r1; i += OBJ_WARPS) {
         int64_t beg, end;
         const bool ok = row_bounds(ptr, i, nnz, beg, end);
-        const TV *u = U + i * ldu;
+        TV u[KP];
+#pragma unroll
+        for (int p = 0; p < KP; ++p) u[p] = (p < k) ? U[i * ldu + p] : TV(0);
         double sse = 0.0;
         for (int64_t t = beg + lane; t < end; t += 32) {
             const int32_t j = __ldg(idx + t);
             if (j < 0 || (int64_t)j >= n) continue;
-            const TV *v = V + (int64_t)j * KP;
+            const VT *v = reinterpret_cast<const VT *>(V + (int64_t)j * KP);
             TV d = TV(0);
-            for (int p = 0; p < k; ++p) d = my_fma(u[p], v[p], d);
+#pragma unroll
+            for (int e4 = 0; e4 < KP / VN; ++e4) {
+                const VT x = __ldg(v + e4);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) d = my_fma(u[e4 * VN + e], vget(x, e), d);
+            }
             const double e = (double)__ldg(val + t) - (double)d;
             sse += e * e;
         }
         sse = warp_sum(sse);
-        double nu = 0.0;
-        if (lane < k) nu = (double)u[lane] * (double)u[lane];
-        nu = warp_sum(nu);
         if (lane == 0) {
+            double nu = 0.0;
+#pragma unroll
+            for (int p = 0; p < KP; ++p) nu += (double)u[p] * (double)u[p];
             sse_w += sse;
             nu_w += nu;
             if (row_rmse) {
@@ -64,38 +76,43 @@ k_objective_rows(int64_t m, int64_t nnz, const int64_t *__restrict__ ptr,
             }
         }
     }
+    // this CTA's slice of V (rows of KP elements, padding is zero)
+    const int64_t vper = (n + G - 1) / G;
+    const int64_t v0 = blockIdx.x * vper * KP, v1 = min(n, (blockIdx.x + 1) * vper) * KP;
+    for (int64_t e = v0 + threadIdx.x; e < v1; e += blockDim.x) {
+        const double x = (double)V[e];
+        nv_w += x * x;
+    }
+    nv_w = warp_sum(nv_w);
     if (lane == 0) {
         ws[warp][0] = sse_w;
         ws[warp][1] = nu_w;
+        ws[warp][2] = nv_w;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0;
+        double sa = 0.0, sb = 0.0, sc = 0.0;
         for (int w = 0; w < OBJ_WARPS; ++w) {
             sa += ws[w][0];
             sb += ws[w][1];
+            sc += ws[w][2];
         }
-        part[2 * blockIdx.x] = sa;
-        part[2 * blockIdx.x + 1] = sb;
+        part[3 * blockIdx.x] = sa;
+        part[3 * blockIdx.x + 1] = sb;
+        part[3 * blockIdx.x + 2] = sc;
     }
 }
 
-template <typename TV>
 __global__ void __launch_bounds__(1024)
-k_objective_final(int64_t G, const double *__restrict__ part, const TV *__restrict__ V,
-                  int64_t n, int KP, int k, double lambda, double *__restrict__ J) {
+k_objective_final(int64_t G, const double *__restrict__ part, double lambda,
+                  double *__restrict__ J) {
     __shared__ double ws[32][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double a = 0.0, b = 0.0, c = 0.0;
     for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
-        a += part[2 * g];
-        b += part[2 * g + 1];
-    }
-    for (int64_t e = threadIdx.x; e < n * KP; e += blockDim.x) {
-        if ((int)(e % KP) < k) {
-            const double v = (double)V[e];
-            c += v * v;
-        }
+        a += part[3 * g];
+        b += part[3 * g + 1];
+        c += part[3 * g + 2];
     }
     a = warp_sum(a);
     b = warp_sum(b);
@@ -122,13 +139,23 @@ cudaError_t launch_objective(int64_t m, int64_t nnz, const int64_t *ptr, const i
                              const TV *val, const TV *U, int64_t ldu, int k, const TV *V,
                              int64_t n, int KP, double lambda, double *part, double *J_out,
                              float *row_rmse, cudaStream_t st) {
-    const int64_t G = objective_parts(m);
-    if (m > 0)
-        k_objective_rows<TV><<<(unsigned)G, OBJ_WARPS * 32, 0, st>>>(
-            m, nnz, ptr, idx, val, U, ldu, k, V, n, KP, part, row_rmse);
-    else
-        cudaMemsetAsync(part, 0, sizeof(double) * 2, st);
-    k_objective_final<TV><<<1, 1024, 0, st>>>(m > 0 ? G : 1, part, V, n, KP, k, lambda, J_out);
+    const int64_t G = objective_parts(m > n ? m : n);
+    switch (KP) {
+        case 8:
+            k_objective_rows<TV, 8><<<(unsigned)G, OBJ_WARPS * 32, 0, st>>>(
+                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse);
+            break;
+        case 16:
+            k_objective_rows<TV, 16><<<(unsigned)G, OBJ_WARPS * 32, 0, st>>>(
+                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse);
+            break;
+        case 32:
+            k_objective_rows<TV, 32><<<(unsigned)G, OBJ_WARPS * 32, 0, st>>>(
+                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    k_objective_final<<<1, 1024, 0, st>>>(G, part, lambda, J_out);
     return cudaGetLastError();
 }
 

@@ -177,14 +177,15 @@ int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const i
                int32_t *col_status, double *J_hist, cudaStream_t stream) {
     const int64_t n = h->n;
     const int KP = h->KP;
-    const int64_t nb = csc_blocks(m, n, nnz);
+    const CscPlan plan = csc_plan(m, n, nnz, 0);
+    const int64_t nb = plan.nb;
     CK(h, ensure(h, h->U_w, sizeof(TV) * std::max<int64_t>(m, 1) * KP));
     CK(h, ensure(h, h->csc_ptr, sizeof(int64_t) * (n + 1)));
     CK(h, ensure(h, h->csc_idx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
     CK(h, ensure(h, h->csc_val, sizeof(TV) * std::max<int64_t>(nnz, 1)));
     CK(h, ensure(h, h->cnt, sizeof(int32_t) * n * nb));
     CK(h, ensure(h, h->tot, sizeof(int64_t) * n));
-    CK(h, ensure(h, h->part, sizeof(double) * 2 * objective_parts(std::max<int64_t>(m, n))));
+    CK(h, ensure(h, h->part, sizeof(double) * 3 * objective_parts(std::max<int64_t>(m, n))));
     TV *Uw = (TV *)h->U_w.p;
     TV *V = (TV *)h->V.p;
     int64_t *cptr = (int64_t *)h->csc_ptr.p;
@@ -197,7 +198,7 @@ int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const i
         cudaError_t e = cudaMemsetAsync(Uw, 0, sizeof(TV) * m * KP, st);
         if (e != cudaSuccess) return e;
         e = launch_csr_to_csc<TV>(m, n, nnz, ptr, idx, val, cptr, cidx, cval, (int32_t *)h->cnt.p,
-                                  (int64_t *)h->tot.p, nb, st);
+                                  (int64_t *)h->tot.p, plan, st);
         if (e != cudaSuccess) return e;
         for (int s = 0; s < sweeps; ++s) {
             SolveArgs<TV> ua{m, nnz, ptr, idx, val, V, n, Uw, KP, KP, row_status, lam};
@@ -287,7 +288,7 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
         h->base_default = ci * cfg->n_gpu_caps + gi;
     }
     DeviceGuard g(h->device);
-    if (prepare_csr_to_csc(50000) != cudaSuccess || prepare_row_solve() != cudaSuccess ||
+    if (prepare_csr_to_csc(CSC_MAX_N) != cudaSuccess || prepare_row_solve() != cudaSuccess ||
         prepare_row_solve_tc() != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -318,8 +319,9 @@ int open_cf_set_V(open_cf_t *h, const void *V, int64_t n, void *stream) {
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (!V || n <= 0) return fail(h, OPEN_CF_INVALID_ARG, "V is NULL or n <= 0");
-    if (n > 50000) return fail(h, OPEN_CF_UNSUPPORTED, "n = %lld settings exceeds 50000",
-                               (long long)n);
+    if (n > CSC_MAX_N)
+        return fail(h, OPEN_CF_UNSUPPORTED, "n = %lld settings exceeds %lld", (long long)n,
+                    (long long)CSC_MAX_N);
     if (!h->cpu_caps.empty() && n != (int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size())
         return fail(h, OPEN_CF_INVALID_ARG, "n = %lld != n_cpu_caps * n_gpu_caps", (long long)n);
     DeviceGuard g(h->device);
@@ -549,7 +551,7 @@ int open_cf_objective(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
     if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: fit or set V first");
     if (!J_out || (m > 0 && !U)) return fail(h, OPEN_CF_INVALID_ARG, "J_out or U is NULL");
     DeviceGuard g(h->device);
-    CK(h, ensure(h, h->part, sizeof(double) * 2 * objective_parts(std::max<int64_t>(m, 1))));
+    CK(h, ensure(h, h->part, sizeof(double) * 3 * objective_parts(std::max<int64_t>(m, h->n))));
     if (h->f64)
         CK(h, launch_objective<double>(m, nnz, row_ptr, col, as<double>(val), as<double>(U), h->k,
                                        h->k, (double *)h->V.p, h->n, h->KP, h->cfg.lambda,
@@ -570,19 +572,21 @@ int open_cf_csr_to_csc(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const in
     if (rc) return rc;
     if (n <= 0 || !col_ptr || (nnz > 0 && (!row_idx || !cval)))
         return fail(h, OPEN_CF_INVALID_ARG, "bad n or output arrays");
-    if (n > 50000) return fail(h, OPEN_CF_UNSUPPORTED, "n exceeds 50000 columns");
+    if (n > CSC_MAX_N) return fail(h, OPEN_CF_UNSUPPORTED, "n exceeds %lld columns",
+                                   (long long)CSC_MAX_N);
     DeviceGuard g(h->device);
-    const int64_t nb = csc_blocks(m, n, nnz);
+    const CscPlan plan = csc_plan(m, n, nnz, 0);
+    const int64_t nb = plan.nb;
     CK(h, ensure(h, h->cnt, sizeof(int32_t) * n * nb));
     CK(h, ensure(h, h->tot, sizeof(int64_t) * n));
     if (h->f64)
         CK(h, launch_csr_to_csc<double>(m, n, nnz, row_ptr, col, as<double>(val), col_ptr, row_idx,
                                         (double *)cval, (int32_t *)h->cnt.p,
-                                        (int64_t *)h->tot.p, nb, S(stream)));
+                                        (int64_t *)h->tot.p, plan, S(stream)));
     else
         CK(h, launch_csr_to_csc<float>(m, n, nnz, row_ptr, col, as<float>(val), col_ptr, row_idx,
                                        (float *)cval, (int32_t *)h->cnt.p, (int64_t *)h->tot.p,
-                                       nb, S(stream)));
+                                       plan, S(stream)));
     return OPEN_CF_OK;
 }
 

@@ -50,14 +50,28 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// cp.async with zero fill: copies src_bytes (0 or the full size) and zeroes the rest.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 template <int KP, typename TC> struct alignas(16) TcSmem {
     static constexpr int SPW = 32 / KP;
     static constexpr int LD = KP + 8;
-    float stage[32][LD];
-    float sr[32];
+    float stage[2][32][LD];   // double-buffered staged factor rows
+    float sr[2][32];
     struct alignas(16) Seg {
         union {
             float G[KP][KP + 1];   // Gram (lower triangle), then
@@ -99,103 +113,172 @@ k_row_solve_tc(SolveArgs<float> a) {
                                           : (int64_t)gridDim.x;
 
     for (int64_t base = sys0; base < a.m; base += sys_stride) {
+        // ---------------- Gram phase -------------------------------------
+        // The warp's work is a list of 32-observation items: the chunks of
+        // its SPW systems in order (WPS = 1), or this warp's slice of the
+        // chunks of one long system (WPS > 1).  Items are software-pipelined:
+        // item w+1's factor rows stream into the other stage buffer with
+        // cp.async (zero-filled past the row end) while item w is on the
+        // tensor cores, and column indices are fetched two items ahead.
+        int64_t beg_s[SPW], s_s[SPW];
         bool bad_s[SPW];
-        int64_t s_s[SPW];
-        // ---------------- Gram phase: whole warp per system -----------------
+        int nch[SPW];
+        int nitems = 0;
 #pragma unroll
         for (int si = 0; si < SPW; ++si) {
             const int64_t i = base + si;
             int64_t beg = 0, end = 0;
-            bool bad = false;
-            if (i < a.m) bad = !row_bounds(a.ptr, i, a.nnz, beg, end);
-            const int64_t s = end - beg;
-            float d[NBLK][4], dr[MB][4];
+            bad_s[si] = false;
+            if (i < a.m) bad_s[si] = !row_bounds(a.ptr, i, a.nnz, beg, end);
+            beg_s[si] = beg;
+            s_s[si] = end - beg;
+            if (WPS == 1) {
+                nch[si] = (int)((s_s[si] + 31) / 32);
+            } else {
+                const int64_t all = (s_s[si] + 31) / 32;   // chunks of the system
+                nch[si] = (int)((all > warp) ? (all - warp + WPS - 1) / WPS : 0);
+            }
+            nitems += nch[si];
+        }
+        // item w -> (system, first observation)
+        auto item = [&](int w, int &si, int64_t &c0) {
+            si = 0;
+            if (SPW == 2 && w >= nch[0]) {
+                w -= nch[0];
+                si = 1;
+            }
+            c0 = (WPS == 1) ? (int64_t)w * 32 : ((int64_t)w * WPS + warp) * 32;
+        };
+        bool badf[SPW];
+#pragma unroll
+        for (int si = 0; si < SPW; ++si) badf[si] = false;
+        auto load_idx = [&](int w) -> int32_t {
+            int si; int64_t c0;
+            item(w, si, c0);
+            int64_t bg = 0, ss = 0;
+#pragma unroll
+            for (int t = 0; t < SPW; ++t) if (t == si) { bg = beg_s[t]; ss = s_s[t]; }
+            const int64_t tt = c0 + lane;
+            int32_t j = 0;
+            if (tt < ss) {
+                j = __ldg(a.idx + bg + tt);
+                if (j < 0 || (int64_t)j >= a.n_other) {
+#pragma unroll
+                    for (int t = 0; t < SPW; ++t) if (t == si) badf[t] = true;
+                    j = 0;
+                }
+            }
+            return j;
+        };
+        auto issue = [&](int w, int32_t j, int buf) {
+            int si; int64_t c0;
+            item(w, si, c0);
+            int64_t bg = 0, ss = 0;
+#pragma unroll
+            for (int t = 0; t < SPW; ++t) if (t == si) { bg = beg_s[t]; ss = s_s[t]; }
+            const int64_t tt = c0 + lane;
+            const bool v = tt < ss;
+            const float *src = a.F + (int64_t)j * KP;
+#pragma unroll
+            for (int e4 = 0; e4 < KP / 4; ++e4)
+                cp_async16(&W.stage[buf][lane][4 * e4], src + 4 * e4, v ? 16 : 0);
+            cp_async4(&W.sr[buf][lane], v ? (const void *)(a.val + bg + tt) : (const void *)a.F,
+                      v ? 4 : 0);
+        };
+
+        float d[SPW][NBLK][4], dr[SPW][MB][4];
+#pragma unroll
+        for (int si = 0; si < SPW; ++si) {
 #pragma unroll
             for (int t = 0; t < NBLK; ++t)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) d[t][e] = 0.0f;
+                for (int e = 0; e < 4; ++e) d[si][t][e] = 0.0f;
 #pragma unroll
             for (int mb = 0; mb < MB; ++mb)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) dr[mb][e] = 0.0f;
-
-            const int wsub = (WPS == 1) ? 0 : warp;
-            for (int64_t c0 = (int64_t)wsub * 32; c0 < s; c0 += 32 * WPS) {
-                const int64_t t = c0 + lane;
-                float4 *dst = reinterpret_cast<float4 *>(&W.stage[lane][0]);
-                if (t < s) {
-                    int32_t j = __ldg(a.idx + beg + t);
-                    float r = __ldg(a.val + beg + t);
-                    if (j < 0 || (int64_t)j >= a.n_other) {
-                        bad = true;
-                        j = 0;
-                        r = 0.0f;
-                    }
-                    const float4 *src = reinterpret_cast<const float4 *>(a.F + (int64_t)j * KP);
-#pragma unroll
-                    for (int e4 = 0; e4 < KP / 4; ++e4) dst[e4] = __ldg(src + e4);
-                    W.sr[lane] = r;
-                } else {
-#pragma unroll
-                    for (int e4 = 0; e4 < KP / 4; ++e4) dst[e4] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    W.sr[lane] = 0.0f;
-                }
+                for (int e = 0; e < 4; ++e) dr[si][mb][e] = 0.0f;
+        }
+        if (nitems > 0) {
+            issue(0, load_idx(0), 0);
+            cp_async_commit();
+            int32_t jn = nitems > 1 ? load_idx(1) : 0;
+            for (int w = 0; w < nitems; ++w) {
+                if (w + 1 < nitems) issue(w + 1, jn, (w + 1) & 1);
+                cp_async_commit();
+                if (w + 2 < nitems) jn = load_idx(w + 2);
+                cp_async_wait1();
                 __syncwarp();
-                const int nks = (int)((min((int64_t)32, s - c0) + 7) / 8);
+                int si; int64_t c0;
+                item(w, si, c0);
+                int64_t ss = 0;
+#pragma unroll
+                for (int t = 0; t < SPW; ++t) if (t == si) ss = s_s[t];
+                const int buf = w & 1;
+                const int nks = (int)((min((int64_t)32, ss - c0) + 7) / 8);
                 for (int ks = 0; ks < nks; ++ks) {
                     const int k0 = ks * 8;
                     uint32_t ah[MB][4], al[MB][4];
 #pragma unroll
                     for (int mb = 0; mb < MB; ++mb) {
-                        split_tf32(W.stage[k0 + tid4][mb * 16 + gid], ah[mb][0], al[mb][0]);
-                        split_tf32(W.stage[k0 + tid4][mb * 16 + gid + 8], ah[mb][1], al[mb][1]);
-                        split_tf32(W.stage[k0 + tid4 + 4][mb * 16 + gid], ah[mb][2], al[mb][2]);
-                        split_tf32(W.stage[k0 + tid4 + 4][mb * 16 + gid + 8], ah[mb][3],
+                        split_tf32(W.stage[buf][k0 + tid4][mb * 16 + gid], ah[mb][0], al[mb][0]);
+                        split_tf32(W.stage[buf][k0 + tid4][mb * 16 + gid + 8], ah[mb][1],
+                                   al[mb][1]);
+                        split_tf32(W.stage[buf][k0 + tid4 + 4][mb * 16 + gid], ah[mb][2],
+                                   al[mb][2]);
+                        split_tf32(W.stage[buf][k0 + tid4 + 4][mb * 16 + gid + 8], ah[mb][3],
                                    al[mb][3]);
                     }
                     uint32_t rh0, rl0, rh1, rl1;
-                    split_tf32(gid == 0 ? W.sr[k0 + tid4] : 0.0f, rh0, rl0);
-                    split_tf32(gid == 0 ? W.sr[k0 + tid4 + 4] : 0.0f, rh1, rl1);
+                    split_tf32(gid == 0 ? W.sr[buf][k0 + tid4] : 0.0f, rh0, rl0);
+                    split_tf32(gid == 0 ? W.sr[buf][k0 + tid4 + 4] : 0.0f, rh1, rl1);
 #pragma unroll
-                    for (int tb = 0; tb < NBLK; ++tb) {
-                        const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
-                        const int src_mb = nb >> 1, h = nb & 1;
-                        const uint32_t bh0 = ah[src_mb][h], bh1 = ah[src_mb][2 + h];
-                        const uint32_t bl0 = al[src_mb][h], bl1 = al[src_mb][2 + h];
-                        mma_tf32(d[tb], al[mb], bh0, bh1);
-                        mma_tf32(d[tb], ah[mb], bl0, bl1);
-                        mma_tf32(d[tb], ah[mb], bh0, bh1);
-                    }
+                    for (int sx = 0; sx < SPW; ++sx) {
+                        if (sx != si) continue;   // warp-uniform: accumulators stay in registers
 #pragma unroll
-                    for (int mb = 0; mb < MB; ++mb) {
-                        mma_tf32(dr[mb], al[mb], rh0, rh1);
-                        mma_tf32(dr[mb], ah[mb], rl0, rl1);
-                        mma_tf32(dr[mb], ah[mb], rh0, rh1);
+                        for (int tb = 0; tb < NBLK; ++tb) {
+                            const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
+                            const int src_mb = nb >> 1, h = nb & 1;
+                            const uint32_t bh0 = ah[src_mb][h], bh1 = ah[src_mb][2 + h];
+                            const uint32_t bl0 = al[src_mb][h], bl1 = al[src_mb][2 + h];
+                            mma_tf32(d[sx][tb], al[mb], bh0, bh1);
+                            mma_tf32(d[sx][tb], ah[mb], bl0, bl1);
+                            mma_tf32(d[sx][tb], ah[mb], bh0, bh1);
+                        }
+#pragma unroll
+                        for (int mb = 0; mb < MB; ++mb) {
+                            mma_tf32(dr[sx][mb], al[mb], rh0, rh1);
+                            mma_tf32(dr[sx][mb], ah[mb], rl0, rl1);
+                            mma_tf32(dr[sx][mb], ah[mb], rh0, rh1);
+                        }
                     }
                 }
-                __syncwarp();
+                __syncwarp();   // this buffer is refilled two items later
             }
-            // fragments -> shared Gram (lower-triangle blocks) and RHS
+        }
+        // fragments -> shared Gram (lower-triangle blocks) and RHS
+#pragma unroll
+        for (int si = 0; si < SPW; ++si) {
             float (*G)[KP + 1] = W.seg[si].G;
 #pragma unroll
             for (int tb = 0; tb < NBLK; ++tb) {
                 const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
                 const int r0 = mb * 16 + gid, c = nb * 8 + 2 * tid4;
-                G[r0][c] = d[tb][0];
-                G[r0][c + 1] = d[tb][1];
-                G[r0 + 8][c] = d[tb][2];
-                G[r0 + 8][c + 1] = d[tb][3];
+                G[r0][c] = d[si][tb][0];
+                G[r0][c + 1] = d[si][tb][1];
+                G[r0 + 8][c] = d[si][tb][2];
+                G[r0 + 8][c + 1] = d[si][tb][3];
             }
             if (tid4 == 0) {
 #pragma unroll
                 for (int mb = 0; mb < MB; ++mb) {
-                    W.seg[si].b[mb * 16 + gid] = dr[mb][0];
-                    W.seg[si].b[mb * 16 + gid + 8] = dr[mb][2];
+                    W.seg[si].b[mb * 16 + gid] = dr[si][mb][0];
+                    W.seg[si].b[mb * 16 + gid + 8] = dr[si][mb][2];
                 }
             }
-            bad_s[si] = __any_sync(FULL, bad) != 0;
-            s_s[si] = s;
         }
+        // an out-of-range column flags only the system it was read for
+#pragma unroll
+        for (int si = 0; si < SPW; ++si) bad_s[si] = bad_s[si] || (__any_sync(FULL, badf[si]) != 0);
         if constexpr (WPS > 1) {
             bad_s[0] = __syncthreads_or(bad_s[0]) != 0;
         } else {
@@ -312,7 +395,7 @@ cudaError_t prepare_row_solve_tc() {
     return tc_attr<32, double, 4>();
 }
 
-constexpr int64_t LONG_ROW_TC = 96;
+constexpr int64_t LONG_ROW_TC = 512;   // mean observations per row that warrant 4 warps
 
 template <int KP, typename TC>
 static cudaError_t launch_tc_kp(const SolveArgs<float> &a, cudaStream_t st) {

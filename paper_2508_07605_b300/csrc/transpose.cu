@@ -6,40 +6,44 @@
 // increasing row order, so the V-half sums in a fixed order and a fit is
 // bit-reproducible.
 //
-// Rows are cut into nb contiguous blocks.  Pass 1 counts, per block, how many
-// entries fall in each column (cnt[b][c], shared-memory atomics); pass 2 turns
-// the counts into per-block exclusive offsets within each column and column
-// totals; pass 3 scans the totals into col_ptr; pass 4 lets one warp per block
-// walk its rows in order and place each entry at
-// col_ptr[c] + offset[b][c] + (entries of column c this block placed so far).
-// A row holds each column at most once, so the lanes of a warp never race on
-// one cursor.
+// Rows are cut into nb contiguous blocks of RB = 32 * S rows.  Pass 1 counts,
+// per block, how many entries fall in each column (cnt[b][c], shared-memory
+// atomics); pass 2 turns the counts into per-block exclusive offsets within
+// each column and column totals; pass 3 scans the totals into col_ptr; pass 4
+// places every entry at once: a block walks its rows in S sub-blocks of 32;
+// for each sub-block it ORs, per column, a bit for every row that holds the
+// column, so the stable rank of entry (r, c) inside its column is
+// popc(mask[c] & bits below r) plus the column's entries from earlier
+// sub-blocks and blocks.  A row holds each column at most once.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace ocf {
 
-int64_t csc_blocks(int64_t m, int64_t n, int64_t nnz) {
-    int64_t nb = nnz / (n > 0 ? n : 1);
-    if (nb < 148) nb = 148;
-    if (nb > 4096) nb = 4096;
-    if (nb > m) nb = m;
-    if (nb < 1) nb = 1;
-    return nb;
-}
-
-static __device__ __forceinline__ int64_t rows_per_block(int64_t m, int64_t nb) {
-    return (m + nb - 1) / nb;
+CscPlan csc_plan(int64_t m, int64_t n, int64_t nnz, int64_t nb_cap) {
+    int64_t target = nnz / (n > 0 ? n : 1);   // counters ~ entries
+    if (target < 148) target = 148;
+    if (target > 4096) target = 4096;
+    if (nb_cap > 0 && target > nb_cap) target = nb_cap;
+    if (target < 1) target = 1;
+    const int64_t mm = m > 0 ? m : 1;
+    int64_t rb = (mm + target - 1) / target;
+    rb = ((rb + 31) / 32) * 32;
+    int64_t nb = (mm + rb - 1) / rb;
+    while (nb_cap > 0 && nb > nb_cap) {   // rounding can overshoot a hard cap
+        rb += 32;
+        nb = (mm + rb - 1) / rb;
+    }
+    return CscPlan{rb, nb};
 }
 
 __global__ void k_csc_count(int64_t m, int64_t n, int64_t nnz, const int64_t *__restrict__ ptr,
                             const int32_t *__restrict__ idx, int32_t *__restrict__ cnt,
-                            int64_t nb) {
+                            int64_t RB) {
     extern __shared__ int32_t sc[];
     const int64_t b = blockIdx.x;
     for (int64_t c = threadIdx.x; c < n; c += blockDim.x) sc[c] = 0;
     __syncthreads();
-    const int64_t RB = rows_per_block(m, nb);
     const int64_t r0 = b * RB, r1 = min(m, r0 + RB);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t r = r0 + warp; r < r1; r += nw) {
@@ -123,73 +127,89 @@ k_csc_colptr(int64_t n, const int64_t *__restrict__ tot, int64_t *__restrict__ c
 }
 
 template <typename TV>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(256)
 k_csc_scatter(int64_t m, int64_t n, int64_t nnz, const int64_t *__restrict__ ptr,
               const int32_t *__restrict__ idx, const TV *__restrict__ val,
               const int32_t *__restrict__ cnt, const int64_t *__restrict__ cptr,
-              int32_t *__restrict__ ridx, TV *__restrict__ cval, int64_t nb) {
-    extern __shared__ int32_t cur[];  // entries of column c placed so far (offset in column)
+              int32_t *__restrict__ ridx, TV *__restrict__ cval, int64_t RB) {
+    extern __shared__ uint32_t sm32[];
+    uint32_t *mask = sm32;                              // [n] rows of the sub-block holding c
+    int32_t *run = reinterpret_cast<int32_t *>(sm32 + n);   // [n] placed so far in column c
     const int64_t b = blockIdx.x;
-    for (int64_t c = threadIdx.x; c < n; c += 32) cur[c] = cnt[b * n + c];
-    __syncwarp();
-    const int64_t RB = rows_per_block(m, nb);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) run[c] = cnt[b * n + c];
     const int64_t r0 = b * RB, r1 = min(m, r0 + RB);
-    for (int64_t r = r0; r < r1; ++r) {
-        int64_t beg, end;
-        if (row_bounds(ptr, r, nnz, beg, end)) {
-            for (int64_t e = beg + threadIdx.x; e < end; e += 32) {
+    for (int64_t rs = r0; rs < r1; rs += 32) {
+        const int64_t re = min(r1, rs + 32);
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) mask[c] = 0u;
+        __syncthreads();
+        for (int64_t r = rs + warp; r < re; r += nw) {
+            int64_t beg, end;
+            if (!row_bounds(ptr, r, nnz, beg, end)) continue;
+            const uint32_t bit = 1u << (unsigned)(r - rs);
+            for (int64_t e = beg + lane; e < end; e += 32) {
+                const int32_t c = __ldg(idx + e);
+                if (c >= 0 && (int64_t)c < n) atomicOr(&mask[c], bit);
+            }
+        }
+        __syncthreads();
+        for (int64_t r = rs + warp; r < re; r += nw) {
+            int64_t beg, end;
+            if (!row_bounds(ptr, r, nnz, beg, end)) continue;
+            const uint32_t below = (1u << (unsigned)(r - rs)) - 1u;
+            for (int64_t e = beg + lane; e < end; e += 32) {
                 const int32_t c = __ldg(idx + e);
                 if (c >= 0 && (int64_t)c < n) {
-                    const int32_t o = cur[c];
-                    cur[c] = o + 1;
-                    const int64_t pos = __ldg(cptr + c) + o;
+                    const int64_t pos = __ldg(cptr + c) + run[c] + __popc(mask[c] & below);
                     ridx[pos] = (int32_t)r;
                     cval[pos] = __ldg(val + e);
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) run[c] += __popc(mask[c]);
+        __syncthreads();
     }
 }
 
-// Largest n the shared-memory counters allow (4 bytes per column).
-constexpr int64_t CSC_MAX_N = (200 * 1024) / 4;
-
 cudaError_t prepare_csr_to_csc(int64_t n_max) {
     if (n_max > CSC_MAX_N) return cudaErrorInvalidValue;
-    const int bytes = (int)(sizeof(int32_t) * (n_max > 12288 ? n_max : 12288));
+    const int nn = (int)(n_max > 6144 ? n_max : 6144);
     cudaError_t e = cudaFuncSetAttribute(k_csc_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         bytes);
+                                         (int)sizeof(int32_t) * nn);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_csc_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             bytes);
+                             2 * (int)sizeof(int32_t) * nn);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_csc_scatter<double>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * (int)sizeof(int32_t) * nn);
 }
 
 template <typename TV>
 cudaError_t launch_csr_to_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *ptr,
                               const int32_t *idx, const TV *val, int64_t *cptr, int32_t *ridx,
-                              TV *cval, int32_t *cnt, int64_t *tot, int64_t nb, cudaStream_t st) {
+                              TV *cval, int32_t *cnt, int64_t *tot, CscPlan plan,
+                              cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (m <= 0) return cudaMemsetAsync(cptr, 0, sizeof(int64_t) * (n + 1), st);
+    const int64_t nb = plan.nb;
     const size_t sm = sizeof(int32_t) * n;
-    k_csc_count<<<(unsigned)nb, 256, sm, st>>>(m, n, nnz, ptr, idx, cnt, nb);
+    k_csc_count<<<(unsigned)nb, 256, sm, st>>>(m, n, nnz, ptr, idx, cnt, plan.rb);
     k_csc_scan_blocks<<<(unsigned)((n + 31) / 32), 1024, 0, st>>>(n, nb, cnt, tot);
     k_csc_colptr<<<1, 1024, 0, st>>>(n, tot, cptr);
-    k_csc_scatter<TV><<<(unsigned)nb, 32, sm, st>>>(m, n, nnz, ptr, idx, val, cnt, cptr, ridx,
-                                                   cval, nb);
+    k_csc_scatter<TV><<<(unsigned)nb, 256, 2 * sm, st>>>(m, n, nnz, ptr, idx, val, cnt, cptr,
+                                                        ridx, cval, plan.rb);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_csr_to_csc<float>(int64_t, int64_t, int64_t, const int64_t *,
                                               const int32_t *, const float *, int64_t *,
-                                              int32_t *, float *, int32_t *, int64_t *, int64_t,
+                                              int32_t *, float *, int32_t *, int64_t *, CscPlan,
                                               cudaStream_t);
 template cudaError_t launch_csr_to_csc<double>(int64_t, int64_t, int64_t, const int64_t *,
                                                const int32_t *, const double *, int64_t *,
                                                int32_t *, double *, int32_t *, int64_t *,
-                                               int64_t, cudaStream_t);
+                                               CscPlan, cudaStream_t);
 
 }  // namespace ocf

@@ -123,7 +123,8 @@ def test_empty_inputs():
 
 
 # ---------------------------------------------------------------- CSR -> CSC
-@pytest.mark.parametrize("m,n,density", [(500, 300, 0.05), (4096, 1024, 0.05), (37, 5, 0.9)])
+@pytest.mark.parametrize("m,n,density", [(500, 300, 0.05), (4096, 1024, 0.05), (37, 5, 0.9),
+                                         (10000, 1000, 0.01)])
 def test_csr_to_csc_bit_exact(orc, m, n, density):
     prob = synth.make_sparse_problem(seed=m, m=m, n_cpu=1, n_gpu=n, rank=4, density=density,
                                      k=4, n_heldout=8)
