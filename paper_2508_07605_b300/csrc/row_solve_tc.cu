@@ -79,7 +79,6 @@ template <int KP, typename TC> struct alignas(16) TcSmem {
         };
         float b[KP];
         TC col[2][KP];
-        TC dinv[KP];
     } seg[SPW];
 };
 
@@ -319,43 +318,65 @@ k_row_solve_tc(SolveArgs<float> a) {
                 if (e == q) A[e] += TC(a.lambda);
             __syncwarp();   // every lane has read G before L overwrites it
 
-            bool fail = false;
+            // Right-looking Cholesky, lane q owning row q.  l = A[q][p] / sqrt(piv)
+            // for every lane (the pivot lane gets sqrt(piv) itself); a pivot that
+            // is not > 0 turns the solution non-finite, which flags the row.
+            TC dv[KP];
+            TC myinv = TC(0);
 #pragma unroll
             for (int p = 0; p < KP; ++p) {
-                TC piv = __shfl_sync(FULL, A[p], p, KP);
-                if (!(piv > TC(0))) {
-                    fail = true;
-                    piv = TC(1);
-                }
+                const TC piv = __shfl_sync(FULL, A[p], p, KP);
                 const TC inv = rsq(piv);
-                const TC l = (q == p) ? piv * inv : A[p] * inv;
+                dv[p] = inv;
+                if (q == p) myinv = inv;
+                const TC l = A[p] * inv;
                 A[p] = l;
                 TC *cb = S.col[p & 1];
                 if (writer) cb[q] = l;
-                if (writer && q == 0) S.dinv[p] = inv;
                 __syncwarp();
+                constexpr int VN = 16 / (int)sizeof(TC);
 #pragma unroll
-                for (int r = p + 1; r < KP; ++r) A[r] = my_fma(-l, cb[r], A[r]);
+                for (int r4 = ((p + 1) / VN) * VN; r4 < KP; r4 += VN) {
+                    if constexpr (VN == 4) {
+                        const float4 x = *reinterpret_cast<const float4 *>(cb + r4);
+                        const TC xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (r4 + e > p) A[r4 + e] = my_fma(-l, xs[e], A[r4 + e]);
+                    } else {
+                        const double2 x = *reinterpret_cast<const double2 *>(cb + r4);
+                        const TC xs[2] = {(TC)x.x, (TC)x.y};
+#pragma unroll
+                        for (int e = 0; e < 2; ++e)
+                            if (r4 + e > p) A[r4 + e] = my_fma(-l, xs[e], A[r4 + e]);
+                    }
+                }
             }
-            TC y = bt, yq = TC(0);
+            // forward substitution L y = b: after step q, y on lane q is final
+            TC y = bt;
 #pragma unroll
             for (int p = 0; p < KP; ++p) {
-                const TC yp = __shfl_sync(FULL, y, p, KP) * S.dinv[p];
-                if (q == p) yq = yp;
+                const TC yp = __shfl_sync(FULL, y, p, KP) * dv[p];
                 if (q > p) y = my_fma(-A[p], yp, y);
             }
+            const TC yq = y * myinv;
             if (writer) {
 #pragma unroll
                 for (int e = 0; e < KP; ++e) S.L[q][e] = A[e];
             }
             __syncwarp();
-            TC x = yq, xq = TC(0);
+            // back substitution L^T x = y
+            TC x = yq;
 #pragma unroll
             for (int p = KP - 1; p >= 0; --p) {
-                const TC xp = __shfl_sync(FULL, x, p, KP) * S.dinv[p];
-                if (q == p) xq = xp;
+                const TC xp = __shfl_sync(FULL, x, p, KP) * dv[p];
                 if (q < p) x = my_fma(-S.L[p][q], xp, x);
             }
+            TC xq = x * myinv;
+            bool fail = !isfinite((double)xq);
+#pragma unroll
+            for (int off = 1; off < KP; off <<= 1)
+                fail |= __shfl_xor_sync(FULL, (int)fail, off) != 0;
             const int64_t i = base + slot;
             if (writer && i < a.m) {
                 int32_t st = ST_OK;
@@ -395,7 +416,7 @@ cudaError_t prepare_row_solve_tc() {
     return tc_attr<32, double, 4>();
 }
 
-constexpr int64_t LONG_ROW_TC = 512;   // mean observations per row that warrant 4 warps
+constexpr int64_t LONG_ROW_TC = 96;   // mean observations per row that warrant 4 warps
 
 template <int KP, typename TC>
 static cudaError_t launch_tc_kp(const SolveArgs<float> &a, cudaStream_t st) {
