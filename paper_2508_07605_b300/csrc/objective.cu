@@ -25,6 +25,25 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Compensated (Kahan) running sum in the factor type: B300 executes FP64 at a
+// small fraction of the FP32 rate, so the FP32 path accumulates in FP32 with a
+// compensation term and touches FP64 only once per CTA.
+template <typename T> struct KSum {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T x) {
+        const T y = x - c;
+        const T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
 // Per CTA: a fixed contiguous range of rows (one warp per row, lanes over the
 // row's entries, u held in registers, v_j read as 16-byte vectors) and a fixed
 // slice of V's rows for |V|^2.  part[3b .. 3b+2] = (SSE, |U|^2, |V|^2) of CTA b.
@@ -41,14 +60,14 @@ k_objective_rows(int64_t m, int64_t nnz, const int64_t *__restrict__ ptr,
     const int64_t G = gridDim.x;
     const int64_t per = (m + G - 1) / G;
     const int64_t r0 = blockIdx.x * per, r1 = min(m, r0 + per);
-    double sse_w = 0.0, nu_w = 0.0, nv_w = 0.0;
+    KSum<TV> sse_w, nu_w;
     for (int64_t i = r0 + warp; i < r1; i += OBJ_WARPS) {
         int64_t beg, end;
         const bool ok = row_bounds(ptr, i, nnz, beg, end);
         TV u[KP];
 #pragma unroll
         for (int p = 0; p < KP; ++p) u[p] = (p < k) ? U[i * ldu + p] : TV(0);
-        double sse = 0.0;
+        TV sse = TV(0);
         for (int64_t t = beg + lane; t < end; t += 32) {
             const int32_t j = __ldg(idx + t);
             if (j < 0 || (int64_t)j >= n) continue;
@@ -60,34 +79,32 @@ k_objective_rows(int64_t m, int64_t nnz, const int64_t *__restrict__ ptr,
 #pragma unroll
                 for (int e = 0; e < VN; ++e) d = my_fma(u[e4 * VN + e], vget(x, e), d);
             }
-            const double e = (double)__ldg(val + t) - (double)d;
-            sse += e * e;
+            const TV e = __ldg(val + t) - d;
+            sse = my_fma(e, e, sse);
         }
-        sse = warp_sum(sse);
+        sse = warp_sum_t(sse);
         if (lane == 0) {
-            double nu = 0.0;
+            TV nu = TV(0);
 #pragma unroll
-            for (int p = 0; p < KP; ++p) nu += (double)u[p] * (double)u[p];
-            sse_w += sse;
-            nu_w += nu;
+            for (int p = 0; p < KP; ++p) nu = my_fma(u[p], u[p], nu);
+            sse_w.add(sse);
+            nu_w.add(nu);
             if (row_rmse) {
                 const int64_t s = end - beg;
-                row_rmse[i] = (ok && s > 0) ? (float)sqrt(sse / (double)s) : 0.0f;
+                row_rmse[i] = (ok && s > 0) ? (float)sqrt((double)sse / (double)s) : 0.0f;
             }
         }
     }
     // this CTA's slice of V (rows of KP elements, padding is zero)
     const int64_t vper = (n + G - 1) / G;
     const int64_t v0 = blockIdx.x * vper * KP, v1 = min(n, (blockIdx.x + 1) * vper) * KP;
-    for (int64_t e = v0 + threadIdx.x; e < v1; e += blockDim.x) {
-        const double x = (double)V[e];
-        nv_w += x * x;
-    }
-    nv_w = warp_sum(nv_w);
+    TV nv = TV(0);
+    for (int64_t e = v0 + threadIdx.x; e < v1; e += blockDim.x) nv = my_fma(V[e], V[e], nv);
+    nv = warp_sum_t(nv);
     if (lane == 0) {
-        ws[warp][0] = sse_w;
-        ws[warp][1] = nu_w;
-        ws[warp][2] = nv_w;
+        ws[warp][0] = (double)sse_w.s - (double)sse_w.c;
+        ws[warp][1] = (double)nu_w.s - (double)nu_w.c;
+        ws[warp][2] = (double)nv;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -103,13 +120,12 @@ k_objective_rows(int64_t m, int64_t nnz, const int64_t *__restrict__ ptr,
     }
 }
 
-__global__ void __launch_bounds__(1024)
+// One warp: a few FP64 additions per lane instead of a CTA-wide FP64 tree.
+__global__ void __launch_bounds__(32)
 k_objective_final(int64_t G, const double *__restrict__ part, double lambda,
                   double *__restrict__ J) {
-    __shared__ double ws[32][3];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double a = 0.0, b = 0.0, c = 0.0;
-    for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
+    for (int64_t g = threadIdx.x; g < G; g += 32) {
         a += part[3 * g];
         b += part[3 * g + 1];
         c += part[3 * g + 2];
@@ -117,21 +133,7 @@ k_objective_final(int64_t G, const double *__restrict__ part, double lambda,
     a = warp_sum(a);
     b = warp_sum(b);
     c = warp_sum(c);
-    if (lane == 0) {
-        ws[w][0] = a;
-        ws[w][1] = b;
-        ws[w][2] = c;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0, sc = 0.0;
-        for (int i = 0; i < 32; ++i) {
-            sa += ws[i][0];
-            sb += ws[i][1];
-            sc += ws[i][2];
-        }
-        *J = sa + lambda * (sb + sc);
-    }
+    if (threadIdx.x == 0) *J = a + lambda * (b + c);
 }
 
 template <typename TV>
@@ -155,7 +157,7 @@ cudaError_t launch_objective(int64_t m, int64_t nnz, const int64_t *ptr, const i
             break;
         default: return cudaErrorInvalidValue;
     }
-    k_objective_final<<<1, 1024, 0, st>>>(G, part, lambda, J_out);
+    k_objective_final<<<1, 32, 0, st>>>(G, part, lambda, J_out);
     return cudaGetLastError();
 }
 

@@ -21,9 +21,10 @@
 namespace ocf {
 
 struct Cand {
-    float sv;
-    float cg;
-    int32_t j;
+    float sv;    // saving
+    float cg;    // c + g
+    int32_t j;   // setting (-1: none)
+    float Ethr;  // screening threshold derived from this candidate's exact energy
 };
 
 // a better than b?  (saving desc, c+g asc, index asc; j < 0 means none)
@@ -35,16 +36,87 @@ __device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
     return a.j < b.j;
 }
 
-__device__ __forceinline__ void alg2_consider(Cand &best, float tb, float t, float cg, float Eb,
-                                              float gamma, int32_t j) {
-    if (!(tb > 0.0f) || !(t > 0.0f)) return;
-    const float p = __fdiv_rn(tb, t);
-    const float loss = __fsub_rn(1.0f, p);
-    if (!(loss <= gamma)) return;
+// Per-row constants of the selection.  loss(t) = 1 - t_b / t is evaluated as
+// fl(1 - fl(t_b / t)), which is non-decreasing in t (correctly rounded
+// division and subtraction are monotone), so "loss <= gamma" holds exactly for
+// 0 < t <= tstar, the largest float that passes; tstar is found by bisection
+// over float bit patterns.  tstar = -1 when the baseline runtime is not > 0.
+struct RowCtx {
+    float tb, tstar, rtb;
+};
+
+__device__ __forceinline__ RowCtx alg2_row(float tb, float gamma) {
+    RowCtx r{tb, -1.0f, 0.0f};
+    if (!(tb > 0.0f)) return r;
+    r.rtb = __frcp_rn(tb);
+    auto ok = [&](uint32_t bits) {
+        const float t = __uint_as_float(bits);
+        return __fsub_rn(1.0f, __fdiv_rn(tb, t)) <= gamma;
+    };
+    uint32_t lo = 0u, hi = 0x7f7fffffu;   // ok(tiny t) always; bisect up to FLT_MAX
+    if (ok(hi)) {
+        r.tstar = __uint_as_float(0x7f800000u);   // every finite t > 0 is valid
+        return r;
+    }
+    while (hi - lo > 1u) {
+        const uint32_t mid = lo + (hi - lo) / 2u;
+        if (ok(mid)) lo = mid; else hi = mid;
+    }
+    r.tstar = __uint_as_float(lo);
+    return r;
+}
+
+// Exact FP32 evaluation (the order the oracle fixes), reached only by
+// candidates the screen cannot exclude.  The screen: E ~ cg * t / t_b from two
+// multiplies is within 2^-20 of the exact E = fl(cg / fl(t_b / t)); a candidate
+// whose estimate exceeds best.Ethr = (E_best + 2^-16 (E_base + E_best)) (1 + 2^-19)
+// has an exact energy so far above the best's that its saving is strictly
+// smaller, so it can neither win nor tie.
+__device__ __forceinline__ void alg2_consider(Cand &best, const RowCtx &r, float t, float cg,
+                                              float Eb, int32_t j) {
+    if (!(t > 0.0f) || !(t <= r.tstar)) return;
+    if (best.j >= 0 && __fmul_rn(__fmul_rn(cg, t), r.rtb) > best.Ethr) return;
+    const float p = __fdiv_rn(r.tb, t);
     const float E = __fdiv_rn(cg, p);
     const float sv = __fdiv_rn(__fsub_rn(Eb, E), Eb);
-    Cand c{sv, cg, j};
+    const float thr = __fmul_rn(__fadd_rn(E, __fmul_rn(1.52587890625e-05f, __fadd_rn(Eb, E))),
+                                1.0000019073486328f);
+    Cand c{sv, cg, j, thr};
     if (better(c, best)) best = c;
+}
+
+// Cheap energy estimate cg * t / t_b of a valid element; NaN when invalid, so
+// fminf ignores it and every comparison with a bound is false.
+__device__ __forceinline__ float alg2_estimate(const RowCtx &r, float t, float cg) {
+    if (!(t > 0.0f) || !(t <= r.tstar)) return __int_as_float(0x7fffffff);
+    return __fmul_rn(__fmul_rn(cg, t), r.rtb);
+}
+
+// Screening bound from an estimate: an element whose estimate exceeds
+// bound(Emin) has an exact energy beyond E(argmin) + 2^-16 (E_base + E), so it
+// can neither win nor tie against the element that produced Emin.
+__device__ __forceinline__ float alg2_bound(float Emin, float Eb) {
+    const float hi = __fmul_rn(Emin, 1.0000038146972656f);   // estimate error 2^-20, twice
+    return __fmul_rn(__fadd_rn(hi, __fmul_rn(1.52587890625e-05f, __fadd_rn(Eb, hi))),
+                     1.0000019073486328f);
+}
+
+// Exact evaluation of an element that survived the screen (t valid).
+__device__ __forceinline__ void alg2_exact(Cand &best, const RowCtx &r, float t, float cg,
+                                           float Eb, int32_t j) {
+    const float p = __fdiv_rn(r.tb, t);
+    const float E = __fdiv_rn(cg, p);
+    const float sv = __fdiv_rn(__fsub_rn(Eb, E), Eb);
+    const float thr = __fmul_rn(__fadd_rn(E, __fmul_rn(1.52587890625e-05f, __fadd_rn(Eb, E))),
+                                1.0000019073486328f);
+    Cand c{sv, cg, j, thr};
+    if (better(c, best)) best = c;
+}
+
+template <int LANES> __device__ __forceinline__ float group_min(float v) {
+#pragma unroll
+    for (int off = 1; off < LANES; off <<= 1) v = fminf(v, __shfl_xor_sync(FULL, v, off));
+    return v;
 }
 
 __device__ __forceinline__ Cand shfl_cand(const Cand &c, int off) {
@@ -52,74 +124,82 @@ __device__ __forceinline__ Cand shfl_cand(const Cand &c, int off) {
     o.sv = __shfl_xor_sync(FULL, c.sv, off);
     o.cg = __shfl_xor_sync(FULL, c.cg, off);
     o.j = __shfl_xor_sync(FULL, c.j, off);
+    o.Ethr = __shfl_xor_sync(FULL, c.Ethr, off);
     return o;
 }
 
 constexpr int PT = 256;
 
-template <typename TV>
-__device__ __forceinline__ void load4(const TV *p, TV (&x)[4]) {
-    if constexpr (sizeof(TV) == 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(p);
-        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-    } else {
-        const double2 v0 = *reinterpret_cast<const double2 *>(p);
-        const double2 v1 = *reinterpret_cast<const double2 *>(p + 2);
-        x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
-    }
-}
-
 // T[i][j] = sum_p U[i][p] V[j][p] as one FMA chain in p order (in TV), then
 // the selection on float(T).  The baseline runtime uses the identical chain so
 // that t_b equals T[i][base] bit for bit and the baseline's loss is exactly 0.
-// Tile: BM rows x BN settings per step, 256 threads as TY x TX with TY = BM/4
-// (each thread a 4 x 4 micro-tile); BM = 16 keeps enough CTAs in flight when
-// there are few rows, BM = 64 reuses each V tile over more rows when there
-// are many.
+//
+// Tile: BM rows x BN settings per step, 256 threads as TY x TX (TY = BM/4),
+// each thread 4 rows (ty*4 + r) x 4 settings (tx + TX*c, strided so that a
+// warp reads distinct V rows without bank conflicts).  U and V tiles are kept
+// row-major in shared memory (rows padded by 16 bytes) and filled with 16-byte
+// copies; the inner loop reads 4 consecutive p at a time (16-byte loads).
+// BM = 16 keeps enough CTAs busy when rows are few, BM = 64 reuses each V
+// tile over more rows when they are many.
 template <typename TV, int KP, int BM>
 __global__ void __launch_bounds__(PT) k_predict_select(PredictArgs<TV> a) {
     constexpr int TY = BM / 4, TX = PT / TY, BN = 4 * TX;
     constexpr int WPR = TX > 32 ? TX / 32 : 1;       // warps sharing one row group
-    __shared__ __align__(16) TV Us[KP][BM];
-    __shared__ __align__(16) TV Vs[KP][BN + 4];
+    constexpr int VN = 16 / (int)sizeof(TV);          // elements per 16 bytes
+    constexpr int LD = KP + VN;                       // padded row
+    using VT = typename Vec4<TV>::type;
+    __shared__ __align__(16) TV Us[BM][LD];
+    __shared__ __align__(16) TV Vs[BN][LD];
     __shared__ float cgs[BN];
-    __shared__ float tbs[BM];
+    __shared__ RowCtx rcs[BM];
     __shared__ Cand xw[TY][WPR][4];
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const bool sel = a.cg != nullptr;
     const int64_t row_tiles = (a.m + BM - 1) / BM;
-    const bool vec_store = sizeof(TV) == 4 && (a.n & 3) == 0 &&
-                           ((reinterpret_cast<uintptr_t>(a.T) & 15) == 0);
+    const bool u_vec = (a.ldu % VN) == 0 && a.k == KP &&
+                       (reinterpret_cast<uintptr_t>(a.U) & 15) == 0;
 
     for (int64_t rt = blockIdx.x; rt < row_tiles; rt += gridDim.x) {
         const int64_t r0 = rt * BM;
         __syncthreads();
-        for (int e = tid; e < KP * BM; e += PT) {
-            const int ii = e / KP, p = e % KP;
-            const int64_t r = r0 + ii;
-            TV u = TV(0);
-            if (r < a.m && p < a.k) u = a.U[r * a.ldu + p];
-            Us[p][ii] = u;
+        if (u_vec) {
+            for (int e = tid; e < BM * (KP / VN); e += PT) {
+                const int ii = e / (KP / VN), p4 = e % (KP / VN);
+                const int64_t r = r0 + ii;
+                VT x;
+                if (r < a.m) x = *reinterpret_cast<const VT *>(a.U + r * a.ldu + p4 * VN);
+                else x = VT{};
+                *reinterpret_cast<VT *>(&Us[ii][p4 * VN]) = x;
+            }
+        } else {
+            for (int e = tid; e < BM * KP; e += PT) {
+                const int ii = e / KP, p = e % KP;
+                const int64_t r = r0 + ii;
+                Us[ii][p] = (r < a.m && p < a.k) ? a.U[r * a.ldu + p] : TV(0);
+            }
         }
         __syncthreads();
         if (sel && tid < BM) {
             const TV *vb = a.V + a.base * KP;
             TV acc = TV(0);
 #pragma unroll
-            for (int p = 0; p < KP; ++p) acc = my_fma(Us[p][tid], vb[p], acc);
-            tbs[tid] = (float)acc;
+            for (int p = 0; p < KP; ++p) acc = my_fma(Us[tid][p], vb[p], acc);
+            rcs[tid] = alg2_row((float)acc, a.gamma);
         }
         Cand best[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) best[r] = Cand{0.0f, 0.0f, -1};
+        for (int r = 0; r < 4; ++r) best[r] = Cand{0.0f, 0.0f, -1, 0.0f};
 
         for (int64_t c0 = 0; c0 < a.n; c0 += BN) {
             __syncthreads();
-            for (int e = tid; e < KP * BN; e += PT) {
-                const int jj = e / KP, p = e % KP;
+            for (int e = tid; e < BN * (KP / VN); e += PT) {
+                const int jj = e / (KP / VN), p4 = e % (KP / VN);
                 const int64_t j = c0 + jj;
-                Vs[p][jj] = (j < a.n) ? a.V[j * KP + p] : TV(0);
+                VT x;
+                if (j < a.n) x = __ldg(reinterpret_cast<const VT *>(a.V + j * KP) + p4);
+                else x = VT{};
+                *reinterpret_cast<VT *>(&Vs[jj][p4 * VN]) = x;
             }
             if (sel)
                 for (int e = tid; e < BN; e += PT) cgs[e] = (c0 + e < a.n) ? a.cg[c0 + e] : 0.0f;
@@ -130,39 +210,62 @@ __global__ void __launch_bounds__(PT) k_predict_select(PredictArgs<TV> a) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[r][c] = TV(0);
 #pragma unroll
-            for (int p = 0; p < KP; ++p) {
-                TV u[4], v[4];
-                load4<TV>(&Us[p][ty * 4], u);
-                load4<TV>(&Vs[p][tx * 4], v);
+            for (int p4 = 0; p4 < KP; p4 += VN) {
+                TV u[4][VN], v[4][VN];
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r) {
+                    const VT x = *reinterpret_cast<const VT *>(&Us[ty * 4 + r][p4]);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[r][c] = my_fma(u[r], v[c], acc[r][c]);
+                    for (int e = 0; e < VN; ++e) u[r][e] = vget(x, e);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const VT x = *reinterpret_cast<const VT *>(&Vs[tx + TX * c][p4]);
+#pragma unroll
+                    for (int e = 0; e < VN; ++e) v[c][e] = vget(x, e);
+                }
+#pragma unroll
+                for (int e = 0; e < VN; ++e)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c] = my_fma(u[r][e], v[c][e], acc[r][c]);
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int64_t i = r0 + ty * 4 + r;
-                if (i >= a.m) continue;
-                const int64_t j0 = c0 + tx * 4;
-                if (a.T) {
+                if (a.T && i < a.m) {
                     TV *trow = a.T + i * a.n;
-                    if (vec_store && j0 + 3 < a.n) {
-                        *reinterpret_cast<float4 *>(trow + j0) =
-                            make_float4((float)acc[r][0], (float)acc[r][1], (float)acc[r][2],
-                                        (float)acc[r][3]);
-                    } else {
 #pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (j0 + c < a.n) trow[j0 + c] = acc[r][c];
+                    for (int c = 0; c < 4; ++c) {
+                        const int64_t j = c0 + tx + TX * c;
+                        if (j < a.n) trow[j] = acc[r][c];
                     }
                 }
-                if (sel) {
-                    const float tb = tbs[ty * 4 + r];
+            }
+            if (sel) {
+                constexpr int LANES = TX < 32 ? TX : 32;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const RowCtx rc = rcs[ty * 4 + r];
+                    float est[4];
+                    float emin = __int_as_float(0x7fffffff);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int64_t j = c0 + tx + TX * c;
+                        est[c] = (j < a.n) ? alg2_estimate(rc, (float)acc[r][c], cgs[tx + TX * c])
+                                           : __int_as_float(0x7fffffff);
+                        emin = fminf(emin, est[c]);
+                    }
+                    // lanes sharing this row agree on one bound (warp-uniform screen)
+                    emin = group_min<LANES>(emin);
+                    float bound = alg2_bound(emin, a.Ebase);
+                    if (best[r].j >= 0) bound = fminf(bound, best[r].Ethr);
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
-                        if (j0 + c < a.n)
-                            alg2_consider(best[r], tb, (float)acc[r][c], cgs[tx * 4 + c],
-                                          a.Ebase, a.gamma, (int32_t)(j0 + c));
+                        if (est[c] <= bound)
+                            alg2_exact(best[r], rc, (float)acc[r][c], cgs[tx + TX * c], a.Ebase,
+                                       (int32_t)(c0 + tx + TX * c));
                 }
             }
         }
@@ -217,7 +320,9 @@ static cudaError_t launch_bm(const PredictArgs<TV> &a, cudaStream_t st) {
 
 template <typename TV> cudaError_t launch_predict_select(const PredictArgs<TV> &a, cudaStream_t st) {
     if (a.m <= 0 || a.n <= 0) return cudaSuccess;
-    if (sizeof(TV) == 4 && (a.m + 63) / 64 < 2 * NUM_SMS_HINT) return launch_bm<TV, 16>(a, st);
+    if constexpr (sizeof(TV) == 4) {
+        if ((a.m + 63) / 64 < 2 * NUM_SMS_HINT) return launch_bm<TV, 16>(a, st);
+    }
     return launch_bm<TV, 64>(a, st);
 }
 
@@ -234,10 +339,27 @@ k_select(int64_t m, int64_t n, const float *__restrict__ T, int64_t ld,
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = w; i < m; i += nw) {
         const float *t = T + i * ld;
-        const float tb = __ldg(t + base);
-        Cand b{0.0f, 0.0f, -1};
-        for (int64_t j = lane; j < n; j += 32)
-            alg2_consider(b, tb, __ldg(t + j), __ldg(cg + j), Eb, gamma, (int32_t)j);
+        const RowCtx rc = alg2_row(__ldg(t + base), gamma);
+        Cand b{0.0f, 0.0f, -1, 0.0f};
+        constexpr int U8 = 8;   // 8 steps of 32 settings in flight per load batch
+        for (int64_t j0 = 0; j0 < n; j0 += 32 * U8) {
+            float tj[U8], cj[U8];
+#pragma unroll
+            for (int u = 0; u < U8; ++u) {
+                const int64_t j = j0 + 32 * u + lane;
+                tj[u] = (j < n) ? __ldg(t + j) : 0.0f;
+                cj[u] = (j < n) ? __ldg(cg + j) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < U8; ++u) {
+                const int64_t j = j0 + 32 * u + lane;
+                const float est =
+                    (j < n) ? alg2_estimate(rc, tj[u], cj[u]) : __int_as_float(0x7fffffff);
+                float bound = alg2_bound(group_min<32>(est), Eb);
+                if (b.j >= 0) bound = fminf(bound, b.Ethr);
+                if (est <= bound) alg2_exact(b, rc, tj[u], cj[u], Eb, (int32_t)j);
+            }
+        }
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const Cand o = shfl_cand(b, off);

@@ -373,7 +373,7 @@ k_row_solve_tc(SolveArgs<float> a) {
                 if (q < p) x = my_fma(-S.L[p][q], xp, x);
             }
             TC xq = x * myinv;
-            bool fail = !isfinite((double)xq);
+            bool fail = !isfinite(xq);
 #pragma unroll
             for (int off = 1; off < KP; off <<= 1)
                 fail |= __shfl_xor_sync(FULL, (int)fail, off) != 0;
