@@ -41,6 +41,23 @@ def algorithmic_flops_half(nnz, rows, k):
     return nnz * (k * (k + 1) + 2 * k) + rows * (k ** 3 / 3.0 + 2 * k * k)
 
 
+def profiled_traffic(kernel_src, profile_md):
+    """DRAM bytes per launch (U-half + V-half) from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    import hashlib
+    import re
+    try:
+        src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        text = open(profile_md).read()
+    except OSError:
+        return None
+    m = re.search(r"sha256 \(first 16 hex\): ([0-9a-f]{16})", text)
+    b = re.search(r"\| dram_bytes_per_launch \| (\d+) \| (\d+) \|", text)
+    if not m or not b or m.group(1) != src_hash:
+        return None
+    return (int(b.group(1)) + int(b.group(2))) / 2.0
+
+
 def fp32_alu_peak_tflops(sm_mhz):
     # 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -326,7 +343,11 @@ def run_gpu(args):
                          "gate": "gpu <= oracle + 1e-3", "pass": rmse_gpu <= rmse_orc + 1e-3},
         "roofline": {"kernel": "k_row_solve_tc<16,float> (U-half + V-half)", "bound": "alu",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic(
+                         os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "row_solve_tc.cu"),
+                         os.path.join(ROOT, "profiles", "rowsolve_tc_c2.md")),
+                     "traffic_unit": "DRAM bytes per launch (mean of U- and V-half, ncu)",
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (derived)",
                      "launch_us": {"u_half": t_u * 1e6, "v_half": t_v * 1e6}},
         "cpu_baseline": {"value": units / t_orc, "unit": "row-solves/s",
