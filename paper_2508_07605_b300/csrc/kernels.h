@@ -21,6 +21,8 @@ template <typename TV> struct SolveArgs {
     int kout;
     int32_t *status;      // per-row status or null
     double lambda;
+    const void *Fb = nullptr;   // BF16 split copy of F: rows [hi (KP) | lo (KP)], BF16 path
+    void *outb = nullptr;       // optional split BF16 copy of the output rows (stride 2*KP)
 };
 
 template <typename TV, typename TC>
@@ -42,9 +44,9 @@ cudaError_t launch_csr_to_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *
 cudaError_t prepare_csr_to_csc(int64_t n_max);
 cudaError_t prepare_row_solve();
 
-// FP32 path with the Gram and RHS on tensor cores (3-pass TF32 mma.sync),
-// KP in {16, 32}.
-cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp64,
+// FP32 path with the Gram and RHS on tensor cores, KP in {16, 32}: 3-pass TF32
+// mma.sync (FP32 accuracy), or BF16 operands (bf16 = true; a.Fb required).
+cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp64, bool bf16,
                                 cudaStream_t st);
 cudaError_t prepare_row_solve_tc();
 
@@ -86,6 +88,9 @@ template <typename TV>
 cudaError_t launch_unpack_rows(const TV *src, int64_t rows, int KP, int k, TV *dst,
                                cudaStream_t st);                  // [rows,KP] -> [rows,k]
 cudaError_t launch_to_bf16(const float *src, int64_t count, void *dst, cudaStream_t st);
+// rows of KP floats -> rows [bf16(x) (KP) | bf16(x - bf16(x)) (KP)]
+cudaError_t launch_to_bf16_split(const float *src, int64_t rows, int KP, void *dst,
+                                 cudaStream_t st);
 template <typename TV>
 cudaError_t launch_dense_to_csr(const TV *P, int64_t m, int64_t n, int64_t ld, int64_t *ptr,
                                 int32_t *idx, TV *val, cudaStream_t st);

@@ -45,6 +45,20 @@ __global__ void k_to_bf16(const float *__restrict__ src, int64_t count,
         dst[e] = __float2bfloat16_rn(src[e]);
 }
 
+__global__ void k_to_bf16_split(const float *__restrict__ src, int64_t rows, int KP,
+                                __nv_bfloat16 *__restrict__ dst) {
+    const int64_t total = rows * KP;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / KP;
+        const int p = (int)(e % KP);
+        const float x = src[e];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        dst[r * 2 * KP + p] = hi;
+        dst[r * 2 * KP + KP + p] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
 template <typename TV>
 __global__ void k_dense_to_csr(const TV *__restrict__ P, int64_t m, int64_t n, int64_t ld,
                                int64_t *__restrict__ ptr, int32_t *__restrict__ idx,
@@ -106,6 +120,14 @@ cudaError_t launch_to_bf16(const float *src, int64_t count, void *dst, cudaStrea
     if (count <= 0) return cudaSuccess;
     k_to_bf16<<<grid_for(count, 256), 256, 0, st>>>(src, count,
                                                     reinterpret_cast<__nv_bfloat16 *>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16_split(const float *src, int64_t rows, int KP, void *dst,
+                                 cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    k_to_bf16_split<<<grid_for(rows * KP, 256), 256, 0, st>>>(
+        src, rows, KP, reinterpret_cast<__nv_bfloat16 *>(dst));
     return cudaGetLastError();
 }
 

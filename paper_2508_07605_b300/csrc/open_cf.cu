@@ -149,13 +149,16 @@ int run_graph(open_cf_t *h, std::vector<int64_t> key, cudaStream_t stream, F &&e
     return OPEN_CF_OK;
 }
 
-// One ALS half-step with the handle's precision.
+// One ALS half-step with the handle's precision.  In BF16-Gram mode a.Fb is
+// the BF16 copy of a.F (and a.outb, if set, receives the BF16 copy of the output).
 template <typename TV>
 cudaError_t half_step(open_cf_t *h, const SolveArgs<TV> &a, cudaStream_t st) {
     if constexpr (sizeof(TV) == 8) {
         return launch_row_solve<double, double>(a, h->KP, st);
     } else {
-        if (h->KP >= 16) return launch_row_solve_tc(a, h->KP, h->cfg.cholesky_fp64 != 0, st);
+        const bool bf = h->cfg.precision == OPEN_CF_BF16_GRAM;
+        if (bf || h->KP >= 16)
+            return launch_row_solve_tc(a, h->KP, h->cfg.cholesky_fp64 != 0, bf, st);
         if (h->cfg.cholesky_fp64) return launch_row_solve<float, double>(a, h->KP, st);
         return launch_row_solve<float, float>(a, h->KP, st);
     }
@@ -186,6 +189,8 @@ int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const i
     CK(h, ensure(h, h->cnt, sizeof(int32_t) * n * nb));
     CK(h, ensure(h, h->tot, sizeof(int64_t) * n));
     CK(h, ensure(h, h->part, sizeof(double) * 3 * objective_parts(std::max<int64_t>(m, n))));
+    const bool bf = h->cfg.precision == OPEN_CF_BF16_GRAM;
+    if (bf) CK(h, ensure(h, h->Ub16, 4 * std::max<int64_t>(m, 1) * KP));   // split BF16 rows
     TV *Uw = (TV *)h->U_w.p;
     TV *V = (TV *)h->V.p;
     int64_t *cptr = (int64_t *)h->csc_ptr.p;
@@ -202,6 +207,10 @@ int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const i
         if (e != cudaSuccess) return e;
         for (int s = 0; s < sweeps; ++s) {
             SolveArgs<TV> ua{m, nnz, ptr, idx, val, V, n, Uw, KP, KP, row_status, lam};
+            if (bf) {
+                ua.Fb = h->Vb16.p;
+                ua.outb = h->Ub16.p;
+            }
             if ((e = half_step<TV>(h, ua, st)) != cudaSuccess) return e;
             if (J_hist &&
                 (e = launch_objective<TV>(m, nnz, ptr, idx, val, Uw, KP, k, V, n, KP, lam,
@@ -209,6 +218,10 @@ int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const i
                     cudaSuccess)
                 return e;
             SolveArgs<TV> va{n, nnz, cptr, cidx, cval, Uw, m, V, KP, KP, col_status, lam};
+            if (bf) {
+                va.Fb = h->Ub16.p;
+                va.outb = h->Vb16.p;
+            }
             if ((e = half_step<TV>(h, va, st)) != cudaSuccess) return e;
             if (J_hist &&
                 (e = launch_objective<TV>(m, nnz, ptr, idx, val, Uw, KP, k, V, n, KP, lam,
@@ -250,7 +263,6 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
     if (cfg->precision != OPEN_CF_FP64 && cfg->precision != OPEN_CF_FP32 &&
         cfg->precision != OPEN_CF_BF16_GRAM)
         return OPEN_CF_INVALID_ARG;
-    if (cfg->precision == OPEN_CF_BF16_GRAM) return OPEN_CF_UNSUPPORTED;
     if (cfg->n_cpu_caps < 0 || cfg->n_gpu_caps < 0 ||
         ((cfg->n_cpu_caps > 0) != (cfg->n_gpu_caps > 0)))
         return OPEN_CF_INVALID_ARG;
@@ -270,6 +282,7 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
     h->device = cfg->device;
     h->k = cfg->k;
     h->KP = padded_k(cfg->k);
+    if (cfg->precision == OPEN_CF_BF16_GRAM && h->KP < 16) h->KP = 16;   // tensor-core tiles
     h->f64 = cfg->precision == OPEN_CF_FP64;
     h->esz = h->f64 ? 8 : 4;
     if (cfg->n_cpu_caps > 0) {
@@ -331,6 +344,10 @@ int open_cf_set_V(open_cf_t *h, const void *V, int64_t n, void *stream) {
         CK(h, launch_pack_rows<double>(as<double>(V), n, h->k, h->k, (double *)h->V.p, h->KP, st));
     else
         CK(h, launch_pack_rows<float>(as<float>(V), n, h->k, h->k, (float *)h->V.p, h->KP, st));
+    if (h->cfg.precision == OPEN_CF_BF16_GRAM) {
+        CK(h, ensure(h, h->Vb16, 4 * n * h->KP));   // split BF16 rows [hi | lo]
+        CK(h, launch_to_bf16_split((const float *)h->V.p, n, h->KP, h->Vb16.p, st));
+    }
     if (!h->cpu_caps.empty() && h->n != n) {
         std::vector<float> cg(n);
         const int ng = (int)h->gpu_caps.size();
@@ -446,6 +463,7 @@ int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
         } else {
             SolveArgs<float> a{m_new, nnz, row_ptr, col, as<float>(val), (float *)h->V.p,
                                h->n, (float *)U_out, h->k, h->k, status, h->cfg.lambda};
+            if (h->cfg.precision == OPEN_CF_BF16_GRAM) a.Fb = h->Vb16.p;
             CK(h, half_step<float>(h, a, st));
         }
         return OPEN_CF_OK;

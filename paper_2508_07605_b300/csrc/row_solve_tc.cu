@@ -23,6 +23,7 @@
 // partial Grams in a fixed order through shared memory, and warp 0 solves.
 // Staging: lane t loads observation t's factor row (16-byte loads) into a
 // padded tile (stride KP+8 floats: the fragment loads are conflict-free).
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -64,13 +65,37 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_by
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
+// BF16 operands: m16n8k16 MMA with FP32 accumulation, fragments of the staged
+// row-major tile read transposed by ldmatrix.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void *p) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(s));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
-template <int KP, typename TC> struct alignas(16) TcSmem {
+template <int KP, typename TC, bool BF> struct alignas(16) TcSmem {
     static constexpr int SPW = 32 / KP;
-    static constexpr int LD = KP + 8;
-    float stage[2][32][LD];   // double-buffered staged factor rows
+    // Staged rows padded to KP+8 elements (conflict-free fragment loads,
+    // 16-byte aligned rows).  FP32: one tile of 32 rows per buffer.  BF16: the
+    // hi and lo halves of each split row go to two tiles of 32 BF16 rows.
+    static constexpr int ROWB = (BF ? 2 : 4) * (KP + 8);
+    alignas(16) unsigned char stage[2][BF ? 2 : 1][32][ROWB];   // double-buffered
     float sr[2][32];
     struct alignas(16) Seg {
         union {
@@ -90,14 +115,14 @@ template <int KP> struct Blocks {
     __device__ static constexpr int nb_of(int t) { return KP == 16 ? t : (t < 2 ? t : t - 2); }
 };
 
-template <int KP, typename TC, int WPS>
+template <int KP, typename TC, int WPS, bool BF>
 __global__ void __launch_bounds__(WPS == 1 ? (sizeof(TC) == 8 && KP == 32 ? 128 : 256) : 32 * WPS)
 k_row_solve_tc(SolveArgs<float> a) {
     constexpr int WARPS = (WPS == 1) ? ((sizeof(TC) == 8 && KP == 32) ? 4 : 8) : WPS;
     constexpr int SPW = (WPS == 1) ? 32 / KP : 1;   // systems per warp
     constexpr int MB = Blocks<KP>::MB;
     constexpr int NBLK = Blocks<KP>::NBLK;
-    using WS = TcSmem<KP, TC>;
+    using WS = TcSmem<KP, TC, BF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WS *smem = reinterpret_cast<WS *>(smem_raw);
 
@@ -177,11 +202,25 @@ k_row_solve_tc(SolveArgs<float> a) {
             for (int t = 0; t < SPW; ++t) if (t == si) { bg = beg_s[t]; ss = s_s[t]; }
             const int64_t tt = c0 + lane;
             const bool v = tt < ss;
-            const float *src = a.F + (int64_t)j * KP;
+            if constexpr (BF) {
+                // split row [hi (KP bf16) | lo (KP bf16)] -> hi tile, lo tile
+                const unsigned char *src =
+                    reinterpret_cast<const unsigned char *>(a.Fb) + (int64_t)j * KP * 4;
+                constexpr int NCP = 2 * KP / 16;
 #pragma unroll
-            for (int e4 = 0; e4 < KP / 4; ++e4)
-                cp_async16(&W.stage[buf][lane][4 * e4], src + 4 * e4, v ? 16 : 0);
-            cp_async4(&W.sr[buf][lane], v ? (const void *)(a.val + bg + tt) : (const void *)a.F,
+                for (int e = 0; e < NCP; ++e) {
+                    cp_async16(&W.stage[buf][0][lane][16 * e], src + 16 * e, v ? 16 : 0);
+                    cp_async16(&W.stage[buf][1][lane][16 * e], src + 2 * KP + 16 * e, v ? 16 : 0);
+                }
+            } else {
+                const unsigned char *src =
+                    reinterpret_cast<const unsigned char *>(a.F + (int64_t)j * KP);
+                constexpr int NCP = 4 * KP / 16;
+#pragma unroll
+                for (int e = 0; e < NCP; ++e)
+                    cp_async16(&W.stage[buf][0][lane][16 * e], src + 16 * e, v ? 16 : 0);
+            }
+            cp_async4(&W.sr[buf][lane], v ? (const void *)(a.val + bg + tt) : (const void *)a.val,
                       v ? 4 : 0);
         };
 
@@ -213,18 +252,75 @@ k_row_solve_tc(SolveArgs<float> a) {
 #pragma unroll
                 for (int t = 0; t < SPW; ++t) if (t == si) ss = s_s[t];
                 const int buf = w & 1;
-                const int nks = (int)((min((int64_t)32, ss - c0) + 7) / 8);
+                const int cnt = (int)min((int64_t)32, ss - c0);
+                if constexpr (BF) {
+                    // 16 observations per MMA step; fragments of the hi (H) and lo (L)
+                    // tiles from ldmatrix.trans.  S^T S ~ H^T H + H^T L + L^T H and
+                    // S^T r ~ H^T r_h + H^T r_l + L^T r_h: ~16-bit operands.
+                    const int nks = (cnt + 15) / 16;
+                    const __nv_bfloat16 *sH =
+                        reinterpret_cast<const __nv_bfloat16 *>(&W.stage[buf][0][0][0]);
+                    const __nv_bfloat16 *sL =
+                        reinterpret_cast<const __nv_bfloat16 *>(&W.stage[buf][1][0][0]);
+                    constexpr int LDE = WS::ROWB / 2;
+                    const int mi = lane >> 3, rr = lane & 7;
+                    for (int ks = 0; ks < nks; ++ks) {
+                        const int k0 = ks * 16;
+                        uint32_t aH[MB][4], aL[MB][4];
+#pragma unroll
+                        for (int mb = 0; mb < MB; ++mb) {
+                            const int off = (k0 + (mi >> 1) * 8 + rr) * LDE + mb * 16 + (mi & 1) * 8;
+                            ldsm_x4_trans(aH[mb], sH + off);
+                            ldsm_x4_trans(aL[mb], sL + off);
+                        }
+                        float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+                        if (gid == 0) {
+                            r0 = W.sr[buf][k0 + 2 * tid4];
+                            r1 = W.sr[buf][k0 + 2 * tid4 + 1];
+                            r2 = W.sr[buf][k0 + 2 * tid4 + 8];
+                            r3 = W.sr[buf][k0 + 2 * tid4 + 9];
+                        }
+                        const float h0 = __bfloat162float(__float2bfloat16_rn(r0));
+                        const float h1 = __bfloat162float(__float2bfloat16_rn(r1));
+                        const float h2 = __bfloat162float(__float2bfloat16_rn(r2));
+                        const float h3 = __bfloat162float(__float2bfloat16_rn(r3));
+                        const uint32_t rh0 = pack_bf16(h0, h1), rh1 = pack_bf16(h2, h3);
+                        const uint32_t rl0 = pack_bf16(r0 - h0, r1 - h1);
+                        const uint32_t rl1 = pack_bf16(r2 - h2, r3 - h3);
+#pragma unroll
+                        for (int sx = 0; sx < SPW; ++sx) {
+                            if (sx != si) continue;
+#pragma unroll
+                            for (int tb = 0; tb < NBLK; ++tb) {
+                                const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
+                                const int sm = nb >> 1, h = nb & 1;
+                                mma_bf16(d[sx][tb], aL[mb], aH[sm][h], aH[sm][2 + h]);
+                                mma_bf16(d[sx][tb], aH[mb], aL[sm][h], aL[sm][2 + h]);
+                                mma_bf16(d[sx][tb], aH[mb], aH[sm][h], aH[sm][2 + h]);
+                            }
+#pragma unroll
+                            for (int mb = 0; mb < MB; ++mb) {
+                                mma_bf16(dr[sx][mb], aL[mb], rh0, rh1);
+                                mma_bf16(dr[sx][mb], aH[mb], rl0, rl1);
+                                mma_bf16(dr[sx][mb], aH[mb], rh0, rh1);
+                            }
+                        }
+                    }
+                } else {
+                const int nks = (cnt + 7) / 8;
+                const float *stf = reinterpret_cast<const float *>(&W.stage[buf][0][0][0]);
+                constexpr int LDF = WS::ROWB / 4;
                 for (int ks = 0; ks < nks; ++ks) {
                     const int k0 = ks * 8;
                     uint32_t ah[MB][4], al[MB][4];
 #pragma unroll
                     for (int mb = 0; mb < MB; ++mb) {
-                        split_tf32(W.stage[buf][k0 + tid4][mb * 16 + gid], ah[mb][0], al[mb][0]);
-                        split_tf32(W.stage[buf][k0 + tid4][mb * 16 + gid + 8], ah[mb][1],
+                        split_tf32(stf[(k0 + tid4) * LDF + mb * 16 + gid], ah[mb][0], al[mb][0]);
+                        split_tf32(stf[(k0 + tid4) * LDF + mb * 16 + gid + 8], ah[mb][1],
                                    al[mb][1]);
-                        split_tf32(W.stage[buf][k0 + tid4 + 4][mb * 16 + gid], ah[mb][2],
+                        split_tf32(stf[(k0 + tid4 + 4) * LDF + mb * 16 + gid], ah[mb][2],
                                    al[mb][2]);
-                        split_tf32(W.stage[buf][k0 + tid4 + 4][mb * 16 + gid + 8], ah[mb][3],
+                        split_tf32(stf[(k0 + tid4 + 4) * LDF + mb * 16 + gid + 8], ah[mb][3],
                                    al[mb][3]);
                     }
                     uint32_t rh0, rl0, rh1, rl1;
@@ -250,6 +346,7 @@ k_row_solve_tc(SolveArgs<float> a) {
                             mma_tf32(dr[sx][mb], ah[mb], rh0, rh1);
                         }
                     }
+                }
                 }
                 __syncwarp();   // this buffer is refilled two items later
             }
@@ -385,6 +482,13 @@ k_row_solve_tc(SolveArgs<float> a) {
                 else if (fail) st = ST_NOT_SPD;
                 if (st != ST_OK) xq = TC(0);
                 if (q < a.kout) a.out[i * a.ldo + q] = (float)xq;
+                if (a.outb) {   // split BF16 copy [hi | lo] of the output row
+                    const float xf = (float)xq;
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
+                    __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.outb) + i * 2 * KP;
+                    ob[q] = hi;
+                    ob[KP + q] = __float2bfloat16_rn(xf - __bfloat162float(hi));
+                }
                 if (a.status && q == 0) a.status[i] = st;
             }
             __syncwarp();
@@ -393,54 +497,71 @@ k_row_solve_tc(SolveArgs<float> a) {
     }
 }
 
-template <int KP, typename TC, int WPS> static size_t tc_smem_bytes() {
+template <int KP, typename TC, int WPS, bool BF> static size_t tc_smem_bytes() {
     constexpr int WARPS = (WPS == 1) ? ((sizeof(TC) == 8 && KP == 32) ? 4 : 8) : WPS;
-    return sizeof(TcSmem<KP, TC>) * WARPS;
+    return sizeof(TcSmem<KP, TC, BF>) * WARPS;
 }
 
-template <int KP, typename TC, int WPS> static cudaError_t tc_attr() {
-    return cudaFuncSetAttribute(k_row_solve_tc<KP, TC, WPS>,
+template <int KP, typename TC, int WPS, bool BF> static cudaError_t tc_attr() {
+    return cudaFuncSetAttribute(k_row_solve_tc<KP, TC, WPS, BF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tc_smem_bytes<KP, TC, WPS>());
+                                (int)tc_smem_bytes<KP, TC, WPS, BF>());
+}
+
+template <bool BF> static cudaError_t tc_attrs() {
+    cudaError_t e;
+    if ((e = tc_attr<16, float, 1, BF>()) != cudaSuccess) return e;
+    if ((e = tc_attr<32, float, 1, BF>()) != cudaSuccess) return e;
+    if ((e = tc_attr<16, float, 4, BF>()) != cudaSuccess) return e;
+    if ((e = tc_attr<32, float, 4, BF>()) != cudaSuccess) return e;
+    if ((e = tc_attr<16, double, 1, BF>()) != cudaSuccess) return e;
+    if ((e = tc_attr<32, double, 1, BF>()) != cudaSuccess) return e;
+    if ((e = tc_attr<16, double, 4, BF>()) != cudaSuccess) return e;
+    return tc_attr<32, double, 4, BF>();
 }
 
 cudaError_t prepare_row_solve_tc() {
-    cudaError_t e;
-    if ((e = tc_attr<16, float, 1>()) != cudaSuccess) return e;
-    if ((e = tc_attr<32, float, 1>()) != cudaSuccess) return e;
-    if ((e = tc_attr<16, float, 4>()) != cudaSuccess) return e;
-    if ((e = tc_attr<32, float, 4>()) != cudaSuccess) return e;
-    if ((e = tc_attr<16, double, 1>()) != cudaSuccess) return e;
-    if ((e = tc_attr<32, double, 1>()) != cudaSuccess) return e;
-    if ((e = tc_attr<16, double, 4>()) != cudaSuccess) return e;
-    return tc_attr<32, double, 4>();
+    cudaError_t e = tc_attrs<false>();
+    if (e != cudaSuccess) return e;
+    return tc_attrs<true>();
 }
 
 constexpr int64_t LONG_ROW_TC = 96;   // mean observations per row that warrant 4 warps
 
-template <int KP, typename TC>
+template <int KP, typename TC, bool BF>
 static cudaError_t launch_tc_kp(const SolveArgs<float> &a, cudaStream_t st) {
     if (a.nnz >= LONG_ROW_TC * a.m) {
         int64_t blocks = a.m;
         if (blocks > NUM_SMS_HINT * 64) blocks = NUM_SMS_HINT * 64;
-        k_row_solve_tc<KP, TC, 4><<<(unsigned)blocks, 128, tc_smem_bytes<KP, TC, 4>(), st>>>(a);
+        k_row_solve_tc<KP, TC, 4, BF>
+            <<<(unsigned)blocks, 128, tc_smem_bytes<KP, TC, 4, BF>(), st>>>(a);
     } else {
         constexpr int WARPS = (sizeof(TC) == 8 && KP == 32) ? 4 : 8;
         const int64_t per = (int64_t)WARPS * (32 / KP);
         int64_t blocks = (a.m + per - 1) / per;
         if (blocks > NUM_SMS_HINT * 32) blocks = NUM_SMS_HINT * 32;
-        k_row_solve_tc<KP, TC, 1>
-            <<<(unsigned)blocks, WARPS * 32, tc_smem_bytes<KP, TC, 1>(), st>>>(a);
+        k_row_solve_tc<KP, TC, 1, BF>
+            <<<(unsigned)blocks, WARPS * 32, tc_smem_bytes<KP, TC, 1, BF>(), st>>>(a);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp64,
+template <bool BF>
+static cudaError_t launch_tc_bf(const SolveArgs<float> &a, int KP, bool chol_fp64,
+                                cudaStream_t st) {
+    if (KP == 16)
+        return chol_fp64 ? launch_tc_kp<16, double, BF>(a, st) : launch_tc_kp<16, float, BF>(a, st);
+    if (KP == 32)
+        return chol_fp64 ? launch_tc_kp<32, double, BF>(a, st) : launch_tc_kp<32, float, BF>(a, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp64, bool bf16,
                                 cudaStream_t st) {
     if (a.m <= 0) return cudaSuccess;
-    if (KP == 16) return chol_fp64 ? launch_tc_kp<16, double>(a, st) : launch_tc_kp<16, float>(a, st);
-    if (KP == 32) return chol_fp64 ? launch_tc_kp<32, double>(a, st) : launch_tc_kp<32, float>(a, st);
-    return cudaErrorInvalidValue;
+    if (bf16 && !a.Fb) return cudaErrorInvalidValue;
+    return bf16 ? launch_tc_bf<true>(a, KP, chol_fp64, st)
+                : launch_tc_bf<false>(a, KP, chol_fp64, st);
 }
 
 }  // namespace ocf
