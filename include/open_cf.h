@@ -182,6 +182,36 @@ int open_cf_validate_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const 
                          const int32_t *col, const void *val, int32_t *result_host,
                          void *stream);
 
+/* Batched completion (extension): P independent completion problems of
+ * uneven size -- each its own apps x settings matrix with its own rank k_p --
+ * fitted with cfg.sweeps ALS sweeps each (cfg.lambda) in one persistent,
+ * graph-captured launch.  Handle precision must be OPEN_CF_FP32.
+ *  m_host, n_host, k_host, nnz_host: per-problem sizes (host, P entries);
+ *    1 <= n_p <= 1024, 1 <= k_p <= OPEN_CF_MAX_K, sum of nnz_host = nnz.
+ *  row_ptr: int64[sum m_p + 1], the problems' CSR rows stacked in problem
+ *    order, with global entry offsets; col: int32[nnz] column indices LOCAL to
+ *    each problem (0 <= col < n_p); val: float[nnz].
+ *  V_inout: float, the problems' n_p x k_p initial V stacked in problem order
+ *    (the random initialisation is passed in); overwritten with the fitted V.
+ *  U_out: float, the problems' m_p x k_p factors stacked (may be NULL).
+ * Problems are ordered by estimated cost and split into a large and a small
+ * class with their own warps per problem (see open_cf_batched_tune). */
+int open_cf_batched_fit(open_cf_t *h, int64_t P, const int64_t *m_host, const int64_t *n_host,
+                        const int32_t *k_host, const int64_t *nnz_host, int64_t nnz,
+                        const int64_t *row_ptr, const int32_t *col, const float *val,
+                        float *V_inout, float *U_out, void *stream);
+
+/* Autotuner of the batched fit: times 2-sweep trial runs over the candidate
+ * warps-per-problem of the large class {2, 4, 8} and of the small class
+ * {1, 2, 4}, keeps the fastest pair in the handle for later
+ * open_cf_batched_fit calls and writes it to W_out_host[2] (may be NULL).
+ * V_scratch receives trial results (same layout as V_inout; pass a copy of
+ * the initial V).  Synchronises `stream`. */
+int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const int64_t *n_host,
+                         const int32_t *k_host, const int64_t *nnz_host, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col, const float *val,
+                         float *V_scratch, int32_t *W_out_host, void *stream);
+
 /* Allocation-free CSR -> CSC (no counterpart in the paper; a service of this
  * library).  Some callers cannot allocate device memory: their host framework
  * owns every device allocation through its own pool and forbids direct

@@ -59,6 +59,10 @@ _SIGNATURES = {
     "open_cf_validate_csr": (ctypes.c_int, [_V, _I64, _I64, _I64, _V, _V, _V,
                                             ctypes.POINTER(_I32), _V]),
     "open_cf_csr_to_csc_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
+    "open_cf_batched_fit": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V, _I64, _V, _V, _V, _V, _V,
+                                           _V]),
+    "open_cf_batched_tune": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V, _I64, _V, _V, _V, _V, _V,
+                                            _V]),
 }
 
 _lib = None
@@ -241,6 +245,34 @@ class OpenCF:
                                              _ptr(val), _ptr(cptr), _ptr(ridx), _ptr(cval),
                                              self._stream()))
         return cptr, ridx[:nnz], cval[:nnz]
+
+    def batched_fit(self, m, n, k, nnz_p, row_ptr, col, val, V, want_U: bool = True):
+        """Batched completion: m, n, k, nnz_p are host int sequences (one entry
+        per problem); row_ptr/col/val the stacked CSR on the device; V the
+        stacked initial V (float32, overwritten in place with the fitted V)."""
+        import numpy as np
+        m = np.ascontiguousarray(m, dtype=np.int64); n = np.ascontiguousarray(n, dtype=np.int64)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        nz = np.ascontiguousarray(nnz_p, dtype=np.int64)
+        self._csr(row_ptr, col, val)
+        self._real(V, "V")
+        U = self._empty(int((m * k).sum())) if want_U else None
+        self._check(lib().open_cf_batched_fit(
+            self._h, len(m), m.ctypes.data, n.ctypes.data, k.ctypes.data, nz.ctypes.data,
+            col.numel(), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(V), _ptr(U), self._stream()))
+        return U
+
+    def batched_tune(self, m, n, k, nnz_p, row_ptr, col, val, V_scratch):
+        import numpy as np
+        m = np.ascontiguousarray(m, dtype=np.int64); n = np.ascontiguousarray(n, dtype=np.int64)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        nz = np.ascontiguousarray(nnz_p, dtype=np.int64)
+        W = (ctypes.c_int32 * 2)()
+        self._check(lib().open_cf_batched_tune(
+            self._h, len(m), m.ctypes.data, n.ctypes.data, k.ctypes.data, nz.ctypes.data,
+            col.numel(), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(V_scratch), W,
+            self._stream()))
+        return int(W[0]), int(W[1])
 
     def validate_csr(self, row_ptr, col, val, n: int) -> int:
         m, nnz = self._csr(row_ptr, col, val)

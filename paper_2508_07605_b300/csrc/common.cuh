@@ -20,7 +20,7 @@ constexpr int32_t ST_BAD = OPEN_CF_ROW_BAD_INPUT;
 
 // Padded rank: factors live in HBM as rows of KP elements (zero padded), so a
 // row is a whole number of 16-byte vectors and the padded unknowns solve to 0.
-inline int padded_k(int k) { return k <= 8 ? 8 : (k <= 16 ? 16 : 32); }
+__host__ __device__ inline int padded_k(int k) { return k <= 8 ? 8 : (k <= 16 ? 16 : 32); }
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {

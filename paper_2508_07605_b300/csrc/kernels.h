@@ -50,6 +50,42 @@ cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp6
                                 cudaStream_t st);
 cudaError_t prepare_row_solve_tc();
 
+// Batched ALS over independent problems (batched.cu).  Per-problem arrays are
+// indexed by problem id p; order[] lists problem ids in processing order;
+// classes are consecutive ranges of order[] with their own warps per problem.
+constexpr int BATCH_MAX_CLASSES = 4;
+constexpr int64_t BATCH_MAX_N = 1024;
+struct BatchArgs {
+    int64_t P;
+    const int32_t *order;
+    const int64_t *m, *n;
+    const int32_t *k;
+    const int64_t *row_off;   // first global row of p (index into row_ptr)
+    const int64_t *col_off;   // prefix sum of n: p's columns in the global CSC
+    const int64_t *fu_off;    // p's padded U rows (KP_p floats each) in Uw
+    const int64_t *fv_off;    // p's padded V rows in Vw
+    const int64_t *row_ptr;   // global CSR row pointer (global entry offsets)
+    const int32_t *col;       // local column indices
+    const float *val;
+    int64_t nnz;
+    float *Uw, *Vw;
+    int64_t *cptr;            // CSC pointers: problem p uses [col_off[p] + p, +n_p] (global offsets)
+    int32_t *cidx;            // CSC local row indices (same entry ranges as the CSR)
+    float *cval;
+    int32_t *counter;         // work queue position per class (zeroed before launch)
+    int sweeps;
+    double lambda;
+    int n_classes;
+    int32_t class_end[BATCH_MAX_CLASSES];
+    int32_t class_W[BATCH_MAX_CLASSES];
+};
+cudaError_t prepare_batched();
+size_t batched_smem_bytes();
+cudaError_t launch_batched(const BatchArgs &b, int grid, cudaStream_t st);
+cudaError_t launch_batched_pack(int64_t P, const int64_t *rows, const int32_t *k,
+                                const int64_t *t_off, const int64_t *f_off, const float *src,
+                                float *dst, bool to_padded, cudaStream_t st);
+
 // Reconstruction T = U V^T fused with Algorithm 2.
 template <typename TV> struct PredictArgs {
     int64_t m, n;

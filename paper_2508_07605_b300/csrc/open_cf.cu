@@ -49,6 +49,12 @@ struct open_cf {
     int64_t m_off = 0, nnz_off = 0;
     // workspaces
     Buf U_w, csc_ptr, csc_idx, csc_val, cnt, tot, part, flag, j_ptr, j_idx, j_val, Ub16;
+    // batched fits: planned metadata (device), workspaces, tuned warps per class
+    Buf b_meta, b_Uw, b_Vw, b_cptr, b_cidx, b_cval, b_counter;
+    std::vector<int64_t> b_key;       // host description of the planned batch
+    int32_t b_W[2] = {8, 2};          // warps per problem: large class, small class
+    int32_t b_class_end[2] = {0, 0};
+    int64_t b_Um = 0, b_Vn = 0;       // padded factor sizes (floats)
     uint64_t generation = 0;  // bumps whenever a workspace moves
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
@@ -252,6 +258,198 @@ template <typename TV> TV *as(const void *p) { return (TV *)p; }
 
 }  // namespace
 
+namespace {
+
+// Device layout of the planned batch metadata (one buffer of int64 words).
+struct BatchPlan {
+    int64_t P, nnz, sum_m, sum_n;
+    // word offsets inside b_meta
+    int64_t o_m, o_n, o_k, o_rowoff, o_coloff, o_fu, o_fv, o_tu, o_tv, o_order;
+};
+
+BatchPlan batch_layout(int64_t P) {
+    BatchPlan L{};
+    L.P = P;
+    int64_t w = 0;
+    L.o_m = w; w += P;
+    L.o_n = w; w += P;
+    L.o_k = w; w += (P + 1) / 2;          // int32
+    L.o_rowoff = w; w += P + 1;
+    L.o_coloff = w; w += P + 1;
+    L.o_fu = w; w += P + 1;
+    L.o_fv = w; w += P + 1;
+    L.o_tu = w; w += P + 1;
+    L.o_tv = w; w += P + 1;
+    L.o_order = w; w += (P + 1) / 2;      // int32
+    L.sum_m = w;                          // total words (reused below)
+    return L;
+}
+
+// Validate, plan (offsets, cost order, classes) and upload the batch when its
+// description changed since the last call.
+int batch_plan(open_cf_t *h, int64_t P, const int64_t *m, const int64_t *n, const int32_t *k,
+               const int64_t *nnz_p, int64_t nnz, BatchPlan &L) {
+    if (P <= 0 || !m || !n || !k || !nnz_p) return fail(h, OPEN_CF_INVALID_ARG, "bad batch description");
+    int64_t tot = 0;
+    for (int64_t p = 0; p < P; ++p) {
+        if (m[p] < 0 || n[p] < 1 || nnz_p[p] < 0 || nnz_p[p] > m[p] * n[p])
+            return fail(h, OPEN_CF_INVALID_ARG, "problem %lld: bad m, n or nnz", (long long)p);
+        if (n[p] > BATCH_MAX_N)
+            return fail(h, OPEN_CF_UNSUPPORTED, "problem %lld: n > %lld", (long long)p,
+                        (long long)BATCH_MAX_N);
+        if (k[p] < 1 || k[p] > OPEN_CF_MAX_K)
+            return fail(h, OPEN_CF_UNSUPPORTED, "problem %lld: k out of range", (long long)p);
+        tot += nnz_p[p];
+    }
+    if (tot != nnz) return fail(h, OPEN_CF_INVALID_ARG, "sum of per-problem nnz != nnz");
+    L = batch_layout(P);
+    const int64_t words = L.sum_m;
+    std::vector<int64_t> key;
+    key.reserve(4 * P + 4);
+    key.push_back(P);
+    key.push_back(nnz);
+    key.push_back(h->b_W[0]);
+    key.push_back(h->b_W[1]);
+    for (int64_t p = 0; p < P; ++p) {
+        key.push_back(m[p]);
+        key.push_back(n[p]);
+        key.push_back(k[p]);
+        key.push_back(nnz_p[p]);
+    }
+    std::vector<int64_t> meta(words, 0);
+    int32_t *k32 = reinterpret_cast<int32_t *>(meta.data() + L.o_k);
+    int32_t *ord = reinterpret_cast<int32_t *>(meta.data() + L.o_order);
+    int64_t sm = 0, sn = 0, fu = 0, fv = 0, tu = 0, tv = 0;
+    std::vector<double> cost(P);
+    for (int64_t p = 0; p < P; ++p) {
+        const int KP = padded_k(k[p]);
+        meta[L.o_m + p] = m[p];
+        meta[L.o_n + p] = n[p];
+        k32[p] = k[p];
+        meta[L.o_rowoff + p] = sm;
+        meta[L.o_coloff + p] = sn;
+        meta[L.o_fu + p] = fu;
+        meta[L.o_fv + p] = fv;
+        meta[L.o_tu + p] = tu;
+        meta[L.o_tv + p] = tv;
+        sm += m[p];
+        sn += n[p];
+        fu += m[p] * KP;
+        fv += n[p] * KP;
+        tu += m[p] * k[p];
+        tv += n[p] * k[p];
+        // cost of one sweep: masked Grams + factorisations
+        cost[p] = (double)nnz_p[p] * 2.0 * KP * KP + (double)(m[p] + n[p]) * KP * KP * KP / 3.0;
+    }
+    meta[L.o_rowoff + P] = sm;
+    meta[L.o_coloff + P] = sn;
+    meta[L.o_fu + P] = fu;
+    meta[L.o_fv + P] = fv;
+    meta[L.o_tu + P] = tu;
+    meta[L.o_tv + P] = tv;
+    std::vector<int32_t> order(P);
+    for (int64_t p = 0; p < P; ++p) order[p] = (int32_t)p;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+    for (int64_t p = 0; p < P; ++p) ord[p] = order[p];
+    // class 0: the costliest problems that together take ~half of the work
+    double total = 0.0;
+    for (double c : cost) total += c;
+    double acc = 0.0;
+    int32_t split = 0;
+    while (split < P && acc < 0.5 * total) acc += cost[order[split++]];
+    h->b_class_end[0] = split;
+    h->b_class_end[1] = (int32_t)P;
+    h->b_Um = fu;
+    h->b_Vn = fv;
+    L.nnz = nnz;
+    L.sum_n = sn;
+    const int64_t sum_m = sm;
+    CK(h, ensure(h, h->b_Uw, sizeof(float) * std::max<int64_t>(fu, 1)));
+    CK(h, ensure(h, h->b_Vw, sizeof(float) * std::max<int64_t>(fv, 1)));
+    CK(h, ensure(h, h->b_cptr, sizeof(int64_t) * (sn + P)));
+    CK(h, ensure(h, h->b_cidx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    CK(h, ensure(h, h->b_cval, sizeof(float) * std::max<int64_t>(nnz, 1)));
+    CK(h, ensure(h, h->b_counter, sizeof(int32_t) * BATCH_MAX_CLASSES));
+    CK(h, ensure(h, h->b_meta, sizeof(int64_t) * words));
+    if (key != h->b_key) {
+        CK(h, cudaMemcpy(h->b_meta.p, meta.data(), sizeof(int64_t) * words,
+                         cudaMemcpyHostToDevice));
+        h->b_key.swap(key);
+    }
+    L.sum_m = sum_m;
+    return OPEN_CF_OK;
+}
+
+BatchArgs batch_args(open_cf_t *h, const BatchPlan &L, const int64_t *row_ptr, const int32_t *col,
+                     const float *val, int sweeps) {
+    const int64_t *meta = (const int64_t *)h->b_meta.p;
+    BatchArgs b{};
+    b.P = L.P;
+    b.order = reinterpret_cast<const int32_t *>(meta + L.o_order);
+    b.m = meta + L.o_m;
+    b.n = meta + L.o_n;
+    b.k = reinterpret_cast<const int32_t *>(meta + L.o_k);
+    b.row_off = meta + L.o_rowoff;
+    b.col_off = meta + L.o_coloff;
+    b.fu_off = meta + L.o_fu;
+    b.fv_off = meta + L.o_fv;
+    b.row_ptr = row_ptr;
+    b.col = col;
+    b.val = val;
+    b.nnz = L.nnz;
+    b.Uw = (float *)h->b_Uw.p;
+    b.Vw = (float *)h->b_Vw.p;
+    b.cptr = (int64_t *)h->b_cptr.p;
+    b.cidx = (int32_t *)h->b_cidx.p;
+    b.cval = (float *)h->b_cval.p;
+    b.counter = (int32_t *)h->b_counter.p;
+    b.sweeps = sweeps;
+    b.lambda = h->cfg.lambda;
+    b.n_classes = 2;
+    b.class_end[0] = h->b_class_end[0];
+    b.class_end[1] = h->b_class_end[1];
+    b.class_W[0] = h->b_W[0];
+    b.class_W[1] = h->b_W[1];
+    return b;
+}
+
+// Persistent grid: as many CTAs as fit on every SM at once (shared memory
+// bound; at most 2 per SM with 128 registers x 256 threads).
+int batched_grid(open_cf_t *h) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, h->device);
+    const size_t smem = batched_smem_bytes();
+    int per_sm = (int)std::max<size_t>(1, (size_t)prop.sharedMemPerMultiprocessor / (smem + 1024));
+    if (per_sm > 2) per_sm = 2;
+    return prop.multiProcessorCount * per_sm;
+}
+
+// Enqueue one batched fit: pack V, the persistent kernel, unpack U and V.
+cudaError_t batch_enqueue(open_cf_t *h, const BatchPlan &L, const BatchArgs &b, float *V_inout,
+                          float *U_out, int grid, cudaStream_t st) {
+    const int64_t *meta = (const int64_t *)h->b_meta.p;
+    const int32_t *k32 = reinterpret_cast<const int32_t *>(meta + L.o_k);
+    cudaError_t e = cudaMemsetAsync(h->b_counter.p, 0, sizeof(int32_t) * BATCH_MAX_CLASSES, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(h->b_Uw.p, 0, sizeof(float) * std::max<int64_t>(h->b_Um, 1), st);
+    if (e != cudaSuccess) return e;
+    e = launch_batched_pack(L.P, meta + L.o_n, k32, meta + L.o_tv, meta + L.o_fv, V_inout,
+                            (float *)h->b_Vw.p, true, st);
+    if (e != cudaSuccess) return e;
+    e = launch_batched(b, grid, st);
+    if (e != cudaSuccess) return e;
+    if (U_out) {
+        e = launch_batched_pack(L.P, meta + L.o_m, k32, meta + L.o_tu, meta + L.o_fu,
+                                (const float *)h->b_Uw.p, U_out, false, st);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_batched_pack(L.P, meta + L.o_n, k32, meta + L.o_tv, meta + L.o_fv,
+                               (const float *)h->b_Vw.p, V_inout, false, st);
+}
+
+}  // namespace
+
 extern "C" {
 
 int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
@@ -302,7 +500,7 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
     }
     DeviceGuard g(h->device);
     if (prepare_csr_to_csc(CSC_MAX_N) != cudaSuccess || prepare_row_solve() != cudaSuccess ||
-        prepare_row_solve_tc() != cudaSuccess) {
+        prepare_row_solve_tc() != cudaSuccess || prepare_batched() != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return OPEN_CF_CUDA_ERROR;
@@ -320,7 +518,8 @@ void open_cf_destroy(open_cf_t *h) {
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         for (Buf *b : {&h->V, &h->Vb16, &h->cg, &h->off_ptr, &h->off_idx, &h->off_val, &h->U_w,
                        &h->csc_ptr, &h->csc_idx, &h->csc_val, &h->cnt, &h->tot, &h->part,
-                       &h->flag, &h->j_ptr, &h->j_idx, &h->j_val, &h->Ub16})
+                       &h->flag, &h->j_ptr, &h->j_idx, &h->j_val, &h->Ub16, &h->b_meta, &h->b_Uw,
+                       &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter})
             free_buf(*b);
     }
     delete h;
@@ -630,6 +829,84 @@ int open_cf_validate_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const 
     CK(h, cudaMemcpyAsync(&f, h->flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
     *result_host = (f == 0x7f7f7f7f) ? 0 : f;
+    return OPEN_CF_OK;
+}
+
+int open_cf_batched_fit(open_cf_t *h, int64_t P, const int64_t *m_host, const int64_t *n_host,
+                        const int32_t *k_host, const int64_t *nnz_host, int64_t nnz,
+                        const int64_t *row_ptr, const int32_t *col, const float *val,
+                        float *V_inout, float *U_out, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (h->cfg.precision != OPEN_CF_FP32)
+        return fail(h, OPEN_CF_UNSUPPORTED, "batched fits run in OPEN_CF_FP32 precision");
+    if (!row_ptr || !V_inout || (nnz > 0 && (!col || !val)))
+        return fail(h, OPEN_CF_INVALID_ARG, "NULL array");
+    DeviceGuard g(h->device);
+    BatchPlan L;
+    int rc = batch_plan(h, P, m_host, n_host, k_host, nnz_host, nnz, L);
+    if (rc) return rc;
+    const BatchArgs b = batch_args(h, L, row_ptr, col, val, h->cfg.sweeps);
+    const int grid = batched_grid(h);
+    std::vector<int64_t> key = {2, P, nnz, (int64_t)row_ptr, (int64_t)col, (int64_t)val,
+                                (int64_t)V_inout, (int64_t)U_out, h->b_W[0], h->b_W[1],
+                                h->b_class_end[0]};
+    return run_graph(h, key, S(stream), [&](cudaStream_t st) {
+        return batch_enqueue(h, L, b, V_inout, U_out, grid, st);
+    });
+}
+
+int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const int64_t *n_host,
+                         const int32_t *k_host, const int64_t *nnz_host, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col, const float *val,
+                         float *V_scratch, int32_t *W_out_host, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (h->cfg.precision != OPEN_CF_FP32)
+        return fail(h, OPEN_CF_UNSUPPORTED, "batched fits run in OPEN_CF_FP32 precision");
+    if (!row_ptr || !V_scratch || (nnz > 0 && (!col || !val)))
+        return fail(h, OPEN_CF_INVALID_ARG, "NULL array");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const int grid = batched_grid(h);
+    const int cand_large[3] = {2, 4, 8}, cand_small[3] = {1, 2, 4};
+    float best_ms = 0.0f;
+    int32_t bw0 = h->b_W[0], bw1 = h->b_W[1];
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    bool first = true;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            h->b_W[0] = cand_large[a];
+            h->b_W[1] = cand_small[c];
+            BatchPlan L;
+            int rc = batch_plan(h, P, m_host, n_host, k_host, nnz_host, nnz, L);
+            if (rc) return rc;
+            const BatchArgs b = batch_args(h, L, row_ptr, col, val, 2);   // 2 sweeps per trial
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {   // first run warms caches
+                CK(h, cudaEventRecord(e0, st));
+                CK(h, batch_enqueue(h, L, b, V_scratch, nullptr, grid, st));
+                CK(h, cudaEventRecord(e1, st));
+                CK(h, cudaEventSynchronize(e1));
+                CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (first || ms < best_ms) {
+                best_ms = ms;
+                bw0 = h->b_W[0];
+                bw1 = h->b_W[1];
+                first = false;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->b_W[0] = bw0;
+    h->b_W[1] = bw1;
+    if (W_out_host) {
+        W_out_host[0] = bw0;
+        W_out_host[1] = bw1;
+    }
     return OPEN_CF_OK;
 }
 

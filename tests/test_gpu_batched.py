@@ -1,0 +1,115 @@
+"""Batched completion of many independent, uneven problems in one persistent
+launch, against the FP64 oracle run problem by problem."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+from gpu_util import DEV, TOL_FP32, dev, host, rounded, solve_err
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2508_07605_b300 as ocf  # noqa: E402
+
+
+def _batch(seed, n_problems, extra_edge=True):
+    bp = synth.make_batched(seed=seed, n_problems=n_problems, n_heldout=256)
+    if extra_edge:
+        rng = np.random.default_rng(seed + 1)
+        # edge problems: k=1, k=32 with n=1, and a problem with empty rows
+        bp.problems.append(synth.make_sparse_problem(m=40, n_cpu=1, n_gpu=30, rank=1, density=0.3,
+                                                     k=1, lam=0.05, n_heldout=16, rng=rng))
+        bp.problems.append(synth.make_sparse_problem(m=50, n_cpu=1, n_gpu=1, rank=2, density=0.9,
+                                                     k=32, lam=0.05, n_heldout=1, rng=rng))
+        bp.problems.append(synth.make_sparse_problem(m=300, n_cpu=1, n_gpu=64, rank=8,
+                                                     density=0.005, k=8, lam=0.05, n_heldout=16,
+                                                     rng=rng))
+    return bp
+
+
+def _run(h, bp, V0_override=None):
+    c = bp.concat()
+    val = rounded(c["val"], torch.float32)
+    V = dev(rounded(c["V0"], torch.float32) if V0_override is None else V0_override,
+            torch.float32)
+    nnz_p = np.array([p.nnz for p in bp.problems])
+    U = h.batched_fit(c["m"], c["n"], c["k"], nnz_p, dev(c["row_ptr"], torch.int64),
+                      dev(c["col"], torch.int32), dev(val, torch.float32), V)
+    torch.cuda.synchronize()
+    return c, val, host(U).astype(np.float64), host(V).astype(np.float64)
+
+
+def _slices(c, t):
+    return [slice(int(c[t][p]), int(c[t][p + 1])) for p in range(len(c["m"]))]
+
+
+def test_batched_one_sweep_stepwise(orc):
+    bp = _batch(11, 120)
+    h = ocf.OpenCF(k=4, lam=0.05, sweeps=1)
+    c, val, U, V = _run(h, bp)
+    us, vs = _slices(c, "u_off"), _slices(c, "v_off")
+    worst_u = worst_v = 0.0
+    for t, p in enumerate(bp.problems):
+        k = p.k
+        V0 = rounded(p.V0, torch.float32)
+        pv = val[int(c["nnz_off"][t]):int(c["nnz_off"][t + 1])]
+        Ug = U[us[t]].reshape(p.m, k)
+        Vg = V[vs[t]].reshape(p.n, k)
+        Ur, _ = orc.half_step(p.row_ptr, p.col, pv, V0, p.lam)
+        eu = solve_err(Ug, Ur, V0, p.row_ptr, p.col, pv, p.lam)
+        cp, ci, cv = orc.transpose(p.row_ptr, p.col, pv, p.n)
+        Vr, _ = orc.half_step(cp, ci, cv, Ug, p.lam)
+        ev = solve_err(Vg, Vr, Ug, cp, ci, cv, p.lam)
+        worst_u = max(worst_u, eu.max(initial=0.0))
+        worst_v = max(worst_v, ev.max(initial=0.0))
+    assert worst_u <= TOL_FP32 and worst_v <= TOL_FP32, (worst_u, worst_v)
+
+
+def test_batched_fit_heldout_rmse_and_tuning_invariance(orc):
+    bp = _batch(12, 150)
+    h = ocf.OpenCF(k=4, lam=0.05, sweeps=15)
+    c, val, U, V = _run(h, bp)
+    us, vs = _slices(c, "u_off"), _slices(c, "v_off")
+    se_g = se_o = 0.0
+    cnt = 0
+    for t, p in enumerate(bp.problems):
+        pv = val[int(c["nnz_off"][t]):int(c["nnz_off"][t + 1])]
+        Ug = U[us[t]].reshape(p.m, p.k); Vg = V[vs[t]].reshape(p.n, p.k)
+        Ur, Vr, _, _, _ = orc.als(p.row_ptr, p.col, pv, p.n, rounded(p.V0, torch.float32),
+                                  p.lam, 15)
+        if len(p.heldout_rows) == 0:
+            continue
+        pg = np.einsum("tk,tk->t", Ug[p.heldout_rows], Vg[p.heldout_cols])
+        po = np.einsum("tk,tk->t", Ur[p.heldout_rows], Vr[p.heldout_cols])
+        se_g += np.sum((pg - p.heldout_truth) ** 2)
+        se_o += np.sum((po - p.heldout_truth) ** 2)
+        cnt += len(pg)
+    rmse_g, rmse_o = np.sqrt(se_g / cnt), np.sqrt(se_o / cnt)
+    assert rmse_g <= rmse_o + 1e-3, (rmse_g, rmse_o)
+    # the autotuner changes only how problems map to warps, never the result
+    cc = bp.concat()
+    nnz_p = np.array([p.nnz for p in bp.problems])
+    Vs = dev(rounded(cc["V0"], torch.float32), torch.float32)
+    W = h.batched_tune(cc["m"], cc["n"], cc["k"], nnz_p, dev(cc["row_ptr"], torch.int64),
+                       dev(cc["col"], torch.int32), dev(val, torch.float32), Vs)
+    assert W[0] in (2, 4, 8) and W[1] in (1, 2, 4)
+    _, _, U2, V2 = _run(h, bp)
+    assert np.array_equal(U, U2) and np.array_equal(V, V2)
+
+
+def test_batched_rejects_bad_descriptions():
+    h = ocf.OpenCF(k=4, lam=0.05, sweeps=1)
+    z64 = torch.zeros(2, dtype=torch.int64, device=DEV)
+    z32 = torch.zeros(1, dtype=torch.int32, device=DEV)
+    f = torch.zeros(1, device=DEV)
+    V = torch.zeros(4, device=DEV)
+    with pytest.raises(ocf.OpenCFError) as e:
+        h.batched_fit([1], [2000], [2], [1], z64, z32, f, V)       # n > 1024
+    assert e.value.code == ocf.UNSUPPORTED
+    with pytest.raises(ocf.OpenCFError) as e:
+        h.batched_fit([1], [2], [2], [5], z64, z32, f, V)          # nnz_p > m*n
+    assert e.value.code == ocf.INVALID_ARG
