@@ -459,15 +459,134 @@ def run_gpu_large(args):
     return 0
 
 
+WORKLOAD_C3 = "batched: 10,000 independent completion problems, apps log-uniform 32-512, settings " \
+              "log-uniform 64-1024, rank 8-32 (k = rank), density log-uniform 2-20%, lambda=0.05, " \
+              "15 sweeps, FP32, one persistent graph-captured launch, autotuned warps per problem"
+
+
+def run_gpu_batched(args):
+    """Workload 3: all problems fitted by one persistent launch; compared with
+    the same fits issued problem by problem through open_cf_fit_csr."""
+    import torch
+
+    import paper_2508_07605_b300 as ocf
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    bp = synth.make_batched(seed=0, n_problems=args.problems, n_heldout=64)
+    t_gen = time.perf_counter() - t0
+    c = bp.concat()
+    nnz_p = np.array([p.nnz for p in bp.problems])
+    units = 15 * int(c["m"].sum() + c["n"].sum())
+    rp = torch.as_tensor(c["row_ptr"]).to(dev)
+    col = torch.as_tensor(c["col"]).to(dev)
+    val = torch.as_tensor(c["val"].astype(np.float32)).to(dev)
+    V0 = torch.as_tensor(c["V0"].astype(np.float32)).to(dev)
+    h = ocf.OpenCF(k=4, lam=0.05, sweeps=15)
+    Vs = V0.clone()
+    t0 = time.perf_counter()
+    W = h.batched_tune(c["m"], c["n"], c["k"], nnz_p, rp, col, val, Vs)
+    t_tune = time.perf_counter() - t0
+    V = V0.clone()
+    for _ in range(max(args.warmup, 3)):
+        V.copy_(V0)
+        h.batched_fit(c["m"], c["n"], c["k"], nnz_p, rp, col, val, V)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_c3.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                          else "/tmp/clocks_bench_c3.csv")
+    with clocks:
+        for i in range(args.steps):
+            V.copy_(V0)
+            flush.zero_()
+            ev[i][0].record(stream)
+            U = h.batched_fit(c["m"], c["n"], c["k"], nnz_p, rp, col, val, V)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    t_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps / 1e3
+    # plain GPU ALS: the same fits issued problem by problem (sample of problems)
+    sample = list(range(0, len(bp), max(1, len(bp) // 200)))
+    hs = {}
+    def plain(i):
+        p = bp.problems[i]
+        key = p.k
+        if key not in hs:
+            hs[key] = ocf.OpenCF(k=p.k, lam=0.05, sweeps=15)
+        hh = hs[key]
+        hh.set_V(torch.as_tensor(p.V0.astype(np.float32)).to(dev))
+        return hh.fit_csr(torch.as_tensor(p.row_ptr).to(dev), torch.as_tensor(p.col).to(dev),
+                          torch.as_tensor(p.val.astype(np.float32)).to(dev), p.n)
+    tens = [(torch.as_tensor(bp.problems[i].row_ptr).to(dev),
+             torch.as_tensor(bp.problems[i].col).to(dev),
+             torch.as_tensor(bp.problems[i].val.astype(np.float32)).to(dev),
+             torch.as_tensor(bp.problems[i].V0.astype(np.float32)).to(dev)) for i in sample]
+    def plain_t(j):
+        i = sample[j]
+        p = bp.problems[i]
+        if p.k not in hs:
+            hs[p.k] = ocf.OpenCF(k=p.k, lam=0.05, sweeps=15)
+        hh = hs[p.k]
+        r_, c_, v_, V_ = tens[j]
+        hh.set_V(V_)
+        return hh.fit_csr(r_, c_, v_, p.n)
+    for j in range(len(sample)):
+        plain_t(j)        # capture each problem's graph once
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in range(len(sample)):
+        plain_t(j)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    plain_units = 15 * sum(bp.problems[i].m + bp.problems[i].n for i in sample)
+    # oracle on a bounded sample of the problems
+    import oracle as orc
+    orc.build()
+    t0 = time.perf_counter()
+    osamp = sample[:60]
+    for i in osamp:
+        p = bp.problems[i]
+        orc.als(p.row_ptr, p.col, p.val, p.n, p.V0, p.lam, 15)
+    t_orc = time.perf_counter() - t0
+    orc_units = 15 * sum(bp.problems[i].m + bp.problems[i].n for i in osamp)
+    line = {
+        "metric": "ALS row-solves/s", "value": units / t_step, "unit": "row-solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_C3, "problems": len(bp), "nnz": int(c["val"].size),
+                   "row_solves_per_step": units, "tuned_warps_per_problem": {"large": W[0],
+                                                                            "small": W[1]},
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "plain_gpu_per_problem": {"value": plain_units / t_plain, "unit": "row-solves/s",
+                                  "sample_problems": len(sample),
+                                  "speedup_batched": (units / t_step) / (plain_units / t_plain)},
+        "tune_s": t_tune, "generate_s": t_gen,
+        "cpu_baseline": {"value": orc_units / t_orc, "unit": "row-solves/s",
+                         "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": f"FP64 ALS fits of {len(osamp)} sampled problems"},
+        "clocks": clocks.summary(0),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
                     help="c2: 4096x1024 fit (default, the headline line); "
+                         "c3: 10,000 uneven problems in one batched launch; "
                          "c5: 1M x 4096 BF16-Gram fold-in + selection")
+    ap.add_argument("--problems", type=int, default=10000, help="c3 only: number of problems")
     ap.add_argument("--fp32-cholesky", action="store_true",
                     help="c5 only: FP32 instead of FP64 k x k factorisation")
     args = ap.parse_args()
@@ -475,6 +594,8 @@ def main():
         return run_reference(args)
     if args.workload == "c5":
         return run_gpu_large(args)
+    if args.workload == "c3":
+        return run_gpu_batched(args)
     return run_gpu(args)
 
 
