@@ -576,16 +576,218 @@ def run_gpu_batched(args):
     return 0
 
 
+WORKLOAD_C4 = "learned warm start: MLP 48->256->256->32 SELU (BF16 tensor cores, FP32 " \
+              "accumulation) trained on fold-in factors of 2^20 synthetic apps (full 4096-setting " \
+              "profiles) against a fixed V (64x64 caps, k=32, fit_offline of a 4096-app block, " \
+              "15 sweeps); completes 2^20 new apps from 16 observed settings each, ALS fold-in " \
+              "fallback where the observed-entry RMSE > 0.02"
+MLP_SIZES = (48, 256, 256, 32)
+
+
+def _mlp_split(flat):
+    out, o = [], 0
+    for a, b in zip(MLP_SIZES[:-1], MLP_SIZES[1:]):
+        out.append(flat[o:o + a * b].reshape(a, b)); o += a * b
+        out.append(flat[o:o + b]); o += b
+    return out
+
+
+def run_gpu_learned(args):
+    """Workload 4: one step = completion of 2^20 new apps by the learned warm
+    start (features -> MLP -> observed-entry residual -> fold-in of the rows
+    above the threshold); the plain fold-in of the same rows is timed beside it."""
+    import math
+
+    import torch
+
+    import paper_2508_07605_b300 as ocf
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wl = synth.make_learned(seed=0, device=dev)
+    cpu, gpu = synth.cap_grid(wl.n_cpu, wl.n_gpu)
+    K, S = wl.k, wl.s_obs
+    # offline phase: V from the dense offline block
+    h = ocf.OpenCF(k=K, lam=wl.lam, sweeps=15, cpu_caps=cpu, gpu_caps=gpu,
+                   mlp_fallback_threshold=0.02)
+    off, _, _ = wl.draw_apps(4096)
+    g0 = torch.Generator(device=dev)
+    g0.manual_seed(7)
+    h.set_V(torch.randn(wl.n, K, generator=g0, device=dev) / math.sqrt(K))
+    h.fit_offline(off)
+    V = h.get_V()
+    del off
+    # training: pool of 2^20 apps, targets = fold-in of their full profiles
+    pool = 1 << 20
+    pc, pv, pt = synth.learned_pool(wl, h, pool)
+    rng = np.random.default_rng(0)
+    flat0 = np.concatenate([np.asarray(p, np.float32).reshape(-1)
+                            for p in synth.mlp_init(rng, MLP_SIZES, out_scale=0.1)])
+    h.mlp_set_params(torch.tensor(flat0, device=dev))
+    B, steps, lr0 = 4096, args.train_steps, 2e-3
+    rp = torch.arange(0, (B + 1) * S, S, dtype=torch.int64, device=dev)
+    cb = torch.empty(B, S, dtype=torch.int32, device=dev)
+    vb = torch.empty(B, S, dtype=torch.float32, device=dev)
+    tb = torch.empty(B, K, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1)
+    pos = pool
+    t_samples = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for step in range(steps):
+        if pos + B > pool:
+            perm = torch.randperm(pool, generator=gen, device=dev)
+            pos = 0
+        idx = perm[pos:pos + B]
+        pos += B
+        torch.index_select(pc, 0, idx, out=cb)
+        torch.index_select(pv, 0, idx, out=vb)
+        torch.index_select(pt, 0, idx, out=tb)
+        e0.record(stream)
+        h.mlp_train_step(rp, cb.view(-1), vb.view(-1), tb,
+                         lr=lr0 * 0.5 * (1 + math.cos(math.pi * step / steps)))
+        e1.record(stream)
+        if step >= 10 and step % 64 == 0:   # sampled: an event sync costs more than a step
+            e1.synchronize()
+            t_samples.append(e0.elapsed_time(e1) / 1e3)
+    train_sps = B / statistics.mean(t_samples) if t_samples else None
+    del pc, pv, pt
+    # new apps: 2^20, 16 observed settings each; noiseless rows kept for 65,536 of them
+    M = 1 << 20
+    cols, vals = [], []
+    clean_eval = None
+    for s0 in range(0, M, 65536):
+        noisy, clean, obs = wl.draw_apps(65536)
+        cols.append(obs.reshape(-1)); vals.append(torch.gather(noisy, 1, obs.to(torch.int64)))
+        if clean_eval is None:
+            clean_eval = clean
+        del noisy, clean
+    col = torch.cat(cols).contiguous(); val = torch.cat(vals).reshape(-1).contiguous()
+    row_ptr = torch.arange(0, (M + 1) * S, S, dtype=torch.int64, device=dev)
+    del cols, vals
+    h_mlp = ocf.OpenCF(k=K, lam=wl.lam, cpu_caps=cpu, gpu_caps=gpu, mlp_fallback_threshold=1e30)
+    h_mlp.set_V(V)
+    h_mlp.mlp_set_params(h.mlp_get_params())
+
+    def learned():
+        return h.mlp_infer(row_ptr, col, val)
+
+    def mlp_only():
+        return h_mlp.mlp_infer(row_ptr, col, val)
+
+    def plain():
+        return h.complete_rows(row_ptr, col, val)
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream); out = fn(); b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / reps / 1e3, out
+
+    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_c4.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                          else "/tmp/clocks_bench_c4.csv")
+    with clocks:
+        t_learned, (U, st) = timed(learned, args.steps)
+        t_mlp, (Um, _) = timed(mlp_only, args.steps)
+        t_plain, (Uf, stf) = timed(plain, args.steps)
+    E = clean_eval.shape[0]
+
+    def rmse(Ux):
+        return float(torch.sqrt(torch.mean((Ux[:E] @ V.T - clean_eval) ** 2)).item())
+
+    frac_fb = float((st == 3).float().mean().item())
+    # error against the FP64 oracle on a 10k-row sample, and the oracle's time
+    import oracle as orc
+    orc.build()
+    sample = np.sort(np.random.default_rng(0).choice(M, 10000, replace=False))
+    sc = col.view(M, S)[torch.as_tensor(sample, device=dev)].cpu().numpy()
+    sv = val.view(M, S)[torch.as_tensor(sample, device=dev)].double().cpu().numpy()
+    sp = np.arange(0, (len(sample) + 1) * S, S, dtype=np.int64)
+    params = _mlp_split(h.mlp_get_params().double().cpu().numpy())
+    Vd = V.double().cpu().numpy()
+    t0 = time.perf_counter()
+    X = orc.mlp_features(sp, sc.reshape(-1), sv.reshape(-1), cpu, gpu)
+    _, _, Y = orc.mlp_forward(X, params)
+    rr = orc.row_rmse(sp, sc.reshape(-1), sv.reshape(-1), Y, Vd)
+    fb_o = ~(rr <= 0.02)
+    fb = np.flatnonzero(fb_o)
+    if len(fb):
+        fp = np.arange(0, (len(fb) + 1) * S, S, dtype=np.int64)
+        orc.half_step(fp, sc[fb].reshape(-1), sv[fb].reshape(-1), Vd, wl.lam)
+    t_orc = time.perf_counter() - t0
+    # parity: each row against the oracle's result for the branch the GPU took
+    # (the fallback decision is a threshold on the GPU's own FP32 residual)
+    st_s = st[torch.as_tensor(sample, device=dev)].cpu().numpy()
+    fb_g = st_s == 3
+    gp = np.arange(0, (int(fb_g.sum()) + 1) * S, S, dtype=np.int64)
+    Ufb_o, _ = orc.half_step(gp, sc[fb_g].reshape(-1), sv[fb_g].reshape(-1), Vd, wl.lam)
+    Ug = U[torch.as_tensor(sample, device=dev)].double().cpu().numpy()
+
+    def rel(Ua, Ub):
+        Ta, Tb = Ua @ Vd.T, Ub @ Vd.T
+        return np.linalg.norm(Ta - Tb, axis=1) / np.maximum(np.linalg.norm(Tb, axis=1), 1e-30)
+
+    rel_mlp = rel(Ug[~fb_g], Y[~fb_g])
+    rel_fb = rel(Ug[fb_g], Ufb_o) if fb_g.any() else np.zeros(1)
+    agree = float(np.mean(fb_g == fb_o))
+    fl_fwd = 2.0 * (48 * 256 + 256 * 256 + 256 * 32) * M
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16_peak = float(peaks.get("bf16_tflops", 1736.0))
+    line = {
+        "metric": "row completions/s (learned warm start + ALS fallback)",
+        "value": M / t_learned, "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_learned * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_C4, "m": M, "n": wl.n, "k": K, "s_obs": S,
+                   "train_steps": steps, "batch": B,
+                   "l2": "inputs (~0.3 GB) and factors exceed L2"},
+        "plain_fold_in": {"value": M / t_plain, "unit": "rows/s", "ms": t_plain * 1e3},
+        "mlp_only": {"value": M / t_mlp, "unit": "rows/s", "ms": t_mlp * 1e3},
+        "fallback_fraction": frac_fb,
+        "train_samples_per_s": train_sps,
+        "heldout_rmse": {"learned_with_fallback": rmse(U), "mlp_only": rmse(Um),
+                         "plain_fold_in": rmse(Uf), "eval_apps": E,
+                         "truth": "noiseless rows of the synthetic model"},
+        "error_vs_fp64_oracle": {"sample_rows": len(sample),
+                                 "mlp_rows_pred_rel_err_max": float(rel_mlp.max()),
+                                 "mlp_rows_pred_rel_err_median": float(np.median(rel_mlp)),
+                                 "mlp_rows_gate": 2e-2,
+                                 "fallback_rows_pred_rel_err_max": float(rel_fb.max()),
+                                 "fallback_rows_gate": 1e-5,
+                                 "fallback_decision_agreement": agree},
+        "roofline": {"kernel": "MLP forward (k_gemm_bf16 x3 + features), mma.sync m16n8k16",
+                     "bound": "tensor", "achieved": fl_fwd / t_mlp / 1e12, "peak": bf16_peak,
+                     "unit": "TFLOP/s", "frac": fl_fwd / t_mlp / 1e12 / bf16_peak,
+                     "traffic": None, "peak_kind": "bf16_tflops (burst) of measured"},
+        "cpu_baseline": {"value": len(sample) / t_orc, "unit": "rows/s",
+                         "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": "FP64 features + MLP forward + residual + fold-in of the "
+                                   "fallback rows, 10k sampled new apps"},
+        "clocks": clocks.summary(0),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: 4096x1024 fit (default, the headline line); "
                          "c3: 10,000 uneven problems in one batched launch; "
+                         "c4: learned warm start (MLP + ALS fallback) on 2^20 new apps; "
                          "c5: 1M x 4096 BF16-Gram fold-in + selection")
+    ap.add_argument("--train-steps", type=int, default=30000,
+                    help="c4 only: training steps (batch 4096) before the timed completions")
     ap.add_argument("--problems", type=int, default=10000, help="c3 only: number of problems")
     ap.add_argument("--fp32-cholesky", action="store_true",
                     help="c5 only: FP32 instead of FP64 k x k factorisation")
@@ -596,6 +798,8 @@ def main():
         return run_gpu_large(args)
     if args.workload == "c3":
         return run_gpu_batched(args)
+    if args.workload == "c4":
+        return run_gpu_learned(args)
     return run_gpu(args)
 
 

@@ -212,6 +212,50 @@ int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const i
                          const int64_t *row_ptr, const int32_t *col, const float *val,
                          float *V_scratch, int32_t *W_out_host, void *stream);
 
+/* ---- Learned warm start (Sec. "Collaborative Filtering Model": the paper's
+ * CF model is an MLP with SELU activations; Sec. "Online Performance
+ * Prediction": fill in a new application's row from its online profile).
+ * An MLP maps an application's first 16 observed settings, each encoded as
+ * (CPU cap, GPU cap, runtime) with caps scaled to [0, 1] over the grid (48
+ * inputs), through 256 -> 256 SELU units to its factor u (k = 32 outputs).
+ * Training targets are factors from the ALS fold-in; the loss is
+ * (1/B) sum_r (u_r - u*_r)^T (V^T V) (u_r - u*_r), the squared error of the
+ * predicted row u V^T.  Products run on BF16 tensor cores with FP32
+ * accumulation; parameters, gradients and Adam moments are FP32.
+ * Requirements: k = 32, precision FP32 or BF16_GRAM, V set, cap grid given
+ * in the config; otherwise OPEN_CF_UNSUPPORTED / OPEN_CF_NOT_FITTED /
+ * OPEN_CF_INVALID_ARG. */
+
+/* Parameter vector (float, device), 86,560 entries in this order:
+ * W1[48][256], b1[256], W2[256][256], b2[256], W3[256][32], b3[32]; each W is
+ * [inputs][outputs] row-major.  Setting the parameters resets Adam. */
+#define OPEN_CF_MLP_PARAMS 86560
+int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream);
+int open_cf_mlp_get_params(open_cf_t *h, float *params_out, void *stream);
+
+/* One training step on a batch of B rows (CSR as everywhere; the first 16
+ * entries of each row form its features) with targets U_target (B x 32
+ * float).  loss_out (one double, device, may be NULL) receives the loss
+ * before the update.  grads_out NULL: Adam update (beta1 0.9, beta2 0.999,
+ * eps 1e-8, step size lr).  grads_out non-NULL (OPEN_CF_MLP_PARAMS floats):
+ * the gradient is written there and the parameters are left unchanged.
+ * B <= 2^20. */
+int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *row_ptr,
+                           const int32_t *col, const float *val, const float *U_target, float lr,
+                           double *loss_out, float *grads_out, void *stream);
+
+/* Warm-started online completion: U_out (m x 32 float) = MLP(features of
+ * each row); then the observed-entry RMSE of every row under U_out V^T
+ * (row_rmse, m floats, may be NULL) decides the fallback: a row whose RMSE is
+ * above cfg.mlp_fallback_threshold (or not finite) is re-solved by the ridge
+ * fold-in of open_cf_complete_rows.  status (int32[m], may be NULL):
+ * OPEN_CF_ROW_OK (MLP factor kept), OPEN_CF_ROW_FALLBACK_USED (ALS factor),
+ * or the fold-in's own code for a fallback row it could not solve.  A row
+ * with no observations keeps the MLP's output (RMSE 0). */
+int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                      const int32_t *col, const float *val, float *U_out, int32_t *status,
+                      float *row_rmse, void *stream);
+
 /* Allocation-free CSR -> CSC (no counterpart in the paper; a service of this
  * library).  Some callers cannot allocate device memory: their host framework
  * owns every device allocation through its own pool and forbids direct

@@ -63,7 +63,13 @@ _SIGNATURES = {
                                            _V]),
     "open_cf_batched_tune": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V, _I64, _V, _V, _V, _V, _V,
                                             _V]),
+    "open_cf_mlp_set_params": (ctypes.c_int, [_V, _V, _V]),
+    "open_cf_mlp_get_params": (ctypes.c_int, [_V, _V, _V]),
+    "open_cf_mlp_train_step": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _F, _V, _V, _V]),
+    "open_cf_mlp_infer": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
 }
+
+MLP_PARAMS = 86560   # OPEN_CF_MLP_PARAMS
 
 _lib = None
 
@@ -273,6 +279,47 @@ class OpenCF:
             col.numel(), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(V_scratch), W,
             self._stream()))
         return int(W[0]), int(W[1])
+
+    # -- learned warm start ------------------------------------------------
+    def _f32(self, t, name, numel=None):
+        if t.device != self.device or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 tensor on {self.device}")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"{name} must have {numel} entries")
+        return t
+
+    def mlp_set_params(self, params):
+        self._f32(params, "params", MLP_PARAMS)
+        self._check(lib().open_cf_mlp_set_params(self._h, _ptr(params), self._stream()))
+
+    def mlp_get_params(self):
+        out = self._empty(MLP_PARAMS, dtype=torch.float32)
+        self._check(lib().open_cf_mlp_get_params(self._h, _ptr(out), self._stream()))
+        return out
+
+    def mlp_train_step(self, row_ptr, col, val, U_target, lr: float = 1e-3, loss=None,
+                       grads: bool = False):
+        """One Adam step (grads False) or the gradient alone (grads True,
+        parameters unchanged).  ``loss``: optional float64 device tensor of
+        one element that receives the loss before the update."""
+        B, nnz = self._csr(row_ptr, col, val)
+        self._f32(U_target, "U_target", B * self.k)
+        if loss is not None and (loss.dtype != torch.float64 or loss.device != self.device):
+            raise ValueError("loss must be a float64 tensor on the device")
+        g = self._empty(MLP_PARAMS, dtype=torch.float32) if grads else None
+        self._check(lib().open_cf_mlp_train_step(self._h, B, nnz, _ptr(row_ptr), _ptr(col),
+                                                 _ptr(val), _ptr(U_target), float(lr),
+                                                 _ptr(loss), _ptr(g), self._stream()))
+        return g
+
+    def mlp_infer(self, row_ptr, col, val, row_rmse: bool = False):
+        m, nnz = self._csr(row_ptr, col, val)
+        U = self._empty(m, self.k, dtype=torch.float32)
+        st = self._empty(m, dtype=torch.int32)
+        rr = self._empty(m, dtype=torch.float32) if row_rmse else None
+        self._check(lib().open_cf_mlp_infer(self._h, m, nnz, _ptr(row_ptr), _ptr(col), _ptr(val),
+                                            _ptr(U), _ptr(st), _ptr(rr), self._stream()))
+        return (U, st, rr) if row_rmse else (U, st)
 
     def validate_csr(self, row_ptr, col, val, n: int) -> int:
         m, nnz = self._csr(row_ptr, col, val)

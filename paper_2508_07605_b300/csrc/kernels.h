@@ -23,6 +23,8 @@ template <typename TV> struct SolveArgs {
     double lambda;
     const void *Fb = nullptr;   // BF16 split copy of F: rows [hi (KP) | lo (KP)], BF16 path
     void *outb = nullptr;       // optional split BF16 copy of the output rows (stride 2*KP)
+    const int32_t *row_map = nullptr;   // optional: system i is CSR row row_map[i]
+    const int64_t *m_dev = nullptr;     // optional: number of systems read on the device
 };
 
 template <typename TV, typename TC>
@@ -85,6 +87,46 @@ cudaError_t launch_batched(const BatchArgs &b, int grid, cudaStream_t st);
 cudaError_t launch_batched_pack(int64_t P, const int64_t *rows, const int32_t *k,
                                 const int64_t *t_off, const int64_t *f_off, const float *src,
                                 float *dst, bool to_padded, cudaStream_t st);
+
+// MLP warm start (mlp.cu).
+constexpr int MLP_IN = 48, MLP_INP = 64, MLP_H = 256, MLP_SIN = 16;
+enum { EPI_BIAS_SELU = 0, EPI_BIAS = 1, EPI_DSELU = 2, EPI_PART = 3 };
+struct GemmArgs {
+    int M, N, K;
+    const void *A;            // bf16: [M,K] row-major, or [K,M] when transposed
+    int lda;
+    const void *B;            // bf16: [K,N] row-major, or [N,K] when transposed
+    int ldb;
+    const float *bias;        // [N]
+    const void *Zin;          // bf16 [M,N] pre-activations (EPI_DSELU)
+    void *out_bf;             // bf16 output
+    float *out_f;             // FP32 output / split-K partials
+    void *out_z;              // bf16 pre-activation output (EPI_BIAS_SELU)
+    int ldo;
+};
+cudaError_t launch_gemm(const GemmArgs &g, bool at, bool bt, int epi, int splits,
+                        cudaStream_t st);
+cudaError_t launch_mlp_features(int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
+                                const float *val, const float *cnorm, const float *gnorm,
+                                int64_t n, void *X, cudaStream_t st);
+cudaError_t launch_sum_parts(int64_t count, int splits, const float *part, float *out,
+                             cudaStream_t st);
+cudaError_t launch_colsum(int M, int N, const void *A, float *part, float *out, cudaStream_t st);
+cudaError_t launch_mlp_loss(int B, int k, const float *Y, const float *T, const float *G,
+                            void *dY, int ldd, float *part, double *loss, cudaStream_t st);
+cudaError_t launch_gram_v(int64_t n, int KP, int k, const float *V, float *part, float *G,
+                          cudaStream_t st);   // part: 64 * k * k floats
+// state: 16 bytes of device memory {int64 t; float lr} (zero = before step 1)
+cudaError_t launch_adam(int64_t count, float *th, const float *g, float *m1, float *m2, float b1,
+                        float b2, float eps, void *state, const int64_t *bf_map, void *thb,
+                        cudaStream_t st);
+cudaError_t launch_adam_set_lr(void *state, float lr, cudaStream_t st);
+cudaError_t launch_to_bf16_map(int64_t count, const float *th, const int64_t *bf_map, void *thb,
+                               cudaStream_t st);
+cudaError_t launch_fallback_rows(int64_t m, const float *rmse, float thr, int32_t *list,
+                                 int64_t *count, int32_t *status, cudaStream_t st);
+cudaError_t launch_fallback_mark(int64_t m, const int32_t *list, const int64_t *count,
+                                 int32_t *status, cudaStream_t st);
 
 // Reconstruction T = U V^T fused with Algorithm 2.
 template <typename TV> struct PredictArgs {

@@ -55,6 +55,10 @@ struct open_cf {
     int32_t b_W[2] = {8, 2};          // warps per problem: large class, small class
     int32_t b_class_end[2] = {0, 0};
     int64_t b_Um = 0, b_Vn = 0;       // padded factor sizes (floats)
+    // learned warm start: FP32 master parameters, Adam moments, BF16 weights, scratch
+    Buf mlp_th, mlp_g, mlp_m1, mlp_m2, mlp_bf, mlp_map, mlp_t, mlp_cn, mlp_scr, mlp_G;
+    bool mlp_ready = false;
+    int64_t mlp_Bcap = 0;
     uint64_t generation = 0;  // bumps whenever a workspace moves
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
@@ -450,6 +454,115 @@ cudaError_t batch_enqueue(open_cf_t *h, const BatchPlan &L, const BatchArgs &b, 
 
 }  // namespace
 
+namespace {
+
+// Parameter layout.  External (the caller's, and the oracle's): W1[48][256],
+// b1[256], W2[256][256], b2[256], W3[256][32], b3[32] = 86,560 floats.
+// Internal: W1 padded to [64][256] (rows 48..63 stay zero), rest identical.
+constexpr int64_t MLP_K = 32;
+constexpr int64_t P_EXT = MLP_IN * MLP_H + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H * MLP_K + MLP_K;
+constexpr int64_t P_INT = P_EXT + (MLP_INP - MLP_IN) * MLP_H;
+static_assert(P_EXT == OPEN_CF_MLP_PARAMS, "parameter count of the C ABI");
+constexpr int64_t OFF_W1 = 0, OFF_B1 = MLP_INP * MLP_H, OFF_W2 = OFF_B1 + MLP_H,
+                  OFF_B2 = OFF_W2 + MLP_H * MLP_H, OFF_W3 = OFF_B2 + MLP_H,
+                  OFF_B3 = OFF_W3 + MLP_H * MLP_K;
+// BF16 weight copies: W1b [64][256], W2b [256][256], W3b [256][32]
+constexpr int64_t BF_W1 = 0, BF_W2 = MLP_INP * MLP_H, BF_W3 = BF_W2 + MLP_H * MLP_H,
+                  BF_TOTAL = BF_W3 + MLP_H * MLP_K;
+
+struct MlpScratch {   // per chunk of Bp rows (multiple of 64)
+    void *X, *Z1, *H1, *Z2, *H2, *dY, *dZ2, *dZ1;
+    float *Y, *part, *cpart, *lpart;
+};
+
+size_t mlp_scratch_bytes(int64_t Bp) {
+    return 2 * (size_t)Bp * MLP_INP + 2 * 7 * (size_t)Bp * MLP_H + 2 * (size_t)Bp * MLP_K +
+           4 * (size_t)Bp * MLP_K + 4 * (size_t)(1 << 20) + 4 * (size_t)(Bp / 128 + 1) * MLP_H +
+           4 * 1024 + 8 * 256;
+}
+
+MlpScratch mlp_scratch(open_cf_t *h, int64_t Bp) {
+    unsigned char *p = (unsigned char *)h->mlp_scr.p;
+    auto take = [&](size_t bytes) {
+        void *q = p;
+        p += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    MlpScratch S;
+    S.X = take(2 * Bp * MLP_INP);
+    S.Z1 = take(2 * Bp * MLP_H);
+    S.H1 = take(2 * Bp * MLP_H);
+    S.Z2 = take(2 * Bp * MLP_H);
+    S.H2 = take(2 * Bp * MLP_H);
+    S.dY = take(2 * Bp * MLP_K);
+    S.dZ2 = take(2 * Bp * MLP_H);
+    S.dZ1 = take(2 * Bp * MLP_H);
+    S.Y = (float *)take(4 * Bp * MLP_K);
+    S.part = (float *)take(4 * (size_t)(1 << 20));
+    S.cpart = (float *)take(4 * (size_t)(Bp / 128 + 1) * MLP_H);
+    S.lpart = (float *)take(4 * 1024);
+    return S;
+}
+
+int mlp_check(open_cf_t *h) {
+    if (h->k != MLP_K) return fail(h, OPEN_CF_UNSUPPORTED, "the learned warm start has k = 32");
+    if (h->f64) return fail(h, OPEN_CF_UNSUPPORTED, "the learned warm start runs in FP32 modes");
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "set or fit V first");
+    if (h->cpu_caps.empty()) return fail(h, OPEN_CF_INVALID_ARG, "features need the cap grid");
+    if ((int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size() != h->n)
+        return fail(h, OPEN_CF_INVALID_ARG, "cap grid size differs from the settings of V");
+    if (!h->mlp_ready) return fail(h, OPEN_CF_NOT_FITTED, "set the MLP parameters first");
+    return OPEN_CF_OK;
+}
+
+int mlp_ensure_scratch(open_cf_t *h, int64_t Bp) {
+    if (Bp > h->mlp_Bcap) {
+        CK(h, ensure(h, h->mlp_scr, mlp_scratch_bytes(Bp) + 16 * 256));
+        h->mlp_Bcap = Bp;
+    }
+    return OPEN_CF_OK;
+}
+
+// Forward pass of Bp rows (features already in S.X).
+cudaError_t mlp_forward(open_cf_t *h, const MlpScratch &S, int Bp, cudaStream_t st) {
+    const float *th = (const float *)h->mlp_th.p;
+    const unsigned char *wb = (const unsigned char *)h->mlp_bf.p;
+    GemmArgs g{};
+    g.M = Bp; g.N = MLP_H; g.K = MLP_INP;
+    g.A = S.X; g.lda = MLP_INP; g.B = wb + 2 * BF_W1; g.ldb = MLP_H;
+    g.bias = th + OFF_B1; g.out_bf = S.H1; g.out_z = S.Z1; g.ldo = MLP_H;
+    cudaError_t e = launch_gemm(g, false, false, EPI_BIAS_SELU, 1, st);
+    if (e != cudaSuccess) return e;
+    g.K = MLP_H; g.A = S.H1; g.lda = MLP_H; g.B = wb + 2 * BF_W2; g.bias = th + OFF_B2;
+    g.out_bf = S.H2; g.out_z = S.Z2;
+    if ((e = launch_gemm(g, false, false, EPI_BIAS_SELU, 1, st)) != cudaSuccess) return e;
+    GemmArgs g3{};
+    g3.M = Bp; g3.N = MLP_K; g3.K = MLP_H; g3.A = S.H2; g3.lda = MLP_H; g3.B = wb + 2 * BF_W3;
+    g3.ldb = MLP_K; g3.bias = th + OFF_B3; g3.out_f = S.Y; g3.ldo = MLP_K;
+    return launch_gemm(g3, false, false, EPI_BIAS, 1, st);
+}
+
+int splits_for(int64_t Kdim, int want) {
+    int s = want;
+    while (s > 1 && (Kdim % (32LL * s) != 0)) s >>= 1;
+    return s;
+}
+
+// dW = A^T dZ over Bp rows (split-K, fixed-order sum) into grad region g_out.
+cudaError_t weight_grad(const MlpScratch &S, const void *A, int M, const void *dZ, int N, int Bp,
+                        float *g_out, cudaStream_t st) {
+    const int want = (int)std::max<int64_t>(1, 256 / (((M + 63) / 64) * ((N + 63) / 64)));
+    const int s = splits_for(Bp, std::min(want, (int)((1 << 20) / ((int64_t)M * N))));
+    GemmArgs g{};
+    g.M = M; g.N = N; g.K = Bp; g.A = A; g.lda = M; g.B = dZ; g.ldb = N; g.out_f = S.part;
+    g.ldo = N;
+    cudaError_t e = launch_gemm(g, true, false, EPI_PART, s, st);
+    if (e != cudaSuccess) return e;
+    return launch_sum_parts((int64_t)M * N, s, S.part, g_out, st);
+}
+
+}  // namespace
+
 extern "C" {
 
 int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
@@ -519,7 +632,9 @@ void open_cf_destroy(open_cf_t *h) {
         for (Buf *b : {&h->V, &h->Vb16, &h->cg, &h->off_ptr, &h->off_idx, &h->off_val, &h->U_w,
                        &h->csc_ptr, &h->csc_idx, &h->csc_val, &h->cnt, &h->tot, &h->part,
                        &h->flag, &h->j_ptr, &h->j_idx, &h->j_val, &h->Ub16, &h->b_meta, &h->b_Uw,
-                       &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter})
+                       &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter, &h->mlp_th,
+                       &h->mlp_g, &h->mlp_m1, &h->mlp_m2, &h->mlp_bf, &h->mlp_map, &h->mlp_t,
+                       &h->mlp_cn, &h->mlp_scr, &h->mlp_G})
             free_buf(*b);
     }
     delete h;
@@ -907,6 +1022,191 @@ int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const i
         W_out_host[0] = bw0;
         W_out_host[1] = bw1;
     }
+    return OPEN_CF_OK;
+}
+
+int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (h->k != MLP_K) return fail(h, OPEN_CF_UNSUPPORTED, "the learned warm start has k = 32");
+    if (h->f64) return fail(h, OPEN_CF_UNSUPPORTED, "the learned warm start runs in FP32 modes");
+    if (!params) return fail(h, OPEN_CF_INVALID_ARG, "params is NULL");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    CK(h, ensure(h, h->mlp_th, 4 * P_INT));
+    CK(h, ensure(h, h->mlp_g, 4 * P_INT));
+    CK(h, ensure(h, h->mlp_m1, 4 * P_INT));
+    CK(h, ensure(h, h->mlp_m2, 4 * P_INT));
+    CK(h, ensure(h, h->mlp_bf, 2 * BF_TOTAL));
+    CK(h, ensure(h, h->mlp_map, 8 * P_INT));
+    CK(h, ensure(h, h->mlp_t, 16));
+    CK(h, ensure(h, h->mlp_G, 4 * MLP_K * MLP_K));
+    float *th = (float *)h->mlp_th.p;
+    CK(h, cudaMemsetAsync(th, 0, 4 * P_INT, st));
+    CK(h, cudaMemcpyAsync(th, params, 4 * MLP_IN * MLP_H, cudaMemcpyDeviceToDevice, st));
+    CK(h, cudaMemcpyAsync(th + OFF_B1, params + MLP_IN * MLP_H, 4 * (P_EXT - MLP_IN * MLP_H),
+                          cudaMemcpyDeviceToDevice, st));
+    CK(h, cudaMemsetAsync(h->mlp_m1.p, 0, 4 * P_INT, st));
+    CK(h, cudaMemsetAsync(h->mlp_m2.p, 0, 4 * P_INT, st));
+    CK(h, cudaMemsetAsync(h->mlp_t.p, 0, 16, st));
+    std::vector<int64_t> map(P_INT, -1);
+    for (int64_t e = 0; e < MLP_INP * MLP_H; ++e) map[OFF_W1 + e] = BF_W1 + e;
+    for (int64_t e = 0; e < MLP_H * MLP_H; ++e) map[OFF_W2 + e] = BF_W2 + e;
+    for (int64_t e = 0; e < MLP_H * MLP_K; ++e) map[OFF_W3 + e] = BF_W3 + e;
+    CK(h, cudaMemcpy(h->mlp_map.p, map.data(), 8 * P_INT, cudaMemcpyHostToDevice));
+    CK(h, launch_to_bf16_map(P_INT, th, (const int64_t *)h->mlp_map.p, h->mlp_bf.p, st));
+    // normalised caps of every setting (features), FP32
+    const int64_t ns = (int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size();
+    if (ns > 0) {
+        const double cmin = *std::min_element(h->cpu_caps.begin(), h->cpu_caps.end());
+        const double cmax = *std::max_element(h->cpu_caps.begin(), h->cpu_caps.end());
+        const double gmin = *std::min_element(h->gpu_caps.begin(), h->gpu_caps.end());
+        const double gmax = *std::max_element(h->gpu_caps.begin(), h->gpu_caps.end());
+        const int ng = (int)h->gpu_caps.size();
+        std::vector<float> cn(2 * ns);
+        for (int64_t j = 0; j < ns; ++j) {
+            const double c = h->cpu_caps[j / ng], gg = h->gpu_caps[j % ng];
+            cn[j] = (float)(cmax > cmin ? (c - cmin) / (cmax - cmin) : 0.0);
+            cn[ns + j] = (float)(gmax > gmin ? (gg - gmin) / (gmax - gmin) : 0.0);
+        }
+        CK(h, ensure(h, h->mlp_cn, 4 * 2 * ns));
+        CK(h, cudaMemcpy(h->mlp_cn.p, cn.data(), 4 * 2 * ns, cudaMemcpyHostToDevice));
+    }
+    CK(h, cudaStreamSynchronize(st));
+    h->mlp_ready = true;
+    return OPEN_CF_OK;
+}
+
+int open_cf_mlp_get_params(open_cf_t *h, float *params_out, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!h->mlp_ready) return fail(h, OPEN_CF_NOT_FITTED, "set the MLP parameters first");
+    if (!params_out) return fail(h, OPEN_CF_INVALID_ARG, "params_out is NULL");
+    DeviceGuard g(h->device);
+    const float *th = (const float *)h->mlp_th.p;
+    CK(h, cudaMemcpyAsync(params_out, th, 4 * MLP_IN * MLP_H, cudaMemcpyDeviceToDevice, S(stream)));
+    CK(h, cudaMemcpyAsync(params_out + MLP_IN * MLP_H, th + OFF_B1, 4 * (P_EXT - MLP_IN * MLP_H),
+                          cudaMemcpyDeviceToDevice, S(stream)));
+    return OPEN_CF_OK;
+}
+
+int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *row_ptr,
+                           const int32_t *col, const float *val, const float *U_target, float lr,
+                           double *loss_out, float *grads_out, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    rc = check_csr_args(h, B, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (B <= 0 || !U_target) return fail(h, OPEN_CF_INVALID_ARG, "empty batch or no targets");
+    if (!(lr >= 0.0f) || !std::isfinite(lr)) return fail(h, OPEN_CF_INVALID_ARG, "bad lr");
+    if (B > (1 << 20)) return fail(h, OPEN_CF_UNSUPPORTED, "batch above 2^20 rows");
+    DeviceGuard g(h->device);
+    const int Bp = (int)((B + 63) / 64 * 64);
+    rc = mlp_ensure_scratch(h, Bp);
+    if (rc) return rc;
+    const MlpScratch Sx = mlp_scratch(h, Bp);
+    const int64_t ns = h->n;
+    std::vector<int64_t> key = {3, B, nnz, (int64_t)row_ptr, (int64_t)col, (int64_t)val,
+                                (int64_t)U_target, (int64_t)loss_out, (int64_t)grads_out};
+    if (!grads_out) CK(h, launch_adam_set_lr(h->mlp_t.p, lr, S(stream)));
+    return run_graph(h, key, S(stream), [&](cudaStream_t st) -> cudaError_t {
+        float *th = (float *)h->mlp_th.p, *gr = (float *)h->mlp_g.p;
+        const float *cn = (const float *)h->mlp_cn.p;
+        cudaError_t e = cudaMemsetAsync(Sx.X, 0, 2 * (size_t)Bp * MLP_INP, st);
+        if (e != cudaSuccess) return e;
+        if ((e = launch_mlp_features(B, nnz, row_ptr, col, val, cn, cn + ns, ns, Sx.X, st)))
+            return e;
+        if ((e = mlp_forward(h, Sx, Bp, st))) return e;
+        if ((e = launch_gram_v(ns, h->KP, MLP_K, (const float *)h->V.p, Sx.part,
+                               (float *)h->mlp_G.p, st)))
+            return e;
+        if ((e = cudaMemsetAsync(Sx.dY, 0, 2 * (size_t)Bp * MLP_K, st))) return e;
+        if ((e = launch_mlp_loss((int)B, MLP_K, Sx.Y, U_target, (const float *)h->mlp_G.p, Sx.dY,
+                                 MLP_K, Sx.lpart, loss_out, st)))
+            return e;
+        const unsigned char *wb = (const unsigned char *)h->mlp_bf.p;
+        // layer 3
+        if ((e = weight_grad(Sx, Sx.H2, MLP_H, Sx.dY, MLP_K, Bp, gr + OFF_W3, st))) return e;
+        if ((e = launch_colsum(Bp, MLP_K, Sx.dY, Sx.cpart, gr + OFF_B3, st))) return e;
+        GemmArgs gb{};
+        gb.M = Bp; gb.N = MLP_H; gb.K = MLP_K; gb.A = Sx.dY; gb.lda = MLP_K;
+        gb.B = wb + 2 * BF_W3; gb.ldb = MLP_K; gb.Zin = Sx.Z2; gb.out_bf = Sx.dZ2; gb.ldo = MLP_H;
+        if ((e = launch_gemm(gb, false, true, EPI_DSELU, 1, st))) return e;
+        // layer 2
+        if ((e = weight_grad(Sx, Sx.H1, MLP_H, Sx.dZ2, MLP_H, Bp, gr + OFF_W2, st))) return e;
+        if ((e = launch_colsum(Bp, MLP_H, Sx.dZ2, Sx.cpart, gr + OFF_B2, st))) return e;
+        gb.K = MLP_H; gb.A = Sx.dZ2; gb.lda = MLP_H; gb.B = wb + 2 * BF_W2; gb.ldb = MLP_H;
+        gb.Zin = Sx.Z1; gb.out_bf = Sx.dZ1;
+        if ((e = launch_gemm(gb, false, true, EPI_DSELU, 1, st))) return e;
+        // layer 1 (the padded input columns give zero gradients)
+        if ((e = weight_grad(Sx, Sx.X, MLP_INP, Sx.dZ1, MLP_H, Bp, gr + OFF_W1, st))) return e;
+        if ((e = launch_colsum(Bp, MLP_H, Sx.dZ1, Sx.cpart, gr + OFF_B1, st))) return e;
+        if (grads_out) {
+            if ((e = cudaMemcpyAsync(grads_out, gr, 4 * MLP_IN * MLP_H, cudaMemcpyDeviceToDevice, st)))
+                return e;
+            return cudaMemcpyAsync(grads_out + MLP_IN * MLP_H, gr + OFF_B1,
+                                   4 * (P_EXT - MLP_IN * MLP_H), cudaMemcpyDeviceToDevice, st);
+        }
+        return launch_adam(P_INT, th, gr, (float *)h->mlp_m1.p, (float *)h->mlp_m2.p, 0.9f,
+                           0.999f, 1e-8f, h->mlp_t.p, (const int64_t *)h->mlp_map.p, h->mlp_bf.p,
+                           st);
+    });
+}
+
+int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                      const int32_t *col, const float *val, float *U_out, int32_t *status,
+                      float *row_rmse, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    rc = check_csr_args(h, m, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (m > 0 && !U_out) return fail(h, OPEN_CF_INVALID_ARG, "U_out is NULL");
+    if (m == 0) return OPEN_CF_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const int64_t chunk = 65536;
+    rc = mlp_ensure_scratch(h, std::min<int64_t>((m + 63) / 64 * 64, chunk));
+    if (rc) return rc;
+    const int64_t ns = h->n;
+    const float *cn = (const float *)h->mlp_cn.p;
+    for (int64_t r0 = 0; r0 < m; r0 += chunk) {
+        const int64_t mc = std::min(chunk, m - r0);
+        const int Bp = (int)((mc + 63) / 64 * 64);
+        const MlpScratch Sx = mlp_scratch(h, Bp);
+        CK(h, cudaMemsetAsync(Sx.X, 0, 2 * (size_t)Bp * MLP_INP, st));
+        CK(h, launch_mlp_features(mc, nnz, row_ptr + r0, col, val, cn, cn + ns, ns, Sx.X, st));
+        CK(h, mlp_forward(h, Sx, Bp, st));
+        CK(h, cudaMemcpyAsync(U_out + r0 * MLP_K, Sx.Y, 4 * mc * MLP_K, cudaMemcpyDeviceToDevice,
+                              st));
+    }
+    // observed-entry RMSE of the learned factors; rows above the threshold fall back to ALS
+    CK(h, ensure(h, h->part, sizeof(double) * 3 * objective_parts(std::max<int64_t>(m, h->n))));
+    CK(h, ensure(h, h->flag, 64));
+    CK(h, ensure(h, h->j_idx, sizeof(int32_t) * m));   // fallback row list
+    float *rm = row_rmse;
+    if (!rm) {
+        CK(h, ensure(h, h->csc_val, sizeof(float) * std::max<int64_t>(m, 1)));
+        rm = (float *)h->csc_val.p;
+    }
+    double *Jtmp = (double *)h->flag.p + 1;
+    CK(h, launch_objective<float>(m, nnz, row_ptr, col, val, U_out, MLP_K, MLP_K,
+                                  (const float *)h->V.p, h->n, h->KP, h->cfg.lambda,
+                                  (double *)h->part.p, Jtmp, rm, st));
+    int64_t *cnt = (int64_t *)h->flag.p;
+    CK(h, cudaMemsetAsync(cnt, 0, sizeof(int64_t), st));
+    CK(h, launch_fallback_rows(m, rm, h->cfg.mlp_fallback_threshold, (int32_t *)h->j_idx.p, cnt,
+                               status, st));
+    SolveArgs<float> a{m, nnz, row_ptr, col, val, (const float *)h->V.p, h->n, U_out, MLP_K,
+                       MLP_K, status, h->cfg.lambda};
+    a.row_map = (const int32_t *)h->j_idx.p;
+    a.m_dev = cnt;
+    if (h->cfg.precision == OPEN_CF_BF16_GRAM) a.Fb = h->Vb16.p;
+    CK(h, half_step<float>(h, a, st));
+    CK(h, launch_fallback_mark(m, (const int32_t *)h->j_idx.p, cnt, status, st));
     return OPEN_CF_OK;
 }
 

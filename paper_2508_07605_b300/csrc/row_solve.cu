@@ -43,8 +43,9 @@ k_row_solve(SolveArgs<TV> a) {
     // WPS == 1: one system per warp; WPS > 1: one system per CTA.
     const int64_t sys0 = (WPS == 1) ? (int64_t)blockIdx.x * WARPS + warp : (int64_t)blockIdx.x;
     const int64_t sys_stride = (WPS == 1) ? (int64_t)gridDim.x * WARPS : (int64_t)gridDim.x;
-    for (int64_t i = sys0; i < a.m; i += sys_stride)
-        solve_system<TV, TC, KP, WPS>(a, i, smem, warp, lane);
+    const int64_t M = a.m_dev ? *a.m_dev : a.m;   // systems (a device count for compacted lists)
+    for (int64_t i = sys0; i < M; i += sys_stride)
+        solve_system<TV, TC, KP, WPS>(a, a.row_map ? a.row_map[i] : i, smem, warp, lane);
 }
 
 template <typename TV, typename TC, int KP, int WPS>

@@ -135,8 +135,9 @@ k_row_solve_tc(SolveArgs<float> a) {
                                     : (int64_t)blockIdx.x;
     const int64_t sys_stride = (WPS == 1) ? (int64_t)gridDim.x * WARPS * SPW
                                           : (int64_t)gridDim.x;
+    const int64_t M = a.m_dev ? *a.m_dev : a.m;   // systems (a device count for compacted lists)
 
-    for (int64_t base = sys0; base < a.m; base += sys_stride) {
+    for (int64_t base = sys0; base < M; base += sys_stride) {
         // ---------------- Gram phase -------------------------------------
         // The warp's work is a list of 32-observation items: the chunks of
         // its SPW systems in order (WPS = 1), or this warp's slice of the
@@ -153,7 +154,7 @@ k_row_solve_tc(SolveArgs<float> a) {
             const int64_t i = base + si;
             int64_t beg = 0, end = 0;
             bad_s[si] = false;
-            if (i < a.m) bad_s[si] = !row_bounds(a.ptr, i, a.nnz, beg, end);
+            if (i < M) bad_s[si] = !row_bounds(a.ptr, a.row_map ? a.row_map[i] : i, a.nnz, beg, end);
             beg_s[si] = beg;
             s_s[si] = end - beg;
             if (WPS == 1) {
@@ -474,8 +475,9 @@ k_row_solve_tc(SolveArgs<float> a) {
 #pragma unroll
             for (int off = 1; off < KP; off <<= 1)
                 fail |= __shfl_xor_sync(FULL, (int)fail, off) != 0;
-            const int64_t i = base + slot;
-            if (writer && i < a.m) {
+            const int64_t is = base + slot;
+            if (writer && is < M) {
+                const int64_t i = a.row_map ? a.row_map[is] : is;
                 int32_t st = ST_OK;
                 if (bad) st = ST_BAD;
                 else if (s == 0) st = ST_EMPTY;

@@ -355,17 +355,26 @@ class LearnedWorkload:
     lam: float
     s_obs: int
     scale: float
-    Vt: object        # ground-truth setting factors [n, rank] (torch)
-    offline: object   # dense noisy offline block [m_off, n] (torch float32)
+    Vt: object        # ground-truth setting factors [n, rank] (torch), smooth in the caps
+    A: object         # trait loadings [traits, rank]
     gen: object       # torch generator for app draws
     device: object
     rank: int
+    traits: int
+    spread: float
+
+    def V_fixed(self):
+        """The fixed setting factors of the handle, V = Vt / sqrt(scale), so
+        that a row of normalised runtimes is (u / sqrt(scale)) V^T."""
+        return (self.Vt / math.sqrt(self.scale)).contiguous()
 
     def draw_apps(self, count: int):
-        """``count`` new apps: full noisy rows [count, n], noiseless rows, and
+        """``count`` new apps: noisy rows [count, n], noiseless rows, and
         ``s_obs`` distinct observed settings per app (sorted, int32)."""
         torch = _torch()
-        Ua = torch.randn(count, self.rank, generator=self.gen, device=self.device) / 2.0
+        z = torch.randn(count, self.traits, generator=self.gen, device=self.device)
+        Ua = z @ self.A + self.spread * torch.randn(count, self.rank, generator=self.gen,
+                                                    device=self.device)
         clean = (Ua @ self.Vt.T) / self.scale
         noisy = clean + NOISE_STD * torch.randn(clean.shape, generator=self.gen,
                                                 device=self.device)
@@ -374,29 +383,87 @@ class LearnedWorkload:
         return noisy, clean, obs
 
 
+def dense_rows_csr(rows):
+    """CSR of fully observed rows [m, n] (every setting, in index order)."""
+    torch = _torch()
+    m, n = rows.shape
+    dev = rows.device
+    row_ptr = torch.arange(0, (m + 1) * n, n, dtype=torch.int64, device=dev)
+    col = torch.arange(n, dtype=torch.int32, device=dev).repeat(m)
+    return row_ptr, col, rows.reshape(-1).contiguous()
+
+
+def learned_pool(wl: "LearnedWorkload", handle, count: int, chunk: int = 65536):
+    """Training pool of the learned warm start: ``count`` apps, each with its
+    ``s_obs`` observed entries (features) and, as target, the factor the
+    plain fold-in computes from the app's full noisy profile.  Returns
+    (col [count, s_obs] int32, val [count, s_obs] float32, U_target [count, k])."""
+    torch = _torch()
+    cols, vals, tgts = [], [], []
+    for s in range(0, count, chunk):
+        c = min(chunk, count - s)
+        noisy, _, obs = wl.draw_apps(c)
+        U, _ = handle.complete_rows(*dense_rows_csr(noisy))
+        cols.append(obs)
+        vals.append(torch.gather(noisy, 1, obs.to(torch.int64)))
+        tgts.append(U)
+        del noisy
+    return torch.cat(cols), torch.cat(vals), torch.cat(tgts)
+
+
+def observed_csr(rows, obs):
+    """CSR of the entries ``obs`` [m, s] (sorted per row) of ``rows`` [m, n]."""
+    torch = _torch()
+    m, s = obs.shape
+    row_ptr = torch.arange(0, (m + 1) * s, s, dtype=torch.int64, device=rows.device)
+    val = torch.gather(rows, 1, obs.to(torch.int64)).reshape(-1).contiguous()
+    return row_ptr, obs.reshape(-1).contiguous(), val
+
+
 def make_learned(seed: int = 0, n_cpu: int = 64, n_gpu: int = 64, rank: int = 32, k: int = 32,
-                 lam: float = 0.05, m_off: int = 4096, s_obs: int = 16,
-                 device="cuda") -> LearnedWorkload:
-    """Fixed 4096-setting V from a dense 4096-app offline block of the same
-    generative model (rank-32 truth U V^T / max|U V^T| plus noise)."""
+                 lam: float = 0.05, s_obs: int = 16, traits: int = 4, spread: float = 0.05,
+                 smooth_terms: int = 6, device="cuda") -> LearnedWorkload:
+    """Workload of the learned warm start (4096 settings, k = 32, 16 observed
+    settings per new app).
+
+    Runtime varies smoothly with the caps, so each true setting factor is a
+    random combination of low-frequency cosines of the normalised caps:
+    Vt[j] = sum_{a,b < smooth_terms} cos(pi a c_j) cos(pi b g_j) w_ab with
+    w_ab ~ N(0, I) * 0.6^(a+b).  Applications share a few traits (compute vs
+    memory intensity and the like): u = z A + spread * e, z ~ N(0, I_traits),
+    A ~ N(0, 1/traits), e ~ N(0, I).  Rows are u Vt^T / scale plus N(0, 0.01)
+    noise, scale = max |u Vt^T| over a 4096-app draw."""
     torch = _torch()
     n = n_cpu * n_gpu
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
-    Vt = torch.randn(n, rank, generator=gen, device=device) / 2.0
-    Uo = torch.randn(m_off, rank, generator=gen, device=device) / 2.0
-    M = Uo @ Vt.T
-    scale = float(M.abs().max().item())
-    offline = M / scale + NOISE_STD * torch.randn(M.shape, generator=gen, device=device)
-    return LearnedWorkload(n, n_cpu, n_gpu, k, lam, s_obs, scale, Vt, offline.contiguous(),
-                           gen, device, rank)
+    c = torch.linspace(0.0, 1.0, n_cpu, device=device, dtype=torch.float64)
+    g = torch.linspace(0.0, 1.0, n_gpu, device=device, dtype=torch.float64)
+    cc = c.repeat_interleave(n_gpu)
+    gg = g.repeat(n_cpu)
+    basis = []
+    for a in range(smooth_terms):
+        for b in range(smooth_terms):
+            basis.append(torch.cos(math.pi * a * cc) * torch.cos(math.pi * b * gg) * 0.6 ** (a + b))
+    Phi = torch.stack(basis, 1).float()
+    W = torch.randn(Phi.shape[1], rank, generator=gen, device=device)
+    Vt = (Phi @ W).contiguous()
+    A = torch.randn(traits, rank, generator=gen, device=device) / math.sqrt(traits)
+    z = torch.randn(4096, traits, generator=gen, device=device)
+    Uo = z @ A + spread * torch.randn(4096, rank, generator=gen, device=device)
+    scale = float((Uo @ Vt.T).abs().max().item())
+    return LearnedWorkload(n, n_cpu, n_gpu, k, lam, s_obs, scale, Vt, A, gen, device, rank,
+                           traits, spread)
 
 
-def mlp_init(rng: np.random.Generator, sizes=(48, 256, 256, 32)):
+def mlp_init(rng: np.random.Generator, sizes=(48, 256, 256, 32), out_scale: float = 1.0):
     """LeCun-normal initial weights (the SELU recommendation of Klambauer et
-    al. 2017) and zero biases; W_l is stored [in, out] row-major."""
+    al. 2017) and zero biases; W_l is stored [in, out] row-major.  The last
+    layer's weights are multiplied by ``out_scale`` (targets far smaller than
+    one train faster from a small initial output)."""
     params = []
     for a, b in zip(sizes[:-1], sizes[1:]):
         params.append(rng.standard_normal((a, b)) / math.sqrt(a))
         params.append(np.zeros(b))
+    params[-2] = params[-2] * out_scale
     return params
