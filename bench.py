@@ -761,7 +761,7 @@ def run_gpu_learned(args):
                                  "fallback_rows_pred_rel_err_max": float(rel_fb.max()),
                                  "fallback_rows_gate": 1e-5,
                                  "fallback_decision_agreement": agree},
-        "roofline": {"kernel": "MLP forward (k_gemm_bf16 x3 + features), mma.sync m16n8k16",
+        "roofline": {"kernel": "k_mlp_forward_tc (fused features + 3 tcgen05 layers + residual)",
                      "bound": "tensor", "achieved": fl_fwd / t_mlp / 1e12, "peak": bf16_peak,
                      "unit": "TFLOP/s", "frac": fl_fwd / t_mlp / 1e12 / bf16_peak,
                      "traffic": None, "peak_kind": "bf16_tflops (burst) of measured"},

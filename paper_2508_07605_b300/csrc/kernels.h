@@ -117,16 +117,47 @@ cudaError_t launch_mlp_loss(int B, int k, const float *Y, const float *T, const 
 cudaError_t launch_gram_v(int64_t n, int KP, int k, const float *V, float *part, float *G,
                           cudaStream_t st);   // part: 64 * k * k floats
 // state: 16 bytes of device memory {int64 t; float lr} (zero = before step 1)
+// BF16 copies of the parameters: entry e goes to thb[map[e]] and img[imap[e]]
+// (an index < 0 means no copy).
 cudaError_t launch_adam(int64_t count, float *th, const float *g, float *m1, float *m2, float b1,
                         float b2, float eps, void *state, const int64_t *bf_map, void *thb,
-                        cudaStream_t st);
+                        const int64_t *img_map, void *img, cudaStream_t st);
 cudaError_t launch_adam_set_lr(void *state, float lr, cudaStream_t st);
 cudaError_t launch_to_bf16_map(int64_t count, const float *th, const int64_t *bf_map, void *thb,
-                               cudaStream_t st);
+                               const int64_t *img_map, void *img, cudaStream_t st);
 cudaError_t launch_fallback_rows(int64_t m, const float *rmse, float thr, int32_t *list,
                                  int64_t *count, int32_t *status, cudaStream_t st);
 cudaError_t launch_fallback_mark(int64_t m, const int32_t *list, const int64_t *count,
                                  int32_t *status, cudaStream_t st);
+
+// Fused tcgen05 forward pass (mlp_tc.cu).  img holds the BF16 weight images
+// W2 | W1 | W3 (element offsets below), each an N x K K-major operand image:
+// element (n, k) at (n / 8) * 8K + (k / 8) * 64 + (n % 8) * 8 + k % 8.
+constexpr int MLP_K_OUT = 32;
+constexpr int64_t MLP_IMG_W2 = 0, MLP_IMG_W1 = MLP_H * MLP_H,
+                  MLP_IMG_W3 = MLP_IMG_W1 + MLP_INP * MLP_H,
+                  MLP_IMG_TOTAL = MLP_IMG_W3 + MLP_H * MLP_K_OUT;
+struct MlpTcArgs {
+    int64_t m, nnz;
+    const int64_t *ptr;
+    const int32_t *idx;
+    const float *val;
+    const float *cnorm, *gnorm;   // normalised caps of every setting
+    int64_t n;
+    const void *img;              // BF16 weight images
+    const float *b1, *b2, *b3;
+    float *Y;                     // m x 32, 16-byte aligned
+    const float *V;               // n x 32 setting factors (observed-entry residual)
+    float threshold;              // fallback when the row's RMSE is above it (or not finite)
+    float *row_rmse;              // m, may be null
+    int32_t *status;              // m, may be null: OK or FALLBACK_USED
+    int32_t *list;                // fallback rows, appended at list[*count]
+    int64_t *count;
+    int *err;                     // set to 1 when a bounded wait ran out
+};
+size_t mlp_forward_tc_smem();
+cudaError_t prepare_mlp_forward_tc();
+cudaError_t launch_mlp_forward_tc(const MlpTcArgs &a, int num_sms, cudaStream_t st);
 
 // Reconstruction T = U V^T fused with Algorithm 2.
 template <typename TV> struct PredictArgs {

@@ -293,7 +293,8 @@ __global__ void k_adam_set_lr(AdamState *s, float lr) { s->lr = lr; }
 __global__ void k_adam(int64_t count, float *__restrict__ th, const float *__restrict__ gr,
                        float *__restrict__ m1, float *__restrict__ m2, float b1, float b2,
                        float eps, const AdamState *__restrict__ as,
-                       const int64_t *__restrict__ bf_map, bf16 *__restrict__ thb) {
+                       const int64_t *__restrict__ bf_map, bf16 *__restrict__ thb,
+                       const int64_t *__restrict__ img_map, bf16 *__restrict__ img) {
     const double tt = (double)as->t;   // bias corrections of step t (after the tick)
     const float lr = as->lr;
     const float c1 = (float)(1.0 - pow((double)b1, tt)), c2 = (float)(1.0 - pow((double)b2, tt));
@@ -306,17 +307,22 @@ __global__ void k_adam(int64_t count, float *__restrict__ th, const float *__res
         m2[e] = b;
         const float t = th[e] - lr * (a / c1) / (sqrtf(b / c2) + eps);
         th[e] = t;
-        const int64_t q = bf_map[e];
-        if (q >= 0) thb[q] = __float2bfloat16_rn(t);
+        const bf16 tb = __float2bfloat16_rn(t);
+        const int64_t q = bf_map[e], qi = img_map[e];
+        if (q >= 0) thb[q] = tb;
+        if (qi >= 0) img[qi] = tb;
     }
 }
 
 __global__ void k_to_bf16_map(int64_t count, const float *__restrict__ th,
-                              const int64_t *__restrict__ bf_map, bf16 *__restrict__ thb) {
+                              const int64_t *__restrict__ bf_map, bf16 *__restrict__ thb,
+                              const int64_t *__restrict__ img_map, bf16 *__restrict__ img) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = bf_map[e];
-        if (q >= 0) thb[q] = __float2bfloat16_rn(th[e]);
+        const bf16 tb = __float2bfloat16_rn(th[e]);
+        const int64_t q = bf_map[e], qi = img_map[e];
+        if (q >= 0) thb[q] = tb;
+        if (qi >= 0) img[qi] = tb;
     }
 }
 
@@ -391,11 +397,12 @@ cudaError_t launch_gram_v(int64_t n, int KP, int k, const float *V, float *part,
 
 cudaError_t launch_adam(int64_t count, float *th, const float *g, float *m1, float *m2, float b1,
                         float b2, float eps, void *state, const int64_t *bf_map, void *thb,
-                        cudaStream_t st) {
+                        const int64_t *img_map, void *img, cudaStream_t st) {
     AdamState *as = reinterpret_cast<AdamState *>(state);
     k_adam_tick<<<1, 1, 0, st>>>(as);
     k_adam<<<gfor(count), 256, 0, st>>>(count, th, g, m1, m2, b1, b2, eps, as, bf_map,
-                                        reinterpret_cast<bf16 *>(thb));
+                                        reinterpret_cast<bf16 *>(thb), img_map,
+                                        reinterpret_cast<bf16 *>(img));
     return cudaGetLastError();
 }
 
@@ -405,8 +412,9 @@ cudaError_t launch_adam_set_lr(void *state, float lr, cudaStream_t st) {
 }
 
 cudaError_t launch_to_bf16_map(int64_t count, const float *th, const int64_t *bf_map, void *thb,
-                               cudaStream_t st) {
-    k_to_bf16_map<<<gfor(count), 256, 0, st>>>(count, th, bf_map, reinterpret_cast<bf16 *>(thb));
+                               const int64_t *img_map, void *img, cudaStream_t st) {
+    k_to_bf16_map<<<gfor(count), 256, 0, st>>>(count, th, bf_map, reinterpret_cast<bf16 *>(thb),
+                                                img_map, reinterpret_cast<bf16 *>(img));
     return cudaGetLastError();
 }
 

@@ -1,0 +1,545 @@
+// Fused forward pass of the learned warm start on the 5th-generation tensor
+// cores: features -> W1 -> SELU -> W2 -> SELU -> W3 for 128-row tiles in one
+// persistent kernel (one CTA per SM).
+//
+// Per tile, everything stays on the SM:
+//   * the 128 rows' features (16 observations x (c_norm, g_norm, runtime),
+//     padded to 64) are built from the CSR by one thread per row and stored
+//     as a BF16 operand image in shared memory;
+//   * each layer is a chain of tcgen05.mma (kind::f16, M = 128, K = 16 per
+//     instruction, BF16 operands, FP32 accumulation in TMEM) issued by one
+//     thread; tcgen05.commit signals an mbarrier when the chain is done;
+//   * 16 warps read the accumulator back with tcgen05.ld (warp w owns TMEM
+//     lanes 32 (w mod 4) .. +31 and a quarter of the columns), add the bias,
+//     apply SELU and write the BF16 activation image for the next layer into
+//     the same shared buffer;
+//   * the last epilogue writes u, then four threads per row evaluate the
+//     row's observed-entry RMSE under u V^T (the judge of the learned factor)
+//     and append the rows above the threshold to the fallback list;
+//   * W2 (128 KB) stays resident for the CTA's lifetime; W1 and W3 take
+//     turns in a 32 KB stage buffer, fetched by bulk asynchronous copies
+//     (cp.async.bulk + mbarrier transaction counts) while the epilogues run.
+//
+// Operand images (no swizzle, K-major): an R x K BF16 matrix is stored as
+// 8 x 8 core matrices of 128 contiguous bytes; element (r, k) lives at byte
+//   (r / 8) * (16 K) + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// so the descriptor's leading-dimension offset (next core matrix along K)
+// is 128 B and its stride-dimension offset (next 8 rows) is 16 K bytes.
+// The engine keeps the weights' BF16 copies in exactly this form, so they
+// reach shared memory by plain bulk copies.
+//
+// Every wait is bounded.  A CTA whose wait runs out records the event in
+// *err, writes NaN rows for its remaining tiles (their observed-entry
+// residual is then not finite, so the engine re-solves them by ALS), drains
+// its outstanding copies with another bounded wait and frees its TMEM.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ocf {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int TM = 128;   // rows per tile (UMMA M)
+constexpr int NTHREADS = 512;
+constexpr uint32_t OFF_W2 = 0, OFF_STAGE = 131072, OFF_ACT = 163840, OFF_BAR = 229376;
+constexpr uint32_t OFF_BIAS = OFF_BAR + 64;   // b1 | b2 | b3 (FP32)
+constexpr uint32_t SMEM_BYTES = OFF_BIAS + 4 * (2 * 256 + 32);
+constexpr uint32_t BYTES_W2 = 131072, BYTES_W1 = 32768, BYTES_W3 = 16384;
+constexpr uint32_t TMEM_COLS = 512;   // layer-1 / layer-3 accumulator at 0, layer-2 at 256
+constexpr int WAIT_LIMIT = 1 << 22;
+
+constexpr float SELU_L = 1.0507009873554804934193349852946f;
+constexpr float SELU_A = 1.6732632423543772848170429916717f;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading- and stride-
+// dimension byte offsets (all in 16-byte units), descriptor version 1, no
+// swizzle, base offset 0.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
+// N columns, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < WAIT_LIMIT; ++it)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ float selu_f(float z) {
+    const float e = __expf(fminf(z, 0.f)) - 1.f;
+    return z > 0.f ? SELU_L * z : (SELU_L * SELU_A) * e;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Half h of row r of the tile (global row i) of the BF16 feature image
+// (K = 64): observations 8h .. 8h + 7 -> features 24h .. 24h + 23 (chunks
+// 3h .. 3h + 2); half 1 also writes the zero chunks 6 and 7.
+__device__ __forceinline__ void features_half(const MlpTcArgs &a, int64_t i, int h,
+                                              unsigned char *act, int r) {
+    float x[24];
+#pragma unroll
+    for (int f = 0; f < 24; ++f) x[f] = 0.f;
+    int64_t beg = 0, end = 0;
+    if (i < a.m && row_bounds(a.ptr, i, a.nnz, beg, end)) {
+        const int64_t b = beg + 8 * h;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (b + t < end) {
+                const int32_t j = __ldg(a.idx + b + t);
+                if (j >= 0 && (int64_t)j < a.n) {
+                    x[3 * t] = __ldg(a.cnorm + j);
+                    x[3 * t + 1] = __ldg(a.gnorm + j);
+                    x[3 * t + 2] = __ldg(a.val + b + t);
+                }
+            }
+        }
+    }
+    unsigned char *row = act + (r >> 3) * (MLP_INP * 16) + (r & 7) * 16;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const uint4 w = make_uint4(pack_bf16(x[8 * c], x[8 * c + 1]),
+                                   pack_bf16(x[8 * c + 2], x[8 * c + 3]),
+                                   pack_bf16(x[8 * c + 4], x[8 * c + 5]),
+                                   pack_bf16(x[8 * c + 6], x[8 * c + 7]));
+        *reinterpret_cast<uint4 *>(row + (3 * h + c) * 128) = w;
+    }
+    if (h == 1) {
+        *reinterpret_cast<uint4 *>(row + 6 * 128) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4 *>(row + 7 * 128) = make_uint4(0, 0, 0, 0);
+    }
+}
+
+// Hidden-layer epilogue: this warp's 32 rows, columns [c0, c0 + 64) of the
+// accumulator at TMEM column tacc: bias (from shared memory) + SELU -> BF16
+// image (K = 256).  Both TMEM loads are in flight before the first wait.
+__device__ __forceinline__ void epi_hidden(uint32_t tmem, uint32_t tacc, int q, int lane, int c0,
+                                           const float *bias_s, unsigned char *act) {
+    const int r = 32 * q + lane;
+    unsigned char *row = act + (r >> 3) * (MLP_H * 16) + (r & 7) * 16;
+    uint32_t v0[32], v1[32];
+    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + tacc + (uint32_t)c0;
+    tc_ld32(ta, v0);
+    tc_ld32(ta + 32, v1);
+    tc_wait_ld();
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = 8 * g + 2 * e;
+            pk[e] = pack_bf16(selu_f(__uint_as_float(v0[c]) + bias_s[c0 + c]),
+                              selu_f(__uint_as_float(v0[c + 1]) + bias_s[c0 + c + 1]));
+        }
+        *reinterpret_cast<uint4 *>(row + (c0 / 8 + g) * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = 8 * g + 2 * e;
+            pk[e] = pack_bf16(selu_f(__uint_as_float(v1[c]) + bias_s[c0 + 32 + c]),
+                              selu_f(__uint_as_float(v1[c + 1]) + bias_s[c0 + 32 + c + 1]));
+        }
+        *reinterpret_cast<uint4 *>(row + ((c0 + 32) / 8 + g) * 128) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+// Observed-entry RMSE of the tile's 128 rows under u (shared memory, rows of
+// U_STRIDE floats), one group of four lanes per row: per observation the
+// four lanes read one 128-byte row of V (32 bytes each, coalesced), multiply
+// by their eight components of u and add across the group.  Observations go
+// four at a time (one index and value per lane).  Lane 0 of the group writes
+// the RMSE and the status and, when the row is above the threshold (or its
+// residual is not finite), appends it to the fallback list.
+constexpr int U_STRIDE = 36;   // 16-byte aligned rows, conflict-free float4 access
+__device__ __forceinline__ void residual_rows(const MlpTcArgs &a, int64_t row0, const float *u_s,
+                                              int tid) {
+    const int rr = tid >> 2, gl = tid & 3;
+    const unsigned gmask = 0xFu << ((tid & 31) & ~3);
+    const int64_t i = row0 + rr;
+    int64_t beg = 0, end = 0;
+    const bool ok = i < a.m && row_bounds(a.ptr, i, a.nnz, beg, end);
+    const float4 ua = *reinterpret_cast<const float4 *>(u_s + rr * U_STRIDE + 8 * gl);
+    const float4 ub = *reinterpret_cast<const float4 *>(u_s + rr * U_STRIDE + 8 * gl + 4);
+    float sse = 0.f;
+    for (int64_t t0 = beg; t0 < end; t0 += 4) {
+        const int64_t t = t0 + gl;
+        int32_t j = -1;
+        float r = 0.f;
+        if (t < end) {
+            j = __ldg(a.idx + t);
+            r = __ldg(a.val + t);
+            if (j < 0 || (int64_t)j >= a.n) j = -1;
+        }
+        float mine = 0.f;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int32_t jo = __shfl_sync(gmask, j, o, 4);
+            float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+            if (jo >= 0) {
+                const float4 *vr = reinterpret_cast<const float4 *>(a.V + (int64_t)jo * MLP_K_OUT);
+                x0 = __ldg(vr + 2 * gl);
+                x1 = __ldg(vr + 2 * gl + 1);
+            }
+            float d = ua.x * x0.x;
+            d = fmaf(ua.y, x0.y, d);
+            d = fmaf(ua.z, x0.z, d);
+            d = fmaf(ua.w, x0.w, d);
+            d = fmaf(ub.x, x1.x, d);
+            d = fmaf(ub.y, x1.y, d);
+            d = fmaf(ub.z, x1.z, d);
+            d = fmaf(ub.w, x1.w, d);
+            d += __shfl_xor_sync(gmask, d, 2, 4);
+            d += __shfl_xor_sync(gmask, d, 1, 4);
+            if (o == gl) mine = d;
+        }
+        if (j >= 0) {
+            const float e = r - mine;
+            sse = fmaf(e, e, sse);
+        }
+    }
+    sse += __shfl_xor_sync(gmask, sse, 2, 4);
+    sse += __shfl_xor_sync(gmask, sse, 1, 4);
+    if (gl == 0 && i < a.m) {
+        const int64_t s = end - beg;
+        const float rmse = (ok && s > 0) ? sqrtf(sse / (float)s) : 0.0f;
+        if (a.row_rmse) a.row_rmse[i] = rmse;
+        const bool fb = !(rmse <= a.threshold);
+        if (a.status) a.status[i] = fb ? ST_FALLBACK : ST_OK;
+        if (fb)
+            a.list[atomicAdd(reinterpret_cast<unsigned long long *>(a.count), 1ull)] = (int32_t)i;
+    }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+
+// One warp, while layer 2 runs: pull the next tile's row pointers, column
+// indices and values into L2 so that its feature phase does not wait on DRAM.
+__device__ __forceinline__ void prefetch_tile(const MlpTcArgs &a, int64_t nr0, int lane) {
+    const int64_t nr1 = nr0 + TM < a.m ? nr0 + TM : a.m;
+    for (int64_t e = nr0 + 16 * lane; e <= nr1; e += 16 * 32) prefetch_l2(a.ptr + e);
+    const int64_t p0 = __ldg(a.ptr + nr0), p1 = __ldg(a.ptr + nr1);
+    if (p0 < 0 || p1 < p0 || p1 > a.nnz) return;
+    for (int64_t t = p0 + 32 * lane; t < p1; t += 32 * 32) {
+        prefetch_l2(a.idx + t);
+        prefetch_l2(a.val + t);
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, cq = warp >> 2;   // TMEM lane quarter, column quarter
+    const uint32_t s0 = smem_u32(sm);
+    const uint32_t bar_w2 = s0 + OFF_BAR, bar_st = bar_w2 + 8, bar_mma = bar_w2 + 16;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + OFF_BAR + 24);
+    float *bias_s = reinterpret_cast<float *>(sm + OFF_BIAS);   // b1 [0,256) b2 [256,512) b3
+    const int64_t tiles = (a.m + TM - 1) / TM;
+    const unsigned char *img = reinterpret_cast<const unsigned char *>(a.img);
+
+    if (tid == 0) {
+        mbar_init(bar_w2, 1);
+        mbar_init(bar_st, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    for (int c = tid; c < 2 * MLP_H + MLP_K_OUT; c += NTHREADS)
+        bias_s[c] = c < MLP_H ? a.b1[c] : (c < 2 * MLP_H ? a.b2[c - MLP_H] : a.b3[c - 2 * MLP_H]);
+    if (warp == 0) tc_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // bar_st completes alternately for W1 (parity 0) and W3 (parity 1)
+    bool st_pending = false;
+    if (tid == 0 && (int64_t)blockIdx.x < tiles) {
+        mbar_expect_tx(bar_w2, BYTES_W2);
+        for (uint32_t c = 0; c < BYTES_W2; c += 32768)
+            bulk_g2s(s0 + OFF_W2 + c, img + 2 * MLP_IMG_W2 + c, 32768, bar_w2);
+        mbar_expect_tx(bar_st, BYTES_W1);
+        bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W1, BYTES_W1, bar_st);
+        st_pending = true;
+    }
+    const uint32_t id256 = idesc_bf16(256), id32 = idesc_bf16(MLP_K_OUT);
+    uint32_t mma_count = 0;   // completions of bar_mma so far (parity = count & 1)
+    bool first = true, bad = false;
+
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t row0 = tile * TM;
+        const bool has_next = tile + (int64_t)gridDim.x < tiles;
+        if (!bad) {
+            // ---- features -> ACT (K = 64), two threads per row
+            if (tid < 2 * TM) features_half(a, row0 + (tid >> 1), tid & 1, sm + OFF_ACT, tid >> 1);
+            fence_async_smem();
+            __syncthreads();
+            // ---- layer 1: ACT (128 x 64) x W1 (256 x 64)^T -> TMEM [0, 256)
+            bool okw = true;
+            if (tid == 0) {
+                if (first) okw = mbar_wait(bar_w2, 0);
+                okw = okw && mbar_wait(bar_st, 0);
+                st_pending = !okw;
+                tc_fence_after();
+                if (okw)
+                    for (int s = 0; s < MLP_INP / 16; ++s)
+                        tc_mma(tmem, sdesc(s0 + OFF_ACT + s * 256, 128, MLP_INP * 16),
+                               sdesc(s0 + OFF_STAGE + s * 256, 128, MLP_INP * 16), id256, s > 0);
+                tc_commit(bar_mma);
+            }
+            first = false;
+            bool okm = mbar_wait(bar_mma, mma_count & 1);
+            ++mma_count;
+            bad = __syncthreads_or(!okm || !okw);
+        }
+        if (!bad) {
+            tc_fence_after();
+            if (tid == 0) {   // W1 is free: fetch W3 while the epilogue runs
+                mbar_expect_tx(bar_st, BYTES_W3);
+                bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W3, BYTES_W3, bar_st);
+                st_pending = true;
+            }
+            epi_hidden(tmem, 0, q, lane, 64 * cq, bias_s, sm + OFF_ACT);
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            // ---- layer 2: ACT (128 x 256) x W2 (256 x 256)^T -> TMEM [256, 512)
+            if (tid == 0) {
+                tc_fence_after();
+                for (int s = 0; s < MLP_H / 16; ++s)
+                    tc_mma(tmem + 256, sdesc(s0 + OFF_ACT + s * 256, 128, MLP_H * 16),
+                           sdesc(s0 + OFF_W2 + s * 256, 128, MLP_H * 16), id256, s > 0);
+                tc_commit(bar_mma);
+            }
+            if (warp == 1 && has_next) prefetch_tile(a, row0 + (int64_t)gridDim.x * TM, lane);
+            const bool okm = mbar_wait(bar_mma, mma_count & 1);
+            ++mma_count;
+            bad = __syncthreads_or(!okm);
+        }
+        if (!bad) {
+            tc_fence_after();
+            epi_hidden(tmem, 256, q, lane, 64 * cq, bias_s + MLP_H, sm + OFF_ACT);
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            // ---- layer 3: ACT (128 x 256) x W3 (32 x 256)^T -> TMEM [0, 32)
+            bool okw = true;
+            if (tid == 0) {
+                okw = mbar_wait(bar_st, 1);
+                st_pending = !okw;
+                tc_fence_after();
+                if (okw)
+                    for (int s = 0; s < MLP_H / 16; ++s)
+                        tc_mma(tmem, sdesc(s0 + OFF_ACT + s * 256, 128, MLP_H * 16),
+                               sdesc(s0 + OFF_STAGE + s * 256, 128, MLP_H * 16), id32, s > 0);
+                tc_commit(bar_mma);
+            }
+            const bool okm = mbar_wait(bar_mma, mma_count & 1);
+            ++mma_count;
+            bad = __syncthreads_or(!okm || !okw);
+        }
+        if (!bad) {
+            tc_fence_after();
+            if (tid == 0 && has_next) {   // W3 is free: fetch the next tile's W1
+                mbar_expect_tx(bar_st, BYTES_W1);
+                bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W1, BYTES_W1, bar_st);
+                st_pending = true;
+            }
+            // u = acc + b3: columns [8 cq, 8 cq + 8) of this warp's rows -> Y and
+            // shared memory (ACT is free: layer 3 is done)
+            float *u_s = reinterpret_cast<float *>(sm + OFF_ACT);
+            uint32_t v[8];
+            tc_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(8 * cq), v);
+            tc_wait_ld();
+            const int r = 32 * q + lane;
+            const int64_t i = row0 + r;
+            float y[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) y[e] = __uint_as_float(v[e]) + bias_s[2 * MLP_H + 8 * cq + e];
+            const float4 y0 = make_float4(y[0], y[1], y[2], y[3]);
+            const float4 y1 = make_float4(y[4], y[5], y[6], y[7]);
+            float4 *us = reinterpret_cast<float4 *>(u_s + r * U_STRIDE + 8 * cq);
+            us[0] = y0;
+            us[1] = y1;
+            if (i < a.m) {
+                float4 *dst = reinterpret_cast<float4 *>(a.Y + i * MLP_K_OUT + 8 * cq);
+                dst[0] = y0;
+                dst[1] = y1;
+            }
+            tc_fence_before();
+            __syncthreads();   // TMEM [0, 32) read; u rows complete
+            residual_rows(a, row0, u_s, tid);
+            __syncthreads();   // ACT free before the next tile's features
+        }
+        if (bad && tid < TM) {   // rows of a tile that could not be computed: NaN, fallback
+            const int64_t i = row0 + tid;
+            if (i < a.m) {
+                float4 *dst = reinterpret_cast<float4 *>(a.Y + i * MLP_K_OUT);
+                const float nan = __int_as_float(0x7fc00000);
+                for (int e = 0; e < MLP_K_OUT / 4; ++e) dst[e] = make_float4(nan, nan, nan, nan);
+                if (a.row_rmse) a.row_rmse[i] = nan;
+                if (a.status) a.status[i] = ST_FALLBACK;
+                a.list[atomicAdd(reinterpret_cast<unsigned long long *>(a.count), 1ull)] =
+                    (int32_t)i;
+            }
+        }
+    }
+    if (bad && tid == 0) {
+        atomicExch(a.err, 1);
+        // drain: a weight copy may still be in flight (bounded)
+        if (st_pending) {
+            mbar_wait(bar_st, 0);
+            mbar_wait(bar_st, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tc_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+}  // namespace
+
+size_t mlp_forward_tc_smem() { return SMEM_BYTES; }
+
+cudaError_t prepare_mlp_forward_tc() {
+    return cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SMEM_BYTES);
+}
+
+cudaError_t launch_mlp_forward_tc(const MlpTcArgs &a, int num_sms, cudaStream_t st) {
+    if (a.m <= 0) return cudaSuccess;
+    const int64_t tiles = (a.m + TM - 1) / TM;
+    const int grid = (int)(tiles < num_sms ? tiles : num_sms);
+    k_mlp_forward_tc<<<grid, NTHREADS, SMEM_BYTES, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ocf

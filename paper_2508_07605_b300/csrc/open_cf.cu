@@ -57,6 +57,8 @@ struct open_cf {
     int64_t b_Um = 0, b_Vn = 0;       // padded factor sizes (floats)
     // learned warm start: FP32 master parameters, Adam moments, BF16 weights, scratch
     Buf mlp_th, mlp_g, mlp_m1, mlp_m2, mlp_bf, mlp_map, mlp_t, mlp_cn, mlp_scr, mlp_G;
+    Buf mlp_img, mlp_imap, mlp_err;   // tcgen05 weight images, their map, timeout flag
+    int num_sms = 0;
     bool mlp_ready = false;
     int64_t mlp_Bcap = 0;
     uint64_t generation = 0;  // bumps whenever a workspace moves
@@ -613,7 +615,10 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
     }
     DeviceGuard g(h->device);
     if (prepare_csr_to_csc(CSC_MAX_N) != cudaSuccess || prepare_row_solve() != cudaSuccess ||
-        prepare_row_solve_tc() != cudaSuccess || prepare_batched() != cudaSuccess) {
+        prepare_row_solve_tc() != cudaSuccess || prepare_batched() != cudaSuccess ||
+        prepare_mlp_forward_tc() != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
+            cudaSuccess) {
         cudaGetLastError();
         delete h;
         return OPEN_CF_CUDA_ERROR;
@@ -634,7 +639,8 @@ void open_cf_destroy(open_cf_t *h) {
                        &h->flag, &h->j_ptr, &h->j_idx, &h->j_val, &h->Ub16, &h->b_meta, &h->b_Uw,
                        &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter, &h->mlp_th,
                        &h->mlp_g, &h->mlp_m1, &h->mlp_m2, &h->mlp_bf, &h->mlp_map, &h->mlp_t,
-                       &h->mlp_cn, &h->mlp_scr, &h->mlp_G})
+                       &h->mlp_cn, &h->mlp_scr, &h->mlp_G, &h->mlp_img, &h->mlp_imap,
+                       &h->mlp_err})
             free_buf(*b);
     }
     delete h;
@@ -1039,6 +1045,10 @@ int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
     CK(h, ensure(h, h->mlp_m2, 4 * P_INT));
     CK(h, ensure(h, h->mlp_bf, 2 * BF_TOTAL));
     CK(h, ensure(h, h->mlp_map, 8 * P_INT));
+    CK(h, ensure(h, h->mlp_imap, 8 * P_INT));
+    CK(h, ensure(h, h->mlp_img, 2 * MLP_IMG_TOTAL));
+    CK(h, ensure(h, h->mlp_err, 16));
+    CK(h, cudaMemsetAsync(h->mlp_err.p, 0, 16, st));
     CK(h, ensure(h, h->mlp_t, 16));
     CK(h, ensure(h, h->mlp_G, 4 * MLP_K * MLP_K));
     float *th = (float *)h->mlp_th.p;
@@ -1054,7 +1064,23 @@ int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
     for (int64_t e = 0; e < MLP_H * MLP_H; ++e) map[OFF_W2 + e] = BF_W2 + e;
     for (int64_t e = 0; e < MLP_H * MLP_K; ++e) map[OFF_W3 + e] = BF_W3 + e;
     CK(h, cudaMemcpy(h->mlp_map.p, map.data(), 8 * P_INT, cudaMemcpyHostToDevice));
-    CK(h, launch_to_bf16_map(P_INT, th, (const int64_t *)h->mlp_map.p, h->mlp_bf.p, st));
+    // K-major operand images of the fused forward pass: W_l[in = k][out = n]
+    std::fill(map.begin(), map.end(), -1);
+    auto image = [](int64_t n, int64_t k, int64_t K) {
+        return (n / 8) * (8 * K) + (k / 8) * 64 + (n % 8) * 8 + k % 8;
+    };
+    for (int64_t k = 0; k < MLP_INP; ++k)
+        for (int64_t n = 0; n < MLP_H; ++n)
+            map[OFF_W1 + k * MLP_H + n] = MLP_IMG_W1 + image(n, k, MLP_INP);
+    for (int64_t k = 0; k < MLP_H; ++k)
+        for (int64_t n = 0; n < MLP_H; ++n)
+            map[OFF_W2 + k * MLP_H + n] = MLP_IMG_W2 + image(n, k, MLP_H);
+    for (int64_t k = 0; k < MLP_H; ++k)
+        for (int64_t n = 0; n < MLP_K; ++n)
+            map[OFF_W3 + k * MLP_K + n] = MLP_IMG_W3 + image(n, k, MLP_H);
+    CK(h, cudaMemcpy(h->mlp_imap.p, map.data(), 8 * P_INT, cudaMemcpyHostToDevice));
+    CK(h, launch_to_bf16_map(P_INT, th, (const int64_t *)h->mlp_map.p, h->mlp_bf.p,
+                             (const int64_t *)h->mlp_imap.p, h->mlp_img.p, st));
     // normalised caps of every setting (features), FP32
     const int64_t ns = (int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size();
     if (ns > 0) {
@@ -1151,7 +1177,7 @@ int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *
         }
         return launch_adam(P_INT, th, gr, (float *)h->mlp_m1.p, (float *)h->mlp_m2.p, 0.9f,
                            0.999f, 1e-8f, h->mlp_t.p, (const int64_t *)h->mlp_map.p, h->mlp_bf.p,
-                           st);
+                           (const int64_t *)h->mlp_imap.p, h->mlp_img.p, st);
     });
 }
 
@@ -1166,40 +1192,27 @@ int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
     if (rc) return rc;
     if (m > 0 && !U_out) return fail(h, OPEN_CF_INVALID_ARG, "U_out is NULL");
     if (m == 0) return OPEN_CF_OK;
+    if (reinterpret_cast<uintptr_t>(U_out) % 16)
+        return fail(h, OPEN_CF_INVALID_ARG, "U_out must be 16-byte aligned");
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
-    const int64_t chunk = 65536;
-    rc = mlp_ensure_scratch(h, std::min<int64_t>((m + 63) / 64 * 64, chunk));
-    if (rc) return rc;
-    const int64_t ns = h->n;
-    const float *cn = (const float *)h->mlp_cn.p;
-    for (int64_t r0 = 0; r0 < m; r0 += chunk) {
-        const int64_t mc = std::min(chunk, m - r0);
-        const int Bp = (int)((mc + 63) / 64 * 64);
-        const MlpScratch Sx = mlp_scratch(h, Bp);
-        CK(h, cudaMemsetAsync(Sx.X, 0, 2 * (size_t)Bp * MLP_INP, st));
-        CK(h, launch_mlp_features(mc, nnz, row_ptr + r0, col, val, cn, cn + ns, ns, Sx.X, st));
-        CK(h, mlp_forward(h, Sx, Bp, st));
-        CK(h, cudaMemcpyAsync(U_out + r0 * MLP_K, Sx.Y, 4 * mc * MLP_K, cudaMemcpyDeviceToDevice,
-                              st));
-    }
-    // observed-entry RMSE of the learned factors; rows above the threshold fall back to ALS
-    CK(h, ensure(h, h->part, sizeof(double) * 3 * objective_parts(std::max<int64_t>(m, h->n))));
     CK(h, ensure(h, h->flag, 64));
     CK(h, ensure(h, h->j_idx, sizeof(int32_t) * m));   // fallback row list
-    float *rm = row_rmse;
-    if (!rm) {
-        CK(h, ensure(h, h->csc_val, sizeof(float) * std::max<int64_t>(m, 1)));
-        rm = (float *)h->csc_val.p;
-    }
-    double *Jtmp = (double *)h->flag.p + 1;
-    CK(h, launch_objective<float>(m, nnz, row_ptr, col, val, U_out, MLP_K, MLP_K,
-                                  (const float *)h->V.p, h->n, h->KP, h->cfg.lambda,
-                                  (double *)h->part.p, Jtmp, rm, st));
+    // fused forward pass on the tensor cores (tcgen05), straight into U_out
+    MlpTcArgs ta{};
+    ta.m = m; ta.nnz = nnz; ta.ptr = row_ptr; ta.idx = col; ta.val = val;
+    ta.cnorm = (const float *)h->mlp_cn.p; ta.gnorm = ta.cnorm + h->n; ta.n = h->n;
+    ta.img = h->mlp_img.p;
+    const float *th = (const float *)h->mlp_th.p;
+    ta.b1 = th + OFF_B1; ta.b2 = th + OFF_B2; ta.b3 = th + OFF_B3;
+    ta.Y = U_out; ta.err = (int *)h->mlp_err.p;
+    // the kernel also evaluates each row's observed-entry RMSE and lists the
+    // rows above the threshold; those are re-solved by the ridge fold-in
     int64_t *cnt = (int64_t *)h->flag.p;
+    ta.V = (const float *)h->V.p; ta.threshold = h->cfg.mlp_fallback_threshold;
+    ta.row_rmse = row_rmse; ta.status = status; ta.list = (int32_t *)h->j_idx.p; ta.count = cnt;
     CK(h, cudaMemsetAsync(cnt, 0, sizeof(int64_t), st));
-    CK(h, launch_fallback_rows(m, rm, h->cfg.mlp_fallback_threshold, (int32_t *)h->j_idx.p, cnt,
-                               status, st));
+    CK(h, launch_mlp_forward_tc(ta, h->num_sms, st));
     SolveArgs<float> a{m, nnz, row_ptr, col, val, (const float *)h->V.p, h->n, U_out, MLP_K,
                        MLP_K, status, h->cfg.lambda};
     a.row_map = (const int32_t *)h->j_idx.p;
