@@ -618,7 +618,7 @@ def run_gpu_learned(args):
     V = h.get_V()
     del off
     # training: pool of 2^20 apps, targets = fold-in of their full profiles
-    pool = 1 << 20
+    pool = args.pool
     pc, pv, pt = synth.learned_pool(wl, h, pool)
     rng = np.random.default_rng(0)
     flat0 = np.concatenate([np.asarray(p, np.float32).reshape(-1)
@@ -652,12 +652,13 @@ def run_gpu_learned(args):
             t_samples.append(e0.elapsed_time(e1) / 1e3)
     train_sps = B / statistics.mean(t_samples) if t_samples else None
     del pc, pv, pt
-    # new apps: 2^20, 16 observed settings each; noiseless rows kept for 65,536 of them
-    M = 1 << 20
+    # new apps (2^20 by default), 16 observed settings each; noiseless rows kept
+    # for the first 65,536 of them
+    M = args.rows
     cols, vals = [], []
     clean_eval = None
     for s0 in range(0, M, 65536):
-        noisy, clean, obs = wl.draw_apps(65536)
+        noisy, clean, obs = wl.draw_apps(min(65536, M - s0))
         cols.append(obs.reshape(-1)); vals.append(torch.gather(noisy, 1, obs.to(torch.int64)))
         if clean_eval is None:
             clean_eval = clean
@@ -705,7 +706,7 @@ def run_gpu_learned(args):
     # error against the FP64 oracle on a 10k-row sample, and the oracle's time
     import oracle as orc
     orc.build()
-    sample = np.sort(np.random.default_rng(0).choice(M, 10000, replace=False))
+    sample = np.sort(np.random.default_rng(0).choice(M, min(M, 10000), replace=False))
     sc = col.view(M, S)[torch.as_tensor(sample, device=dev)].cpu().numpy()
     sv = val.view(M, S)[torch.as_tensor(sample, device=dev)].double().cpu().numpy()
     sp = np.arange(0, (len(sample) + 1) * S, S, dtype=np.int64)
@@ -745,7 +746,7 @@ def run_gpu_learned(args):
         "warmup": args.warmup, "ms_per_step": t_learned * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_C4, "m": M, "n": wl.n, "k": K, "s_obs": S,
-                   "train_steps": steps, "batch": B,
+                   "train_steps": steps, "batch": B, "pool": pool,
                    "l2": "inputs (~0.3 GB) and factors exceed L2"},
         "plain_fold_in": {"value": M / t_plain, "unit": "rows/s", "ms": t_plain * 1e3},
         "mlp_only": {"value": M / t_mlp, "unit": "rows/s", "ms": t_mlp * 1e3},
@@ -788,6 +789,8 @@ def main():
                          "c5: 1M x 4096 BF16-Gram fold-in + selection")
     ap.add_argument("--train-steps", type=int, default=30000,
                     help="c4 only: training steps (batch 4096) before the timed completions")
+    ap.add_argument("--pool", type=int, default=1 << 20, help="c4 only: training apps")
+    ap.add_argument("--rows", type=int, default=1 << 20, help="c4 only: new apps completed")
     ap.add_argument("--problems", type=int, default=10000, help="c3 only: number of problems")
     ap.add_argument("--fp32-cholesky", action="store_true",
                     help="c5 only: FP32 instead of FP64 k x k factorisation")
