@@ -142,7 +142,8 @@ struct MlpTcArgs {
     const int64_t *ptr;
     const int32_t *idx;
     const float *val;
-    const float *cnorm, *gnorm;   // normalised caps of every setting
+    const float *ccap, *gcap;     // normalised CPU caps [n_cpu], GPU caps [n_gpu]
+    int32_t n_gpu;                // setting j = c * n_gpu + g
     int64_t n;
     const void *img;              // BF16 weight images
     const float *b1, *b2, *b3;

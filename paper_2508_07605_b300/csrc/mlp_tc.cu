@@ -193,42 +193,54 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// Half h of row r of the tile (global row i) of the BF16 feature image
-// (K = 64): observations 8h .. 8h + 7 -> features 24h .. 24h + 23 (chunks
-// 3h .. 3h + 2); half 1 also writes the zero chunks 6 and 7.
-__device__ __forceinline__ void features_half(const MlpTcArgs &a, int64_t i, int h,
-                                              unsigned char *act, int r) {
-    float x[24];
+// The tile's rows are shared by groups of four lanes (row r = tid / 4, lane
+// g = tid % 4), the same mapping the residual uses: lane g takes the row's
+// observation slots g, g + 4, g + 8, g + 12 (the first 16 in setting order),
+// keeps their indices and values in registers until the residual, and writes
+// their features (c_norm, g_norm, runtime) into the BF16 feature image (K = 64;
+// slot s -> features 3s .. 3s + 2; features 48 .. 63 stay zero).
+struct RowObs {
+    int64_t beg, end;
+    bool ok;
+    int32_t j[4];   // -1: no observation in the slot, or an index out of range
+    float v[4];
+};
+
+__device__ __forceinline__ void features_quad(const MlpTcArgs &a, int64_t i, int r, int g,
+                                              unsigned char *act, RowObs &o) {
+    o.beg = 0;
+    o.end = 0;
+    o.ok = i < a.m && row_bounds(a.ptr, i, a.nnz, o.beg, o.end);
 #pragma unroll
-    for (int f = 0; f < 24; ++f) x[f] = 0.f;
-    int64_t beg = 0, end = 0;
-    if (i < a.m && row_bounds(a.ptr, i, a.nnz, beg, end)) {
-        const int64_t b = beg + 8 * h;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            if (b + t < end) {
-                const int32_t j = __ldg(a.idx + b + t);
-                if (j >= 0 && (int64_t)j < a.n) {
-                    x[3 * t] = __ldg(a.cnorm + j);
-                    x[3 * t + 1] = __ldg(a.gnorm + j);
-                    x[3 * t + 2] = __ldg(a.val + b + t);
-                }
-            }
+    for (int b = 0; b < 4; ++b) {
+        const int64_t t = o.beg + g + 4 * b;
+        o.j[b] = -1;
+        o.v[b] = 0.f;
+        if (o.ok && t < o.end) {
+            const int32_t jj = __ldg(a.idx + t);
+            o.v[b] = __ldg(a.val + t);
+            if (jj >= 0 && (int64_t)jj < a.n) o.j[b] = jj;
         }
     }
     unsigned char *row = act + (r >> 3) * (MLP_INP * 16) + (r & 7) * 16;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const uint4 w = make_uint4(pack_bf16(x[8 * c], x[8 * c + 1]),
-                                   pack_bf16(x[8 * c + 2], x[8 * c + 3]),
-                                   pack_bf16(x[8 * c + 4], x[8 * c + 5]),
-                                   pack_bf16(x[8 * c + 6], x[8 * c + 7]));
-        *reinterpret_cast<uint4 *>(row + (3 * h + c) * 128) = w;
+    for (int b = 0; b < 4; ++b) {
+        const int s = g + 4 * b;
+        float c = 0.f, gg = 0.f, v = 0.f;
+        if (o.j[b] >= 0) {
+            const int32_t ci = o.j[b] / a.n_gpu;
+            c = __ldg(a.ccap + ci);
+            gg = __ldg(a.gcap + (o.j[b] - ci * a.n_gpu));
+            v = o.v[b];
+        }
+        const float x[3] = {c, gg, v};
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int f = 3 * s + e;
+            *reinterpret_cast<bf16 *>(row + (f >> 3) * 128 + (f & 7) * 2) = __float2bfloat16_rn(x[e]);
+        }
     }
-    if (h == 1) {
-        *reinterpret_cast<uint4 *>(row + 6 * 128) = make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4 *>(row + 7 * 128) = make_uint4(0, 0, 0, 0);
-    }
+    if (g < 2) *reinterpret_cast<uint4 *>(row + (6 + g) * 128) = make_uint4(0, 0, 0, 0);
 }
 
 // Hidden-layer epilogue: this warp's 32 rows, columns [c0, c0 + 64) of the
@@ -271,51 +283,87 @@ __device__ __forceinline__ void epi_hidden(uint32_t tmem, uint32_t tacc, int q, 
 // Observed-entry RMSE of the tile's 128 rows under u (shared memory, rows of
 // U_STRIDE floats), one group of four lanes per row: per observation the
 // four lanes read one 128-byte row of V (32 bytes each, coalesced), multiply
-// by their eight components of u and add across the group.  Observations go
-// four at a time (one index and value per lane).  Lane 0 of the group writes
-// the RMSE and the status and, when the row is above the threshold (or its
-// residual is not finite), appends it to the fallback list.
+// by their eight components of u and add across the group.  The first 16
+// observations come from the registers the feature phase filled (lane g holds
+// slots g, g + 4, ...); a row with more observations reads the rest four at a
+// time.  Lane 0 of the group writes the RMSE and the status and, when the row
+// is above the threshold (or its residual is not finite), appends it to the
+// fallback list.
 constexpr int U_STRIDE = 36;   // 16-byte aligned rows, conflict-free float4 access
-__device__ __forceinline__ void residual_rows(const MlpTcArgs &a, int64_t row0, const float *u_s,
-                                              int tid) {
-    const int rr = tid >> 2, gl = tid & 3;
-    const unsigned gmask = 0xFu << ((tid & 31) & ~3);
-    const int64_t i = row0 + rr;
-    int64_t beg = 0, end = 0;
-    const bool ok = i < a.m && row_bounds(a.ptr, i, a.nnz, beg, end);
-    const float4 ua = *reinterpret_cast<const float4 *>(u_s + rr * U_STRIDE + 8 * gl);
-    const float4 ub = *reinterpret_cast<const float4 *>(u_s + rr * U_STRIDE + 8 * gl + 4);
+
+__device__ __forceinline__ float dot8(const float4 &ua, const float4 &ub, const float4 &x0,
+                                      const float4 &x1) {
+    float d = ua.x * x0.x;
+    d = fmaf(ua.y, x0.y, d);
+    d = fmaf(ua.z, x0.z, d);
+    d = fmaf(ua.w, x0.w, d);
+    d = fmaf(ub.x, x1.x, d);
+    d = fmaf(ub.y, x1.y, d);
+    d = fmaf(ub.z, x1.z, d);
+    return fmaf(ub.w, x1.w, d);
+}
+
+__device__ __forceinline__ void residual_quad(const MlpTcArgs &a, int64_t i, const float *u_s,
+                                              int rr, int g, const RowObs &o) {
+    const unsigned gmask = 0xFu << ((threadIdx.x & 31) & ~3);
+    const float4 ua = *reinterpret_cast<const float4 *>(u_s + rr * U_STRIDE + 8 * g);
+    const float4 ub = *reinterpret_cast<const float4 *>(u_s + rr * U_STRIDE + 8 * g + 4);
+    const float4 *V4 = reinterpret_cast<const float4 *>(a.V);
     float sse = 0.f;
-    for (int64_t t0 = beg; t0 < end; t0 += 4) {
-        const int64_t t = t0 + gl;
+    // two slots (eight observations) per round: 16 rows of V in flight per lane
+#pragma unroll
+    for (int bp = 0; bp < 4; bp += 2) {
+        int32_t jq[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) jq[k] = __shfl_sync(gmask, o.j[bp + (k >> 2)], k & 3, 4);
+        float4 x0[8], x1[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            x0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            x1[k] = x0[k];
+            if (jq[k] >= 0) {
+                x0[k] = __ldg(V4 + (int64_t)jq[k] * (MLP_K_OUT / 4) + 2 * g);
+                x1[k] = __ldg(V4 + (int64_t)jq[k] * (MLP_K_OUT / 4) + 2 * g + 1);
+            }
+        }
+#pragma unroll
+        for (int b2 = 0; b2 < 2; ++b2) {
+            float mine = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float d = dot8(ua, ub, x0[4 * b2 + q], x1[4 * b2 + q]);
+                d += __shfl_xor_sync(gmask, d, 2, 4);
+                d += __shfl_xor_sync(gmask, d, 1, 4);
+                if (q == g) mine = d;
+            }
+            if (o.j[bp + b2] >= 0) {
+                const float e = o.v[bp + b2] - mine;
+                sse = fmaf(e, e, sse);
+            }
+        }
+    }
+    for (int64_t t0 = o.beg + 16; t0 < o.end; t0 += 4) {   // group-uniform
+        const int64_t t = t0 + g;
         int32_t j = -1;
         float r = 0.f;
-        if (t < end) {
+        if (t < o.end) {
             j = __ldg(a.idx + t);
             r = __ldg(a.val + t);
             if (j < 0 || (int64_t)j >= a.n) j = -1;
         }
         float mine = 0.f;
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            const int32_t jo = __shfl_sync(gmask, j, o, 4);
+        for (int q = 0; q < 4; ++q) {
+            const int32_t jo = __shfl_sync(gmask, j, q, 4);
             float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
             if (jo >= 0) {
-                const float4 *vr = reinterpret_cast<const float4 *>(a.V + (int64_t)jo * MLP_K_OUT);
-                x0 = __ldg(vr + 2 * gl);
-                x1 = __ldg(vr + 2 * gl + 1);
+                x0 = __ldg(V4 + (int64_t)jo * (MLP_K_OUT / 4) + 2 * g);
+                x1 = __ldg(V4 + (int64_t)jo * (MLP_K_OUT / 4) + 2 * g + 1);
             }
-            float d = ua.x * x0.x;
-            d = fmaf(ua.y, x0.y, d);
-            d = fmaf(ua.z, x0.z, d);
-            d = fmaf(ua.w, x0.w, d);
-            d = fmaf(ub.x, x1.x, d);
-            d = fmaf(ub.y, x1.y, d);
-            d = fmaf(ub.z, x1.z, d);
-            d = fmaf(ub.w, x1.w, d);
+            float d = dot8(ua, ub, x0, x1);
             d += __shfl_xor_sync(gmask, d, 2, 4);
             d += __shfl_xor_sync(gmask, d, 1, 4);
-            if (o == gl) mine = d;
+            if (q == g) mine = d;
         }
         if (j >= 0) {
             const float e = r - mine;
@@ -324,9 +372,9 @@ __device__ __forceinline__ void residual_rows(const MlpTcArgs &a, int64_t row0, 
     }
     sse += __shfl_xor_sync(gmask, sse, 2, 4);
     sse += __shfl_xor_sync(gmask, sse, 1, 4);
-    if (gl == 0 && i < a.m) {
-        const int64_t s = end - beg;
-        const float rmse = (ok && s > 0) ? sqrtf(sse / (float)s) : 0.0f;
+    if (g == 0 && i < a.m) {
+        const int64_t s = o.end - o.beg;
+        const float rmse = (o.ok && s > 0) ? sqrtf(sse / (float)s) : 0.0f;
         if (a.row_rmse) a.row_rmse[i] = rmse;
         const bool fb = !(rmse <= a.threshold);
         if (a.status) a.status[i] = fb ? ST_FALLBACK : ST_OK;
@@ -390,13 +438,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
     const uint32_t id256 = idesc_bf16(256), id32 = idesc_bf16(MLP_K_OUT);
     uint32_t mma_count = 0;   // completions of bar_mma so far (parity = count & 1)
     bool first = true, bad = false;
+    RowObs obs;   // this lane's share of its row, from the feature phase to the residual
 
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int64_t row0 = tile * TM;
         const bool has_next = tile + (int64_t)gridDim.x < tiles;
         if (!bad) {
-            // ---- features -> ACT (K = 64), two threads per row
-            if (tid < 2 * TM) features_half(a, row0 + (tid >> 1), tid & 1, sm + OFF_ACT, tid >> 1);
+            // ---- features -> ACT (K = 64), four lanes per row
+            features_quad(a, row0 + (tid >> 2), tid >> 2, tid & 3, sm + OFF_ACT, obs);
             fence_async_smem();
             __syncthreads();
             // ---- layer 1: ACT (128 x 64) x W1 (256 x 64)^T -> TMEM [0, 256)
@@ -493,7 +542,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
             }
             tc_fence_before();
             __syncthreads();   // TMEM [0, 32) read; u rows complete
-            residual_rows(a, row0, u_s, tid);
+            residual_quad(a, row0 + (tid >> 2), u_s, tid >> 2, tid & 3, obs);
             __syncthreads();   // ACT free before the next tile's features
         }
         if (bad && tid < TM) {   // rows of a tile that could not be computed: NaN, fallback

@@ -1088,15 +1088,19 @@ int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
         const double cmax = *std::max_element(h->cpu_caps.begin(), h->cpu_caps.end());
         const double gmin = *std::min_element(h->gpu_caps.begin(), h->gpu_caps.end());
         const double gmax = *std::max_element(h->gpu_caps.begin(), h->gpu_caps.end());
-        const int ng = (int)h->gpu_caps.size();
-        std::vector<float> cn(2 * ns);
+        const int nc = (int)h->cpu_caps.size(), ng = (int)h->gpu_caps.size();
+        // [c_norm per setting | g_norm per setting | c_norm per CPU cap | g_norm per GPU cap]
+        std::vector<float> cn(2 * ns + nc + ng);
+        auto cnorm = [&](double c) { return (float)(cmax > cmin ? (c - cmin) / (cmax - cmin) : 0.0); };
+        auto gnorm = [&](double g) { return (float)(gmax > gmin ? (g - gmin) / (gmax - gmin) : 0.0); };
         for (int64_t j = 0; j < ns; ++j) {
-            const double c = h->cpu_caps[j / ng], gg = h->gpu_caps[j % ng];
-            cn[j] = (float)(cmax > cmin ? (c - cmin) / (cmax - cmin) : 0.0);
-            cn[ns + j] = (float)(gmax > gmin ? (gg - gmin) / (gmax - gmin) : 0.0);
+            cn[j] = cnorm(h->cpu_caps[j / ng]);
+            cn[ns + j] = gnorm(h->gpu_caps[j % ng]);
         }
-        CK(h, ensure(h, h->mlp_cn, 4 * 2 * ns));
-        CK(h, cudaMemcpy(h->mlp_cn.p, cn.data(), 4 * 2 * ns, cudaMemcpyHostToDevice));
+        for (int c = 0; c < nc; ++c) cn[2 * ns + c] = cnorm(h->cpu_caps[c]);
+        for (int g = 0; g < ng; ++g) cn[2 * ns + nc + g] = gnorm(h->gpu_caps[g]);
+        CK(h, ensure(h, h->mlp_cn, 4 * cn.size()));
+        CK(h, cudaMemcpy(h->mlp_cn.p, cn.data(), 4 * cn.size(), cudaMemcpyHostToDevice));
     }
     CK(h, cudaStreamSynchronize(st));
     h->mlp_ready = true;
@@ -1201,7 +1205,10 @@ int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
     // fused forward pass on the tensor cores (tcgen05), straight into U_out
     MlpTcArgs ta{};
     ta.m = m; ta.nnz = nnz; ta.ptr = row_ptr; ta.idx = col; ta.val = val;
-    ta.cnorm = (const float *)h->mlp_cn.p; ta.gnorm = ta.cnorm + h->n; ta.n = h->n;
+    ta.ccap = (const float *)h->mlp_cn.p + 2 * h->n;
+    ta.gcap = ta.ccap + h->cpu_caps.size();
+    ta.n_gpu = (int32_t)h->gpu_caps.size();
+    ta.n = h->n;
     ta.img = h->mlp_img.p;
     const float *th = (const float *)h->mlp_th.p;
     ta.b1 = th + OFF_B1; ta.b2 = th + OFF_B2; ta.b3 = th + OFF_B3;

@@ -63,7 +63,9 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_by
                  "r"(src_bytes));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
 
 // BF16 operands: m16n8k16 MMA with FP32 accumulation, fragments of the staged
 // row-major tile read transposed by ldmatrix.
@@ -89,14 +91,20 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
-template <int KP, typename TC, bool BF> struct alignas(16) TcSmem {
+// Per-warp shared memory.  The staging buffers (NST stages of 32 factor
+// rows) are dead once the warp's Gram is in registers, so the Gram / factor
+// area of the solve phase overlays them: a warp needs max(staging, solve),
+// not the sum, which keeps 16 warps per SM resident for KP = 32.
+template <int KP, typename TC, bool BF, int NST> struct alignas(16) TcSmem {
     static constexpr int SPW = 32 / KP;
     // Staged rows padded to KP+8 elements (conflict-free fragment loads,
     // 16-byte aligned rows).  FP32: one tile of 32 rows per buffer.  BF16: the
     // hi and lo halves of each split row go to two tiles of 32 BF16 rows.
     static constexpr int ROWB = (BF ? 2 : 4) * (KP + 8);
-    alignas(16) unsigned char stage[2][BF ? 2 : 1][32][ROWB];   // double-buffered
-    float sr[2][32];
+    struct alignas(16) Stage {
+        alignas(16) unsigned char stage[NST][BF ? 2 : 1][32][ROWB];
+        float sr[NST][32];
+    };
     struct alignas(16) Seg {
         union {
             float G[KP][KP + 1];   // Gram (lower triangle), then
@@ -104,8 +112,17 @@ template <int KP, typename TC, bool BF> struct alignas(16) TcSmem {
         };
         float b[KP];
         TC col[2][KP];
-    } seg[SPW];
+    };
+    union {
+        Stage ld;
+        Seg seg[SPW];
+    };
 };
+
+// Pipeline depth (items in flight).  Measured on the 4096 x 1024 fit: 3 or 4
+// stages do not shorten the U-half (its items wait on the tensor-core chain,
+// not on the copies) and cost occupancy, so every configuration uses 2.
+template <int KP, int WPS> constexpr int tc_stages() { return 2; }
 
 template <int KP> struct Blocks {
     static constexpr int MB = KP / 16;
@@ -122,7 +139,8 @@ k_row_solve_tc(SolveArgs<float> a) {
     constexpr int SPW = (WPS == 1) ? 32 / KP : 1;   // systems per warp
     constexpr int MB = Blocks<KP>::MB;
     constexpr int NBLK = Blocks<KP>::NBLK;
-    using WS = TcSmem<KP, TC, BF>;
+    constexpr int NST = tc_stages<KP, WPS>();
+    using WS = TcSmem<KP, TC, BF, NST>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WS *smem = reinterpret_cast<WS *>(smem_raw);
 
@@ -210,8 +228,8 @@ k_row_solve_tc(SolveArgs<float> a) {
                 constexpr int NCP = 2 * KP / 16;
 #pragma unroll
                 for (int e = 0; e < NCP; ++e) {
-                    cp_async16(&W.stage[buf][0][lane][16 * e], src + 16 * e, v ? 16 : 0);
-                    cp_async16(&W.stage[buf][1][lane][16 * e], src + 2 * KP + 16 * e, v ? 16 : 0);
+                    cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, v ? 16 : 0);
+                    cp_async16(&W.ld.stage[buf][1][lane][16 * e], src + 2 * KP + 16 * e, v ? 16 : 0);
                 }
             } else {
                 const unsigned char *src =
@@ -219,9 +237,9 @@ k_row_solve_tc(SolveArgs<float> a) {
                 constexpr int NCP = 4 * KP / 16;
 #pragma unroll
                 for (int e = 0; e < NCP; ++e)
-                    cp_async16(&W.stage[buf][0][lane][16 * e], src + 16 * e, v ? 16 : 0);
+                    cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, v ? 16 : 0);
             }
-            cp_async4(&W.sr[buf][lane], v ? (const void *)(a.val + bg + tt) : (const void *)a.val,
+            cp_async4(&W.ld.sr[buf][lane], v ? (const void *)(a.val + bg + tt) : (const void *)a.val,
                       v ? 4 : 0);
         };
 
@@ -238,21 +256,36 @@ k_row_solve_tc(SolveArgs<float> a) {
                 for (int e = 0; e < 4; ++e) dr[si][mb][e] = 0.0f;
         }
         if (nitems > 0) {
+            // NST - 1 items in flight ahead of the one on the tensor cores; the
+            // column indices of the next NST - 1 items wait in registers (jr).
+            int32_t jr[NST - 1];
             issue(0, load_idx(0), 0);
             cp_async_commit();
-            int32_t jn = nitems > 1 ? load_idx(1) : 0;
-            for (int w = 0; w < nitems; ++w) {
-                if (w + 1 < nitems) issue(w + 1, jn, (w + 1) & 1);
+#pragma unroll
+            for (int t = 0; t < NST - 1; ++t) jr[t] = (1 + t < nitems) ? load_idx(1 + t) : 0;
+#pragma unroll
+            for (int p = 1; p < NST - 1; ++p) {
+                if (p < nitems) issue(p, jr[0], p);
                 cp_async_commit();
-                if (w + 2 < nitems) jn = load_idx(w + 2);
-                cp_async_wait1();
+#pragma unroll
+                for (int t = 0; t < NST - 2; ++t) jr[t] = jr[t + 1];
+                jr[NST - 2] = (p + NST - 1 < nitems) ? load_idx(p + NST - 1) : 0;
+            }
+            for (int w = 0; w < nitems; ++w) {
+                const int wn = w + NST - 1;
+                if (wn < nitems) issue(wn, jr[0], wn % NST);
+                cp_async_commit();
+#pragma unroll
+                for (int t = 0; t < NST - 2; ++t) jr[t] = jr[t + 1];
+                jr[NST - 2] = (wn + NST - 1 < nitems) ? load_idx(wn + NST - 1) : 0;
+                cp_async_wait<NST - 1>();
                 __syncwarp();
                 int si; int64_t c0;
                 item(w, si, c0);
                 int64_t ss = 0;
 #pragma unroll
                 for (int t = 0; t < SPW; ++t) if (t == si) ss = s_s[t];
-                const int buf = w & 1;
+                const int buf = w % NST;
                 const int cnt = (int)min((int64_t)32, ss - c0);
                 if constexpr (BF) {
                     // 16 observations per MMA step; fragments of the hi (H) and lo (L)
@@ -260,9 +293,9 @@ k_row_solve_tc(SolveArgs<float> a) {
                     // S^T r ~ H^T r_h + H^T r_l + L^T r_h: ~16-bit operands.
                     const int nks = (cnt + 15) / 16;
                     const __nv_bfloat16 *sH =
-                        reinterpret_cast<const __nv_bfloat16 *>(&W.stage[buf][0][0][0]);
+                        reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][0][0][0]);
                     const __nv_bfloat16 *sL =
-                        reinterpret_cast<const __nv_bfloat16 *>(&W.stage[buf][1][0][0]);
+                        reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][1][0][0]);
                     constexpr int LDE = WS::ROWB / 2;
                     const int mi = lane >> 3, rr = lane & 7;
                     for (int ks = 0; ks < nks; ++ks) {
@@ -276,10 +309,10 @@ k_row_solve_tc(SolveArgs<float> a) {
                         }
                         float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
                         if (gid == 0) {
-                            r0 = W.sr[buf][k0 + 2 * tid4];
-                            r1 = W.sr[buf][k0 + 2 * tid4 + 1];
-                            r2 = W.sr[buf][k0 + 2 * tid4 + 8];
-                            r3 = W.sr[buf][k0 + 2 * tid4 + 9];
+                            r0 = W.ld.sr[buf][k0 + 2 * tid4];
+                            r1 = W.ld.sr[buf][k0 + 2 * tid4 + 1];
+                            r2 = W.ld.sr[buf][k0 + 2 * tid4 + 8];
+                            r3 = W.ld.sr[buf][k0 + 2 * tid4 + 9];
                         }
                         const float h0 = __bfloat162float(__float2bfloat16_rn(r0));
                         const float h1 = __bfloat162float(__float2bfloat16_rn(r1));
@@ -309,7 +342,7 @@ k_row_solve_tc(SolveArgs<float> a) {
                     }
                 } else {
                 const int nks = (cnt + 7) / 8;
-                const float *stf = reinterpret_cast<const float *>(&W.stage[buf][0][0][0]);
+                const float *stf = reinterpret_cast<const float *>(&W.ld.stage[buf][0][0][0]);
                 constexpr int LDF = WS::ROWB / 4;
                 for (int ks = 0; ks < nks; ++ks) {
                     const int k0 = ks * 8;
@@ -325,8 +358,8 @@ k_row_solve_tc(SolveArgs<float> a) {
                                    al[mb][3]);
                     }
                     uint32_t rh0, rl0, rh1, rl1;
-                    split_tf32(gid == 0 ? W.sr[buf][k0 + tid4] : 0.0f, rh0, rl0);
-                    split_tf32(gid == 0 ? W.sr[buf][k0 + tid4 + 4] : 0.0f, rh1, rl1);
+                    split_tf32(gid == 0 ? W.ld.sr[buf][k0 + tid4] : 0.0f, rh0, rl0);
+                    split_tf32(gid == 0 ? W.ld.sr[buf][k0 + tid4 + 4] : 0.0f, rh1, rl1);
 #pragma unroll
                     for (int sx = 0; sx < SPW; ++sx) {
                         if (sx != si) continue;   // warp-uniform: accumulators stay in registers
@@ -349,9 +382,11 @@ k_row_solve_tc(SolveArgs<float> a) {
                     }
                 }
                 }
-                __syncwarp();   // this buffer is refilled two items later
+                __syncwarp();   // this buffer is refilled NST items later
             }
         }
+        cp_async_wait<0>();   // nothing in flight before the solve area overlays the stages
+        __syncwarp();
         // fragments -> shared Gram (lower-triangle blocks) and RHS
 #pragma unroll
         for (int si = 0; si < SPW; ++si) {
@@ -501,7 +536,7 @@ k_row_solve_tc(SolveArgs<float> a) {
 
 template <int KP, typename TC, int WPS, bool BF> static size_t tc_smem_bytes() {
     constexpr int WARPS = (WPS == 1) ? ((sizeof(TC) == 8 && KP == 32) ? 4 : 8) : WPS;
-    return sizeof(TcSmem<KP, TC, BF>) * WARPS;
+    return sizeof(TcSmem<KP, TC, BF, tc_stages<KP, WPS>()>) * WARPS;
 }
 
 template <int KP, typename TC, int WPS, bool BF> static cudaError_t tc_attr() {
