@@ -152,7 +152,12 @@ int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
  * The selection is evaluated in FP32 in exactly that operation order.
  * baseline_setting = -1 selects (max CPU cap, max GPU cap).  A row whose
  * baseline runtime is not > 0 gets best = -1 and saving = 0.  Needs a cap grid
- * when best or saving is requested. */
+ * when best or saving is requested.
+ * Precision: FP32 / FP64 modes form T with FMA chains in the handle's type.
+ * OPEN_CF_BF16_GRAM with 16 < k <= 32 forms T on the tensor cores from split
+ * BF16 copies of U and V (hi + lo, FP32 accumulation; predicted runtimes
+ * within ~2^-16 relative of FP32); the selection is then exact on that T,
+ * the values T_out receives. */
 int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t *best,
                     float *saving, float gamma, int32_t baseline_setting, void *stream);
 

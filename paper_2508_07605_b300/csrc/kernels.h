@@ -130,6 +130,32 @@ cudaError_t launch_fallback_rows(int64_t m, const float *rmse, float thr, int32_
 cudaError_t launch_fallback_mark(int64_t m, const int32_t *list, const int64_t *count,
                                  int32_t *status, cudaStream_t st);
 
+// Reconstruction on the tensor cores fused with Algorithm 2 (predict_tc.cu):
+// BF16-Gram precision mode, KP = 32.  Vimg: split BF16 operand images of V in
+// chunks of 256 settings (launch_v_image; predict_tc_image_bytes(n) bytes).
+constexpr int64_t PREDICT_TC_CG_MAX = 16384;   // c + g table kept in shared memory up to here
+struct PredictTcArgs {
+    int64_t m, n;
+    const float *U;       // m rows of k floats, stride ldu
+    int64_t ldu;
+    int k;
+    const void *Vimg;
+    const float *cg;      // n: c_j + g_j
+    const float *cg_pad;  // the same, zero-padded to whole chunks of 256 (used when n > PREDICT_TC_CG_MAX)
+    int64_t base;
+    float Ebase, gamma;
+    bool select;          // run Algorithm 2
+    float *T;             // m x n or null
+    bool t_vec;           // T 16-byte aligned and n % 4 == 0
+    int32_t *best;
+    float *saving;
+    int *err;
+};
+size_t predict_tc_image_bytes(int64_t n);
+cudaError_t prepare_predict_tc();
+cudaError_t launch_v_image(const float *V, int64_t n, void *img, cudaStream_t st);
+cudaError_t launch_predict_select_tc(const PredictTcArgs &a, int num_sms, cudaStream_t st);
+
 // Fused tcgen05 forward pass (mlp_tc.cu).  img holds the BF16 weight images
 // W2 | W1 | W3 (element offsets below), each an N x K K-major operand image:
 // element (n, k) at (n / 8) * 8K + (k / 8) * 64 + (n % 8) * 8 + k % 8.

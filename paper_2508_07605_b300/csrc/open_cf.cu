@@ -58,6 +58,7 @@ struct open_cf {
     // learned warm start: FP32 master parameters, Adam moments, BF16 weights, scratch
     Buf mlp_th, mlp_g, mlp_m1, mlp_m2, mlp_bf, mlp_map, mlp_t, mlp_cn, mlp_scr, mlp_G;
     Buf mlp_img, mlp_imap, mlp_err;   // tcgen05 weight images, their map, timeout flag
+    Buf vimg, pt_err;                 // split BF16 operand images of V, timeout flag (predict)
     int num_sms = 0;
     bool mlp_ready = false;
     int64_t mlp_Bcap = 0;
@@ -616,7 +617,7 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
     DeviceGuard g(h->device);
     if (prepare_csr_to_csc(CSC_MAX_N) != cudaSuccess || prepare_row_solve() != cudaSuccess ||
         prepare_row_solve_tc() != cudaSuccess || prepare_batched() != cudaSuccess ||
-        prepare_mlp_forward_tc() != cudaSuccess ||
+        prepare_mlp_forward_tc() != cudaSuccess || prepare_predict_tc() != cudaSuccess ||
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
             cudaSuccess) {
         cudaGetLastError();
@@ -640,7 +641,7 @@ void open_cf_destroy(open_cf_t *h) {
                        &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter, &h->mlp_th,
                        &h->mlp_g, &h->mlp_m1, &h->mlp_m2, &h->mlp_bf, &h->mlp_map, &h->mlp_t,
                        &h->mlp_cn, &h->mlp_scr, &h->mlp_G, &h->mlp_img, &h->mlp_imap,
-                       &h->mlp_err})
+                       &h->mlp_err, &h->vimg, &h->pt_err})
             free_buf(*b);
     }
     delete h;
@@ -844,6 +845,25 @@ int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t
                               sel ? (float *)h->cg.p : nullptr, base, Eb, gamma,
                               (double *)T_out, best, saving};
         CK(h, launch_predict_select<double>(a, S(stream)));
+    } else if (h->cfg.precision == OPEN_CF_BF16_GRAM && h->KP == 32 &&
+               h->n <= PREDICT_TC_CG_MAX) {
+        // tensor cores: split-BF16 U V^T in TMEM, Algorithm 2 in the epilogue
+        if (m == 0) return OPEN_CF_OK;
+        cudaStream_t st = S(stream);
+        if (!h->pt_err.p) {
+            CK(h, ensure(h, h->pt_err, 16));
+            CK(h, cudaMemsetAsync(h->pt_err.p, 0, 16, st));
+        }
+        CK(h, ensure(h, h->vimg, predict_tc_image_bytes(h->n)));
+        CK(h, launch_v_image((const float *)h->V.p, h->n, h->vimg.p, st));
+        PredictTcArgs a{};
+        a.m = m; a.n = h->n; a.U = as<float>(U); a.ldu = h->k; a.k = h->k;
+        a.Vimg = h->vimg.p; a.cg = sel ? (const float *)h->cg.p : nullptr;
+        a.base = sel ? base : 0; a.Ebase = Eb; a.gamma = gamma; a.select = sel;
+        a.T = (float *)T_out;
+        a.t_vec = T_out && (reinterpret_cast<uintptr_t>(T_out) % 16 == 0) && (h->n % 4 == 0);
+        a.best = best; a.saving = saving; a.err = (int *)h->pt_err.p;
+        CK(h, launch_predict_select_tc(a, h->num_sms, st));
     } else {
         PredictArgs<float> a{m, h->n, h->KP, h->k, as<float>(U), h->k, (float *)h->V.p,
                              sel ? (float *)h->cg.p : nullptr, base, Eb, gamma, (float *)T_out,

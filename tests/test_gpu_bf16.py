@@ -106,3 +106,50 @@ def test_bf16_large_foldin_sampled(orc):
     err = _pred_err(host(U)[rows], Uref, V)
     ok = np.diff(np.array(sp)) > 0
     assert err[ok].max() <= TOL_T, (err[ok].max(), np.median(err[ok]))
+
+
+def _pred_inputs(rng, m, n, k):
+    U = rounded(rng.standard_normal((m, k)) * 0.3, torch.float32)
+    V = rounded(rng.standard_normal((n, k)) * 0.3, torch.float32)
+    U[:, 0] = np.abs(U[:, 0]) + 1.5          # most predicted runtimes positive
+    V[:, 0] = np.abs(V[:, 0]) + 0.5
+    return U, V
+
+
+@pytest.mark.parametrize("m,n_cpu,n_gpu,baseline", [
+    (1, 64, 64, -1),                # one row, 16 chunks of 256 settings
+    (300, 20, 50, -1),              # ragged last chunk (1000 settings)
+    (148 * 128 + 77, 16, 64, 700),  # more tiles than SMs, a ragged tile; baseline in chunk 2
+    (517, 8, 15, 3),                # fewer settings than one chunk
+])
+@pytest.mark.parametrize("gamma", [0.0, 0.1])
+def test_bf16_predict_select_tensor_cores(orc, m, n_cpu, n_gpu, baseline, gamma):
+    """k = 32 in BF16-Gram mode: T = U V^T from split BF16 operands on the
+    tensor cores.  T against the FP64 oracle within the BF16 gate; the
+    selection bit for bit equal to the oracle's FP32 Algorithm 2 on the T the
+    kernel wrote; the same decisions without the dense output."""
+    rng = np.random.default_rng(m + n_cpu)
+    k = 32
+    n = n_cpu * n_gpu
+    U, V = _pred_inputs(rng, m, n, k)
+    if m > 5:
+        U[5] = 0.0                          # a row whose baseline runtime is 0
+    cpu, gpu = synth.cap_grid(n_cpu, n_gpu)
+    h = ocf.OpenCF(k=k, lam=0.05, precision="bf16_gram", cpu_caps=cpu, gpu_caps=gpu)
+    h.set_V(dev(V, torch.float32))
+    T, best, sav = h.predict(dev(U, torch.float32), gamma=gamma, baseline=baseline)
+    _, best2, sav2 = h.predict(dev(U, torch.float32), gamma=gamma, baseline=baseline,
+                               want_T=False)
+    torch.cuda.synchronize()
+    Tg = host(T).astype(np.float64)
+    Tr = orc.predict(U, V)
+    ok = np.linalg.norm(Tr, axis=1) > 0
+    err = np.linalg.norm(Tg - Tr, axis=1)[ok] / np.linalg.norm(Tr, axis=1)[ok]
+    assert err.max() <= 1e-4, err.max()   # split BF16: ~2^-16 relative, well inside 2e-3
+    b_or, s_or = orc.select_f32(host(T).astype(np.float32), cpu, gpu, gamma,
+                                baseline if baseline >= 0 else -1)
+    assert np.array_equal(host(best), b_or)
+    assert np.array_equal(host(sav), s_or)
+    assert torch.equal(best, best2) and torch.equal(sav, sav2)
+    if m > 5:
+        assert host(best)[5] == -1
