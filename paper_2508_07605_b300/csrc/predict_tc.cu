@@ -8,18 +8,18 @@
 // The selection is then exact in FP32 on the T the kernel produces (the
 // value it writes when the dense matrix is requested).
 //
-// One persistent CTA per SM, 10 warps with fixed roles:
-//   * warp 8 streams the settings in chunks of 256 (hi and lo operand images
+// One persistent CTA per SM, 18 warps with fixed roles:
+//   * warp 16 streams the settings in chunks of 256 (hi and lo operand images
 //     of V, 32 KB) into a two-stage shared ring with cp.async.bulk;
-//   * warp 9 owns the tensor memory (512 columns: two 256-column
+//   * warp 17 owns the tensor memory (512 columns: two 256-column
 //     accumulators) and issues, per chunk, six tcgen05.mma (M = 128 rows of
 //     U, N = 256 settings, K = 16) into the free accumulator, then commits
 //     to the chunk's "stage free" and "accumulator full" mbarriers;
-//   * warps 0..7 read an accumulator (warp w: TMEM lanes 32 (w mod 4) ..,
-//     128 of the 256 columns, 32 at a time), release it, and run the screened
+//   * warps 0..15 read an accumulator (warp w: TMEM lanes 32 (w mod 4) ..,
+//     64 of the 256 columns, 16 at a time), release it, and run the screened
 //     Algorithm 2 on their settings of their row, one thread per row; the
 //     chunk holding the baseline setting goes first so that t_b is known; the
-//     two column halves of a row are merged at the end of the tile.
+//     four column quarters of a row are merged at the end of the tile.
 // Accumulator j of chunk g is reused by chunk g + 2, so the tensor cores fill
 // one accumulator while the epilogue drains the other.
 //
@@ -37,7 +37,8 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128, CN = 256, KPT = 32;
-constexpr int NEPI = 8;                        // epilogue warps
+constexpr int NEPI = 16;                       // epilogue warps
+constexpr int GS = 16;                         // settings per TMEM load and screening group
 constexpr int NCQ = NEPI / 4;                  // column groups (warps per TMEM lane quarter)
 constexpr int CPW = CN / NCQ;                  // settings per epilogue warp and chunk
 constexpr int PRODUCER = NEPI, ISSUER = NEPI + 1;
@@ -65,20 +66,20 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 // registers.
 // The lanes of a warp hold different rows, so an exact evaluation taken by
 // one lane is paid by all: the screen therefore tracks the smallest estimate
-// of each group of 32 settings together with its element, evaluates that
+// of each group of GS settings together with its element, evaluates that
 // element exactly on every lane at once, and leaves to a divergent second pass
 // only the rare elements that come within the screening margin of it.
-__device__ __forceinline__ void store32(const uint32_t (&v)[32], float *trow, int64_t j0,
+__device__ __forceinline__ void store16(const uint32_t (&v)[GS], float *trow, int64_t j0,
                                         int64_t n, bool vec) {
-    if (vec && j0 + 32 <= n) {
+    if (vec && j0 + GS <= n) {
 #pragma unroll
-        for (int e = 0; e < 32; e += 4)
+        for (int e = 0; e < GS; e += 4)
             *reinterpret_cast<float4 *>(trow + j0 + e) =
                 make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
                             __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
     } else {
 #pragma unroll
-        for (int e = 0; e < 32; ++e)
+        for (int e = 0; e < GS; ++e)
             if (j0 + e < n) trow[j0 + e] = __uint_as_float(v[e]);
     }
 }
@@ -226,64 +227,72 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                     named_sync(BAR_EPI, NEPI * 32);
                     if (a.select) rc = alg2_row(tb_s[r], a.gamma);
                 }
-                // groups of 32 settings: one TMEM load in registers at a time
+                // groups of GS settings: one TMEM load in registers at a time
 #pragma unroll 1
-                for (int hh = 0; hh < CPW / 32; ++hh) {
-                    uint32_t v[32];
-                    tc_ld32(ta + (uint32_t)(32 * hh), v);
+                for (int hh = 0; hh < CPW / GS; ++hh) {
+                    uint32_t v[GS];
+                    tc_ld16(ta + (uint32_t)(GS * hh), v);
                     tc_wait_ld();
-                    if (hh == CPW / 32 - 1) {   // all read: the accumulator is free
+                    if (hh == CPW / GS - 1) {   // all read: the accumulator is free
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(aempty(ab));
                     }
-                    const int64_t j0 = (int64_t)chunk * CN + CPW * cq + 32 * hh;
-                    const int nv = (int)(a.n - j0 < 32 ? a.n - j0 : 32);   // settings in range
-                    if (a.T && i < a.m) store32(v, a.T + i * a.n, j0, a.n, a.t_vec);
+                    const int64_t j0 = (int64_t)chunk * CN + CPW * cq + GS * hh;
+                    const int nv = (int)(a.n - j0 < GS ? a.n - j0 : GS);   // settings in range
+                    if (a.T && i < a.m) store16(v, a.T + i * a.n, j0, a.n, a.t_vec);
                     if (a.select) {
-                        // c + g of the group's 32 settings (padded with zeros past n)
-                        float cgv[32];
+                        // c + g of the group's settings (padded with zeros past n)
+                        float cgv[GS];
                         const float4 *cg4 = reinterpret_cast<const float4 *>(
                             cg_smem ? (const float *)cg_s + j0 : a.cg_pad + j0);
 #pragma unroll
-                        for (int e4 = 0; e4 < 8; ++e4) {
+                        for (int e4 = 0; e4 < GS / 4; ++e4) {
                             const float4 x = cg4[e4];
                             cgv[4 * e4] = x.x;
                             cgv[4 * e4 + 1] = x.y;
                             cgv[4 * e4 + 2] = x.z;
                             cgv[4 * e4 + 3] = x.w;
                         }
-                        // pass 1: smallest estimate, its element, t and c (branch-free)
+                        // pass 1 (branch-free): the smallest estimate with its element and
+                        // t, and the second smallest.  Validity 0 < t <= t* is one unsigned
+                        // compare on the bit patterns (positive floats order like their
+                        // bits; zero, negatives and NaN fall outside), tsb = 0 for a row
+                        // without a valid baseline.
                         const float inf = __int_as_float(0x7f800000);
-                        float me = inf, mt = 0.0f, mc = 0.0f;
+                        const uint32_t tsb = rc.tstar > 0.0f ? __float_as_uint(rc.tstar) : 0u;
+                        float me = inf, me2 = inf, mt = 0.0f;
                         int mi = -1;
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const float t = e < nv ? __uint_as_float(v[e]) : -1.0f;
-                            const bool ok = t > 0.0f && t <= rc.tstar;
-                            const float est = ok ? __fmul_rn(__fmul_rn(cgv[e], t), rc.rtb) : inf;
-                            const bool lt = est < me;
+                        for (int e = 0; e < GS; ++e) {
+                            const uint32_t tb = e < nv ? v[e] : 0u;
+                            const bool ok = (tb - 1u) < tsb;
+                            const float t = __uint_as_float(tb);
+                            const float est = __fmul_rn(__fmul_rn(cgv[e], t), rc.rtb);
+                            const bool lt = ok && est < me;
+                            me2 = lt ? me : (ok ? fminf(me2, est) : me2);
                             me = lt ? est : me;
                             mt = lt ? t : mt;
-                            mc = lt ? cgv[e] : mc;
                             mi = lt ? e : mi;
                         }
                         if (mi >= 0) {   // some valid setting in this group
                             float bound = alg2_bound(me, a.Ebase);
                             if (best.j >= 0) bound = fminf(bound, best.Ethr);
                             if (me <= bound) {
+                                const float mc = cg_smem ? cg_s[j0 + mi] : a.cg_pad[j0 + mi];
                                 alg2_exact(best, rc, mt, mc, a.Ebase, (int32_t)(j0 + mi));
                                 bound = fminf(bound, best.Ethr);
                             }
-                            // pass 2: the rare settings within the screening margin
+                            // pass 2, only when another setting is within the margin (rare)
+                            if (me2 <= bound) {
 #pragma unroll
-                            for (int e = 0; e < 32; ++e) {
-                                const float t = e < nv ? __uint_as_float(v[e]) : -1.0f;
-                                const bool ok = t > 0.0f && t <= rc.tstar;
-                                const float est =
-                                    ok ? __fmul_rn(__fmul_rn(cgv[e], t), rc.rtb) : inf;
-                                if (est <= bound && e != mi)
-                                    exact_call(best, rc, t, cgv[e], a.Ebase, (int32_t)(j0 + e));
+                                for (int e = 0; e < GS; ++e) {
+                                    const uint32_t tb = e < nv ? v[e] : 0u;
+                                    const float t = __uint_as_float(tb);
+                                    const float est = __fmul_rn(__fmul_rn(cgv[e], t), rc.rtb);
+                                    if ((tb - 1u) < tsb && est <= bound && e != mi)
+                                        exact_call(best, rc, t, cgv[e], a.Ebase, (int32_t)(j0 + e));
+                                }
                             }
                         }
                     }
