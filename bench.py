@@ -431,6 +431,8 @@ def run_gpu_large(args):
     rel = np.linalg.norm(Tg - Tr, axis=1) / np.maximum(np.linalg.norm(Tr, axis=1), 1e-30)
     # roofline of the fold-in kernel: algorithmic FLOPs of the solves
     k = prob.k
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16_peak = float(peaks.get("bf16_tflops", 1745.0))
     fl = nnz * (k * (k + 1) + 2 * k) + prob.m * (k ** 3 / 3.0 + 2 * k * k)
     line = {
         "metric": "ALS row-solves/s", "value": prob.m / step_s, "unit": "row-solves/s",
@@ -450,6 +452,14 @@ def run_gpu_large(args):
                      "frac": fl / t_fold / 1e12 / fp32_alu_peak_tflops(2032.0),
                      "hbm_bytes_algorithmic": int(nnz * 8 + (prob.m + 1) * 8 + prob.m * k * 4),
                      "hbm_gbs_achieved": (nnz * 8 + (prob.m + 1) * 8 + prob.m * k * 4) / t_fold / 1e9},
+        "predict_roofline": {"kernel": "k_predict_select_tc (split-BF16 U V^T on tcgen05 + "
+                                       "Algorithm 2 from TMEM)",
+                             "bound": "alu (selection epilogue)",
+                             "tensor_achieved": 2.0 * prob.m * prob.n * k / t_pred / 1e12,
+                             "tensor_peak": bf16_peak, "unit": "TFLOP/s",
+                             "tensor_frac": 2.0 * prob.m * prob.n * k / t_pred / 1e12 / bf16_peak,
+                             "note": "algorithmic 2mnk; the split form issues 3x that on the "
+                                     "tensor pipe"},
         "cpu_baseline": {"value": len(rows) / t_orc, "unit": "row-solves/s",
                          "cores": orc.num_threads(), "kind": "oracle",
                          "sample": "FP64 fold-in of the 10k sampled rows"},
