@@ -88,6 +88,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// Programmatic dependent launch: a half-step lets the next one launch as soon
+// as all of its CTAs are running, and waits for its predecessor only before
+// the first access to data a predecessor writes (the other factor, the
+// compacted row list).  The CSR / CSC arrays read before the wait are never
+// written by a preceding half-step.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
@@ -153,6 +163,8 @@ k_row_solve_tc(SolveArgs<float> a) {
                                     : (int64_t)blockIdx.x;
     const int64_t sys_stride = (WPS == 1) ? (int64_t)gridDim.x * WARPS * SPW
                                           : (int64_t)gridDim.x;
+    pdl_trigger();
+    if (a.m_dev || a.row_map) pdl_wait();         // the list comes from the preceding kernel
     const int64_t M = a.m_dev ? *a.m_dev : a.m;   // systems (a device count for compacted lists)
 
     for (int64_t base = sys0; base < M; base += sys_stride) {
@@ -255,6 +267,7 @@ k_row_solve_tc(SolveArgs<float> a) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) dr[si][mb][e] = 0.0f;
         }
+        pdl_wait();   // from here on the other factor is read
         if (nitems > 0) {
             // NST - 1 items in flight ahead of the one on the tensor cores; the
             // column indices of the next NST - 1 items wait in registers (jr).
@@ -565,22 +578,36 @@ cudaError_t prepare_row_solve_tc() {
 
 constexpr int64_t LONG_ROW_TC = 96;   // mean observations per row that warrant 4 warps
 
+template <typename K>
+static cudaError_t launch_pdl(K kernel, unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t st, const SolveArgs<float> &a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <int KP, typename TC, bool BF>
 static cudaError_t launch_tc_kp(const SolveArgs<float> &a, cudaStream_t st) {
     if (a.nnz >= LONG_ROW_TC * a.m) {
         int64_t blocks = a.m;
         if (blocks > NUM_SMS_HINT * 64) blocks = NUM_SMS_HINT * 64;
-        k_row_solve_tc<KP, TC, 4, BF>
-            <<<(unsigned)blocks, 128, tc_smem_bytes<KP, TC, 4, BF>(), st>>>(a);
-    } else {
-        constexpr int WARPS = (sizeof(TC) == 8 && KP == 32) ? 4 : 8;
-        const int64_t per = (int64_t)WARPS * (32 / KP);
-        int64_t blocks = (a.m + per - 1) / per;
-        if (blocks > NUM_SMS_HINT * 32) blocks = NUM_SMS_HINT * 32;
-        k_row_solve_tc<KP, TC, 1, BF>
-            <<<(unsigned)blocks, WARPS * 32, tc_smem_bytes<KP, TC, 1, BF>(), st>>>(a);
+        return launch_pdl(k_row_solve_tc<KP, TC, 4, BF>, (unsigned)blocks, 128,
+                          tc_smem_bytes<KP, TC, 4, BF>(), st, a);
     }
-    return cudaGetLastError();
+    constexpr int WARPS = (sizeof(TC) == 8 && KP == 32) ? 4 : 8;
+    const int64_t per = (int64_t)WARPS * (32 / KP);
+    int64_t blocks = (a.m + per - 1) / per;
+    if (blocks > NUM_SMS_HINT * 32) blocks = NUM_SMS_HINT * 32;
+    return launch_pdl(k_row_solve_tc<KP, TC, 1, BF>, (unsigned)blocks, WARPS * 32,
+                      tc_smem_bytes<KP, TC, 1, BF>(), st, a);
 }
 
 template <bool BF>
