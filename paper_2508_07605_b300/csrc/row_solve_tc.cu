@@ -338,18 +338,19 @@ k_row_solve_tc(SolveArgs<float> a) {
                         for (int sx = 0; sx < SPW; ++sx) {
                             if (sx != si) continue;
 #pragma unroll
-                            for (int tb = 0; tb < NBLK; ++tb) {
-                                const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
-                                const int sm = nb >> 1, h = nb & 1;
-                                mma_bf16(d[sx][tb], aL[mb], aH[sm][h], aH[sm][2 + h]);
-                                mma_bf16(d[sx][tb], aH[mb], aL[sm][h], aL[sm][2 + h]);
-                                mma_bf16(d[sx][tb], aH[mb], aH[sm][h], aH[sm][2 + h]);
-                            }
+                            for (int ps = 0; ps < 3; ++ps) {   // pass-major, as above
 #pragma unroll
-                            for (int mb = 0; mb < MB; ++mb) {
-                                mma_bf16(dr[sx][mb], aL[mb], rh0, rh1);
-                                mma_bf16(dr[sx][mb], aH[mb], rl0, rl1);
-                                mma_bf16(dr[sx][mb], aH[mb], rh0, rh1);
+                                for (int tb = 0; tb < NBLK; ++tb) {
+                                    const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
+                                    const int sm = nb >> 1, h = nb & 1;
+                                    const uint32_t *bsrc = (ps == 1) ? aL[sm] : aH[sm];
+                                    mma_bf16(d[sx][tb], ps == 0 ? aL[mb] : aH[mb], bsrc[h],
+                                             bsrc[2 + h]);
+                                }
+#pragma unroll
+                                for (int mb = 0; mb < MB; ++mb)
+                                    mma_bf16(dr[sx][mb], ps == 0 ? aL[mb] : aH[mb],
+                                             ps == 1 ? rl0 : rh0, ps == 1 ? rl1 : rh1);
                             }
                         }
                     }
@@ -376,21 +377,22 @@ k_row_solve_tc(SolveArgs<float> a) {
 #pragma unroll
                     for (int sx = 0; sx < SPW; ++sx) {
                         if (sx != si) continue;   // warp-uniform: accumulators stay in registers
+                        // pass-major order: consecutive MMAs go to different
+                        // accumulators, so the three passes of one block do not
+                        // wait on each other back to back
 #pragma unroll
-                        for (int tb = 0; tb < NBLK; ++tb) {
-                            const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
-                            const int src_mb = nb >> 1, h = nb & 1;
-                            const uint32_t bh0 = ah[src_mb][h], bh1 = ah[src_mb][2 + h];
-                            const uint32_t bl0 = al[src_mb][h], bl1 = al[src_mb][2 + h];
-                            mma_tf32(d[sx][tb], al[mb], bh0, bh1);
-                            mma_tf32(d[sx][tb], ah[mb], bl0, bl1);
-                            mma_tf32(d[sx][tb], ah[mb], bh0, bh1);
-                        }
+                        for (int ps = 0; ps < 3; ++ps) {
 #pragma unroll
-                        for (int mb = 0; mb < MB; ++mb) {
-                            mma_tf32(dr[sx][mb], al[mb], rh0, rh1);
-                            mma_tf32(dr[sx][mb], ah[mb], rl0, rl1);
-                            mma_tf32(dr[sx][mb], ah[mb], rh0, rh1);
+                            for (int tb = 0; tb < NBLK; ++tb) {
+                                const int mb = Blocks<KP>::mb_of(tb), nb = Blocks<KP>::nb_of(tb);
+                                const int src_mb = nb >> 1, h = nb & 1;
+                                const uint32_t *bsrc = (ps == 1) ? al[src_mb] : ah[src_mb];
+                                mma_tf32(d[sx][tb], ps == 0 ? al[mb] : ah[mb], bsrc[h], bsrc[2 + h]);
+                            }
+#pragma unroll
+                            for (int mb = 0; mb < MB; ++mb)
+                                mma_tf32(dr[sx][mb], ps == 0 ? al[mb] : ah[mb],
+                                         ps == 1 ? rl0 : rh0, ps == 1 ? rl1 : rh1);
                         }
                     }
                 }
