@@ -75,6 +75,7 @@ def lib():
             "orc_adam": (None, [_I64, _d, _d, _d, _d, _I64, _D, _D, _D, _D]),
             "orc_mlp_features": (None, [_I64, _i64, _i32, _d, _I32, _I32, _d, _d,
                                         ctypes.c_int, _d]),
+            "orc_phase_detect": (None, [_I64, _I64, _I64, _f, _F, _I32, _I32, _i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -281,3 +282,14 @@ def mlp_features(row_ptr, col, val, cpu_caps, gpu_caps, s_in=16):
     lib().orc_mlp_features(m, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d), len(cpu), len(gpu),
                            _p(cpu, _d), _p(gpu, _d), s_in, _p(X, _d))
     return X
+
+
+def phase_detect(power, p_th=60.0, window=25, intervals=5):
+    """Algorithm 1 on each row of `power` (float32 [traces, len]); returns the
+    index of the sample at which a transition is first reported, or -1."""
+    power = _c(np.atleast_2d(power), np.float32)
+    n, L = power.shape
+    first = np.zeros(n, dtype=np.int64)
+    lib().orc_phase_detect(n, L, L, _p(power, _f), np.float32(p_th), int(window), int(intervals),
+                           _p(first, _i64))
+    return first

@@ -493,3 +493,47 @@ void orc_mlp_features(int64_t m, const int64_t *ptr, const int32_t *idx, const d
         }
     }
 }
+
+/* Algorithm 1 (phase-transition detection), followed step by step for each
+ * of n_traces power traces (row t of `power`, ld floats apart, len samples
+ * taken every delta seconds): samples enter a circular buffer Q of capacity
+ * N = W / delta; whenever Q is full it is divided into n_int consecutive
+ * intervals of N / n_int samples, and a transition is reported when no
+ * sample of any interval lies below p_th.  first[t] is the index of the
+ * sample whose arrival produced the first report, or -1. */
+void orc_phase_detect(int64_t n_traces, int64_t len, int64_t ld, const float *power, float p_th,
+                      int32_t N, int32_t n_int, int64_t *first) {
+    float *Q = (float *)malloc(sizeof(float) * (size_t)(N > 0 ? N : 1));
+    for (int64_t t = 0; t < n_traces; ++t) {
+        const float *pw = power + t * ld;
+        int32_t head = 0, count = 0;   /* oldest sample at Q[head] */
+        first[t] = -1;
+        for (int64_t s = 0; s < len; ++s) {
+            /* append p, removing the oldest if full */
+            if (count < N) {
+                Q[(head + count) % N] = pw[s];
+                ++count;
+            } else {
+                Q[head] = pw[s];
+                head = (head + 1) % N;
+            }
+            if (count == N) {
+                int flag = 1;
+                const int32_t per = N / n_int;
+                for (int32_t k = 0; k < n_int && flag; ++k) {       /* each interval I */
+                    for (int32_t e = 0; e < per; ++e) {
+                        if (Q[(head + k * per + e) % N] < p_th) {    /* any value below */
+                            flag = 0;
+                            break;
+                        }
+                    }
+                }
+                if (flag) {
+                    first[t] = s;
+                    break;
+                }
+            }
+        }
+    }
+    free(Q);
+}

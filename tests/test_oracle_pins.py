@@ -279,3 +279,45 @@ def test_mlp_features_hand_example(orc):
     # setting 1 = (100 W, 150 W) -> (0, 1); setting 4 = (300 W, 50 W) -> (1, 0)
     assert np.array_equal(X[0], [0, 1, 0.3, 1, 0, 0.9, 0, 0, 0])
     assert np.array_equal(X[1], np.zeros(9))
+
+
+# ---------------------------------------------------------------- Algorithm 1
+def _phase_trace(segments):
+    """Concatenate (value, count) segments into one float32 power trace."""
+    return np.concatenate([np.full(c, v, np.float32) for v, c in segments])
+
+
+def test_phase_detection_hand_cases(orc):
+    """Algorithm 1 (Sec. "Online Performance Prediction"): delta 0.2 s,
+    W 5 s -> N = 25 samples, P_th 60 W, five 1-s intervals; a transition is
+    reported on the sample that completes 25 consecutive readings none of
+    which is below 60 W (a reading of exactly 60 W is not below)."""
+    cases = [
+        (_phase_trace([(100.0, 24)]), -1),                       # buffer never full
+        (_phase_trace([(100.0, 25)]), 24),                       # full at sample 24
+        (_phase_trace([(60.0, 30)]), 24),                        # equal to P_th passes
+        (_phase_trace([(40.0, 10), (75.0, 25), (40.0, 5)]), 34),
+        (_phase_trace([(40.0, 5), (90.0, 15), (59.9, 1), (90.0, 30)]), 45),
+        (_phase_trace([(40.0, 3), (90.0, 24), (50.0, 1), (90.0, 24)]), -1),
+    ]
+    got = [int(orc.phase_detect(tr)[0]) for tr, _ in cases]
+    assert got == [want for _, want in cases]
+
+
+def test_phase_detection_equals_sliding_window_minimum(orc):
+    """The five-interval check is the same as 'the minimum of the last 25
+    readings is not below P_th': compare with that plain definition on
+    random traces, and with one interval instead of five."""
+    rng = np.random.default_rng(0)
+    P = rng.uniform(40.0, 80.0, (200, 300)).astype(np.float32)
+    P[rng.random((200, 300)) < 0.7] += 30.0
+    got = orc.phase_detect(P)
+    assert np.array_equal(got, orc.phase_detect(P, intervals=1))
+    for t in range(200):
+        ok = P[t] >= np.float32(60.0)
+        want = -1
+        for s in range(24, 300):
+            if ok[s - 24:s + 1].all():
+                want = s
+                break
+        assert got[t] == want
