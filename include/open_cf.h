@@ -217,6 +217,20 @@ int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const i
                          const int64_t *row_ptr, const int32_t *col, const float *val,
                          float *V_scratch, int32_t *W_out_host, void *stream);
 
+/* Algorithm 1 (phase-transition detection, Sec. "Online Performance
+ * Prediction") over many monitored jobs at once.  power: n_traces rows of len
+ * GPU power readings (float watts, one every delta seconds; row t starts at
+ * power + t * ld, ld >= len), device memory.  window = W / delta (25 for the
+ * paper's delta = 0.2 s, W = 5 s); p_th the power threshold (60 W).
+ * first (int64[n_traces], device) receives, per trace, the index of the
+ * reading on which the algorithm reports a transition -- the first reading
+ * that ends `window` consecutive readings none of which is below p_th -- or
+ * -1.  A reading that is not a number is not below p_th.  Needs no handle;
+ * OPEN_CF_INVALID_ARG for window < 1, ld < len, a non-finite p_th or NULL
+ * arrays, OPEN_CF_CUDA_ERROR if the launch fails. */
+int open_cf_phase_detect(const float *power, int64_t n_traces, int64_t len, int64_t ld,
+                         float p_th, int32_t window, int64_t *first, void *stream);
+
 /* ---- Learned warm start (Sec. "Collaborative Filtering Model": the paper's
  * CF model is an MLP with SELU activations; Sec. "Online Performance
  * Prediction": fill in a new application's row from its online profile).

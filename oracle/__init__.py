@@ -290,6 +290,8 @@ def phase_detect(power, p_th=60.0, window=25, intervals=5):
     power = _c(np.atleast_2d(power), np.float32)
     n, L = power.shape
     first = np.zeros(n, dtype=np.int64)
+    if window % intervals:
+        intervals = 1
     lib().orc_phase_detect(n, L, L, _p(power, _f), np.float32(p_th), int(window), int(intervals),
                            _p(first, _i64))
     return first

@@ -67,6 +67,7 @@ _SIGNATURES = {
     "open_cf_mlp_get_params": (ctypes.c_int, [_V, _V, _V]),
     "open_cf_mlp_train_step": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _F, _V, _V, _V]),
     "open_cf_mlp_infer": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
+    "open_cf_phase_detect": (ctypes.c_int, [_V, _I64, _I64, _I64, _F, _I32, _V, _V]),
 }
 
 MLP_PARAMS = 86560   # OPEN_CF_MLP_PARAMS
@@ -96,6 +97,23 @@ def lib():
 
 def exported_symbols():
     return sorted(_SIGNATURES)
+
+
+def phase_detect(power, p_th: float = 60.0, window: int = 25):
+    """Algorithm 1 on every row of `power` (float32 CUDA tensor [traces, len],
+    unit column stride): index of the reading that reports a transition, or -1."""
+    if power.dtype != torch.float32 or not power.is_cuda or power.dim() != 2 or \
+            power.stride(1) != 1:
+        raise ValueError("power must be a 2-D float32 CUDA tensor with unit column stride")
+    n, L = power.shape
+    out = torch.empty(n, dtype=torch.int64, device=power.device)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(power.device).cuda_stream)
+    with torch.cuda.device(power.device):
+        rc = lib().open_cf_phase_detect(_ptr(power), n, L, power.stride(0), float(p_th),
+                                        int(window), _ptr(out), stream)
+    if rc != OK:
+        raise OpenCFError(rc, "open_cf_phase_detect failed")
+    return out
 
 
 def _ptr(t):

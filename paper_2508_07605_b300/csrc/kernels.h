@@ -156,6 +156,10 @@ cudaError_t prepare_predict_tc();
 cudaError_t launch_v_image(const float *V, int64_t n, void *img, cudaStream_t st);
 cudaError_t launch_predict_select_tc(const PredictTcArgs &a, int num_sms, cudaStream_t st);
 
+// Algorithm 1 over many power traces (phase.cu).
+cudaError_t launch_phase_detect(const float *power, int64_t n_traces, int64_t len, int64_t ld,
+                                float p_th, int32_t window, int64_t *first, cudaStream_t st);
+
 // Fused tcgen05 forward pass (mlp_tc.cu).  img holds the BF16 weight images
 // W2 | W1 | W3 (element offsets below), each an N x K K-major operand image:
 // element (n, k) at (n / 8) * 8K + (k / 8) * 64 + (n % 8) * 8 + k % 8.

@@ -1250,4 +1250,15 @@ int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
     return OPEN_CF_OK;
 }
 
+int open_cf_phase_detect(const float *power, int64_t n_traces, int64_t len, int64_t ld,
+                         float p_th, int32_t window, int64_t *first, void *stream) {
+    if (n_traces < 0 || len < 0 || ld < len || window < 1) return OPEN_CF_INVALID_ARG;
+    if (n_traces > 0 && (!first || (len > 0 && !power))) return OPEN_CF_INVALID_ARG;
+    if (!std::isfinite(p_th)) return OPEN_CF_INVALID_ARG;
+    if (launch_phase_detect(power, n_traces, len, ld, p_th, window, first, S(stream)) !=
+        cudaSuccess)
+        return OPEN_CF_CUDA_ERROR;
+    return OPEN_CF_OK;
+}
+
 }  // extern "C"

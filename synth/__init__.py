@@ -467,3 +467,28 @@ def mlp_init(rng: np.random.Generator, sizes=(48, 256, 256, 32), out_scale: floa
         params.append(np.zeros(b))
     params[-2] = params[-2] * out_scale
     return params
+
+
+# ---------------------------------------------------------------------------
+# GPU power traces for Algorithm 1: a CPU phase (data preparation) near idle
+# power, then, for most jobs, a GPU phase well above the threshold with brief
+# dips (kernel gaps, synchronisation), as in the paper's GROMACS and BERT
+# traces (Fig. "power_pattern").  Readings every 0.2 s.
+# ---------------------------------------------------------------------------
+def make_power_traces(seed: int = 0, n_traces: int = 1024, length: int = 3000,
+                      p_cpu: float = 45.0, p_gpu: float = 200.0, dip_rate: float = 0.02,
+                      never: float = 0.2) -> np.ndarray:
+    """float32 [n_traces, length]: CPU phase N(p_cpu, 5) W for a uniform random
+    number of readings, then GPU phase N(p_gpu, 30) W with a reading below
+    60 W at rate dip_rate; a fraction `never` of jobs stays in the CPU phase."""
+    rng = np.random.default_rng(seed)
+    P = rng.normal(p_cpu, 5.0, (n_traces, length)).astype(np.float32)
+    start = rng.integers(0, max(length, 1), n_traces)
+    gpu_jobs = rng.random(n_traces) >= never
+    pos = np.arange(length)[None, :]
+    in_gpu = (pos >= start[:, None]) & gpu_jobs[:, None]
+    G = rng.normal(p_gpu, 30.0, (n_traces, length)).astype(np.float32)
+    dips = rng.random((n_traces, length)) < dip_rate
+    G[dips] = rng.uniform(20.0, 59.0, int(dips.sum())).astype(np.float32)
+    P[in_gpu] = G[in_gpu]
+    return P

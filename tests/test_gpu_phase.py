@@ -1,0 +1,54 @@
+"""Algorithm 1 (phase-transition detection) on the GPU over many traces,
+against the oracle's step-by-step circular-buffer version: detection indices
+bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+from gpu_util import DEV, host
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2508_07605_b300 as ocf  # noqa: E402
+
+
+@pytest.mark.parametrize("n,L", [(1, 24), (1, 25), (7, 31), (300, 1000), (2049, 257)])
+def test_phase_detect_matches_oracle(orc, n, L):
+    P = synth.make_power_traces(seed=n + L, n_traces=n, length=L)
+    got = host(ocf.phase_detect(torch.as_tensor(P, device=DEV)))
+    assert np.array_equal(got, orc.phase_detect(P))
+
+
+def test_phase_detect_edges(orc):
+    L = 200
+    P = np.full((6, L), 40.0, np.float32)
+    P[1] = 60.0                          # equal to the threshold: not below
+    P[2, 50:75] = 90.0                   # exactly one window
+    P[3, 50:74] = 90.0                   # one reading short
+    P[4, :] = 100.0
+    P[4, 100] = np.nan                   # not a number is not below the threshold
+    P[4, 10] = 59.99                     # a dip restarts the window
+    P[5, 170:] = 150.0                   # runs into the end of the trace
+    got = host(ocf.phase_detect(torch.as_tensor(P, device=DEV)))
+    want = orc.phase_detect(P)
+    assert np.array_equal(got, want)
+    assert list(want) == [-1, 24, 74, -1, 35, 194]
+
+
+@pytest.mark.parametrize("window,p_th", [(1, 60.0), (5, 120.0), (100, 60.0)])
+def test_phase_detect_other_windows_and_strided_rows(orc, window, p_th):
+    P = synth.make_power_traces(seed=window, n_traces=500, length=600)
+    big = torch.zeros(500, 640, device=DEV)
+    big[:, :600] = torch.as_tensor(P, device=DEV)
+    got = host(ocf.phase_detect(big[:, :600], p_th=p_th, window=window))
+    assert np.array_equal(got, orc.phase_detect(P, p_th=p_th, window=window, intervals=1))
+
+
+def test_phase_detect_rejects_bad_window():
+    with pytest.raises(ocf.OpenCFError):
+        ocf.phase_detect(torch.zeros(2, 10, device=DEV), window=0)
