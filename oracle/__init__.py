@@ -76,6 +76,10 @@ def lib():
             "orc_mlp_features": (None, [_I64, _i64, _i32, _d, _I32, _I32, _d, _d,
                                         ctypes.c_int, _d]),
             "orc_phase_detect": (None, [_I64, _I64, _I64, _f, _F, _I32, _I32, _i64]),
+            "orc_half_step_wr": (None, [_I64, _i64, _i32, _d, _d, ctypes.c_int, _D, _d, _i32]),
+            "orc_objective_wr": (_D, [_I64, _I64, _i64, _i32, _d, _d, _d, ctypes.c_int, _D]),
+            "orc_als_wr": (None, [_I64, _I64, _i64, _i32, _d, ctypes.c_int, _D, ctypes.c_int,
+                                  _d, _d, _d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -295,3 +299,34 @@ def phase_detect(power, p_th=60.0, window=25, intervals=5):
     lib().orc_phase_detect(n, L, L, _p(power, _f), np.float32(p_th), int(window), int(intervals),
                            _p(first, _i64))
     return first
+
+
+def half_step_wr(row_ptr, col, val, F, lam):
+    """Weighted-lambda (ALS-WR) half-step: row i solved with lambda * s_i."""
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    F = _c(F, np.float64)
+    m, k = len(row_ptr) - 1, F.shape[1]
+    out = np.zeros((m, k)); st = np.zeros(m, dtype=np.int32)
+    lib().orc_half_step_wr(m, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d), _p(F, _d), k, lam,
+                           _p(out, _d), _p(st, _i32))
+    return out, st
+
+
+def objective_wr(row_ptr, col, val, U, V, lam):
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    U = _c(U, np.float64); V = _c(V, np.float64)
+    return float(lib().orc_objective_wr(len(row_ptr) - 1, V.shape[0], _p(row_ptr, _i64),
+                                        _p(col, _i32), _p(val, _d), _p(U, _d), _p(V, _d),
+                                        U.shape[1], lam))
+
+
+def als_wr(row_ptr, col, val, n, V0, lam, sweeps, history=False):
+    """ALS-WR from V0; returns (U, V, J_hist or None)."""
+    row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+    V = np.array(V0, dtype=np.float64, copy=True, order="C")
+    m, k = len(row_ptr) - 1, V.shape[1]
+    U = np.zeros((m, k))
+    J = np.zeros(2 * sweeps) if history else None
+    lib().orc_als_wr(m, n, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d), k, lam, sweeps,
+                     _p(U, _d), _p(V, _d), _p(J, _d) if history else None)
+    return U, V, J

@@ -537,3 +537,65 @@ void orc_phase_detect(int64_t n_traces, int64_t len, int64_t ld, const float *po
     }
     free(Q);
 }
+
+/* ALS with weighted-lambda regularisation (ALS-WR, the variant of the ALS
+ * work the paper cites for collaborative filtering): the regulariser of each
+ * factor is lambda times its number of observations,
+ *   J_wr = sum (R_ij - u_i . v_j)^2 + lambda (sum_i s_i |u_i|^2 + sum_j s_j |v_j|^2),
+ * so each row solve is (sum_{j in Omega_i} v_j v_j^T + lambda s_i I) u_i = b_i. */
+void orc_half_step_wr(int64_t m, const int64_t *ptr, const int32_t *idx, const double *val,
+                      const double *F, int k, double lambda, double *out, int32_t *status) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < m; ++i) {
+        const int64_t s = ptr[i + 1] - ptr[i];
+        int st = orc_row_solve(k, lambda * (double)s, s, idx + ptr[i], val + ptr[i], F,
+                               out + i * k);
+        if (status) status[i] = st;
+    }
+}
+
+double orc_objective_wr(int64_t m, int64_t n, const int64_t *ptr, const int32_t *idx,
+                        const double *val, const double *U, const double *V, int k,
+                        double lambda) {
+    double sse = 0.0, nu = 0.0, nv = 0.0;
+    int64_t *cnt = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    for (int64_t i = 0; i < m; ++i) {
+        const double *u = U + i * k;
+        double ui = 0.0;
+        for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+            const double *v = V + (int64_t)idx[t] * k;
+            double d = 0.0;
+            for (int p = 0; p < k; ++p) d += u[p] * v[p];
+            const double e = val[t] - d;
+            sse += e * e;
+            cnt[idx[t]]++;
+        }
+        for (int p = 0; p < k; ++p) ui += u[p] * u[p];
+        nu += (double)(ptr[i + 1] - ptr[i]) * ui;
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        double vj = 0.0;
+        for (int p = 0; p < k; ++p) vj += V[j * k + p] * V[j * k + p];
+        nv += (double)cnt[j] * vj;
+    }
+    free(cnt);
+    return sse + lambda * (nu + nv);
+}
+
+void orc_als_wr(int64_t m, int64_t n, const int64_t *ptr, const int32_t *idx, const double *val,
+                int k, double lambda, int sweeps, double *U, double *V, double *J_hist) {
+    int64_t nnz = ptr[m];
+    int64_t *cptr = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t *cidx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    double *cval = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    orc_transpose(m, n, ptr, idx, val, cptr, cidx, cval);
+    for (int s = 0; s < sweeps; ++s) {
+        orc_half_step_wr(m, ptr, idx, val, V, k, lambda, U, NULL);
+        if (J_hist) J_hist[2 * s] = orc_objective_wr(m, n, ptr, idx, val, U, V, k, lambda);
+        orc_half_step_wr(n, cptr, cidx, cval, U, k, lambda, V, NULL);
+        if (J_hist) J_hist[2 * s + 1] = orc_objective_wr(m, n, ptr, idx, val, U, V, k, lambda);
+    }
+    free(cptr);
+    free(cidx);
+    free(cval);
+}

@@ -321,3 +321,46 @@ def test_phase_detection_equals_sliding_window_minimum(orc):
                 want = s
                 break
         assert got[t] == want
+
+
+# ---------------------------------------------------------------- ALS-WR
+def test_wr_row_solve_is_ridge_with_count_scaled_lambda(orc):
+    """Each weighted-lambda row solve is the least-squares solution of the
+    augmented system [V_Omega; sqrt(lambda s_i) I] u = [r; 0] (brute force by
+    numpy's lstsq on tiny inputs)."""
+    rng = np.random.default_rng(5)
+    m, n, k, lam = 6, 9, 3, 0.3
+    counts = np.array([0, 1, 2, 4, 6, 9])
+    ptr = np.concatenate([[0], np.cumsum(counts)])
+    col = np.concatenate([np.sort(rng.choice(n, c, replace=False)) for c in counts]).astype(np.int32)
+    val = rng.standard_normal(ptr[-1])
+    V = rng.standard_normal((n, k))
+    U, st = orc.half_step_wr(ptr, col, val, V, lam)
+    for i in range(m):
+        c, r = col[ptr[i]:ptr[i + 1]], val[ptr[i]:ptr[i + 1]]
+        if len(c) == 0:
+            assert st[i] == 2 and np.all(U[i] == 0)
+            continue
+        A = np.vstack([V[c], np.sqrt(lam * len(c)) * np.eye(k)])
+        b = np.concatenate([r, np.zeros(k)])
+        ref = np.linalg.lstsq(A, b, rcond=None)[0]
+        assert np.allclose(U[i], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_wr_objective_monotone_and_closed_form(orc):
+    """Every weighted-lambda half-step minimises J_wr exactly in its block, so
+    J_wr never increases; J_wr at given factors equals the definition written
+    out with numpy."""
+    prob = synth.make_sparse_problem(seed=7, m=120, n_cpu=4, n_gpu=10, rank=4, density=0.3,
+                                     k=4, lam=0.05, n_heldout=8)
+    U, V, J = orc.als_wr(prob.row_ptr, prob.col, prob.val, prob.n, prob.V0, prob.lam, 8,
+                         history=True)
+    assert np.all(np.diff(J) <= 1e-12 * np.abs(J[:-1]))
+    rows = np.repeat(np.arange(prob.m), np.diff(prob.row_ptr))
+    res = prob.val - np.einsum("tk,tk->t", U[rows], V[prob.col])
+    s_i = np.diff(prob.row_ptr)
+    s_j = np.bincount(prob.col, minlength=prob.n)
+    want = (res ** 2).sum() + prob.lam * ((s_i * (U ** 2).sum(1)).sum() +
+                                          (s_j * (V ** 2).sum(1)).sum())
+    assert abs(orc.objective_wr(prob.row_ptr, prob.col, prob.val, U, V, prob.lam) - want) <= \
+        1e-10 * abs(want)
