@@ -90,6 +90,10 @@ typedef struct {
     int32_t device;            /* CUDA device ordinal */
     float mlp_fallback_threshold; /* observed-entry RMSE above which the learned
                                      factor is replaced by the ALS solve */
+    int32_t weighted_lambda;   /* 1: weighted-lambda regularisation (ALS-WR of the
+                                  ALS work the paper cites): every row / column
+                                  solve uses lambda * (its observation count), and
+                                  J weights |u_i|^2, |v_j|^2 by those counts */
 } open_cf_config;
 
 /* Create a handle.  Copies cfg and the cap grids.  Fails with

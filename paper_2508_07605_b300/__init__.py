@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
                 ("n_gpu_caps", ctypes.c_int32),
                 ("cpu_caps_w_host", ctypes.POINTER(ctypes.c_double)),
                 ("gpu_caps_w_host", ctypes.POINTER(ctypes.c_double)),
-                ("device", ctypes.c_int32), ("mlp_fallback_threshold", ctypes.c_float)]
+                ("device", ctypes.c_int32), ("mlp_fallback_threshold", ctypes.c_float),
+                ("weighted_lambda", ctypes.c_int32)]
 
 
 _V, _I64, _I32, _F, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_double
@@ -125,7 +126,7 @@ class OpenCF:
 
     def __init__(self, k: int, lam: float, sweeps: int = 15, precision: str = "fp32",
                  cholesky_fp64: bool = False, cpu_caps=None, gpu_caps=None, device: int = 0,
-                 mlp_fallback_threshold: float = 0.02):
+                 mlp_fallback_threshold: float = 0.02, weighted_lambda: bool = False):
         self._h = ctypes.c_void_p(0)
         self.k, self.lam, self.sweeps = int(k), float(lam), int(sweeps)
         self.precision = precision
@@ -139,7 +140,7 @@ class OpenCF:
         cfg = Config(self.k, self.lam, self.sweeps, 0, _PRECISION[precision], int(cholesky_fp64),
                      len(cpu), len(gpu), ctypes.cast(self._cpu, ctypes.POINTER(ctypes.c_double)),
                      ctypes.cast(self._gpu, ctypes.POINTER(ctypes.c_double)), device,
-                     float(mlp_fallback_threshold))
+                     float(mlp_fallback_threshold), int(bool(weighted_lambda)))
         rc = lib().open_cf_create(ctypes.byref(cfg), ctypes.byref(self._h))
         if rc != OK:
             raise OpenCFError(rc, "open_cf_create failed")

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(BW * 32) k_batched_als(BatchArgs b) {
                                 nullptr, b.lambda};
             SolveArgs<float> va{n, b.nnz, b.cptr + c0 + p, b.cidx, b.cval, U, m, V, KP, KP,
                                 nullptr, b.lambda};
+            ua.wr = va.wr = b.wr;
             for (int s = 0; s < b.sweeps; ++s) {
                 run_half(ua, KP, wig, W, gbase, wig, lane);
                 group_sync(bar, gthreads);

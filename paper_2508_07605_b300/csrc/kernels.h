@@ -25,6 +25,7 @@ template <typename TV> struct SolveArgs {
     void *outb = nullptr;       // optional split BF16 copy of the output rows (stride 2*KP)
     const int32_t *row_map = nullptr;   // optional: system i is CSR row row_map[i]
     const int64_t *m_dev = nullptr;     // optional: number of systems read on the device
+    bool wr = false;                    // weighted lambda: the diagonal gets lambda * s_i
 };
 
 template <typename TV, typename TC>
@@ -77,6 +78,7 @@ struct BatchArgs {
     int32_t *counter;         // work queue position per class (zeroed before launch)
     int sweeps;
     double lambda;
+    bool wr;                  // weighted lambda (lambda * observations of the row / column)
     int n_classes;
     int32_t class_end[BATCH_MAX_CLASSES];
     int32_t class_W[BATCH_MAX_CLASSES];
@@ -218,7 +220,13 @@ template <typename TV>
 cudaError_t launch_objective(int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
                              const TV *val, const TV *U, int64_t ldu, int k, const TV *V,
                              int64_t n, int KP, double lambda, double *part, double *J_out,
-                             float *row_rmse, cudaStream_t st);
+                             float *row_rmse, const int32_t *ccount, cudaStream_t st);
+// ccount (int32[n], null = unweighted): observations per column for the
+// weighted-lambda objective sum s_i |u_i|^2 + sum_j s_j |v_j|^2.
+cudaError_t launch_col_counts_from_ptr(int64_t n, const int64_t *cptr, int32_t *cnt,
+                                       cudaStream_t st);
+cudaError_t launch_col_counts(int64_t nnz, int64_t n, const int32_t *idx, int32_t *cnt,
+                              cudaStream_t st);
 
 // Layout helpers.
 template <typename TV>

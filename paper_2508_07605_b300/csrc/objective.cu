@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(OBJ_WARPS * 32)
 k_objective_rows(int64_t m, int64_t nnz, const int64_t *__restrict__ ptr,
                  const int32_t *__restrict__ idx, const TV *__restrict__ val,
                  const TV *__restrict__ U, int64_t ldu, int k, const TV *__restrict__ V,
-                 int64_t n, double *__restrict__ part, float *__restrict__ row_rmse) {
+                 int64_t n, double *__restrict__ part, float *__restrict__ row_rmse,
+                 const int32_t *__restrict__ ccount) {
     using VT = typename Vec4<TV>::type;
     constexpr int VN = Vec4<TV>::N;
     __shared__ double ws[OBJ_WARPS][3];
@@ -87,6 +88,7 @@ k_objective_rows(int64_t m, int64_t nnz, const int64_t *__restrict__ ptr,
             TV nu = TV(0);
 #pragma unroll
             for (int p = 0; p < KP; ++p) nu = my_fma(u[p], u[p], nu);
+            if (ccount) nu *= TV(end - beg);   // weighted lambda: s_i |u_i|^2
             sse_w.add(sse);
             nu_w.add(nu);
             if (row_rmse) {
@@ -99,7 +101,8 @@ k_objective_rows(int64_t m, int64_t nnz, const int64_t *__restrict__ ptr,
     const int64_t vper = (n + G - 1) / G;
     const int64_t v0 = blockIdx.x * vper * KP, v1 = min(n, (blockIdx.x + 1) * vper) * KP;
     TV nv = TV(0);
-    for (int64_t e = v0 + threadIdx.x; e < v1; e += blockDim.x) nv = my_fma(V[e], V[e], nv);
+    for (int64_t e = v0 + threadIdx.x; e < v1; e += blockDim.x)
+        nv = ccount ? my_fma(TV(ccount[e / KP]) * V[e], V[e], nv) : my_fma(V[e], V[e], nv);
     nv = warp_sum_t(nv);
     if (lane == 0) {
         ws[warp][0] = (double)sse_w.s - (double)sse_w.c;
@@ -136,24 +139,60 @@ k_objective_final(int64_t G, const double *__restrict__ part, double lambda,
     if (threadIdx.x == 0) *J = a + lambda * (b + c);
 }
 
+// Observations per column: from a CSC column pointer, or by counting a CSR.
+__global__ void k_count_from_ptr(int64_t n, const int64_t *__restrict__ cptr,
+                                 int32_t *__restrict__ cnt) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        cnt[j] = (int32_t)(cptr[j + 1] - cptr[j]);
+}
+
+__global__ void k_count_cols(int64_t nnz, int64_t n, const int32_t *__restrict__ idx,
+                             int32_t *__restrict__ cnt) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = idx[t];
+        if (j >= 0 && (int64_t)j < n) atomicAdd(cnt + j, 1);
+    }
+}
+
+cudaError_t launch_col_counts_from_ptr(int64_t n, const int64_t *cptr, int32_t *cnt,
+                                       cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t b = (n + 255) / 256;
+    if (b > NUM_SMS_HINT * 8) b = NUM_SMS_HINT * 8;
+    k_count_from_ptr<<<(unsigned)b, 256, 0, st>>>(n, cptr, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_counts(int64_t nnz, int64_t n, const int32_t *idx, int32_t *cnt,
+                              cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n > 0 ? n : 1), st);
+    if (e != cudaSuccess || nnz <= 0) return e;
+    int64_t b = (nnz + 255) / 256;
+    if (b > NUM_SMS_HINT * 16) b = NUM_SMS_HINT * 16;
+    k_count_cols<<<(unsigned)b, 256, 0, st>>>(nnz, n, idx, cnt);
+    return cudaGetLastError();
+}
+
 template <typename TV>
 cudaError_t launch_objective(int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
                              const TV *val, const TV *U, int64_t ldu, int k, const TV *V,
                              int64_t n, int KP, double lambda, double *part, double *J_out,
-                             float *row_rmse, cudaStream_t st) {
+                             float *row_rmse, const int32_t *ccount, cudaStream_t st) {
     const int64_t G = objective_parts(m > n ? m : n);
     switch (KP) {
         case 8:
             k_objective_rows<TV, 8><<<(unsigned)G, OBJ_WARPS * 32, 0, st>>>(
-                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse);
+                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse, ccount);
             break;
         case 16:
             k_objective_rows<TV, 16><<<(unsigned)G, OBJ_WARPS * 32, 0, st>>>(
-                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse);
+                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse, ccount);
             break;
         case 32:
             k_objective_rows<TV, 32><<<(unsigned)G, OBJ_WARPS * 32, 0, st>>>(
-                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse);
+                m, nnz, ptr, idx, val, U, ldu, k, V, n, part, row_rmse, ccount);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -164,10 +203,10 @@ cudaError_t launch_objective(int64_t m, int64_t nnz, const int64_t *ptr, const i
 template cudaError_t launch_objective<float>(int64_t, int64_t, const int64_t *, const int32_t *,
                                              const float *, const float *, int64_t, int,
                                              const float *, int64_t, int, double, double *,
-                                             double *, float *, cudaStream_t);
+                                             double *, float *, const int32_t *, cudaStream_t);
 template cudaError_t launch_objective<double>(int64_t, int64_t, const int64_t *, const int32_t *,
                                               const double *, const double *, int64_t, int,
                                               const double *, int64_t, int, double, double *,
-                                              double *, float *, cudaStream_t);
+                                              double *, float *, const int32_t *, cudaStream_t);
 
 }  // namespace ocf

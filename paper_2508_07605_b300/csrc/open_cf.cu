@@ -59,6 +59,7 @@ struct open_cf {
     Buf mlp_th, mlp_g, mlp_m1, mlp_m2, mlp_bf, mlp_map, mlp_t, mlp_cn, mlp_scr, mlp_G;
     Buf mlp_img, mlp_imap, mlp_err;   // tcgen05 weight images, their map, timeout flag
     Buf vimg, pt_err;                 // split BF16 operand images of V, timeout flag (predict)
+    Buf ccount;                       // observations per column (weighted-lambda objective)
     int num_sms = 0;
     bool mlp_ready = false;
     int64_t mlp_Bcap = 0;
@@ -212,14 +213,21 @@ int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const i
     const int sweeps = h->cfg.sweeps;
     const int k = h->k;
     const double lam = h->cfg.lambda;
+    const bool wr = h->cfg.weighted_lambda != 0;
+    if (wr && J_hist) CK(h, ensure(h, h->ccount, sizeof(int32_t) * std::max<int64_t>(n, 1)));
+    const int32_t *ccount = (wr && J_hist) ? (const int32_t *)h->ccount.p : nullptr;
     auto enqueue = [&](cudaStream_t st) -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(Uw, 0, sizeof(TV) * m * KP, st);
         if (e != cudaSuccess) return e;
         e = launch_csr_to_csc<TV>(m, n, nnz, ptr, idx, val, cptr, cidx, cval, (int32_t *)h->cnt.p,
                                   (int64_t *)h->tot.p, plan, st);
         if (e != cudaSuccess) return e;
+        if (ccount &&
+            (e = launch_col_counts_from_ptr(n, cptr, (int32_t *)ccount, st)) != cudaSuccess)
+            return e;
         for (int s = 0; s < sweeps; ++s) {
             SolveArgs<TV> ua{m, nnz, ptr, idx, val, V, n, Uw, KP, KP, row_status, lam};
+            ua.wr = wr;
             if (bf) {
                 ua.Fb = h->Vb16.p;
                 ua.outb = h->Ub16.p;
@@ -227,10 +235,11 @@ int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const i
             if ((e = half_step<TV>(h, ua, st)) != cudaSuccess) return e;
             if (J_hist &&
                 (e = launch_objective<TV>(m, nnz, ptr, idx, val, Uw, KP, k, V, n, KP, lam,
-                                          (double *)h->part.p, J_hist + 2 * s, nullptr, st)) !=
-                    cudaSuccess)
+                                          (double *)h->part.p, J_hist + 2 * s, nullptr, ccount,
+                                          st)) != cudaSuccess)
                 return e;
             SolveArgs<TV> va{n, nnz, cptr, cidx, cval, Uw, m, V, KP, KP, col_status, lam};
+            va.wr = wr;
             if (bf) {
                 va.Fb = h->Ub16.p;
                 va.outb = h->Vb16.p;
@@ -239,7 +248,7 @@ int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const i
             if (J_hist &&
                 (e = launch_objective<TV>(m, nnz, ptr, idx, val, Uw, KP, k, V, n, KP, lam,
                                           (double *)h->part.p, J_hist + 2 * s + 1, nullptr,
-                                          st)) != cudaSuccess)
+                                          ccount, st)) != cudaSuccess)
                 return e;
         }
         if (U_out && u_rows > 0)
@@ -413,6 +422,7 @@ BatchArgs batch_args(open_cf_t *h, const BatchPlan &L, const int64_t *row_ptr, c
     b.counter = (int32_t *)h->b_counter.p;
     b.sweeps = sweeps;
     b.lambda = h->cfg.lambda;
+    b.wr = h->cfg.weighted_lambda != 0;
     b.n_classes = 2;
     b.class_end[0] = h->b_class_end[0];
     b.class_end[1] = h->b_class_end[1];
@@ -641,7 +651,7 @@ void open_cf_destroy(open_cf_t *h) {
                        &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter, &h->mlp_th,
                        &h->mlp_g, &h->mlp_m1, &h->mlp_m2, &h->mlp_bf, &h->mlp_map, &h->mlp_t,
                        &h->mlp_cn, &h->mlp_scr, &h->mlp_G, &h->mlp_img, &h->mlp_imap,
-                       &h->mlp_err, &h->vimg, &h->pt_err})
+                       &h->mlp_err, &h->vimg, &h->pt_err, &h->ccount})
             free_buf(*b);
     }
     delete h;
@@ -780,10 +790,12 @@ int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
         if (h->f64) {
             SolveArgs<double> a{m_new, nnz, row_ptr, col, as<double>(val), (double *)h->V.p,
                                 h->n, (double *)U_out, h->k, h->k, status, h->cfg.lambda};
+            a.wr = h->cfg.weighted_lambda != 0;
             CK(h, half_step<double>(h, a, st));
         } else {
             SolveArgs<float> a{m_new, nnz, row_ptr, col, as<float>(val), (float *)h->V.p,
                                h->n, (float *)U_out, h->k, h->k, status, h->cfg.lambda};
+            a.wr = h->cfg.weighted_lambda != 0;
             if (h->cfg.precision == OPEN_CF_BF16_GRAM) a.Fb = h->Vb16.p;
             CK(h, half_step<float>(h, a, st));
         }
@@ -910,14 +922,20 @@ int open_cf_objective(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
     if (!J_out || (m > 0 && !U)) return fail(h, OPEN_CF_INVALID_ARG, "J_out or U is NULL");
     DeviceGuard g(h->device);
     CK(h, ensure(h, h->part, sizeof(double) * 3 * objective_parts(std::max<int64_t>(m, h->n))));
+    const int32_t *ccount = nullptr;
+    if (h->cfg.weighted_lambda) {   // observations per column of this matrix
+        CK(h, ensure(h, h->ccount, sizeof(int32_t) * std::max<int64_t>(h->n, 1)));
+        CK(h, launch_col_counts(nnz, h->n, col, (int32_t *)h->ccount.p, S(stream)));
+        ccount = (const int32_t *)h->ccount.p;
+    }
     if (h->f64)
         CK(h, launch_objective<double>(m, nnz, row_ptr, col, as<double>(val), as<double>(U), h->k,
                                        h->k, (double *)h->V.p, h->n, h->KP, h->cfg.lambda,
-                                       (double *)h->part.p, J_out, row_rmse, S(stream)));
+                                       (double *)h->part.p, J_out, row_rmse, ccount, S(stream)));
     else
         CK(h, launch_objective<float>(m, nnz, row_ptr, col, as<float>(val), as<float>(U), h->k,
                                       h->k, (float *)h->V.p, h->n, h->KP, h->cfg.lambda,
-                                      (double *)h->part.p, J_out, row_rmse, S(stream)));
+                                      (double *)h->part.p, J_out, row_rmse, ccount, S(stream)));
     return OPEN_CF_OK;
 }
 
@@ -1244,6 +1262,7 @@ int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
                        MLP_K, status, h->cfg.lambda};
     a.row_map = (const int32_t *)h->j_idx.p;
     a.m_dev = cnt;
+    a.wr = h->cfg.weighted_lambda != 0;
     if (h->cfg.precision == OPEN_CF_BF16_GRAM) a.Fb = h->Vb16.p;
     CK(h, half_step<float>(h, a, st));
     CK(h, launch_fallback_mark(m, (const int32_t *)h->j_idx.p, cnt, status, st));

@@ -461,9 +461,10 @@ k_row_solve_tc(SolveArgs<float> a) {
                 for (int e = 0; e < KP; ++e) A[e] = TC(S.G[q][e]);
                 bt = TC(S.b[q]);
             }
+            const TC lam = a.wr ? TC(a.lambda * (double)s) : TC(a.lambda);   // weighted: lambda s_i
 #pragma unroll
             for (int e = 0; e < KP; ++e)
-                if (e == q) A[e] += TC(a.lambda);
+                if (e == q) A[e] += lam;
             __syncwarp();   // every lane has read G before L overwrites it
 
             // Right-looking Cholesky, lane q owning row q.  l = A[q][p] / sqrt(piv)

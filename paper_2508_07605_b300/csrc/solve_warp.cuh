@@ -111,9 +111,10 @@ __device__ __forceinline__ void solve_system(const SolveArgs<TV> &a, int64_t i,
             for (int e = 0; e < KP; ++e) A[e] = TC(acc[e]);
             bt = TC(bq);
         }
+        const TC lam = a.wr ? TC(a.lambda * (double)s) : TC(a.lambda);   // weighted: lambda s_i
 #pragma unroll
         for (int e = 0; e < KP; ++e)
-            if (e == q) A[e] += TC(a.lambda);
+            if (e == q) A[e] += lam;
 
         // With WPS > 1 every warp holds the summed system; warp 0 solves it.
         if (WPS == 1 || warp == 0) {

@@ -38,13 +38,14 @@ def rounded(a, dtype):
         np.float64)
 
 
-def solve_err(gpu, ref, F, ptr, col, val, lam):
+def solve_err(gpu, ref, F, ptr, col, val, lam, weighted=False):
     """Per-row error of ridge solves, scaled by what FP32 rounding can reach.
 
     Dividing by |u_ref| alone overstates the error when the right-hand side
     sum b = sum_t r_t f_t cancels (u tiny next to its terms): its rounding
     error is ~eps * sum_t |r_t| |f_t|, carried through A^{-1}.  The scale is
-    max(|u_ref|, |A^{-1}|_2 * |sum_t |r_t| |f_t||)."""
+    max(|u_ref|, |A^{-1}|_2 * |sum_t |r_t| |f_t||).  weighted: row i carries
+    lambda * s_i (s_i its observation count) instead of lambda."""
     gpu = np.asarray(gpu, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     out = np.zeros(len(ref))
@@ -55,7 +56,7 @@ def solve_err(gpu, ref, F, ptr, col, val, lam):
         if len(c) == 0:
             out[i] = np.linalg.norm(gpu[i])
             continue
-        A = F[c].T @ F[c] + lam * np.eye(k)
+        A = F[c].T @ F[c] + lam * (len(c) if weighted else 1) * np.eye(k)
         babs = (np.abs(r)[:, None] * np.abs(F[c])).sum(0)
         scale = max(np.linalg.norm(ref[i]), np.linalg.norm(np.linalg.inv(A), 2) *
                     np.linalg.norm(babs))
