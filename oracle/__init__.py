@@ -80,6 +80,11 @@ def lib():
             "orc_objective_wr": (_D, [_I64, _I64, _i64, _i32, _d, _d, _d, ctypes.c_int, _D]),
             "orc_als_wr": (None, [_I64, _I64, _i64, _i32, _d, ctypes.c_int, _D, ctypes.c_int,
                                   _d, _d, _d]),
+            "orc_ncf_net_size": (_I64, [ctypes.c_int] * 3),
+            "orc_ncf_forward": (None, [_I64, _i32, _i32] + [ctypes.c_int] * 3 + [_d] * 6),
+            "orc_ncf_loss_grad": (_D, [_I64, _i32, _i32, _d, _I64, _I64] + [ctypes.c_int] * 3 +
+                                  [_d] * 6),
+            "orc_ncf_predict": (None, [_I64, _I64] + [ctypes.c_int] * 3 + [_d] * 4),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -330,3 +335,74 @@ def als_wr(row_ptr, col, val, n, V0, lam, sweeps, history=False):
     lib().orc_als_wr(m, n, _p(row_ptr, _i64), _p(col, _i32), _p(val, _d), k, lam, sweeps,
                      _p(U, _d), _p(V, _d), _p(J, _d) if history else None)
     return U, V, J
+
+
+# ---------------------------------------------------------------- NCF
+def ncf_net_size(d, h1, h2):
+    return int(lib().orc_ncf_net_size(d, h1, h2))
+
+
+def ncf_forward(ai, sj, Ea, Es, net, h1, h2, keep=False):
+    """Predicted entries y[b] for the pairs (ai[b], sj[b]); with keep, also
+    the pre-activations (Z1, Z2)."""
+    ai = _c(ai, np.int32); sj = _c(sj, np.int32)
+    Ea = _c(Ea, np.float64); Es = _c(Es, np.float64); net = _c(net, np.float64)
+    B, d = len(ai), Ea.shape[1]
+    assert net.size == ncf_net_size(d, h1, h2)
+    y = np.zeros(B)
+    Z1 = np.zeros((B, h1)) if keep else None
+    Z2 = np.zeros((B, h2)) if keep else None
+    lib().orc_ncf_forward(B, _p(ai, _i32), _p(sj, _i32), d, h1, h2, _p(Ea, _d), _p(Es, _d),
+                          _p(net, _d), _p(y, _d), _p(Z1, _d) if keep else None,
+                          _p(Z2, _d) if keep else None)
+    return (y, Z1, Z2) if keep else y
+
+
+def ncf_loss_grad(ai, sj, r, Ea, Es, net, h1, h2):
+    """(L, g_net, gEa, gEs) of the batch's mean squared error."""
+    ai = _c(ai, np.int32); sj = _c(sj, np.int32); r = _c(r, np.float64)
+    Ea = _c(Ea, np.float64); Es = _c(Es, np.float64); net = _c(net, np.float64)
+    (m, d), n = Ea.shape, Es.shape[0]
+    g_net = np.zeros_like(net); gEa = np.zeros_like(Ea); gEs = np.zeros_like(Es)
+    L = lib().orc_ncf_loss_grad(len(ai), _p(ai, _i32), _p(sj, _i32), _p(r, _d), m, n, d, h1, h2,
+                                _p(Ea, _d), _p(Es, _d), _p(net, _d), _p(g_net, _d),
+                                _p(gEa, _d), _p(gEs, _d))
+    return float(L), g_net, gEa, gEs
+
+
+def ncf_predict(Ea, Es, net, h1, h2):
+    """The completed matrix T[i, j] = y(i, j) over every application and setting."""
+    Ea = _c(Ea, np.float64); Es = _c(Es, np.float64); net = _c(net, np.float64)
+    (m, d), n = Ea.shape, Es.shape[0]
+    T = np.zeros((m, n))
+    lib().orc_ncf_predict(m, n, d, h1, h2, _p(Ea, _d), _p(Es, _d), _p(net, _d), _p(T, _d))
+    return T
+
+
+def ncf_train(ai, sj, r, Ea, Es, net, h1, h2, perms, batch, lr, beta1=0.9, beta2=0.999,
+              eps=1e-8):
+    """Mini-batch Adam over the observed entries: epoch e visits them in the
+    order perms[e] in consecutive batches of `batch` (the last one shorter);
+    Adam runs on the packed vector [net, Ea, Es].  Returns (net, Ea, Es,
+    per-step losses)."""
+    ai = np.asarray(ai, np.int32); sj = np.asarray(sj, np.int32); r = np.asarray(r, np.float64)
+    m, d = np.shape(Ea); n = np.shape(Es)[0]
+    nn = np.asarray(net).size
+    theta = np.concatenate([np.asarray(net, np.float64).ravel(),
+                            np.asarray(Ea, np.float64).ravel(),
+                            np.asarray(Es, np.float64).ravel()])
+    m1 = np.zeros_like(theta); m2 = np.zeros_like(theta)
+    losses = []
+    t = 0
+    for perm in perms:
+        for b0 in range(0, len(perm), batch):
+            sel = perm[b0:b0 + batch]
+            net_, Ea_, Es_ = (theta[:nn], theta[nn:nn + m * d].reshape(m, d),
+                              theta[nn + m * d:].reshape(n, d))
+            L, gn, ga, gs = ncf_loss_grad(ai[sel], sj[sel], r[sel], Ea_, Es_, net_, h1, h2)
+            g = np.concatenate([gn, ga.ravel(), gs.ravel()])
+            t += 1
+            adam(theta, g, m1, m2, t, lr, beta1, beta2, eps)
+            losses.append(L)
+    return (theta[:nn].copy(), theta[nn:nn + m * d].reshape(m, d).copy(),
+            theta[nn + m * d:].reshape(n, d).copy(), np.array(losses))

@@ -24,11 +24,17 @@
  *    in FP64 and, for bit-exact comparison of the integer decision, in FP32.
  *  - The MLP of the learned warm start (SELU activations as named in Sec.
  *    "Collaborative Filtering Model"), forward, backward and Adam, in FP64.
+ *  - Neural collaborative filtering, the CF model that section describes
+ *    (application and power-cap-pair embeddings, concatenated, through a SELU
+ *    MLP to one predicted entry): forward, mean-squared-error gradient incl.
+ *    the embedding rows, and the completed matrix.
  *
  * Parity pins (tests/test_oracle_*.py) check this code against numpy's lstsq
  * and cholesky, closed forms (Sherman-Morrison, soft-thresholded SVD),
  * objective monotonicity, normal-equation residuals, exact recovery,
- * hand-computed Algorithm 2 tables and finite differences.
+ * hand-computed Algorithm 2 tables and finite differences; the NCF routines
+ * against PyTorch's FP64 autograd and Adam, finite differences and invariants
+ * (tests/test_oracle_ncf.py).
  */
 #include <math.h>
 #include <stdint.h>
@@ -598,4 +604,141 @@ void orc_als_wr(int64_t m, int64_t n, const int64_t *ptr, const int32_t *idx, co
     free(cptr);
     free(cidx);
     free(cval);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neural collaborative filtering, the paper's CF model (Sec. "Collaborative
+ * Filtering Model"): the application index i and the power-cap-pair index j
+ * select rows of two embedding tables, Ea[m, d] and Es[n, d]; the two rows
+ * are concatenated into x = [Ea_i, Es_j] (2d values) and passed through an
+ * MLP with SELU hidden activations whose single linear output is the
+ * predicted entry P_ij:
+ *     z1 = x W1 + b1,  z2 = selu(z1) W2 + b2,  y = selu(z2) . w3 + b3
+ * with W1 [2d, h1], W2 [h1, h2], w3 [h2] (weights [in, out] row-major).
+ * Training minimises the mean squared error over a batch of observed
+ * entries, L = (1/B) sum_b (y_b - r_b)^2.  net = {W1, b1, W2, b2, w3, b3}
+ * packed in that order. */
+static void ncf_unpack(int d, int h1, int h2, const double *net, const double **W1,
+                       const double **b1, const double **W2, const double **b2,
+                       const double **w3, const double **b3) {
+    *W1 = net;
+    *b1 = *W1 + (int64_t)2 * d * h1;
+    *W2 = *b1 + h1;
+    *b2 = *W2 + (int64_t)h1 * h2;
+    *w3 = *b2 + h2;
+    *b3 = *w3 + h2;
+}
+
+int64_t orc_ncf_net_size(int d, int h1, int h2) {
+    return (int64_t)2 * d * h1 + h1 + (int64_t)h1 * h2 + h2 + h2 + 1;
+}
+
+/* y[b] for the pairs (ai[b], sj[b]); Z1 [B, h1] and Z2 [B, h2] optional. */
+void orc_ncf_forward(int64_t B, const int32_t *ai, const int32_t *sj, int d, int h1, int h2,
+                     const double *Ea, const double *Es, const double *net, double *y,
+                     double *Z1_out, double *Z2_out) {
+    const double *W1, *b1, *W2, *b2, *w3, *b3;
+    ncf_unpack(d, h1, h2, net, &W1, &b1, &W2, &b2, &w3, &b3);
+#pragma omp parallel
+    {
+        double *x = (double *)malloc(sizeof(double) * 2 * (size_t)d);
+        double *z1 = (double *)malloc(sizeof(double) * (size_t)h1);
+        double *z2 = (double *)malloc(sizeof(double) * (size_t)h2);
+#pragma omp for schedule(static)
+        for (int64_t b = 0; b < B; ++b) {
+            for (int t = 0; t < d; ++t) {   /* concatenation of the two embeddings */
+                x[t] = Ea[(int64_t)ai[b] * d + t];
+                x[d + t] = Es[(int64_t)sj[b] * d + t];
+            }
+            for (int o = 0; o < h1; ++o) {
+                double s = b1[o];
+                for (int t = 0; t < 2 * d; ++t) s += x[t] * W1[(int64_t)t * h1 + o];
+                z1[o] = s;
+            }
+            for (int o = 0; o < h2; ++o) {
+                double s = b2[o];
+                for (int t = 0; t < h1; ++t) s += selu(z1[t]) * W2[(int64_t)t * h2 + o];
+                z2[o] = s;
+            }
+            double s = b3[0];
+            for (int t = 0; t < h2; ++t) s += selu(z2[t]) * w3[t];
+            y[b] = s;
+            if (Z1_out) memcpy(Z1_out + b * h1, z1, sizeof(double) * (size_t)h1);
+            if (Z2_out) memcpy(Z2_out + b * h2, z2, sizeof(double) * (size_t)h2);
+        }
+        free(x); free(z1); free(z2);
+    }
+}
+
+/* L = (1/B) sum_b (y_b - r_b)^2 and its gradient: g_net (same packing as net)
+ * and the embedding gradients gEa [m, d], gEs [n, d] (rows of indices that do
+ * not occur in the batch stay 0).  Returns L. */
+double orc_ncf_loss_grad(int64_t B, const int32_t *ai, const int32_t *sj, const double *r, int64_t m,
+                         int64_t n, int d, int h1, int h2, const double *Ea, const double *Es,
+                         const double *net, double *g_net, double *gEa, double *gEs) {
+    const double *W1, *b1, *W2, *b2, *w3, *b3;
+    ncf_unpack(d, h1, h2, net, &W1, &b1, &W2, &b2, &w3, &b3);
+    double *gW1 = g_net, *gb1 = gW1 + (int64_t)2 * d * h1, *gW2 = gb1 + h1;
+    double *gb2 = gW2 + (int64_t)h1 * h2, *gw3 = gb2 + h2, *gb3 = gw3 + h2;
+    memset(g_net, 0, sizeof(double) * (size_t)orc_ncf_net_size(d, h1, h2));
+    memset(gEa, 0, sizeof(double) * (size_t)(m * d));
+    memset(gEs, 0, sizeof(double) * (size_t)(n * d));
+    double *Z1 = (double *)malloc(sizeof(double) * (size_t)(B * h1));
+    double *Z2 = (double *)malloc(sizeof(double) * (size_t)(B * h2));
+    double *y = (double *)malloc(sizeof(double) * (size_t)(B > 0 ? B : 1));
+    double *dz1 = (double *)malloc(sizeof(double) * (size_t)h1);
+    double *dz2 = (double *)malloc(sizeof(double) * (size_t)h2);
+    orc_ncf_forward(B, ai, sj, d, h1, h2, Ea, Es, net, y, Z1, Z2);
+    double L = 0.0;
+    /* samples in order, so every accumulation has a fixed order */
+    for (int64_t b = 0; b < B; ++b) {
+        const double e = y[b] - r[b];
+        L += e * e;
+        const double dy = 2.0 * e / (double)B;
+        const double *z1 = Z1 + b * h1, *z2 = Z2 + b * h2;
+        gb3[0] += dy;
+        for (int t = 0; t < h2; ++t) {
+            gw3[t] += dy * selu(z2[t]);
+            dz2[t] = dy * w3[t] * selu_grad(z2[t]);
+            gb2[t] += dz2[t];
+        }
+        for (int t = 0; t < h1; ++t) {
+            const double a = selu(z1[t]);
+            double s = 0.0;
+            for (int o = 0; o < h2; ++o) {
+                gW2[(int64_t)t * h2 + o] += a * dz2[o];
+                s += W2[(int64_t)t * h2 + o] * dz2[o];
+            }
+            dz1[t] = s * selu_grad(z1[t]);
+            gb1[t] += dz1[t];
+        }
+        const double *ea = Ea + (int64_t)ai[b] * d, *es = Es + (int64_t)sj[b] * d;
+        double *gea = gEa + (int64_t)ai[b] * d, *ges = gEs + (int64_t)sj[b] * d;
+        for (int t = 0; t < d; ++t) {
+            double sa = 0.0, ss = 0.0;
+            for (int o = 0; o < h1; ++o) {
+                gW1[(int64_t)t * h1 + o] += ea[t] * dz1[o];
+                gW1[(int64_t)(d + t) * h1 + o] += es[t] * dz1[o];
+                sa += W1[(int64_t)t * h1 + o] * dz1[o];
+                ss += W1[(int64_t)(d + t) * h1 + o] * dz1[o];
+            }
+            gea[t] += sa;
+            ges[t] += ss;
+        }
+    }
+    free(Z1); free(Z2); free(y); free(dz1); free(dz2);
+    return B > 0 ? L / (double)B : 0.0;
+}
+
+/* The completed matrix: T[i, j] = y(i, j) for every application and setting. */
+void orc_ncf_predict(int64_t m, int64_t n, int d, int h1, int h2, const double *Ea,
+                     const double *Es, const double *net, double *T) {
+    int32_t *ai = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *sj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t j = 0; j < n; ++j) sj[j] = (int32_t)j;
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < n; ++j) ai[j] = (int32_t)i;
+        orc_ncf_forward(n, ai, sj, d, h1, h2, Ea, Es, net, T + i * n, NULL, NULL);
+    }
+    free(ai); free(sj);
 }

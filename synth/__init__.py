@@ -492,3 +492,35 @@ def make_power_traces(seed: int = 0, n_traces: int = 1024, length: int = 3000,
     G[dips] = rng.uniform(20.0, 59.0, int(dips.sum())).astype(np.float32)
     P[in_gpu] = G[in_gpu]
     return P
+
+
+# ---------------------------------------------------------------------------
+# Neural collaborative filtering (the paper's CF model): initial parameters and
+# the per-epoch visiting orders of the observed entries (both are random draws
+# of the method, so they are inputs to the GPU path and the oracle alike).
+NCF_D, NCF_H1, NCF_H2 = 32, 128, 64
+
+
+def ncf_init(rng: np.random.Generator, m: int, n: int, d: int = NCF_D, h1: int = NCF_H1,
+             h2: int = NCF_H2, emb_scale: float = 0.1, out_scale: float = 0.1):
+    """(net, Ea, Es): embeddings N(0, emb_scale^2); LeCun-normal MLP weights
+    [in, out] row-major, zero biases, the output weights scaled by out_scale;
+    net packed as [W1 (2d x h1), b1, W2 (h1 x h2), b2, w3 (h2), b3]."""
+    W1 = rng.standard_normal((2 * d, h1)) / math.sqrt(2 * d)
+    W2 = rng.standard_normal((h1, h2)) / math.sqrt(h1)
+    w3 = rng.standard_normal(h2) / math.sqrt(h2) * out_scale
+    net = np.concatenate([W1.ravel(), np.zeros(h1), W2.ravel(), np.zeros(h2), w3, np.zeros(1)])
+    Ea = rng.standard_normal((m, d)) * emb_scale
+    Es = rng.standard_normal((n, d)) * emb_scale
+    return net, Ea, Es
+
+
+def ncf_perms(rng: np.random.Generator, nnz: int, epochs: int):
+    """One random visiting order of the observed entries per epoch."""
+    return [rng.permutation(nnz).astype(np.int32) for _ in range(epochs)]
+
+
+def coo_from_csr(row_ptr, col):
+    """(app index, setting index) of every observed entry, in CSR order."""
+    ai = np.repeat(np.arange(len(row_ptr) - 1, dtype=np.int32), np.diff(row_ptr))
+    return ai, np.asarray(col, dtype=np.int32)
