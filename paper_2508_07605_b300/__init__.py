@@ -69,9 +69,21 @@ _SIGNATURES = {
     "open_cf_mlp_train_step": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _F, _V, _V, _V]),
     "open_cf_mlp_infer": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
     "open_cf_phase_detect": (ctypes.c_int, [_V, _I64, _I64, _I64, _F, _I32, _V, _V]),
+    "open_cf_ncf_create": (ctypes.c_int, [_I64, _I32, _V, _I32, _V, _I32, ctypes.c_int,
+                                          ctypes.POINTER(_V)]),
+    "open_cf_ncf_destroy": (None, [_V]),
+    "open_cf_ncf_last_error": (ctypes.c_char_p, [_V]),
+    "open_cf_ncf_set_params": (ctypes.c_int, [_V, _V, _V, _V, _V]),
+    "open_cf_ncf_get_params": (ctypes.c_int, [_V, _V, _V, _V, _V]),
+    "open_cf_ncf_train": (ctypes.c_int, [_V, _I64, _V, _V, _V, _I32, _V, _F, _V, _V]),
+    "open_cf_ncf_grad": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V, _V, _V, _V, _V]),
+    "open_cf_ncf_predict": (ctypes.c_int, [_V, _V, _F, _I32, _V, _V, _V]),
+    "open_cf_ncf_skipped": (ctypes.c_int, [_V, ctypes.POINTER(_I64)]),
+    "open_cf_ncf_check": (ctypes.c_int, [_V]),
 }
 
 MLP_PARAMS = 86560   # OPEN_CF_MLP_PARAMS
+NCF_D, NCF_H1, NCF_H2, NCF_NET = 32, 128, 64, 16641   # OPEN_CF_NCF_*
 
 _lib = None
 
@@ -346,3 +358,125 @@ class OpenCF:
         self._check(lib().open_cf_validate_csr(self._h, m, n, nnz, _ptr(row_ptr), _ptr(col),
                                                _ptr(val), ctypes.byref(res), self._stream()))
         return int(res.value)
+
+
+class NCF:
+    """Handle of neural collaborative filtering (open_cf_ncf_create / destroy):
+    m applications, the CPU-major cap grid's n settings, mini-batch capacity
+    `batch` (a multiple of 64)."""
+
+    def __init__(self, m: int, cpu_caps, gpu_caps, batch: int = 1024, device: int = 0):
+        self._h = ctypes.c_void_p(0)
+        self.m = int(m)
+        self.n = len(cpu_caps) * len(gpu_caps)
+        self.batch = int(batch)
+        self.device = torch.device("cuda", device)
+        cpu = (ctypes.c_double * len(cpu_caps))(*[float(c) for c in cpu_caps])
+        gpu = (ctypes.c_double * len(gpu_caps))(*[float(g) for g in gpu_caps])
+        h = ctypes.c_void_p(0)
+        rc = lib().open_cf_ncf_create(self.m, len(cpu_caps), cpu, len(gpu_caps), gpu, self.batch,
+                                      device, ctypes.byref(h))
+        if rc != OK:
+            raise OpenCFError(rc, "open_cf_ncf_create failed")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().open_cf_ncf_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = lib().open_cf_ncf_last_error(self._h)
+            raise OpenCFError(rc, msg.decode() if msg else "")
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _t(self, t, dtype, numel, name):
+        if t.dtype != dtype or t.device != self.device or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor on {self.device}")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"{name} must have {numel} elements")
+        return t
+
+    def set_params(self, net, Ea, Es):
+        self._t(net, torch.float32, NCF_NET, "net")
+        self._t(Ea, torch.float32, self.m * NCF_D, "Ea")
+        self._t(Es, torch.float32, self.n * NCF_D, "Es")
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_ncf_set_params(self._h, _ptr(net), _ptr(Ea), _ptr(Es),
+                                                     self._stream()))
+
+    def get_params(self):
+        net = torch.empty(NCF_NET, dtype=torch.float32, device=self.device)
+        Ea = torch.empty(self.m, NCF_D, dtype=torch.float32, device=self.device)
+        Es = torch.empty(self.n, NCF_D, dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_ncf_get_params(self._h, _ptr(net), _ptr(Ea), _ptr(Es),
+                                                     self._stream()))
+        return net, Ea, Es
+
+    def _coo(self, app, setting, val):
+        nnz = app.numel()
+        self._t(app, torch.int32, nnz, "app")
+        self._t(setting, torch.int32, nnz, "setting")
+        self._t(val, torch.float32, nnz, "val")
+        return nnz
+
+    def steps(self, nnz: int, epochs: int) -> int:
+        return epochs * ((nnz + self.batch - 1) // self.batch)
+
+    def train(self, app, setting, val, perms, lr: float, losses: bool = False):
+        """perms: int32 [epochs, nnz] visiting orders.  Returns the per-step
+        losses (float64 tensor) when asked, else None."""
+        nnz = self._coo(app, setting, val)
+        epochs = perms.shape[0] if perms.dim() == 2 else 0
+        self._t(perms, torch.int32, epochs * nnz, "perms")
+        L = torch.empty(self.steps(nnz, epochs), dtype=torch.float64,
+                        device=self.device) if losses else None
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_ncf_train(self._h, nnz, _ptr(app), _ptr(setting), _ptr(val),
+                                                epochs, _ptr(perms), float(lr), _ptr(L),
+                                                self._stream()))
+        return L
+
+    def grad(self, app, setting, val):
+        """(loss, g_net, g_Ea, g_Es) of one batch, no update."""
+        B = self._coo(app, setting, val)
+        loss = torch.empty(1, dtype=torch.float64, device=self.device)
+        gn = torch.empty(NCF_NET, dtype=torch.float32, device=self.device)
+        ga = torch.empty(self.m, NCF_D, dtype=torch.float32, device=self.device)
+        gs = torch.empty(self.n, NCF_D, dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_ncf_grad(self._h, B, _ptr(app), _ptr(setting), _ptr(val),
+                                               _ptr(loss), _ptr(gn), _ptr(ga), _ptr(gs),
+                                               self._stream()))
+        return loss, gn, ga, gs
+
+    def predict(self, gamma: float = 0.05, T: bool = True, select: bool = True,
+                baseline: int = -1):
+        """(T [m, n] or None, best [m] or None, saving [m] or None)."""
+        Tt = torch.empty(self.m, self.n, dtype=torch.float32, device=self.device) if T else None
+        best = torch.empty(self.m, dtype=torch.int32, device=self.device) if select else None
+        sav = torch.empty(self.m, dtype=torch.float32, device=self.device) if select else None
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_ncf_predict(self._h, _ptr(Tt), float(gamma), int(baseline),
+                                                  _ptr(best), _ptr(sav), self._stream()))
+        return Tt, best, sav
+
+    def skipped(self) -> int:
+        c = _I64(0)
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_ncf_skipped(self._h, ctypes.byref(c)))
+        return int(c.value)
+
+    def check(self):
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_ncf_check(self._h))

@@ -92,7 +92,7 @@ cudaError_t launch_batched_pack(int64_t P, const int64_t *rows, const int32_t *k
 
 // MLP warm start (mlp.cu).
 constexpr int MLP_IN = 48, MLP_INP = 64, MLP_H = 256, MLP_SIN = 16;
-enum { EPI_BIAS_SELU = 0, EPI_BIAS = 1, EPI_DSELU = 2, EPI_PART = 3 };
+enum { EPI_BIAS_SELU = 0, EPI_BIAS = 1, EPI_DSELU = 2, EPI_PART = 3, EPI_SCATTER = 4 };
 struct GemmArgs {
     int M, N, K;
     const void *A;            // bf16: [M,K] row-major, or [K,M] when transposed
@@ -105,6 +105,11 @@ struct GemmArgs {
     float *out_f;             // FP32 output / split-K partials
     void *out_z;              // bf16 pre-activation output (EPI_BIAS_SELU)
     int ldo;
+    // EPI_SCATTER: output row r, column c < N/2 is added (atomically) to
+    // out_f[ri[r] * N/2 + c], column c >= N/2 to out_f[s_off + rj[r] * N/2 + c - N/2];
+    // a negative index skips the row.
+    const int32_t *ri = nullptr, *rj = nullptr;
+    int64_t s_off = 0;
 };
 cudaError_t launch_gemm(const GemmArgs &g, bool at, bool bt, int epi, int splits,
                         cudaStream_t st);
@@ -125,6 +130,12 @@ cudaError_t launch_adam(int64_t count, float *th, const float *g, float *m1, flo
                         float b2, float eps, void *state, const int64_t *bf_map, void *thb,
                         const int64_t *img_map, void *img, cudaStream_t st);
 cudaError_t launch_adam_set_lr(void *state, float lr, cudaStream_t st);
+// The two halves of launch_adam, for callers that update several parameter
+// ranges in one step: advance t once, then update each range (maps may be NULL).
+cudaError_t launch_adam_tick(void *state, cudaStream_t st);
+cudaError_t launch_adam_update(int64_t count, float *th, const float *g, float *m1, float *m2,
+                               float b1, float b2, float eps, const void *state,
+                               const int64_t *bf_map, void *thb, cudaStream_t st);
 cudaError_t launch_to_bf16_map(int64_t count, const float *th, const int64_t *bf_map, void *thb,
                                const int64_t *img_map, void *img, cudaStream_t st);
 cudaError_t launch_fallback_rows(int64_t m, const float *rmse, float thr, int32_t *list,
@@ -246,5 +257,63 @@ template <typename TV>
 cudaError_t launch_validate_csr(int64_t m, int64_t n, int64_t nnz, const int64_t *ptr,
                                 const int32_t *idx, const TV *val, int32_t *flag,
                                 cudaStream_t st);
+
+
+// Neural collaborative filtering (ncf.cu): embeddings d = 32 per side,
+// MLP 64 -> 128 -> 64 -> 1 with SELU hidden units.
+constexpr int NCF_D = 32, NCF_H1 = 128, NCF_H2 = 64;
+constexpr int64_t NCF_OFF_B1 = 2 * NCF_D * NCF_H1;                   // net = W1 | b1 | W2 | b2 | w3 | b3
+constexpr int64_t NCF_OFF_W2 = NCF_OFF_B1 + NCF_H1;
+constexpr int64_t NCF_OFF_B2 = NCF_OFF_W2 + NCF_H1 * NCF_H2;
+constexpr int64_t NCF_OFF_W3 = NCF_OFF_B2 + NCF_H2;
+constexpr int64_t NCF_OFF_B3 = NCF_OFF_W3 + NCF_H2;
+constexpr int64_t NCF_NET = NCF_OFF_B3 + 1;                            // 16641
+struct NcfCtl {                 // device-side position of a training run
+    int64_t step;               // steps done (epoch = step / steps_per_epoch)
+    unsigned long long skipped; // batch entries skipped for out-of-range indices
+    int32_t beff;               // rows of the current batch
+    int32_t pad;
+};
+struct NcfGatherArgs {
+    NcfCtl *ctl;
+    int64_t nnz, spe, m, n;     // entries, steps per epoch, applications, settings
+    int B;                      // batch capacity (multiple of 64)
+    const int32_t *perms;       // [epochs][nnz] visiting orders, or NULL (entries in order)
+    const int32_t *app, *set;   // [nnz] indices of the observed entries
+    const float *val;           // [nnz]
+    const float *Ea, *Es;       // FP32 embedding tables [m][32], [n][32]
+    unsigned char *X;           // bf16 [B][64]
+    float *r;                   // [B]
+    int32_t *ri, *rj;           // [B] (-1: absent row)
+};
+struct NcfHeadArgs {
+    const NcfCtl *ctl;
+    const unsigned char *H2, *Z2;   // bf16 [B][64]
+    unsigned char *dZ2;             // bf16 [B][64]
+    const float *r;
+    const int32_t *ri;
+    const float *w3, *b3;           // FP32 master parameters
+    float *part;                    // [B/64][129]: gb2 | gw3 | gb3
+    float *lpart;                   // [B/64] sums of squared residuals
+    float *y;                       // [B] predictions, or NULL
+};
+struct NcfPredArgs {
+    int64_t m, n;
+    const float *A;                 // [m][128] Ea W1[0:32] + b1
+    const float *S;                 // [n][128] Es W1[32:64]
+    const void *w2img;              // W2 as a UMMA operand image (16 KB)
+    const float *b2, *w3, *b3;
+    float *T;                       // [m][n]
+    int *err;                       // set to 1 if a tensor-core wait ran out
+};
+cudaError_t launch_ncf_gather(const NcfGatherArgs &a, cudaStream_t st);
+cudaError_t launch_ncf_head(const NcfHeadArgs &a, int B, cudaStream_t st);
+cudaError_t launch_ncf_step_end(NcfCtl *ctl, int parts, const float *lpart, double *loss_hist,
+                                double *loss_last, cudaStream_t st);
+cudaError_t launch_ncf_first_layer(int64_t rows, const float *E, const float *W, const float *bias,
+                                   float *out, cudaStream_t st);
+cudaError_t launch_ncf_w2_image(const float *W2, void *img, cudaStream_t st);
+cudaError_t prepare_ncf_predict_tc();
+cudaError_t launch_ncf_predict_tc(const NcfPredArgs &a, int num_sms, cudaStream_t st);
 
 }  // namespace ocf

@@ -177,6 +177,14 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
                 } else if (EPI == EPI_DSELU) {
                     const bf16 zb = reinterpret_cast<const bf16 *>(g.Zin)[o];
                     reinterpret_cast<bf16 *>(g.out_bf)[o] = __float2bfloat16_rn(v * dselu(__bfloat162float(zb)));
+                } else if (EPI == EPI_SCATTER) {   // rows of dX into two gradient tables
+                    const int half = g.N >> 1;
+                    const bool lo = c < half;
+                    const int32_t row = lo ? g.ri[r] : g.rj[r];
+                    if (row >= 0)
+                        atomicAdd(g.out_f + (lo ? 0 : g.s_off) + (int64_t)row * half +
+                                      (lo ? c : c - half),
+                                  v);
                 } else {   // EPI_PART: split-K partial
                     g.out_f[(int64_t)blockIdx.z * g.M * g.N + (int64_t)r * g.N + c] = v;
                 }
@@ -197,6 +205,8 @@ cudaError_t launch_gemm(const GemmArgs &g, bool at, bool bt, int epi, int splits
     if (!at && !bt && epi == EPI_BIAS) return gemm<false, false, EPI_BIAS>(g, splits, st);
     if (!at && bt && epi == EPI_DSELU) return gemm<false, true, EPI_DSELU>(g, splits, st);
     if (at && !bt && epi == EPI_PART) return gemm<true, false, EPI_PART>(g, splits, st);
+    if (!at && bt && epi == EPI_SCATTER && splits == 1 && g.N % 2 == 0)
+        return gemm<false, true, EPI_SCATTER>(g, 1, st);
     return cudaErrorInvalidValue;
 }
 
@@ -308,7 +318,7 @@ __global__ void k_adam(int64_t count, float *__restrict__ th, const float *__res
         const float t = th[e] - lr * (a / c1) / (sqrtf(b / c2) + eps);
         th[e] = t;
         const bf16 tb = __float2bfloat16_rn(t);
-        const int64_t q = bf_map[e], qi = img_map[e];
+        const int64_t q = bf_map ? bf_map[e] : -1, qi = img_map ? img_map[e] : -1;
         if (q >= 0) thb[q] = tb;
         if (qi >= 0) img[qi] = tb;
     }
@@ -320,7 +330,7 @@ __global__ void k_to_bf16_map(int64_t count, const float *__restrict__ th,
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
          e += (int64_t)gridDim.x * blockDim.x) {
         const bf16 tb = __float2bfloat16_rn(th[e]);
-        const int64_t q = bf_map[e], qi = img_map[e];
+        const int64_t q = bf_map ? bf_map[e] : -1, qi = img_map ? img_map[e] : -1;
         if (q >= 0) thb[q] = tb;
         if (qi >= 0) img[qi] = tb;
     }
@@ -403,6 +413,21 @@ cudaError_t launch_adam(int64_t count, float *th, const float *g, float *m1, flo
     k_adam<<<gfor(count), 256, 0, st>>>(count, th, g, m1, m2, b1, b2, eps, as, bf_map,
                                         reinterpret_cast<bf16 *>(thb), img_map,
                                         reinterpret_cast<bf16 *>(img));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_tick(void *state, cudaStream_t st) {
+    k_adam_tick<<<1, 1, 0, st>>>(reinterpret_cast<AdamState *>(state));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_update(int64_t count, float *th, const float *g, float *m1, float *m2,
+                               float b1, float b2, float eps, const void *state,
+                               const int64_t *bf_map, void *thb, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_adam<<<gfor(count), 256, 0, st>>>(count, th, g, m1, m2, b1, b2, eps,
+                                        reinterpret_cast<const AdamState *>(state), bf_map,
+                                        reinterpret_cast<bf16 *>(thb), nullptr, nullptr);
     return cudaGetLastError();
 }
 

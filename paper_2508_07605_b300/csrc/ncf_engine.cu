@@ -1,0 +1,459 @@
+// Engine behind the NCF C ABI (open_cf_ncf.h): the handle owns the FP32
+// parameters, gradients and Adam moments of the model (one packed vector
+// [net | Ea | Es] so that one update kernel covers all of them), the BF16
+// copies of W1 and W2 the GEMMs read, and every batch workspace, all
+// allocated at creation.  A training step is captured once into a CUDA graph
+// and replayed for every step of every epoch: its kernels take their batch
+// position from a device-side counter.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "open_cf_ncf.h"
+
+using namespace ocf;
+
+namespace {
+
+constexpr int64_t NET_PAD = (NCF_NET + 3) / 4 * 4;   // embeddings start 16-byte aligned
+static_assert(NCF_NET == OPEN_CF_NCF_NET, "network size");
+
+struct NBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct StepGraph {
+    std::vector<int64_t> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct open_cf_ncf {
+    int device = 0, num_sms = 0;
+    int64_t m = 0, n = 0;
+    int B = 0, splits = 1;
+    std::vector<double> cpu, gpu;
+    int64_t base_default = 0;
+    bool params_set = false;
+    NBuf theta, grad, m1, m2, bf, bfmap, adam, ctl, loss1;
+    NBuf X, r, ri, rj, Z1, H1, dZ1, Z2, H2, dZ2, hpart, lpart, wpart, cpart;
+    NBuf A, S, w2img, T, cg, err;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<StepGraph> graphs;
+    std::string msg;
+};
+
+namespace {
+
+struct Guard {
+    int prev = -1;
+    explicit Guard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~Guard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int nfail(open_cf_ncf_t *h, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->msg = buf;
+    return code;
+}
+
+int ncuda(open_cf_ncf_t *h, cudaError_t e, const char *where) {
+    cudaGetLastError();
+    return nfail(h, e == cudaErrorMemoryAllocation ? OPEN_CF_OUT_OF_MEMORY : OPEN_CF_CUDA_ERROR,
+                 "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define NCK(h, expr)                                          \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return ncuda((h), e_, #expr);  \
+    } while (0)
+
+cudaError_t alloc(NBuf &b, size_t bytes) {
+    b.bytes = std::max<size_t>(bytes, 256);
+    return cudaMalloc(&b.p, b.bytes);
+}
+
+void release(NBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+cudaStream_t SS(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+float *F(NBuf &b) { return reinterpret_cast<float *>(b.p); }
+
+int64_t n_emb(const open_cf_ncf_t *h) { return (h->m + h->n) * NCF_D; }
+
+// Forward, loss and backward of one batch; with `update`, one Adam step.
+cudaError_t enqueue_step(open_cf_ncf_t *h, int64_t nnz, int64_t spe, const int32_t *app,
+                         const int32_t *set, const float *val, const int32_t *perms,
+                         double *loss_hist, bool update, cudaStream_t st) {
+    const int B = h->B;
+    float *th = F(h->theta), *g = F(h->grad);
+    const float *Ea = th + NET_PAD, *Es = Ea + h->m * NCF_D;
+    const void *W1b = h->bf.p;
+    const void *W2b = reinterpret_cast<const char *>(h->bf.p) + 2 * NCF_OFF_B1;
+    NcfCtl *ctl = reinterpret_cast<NcfCtl *>(h->ctl.p);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(g + NET_PAD, 0, sizeof(float) * n_emb(h), st)) != cudaSuccess) return e;
+    NcfGatherArgs ga{ctl, nnz, spe, h->m, h->n, B, perms, app, set, val, Ea, Es,
+                     reinterpret_cast<unsigned char *>(h->X.p), F(h->r), (int32_t *)h->ri.p,
+                     (int32_t *)h->rj.p};
+    if ((e = launch_ncf_gather(ga, st)) != cudaSuccess) return e;
+    GemmArgs f1{};   // z1 = x W1 + b1, h1 = SELU(z1)
+    f1.M = B; f1.N = NCF_H1; f1.K = 2 * NCF_D;
+    f1.A = h->X.p; f1.lda = 2 * NCF_D; f1.B = W1b; f1.ldb = NCF_H1;
+    f1.bias = th + NCF_OFF_B1; f1.out_z = h->Z1.p; f1.out_bf = h->H1.p; f1.ldo = NCF_H1;
+    if ((e = launch_gemm(f1, false, false, EPI_BIAS_SELU, 1, st)) != cudaSuccess) return e;
+    GemmArgs f2{};   // z2 = h1 W2 + b2, h2 = SELU(z2)
+    f2.M = B; f2.N = NCF_H2; f2.K = NCF_H1;
+    f2.A = h->H1.p; f2.lda = NCF_H1; f2.B = W2b; f2.ldb = NCF_H2;
+    f2.bias = th + NCF_OFF_B2; f2.out_z = h->Z2.p; f2.out_bf = h->H2.p; f2.ldo = NCF_H2;
+    if ((e = launch_gemm(f2, false, false, EPI_BIAS_SELU, 1, st)) != cudaSuccess) return e;
+    NcfHeadArgs ha{ctl, reinterpret_cast<const unsigned char *>(h->H2.p),
+                   reinterpret_cast<const unsigned char *>(h->Z2.p),
+                   reinterpret_cast<unsigned char *>(h->dZ2.p), F(h->r), (const int32_t *)h->ri.p,
+                   th + NCF_OFF_W3, th + NCF_OFF_B3, F(h->hpart), F(h->lpart), nullptr};
+    if ((e = launch_ncf_head(ha, B, st)) != cudaSuccess) return e;
+    if ((e = launch_sum_parts(2 * NCF_H2 + 1, B / 64, F(h->hpart), g + NCF_OFF_B2, st)) !=
+        cudaSuccess)
+        return e;   // gb2 | gw3 | gb3 are contiguous in the packing
+    GemmArgs w2{};   // dW2 = h1^T dz2
+    w2.M = NCF_H1; w2.N = NCF_H2; w2.K = B;
+    w2.A = h->H1.p; w2.lda = NCF_H1; w2.B = h->dZ2.p; w2.ldb = NCF_H2; w2.out_f = F(h->wpart);
+    if ((e = launch_gemm(w2, true, false, EPI_PART, h->splits, st)) != cudaSuccess) return e;
+    if ((e = launch_sum_parts(NCF_H1 * NCF_H2, h->splits, F(h->wpart), g + NCF_OFF_W2, st)) !=
+        cudaSuccess)
+        return e;
+    GemmArgs d1{};   // dz1 = (dz2 W2^T) * SELU'(z1)
+    d1.M = B; d1.N = NCF_H1; d1.K = NCF_H2;
+    d1.A = h->dZ2.p; d1.lda = NCF_H2; d1.B = W2b; d1.ldb = NCF_H2;
+    d1.Zin = h->Z1.p; d1.out_bf = h->dZ1.p; d1.ldo = NCF_H1;
+    if ((e = launch_gemm(d1, false, true, EPI_DSELU, 1, st)) != cudaSuccess) return e;
+    GemmArgs w1{};   // dW1 = x^T dz1
+    w1.M = 2 * NCF_D; w1.N = NCF_H1; w1.K = B;
+    w1.A = h->X.p; w1.lda = 2 * NCF_D; w1.B = h->dZ1.p; w1.ldb = NCF_H1; w1.out_f = F(h->wpart);
+    if ((e = launch_gemm(w1, true, false, EPI_PART, h->splits, st)) != cudaSuccess) return e;
+    if ((e = launch_sum_parts(2 * NCF_D * NCF_H1, h->splits, F(h->wpart), g, st)) != cudaSuccess)
+        return e;
+    if ((e = launch_colsum(B, NCF_H1, h->dZ1.p, F(h->cpart), g + NCF_OFF_B1, st)) != cudaSuccess)
+        return e;
+    GemmArgs dx{};   // dx = dz1 W1^T, scattered into the embedding gradients
+    dx.M = B; dx.N = 2 * NCF_D; dx.K = NCF_H1;
+    dx.A = h->dZ1.p; dx.lda = NCF_H1; dx.B = W1b; dx.ldb = NCF_H1;
+    dx.out_f = g + NET_PAD; dx.ri = (const int32_t *)h->ri.p; dx.rj = (const int32_t *)h->rj.p;
+    dx.s_off = h->m * NCF_D;
+    if ((e = launch_gemm(dx, false, true, EPI_SCATTER, 1, st)) != cudaSuccess) return e;
+    if ((e = launch_ncf_step_end(ctl, B / 64, F(h->lpart), loss_hist, (double *)h->loss1.p, st)) !=
+        cudaSuccess)
+        return e;
+    if (!update) return cudaSuccess;
+    if ((e = launch_adam_tick(h->adam.p, st)) != cudaSuccess) return e;
+    if ((e = launch_adam_update(NCF_NET, th, g, F(h->m1), F(h->m2), 0.9f, 0.999f, 1e-8f,
+                                h->adam.p, (const int64_t *)h->bfmap.p, h->bf.p, st)) !=
+        cudaSuccess)
+        return e;
+    return launch_adam_update(n_emb(h), th + NET_PAD, g + NET_PAD, F(h->m1) + NET_PAD,
+                              F(h->m2) + NET_PAD, 0.9f, 0.999f, 1e-8f, h->adam.p, nullptr,
+                              nullptr, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int open_cf_ncf_create(int64_t m, int32_t n_cpu, const double *cpu_caps_w_host, int32_t n_gpu,
+                       const double *gpu_caps_w_host, int32_t batch, int device,
+                       open_cf_ncf_t **out) {
+    if (!out) return OPEN_CF_INVALID_ARG;
+    *out = nullptr;
+    if (m < 1 || m > (int64_t)1 << 31 || n_cpu < 1 || n_gpu < 1 || !cpu_caps_w_host ||
+        !gpu_caps_w_host || (int64_t)n_cpu * n_gpu > (int64_t)1 << 24)
+        return OPEN_CF_INVALID_ARG;
+    if (batch < 64 || batch > 65536 || batch % 64) return OPEN_CF_INVALID_ARG;
+    for (int c = 0; c < n_cpu; ++c)
+        if (!std::isfinite(cpu_caps_w_host[c])) return OPEN_CF_INVALID_ARG;
+    for (int c = 0; c < n_gpu; ++c)
+        if (!std::isfinite(gpu_caps_w_host[c])) return OPEN_CF_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return OPEN_CF_INVALID_ARG;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return OPEN_CF_CUDA_ERROR;
+    if (!(prop.major == 10 && prop.minor == 3)) return OPEN_CF_UNSUPPORTED;
+    open_cf_ncf_t *h = new open_cf_ncf();
+    h->device = device;
+    h->m = m;
+    h->n = (int64_t)n_cpu * n_gpu;
+    h->B = batch;
+    h->cpu.assign(cpu_caps_w_host, cpu_caps_w_host + n_cpu);
+    h->gpu.assign(gpu_caps_w_host, gpu_caps_w_host + n_gpu);
+    const int64_t ci = std::max_element(h->cpu.begin(), h->cpu.end()) - h->cpu.begin();
+    const int64_t gi = std::max_element(h->gpu.begin(), h->gpu.end()) - h->gpu.begin();
+    h->base_default = ci * n_gpu + gi;
+    // split-K for the two weight gradients: K = batch in slices of >= 128 rows
+    for (int s = 16; s >= 1; --s)
+        if (batch % (32 * s) == 0 && (s == 1 || batch / s >= 128)) {
+            h->splits = s;
+            break;
+        }
+    Guard gd(device);
+    const int64_t P = NET_PAD + n_emb(h);
+    const size_t fB = sizeof(float) * (size_t)batch, hB = 2 * (size_t)batch;
+    std::vector<float> cg(h->n);
+    std::vector<int64_t> map(NET_PAD, -1);
+    for (int64_t e = 0; e < NCF_OFF_B1; ++e) map[e] = e;   // W1 -> bf[0, 8192)
+    for (int64_t e = 0; e < NCF_H1 * NCF_H2; ++e) map[NCF_OFF_W2 + e] = NCF_OFF_B1 + e;   // W2
+    for (int64_t j = 0; j < h->n; ++j)
+        cg[j] = (float)h->cpu[j / n_gpu] + (float)h->gpu[j % n_gpu];
+    cudaError_t e = cudaSuccess;
+    auto A = [&](NBuf &b, size_t bytes) {
+        if (e == cudaSuccess) e = alloc(b, bytes);
+    };
+    A(h->theta, sizeof(float) * P); A(h->grad, sizeof(float) * P);
+    A(h->m1, sizeof(float) * P); A(h->m2, sizeof(float) * P);
+    A(h->bf, 2 * 2 * NCF_OFF_B1); A(h->bfmap, sizeof(int64_t) * NET_PAD);
+    A(h->adam, 16); A(h->ctl, sizeof(NcfCtl)); A(h->loss1, sizeof(double));
+    A(h->X, hB * 2 * NCF_D); A(h->r, fB); A(h->ri, fB); A(h->rj, fB);
+    A(h->Z1, hB * NCF_H1); A(h->H1, hB * NCF_H1); A(h->dZ1, hB * NCF_H1);
+    A(h->Z2, hB * NCF_H2); A(h->H2, hB * NCF_H2); A(h->dZ2, hB * NCF_H2);
+    A(h->hpart, sizeof(float) * (batch / 64) * (2 * NCF_H2 + 1)); A(h->lpart, fB / 64);
+    A(h->wpart, sizeof(float) * h->splits * NCF_H1 * NCF_H2);
+    A(h->cpart, sizeof(float) * ((batch + 127) / 128) * NCF_H1);
+    A(h->A, sizeof(float) * m * NCF_H1); A(h->S, sizeof(float) * h->n * NCF_H1);
+    A(h->w2img, 2 * NCF_H1 * NCF_H2); A(h->cg, sizeof(float) * h->n); A(h->err, 16);
+    if (e == cudaSuccess) e = cudaMemcpy(h->bfmap.p, map.data(), sizeof(int64_t) * NET_PAD,
+                                         cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->cg.p, cg.data(), sizeof(float) * h->n,
+                                         cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->err.p, 0, 16);
+    if (e == cudaSuccess) e = cudaMemset(h->ctl.p, 0, sizeof(NcfCtl));
+    if (e == cudaSuccess) e = prepare_ncf_predict_tc();
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        open_cf_ncf_destroy(h);
+        return e == cudaErrorMemoryAllocation ? OPEN_CF_OUT_OF_MEMORY : OPEN_CF_CUDA_ERROR;
+    }
+    *out = h;
+    return OPEN_CF_OK;
+}
+
+void open_cf_ncf_destroy(open_cf_ncf_t *h) {
+    if (!h) return;
+    {
+        Guard gd(h->device);
+        cudaDeviceSynchronize();
+        for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+        for (NBuf *b : {&h->theta, &h->grad, &h->m1, &h->m2, &h->bf, &h->bfmap, &h->adam, &h->ctl,
+                        &h->loss1, &h->X, &h->r, &h->ri, &h->rj, &h->Z1, &h->H1, &h->dZ1, &h->Z2,
+                        &h->H2, &h->dZ2, &h->hpart, &h->lpart, &h->wpart, &h->cpart, &h->A, &h->S,
+                        &h->w2img, &h->T, &h->cg, &h->err})
+            release(*b);
+    }
+    delete h;
+}
+
+const char *open_cf_ncf_last_error(const open_cf_ncf_t *h) { return h ? h->msg.c_str() : ""; }
+
+int open_cf_ncf_set_params(open_cf_ncf_t *h, const float *net, const float *Ea, const float *Es,
+                           void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!net || !Ea || !Es) return nfail(h, OPEN_CF_INVALID_ARG, "net, Ea and Es are required");
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    float *th = F(h->theta);
+    const int64_t P = NET_PAD + n_emb(h);
+    NCK(h, cudaMemsetAsync(th, 0, sizeof(float) * NET_PAD, st));
+    NCK(h, cudaMemcpyAsync(th, net, sizeof(float) * NCF_NET, cudaMemcpyDeviceToDevice, st));
+    NCK(h, cudaMemcpyAsync(th + NET_PAD, Ea, sizeof(float) * h->m * NCF_D,
+                           cudaMemcpyDeviceToDevice, st));
+    NCK(h, cudaMemcpyAsync(th + NET_PAD + h->m * NCF_D, Es, sizeof(float) * h->n * NCF_D,
+                           cudaMemcpyDeviceToDevice, st));
+    NCK(h, cudaMemsetAsync(h->m1.p, 0, sizeof(float) * P, st));
+    NCK(h, cudaMemsetAsync(h->m2.p, 0, sizeof(float) * P, st));
+    NCK(h, cudaMemsetAsync(h->adam.p, 0, 16, st));
+    NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(NcfCtl), st));
+    NCK(h, launch_to_bf16_map(NET_PAD, th, (const int64_t *)h->bfmap.p, h->bf.p, nullptr, nullptr,
+                              st));
+    h->params_set = true;
+    return OPEN_CF_OK;
+}
+
+int open_cf_ncf_get_params(open_cf_ncf_t *h, float *net, float *Ea, float *Es, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    const float *th = F(h->theta);
+    if (net) NCK(h, cudaMemcpyAsync(net, th, sizeof(float) * NCF_NET, cudaMemcpyDeviceToDevice, st));
+    if (Ea)
+        NCK(h, cudaMemcpyAsync(Ea, th + NET_PAD, sizeof(float) * h->m * NCF_D,
+                               cudaMemcpyDeviceToDevice, st));
+    if (Es)
+        NCK(h, cudaMemcpyAsync(Es, th + NET_PAD + h->m * NCF_D, sizeof(float) * h->n * NCF_D,
+                               cudaMemcpyDeviceToDevice, st));
+    return OPEN_CF_OK;
+}
+
+int open_cf_ncf_train(open_cf_ncf_t *h, int64_t nnz, const int32_t *app, const int32_t *setting,
+                      const float *val, int32_t epochs, const int32_t *perms, float lr,
+                      double *loss_out, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
+    if (nnz < 1 || nnz > INT32_MAX || epochs < 0 || !app || !setting || !val ||
+        (epochs > 0 && !perms))
+        return nfail(h, OPEN_CF_INVALID_ARG, "bad nnz, epochs or array");
+    if (!(lr >= 0.0f) || !std::isfinite(lr)) return nfail(h, OPEN_CF_INVALID_ARG, "bad lr");
+    if (epochs == 0) return OPEN_CF_OK;
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    const int64_t spe = (nnz + h->B - 1) / h->B, steps = spe * epochs;
+    NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(int64_t), st));   // step = 0
+    NCK(h, launch_adam_set_lr(h->adam.p, lr, st));
+    std::vector<int64_t> key{nnz, spe, (int64_t)app, (int64_t)setting, (int64_t)val,
+                             (int64_t)perms, (int64_t)loss_out};
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : h->graphs)
+        if (g.key == key) exec = g.exec;
+    if (!exec) {
+        NCK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_step(h, nnz, spe, app, setting, val, perms, loss_out, true,
+                                     h->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return ncuda(h, e, "training step capture");
+        }
+        if (e2 != cudaSuccess) return ncuda(h, e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return ncuda(h, e, "cudaGraphInstantiate");
+        if (h->graphs.size() >= 8) {
+            cudaGraphExecDestroy(h->graphs.front().exec);
+            h->graphs.erase(h->graphs.begin());
+        }
+        h->graphs.push_back(StepGraph{key, exec});
+    }
+    for (int64_t s = 0; s < steps; ++s) NCK(h, cudaGraphLaunch(exec, st));
+    return OPEN_CF_OK;
+}
+
+int open_cf_ncf_grad(open_cf_ncf_t *h, int64_t B, const int32_t *app, const int32_t *setting,
+                     const float *val, double *loss_out, float *g_net, float *g_Ea, float *g_Es,
+                     void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
+    if (B < 1 || B > h->B || !app || !setting || !val)
+        return nfail(h, OPEN_CF_INVALID_ARG, "B must be in [1, batch] and the arrays given");
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(int64_t), st));
+    NCK(h, enqueue_step(h, B, 1, app, setting, val, nullptr, nullptr, false, st));
+    const float *g = F(h->grad);
+    if (loss_out)
+        NCK(h, cudaMemcpyAsync(loss_out, h->loss1.p, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (g_net)
+        NCK(h, cudaMemcpyAsync(g_net, g, sizeof(float) * NCF_NET, cudaMemcpyDeviceToDevice, st));
+    if (g_Ea)
+        NCK(h, cudaMemcpyAsync(g_Ea, g + NET_PAD, sizeof(float) * h->m * NCF_D,
+                               cudaMemcpyDeviceToDevice, st));
+    if (g_Es)
+        NCK(h, cudaMemcpyAsync(g_Es, g + NET_PAD + h->m * NCF_D, sizeof(float) * h->n * NCF_D,
+                               cudaMemcpyDeviceToDevice, st));
+    return OPEN_CF_OK;
+}
+
+int open_cf_ncf_predict(open_cf_ncf_t *h, float *T_out, float gamma, int32_t baseline_setting,
+                        int32_t *best, float *saving, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
+    const bool sel = best || saving;
+    if (!sel && !T_out) return OPEN_CF_OK;
+    if (!std::isfinite(gamma)) return nfail(h, OPEN_CF_INVALID_ARG, "gamma is not finite");
+    const int64_t base = baseline_setting < 0 ? h->base_default : baseline_setting;
+    if (base >= h->n) return nfail(h, OPEN_CF_INVALID_ARG, "baseline setting out of range");
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    float *T = T_out;
+    if (!T) {
+        const size_t bytes = sizeof(float) * (size_t)h->m * (size_t)h->n;
+        if (h->T.bytes < bytes) {
+            NCK(h, cudaStreamSynchronize(st));
+            release(h->T);
+            NCK(h, alloc(h->T, bytes));
+        }
+        T = F(h->T);
+    }
+    float *th = F(h->theta);
+    const float *Ea = th + NET_PAD, *Es = Ea + h->m * NCF_D;
+    NCK(h, launch_ncf_w2_image(th + NCF_OFF_W2, h->w2img.p, st));
+    NCK(h, launch_ncf_first_layer(h->m, Ea, th, th + NCF_OFF_B1, F(h->A), st));
+    NCK(h, launch_ncf_first_layer(h->n, Es, th + NCF_D * NCF_H1, nullptr, F(h->S), st));
+    NcfPredArgs a{h->m, h->n, F(h->A), F(h->S), h->w2img.p, th + NCF_OFF_B2, th + NCF_OFF_W3,
+                  th + NCF_OFF_B3, T, (int *)h->err.p};
+    NCK(h, launch_ncf_predict_tc(a, h->num_sms, st));
+    if (sel) {
+        const int ng = (int)h->gpu.size();
+        const float Eb = (float)h->cpu[base / ng] + (float)h->gpu[base % ng];
+        NCK(h, launch_select(h->m, h->n, T, h->n, F(h->cg), base, Eb, gamma, best, saving, st));
+    }
+    return OPEN_CF_OK;
+}
+
+int open_cf_ncf_skipped(open_cf_ncf_t *h, int64_t *count_host) {
+    if (!h || !count_host) return OPEN_CF_INVALID_ARG;
+    Guard gd(h->device);
+    NcfCtl c{};
+    NCK(h, cudaDeviceSynchronize());
+    NCK(h, cudaMemcpy(&c, h->ctl.p, sizeof(NcfCtl), cudaMemcpyDeviceToHost));
+    *count_host = (int64_t)c.skipped;
+    return OPEN_CF_OK;
+}
+
+int open_cf_ncf_check(open_cf_ncf_t *h) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    Guard gd(h->device);
+    int flag = 0;
+    NCK(h, cudaDeviceSynchronize());
+    NCK(h, cudaMemcpy(&flag, h->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        NCK(h, cudaMemset(h->err.p, 0, 16));
+        return nfail(h, OPEN_CF_TIMEOUT, "a completion kernel gave up on a tensor-core wait");
+    }
+    return OPEN_CF_OK;
+}
+
+}  // extern "C"

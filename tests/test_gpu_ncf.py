@@ -1,0 +1,245 @@
+"""GPU-vs-oracle parity of neural collaborative filtering (the paper's CF
+model) through the C ABI: the batch gradient (every parameter group, the
+embedding rows included), one Adam step, training end to end against the
+oracle's training on the same initial parameters and visiting orders, and
+the completed matrix with Algorithm 2 on it.
+
+Tolerances.  Products run on BF16 operands (unit roundoff 2^-9) with FP32
+accumulation.  Gradients: per-group relative Frobenius error <= 2e-2 against
+the FP64 oracle fed the same FP32 parameters; 4e-2 for the embedding rows,
+whose gradient is a fourth chained BF16 contraction (dz2, W2, dz1 and W1 all
+rounded) summing 128 terms of mixed sign.  Completed entries: |y_gpu -
+y_ref| <= 2e-2 * (sum_c |w3_c selu(z2_c)| + |b3|), the magnitude of the terms
+the output sums.  Algorithm 2 decides on the GPU's own FP32 T, so its choice
+is compared bit for bit with the oracle's FP32 selection on that T.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+from gpu_util import DEV, dev, host
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU hosts deselect these
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2508_07605_b300 as ocf  # noqa: E402
+
+H1, H2 = ocf.NCF_H1, ocf.NCF_H2
+TOL_GRAD, TOL_EMB = 2e-2, 4e-2
+SELU_L, SELU_A = 1.0507009873554804934193349852946, 1.6732632423543772848170429916717
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _params(seed, m, n, emb=0.5, out=1.0):
+    rng = np.random.default_rng(seed)
+    net, Ea, Es = synth.ncf_init(rng, m, n, emb_scale=emb, out_scale=out)
+    net = net + 0.05 * rng.standard_normal(net.shape)   # non-zero biases
+    return _f32(net), _f32(Ea), _f32(Es)
+
+
+def _handle(m, ncpu, ngpu, batch, params):
+    cpu, gpu = synth.cap_grid(ncpu, ngpu)
+    h = ocf.NCF(m, cpu, gpu, batch=batch)
+    net, Ea, Es = params
+    h.set_params(dev(net, torch.float32), dev(Ea, torch.float32), dev(Es, torch.float32))
+    return h, cpu, gpu
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("batch,B", [(512, 512), (512, 300), (1024, 1024), (64, 17)])
+def test_ncf_gradient_matches_oracle(orc, batch, B):
+    m, ncpu, ngpu = 300, 8, 16
+    n = ncpu * ngpu
+    params = _params(1, m, n)
+    rng = np.random.default_rng(2)
+    ai = rng.integers(0, m, B).astype(np.int32)
+    sj = rng.integers(0, n, B).astype(np.int32)
+    r = _f32(rng.random(B))
+    h, _, _ = _handle(m, ncpu, ngpu, batch, params)
+    loss, gn, ga, gs = h.grad(dev(ai, torch.int32), dev(sj, torch.int32), dev(r, torch.float32))
+    torch.cuda.synchronize()
+    L, rn, ra, rs = orc.ncf_loss_grad(ai, sj, r, params[1], params[2], params[0], H1, H2)
+    assert abs(host(loss)[0] - L) <= 1e-2 * L
+    gn = host(gn)
+    w1, b1, w2 = 64 * H1, 64 * H1 + H1, 64 * H1 + H1 + H1 * H2
+    # W1 | b1 | W2 | b2 + w3 + b3 (the head's three small groups together)
+    for a0, a1 in [(0, w1), (w1, b1), (b1, w2), (w2, ocf.NCF_NET)]:
+        assert _rel(gn[a0:a1], rn[a0:a1]) <= TOL_GRAD, (a0, a1, _rel(gn[a0:a1], rn[a0:a1]))
+    assert _rel(host(ga), ra) <= TOL_EMB, _rel(host(ga), ra)
+    assert _rel(host(gs), rs) <= TOL_EMB, _rel(host(gs), rs)
+    # rows of indices absent from the batch receive exactly nothing
+    absent = np.setdiff1d(np.arange(m), ai)
+    assert np.all(host(ga)[absent] == 0)
+    assert h.skipped() == 0
+    h.close()
+
+
+def test_ncf_out_of_range_entries_are_skipped(orc):
+    m, ncpu, ngpu, B = 200, 4, 16, 256
+    n = ncpu * ngpu
+    params = _params(3, m, n)
+    rng = np.random.default_rng(4)
+    ai = rng.integers(0, m, B).astype(np.int32)
+    sj = rng.integers(0, n, B).astype(np.int32)
+    r = _f32(rng.random(B))
+    bad = np.array([5, 77, 200])
+    ai[bad[0]] = m           # application out of range
+    sj[bad[1]] = -1          # setting out of range
+    sj[bad[2]] = n + 3
+    h, _, _ = _handle(m, ncpu, ngpu, B, params)
+    loss, gn, ga, gs = h.grad(dev(ai, torch.int32), dev(sj, torch.int32), dev(r, torch.float32))
+    torch.cuda.synchronize()
+    keep = np.setdiff1d(np.arange(B), bad)
+    L, rn, ra, rs = orc.ncf_loss_grad(ai[keep], sj[keep], r[keep], params[1], params[2],
+                                      params[0], H1, H2)
+    scale = len(keep) / B          # the GPU's mean still counts the skipped entries
+    assert abs(host(loss)[0] - L * scale) <= 1e-2 * L * scale
+    assert _rel(host(gn), rn * scale) <= TOL_GRAD
+    assert _rel(host(ga), ra * scale) <= TOL_EMB
+    assert h.skipped() == 3
+    h.close()
+
+
+def test_ncf_adam_step_matches_oracle_on_the_gpu_gradient(orc):
+    m, ncpu, ngpu, B = 150, 4, 8, 256
+    n = ncpu * ngpu
+    params = _params(5, m, n)
+    rng = np.random.default_rng(6)
+    ai = dev(rng.integers(0, m, B).astype(np.int32), torch.int32)
+    sj = dev(rng.integers(0, n, B).astype(np.int32), torch.int32)
+    r = dev(_f32(rng.random(B)), torch.float32)
+    h, _, _ = _handle(m, ncpu, ngpu, B, params)
+    _, gn, ga, gs = h.grad(ai, sj, r)
+    perm = torch.arange(B, dtype=torch.int32, device=DEV).reshape(1, B)
+    lr = 1e-3
+    h.train(ai, sj, r, perm, lr)
+    net1, Ea1, Es1 = h.get_params()
+    torch.cuda.synchronize()
+    theta = np.concatenate([p.ravel() for p in params])
+    g = np.concatenate([host(gn), host(ga).ravel(), host(gs).ravel()]).astype(np.float64)
+    m1 = np.zeros_like(theta); m2 = np.zeros_like(theta)
+    ref = theta.copy()
+    orc.adam(ref, g, m1, m2, 1, lr=lr)
+    got = np.concatenate([host(net1), host(Ea1).ravel(), host(Es1).ravel()]).astype(np.float64)
+    # first Adam step: lr * g / (|g| + eps) per entry; FP32 rounding of theta
+    # and of the (re-computed, atomically accumulated) gradient near g = 0
+    assert np.abs(got - ref).max() <= 1e-6 + 1e-3 * lr
+    moved = np.abs(got - theta) > 0.5 * lr
+    assert moved.mean() > 0.05     # the step did move the parameters it should
+    h.close()
+
+
+def test_ncf_training_tracks_the_oracle(orc):
+    prob = synth.make_sparse_problem(seed=3, m=200, n_cpu=4, n_gpu=16, rank=4, density=0.3, k=4,
+                                     lam=0.05, n_heldout=2000)
+    ai, sj = synth.coo_from_csr(prob.row_ptr, prob.col)
+    val = _f32(prob.val)
+    rng = np.random.default_rng(0)
+    net, Ea, Es = synth.ncf_init(rng, prob.m, prob.n)
+    params = (_f32(net), _f32(Ea), _f32(Es))
+    epochs, batch, lr = 12, 256, 3e-3
+    perms = synth.ncf_perms(rng, len(ai), epochs)
+    h, _, _ = _handle(prob.m, 4, 16, batch, params)
+    L = h.train(dev(ai, torch.int32), dev(sj, torch.int32), dev(val, torch.float32),
+                dev(np.stack(perms), torch.int32), lr, losses=True)
+    net_g, Ea_g, Es_g = h.get_params()
+    torch.cuda.synchronize()
+    net_o, Ea_o, Es_o, L_o = orc.ncf_train(ai, sj, val, params[1], params[2], params[0], H1, H2,
+                                           perms, batch, lr)
+    Lg = host(L)
+    assert len(Lg) == len(L_o)
+    # the first steps agree closely; the trajectories then drift (BF16 vs FP64)
+    assert np.abs(Lg[:5] - L_o[:5]).max() <= 2e-2 * L_o[:5].max()
+    assert Lg[-20:].mean() <= 1.2 * L_o[-20:].mean() + 1e-4
+    yg = orc.ncf_forward(prob.heldout_rows, prob.heldout_cols, host(Ea_g), host(Es_g),
+                         host(net_g), H1, H2)
+    yo = orc.ncf_forward(prob.heldout_rows, prob.heldout_cols, Ea_o, Es_o, net_o, H1, H2)
+    rg = np.sqrt(np.mean((yg - prob.heldout_truth) ** 2))
+    ro = np.sqrt(np.mean((yo - prob.heldout_truth) ** 2))
+    assert rg <= 1.15 * ro + 2e-3, (rg, ro)
+    h.close()
+
+
+def _pred_scale(orc, params, m, n):
+    net, Ea, Es = params
+    ai, sj = np.divmod(np.arange(m * n), n)
+    y, _, Z2 = orc.ncf_forward(ai.astype(np.int32), sj.astype(np.int32), Ea, Es, net, H1, H2,
+                               keep=True)
+    w3 = net[-1 - H2:-1]
+    h2 = np.where(Z2 > 0, SELU_L * Z2, SELU_L * SELU_A * np.expm1(np.minimum(Z2, 0)))
+    return y.reshape(m, n), (np.abs(h2 * w3).sum(1) + abs(net[-1])).reshape(m, n)
+
+
+@pytest.mark.parametrize("m,ncpu,ngpu", [(37, 16, 20), (700, 16, 20), (5, 1, 7), (1, 4, 32)])
+def test_ncf_completion_and_selection(orc, m, ncpu, ngpu):
+    n = ncpu * ngpu
+    params = _params(7 + m, m, n, emb=0.5, out=0.3)
+    params[0][-1] = 1.0      # b3: runtimes near 1, so Algorithm 2 sees positive entries
+    h, cpu, gpu = _handle(m, ncpu, ngpu, 64, params)
+    T, best, sav = h.predict(gamma=0.05)
+    torch.cuda.synchronize()
+    h.check()
+    Tref, scale = _pred_scale(orc, params, m, n)
+    Tg = host(T).astype(np.float64)
+    assert np.isfinite(Tg).all()
+    err = np.abs(Tg - Tref) / scale
+    assert err.max() <= 2e-2, err.max()
+    b32, s32 = orc.select_f32(host(T), cpu, gpu, 0.05)
+    assert np.array_equal(host(best), b32)
+    assert np.array_equal(host(sav), s32)
+    # T not requested: same decisions
+    _, best2, sav2 = h.predict(gamma=0.05, T=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(best2), b32) and np.array_equal(host(sav2), s32)
+    h.close()
+
+
+def test_ncf_full_size_completion_sampled(orc):
+    # 4096 applications x 1024 settings (16 CPU x 64 GPU caps), the default
+    # workload's shape, in the launch configuration the benchmark times
+    m, ncpu, ngpu = 4096, 16, 64
+    n = ncpu * ngpu
+    params = _params(11, m, n, emb=0.5, out=0.3)
+    params[0][-1] = 1.0
+    h, cpu, gpu = _handle(m, ncpu, ngpu, 1024, params)
+    T, best, _ = h.predict(gamma=0.05)
+    torch.cuda.synchronize()
+    h.check()
+    rows = np.random.default_rng(0).choice(m, 24, replace=False)
+    sub = (params[0], params[1][rows], params[2])
+    Tref, scale = _pred_scale(orc, sub, len(rows), n)
+    err = np.abs(host(T)[rows].astype(np.float64) - Tref) / scale
+    assert err.max() <= 2e-2, err.max()
+    b32, _ = orc.select_f32(host(T), cpu, gpu, 0.05)
+    assert np.array_equal(host(best), b32)
+    h.close()
+
+
+def test_ncf_argument_errors():
+    cpu, gpu = synth.cap_grid(2, 4)
+    with pytest.raises(ocf.OpenCFError) as e:
+        ocf.NCF(10, cpu, gpu, batch=100)            # not a multiple of 64
+    assert e.value.code == ocf.INVALID_ARG
+    h = ocf.NCF(10, cpu, gpu, batch=64)
+    z = torch.zeros(4, dtype=torch.int32, device=DEV)
+    f = torch.zeros(4, dtype=torch.float32, device=DEV)
+    with pytest.raises(ocf.OpenCFError) as e:
+        h.grad(z, z, f)                             # parameters not set
+    assert e.value.code == ocf.NOT_FITTED
+    net, Ea, Es = _params(0, 10, 8)
+    h.set_params(dev(net, torch.float32), dev(Ea, torch.float32), dev(Es, torch.float32))
+    big = torch.zeros(65, dtype=torch.int32, device=DEV)
+    with pytest.raises(ocf.OpenCFError) as e:
+        h.grad(big, big, torch.zeros(65, device=DEV))   # more than one batch
+    assert e.value.code == ocf.INVALID_ARG
+    h.close()
