@@ -977,6 +977,191 @@ def run_gpu_learned(args):
     return 0
 
 
+WORKLOAD_NCF = "NCF (the paper's CF model): 4096 apps x 1024 settings (16x64 caps), rank-16 " \
+               "truth + N(0,0.01) noise, 5% observed; embeddings 2x32, MLP 64-128-64-1 SELU; one " \
+               "epoch of mini-batch Adam (batch 1024) + completion of all 4096 x 1024 entries " \
+               "+ Algorithm 2 (gamma=0.05)"
+EXP_PER_PAIR = 128 + 64   # SELU exponentials per completed entry (both hidden layers)
+
+
+def mufu_peak_gexp(sm_mhz):
+    # 148 SMs x 16 special-function results per clock (ex2) x clock
+    return 148 * 16 * sm_mhz * 1e6 / 1e9
+
+
+def run_gpu_ncf(args):
+    """NCF: one step = one training epoch over the observed entries + the
+    completed matrix + Algorithm 2 for every application."""
+    import torch
+
+    import paper_2508_07605_b300 as ocf
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    prob = synth.make_c2(seed=0)
+    cpu, gpu = prob.caps()
+    m, n = prob.m, prob.n
+    ai, sj = synth.coo_from_csr(prob.row_ptr, prob.col)
+    nnz = len(ai)
+    batch, lr = 1024, 2e-3
+    rng = np.random.default_rng(0)
+    net, Ea, Es = synth.ncf_init(rng, m, n)
+    epochs_total = max(args.warmup, 3) + args.steps
+    perms = np.stack(synth.ncf_perms(rng, nnz, epochs_total))
+    f32, i32 = torch.float32, torch.int32
+    d_ai, d_sj = torch.as_tensor(ai).to(dev), torch.as_tensor(sj).to(dev)
+    d_val = torch.as_tensor(prob.val.astype(np.float32)).to(dev)
+    d_perm = torch.as_tensor(perms).to(dev)
+    h = ocf.NCF(m, cpu, gpu, batch=batch)
+    p0 = [torch.as_tensor(np.asarray(x, np.float32)).to(dev) for x in (net, Ea, Es)]
+    h.set_params(*p0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    epoch_perm = torch.empty_like(d_perm[:1])   # one buffer: one captured training graph
+
+    def step(e):
+        epoch_perm.copy_(d_perm[e:e + 1])
+        h.train(d_ai, d_sj, d_val, epoch_perm, lr)
+        return h.predict(gamma=GAMMA, T=False)
+
+    W = max(args.warmup, 3)
+    for e in range(W):
+        step(e)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_ncf.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                          else "/tmp/clocks_bench_ncf.csv")
+    with clocks:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            _, best, sav = step(W + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_step = total_ms / args.steps / 1e3
+
+    # ---- parts: one training epoch; the completion alone (T written, no selection)
+    reps = 5
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    T = torch.empty(m, n, dtype=f32, device=dev)
+    flush.zero_()
+    e0.record(stream)
+    for r in range(reps):
+        h.train(d_ai, d_sj, d_val, epoch_perm, lr)
+    e1.record(stream)
+    for r in range(reps):
+        T, _, _ = h.predict(gamma=GAMMA, T=True, select=False)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    t_epoch = e0.elapsed_time(e1) / reps / 1e3
+    t_pred = e1.elapsed_time(e2) / reps / 1e3
+    clk = clocks.summary(0)
+    pairs = m * n
+    sm_mhz = clk["sm_mhz"] or 2032.0
+    mufu = mufu_peak_gexp(sm_mhz)
+    gexp = EXP_PER_PAIR * pairs / t_pred / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16_peak = float(peaks.get("bf16_tflops", 1800.0))
+    tflops = 2.0 * NCF_MMA_MACS * pairs / t_pred / 1e12
+
+    # ---- parity on sampled applications, decisions on the GPU's own T
+    import oracle as orc
+    orc.build()
+    Tg, best, sav = h.predict(gamma=GAMMA, T=True)
+    net_g, Ea_g, Es_g = (x.double().cpu().numpy() for x in h.get_params())
+    torch.cuda.synchronize()
+    rows = np.random.default_rng(1).choice(m, 8, replace=False)
+    Tref = orc.ncf_predict(Ea_g[rows], Es_g, net_g, ocf.NCF_H1, ocf.NCF_H2)
+    Th = Tg.cpu().numpy()
+    b32, _ = orc.select_f32(Th, cpu, gpu, GAMMA)
+    ho = orc.ncf_forward(prob.heldout_rows, prob.heldout_cols, Ea_g, Es_g, net_g,
+                         ocf.NCF_H1, ocf.NCF_H2)
+    rmse = float(np.sqrt(np.mean((ho - prob.heldout_truth) ** 2)))
+
+    # ---- end to end: host inputs in, decisions out, through the C ABI
+    pin = lambda a: torch.as_tensor(a).pin_memory()
+    h_ai, h_sj, h_val = pin(ai), pin(sj), pin(prob.val.astype(np.float32))
+    h_perm = pin(perms[-1:])
+    o_best = torch.empty(m, dtype=i32).pin_memory()
+    o_sav = torch.empty(m, dtype=f32).pin_memory()
+    b_ai, b_sj, b_val = torch.empty_like(d_ai), torch.empty_like(d_sj), torch.empty_like(d_val)
+    b_perm = torch.empty_like(d_perm[-1:])
+
+    def e2e_step():
+        b_ai.copy_(h_ai, non_blocking=True); b_sj.copy_(h_sj, non_blocking=True)
+        b_val.copy_(h_val, non_blocking=True); b_perm.copy_(h_perm, non_blocking=True)
+        h.train(b_ai, b_sj, b_val, b_perm, lr)
+        _, b, s_ = h.predict(gamma=GAMMA, T=False)
+        o_best.copy_(b, non_blocking=True); o_sav.copy_(s_, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ee[i][0].record(stream)
+        e2e_step()
+        ee[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
+
+    # ---- CPU baseline: the oracle's training and completion on a bounded sample
+    tr = 8 * batch
+    t0 = time.perf_counter()
+    orc.ncf_train(ai, sj, prob.val, Ea, Es, net, ocf.NCF_H1, ocf.NCF_H2, [perms[0][:tr]], batch,
+                  lr)
+    t_tr = (time.perf_counter() - t0) / tr
+    t0 = time.perf_counter()
+    orc.ncf_predict(Ea[:16], Es, net, ocf.NCF_H1, ocf.NCF_H2)
+    t_pr = (time.perf_counter() - t0) / (16 * n)
+    t_orc_step = t_tr * nnz + t_pr * pairs
+    spe = (nnz + batch - 1) // batch
+    launches = spe * 20 + 5
+    line = {
+        "metric": "NCF samples/s (epoch + completion + Algorithm 2)", "value": nnz / t_step,
+        "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NCF, "m": m, "n": n, "nnz": nnz, "batch": batch,
+                   "lr": lr, "parallelism": "replicas1",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "parts": {"epoch_ms": t_epoch * 1e3, "steps_per_epoch": spe,
+                  "train_samples_per_s": nnz / t_epoch, "completion_ms": t_pred * 1e3,
+                  "completion_entries_per_s": pairs / t_pred},
+        "heldout_rmse_after_training": rmse,
+        "parity_vs_oracle": {"sample_apps": len(rows),
+                             "max_abs_err": float(np.abs(Th[rows] - Tref).max()),
+                             "decisions_equal_fp32_oracle": bool(np.array_equal(
+                                 best.cpu().numpy(), b32))},
+        "roofline": {"kernel": "k_ncf_predict_tc (completion call: first layer + pairs)",
+                     "bound": "alu", "achieved": gexp, "peak": mufu, "unit": "Gexp/s",
+                     "frac": gexp / mufu, "traffic": None,
+                     "peak_source": "148 SMs x 16 ex2 per clock x median SM clock (derived)",
+                     "note": f"{EXP_PER_PAIR} SELU exponentials per entry; tensor side "
+                             f"{tflops:.1f} TFLOP/s of {bf16_peak:.0f} measured bf16"},
+        "cpu_baseline": {"value": nnz / t_orc_step, "unit": "samples/s",
+                         "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": f"{tr} training samples and 16 completed rows, "
+                                   "extrapolated to one epoch + the full completion"},
+        "e2e": {"value": nnz * args.steps / (e2e_ms / 1e3), "unit": "samples/s",
+                "h2d_bytes_per_step": int(ai.nbytes + sj.nbytes + 4 * nnz + perms[0].nbytes),
+                "d2h_bytes_per_step": int(8 * m)},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+NCF_MMA_MACS = 128 * 64   # h1 W2 per completed entry
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -984,12 +1169,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c4", "c5", "phase"],
+                    choices=["c1", "c2", "c3", "c4", "c5", "phase", "ncf"],
                     help="c1: 64x120 FP64 joint fit; "
                          "c2: 4096x1024 fit (default, the headline line); "
                          "c3: 10,000 uneven problems in one batched launch; "
                          "c4: learned warm start (MLP + ALS fallback) on 2^20 new apps; "
-                         "c5: 1M x 4096 BF16-Gram fold-in + selection")
+                         "c5: 1M x 4096 BF16-Gram fold-in + selection; "
+                         "phase: Algorithm 1 over 2^17 power traces; "
+                         "ncf: the paper's NCF model, one epoch + completion")
     ap.add_argument("--train-steps", type=int, default=30000,
                     help="c4 only: training steps (batch 4096) before the timed completions")
     ap.add_argument("--pool", type=int, default=1 << 20, help="c4 only: training apps")
@@ -1010,6 +1197,8 @@ def main():
         return run_gpu_batched(args)
     if args.workload == "c4":
         return run_gpu_learned(args)
+    if args.workload == "ncf":
+        return run_gpu_ncf(args)
     return run_gpu(args)
 
 

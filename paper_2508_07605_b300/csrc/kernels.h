@@ -92,7 +92,7 @@ cudaError_t launch_batched_pack(int64_t P, const int64_t *rows, const int32_t *k
 
 // MLP warm start (mlp.cu).
 constexpr int MLP_IN = 48, MLP_INP = 64, MLP_H = 256, MLP_SIN = 16;
-enum { EPI_BIAS_SELU = 0, EPI_BIAS = 1, EPI_DSELU = 2, EPI_PART = 3, EPI_SCATTER = 4 };
+enum { EPI_BIAS_SELU = 0, EPI_BIAS = 1, EPI_DSELU = 2, EPI_PART = 3 };
 struct GemmArgs {
     int M, N, K;
     const void *A;            // bf16: [M,K] row-major, or [K,M] when transposed
@@ -105,11 +105,6 @@ struct GemmArgs {
     float *out_f;             // FP32 output / split-K partials
     void *out_z;              // bf16 pre-activation output (EPI_BIAS_SELU)
     int ldo;
-    // EPI_SCATTER: output row r, column c < N/2 is added (atomically) to
-    // out_f[ri[r] * N/2 + c], column c >= N/2 to out_f[s_off + rj[r] * N/2 + c - N/2];
-    // a negative index skips the row.
-    const int32_t *ri = nullptr, *rj = nullptr;
-    int64_t s_off = 0;
 };
 cudaError_t launch_gemm(const GemmArgs &g, bool at, bool bt, int epi, int splits,
                         cudaStream_t st);
@@ -123,19 +118,18 @@ cudaError_t launch_mlp_loss(int B, int k, const float *Y, const float *T, const 
                             void *dY, int ldd, float *part, double *loss, cudaStream_t st);
 cudaError_t launch_gram_v(int64_t n, int KP, int k, const float *V, float *part, float *G,
                           cudaStream_t st);   // part: 64 * k * k floats
-// state: 16 bytes of device memory {int64 t; float lr} (zero = before step 1)
+// Adam step counter and step size in device memory (zero = before step 1).
+struct AdamState {
+    int64_t t;
+    float lr;
+};
+// state: 16 bytes of device memory holding an AdamState
 // BF16 copies of the parameters: entry e goes to thb[map[e]] and img[imap[e]]
 // (an index < 0 means no copy).
 cudaError_t launch_adam(int64_t count, float *th, const float *g, float *m1, float *m2, float b1,
                         float b2, float eps, void *state, const int64_t *bf_map, void *thb,
                         const int64_t *img_map, void *img, cudaStream_t st);
 cudaError_t launch_adam_set_lr(void *state, float lr, cudaStream_t st);
-// The two halves of launch_adam, for callers that update several parameter
-// ranges in one step: advance t once, then update each range (maps may be NULL).
-cudaError_t launch_adam_tick(void *state, cudaStream_t st);
-cudaError_t launch_adam_update(int64_t count, float *th, const float *g, float *m1, float *m2,
-                               float b1, float b2, float eps, const void *state,
-                               const int64_t *bf_map, void *thb, cudaStream_t st);
 cudaError_t launch_to_bf16_map(int64_t count, const float *th, const int64_t *bf_map, void *thb,
                                const int64_t *img_map, void *img, cudaStream_t st);
 cudaError_t launch_fallback_rows(int64_t m, const float *rmse, float thr, int32_t *list,
@@ -274,28 +268,35 @@ struct NcfCtl {                 // device-side position of a training run
     int32_t beff;               // rows of the current batch
     int32_t pad;
 };
-struct NcfGatherArgs {
+struct NcfTrainArgs {            // k_ncf_train_tile: forward + backward of one batch
     NcfCtl *ctl;
+    AdamState *adam;            // advanced once per step (NULL: gradient only)
     int64_t nnz, spe, m, n;     // entries, steps per epoch, applications, settings
     int B;                      // batch capacity (multiple of 64)
     const int32_t *perms;       // [epochs][nnz] visiting orders, or NULL (entries in order)
     const int32_t *app, *set;   // [nnz] indices of the observed entries
     const float *val;           // [nnz]
     const float *Ea, *Es;       // FP32 embedding tables [m][32], [n][32]
-    unsigned char *X;           // bf16 [B][64]
-    float *r;                   // [B]
-    int32_t *ri, *rj;           // [B] (-1: absent row)
+    const void *W1b, *W2b;      // BF16 copies of W1 [64][128] and W2 [128][64]
+    const float *b1, *b2, *w3, *b3;   // FP32 parameters
+    float *part;                // [B/64][part_stride] network-gradient partials (packed order)
+    int64_t part_stride;
+    float *lpart;               // [B/64] sums of squared residuals
+    float *gE;                  // embedding gradients: Ea rows, then Es rows at s_off
+    int64_t s_off;
 };
-struct NcfHeadArgs {
-    const NcfCtl *ctl;
-    const unsigned char *H2, *Z2;   // bf16 [B][64]
-    unsigned char *dZ2;             // bf16 [B][64]
-    const float *r;
-    const int32_t *ri;
-    const float *w3, *b3;           // FP32 master parameters
-    float *part;                    // [B/64][129]: gb2 | gw3 | gb3
-    float *lpart;                   // [B/64] sums of squared residuals
-    float *y;                       // [B] predictions, or NULL
+struct NcfAdamArgs {            // k_ncf_reduce_adam: partials -> gradient -> Adam
+    NcfCtl *ctl;
+    const AdamState *adam;
+    bool update;                // false: write the network gradient only
+    int parts;
+    const float *part;
+    int64_t part_stride;
+    const float *lpart;
+    float *th, *grad, *m1, *m2; // packed [net (net_pad) | Ea | Es]
+    int64_t net_pad, n_emb;
+    void *bf;                   // BF16 W1 | W2
+    double *loss_hist, *loss_last;
 };
 struct NcfPredArgs {
     int64_t m, n;
@@ -306,10 +307,9 @@ struct NcfPredArgs {
     float *T;                       // [m][n]
     int *err;                       // set to 1 if a tensor-core wait ran out
 };
-cudaError_t launch_ncf_gather(const NcfGatherArgs &a, cudaStream_t st);
-cudaError_t launch_ncf_head(const NcfHeadArgs &a, int B, cudaStream_t st);
-cudaError_t launch_ncf_step_end(NcfCtl *ctl, int parts, const float *lpart, double *loss_hist,
-                                double *loss_last, cudaStream_t st);
+cudaError_t prepare_ncf_train();
+cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, cudaStream_t st);
+cudaError_t launch_ncf_refresh_bf(const float *theta, void *bf, cudaStream_t st);
 cudaError_t launch_ncf_first_layer(int64_t rows, const float *E, const float *W, const float *bias,
                                    float *out, cudaStream_t st);
 cudaError_t launch_ncf_w2_image(const float *W2, void *img, cudaStream_t st);

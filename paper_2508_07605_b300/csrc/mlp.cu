@@ -177,14 +177,6 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
                 } else if (EPI == EPI_DSELU) {
                     const bf16 zb = reinterpret_cast<const bf16 *>(g.Zin)[o];
                     reinterpret_cast<bf16 *>(g.out_bf)[o] = __float2bfloat16_rn(v * dselu(__bfloat162float(zb)));
-                } else if (EPI == EPI_SCATTER) {   // rows of dX into two gradient tables
-                    const int half = g.N >> 1;
-                    const bool lo = c < half;
-                    const int32_t row = lo ? g.ri[r] : g.rj[r];
-                    if (row >= 0)
-                        atomicAdd(g.out_f + (lo ? 0 : g.s_off) + (int64_t)row * half +
-                                      (lo ? c : c - half),
-                                  v);
                 } else {   // EPI_PART: split-K partial
                     g.out_f[(int64_t)blockIdx.z * g.M * g.N + (int64_t)r * g.N + c] = v;
                 }
@@ -205,8 +197,6 @@ cudaError_t launch_gemm(const GemmArgs &g, bool at, bool bt, int epi, int splits
     if (!at && !bt && epi == EPI_BIAS) return gemm<false, false, EPI_BIAS>(g, splits, st);
     if (!at && bt && epi == EPI_DSELU) return gemm<false, true, EPI_DSELU>(g, splits, st);
     if (at && !bt && epi == EPI_PART) return gemm<true, false, EPI_PART>(g, splits, st);
-    if (!at && bt && epi == EPI_SCATTER && splits == 1 && g.N % 2 == 0)
-        return gemm<false, true, EPI_SCATTER>(g, 1, st);
     return cudaErrorInvalidValue;
 }
 
@@ -293,10 +283,6 @@ __global__ void __launch_bounds__(1024) k_gram_v_part(int64_t n, int KP, int k,
 // Step counter and step size live on the device, so one captured training
 // step serves every step of a schedule: the host sets lr by a launch ahead of
 // the step (stream-ordered), the step's first kernel advances t.
-struct AdamState {
-    int64_t t;
-    float lr;
-};
 __global__ void k_adam_tick(AdamState *s) { s->t += 1; }
 __global__ void k_adam_set_lr(AdamState *s, float lr) { s->lr = lr; }
 
@@ -305,9 +291,15 @@ __global__ void k_adam(int64_t count, float *__restrict__ th, const float *__res
                        float eps, const AdamState *__restrict__ as,
                        const int64_t *__restrict__ bf_map, bf16 *__restrict__ thb,
                        const int64_t *__restrict__ img_map, bf16 *__restrict__ img) {
-    const double tt = (double)as->t;   // bias corrections of step t (after the tick)
-    const float lr = as->lr;
-    const float c1 = (float)(1.0 - pow((double)b1, tt)), c2 = (float)(1.0 - pow((double)b2, tt));
+    __shared__ float corr[3];   // bias corrections of step t (after the tick), once per CTA
+    if (threadIdx.x == 0) {   // 1 - beta^t as 1 - 2^(t log2 beta), in FP32
+        const float tt = (float)as->t;
+        corr[0] = 1.f - exp2f(tt * log2f(b1));
+        corr[1] = 1.f - exp2f(tt * log2f(b2));
+        corr[2] = as->lr;
+    }
+    __syncthreads();
+    const float c1 = corr[0], c2 = corr[1], lr = corr[2];
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
          e += (int64_t)gridDim.x * blockDim.x) {
         const float g = gr[e];
@@ -413,21 +405,6 @@ cudaError_t launch_adam(int64_t count, float *th, const float *g, float *m1, flo
     k_adam<<<gfor(count), 256, 0, st>>>(count, th, g, m1, m2, b1, b2, eps, as, bf_map,
                                         reinterpret_cast<bf16 *>(thb), img_map,
                                         reinterpret_cast<bf16 *>(img));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adam_tick(void *state, cudaStream_t st) {
-    k_adam_tick<<<1, 1, 0, st>>>(reinterpret_cast<AdamState *>(state));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adam_update(int64_t count, float *th, const float *g, float *m1, float *m2,
-                               float b1, float b2, float eps, const void *state,
-                               const int64_t *bf_map, void *thb, cudaStream_t st) {
-    if (count <= 0) return cudaSuccess;
-    k_adam<<<gfor(count), 256, 0, st>>>(count, th, g, m1, m2, b1, b2, eps,
-                                        reinterpret_cast<const AdamState *>(state), bf_map,
-                                        reinterpret_cast<bf16 *>(thb), nullptr, nullptr);
     return cudaGetLastError();
 }
 

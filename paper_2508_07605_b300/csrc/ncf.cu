@@ -4,14 +4,8 @@
 // concatenated and passed through an MLP 64 -> 128 -> 64 -> 1 with SELU
 // hidden units; the output is the predicted entry P_ij.
 //
-// Training (mini-batches of observed entries, mean squared error, Adam) uses
-// the BF16 tensor-core GEMMs of mlp.cu with fused epilogues plus the kernels
-// here: the batch gather (embedding rows -> BF16 inputs), the output head
-// (y, residual, dL/dz2 and the head's parameter gradients in one pass) and the
-// per-step loss.  The input gradient goes straight back into the two
-// embedding-gradient tables from the GEMM epilogue (EPI_SCATTER).  A training
-// step reads its position (epoch, batch) from a device-side counter, so one
-// captured CUDA graph serves every step.
+// Training (mini-batches of observed entries, mean squared error, Adam) is in
+// ncf_train.cu.
 //
 // Completion (every application x every setting) factors the first layer
 // over the concatenation, x W1 = Ea_i W1[0:32] + Es_j W1[32:64], so it costs
@@ -45,136 +39,9 @@ __device__ __forceinline__ float selu_f(float z) {
     const float e = __expf(fminf(z, 0.f)) - 1.f;
     return z > 0.f ? SELU_L * z : (SELU_L * SELU_A) * e;
 }
-__device__ __forceinline__ float dselu_f(float z) {
-    return z > 0.f ? SELU_L : (SELU_L * SELU_A) * __expf(z);
-}
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&h);
-}
-
-unsigned grid_for(int64_t threads) {
-    int64_t b = (threads + 255) / 256;
-    if (b > NUM_SMS_HINT * 32) b = NUM_SMS_HINT * 32;
-    return (unsigned)(b < 1 ? 1 : b);
-}
-
-// ---------------------------------------------------------------- training
-// Batch rows b < beff take entry e = perm[epoch][off + b] (or off + b when
-// perms is NULL); the others, and entries whose indices are out of range
-// (counted in ctl->skipped), become zero rows with index -1, which every later
-// kernel treats as absent.  Eight threads per row, eight columns each.
-__global__ void k_ncf_gather(NcfGatherArgs a) {
-    const int64_t s = a.ctl->step;
-    const int64_t epoch = s / a.spe, off = (s % a.spe) * (int64_t)a.B;
-    const int64_t left = a.nnz - off;
-    const int beff = (int)(left < a.B ? left : a.B);
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->beff = beff;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)a.B * 8;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(t >> 3), q = (int)(t & 7);
-        bool ok = b < beff;
-        int32_t i = -1, j = -1;
-        int64_t e = 0;
-        if (ok) {
-            e = a.perms ? (int64_t)__ldg(a.perms + epoch * a.nnz + off + b) : off + b;
-            ok = e >= 0 && e < a.nnz;
-            if (ok) {
-                i = __ldg(a.app + e);
-                j = __ldg(a.set + e);
-                ok = i >= 0 && (int64_t)i < a.m && j >= 0 && (int64_t)j < a.n;
-            }
-            if (!ok && q == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->skipped), 1ull);
-        }
-        uint4 pk = make_uint4(0, 0, 0, 0);
-        if (ok) {
-            const float *src = q < 4 ? a.Ea + (int64_t)i * NCF_D + 8 * q
-                                     : a.Es + (int64_t)j * NCF_D + 8 * (q - 4);
-            const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src));
-            const float4 x1 = __ldg(reinterpret_cast<const float4 *>(src) + 1);
-            pk = make_uint4(pack_bf16(x0.x, x0.y), pack_bf16(x0.z, x0.w), pack_bf16(x1.x, x1.y),
-                            pack_bf16(x1.z, x1.w));
-        }
-        *reinterpret_cast<uint4 *>(a.X + ((int64_t)b * 2 * NCF_D + 8 * q) * 2) = pk;
-        if (q == 0) {
-            a.r[b] = ok ? __ldg(a.val + e) : 0.f;
-            a.ri[b] = ok ? i : -1;
-            a.rj[b] = ok ? j : -1;
-        }
-    }
-}
-
-// Output head over 64 batch rows per CTA (8 warps x 8 rows; lane l owns
-// hidden columns 2l, 2l + 1): y = h2 . w3 + b3, e = y - r (0 for absent rows),
-// dy = 2 e / beff, dz2 = dy w3 selu'(z2) (BF16, the operand of the next
-// GEMMs), and per-CTA partials of the gradients of b2, w3, b3 and of sum e^2,
-// reduced over the CTA's warps in a fixed order.
-constexpr int HEAD_PART = NCF_H2 + NCF_H2 + 1;   // gb2 | gw3 | gb3
-__global__ void __launch_bounds__(256) k_ncf_head(NcfHeadArgs a) {
-    __shared__ float red[8][HEAD_PART + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int beff = a.ctl->beff;
-    const float scale = beff > 0 ? 2.f / (float)beff : 0.f;
-    const float w0 = a.w3[2 * lane], w1 = a.w3[2 * lane + 1], b3 = a.b3[0];
-    float gb2_0 = 0.f, gb2_1 = 0.f, gw3_0 = 0.f, gw3_1 = 0.f, gb3 = 0.f, sse = 0.f;
-    for (int u = 0; u < 8; ++u) {
-        const int b = blockIdx.x * 64 + warp * 8 + u;
-        const int64_t o = (int64_t)b * NCF_H2 + 2 * lane;
-        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(a.H2 + o * 2);
-        const __nv_bfloat162 z = *reinterpret_cast<const __nv_bfloat162 *>(a.Z2 + o * 2);
-        const float h0 = __low2float(h), h1 = __high2float(h);
-        float y = fmaf(w1, h1, w0 * h0);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(FULL, y, off);
-        y += b3;
-        const bool live = a.ri[b] >= 0;
-        const float e = live ? y - a.r[b] : 0.f;
-        const float dy = scale * e;
-        const float d0 = dy * w0 * dselu_f(__low2float(z)), d1 = dy * w1 * dselu_f(__high2float(z));
-        *reinterpret_cast<uint32_t *>(a.dZ2 + o * 2) = pack_bf16(d0, d1);
-        if (a.y) a.y[b] = y;
-        gb2_0 += d0; gb2_1 += d1;
-        gw3_0 = fmaf(dy, h0, gw3_0); gw3_1 = fmaf(dy, h1, gw3_1);
-        gb3 += dy;
-        sse = fmaf(e, e, sse);
-    }
-    red[warp][2 * lane] = gb2_0;
-    red[warp][2 * lane + 1] = gb2_1;
-    red[warp][NCF_H2 + 2 * lane] = gw3_0;
-    red[warp][NCF_H2 + 2 * lane + 1] = gw3_1;
-    if (lane == 0) {
-        red[warp][2 * NCF_H2] = gb3;
-        red[warp][2 * NCF_H2 + 1] = sse;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < HEAD_PART + 1; c += blockDim.x) {
-        float s = 0.f;
-        for (int w = 0; w < 8; ++w) s += red[w][c];
-        if (c < HEAD_PART) a.part[(int64_t)blockIdx.x * HEAD_PART + c] = s;
-        else a.lpart[blockIdx.x] = s;
-    }
-}
-
-// End of a step: loss = sum e^2 / beff (fixed order) into the history, then
-// the step counter advances.
-__global__ void k_ncf_step_end(NcfCtl *ctl, int parts, const float *__restrict__ lpart,
-                               double *loss_hist, double *loss_last) {
-    __shared__ double red[256];
-    double s = 0.0;
-    for (int p = threadIdx.x; p < parts; p += blockDim.x) s += (double)lpart[p];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const int beff = ctl->beff;
-        const double L = beff > 0 ? red[0] / (double)beff : 0.0;
-        if (loss_hist) loss_hist[ctl->step] = L;
-        if (loss_last) *loss_last = L;
-        ctl->step += 1;
-    }
 }
 
 // ---------------------------------------------------------------- completion
@@ -381,23 +248,6 @@ __global__ void __launch_bounds__(NP_THREADS) k_ncf_predict_tc(NcfPredArgs a) {
 }
 
 }  // namespace
-
-cudaError_t launch_ncf_gather(const NcfGatherArgs &a, cudaStream_t st) {
-    k_ncf_gather<<<grid_for((int64_t)a.B * 8), 256, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ncf_head(const NcfHeadArgs &a, int B, cudaStream_t st) {
-    if (B % 64) return cudaErrorInvalidValue;
-    k_ncf_head<<<B / 64, 256, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ncf_step_end(NcfCtl *ctl, int parts, const float *lpart, double *loss_hist,
-                                double *loss_last, cudaStream_t st) {
-    k_ncf_step_end<<<1, 256, 0, st>>>(ctl, parts, lpart, loss_hist, loss_last);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_ncf_first_layer(int64_t rows, const float *E, const float *W, const float *bias,
                                    float *out, cudaStream_t st) {

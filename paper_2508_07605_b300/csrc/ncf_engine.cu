@@ -1,10 +1,11 @@
 // Engine behind the NCF C ABI (open_cf_ncf.h): the handle owns the FP32
 // parameters, gradients and Adam moments of the model (one packed vector
 // [net | Ea | Es] so that one update kernel covers all of them), the BF16
-// copies of W1 and W2 the GEMMs read, and every batch workspace, all
-// allocated at creation.  A training step is captured once into a CUDA graph
-// and replayed for every step of every epoch: its kernels take their batch
-// position from a device-side counter.
+// copies of W1 and W2 the training kernel reads, the per-CTA gradient
+// partials and the completion workspaces, all allocated at creation.  A
+// training step (two kernels) is captured once into a CUDA graph and replayed
+// for every step of every epoch: its kernels take their batch position from a
+// device-side counter.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,12 +41,12 @@ struct StepGraph {
 struct open_cf_ncf {
     int device = 0, num_sms = 0;
     int64_t m = 0, n = 0;
-    int B = 0, splits = 1;
+    int B = 0;
     std::vector<double> cpu, gpu;
     int64_t base_default = 0;
     bool params_set = false;
-    NBuf theta, grad, m1, m2, bf, bfmap, adam, ctl, loss1;
-    NBuf X, r, ri, rj, Z1, H1, dZ1, Z2, H2, dZ2, hpart, lpart, wpart, cpart;
+    NBuf theta, grad, m1, m2, bf, adam, ctl, loss1;
+    NBuf part, lpart;
     NBuf A, S, w2img, T, cg, err;
     cudaStream_t cap_stream = nullptr;
     std::vector<StepGraph> graphs;
@@ -110,74 +111,28 @@ int64_t n_emb(const open_cf_ncf_t *h) { return (h->m + h->n) * NCF_D; }
 cudaError_t enqueue_step(open_cf_ncf_t *h, int64_t nnz, int64_t spe, const int32_t *app,
                          const int32_t *set, const float *val, const int32_t *perms,
                          double *loss_hist, bool update, cudaStream_t st) {
-    const int B = h->B;
     float *th = F(h->theta), *g = F(h->grad);
-    const float *Ea = th + NET_PAD, *Es = Ea + h->m * NCF_D;
-    const void *W1b = h->bf.p;
-    const void *W2b = reinterpret_cast<const char *>(h->bf.p) + 2 * NCF_OFF_B1;
     NcfCtl *ctl = reinterpret_cast<NcfCtl *>(h->ctl.p);
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(g + NET_PAD, 0, sizeof(float) * n_emb(h), st)) != cudaSuccess) return e;
-    NcfGatherArgs ga{ctl, nnz, spe, h->m, h->n, B, perms, app, set, val, Ea, Es,
-                     reinterpret_cast<unsigned char *>(h->X.p), F(h->r), (int32_t *)h->ri.p,
-                     (int32_t *)h->rj.p};
-    if ((e = launch_ncf_gather(ga, st)) != cudaSuccess) return e;
-    GemmArgs f1{};   // z1 = x W1 + b1, h1 = SELU(z1)
-    f1.M = B; f1.N = NCF_H1; f1.K = 2 * NCF_D;
-    f1.A = h->X.p; f1.lda = 2 * NCF_D; f1.B = W1b; f1.ldb = NCF_H1;
-    f1.bias = th + NCF_OFF_B1; f1.out_z = h->Z1.p; f1.out_bf = h->H1.p; f1.ldo = NCF_H1;
-    if ((e = launch_gemm(f1, false, false, EPI_BIAS_SELU, 1, st)) != cudaSuccess) return e;
-    GemmArgs f2{};   // z2 = h1 W2 + b2, h2 = SELU(z2)
-    f2.M = B; f2.N = NCF_H2; f2.K = NCF_H1;
-    f2.A = h->H1.p; f2.lda = NCF_H1; f2.B = W2b; f2.ldb = NCF_H2;
-    f2.bias = th + NCF_OFF_B2; f2.out_z = h->Z2.p; f2.out_bf = h->H2.p; f2.ldo = NCF_H2;
-    if ((e = launch_gemm(f2, false, false, EPI_BIAS_SELU, 1, st)) != cudaSuccess) return e;
-    NcfHeadArgs ha{ctl, reinterpret_cast<const unsigned char *>(h->H2.p),
-                   reinterpret_cast<const unsigned char *>(h->Z2.p),
-                   reinterpret_cast<unsigned char *>(h->dZ2.p), F(h->r), (const int32_t *)h->ri.p,
-                   th + NCF_OFF_W3, th + NCF_OFF_B3, F(h->hpart), F(h->lpart), nullptr};
-    if ((e = launch_ncf_head(ha, B, st)) != cudaSuccess) return e;
-    if ((e = launch_sum_parts(2 * NCF_H2 + 1, B / 64, F(h->hpart), g + NCF_OFF_B2, st)) !=
-        cudaSuccess)
-        return e;   // gb2 | gw3 | gb3 are contiguous in the packing
-    GemmArgs w2{};   // dW2 = h1^T dz2
-    w2.M = NCF_H1; w2.N = NCF_H2; w2.K = B;
-    w2.A = h->H1.p; w2.lda = NCF_H1; w2.B = h->dZ2.p; w2.ldb = NCF_H2; w2.out_f = F(h->wpart);
-    if ((e = launch_gemm(w2, true, false, EPI_PART, h->splits, st)) != cudaSuccess) return e;
-    if ((e = launch_sum_parts(NCF_H1 * NCF_H2, h->splits, F(h->wpart), g + NCF_OFF_W2, st)) !=
-        cudaSuccess)
-        return e;
-    GemmArgs d1{};   // dz1 = (dz2 W2^T) * SELU'(z1)
-    d1.M = B; d1.N = NCF_H1; d1.K = NCF_H2;
-    d1.A = h->dZ2.p; d1.lda = NCF_H2; d1.B = W2b; d1.ldb = NCF_H2;
-    d1.Zin = h->Z1.p; d1.out_bf = h->dZ1.p; d1.ldo = NCF_H1;
-    if ((e = launch_gemm(d1, false, true, EPI_DSELU, 1, st)) != cudaSuccess) return e;
-    GemmArgs w1{};   // dW1 = x^T dz1
-    w1.M = 2 * NCF_D; w1.N = NCF_H1; w1.K = B;
-    w1.A = h->X.p; w1.lda = 2 * NCF_D; w1.B = h->dZ1.p; w1.ldb = NCF_H1; w1.out_f = F(h->wpart);
-    if ((e = launch_gemm(w1, true, false, EPI_PART, h->splits, st)) != cudaSuccess) return e;
-    if ((e = launch_sum_parts(2 * NCF_D * NCF_H1, h->splits, F(h->wpart), g, st)) != cudaSuccess)
-        return e;
-    if ((e = launch_colsum(B, NCF_H1, h->dZ1.p, F(h->cpart), g + NCF_OFF_B1, st)) != cudaSuccess)
-        return e;
-    GemmArgs dx{};   // dx = dz1 W1^T, scattered into the embedding gradients
-    dx.M = B; dx.N = 2 * NCF_D; dx.K = NCF_H1;
-    dx.A = h->dZ1.p; dx.lda = NCF_H1; dx.B = W1b; dx.ldb = NCF_H1;
-    dx.out_f = g + NET_PAD; dx.ri = (const int32_t *)h->ri.p; dx.rj = (const int32_t *)h->rj.p;
-    dx.s_off = h->m * NCF_D;
-    if ((e = launch_gemm(dx, false, true, EPI_SCATTER, 1, st)) != cudaSuccess) return e;
-    if ((e = launch_ncf_step_end(ctl, B / 64, F(h->lpart), loss_hist, (double *)h->loss1.p, st)) !=
-        cudaSuccess)
-        return e;
-    if (!update) return cudaSuccess;
-    if ((e = launch_adam_tick(h->adam.p, st)) != cudaSuccess) return e;
-    if ((e = launch_adam_update(NCF_NET, th, g, F(h->m1), F(h->m2), 0.9f, 0.999f, 1e-8f,
-                                h->adam.p, (const int64_t *)h->bfmap.p, h->bf.p, st)) !=
-        cudaSuccess)
-        return e;
-    return launch_adam_update(n_emb(h), th + NET_PAD, g + NET_PAD, F(h->m1) + NET_PAD,
-                              F(h->m2) + NET_PAD, 0.9f, 0.999f, 1e-8f, h->adam.p, nullptr,
-                              nullptr, st);
+    NcfTrainArgs t{};
+    t.ctl = ctl;
+    t.adam = update ? reinterpret_cast<AdamState *>(h->adam.p) : nullptr;
+    t.nnz = nnz; t.spe = spe; t.m = h->m; t.n = h->n; t.B = h->B;
+    t.perms = perms; t.app = app; t.set = set; t.val = val;
+    t.Ea = th + NET_PAD; t.Es = th + NET_PAD + h->m * NCF_D;
+    t.W1b = h->bf.p; t.W2b = reinterpret_cast<const char *>(h->bf.p) + 2 * NCF_OFF_B1;
+    t.b1 = th + NCF_OFF_B1; t.b2 = th + NCF_OFF_B2; t.w3 = th + NCF_OFF_W3; t.b3 = th + NCF_OFF_B3;
+    t.part = F(h->part); t.part_stride = NET_PAD; t.lpart = F(h->lpart);
+    t.gE = g + NET_PAD; t.s_off = h->m * NCF_D;
+    NcfAdamArgs u{};
+    u.ctl = ctl;
+    u.adam = reinterpret_cast<const AdamState *>(h->adam.p);
+    u.update = update;
+    u.parts = h->B / 64; u.part = F(h->part); u.part_stride = NET_PAD; u.lpart = F(h->lpart);
+    u.th = th; u.grad = g; u.m1 = F(h->m1); u.m2 = F(h->m2);
+    u.net_pad = NET_PAD; u.n_emb = n_emb(h);
+    u.bf = h->bf.p;
+    u.loss_hist = loss_hist; u.loss_last = (double *)h->loss1.p;
+    return launch_ncf_train_step(t, u, st);
 }
 
 }  // namespace
@@ -215,19 +170,9 @@ int open_cf_ncf_create(int64_t m, int32_t n_cpu, const double *cpu_caps_w_host, 
     const int64_t ci = std::max_element(h->cpu.begin(), h->cpu.end()) - h->cpu.begin();
     const int64_t gi = std::max_element(h->gpu.begin(), h->gpu.end()) - h->gpu.begin();
     h->base_default = ci * n_gpu + gi;
-    // split-K for the two weight gradients: K = batch in slices of >= 128 rows
-    for (int s = 16; s >= 1; --s)
-        if (batch % (32 * s) == 0 && (s == 1 || batch / s >= 128)) {
-            h->splits = s;
-            break;
-        }
     Guard gd(device);
     const int64_t P = NET_PAD + n_emb(h);
-    const size_t fB = sizeof(float) * (size_t)batch, hB = 2 * (size_t)batch;
     std::vector<float> cg(h->n);
-    std::vector<int64_t> map(NET_PAD, -1);
-    for (int64_t e = 0; e < NCF_OFF_B1; ++e) map[e] = e;   // W1 -> bf[0, 8192)
-    for (int64_t e = 0; e < NCF_H1 * NCF_H2; ++e) map[NCF_OFF_W2 + e] = NCF_OFF_B1 + e;   // W2
     for (int64_t j = 0; j < h->n; ++j)
         cg[j] = (float)h->cpu[j / n_gpu] + (float)h->gpu[j % n_gpu];
     cudaError_t e = cudaSuccess;
@@ -236,23 +181,17 @@ int open_cf_ncf_create(int64_t m, int32_t n_cpu, const double *cpu_caps_w_host, 
     };
     A(h->theta, sizeof(float) * P); A(h->grad, sizeof(float) * P);
     A(h->m1, sizeof(float) * P); A(h->m2, sizeof(float) * P);
-    A(h->bf, 2 * 2 * NCF_OFF_B1); A(h->bfmap, sizeof(int64_t) * NET_PAD);
+    A(h->bf, 2 * 2 * NCF_OFF_B1);
     A(h->adam, 16); A(h->ctl, sizeof(NcfCtl)); A(h->loss1, sizeof(double));
-    A(h->X, hB * 2 * NCF_D); A(h->r, fB); A(h->ri, fB); A(h->rj, fB);
-    A(h->Z1, hB * NCF_H1); A(h->H1, hB * NCF_H1); A(h->dZ1, hB * NCF_H1);
-    A(h->Z2, hB * NCF_H2); A(h->H2, hB * NCF_H2); A(h->dZ2, hB * NCF_H2);
-    A(h->hpart, sizeof(float) * (batch / 64) * (2 * NCF_H2 + 1)); A(h->lpart, fB / 64);
-    A(h->wpart, sizeof(float) * h->splits * NCF_H1 * NCF_H2);
-    A(h->cpart, sizeof(float) * ((batch + 127) / 128) * NCF_H1);
+    A(h->part, sizeof(float) * (batch / 64) * NET_PAD); A(h->lpart, sizeof(float) * (batch / 64));
     A(h->A, sizeof(float) * m * NCF_H1); A(h->S, sizeof(float) * h->n * NCF_H1);
     A(h->w2img, 2 * NCF_H1 * NCF_H2); A(h->cg, sizeof(float) * h->n); A(h->err, 16);
-    if (e == cudaSuccess) e = cudaMemcpy(h->bfmap.p, map.data(), sizeof(int64_t) * NET_PAD,
-                                         cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->cg.p, cg.data(), sizeof(float) * h->n,
                                          cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->err.p, 0, 16);
     if (e == cudaSuccess) e = cudaMemset(h->ctl.p, 0, sizeof(NcfCtl));
     if (e == cudaSuccess) e = prepare_ncf_predict_tc();
+    if (e == cudaSuccess) e = prepare_ncf_train();
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -271,10 +210,9 @@ void open_cf_ncf_destroy(open_cf_ncf_t *h) {
         cudaDeviceSynchronize();
         for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-        for (NBuf *b : {&h->theta, &h->grad, &h->m1, &h->m2, &h->bf, &h->bfmap, &h->adam, &h->ctl,
-                        &h->loss1, &h->X, &h->r, &h->ri, &h->rj, &h->Z1, &h->H1, &h->dZ1, &h->Z2,
-                        &h->H2, &h->dZ2, &h->hpart, &h->lpart, &h->wpart, &h->cpart, &h->A, &h->S,
-                        &h->w2img, &h->T, &h->cg, &h->err})
+        for (NBuf *b : {&h->theta, &h->grad, &h->m1, &h->m2, &h->bf, &h->adam, &h->ctl,
+                        &h->loss1, &h->part, &h->lpart, &h->A, &h->S, &h->w2img, &h->T, &h->cg,
+                        &h->err})
             release(*b);
     }
     delete h;
@@ -301,8 +239,8 @@ int open_cf_ncf_set_params(open_cf_ncf_t *h, const float *net, const float *Ea, 
     NCK(h, cudaMemsetAsync(h->m2.p, 0, sizeof(float) * P, st));
     NCK(h, cudaMemsetAsync(h->adam.p, 0, 16, st));
     NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(NcfCtl), st));
-    NCK(h, launch_to_bf16_map(NET_PAD, th, (const int64_t *)h->bfmap.p, h->bf.p, nullptr, nullptr,
-                              st));
+    NCK(h, cudaMemsetAsync(h->grad.p, 0, sizeof(float) * P, st));   // embedding rows accumulate
+    NCK(h, launch_ncf_refresh_bf(th, h->bf.p, st));
     h->params_set = true;
     return OPEN_CF_OK;
 }
@@ -339,6 +277,7 @@ int open_cf_ncf_train(open_cf_ncf_t *h, int64_t nnz, const int32_t *app, const i
     cudaStream_t st = SS(stream);
     const int64_t spe = (nnz + h->B - 1) / h->B, steps = spe * epochs;
     NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(int64_t), st));   // step = 0
+    NCK(h, cudaMemsetAsync(F(h->grad) + NET_PAD, 0, sizeof(float) * n_emb(h), st));
     NCK(h, launch_adam_set_lr(h->adam.p, lr, st));
     std::vector<int64_t> key{nnz, spe, (int64_t)app, (int64_t)setting, (int64_t)val,
                              (int64_t)perms, (int64_t)loss_out};
@@ -380,6 +319,7 @@ int open_cf_ncf_grad(open_cf_ncf_t *h, int64_t B, const int32_t *app, const int3
     Guard gd(h->device);
     cudaStream_t st = SS(stream);
     NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(int64_t), st));
+    NCK(h, cudaMemsetAsync(F(h->grad) + NET_PAD, 0, sizeof(float) * n_emb(h), st));
     NCK(h, enqueue_step(h, B, 1, app, setting, val, nullptr, nullptr, false, st));
     const float *g = F(h->grad);
     if (loss_out)

@@ -1,0 +1,424 @@
+// One NCF training step (the paper's CF model, Sec. "Collaborative Filtering
+// Model"; mean squared error over a mini-batch of observed entries, Adam) in
+// two kernels.
+//
+// k_ncf_train_tile: one CTA per 64 batch rows runs the whole forward and
+// backward pass of its rows on the SM, with the BF16 weights and every
+// activation in shared memory:
+//   gather   x = [Ea_i, Es_j]                        (64 x 64, BF16)
+//   forward  z1 = x W1 + b1, h1 = SELU(z1)            (64 x 128)
+//            z2 = h1 W2 + b2, h2 = SELU(z2)           (64 x 64)
+//   head     y = h2 . w3 + b3, dy = 2 (y - r) / B, dz2 = dy w3 SELU'(z2)
+//   backward dz1 = (dz2 W2^T) SELU'(z1),  dW2 += h1^T dz2,  dW1 += x^T dz1,
+//            db1 += colsum dz1,  dx = dz1 W1^T -> the two embedding rows
+// Every product is an mma.sync m16n8k16 (BF16 operands, FP32 accumulation)
+// on operands read by ldmatrix from padded shared tiles.  The CTA's share of
+// the network gradient goes to its own partial vector (in the packing of the
+// parameters); the embedding gradients are added atomically into the
+// gradient table (rows of different CTAs can coincide).
+//
+// k_ncf_reduce_adam: sums the partial vectors in CTA order (a fixed order),
+// applies Adam to every parameter (network and both embedding tables, dense
+// moments), refreshes the BF16 copies of W1 and W2, clears the embedding
+// gradient for the next step, and records the step's loss.
+//
+// A step reads its batch position from a device-side counter, so one CUDA
+// graph of the two kernels serves every step of a training run.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ocf {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr float SELU_L = 1.0507009873554804934193349852946f;
+constexpr float SELU_A = 1.6732632423543772848170429916717f;
+
+__device__ __forceinline__ float selu_t(float z) {
+    const float e = __expf(fminf(z, 0.f)) - 1.f;
+    return z > 0.f ? SELU_L * z : (SELU_L * SELU_A) * e;
+}
+__device__ __forceinline__ float dselu_t(float z) {
+    return z > 0.f ? SELU_L : (SELU_L * SELU_A) * __expf(z);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                               uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void ld_x4(uint32_t (&r)[4], const bf16 *p) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
+}
+__device__ __forceinline__ void ld_x4_t(uint32_t (&r)[4], const bf16 *p) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
+}
+
+// Warp tile of a shared-memory product: acc[j] += op(A)[m0 .. m0 + 16, :] op(B)[:, n0 + 8 j ..]
+// over K.  A is [M][K] (row stride lda), or [K][M] when AT; B is [K][N], or
+// [N][K] when BT.  acc[j][e]: row m0 + lane / 4 + 8 (e / 2), column
+// n0 + 8 j + 2 (lane % 4) + e % 2.
+template <bool AT, bool BT, int NT>
+__device__ __forceinline__ void warp_mma(float (&acc)[NT][4], const bf16 *A, int lda,
+                                         const bf16 *B, int ldb, int m0, int n0, int K,
+                                         int lane) {
+    const int mi = lane >> 3, rr = lane & 7;
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t af[4];
+        if (!AT) ld_x4(af, A + (m0 + (lane & 15)) * lda + k0 + (lane >> 4) * 8);
+        else ld_x4_t(af, A + (k0 + (mi >> 1) * 8 + rr) * lda + m0 + (mi & 1) * 8);
+#pragma unroll
+        for (int j = 0; j < NT; j += 2) {
+            const int nb = n0 + 8 * j;
+            uint32_t t[4];
+            if (!BT) ld_x4_t(t, B + (k0 + (mi & 1) * 8 + rr) * ldb + nb + (mi >> 1) * 8);
+            else ld_x4(t, B + (nb + (mi >> 1) * 8 + rr) * ldb + k0 + (mi & 1) * 8);
+            mma_bf16_16816(acc[j], af, t[0], t[1]);
+            mma_bf16_16816(acc[j + 1], af, t[2], t[3]);
+        }
+    }
+}
+
+__device__ __forceinline__ void st_pair(bf16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+
+constexpr int TB = 64;                  // batch rows per CTA
+constexpr int NTH = 256;
+constexpr int SX = 2 * NCF_D + 8;       // row strides (elements) of the padded tiles
+constexpr int S1 = NCF_H1 + 8;
+constexpr int S2 = NCF_H2 + 8;
+constexpr uint32_t O_W1 = 0;                                   // W1  [64][S1]
+constexpr uint32_t O_W2 = O_W1 + 2 * NCF_D * S1 * 2;           // W2  [128][S2]
+constexpr uint32_t O_X = O_W2 + NCF_H1 * S2 * 2;               // x   [64][SX]
+constexpr uint32_t O_Z1 = O_X + TB * SX * 2;                   // z1, h1, dz1 [64][S1]
+constexpr uint32_t O_H1 = O_Z1 + TB * S1 * 2;
+constexpr uint32_t O_DZ1 = O_H1 + TB * S1 * 2;
+constexpr uint32_t O_Z2 = O_DZ1 + TB * S1 * 2;                 // z2, h2, dz2 [64][S2]
+constexpr uint32_t O_H2 = O_Z2 + TB * S2 * 2;
+constexpr uint32_t O_DZ2 = O_H2 + TB * S2 * 2;
+constexpr int HEADP = 2 * NCF_H2 + 2;                          // gb2 | gw3 | gb3 | sse
+constexpr uint32_t O_RED = O_DZ2 + TB * S2 * 2;                // [8][HEADP] floats
+constexpr uint32_t O_R = O_RED + 8 * HEADP * 4;
+constexpr uint32_t O_RI = O_R + TB * 4;
+constexpr uint32_t O_RJ = O_RI + TB * 4;
+constexpr uint32_t TRAIN_SMEM = O_RJ + TB * 4;
+
+__global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    bf16 *W1s = reinterpret_cast<bf16 *>(sm + O_W1), *W2s = reinterpret_cast<bf16 *>(sm + O_W2);
+    bf16 *Xs = reinterpret_cast<bf16 *>(sm + O_X);
+    bf16 *Z1s = reinterpret_cast<bf16 *>(sm + O_Z1), *H1s = reinterpret_cast<bf16 *>(sm + O_H1);
+    bf16 *D1s = reinterpret_cast<bf16 *>(sm + O_DZ1);
+    bf16 *Z2s = reinterpret_cast<bf16 *>(sm + O_Z2), *H2s = reinterpret_cast<bf16 *>(sm + O_H2);
+    bf16 *D2s = reinterpret_cast<bf16 *>(sm + O_DZ2);
+    float *red = reinterpret_cast<float *>(sm + O_RED);
+    float *Rs = reinterpret_cast<float *>(sm + O_R);
+    int32_t *RI = reinterpret_cast<int32_t *>(sm + O_RI), *RJ = reinterpret_cast<int32_t *>(sm + O_RJ);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gid = lane >> 2, t4 = lane & 3;
+
+    // batch position of this step
+    const int64_t s = a.ctl->step;
+    const int64_t epoch = s / a.spe, off = (s % a.spe) * (int64_t)a.B;
+    const int64_t left = a.nnz - off;
+    const int beff = (int)(left < a.B ? left : a.B);
+    if (blockIdx.x == 0 && tid == 0) {
+        a.ctl->beff = beff;
+        if (a.adam) a.adam->t += 1;   // the update kernel of this step reads it
+    }
+
+    // ---- weights (BF16 copies, row-major) and the gathered inputs
+    const bf16 *W1g = reinterpret_cast<const bf16 *>(a.W1b);
+    const bf16 *W2g = reinterpret_cast<const bf16 *>(a.W2b);
+    for (int v = tid; v < 2 * NCF_D * (NCF_H1 / 8); v += NTH) {
+        const int r = v / (NCF_H1 / 8), c8 = (v % (NCF_H1 / 8)) * 8;
+        *reinterpret_cast<uint4 *>(W1s + r * S1 + c8) =
+            __ldg(reinterpret_cast<const uint4 *>(W1g + r * NCF_H1 + c8));
+    }
+    for (int v = tid; v < NCF_H1 * (NCF_H2 / 8); v += NTH) {
+        const int r = v / (NCF_H2 / 8), c8 = (v % (NCF_H2 / 8)) * 8;
+        *reinterpret_cast<uint4 *>(W2s + r * S2 + c8) =
+            __ldg(reinterpret_cast<const uint4 *>(W2g + r * NCF_H2 + c8));
+    }
+    for (int v = tid; v < TB * 8; v += NTH) {
+        const int rr = v >> 3, q = v & 7;
+        const int b = blockIdx.x * TB + rr;
+        bool ok = b < beff;
+        int32_t i = -1, j = -1;
+        int64_t e = 0;
+        if (ok) {
+            e = a.perms ? (int64_t)__ldg(a.perms + epoch * a.nnz + off + b) : off + b;
+            ok = e >= 0 && e < a.nnz;
+            if (ok) {
+                i = __ldg(a.app + e);
+                j = __ldg(a.set + e);
+                ok = i >= 0 && (int64_t)i < a.m && j >= 0 && (int64_t)j < a.n;
+            }
+            if (!ok && q == 0)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->skipped), 1ull);
+        }
+        uint4 pk = make_uint4(0, 0, 0, 0);
+        if (ok) {
+            const float *src = q < 4 ? a.Ea + (int64_t)i * NCF_D + 8 * q
+                                     : a.Es + (int64_t)j * NCF_D + 8 * (q - 4);
+            const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src));
+            const float4 x1 = __ldg(reinterpret_cast<const float4 *>(src) + 1);
+            __nv_bfloat162 p0 = __floats2bfloat162_rn(x0.x, x0.y), p1 = __floats2bfloat162_rn(x0.z, x0.w);
+            __nv_bfloat162 p2 = __floats2bfloat162_rn(x1.x, x1.y), p3 = __floats2bfloat162_rn(x1.z, x1.w);
+            pk = make_uint4(*reinterpret_cast<uint32_t *>(&p0), *reinterpret_cast<uint32_t *>(&p1),
+                            *reinterpret_cast<uint32_t *>(&p2), *reinterpret_cast<uint32_t *>(&p3));
+        }
+        *reinterpret_cast<uint4 *>(Xs + rr * SX + 8 * q) = pk;
+        if (q == 0) {
+            Rs[rr] = ok ? __ldg(a.val + e) : 0.f;
+            RI[rr] = ok ? i : -1;
+            RJ[rr] = ok ? j : -1;
+        }
+    }
+    __syncthreads();
+
+    // ---- z1 = x W1 + b1 (64 x 128, K = 64)
+    {
+        const int m0 = 16 * (warp & 3), n0 = 64 * (warp >> 2);
+        float acc[8][4];
+        warp_mma<false, false, 8>(acc, Xs, SX, W1s, S1, m0, n0, 2 * NCF_D, lane);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
+                const float z0 = acc[j][2 * h] + a.b1[c], z1 = acc[j][2 * h + 1] + a.b1[c + 1];
+                st_pair(Z1s + r * S1 + c, z0, z1);
+                st_pair(H1s + r * S1 + c, selu_t(z0), selu_t(z1));
+            }
+    }
+    __syncthreads();
+
+    // ---- z2 = h1 W2 + b2 (64 x 64, K = 128)
+    {
+        const int m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
+        float acc[4][4];
+        warp_mma<false, false, 4>(acc, H1s, S1, W2s, S2, m0, n0, NCF_H1, lane);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
+                const float z0 = acc[j][2 * h] + a.b2[c], z1 = acc[j][2 * h + 1] + a.b2[c + 1];
+                st_pair(Z2s + r * S2 + c, z0, z1);
+                st_pair(H2s + r * S2 + c, selu_t(z0), selu_t(z1));
+            }
+    }
+    __syncthreads();
+
+    // ---- head: warp w takes rows 8w .. 8w + 7, lane l hidden columns 2l, 2l + 1
+    {
+        const float scale = beff > 0 ? 2.f / (float)beff : 0.f;
+        const float w0 = a.w3[2 * lane], w1 = a.w3[2 * lane + 1], b3 = a.b3[0];
+        float gb2_0 = 0.f, gb2_1 = 0.f, gw3_0 = 0.f, gw3_1 = 0.f, gb3 = 0.f, sse = 0.f;
+        for (int u = 0; u < 8; ++u) {
+            const int r = 8 * warp + u;
+            const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162 *>(H2s + r * S2 + 2 * lane);
+            const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162 *>(Z2s + r * S2 + 2 * lane);
+            const float h0 = __low2float(hh), h1 = __high2float(hh);
+            float y = fmaf(w1, h1, w0 * h0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(FULL, y, o);
+            y += b3;
+            const float e = RI[r] >= 0 ? y - Rs[r] : 0.f;
+            const float dy = scale * e;
+            const float d0 = dy * w0 * dselu_t(__low2float(zz));
+            const float d1 = dy * w1 * dselu_t(__high2float(zz));
+            st_pair(D2s + r * S2 + 2 * lane, d0, d1);
+            gb2_0 += d0; gb2_1 += d1;
+            gw3_0 = fmaf(dy, h0, gw3_0); gw3_1 = fmaf(dy, h1, gw3_1);
+            gb3 += dy;
+            sse = fmaf(e, e, sse);
+        }
+        float *rw = red + warp * HEADP;
+        rw[2 * lane] = gb2_0;
+        rw[2 * lane + 1] = gb2_1;
+        rw[NCF_H2 + 2 * lane] = gw3_0;
+        rw[NCF_H2 + 2 * lane + 1] = gw3_1;
+        if (lane == 0) {
+            rw[2 * NCF_H2] = gb3;
+            rw[2 * NCF_H2 + 1] = sse;
+        }
+    }
+    __syncthreads();
+    float *part = a.part + (int64_t)blockIdx.x * a.part_stride;
+    for (int c = tid; c < HEADP; c += NTH) {
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w) v += red[w * HEADP + c];
+        if (c < HEADP - 1) part[NCF_OFF_B2 + c] = v;   // gb2 | gw3 | gb3, contiguous in the packing
+        else a.lpart[blockIdx.x] = v;
+    }
+
+    // ---- dz1 = (dz2 W2^T) SELU'(z1) (64 x 128, K = 64), and dW2 = h1^T dz2 (128 x 64, K = 64)
+    {
+        const int m0 = 16 * (warp & 3), n0 = 64 * (warp >> 2);
+        float acc[8][4];
+        warp_mma<false, true, 8>(acc, D2s, S2, W2s, S2, m0, n0, NCF_H2, lane);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
+                const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162 *>(Z1s + r * S1 + c);
+                st_pair(D1s + r * S1 + c, acc[j][2 * h] * dselu_t(__low2float(zz)),
+                        acc[j][2 * h + 1] * dselu_t(__high2float(zz)));
+            }
+    }
+    {
+        const int m0 = 16 * warp;
+        float acc[8][4];
+        warp_mma<true, false, 8>(acc, H1s, S1, D2s, S2, m0, 0, TB, lane);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = m0 + gid + 8 * h, c = 8 * j + 2 * t4;
+                *reinterpret_cast<float2 *>(part + NCF_OFF_W2 + r * NCF_H2 + c) =
+                    make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
+            }
+    }
+    __syncthreads();
+
+    // ---- dW1 = x^T dz1 (64 x 128, K = 64), db1 = column sums of dz1
+    {
+        const int m0 = 16 * (warp & 3), n0 = 64 * (warp >> 2);
+        float acc[8][4];
+        warp_mma<true, false, 8>(acc, Xs, SX, D1s, S1, m0, n0, TB, lane);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
+                *reinterpret_cast<float2 *>(part + r * NCF_H1 + c) =
+                    make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
+            }
+    }
+    if (tid < NCF_H1) {
+        float v = 0.f;
+        for (int r = 0; r < TB; ++r) v += __bfloat162float(D1s[r * S1 + tid]);
+        part[NCF_OFF_B1 + tid] = v;
+    }
+    // ---- dx = dz1 W1^T (64 x 64, K = 128) into the embedding gradients
+    {
+        const int m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
+        float acc[4][4];
+        warp_mma<false, true, 4>(acc, D1s, S1, W1s, S1, m0, n0, NCF_H1, lane);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = m0 + gid + 8 * (e >> 1), c = n0 + 8 * j + 2 * t4 + (e & 1);
+                const bool lo = c < NCF_D;
+                const int32_t row = lo ? RI[r] : RJ[r];
+                if (row >= 0)
+                    atomicAdd(a.gE + (lo ? 0 : a.s_off) + (int64_t)row * NCF_D + (lo ? c : c - NCF_D),
+                              acc[j][e]);
+            }
+    }
+}
+
+// Network gradient = sum of the CTA partials (CTA order); Adam on every
+// parameter; BF16 copies of W1, W2; embedding gradient cleared; loss recorded.
+__global__ void __launch_bounds__(256) k_ncf_reduce_adam(NcfAdamArgs a) {
+    __shared__ float corr[3];   // bias corrections of step t and the step size, once per CTA
+    const int64_t total = a.net_pad + a.n_emb;
+    if (threadIdx.x == 0) {
+        corr[0] = corr[1] = 1.f;
+        corr[2] = 0.f;
+        if (a.update) {   // 1 - beta^t as 1 - 2^(t log2 beta), in FP32 (accurate to ~1e-7 here)
+            const float tt = (float)a.adam->t;
+            corr[0] = 1.f - exp2f(tt * log2f(0.9f));
+            corr[1] = 1.f - exp2f(tt * log2f(0.999f));
+            corr[2] = a.adam->lr;
+        }
+    }
+    __syncthreads();
+    const float fc1 = corr[0], fc2 = corr[1], lr = corr[2];
+    bf16 *bf = reinterpret_cast<bf16 *>(a.bf);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float g;
+        if (e < NCF_NET) {
+            g = 0.f;
+            for (int c = 0; c < a.parts; ++c) g += a.part[(int64_t)c * a.part_stride + e];
+            a.grad[e] = g;
+        } else if (e < a.net_pad) {
+            continue;
+        } else {
+            if (!a.update) continue;   // the embedding gradient stays for the caller
+            g = a.grad[e];
+            a.grad[e] = 0.f;
+        }
+        if (!a.update) continue;
+        const float m1 = 0.9f * a.m1[e] + 0.1f * g;
+        const float m2 = 0.999f * a.m2[e] + 0.001f * g * g;
+        a.m1[e] = m1;
+        a.m2[e] = m2;
+        const float t = a.th[e] - lr * (m1 / fc1) / (sqrtf(m2 / fc2) + 1e-8f);
+        a.th[e] = t;
+        if (e < NCF_OFF_B1) bf[e] = __float2bfloat16_rn(t);
+        else if (e >= NCF_OFF_W2 && e < NCF_OFF_B2) bf[NCF_OFF_B1 + (e - NCF_OFF_W2)] = __float2bfloat16_rn(t);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double sse = 0.0;
+        for (int c = 0; c < a.parts; ++c) sse += (double)a.lpart[c];
+        const int beff = a.ctl->beff;
+        const double L = beff > 0 ? sse / (double)beff : 0.0;
+        if (a.loss_hist) a.loss_hist[a.ctl->step] = L;
+        if (a.loss_last) *a.loss_last = L;
+        a.ctl->step += 1;
+    }
+}
+
+// BF16 copies of W1 and W2 from the FP32 parameters (after they are set).
+__global__ void k_ncf_refresh_bf(const float *__restrict__ th, bf16 *__restrict__ bf) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * NCF_OFF_B1;
+         e += gridDim.x * blockDim.x)
+        bf[e] = __float2bfloat16_rn(e < NCF_OFF_B1 ? th[e] : th[NCF_OFF_W2 + e - NCF_OFF_B1]);
+}
+
+}  // namespace
+
+cudaError_t prepare_ncf_train() {
+    return cudaFuncSetAttribute(k_ncf_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TRAIN_SMEM);
+}
+
+cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, cudaStream_t st) {
+    if (t.B % TB || t.B <= 0) return cudaErrorInvalidValue;
+    k_ncf_train_tile<<<t.B / TB, NTH, TRAIN_SMEM, st>>>(t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (u.net_pad + u.n_emb + 255) / 256;
+    if (blocks > NUM_SMS_HINT * 8) blocks = NUM_SMS_HINT * 8;
+    k_ncf_reduce_adam<<<(unsigned)blocks, 256, 0, st>>>(u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ncf_refresh_bf(const float *theta, void *bf, cudaStream_t st) {
+    k_ncf_refresh_bf<<<32, 256, 0, st>>>(theta, reinterpret_cast<bf16 *>(bf));
+    return cudaGetLastError();
+}
+
+}  // namespace ocf
