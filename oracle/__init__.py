@@ -80,6 +80,10 @@ def lib():
             "orc_objective_wr": (_D, [_I64, _I64, _i64, _i32, _d, _d, _d, ctypes.c_int, _D]),
             "orc_als_wr": (None, [_I64, _I64, _i64, _i32, _d, ctypes.c_int, _D, ctypes.c_int,
                                   _d, _d, _d]),
+            "orc_stream_accumulate": (None, [_I64, _i64, _i32, _d, _d, ctypes.c_int, _d, _d,
+                                             _i64]),
+            "orc_stream_solve": (None, [_I64, ctypes.c_int, _d, _d, _i64, _D, ctypes.c_int, _d,
+                                        _i32]),
             "orc_ncf_net_size": (_I64, [ctypes.c_int] * 3),
             "orc_ncf_forward": (None, [_I64, _i32, _i32] + [ctypes.c_int] * 3 + [_d] * 6),
             "orc_ncf_loss_grad": (_D, [_I64, _i32, _i32, _d, _I64, _I64] + [ctypes.c_int] * 3 +
@@ -406,3 +410,36 @@ def ncf_train(ai, sj, r, Ea, Es, net, h1, h2, perms, batch, lr, beta1=0.9, beta2
             losses.append(L)
     return (theta[:nn].copy(), theta[nn:nn + m * d].reshape(m, d).copy(),
             theta[nn + m * d:].reshape(n, d).copy(), np.array(losses))
+
+
+# ---------------------------------------------------------------- streaming refit
+class StreamState:
+    """Per-setting sums of the V-half-step's normal equations over every row
+    ingested so far (G [n, k, k], b [n, k], counts [n]) and the current V."""
+
+    def __init__(self, n, k, lam, weighted=False):
+        self.n, self.k, self.lam, self.weighted = n, k, float(lam), bool(weighted)
+        self.G = np.zeros((n, k, k))
+        self.b = np.zeros((n, k))
+        self.cnt = np.zeros(n, dtype=np.int64)
+        self.V = np.zeros((n, k))
+        self.status = np.zeros(n, dtype=np.int32)
+
+    def add(self, row_ptr, col, val, U):
+        """Add the rank-one terms of rows with known factors U, then re-solve V."""
+        row_ptr = _c(row_ptr, np.int64); col = _c(col, np.int32); val = _c(val, np.float64)
+        U = _c(U, np.float64)
+        lib().orc_stream_accumulate(len(row_ptr) - 1, _p(row_ptr, _i64), _p(col, _i32),
+                                    _p(val, _d), _p(U, _d), self.k, _p(self.G, _d),
+                                    _p(self.b, _d), _p(self.cnt, _i64))
+        lib().orc_stream_solve(self.n, self.k, _p(self.G, _d), _p(self.b, _d),
+                               _p(self.cnt, _i64), self.lam, int(self.weighted), _p(self.V, _d),
+                               _p(self.status, _i32))
+        return self.V
+
+    def ingest(self, row_ptr, col, val):
+        """A batch of new applications: fold-in against the current V, then add."""
+        fold = half_step_wr if self.weighted else half_step
+        U, st = fold(row_ptr, col, val, self.V, self.lam)
+        self.add(row_ptr, col, val, U)
+        return U, st

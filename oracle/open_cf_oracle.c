@@ -24,6 +24,8 @@
  *    in FP64 and, for bit-exact comparison of the integer decision, in FP32.
  *  - The MLP of the learned warm start (SELU activations as named in Sec.
  *    "Collaborative Filtering Model"), forward, backward and Adam, in FP64.
+ *  - The streaming refit of V: per-setting sums of the V-half-step's normal
+ *    equations, grown by each batch of new applications, and the re-solve.
  *  - Neural collaborative filtering, the CF model that section describes
  *    (application and power-cap-pair embeddings, concatenated, through a SELU
  *    MLP to one predicted entry): forward, mean-squared-error gradient incl.
@@ -34,7 +36,8 @@
  * objective monotonicity, normal-equation residuals, exact recovery,
  * hand-computed Algorithm 2 tables and finite differences; the NCF routines
  * against PyTorch's FP64 autograd and Adam, finite differences and invariants
- * (tests/test_oracle_ncf.py).
+ * (tests/test_oracle_ncf.py); the streaming refit against the batch half-step
+ * over the union of ingested rows and numpy's lstsq (tests/test_oracle_stream.py).
  */
 #include <math.h>
 #include <stdint.h>
@@ -741,4 +744,55 @@ void orc_ncf_predict(int64_t m, int64_t n, int d, int h1, int h2, const double *
         orc_ncf_forward(n, ai, sj, d, h1, h2, Ea, Es, net, T + i * n, NULL, NULL);
     }
     free(ai); free(sj);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Streaming refit of V (the joint online refit of Sec. "Online Performance
+ * Prediction" done incrementally): for every setting j the normal equations
+ * of the V-half-step over all rows ingested so far are kept as sums,
+ *     G_j = sum_{i in Omega_j} u_i u_i^T,   b_j = sum_{i in Omega_j} R_ij u_i,
+ *     s_j = |Omega_j|,
+ * so a batch of new applications adds its rank-one terms (its rows' factors
+ * u_i, from the fold-in against the current V) and V is re-solved as
+ *     v_j = (G_j + lambda_j I)^{-1} b_j,  lambda_j = lambda (or lambda s_j, weighted),
+ * with v_j = 0 for a setting no row has observed (as the half-step does). */
+void orc_stream_accumulate(int64_t m, const int64_t *ptr, const int32_t *idx, const double *val,
+                           const double *U, int k, double *G, double *b, int64_t *cnt) {
+    for (int64_t i = 0; i < m; ++i) {
+        const double *u = U + i * k;
+        for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+            const int64_t j = idx[t];
+            double *Gj = G + j * k * k, *bj = b + j * k;
+            for (int p = 0; p < k; ++p) {
+                bj[p] += val[t] * u[p];
+                for (int q = 0; q < k; ++q) Gj[p * k + q] += u[p] * u[q];
+            }
+            cnt[j] += 1;
+        }
+    }
+}
+
+void orc_stream_solve(int64_t n, int k, const double *G, const double *b, const int64_t *cnt,
+                      double lambda, int weighted, double *V, int32_t *status) {
+#pragma omp parallel
+    {
+        double *A = (double *)malloc(sizeof(double) * (size_t)k * k * 2);
+        double *L = A + (size_t)k * k;
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < n; ++j) {
+            int st = ORC_OK;
+            if (cnt[j] == 0) {
+                st = ORC_EMPTY_ROW;
+            } else {
+                const double lam = weighted ? lambda * (double)cnt[j] : lambda;
+                memcpy(A, G + j * k * k, sizeof(double) * (size_t)k * k);
+                for (int p = 0; p < k; ++p) A[p * k + p] += lam;
+                st = orc_cholesky(k, A, L);
+                if (st == ORC_OK) orc_chol_solve(k, L, b + j * k, V + j * k);
+            }
+            if (st != ORC_OK) memset(V + j * k, 0, sizeof(double) * (size_t)k);
+            if (status) status[j] = st;
+        }
+        free(A);
+    }
 }
