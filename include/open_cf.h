@@ -279,6 +279,29 @@ int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
                       const int32_t *col, const float *val, float *U_out, int32_t *status,
                       float *row_rmse, void *stream);
 
+/* Streaming refit of V (Sec. "Online Performance Prediction": new
+ * applications join the matrix and V is refitted with them), done
+ * incrementally.  The handle keeps, for every setting j, the sums of the
+ * V-half-step's normal equations over all rows ingested so far,
+ *     G_j = sum_i u_i u_i^T,  b_j = sum_i R_ij u_i,  s_j = observations,
+ * so that V = argmin over every ingested row with its factor held fixed:
+ *     v_j = (G_j + lambda_j I)^{-1} b_j   (lambda_j = lambda, or lambda s_j when
+ *                                          cfg.weighted_lambda), 0 if s_j = 0.
+ * FP32 or FP64 precision (UNSUPPORTED in BF16_GRAM mode); workspace
+ * n * KP * (KP + 1) reals + 8n bytes (KP = k padded to 8, 16 or 32).
+ *
+ * open_cf_stream_begin: seed the sums with m rows (CSR as everywhere) and their
+ * factors U (m x k real, e.g. the offline block and the U of its fit), then
+ * solve V.  Needs V set (it fixes n); a later open_cf_set_V ends the stream.
+ * open_cf_stream_ingest: a batch of new applications: fold-in of each row
+ * against the current V (U_out m_new x k real, status as open_cf_complete_rows),
+ * their terms added to the sums, every v_j re-solved into the handle's V. */
+int open_cf_stream_begin(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                         const int32_t *col, const void *val, const void *U, void *stream);
+int open_cf_stream_ingest(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_t *row_ptr,
+                          const int32_t *col, const void *val, void *U_out, int32_t *status,
+                          void *stream);
+
 /* Allocation-free CSR -> CSC (no counterpart in the paper; a service of this
  * library).  Some callers cannot allocate device memory: their host framework
  * owns every device allocation through its own pool and forbids direct

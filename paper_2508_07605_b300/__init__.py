@@ -69,6 +69,8 @@ _SIGNATURES = {
     "open_cf_mlp_train_step": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _F, _V, _V, _V]),
     "open_cf_mlp_infer": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
     "open_cf_phase_detect": (ctypes.c_int, [_V, _I64, _I64, _I64, _F, _I32, _V, _V]),
+    "open_cf_stream_begin": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V]),
+    "open_cf_stream_ingest": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V]),
     "open_cf_ncf_create": (ctypes.c_int, [_I64, _I32, _V, _I32, _V, _I32, ctypes.c_int,
                                           ctypes.POINTER(_V)]),
     "open_cf_ncf_destroy": (None, [_V]),
@@ -263,6 +265,23 @@ class OpenCF:
         self._check(lib().open_cf_select(self._h, _ptr(T), m, T.stride(0), _ptr(best), _ptr(sav),
                                          float(gamma), int(baseline), self._stream()))
         return best, sav
+
+    def stream_begin(self, row_ptr, col, val, U):
+        """Seed the streaming refit with rows and their factors U (m x k); V is
+        re-solved over them."""
+        m, nnz = self._csr(row_ptr, col, val)
+        self._real(U, "U")
+        self._check(lib().open_cf_stream_begin(self._h, m, nnz, _ptr(row_ptr), _ptr(col),
+                                               _ptr(val), _ptr(U), self._stream()))
+
+    def stream_ingest(self, row_ptr, col, val):
+        """A batch of new applications: (U_new, status); V is refitted in place."""
+        m, nnz = self._csr(row_ptr, col, val)
+        U = self._empty(m, self.k)
+        st = self._empty(m, dtype=torch.int32)
+        self._check(lib().open_cf_stream_ingest(self._h, m, nnz, _ptr(row_ptr), _ptr(col),
+                                                _ptr(val), _ptr(U), _ptr(st), self._stream()))
+        return U, st
 
     def objective(self, row_ptr, col, val, U, row_rmse: bool = False):
         m, nnz = self._csr(row_ptr, col, val)

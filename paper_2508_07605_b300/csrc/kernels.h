@@ -26,6 +26,14 @@ template <typename TV> struct SolveArgs {
     const int32_t *row_map = nullptr;   // optional: system i is CSR row row_map[i]
     const int64_t *m_dev = nullptr;     // optional: number of systems read on the device
     bool wr = false;                    // weighted lambda: the diagonal gets lambda * s_i
+    // Streaming refit: per-system stored sums of earlier rows' normal equations
+    // (Gram [KP][KP], right-hand side [KP], observation count), indexed by the
+    // CSR row; they are added to this call's sums before lambda, and with
+    // gram_keep the totals are written back.
+    TV *gram = nullptr;
+    TV *gram_b = nullptr;
+    int64_t *gram_n = nullptr;
+    bool gram_keep = false;
 };
 
 template <typename TV, typename TC>

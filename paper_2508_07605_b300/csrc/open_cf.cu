@@ -60,6 +60,8 @@ struct open_cf {
     Buf mlp_img, mlp_imap, mlp_err;   // tcgen05 weight images, their map, timeout flag
     Buf vimg, pt_err;                 // split BF16 operand images of V, timeout flag (predict)
     Buf ccount;                       // observations per column (weighted-lambda objective)
+    Buf sg, sb, sn;                   // streaming refit: per-setting Gram, RHS, count sums
+    bool stream_on = false;
     int num_sms = 0;
     bool mlp_ready = false;
     int64_t mlp_Bcap = 0;
@@ -651,7 +653,8 @@ void open_cf_destroy(open_cf_t *h) {
                        &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter, &h->mlp_th,
                        &h->mlp_g, &h->mlp_m1, &h->mlp_m2, &h->mlp_bf, &h->mlp_map, &h->mlp_t,
                        &h->mlp_cn, &h->mlp_scr, &h->mlp_G, &h->mlp_img, &h->mlp_imap,
-                       &h->mlp_err, &h->vimg, &h->pt_err, &h->ccount})
+                       &h->mlp_err, &h->vimg, &h->pt_err, &h->ccount, &h->sg, &h->sb,
+                       &h->sn})
             free_buf(*b);
     }
     delete h;
@@ -689,6 +692,7 @@ int open_cf_set_V(open_cf_t *h, const void *V, int64_t n, void *stream) {
         CK(h, cudaStreamSynchronize(st));  // host vector goes out of scope
     }
     h->n = n;
+    h->stream_on = false;   // a new V starts a new stream
     h->V_set = true;
     return OPEN_CF_OK;
 }
@@ -831,6 +835,107 @@ int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
                                   st);
     return fit_sweeps<float>(h, m, nz, jp, (int32_t *)h->j_idx.p, (float *)h->j_val.p,
                              (float *)U_out, h->m_off, m_new, nullptr, nullptr, nullptr, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Streaming refit: CSC of a batch of rows with (padded) factors Uw, then the
+// V-half-step with the stored sums added and kept (every setting re-solved).
+template <typename TV>
+int stream_vhalf(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
+                 const TV *val, const TV *Uw, cudaStream_t st) {
+    const int64_t n = h->n;
+    const CscPlan plan = csc_plan(m, n, nnz, 0);
+    CK(h, ensure(h, h->csc_ptr, sizeof(int64_t) * (n + 1)));
+    CK(h, ensure(h, h->csc_idx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    CK(h, ensure(h, h->csc_val, sizeof(TV) * std::max<int64_t>(nnz, 1)));
+    CK(h, ensure(h, h->cnt, sizeof(int32_t) * n * plan.nb));
+    CK(h, ensure(h, h->tot, sizeof(int64_t) * n));
+    int64_t *cptr = (int64_t *)h->csc_ptr.p;
+    CK(h, launch_csr_to_csc<TV>(m, n, nnz, ptr, idx, val, cptr, (int32_t *)h->csc_idx.p,
+                                (TV *)h->csc_val.p, (int32_t *)h->cnt.p, (int64_t *)h->tot.p, plan,
+                                st));
+    SolveArgs<TV> va{n, nnz, cptr, (const int32_t *)h->csc_idx.p, (const TV *)h->csc_val.p, Uw,
+                     m, (TV *)h->V.p, h->KP, h->KP, nullptr, h->cfg.lambda};
+    va.wr = h->cfg.weighted_lambda != 0;
+    va.gram = (TV *)h->sg.p;
+    va.gram_b = (TV *)h->sb.p;
+    va.gram_n = (int64_t *)h->sn.p;
+    va.gram_keep = true;
+    CK(h, half_step<TV>(h, va, st));
+    return OPEN_CF_OK;
+}
+
+template <typename TV>
+int stream_begin_t(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
+                   const TV *val, const TV *U, cudaStream_t st) {
+    const int KP = h->KP;
+    CK(h, ensure(h, h->U_w, sizeof(TV) * std::max<int64_t>(m, 1) * KP));
+    TV *Uw = (TV *)h->U_w.p;
+    if (m > 0) CK(h, launch_pack_rows<TV>(U, m, h->k, h->k, Uw, KP, st));
+    return stream_vhalf<TV>(h, m, nnz, ptr, idx, val, Uw, st);
+}
+
+template <typename TV>
+int stream_ingest_t(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
+                    const TV *val, TV *U_out, int32_t *status, cudaStream_t st) {
+    const int KP = h->KP;
+    CK(h, ensure(h, h->U_w, sizeof(TV) * std::max<int64_t>(m, 1) * KP));
+    TV *Uw = (TV *)h->U_w.p;
+    SolveArgs<TV> ua{m, nnz, ptr, idx, val, (const TV *)h->V.p, h->n, Uw, KP, KP, status,
+                     h->cfg.lambda};
+    ua.wr = h->cfg.weighted_lambda != 0;
+    CK(h, half_step<TV>(h, ua, st));   // fold-in against the current V
+    if (m > 0) CK(h, launch_unpack_rows<TV>(Uw, m, KP, h->k, U_out, st));
+    return stream_vhalf<TV>(h, m, nnz, ptr, idx, val, Uw, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int open_cf_stream_begin(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                         const int32_t *col, const void *val, const void *U, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (h->cfg.precision == OPEN_CF_BF16_GRAM)
+        return fail(h, OPEN_CF_UNSUPPORTED, "the streaming refit runs in FP32 or FP64 mode");
+    int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: the number of settings is unknown");
+    if (m > 0 && !U) return fail(h, OPEN_CF_INVALID_ARG, "U is NULL");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const int64_t n = h->n, KP = h->KP;
+    CK(h, ensure(h, h->sg, h->esz * n * KP * KP));
+    CK(h, ensure(h, h->sb, h->esz * n * KP));
+    CK(h, ensure(h, h->sn, sizeof(int64_t) * n));
+    CK(h, cudaMemsetAsync(h->sg.p, 0, h->esz * n * KP * KP, st));
+    CK(h, cudaMemsetAsync(h->sb.p, 0, h->esz * n * KP, st));
+    CK(h, cudaMemsetAsync(h->sn.p, 0, sizeof(int64_t) * n, st));
+    rc = h->f64 ? stream_begin_t<double>(h, m, nnz, row_ptr, col, as<double>(val), as<double>(U), st)
+                : stream_begin_t<float>(h, m, nnz, row_ptr, col, as<float>(val), as<float>(U), st);
+    if (rc == OPEN_CF_OK) h->stream_on = true;
+    return rc;
+}
+
+int open_cf_stream_ingest(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_t *row_ptr,
+                          const int32_t *col, const void *val, void *U_out, int32_t *status,
+                          void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!h->stream_on) return fail(h, OPEN_CF_NOT_FITTED, "call open_cf_stream_begin first");
+    int rc = check_csr_args(h, m_new, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (m_new > 0 && !U_out) return fail(h, OPEN_CF_INVALID_ARG, "U_out is NULL");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    return h->f64 ? stream_ingest_t<double>(h, m_new, nnz, row_ptr, col, as<double>(val),
+                                            (double *)U_out, status, st)
+                  : stream_ingest_t<float>(h, m_new, nnz, row_ptr, col, as<float>(val),
+                                           (float *)U_out, status, st);
 }
 
 int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t *best,

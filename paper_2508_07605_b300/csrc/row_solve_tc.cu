@@ -461,6 +461,20 @@ k_row_solve_tc(SolveArgs<float> a) {
                 for (int e = 0; e < KP; ++e) A[e] = TC(S.G[q][e]);
                 bt = TC(S.b[q]);
             }
+            if (a.gram && !bad && base + slot < M) {   // streaming: stored sums of earlier rows
+                const int64_t i = a.row_map ? a.row_map[base + slot] : base + slot;
+                float *gq = a.gram + (i * KP + q) * KP;
+#pragma unroll
+                for (int e = 0; e < KP; ++e) A[e] += TC(gq[e]);
+                bt += TC(a.gram_b[i * KP + q]);
+                s += a.gram_n[i];
+                if (a.gram_keep && writer) {
+#pragma unroll
+                    for (int e = 0; e < KP; ++e) gq[e] = (float)A[e];
+                    a.gram_b[i * KP + q] = (float)bt;
+                    if (q == 0) a.gram_n[i] = s;
+                }
+            }
             const TC lam = a.wr ? TC(a.lambda * (double)s) : TC(a.lambda);   // weighted: lambda s_i
 #pragma unroll
             for (int e = 0; e < KP; ++e)

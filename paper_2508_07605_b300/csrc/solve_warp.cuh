@@ -37,7 +37,7 @@ __device__ __forceinline__ void solve_system(const SolveArgs<TV> &a, int64_t i,
     {
         int64_t beg = 0, end = 0;
         bool bad = !row_bounds(a.ptr, i, a.nnz, beg, end);
-        const int64_t s = end - beg;
+        int64_t s = end - beg;
 
         // ---- staged masked Gram + RHS ---------------------------------------
         TV acc[KP];
@@ -110,6 +110,19 @@ __device__ __forceinline__ void solve_system(const SolveArgs<TV> &a, int64_t i,
 #pragma unroll
             for (int e = 0; e < KP; ++e) A[e] = TC(acc[e]);
             bt = TC(bq);
+        }
+        if (a.gram && !bad && (WPS == 1 || warp == 0)) {   // streaming: stored sums of earlier rows
+            TV *gq = a.gram + (i * KP + q) * KP;
+#pragma unroll
+            for (int e = 0; e < KP; ++e) A[e] += TC(gq[e]);
+            bt += TC(a.gram_b[i * KP + q]);
+            s += a.gram_n[i];
+            if (a.gram_keep && g == 0) {
+#pragma unroll
+                for (int e = 0; e < KP; ++e) gq[e] = TV(A[e]);
+                a.gram_b[i * KP + q] = TV(bt);
+                if (q == 0) a.gram_n[i] = s;
+            }
         }
         const TC lam = a.wr ? TC(a.lambda * (double)s) : TC(a.lambda);   // weighted: lambda s_i
 #pragma unroll

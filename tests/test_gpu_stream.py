@@ -1,0 +1,95 @@
+"""GPU-vs-oracle parity of the streaming refit of V: the per-setting sums of
+the V-half-step's normal equations, seeded with an offline block and grown by
+batches of new applications (fold-in against the current V, then every
+setting re-solved).  Checked stepwise: the oracle's state is fed the GPU's own
+factors of each batch, so both sides hold the same sums up to rounding."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+from gpu_util import TOL_FP32, TOL_FP64, csr_dev, dev, host, rounded, row_rel_err
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU hosts deselect these
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2508_07605_b300 as ocf  # noqa: E402
+
+DT = {"fp32": torch.float32, "fp64": torch.float64}
+# FP32: the sums are accumulated in FP32 over every ingested observation
+# (up to ~500 per setting here), so a setting's solve carries that rounding
+# on top of the per-solve gate.
+TOL = {"fp32": 20 * TOL_FP32, "fp64": 100 * TOL_FP64}
+
+
+def _block(rng, m, n, density, dt):
+    rows, cols = [], []
+    for i in range(m):
+        c = np.nonzero(rng.random(n) < density)[0]
+        if len(c) == 0:
+            c = np.array([rng.integers(n)])
+        rows.append(np.full(len(c), i)); cols.append(c)
+    cols = np.concatenate(cols).astype(np.int32)
+    ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum([len(r) for r in rows], out=ptr[1:])
+    return ptr, cols, rounded(0.2 + rng.random(len(cols)), dt)
+
+
+@pytest.mark.parametrize("precision,k,weighted", [("fp32", 16, False), ("fp32", 32, False),
+                                                  ("fp32", 8, False), ("fp32", 16, True),
+                                                  ("fp64", 8, False), ("fp64", 32, True)])
+def test_stream_stepwise_parity(orc, precision, k, weighted):
+    rng = np.random.default_rng(40 + k)
+    dt = DT[precision]
+    n, lam = 128, 0.05
+    off = _block(rng, 600, n, 0.3, dt)
+    U_off = rounded(rng.standard_normal((600, k)) / np.sqrt(k), dt)
+    h = ocf.OpenCF(k=k, lam=lam, precision=precision, weighted_lambda=weighted)
+    h.set_V(dev(np.zeros((n, k)), dt))
+    h.stream_begin(*csr_dev(*off, dt), dev(U_off, dt))
+    V0 = host(h.get_V()).astype(np.float64)
+    torch.cuda.synchronize()
+    ref = orc.StreamState(n, k, lam, weighted)
+    ref.add(*off, U_off)
+    assert row_rel_err(V0, ref.V).max() <= TOL[precision]
+    Vprev = V0
+    for b, (mb, dens) in enumerate([(200, 0.05), (1, 0.5), (350, 0.1)]):
+        batch = _block(rng, mb, n, dens, dt)
+        U, st = h.stream_ingest(*csr_dev(*batch, dt))
+        V = host(h.get_V()).astype(np.float64)
+        torch.cuda.synchronize()
+        fold = orc.half_step_wr if weighted else orc.half_step
+        Uref, sref = fold(*batch, Vprev, lam)
+        assert np.array_equal(host(st), sref)
+        assert row_rel_err(host(U), Uref).max() <= TOL[precision], b
+        ref.add(*batch, host(U).astype(np.float64))
+        assert row_rel_err(V, ref.V).max() <= TOL[precision], (b, row_rel_err(V, ref.V).max())
+        Vprev = V
+
+
+def test_stream_untouched_settings_and_errors(orc):
+    rng = np.random.default_rng(5)
+    n, k, lam = 64, 16, 0.05
+    off = _block(rng, 300, n - 4, 0.3, torch.float32)        # settings 60..63 never observed
+    U_off = rounded(rng.standard_normal((300, k)) / 4, torch.float32)
+    h = ocf.OpenCF(k=k, lam=lam)
+    h.set_V(dev(np.ones((n, k)), torch.float32))
+    with pytest.raises(ocf.OpenCFError) as e:
+        h.stream_ingest(*csr_dev(*off, torch.float32))
+    assert e.value.code == ocf.NOT_FITTED
+    h.stream_begin(*csr_dev(*off, torch.float32), dev(U_off, torch.float32))
+    V = host(h.get_V())
+    torch.cuda.synchronize()
+    assert np.all(V[n - 4:] == 0)
+    h.set_V(dev(np.ones((n, k)), torch.float32))                # a new V ends the stream
+    with pytest.raises(ocf.OpenCFError) as e:
+        h.stream_ingest(*csr_dev(*off, torch.float32))
+    assert e.value.code == ocf.NOT_FITTED
+    hb = ocf.OpenCF(k=32, lam=lam, precision="bf16_gram")
+    hb.set_V(dev(np.ones((n, 32)), torch.float32))
+    with pytest.raises(ocf.OpenCFError) as e:
+        hb.stream_begin(*csr_dev(*off, torch.float32), dev(np.zeros((300, 32)), torch.float32))
+    assert e.value.code == ocf.UNSUPPORTED
