@@ -1141,10 +1141,12 @@ def run_gpu_ncf(args):
                                  best.cpu().numpy(), b32))},
         "roofline": {"kernel": "k_ncf_predict_tc (completion call: first layer + pairs)",
                      "bound": "alu", "achieved": gexp, "peak": mufu, "unit": "Gexp/s",
-                     "frac": gexp / mufu, "traffic": None,
-                     "peak_source": "148 SMs x 16 ex2 per clock x median SM clock (derived)",
-                     "note": f"{EXP_PER_PAIR} SELU exponentials per entry; tensor side "
-                             f"{tflops:.1f} TFLOP/s of {bf16_peak:.0f} measured bf16"},
+                     "frac": gexp / mufu, "traffic": profiled_ncf_traffic(m * n),
+                     "peak_source": "148 SMs x 16 ex2 per clock x median SM clock (derived: "
+                                    "one FP32-rate exponential per SELU)",
+                     "note": f"{EXP_PER_PAIR} SELU exponentials per entry, evaluated as packed "
+                             f"FP16 pairs; tensor side {tflops:.1f} TFLOP/s of {bf16_peak:.0f} "
+                             f"measured bf16"},
         "cpu_baseline": {"value": nnz / t_orc_step, "unit": "samples/s",
                          "cores": orc.num_threads(), "kind": "oracle",
                          "sample": f"{tr} training samples and 16 completed rows, "
@@ -1162,6 +1164,158 @@ def run_gpu_ncf(args):
 NCF_MMA_MACS = 128 * 64   # h1 W2 per completed entry
 
 
+def profiled_ncf_traffic(entries):
+    """DRAM bytes of one completion launch at `entries` entries, scaled from the
+    committed ncu summary's smaller capture (traffic grows with the entries
+    written), or None when the kernel changed since."""
+    import hashlib
+    import re
+    try:
+        src = os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "ncf.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        text = open(os.path.join(ROOT, "profiles", "ncf_predict_tc.md")).read()
+    except OSError:
+        return None
+    m = re.search(r"sha256 \(first 16 hex\): ([0-9a-f]{16})", text)
+    b = re.search(r"\| dram_bytes_per_launch \| (\d+) \| (\d+) entries \|", text)
+    if not m or not b or m.group(1) != h:
+        return None
+    return int(b.group(1)) * entries / int(b.group(2))
+
+
+WORKLOAD_STREAM = "streaming refit: workload 2's matrix as the offline block (fit, 15 sweeps), " \
+                  "then 16 batches of 8192 new apps x 16 observed settings each (rank-16 model, " \
+                  "N(0,0.01) noise); per batch: fold-in against the current V, the batch's " \
+                  "terms added to the per-setting normal-equation sums, all 1024 settings re-solved"
+
+
+def run_gpu_stream(args):
+    """Streaming refit: one step = one batch of new applications ingested."""
+    import torch
+
+    import paper_2508_07605_b300 as ocf
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    w = synth.make_stream(seed=0)
+    off = w.offline
+    cpu, gpu = off.caps()
+    f32 = torch.float32
+    h = ocf.OpenCF(k=off.k, lam=off.lam, sweeps=off.sweeps, cpu_caps=cpu, gpu_caps=gpu)
+    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
+    o_csr = (to(off.row_ptr, torch.int64), to(off.col, torch.int32), to(off.val, f32))
+    h.set_V(to(off.V0, f32))
+    U_off = h.fit_csr(*o_csr, off.n)
+    V_fit = h.get_V().clone()
+    d_batches = [(to(p, torch.int64), to(c, torch.int32), to(v, f32)) for p, c, v in w.batches]
+    nb = len(d_batches)
+    W = max(args.warmup, 3)
+    steps = min(args.steps, nb)
+
+    def restart():
+        h.set_V(V_fit)
+        h.stream_begin(*o_csr, U_off)
+
+    # warm-up on a restarted stream, then the timed stream from the start
+    restart()
+    for b in range(min(W, nb)):
+        h.stream_ingest(*d_batches[b])
+    torch.cuda.synchronize()
+    restart()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_stream.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                          else "/tmp/clocks_bench_stream.csv")
+    U_new = []
+    with clocks:
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            U, _ = h.stream_ingest(*d_batches[i])
+            ev[i][1].record(stream)
+            U_new.append(U)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_step = total_ms / steps / 1e3
+    V_gpu = h.get_V().double().cpu().numpy()
+    clk = clocks.summary(0)
+
+    # ---- oracle: the same stream in FP64 (seeded with the GPU's offline factors)
+    import oracle as orc
+    orc.build()
+    st = orc.StreamState(off.n, off.k, off.lam)
+    st.add(off.row_ptr, off.col, off.val.astype(np.float32).astype(np.float64),
+           U_off.double().cpu().numpy())
+    t0 = time.perf_counter()
+    Uo = []
+    for i in range(steps):
+        p, c, v = w.batches[i]
+        u, _ = st.ingest(p, c, v.astype(np.float32).astype(np.float64))
+        Uo.append(u)
+    t_orc = (time.perf_counter() - t0) / steps
+    vrel = np.linalg.norm(V_gpu - st.V, axis=1) / np.maximum(np.linalg.norm(st.V, axis=1), 1e-30)
+    # held-out error of the first batch's applications under the final V (all settings)
+    rows = w.truth_new.shape[0]
+    Ug = U_new[0][:rows].double().cpu().numpy()
+    rmse_g = float(np.sqrt(np.mean((Ug @ V_gpu.T - w.truth_new) ** 2)))
+    rmse_o = float(np.sqrt(np.mean((Uo[0][:rows] @ st.V.T - w.truth_new) ** 2)))
+
+    # ---- end to end: host batch in, factors out, through the C ABI
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    hb = [(pin(p), pin(c), pin(v.astype(np.float32))) for p, c, v in w.batches[:steps]]
+    db = [torch.empty_like(x) for x in d_batches[0]]
+    o_U = torch.empty(w.batch, off.k, dtype=f32).pin_memory()
+    restart()
+    torch.cuda.synchronize()
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ee[i][0].record(stream)
+        for d_, h_ in zip(db, hb[i]):
+            d_.copy_(h_, non_blocking=True)
+        U, _ = h.stream_ingest(*db)
+        o_U.copy_(U, non_blocking=True)
+        ee[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
+
+    nnz_b = int(w.batches[0][0][-1])
+    k, n = off.k, off.n
+    fl = algorithmic_flops_half(nnz_b, w.batch, k) + algorithmic_flops_half(nnz_b, n, k) + \
+        n * k * k   # + adding the stored sums
+    achieved = fl / t_step / 1e12
+    peak = fp32_alu_peak_tflops(clk["sm_mhz"] or 2032.0)
+    line = {
+        "metric": "streamed apps/s (fold-in + incremental refit of V)",
+        "value": w.batch / t_step, "unit": "apps/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_STREAM, "batch": w.batch, "obs_per_app": 16,
+                   "n": n, "k": k, "parallelism": "replicas1",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "parity_vs_oracle": {"V_max_row_rel_err": float(vrel.max()),
+                             "new_app_rmse": {"gpu": rmse_g, "oracle_fp64": rmse_o}},
+        "roofline": {"kernel": "stream ingest (fold-in + V-half with stored sums)",
+                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2 x median SM clock (derived)"},
+        "cpu_baseline": {"value": w.batch / t_orc, "unit": "apps/s",
+                         "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": f"the same {steps} batches in FP64"},
+        "e2e": {"value": w.batch * steps / (e2e_ms / 1e3), "unit": "apps/s",
+                "h2d_bytes_per_step": int(sum(x.nbytes for x in w.batches[0])),
+                "d2h_bytes_per_step": int(4 * w.batch * k)},
+        "gpu_launches": 9 * steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1169,14 +1323,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c4", "c5", "phase", "ncf"],
+                    choices=["c1", "c2", "c3", "c4", "c5", "phase", "ncf", "stream"],
                     help="c1: 64x120 FP64 joint fit; "
                          "c2: 4096x1024 fit (default, the headline line); "
                          "c3: 10,000 uneven problems in one batched launch; "
                          "c4: learned warm start (MLP + ALS fallback) on 2^20 new apps; "
                          "c5: 1M x 4096 BF16-Gram fold-in + selection; "
                          "phase: Algorithm 1 over 2^17 power traces; "
-                         "ncf: the paper's NCF model, one epoch + completion")
+                         "ncf: the paper's NCF model, one epoch + completion; "
+                         "stream: streaming refit, one batch of 8192 new apps per step")
     ap.add_argument("--train-steps", type=int, default=30000,
                     help="c4 only: training steps (batch 4096) before the timed completions")
     ap.add_argument("--pool", type=int, default=1 << 20, help="c4 only: training apps")
@@ -1199,6 +1354,8 @@ def main():
         return run_gpu_learned(args)
     if args.workload == "ncf":
         return run_gpu_ncf(args)
+    if args.workload == "stream":
+        return run_gpu_stream(args)
     return run_gpu(args)
 
 

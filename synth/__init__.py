@@ -524,3 +524,40 @@ def coo_from_csr(row_ptr, col):
     """(app index, setting index) of every observed entry, in CSR order."""
     ai = np.repeat(np.arange(len(row_ptr) - 1, dtype=np.int32), np.diff(row_ptr))
     return ai, np.asarray(col, dtype=np.int32)
+
+
+# ---------------------------------------------------------------------------
+# Streaming refit: an offline block (workload 2's matrix) and a stream of new
+# applications from the same rank-16 model, each profiled online under a few
+# settings (Sec. "Online Performance Prediction").
+@dataclasses.dataclass
+class StreamWorkload:
+    offline: CompletionProblem
+    batches: list          # [(row_ptr, col, val)] per batch of new applications
+    truth_new: np.ndarray  # [m_new, n] noiseless rows of the new applications
+    batch: int
+
+
+def make_stream(seed: int = 0, n_batches: int = 16, batch: int = 8192, obs: int = 16,
+                truth_rows: int = 2048) -> StreamWorkload:
+    rng = np.random.default_rng(seed)
+    off = make_sparse_problem(seed=seed, keep_truth=False)
+    n, rank = off.n, 16
+    # the offline matrix's generator, re-drawn with the same seed, gives its V;
+    # new applications draw fresh U rows from the same distribution
+    g = np.random.default_rng(seed)
+    Ut = g.standard_normal((off.m, rank)) / 2.0
+    Vt = g.standard_normal((n, rank)) / 2.0
+    scale = float(np.abs(Ut @ Vt.T).max())
+    batches, truth = [], []
+    for _ in range(n_batches):
+        Un = rng.standard_normal((batch, rank)) / 2.0
+        cols = np.sort(np.argsort(rng.random((batch, n)), axis=1)[:, :obs], axis=1)
+        rows = np.repeat(np.arange(batch), obs)
+        tv = np.einsum("bk,bok->bo", Un, Vt[cols]) / scale
+        val = (tv + rng.normal(0.0, NOISE_STD, size=tv.shape)).ravel()
+        ptr = np.arange(0, batch * obs + 1, obs, dtype=np.int64)
+        batches.append((ptr, cols.ravel().astype(np.int32), val))
+        if len(truth) * batch < truth_rows:
+            truth.append(Un @ Vt.T / scale)
+    return StreamWorkload(off, batches, np.concatenate(truth)[:truth_rows], batch)
