@@ -443,3 +443,45 @@ class StreamState:
         U, st = fold(row_ptr, col, val, self.V, self.lam)
         self.add(row_ptr, col, val, U)
         return U, st
+
+
+# ---------------------------------------------------------------- performance predictor
+def pred_unpack(params, n_features, h1=128, h2=64):
+    """Packed [W1 (nf x h1), b1, W2 (h1 x h2), b2, w3, b3] -> the layer list of
+    mlp_forward / mlp_loss_grad (output width 1)."""
+    p = np.asarray(params, dtype=np.float64)
+    o, out = 0, []
+    for shape in [(n_features, h1), (h1,), (h1, h2), (h2,), (h2, 1), (1,)]:
+        size = int(np.prod(shape))
+        out.append(p[o:o + size].reshape(shape))
+        o += size
+    assert o == p.size
+    return out
+
+
+def pred_forward(X, params, n_features):
+    return mlp_forward(X, pred_unpack(params, n_features))[2][:, 0]
+
+
+def pred_loss_grad(X, y, params, n_features):
+    """Mean squared error of the predictor on (X, y) and its packed gradient."""
+    L, grads = mlp_loss_grad(X, pred_unpack(params, n_features), np.asarray(y)[:, None],
+                             np.ones((1, 1)))
+    return L, np.concatenate([g.ravel() for g in grads])
+
+
+def pred_train(X, y, params, n_features, perms, batch, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Mini-batch Adam over the samples in the orders perms[e]; returns
+    (packed parameters, per-step losses)."""
+    theta = np.array(params, dtype=np.float64, copy=True)
+    m1 = np.zeros_like(theta); m2 = np.zeros_like(theta)
+    X = np.asarray(X, np.float64); y = np.asarray(y, np.float64)
+    losses, t = [], 0
+    for perm in perms:
+        for b0 in range(0, len(perm), batch):
+            sel = perm[b0:b0 + batch]
+            L, g = pred_loss_grad(X[sel], y[sel], theta, n_features)
+            t += 1
+            adam(theta, g, m1, m2, t, lr, beta1, beta2, eps)
+            losses.append(L)
+    return theta, np.array(losses)

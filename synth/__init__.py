@@ -561,3 +561,66 @@ def make_stream(seed: int = 0, n_batches: int = 16, batch: int = 8192, obs: int 
         if len(truth) * batch < truth_rows:
             truth.append(Un @ Vt.T / scale)
     return StreamWorkload(off, batches, np.concatenate(truth)[:truth_rows], batch)
+
+
+# ---------------------------------------------------------------------------
+# Offline performance predictor: synthetic profiling runs.  Each application
+# has a CPU share of its baseline runtime and how memory-bound its CPU and GPU
+# parts are; a run under caps (c, g) yields the paper's seven inputs (CPU cap,
+# GPU cap, memory throughput, IPS, SM clock, DRAM active, FP active) and the
+# normalised performance (baseline runtime / runtime, 1 at the largest caps).
+@dataclasses.dataclass
+class CounterRuns:
+    X: np.ndarray      # [N, 7] inputs, each scaled to about [0, 1]
+    y: np.ndarray      # [N] normalised performance
+    app: np.ndarray    # [N] application index
+    setting: np.ndarray  # [N] setting index (CPU-major)
+
+
+def make_counters(seed: int = 0, n_apps: int = 512, n_cpu: int = 16, n_gpu: int = 64,
+                  runs: Optional[int] = None, noise: float = 0.02) -> CounterRuns:
+    """All settings of every application (runs None) or `runs` random settings each."""
+    rng = np.random.default_rng(seed)
+    cpu, gpu = cap_grid(n_cpu, n_gpu)
+    n = n_cpu * n_gpu
+    cpu_share = rng.uniform(0.05, 0.6, n_apps)
+    mem_c = rng.uniform(0.0, 1.0, n_apps)
+    mem_g = rng.uniform(0.0, 1.0, n_apps)
+    flop = rng.uniform(0.2, 1.0, n_apps)
+    ips0 = rng.uniform(0.5, 1.0, n_apps)
+    if runs is None:
+        app = np.repeat(np.arange(n_apps), n)
+        setting = np.tile(np.arange(n), n_apps)
+    else:
+        app = np.repeat(np.arange(n_apps), runs)
+        setting = np.concatenate([rng.choice(n, runs, replace=False) for _ in range(n_apps)])
+    c = cpu[setting // n_gpu] / cpu[-1]
+    g = gpu[setting % n_gpu] / gpu[-1]
+    a = app
+    s_cpu = c ** (0.3 + 0.5 * (1.0 - mem_c[a]))                  # CPU speed under its cap
+    clk = np.minimum(1.0, 1.1 * g ** 0.6)                         # SM clock / max clock
+    s_gpu = mem_g[a] * (1.0 - 0.2 * (1.0 - g)) + (1.0 - mem_g[a]) * clk
+    t = cpu_share[a] / s_cpu + (1.0 - cpu_share[a]) / s_gpu       # runtime / baseline runtime
+    y = 1.0 / t
+    mult = lambda: np.exp(rng.normal(0.0, noise, len(a)))
+    X = np.stack([
+        (cpu[setting // n_gpu] - cpu[0]) / (cpu[-1] - cpu[0]),
+        (gpu[setting % n_gpu] - gpu[0]) / (gpu[-1] - gpu[0]),
+        mem_c[a] * s_cpu ** 0.5 * mult(),                          # memory throughput
+        ips0[a] * s_cpu * (1.0 - 0.5 * mem_c[a]) * mult(),         # IPS
+        clk * mult(),                                              # SM clock
+        mem_g[a] * (1.0 - 0.2 * (1.0 - g)) / (s_gpu + 1e-9) * 0.8 * mult(),   # DRAM active
+        flop[a] * clk * (1.0 - 0.5 * mem_g[a]) * mult(),           # FP active
+    ], axis=1)
+    return CounterRuns(X.astype(np.float64), y.astype(np.float64), app.astype(np.int32),
+                       setting.astype(np.int32))
+
+
+def pred_init(rng: np.random.Generator, n_features: int = 7, out_scale: float = 0.1):
+    """Predictor parameters [W1 (n_features x 128), b1, W2 (128 x 64), b2, w3, b3]
+    (LeCun-normal weights, zero biases, output weights scaled), packed."""
+    W1 = rng.standard_normal((n_features, NCF_H1)) / math.sqrt(n_features)
+    W2 = rng.standard_normal((NCF_H1, NCF_H2)) / math.sqrt(NCF_H1)
+    w3 = rng.standard_normal(NCF_H2) / math.sqrt(NCF_H2) * out_scale
+    return np.concatenate([W1.ravel(), np.zeros(NCF_H1), W2.ravel(), np.zeros(NCF_H2), w3,
+                           np.zeros(1)])

@@ -157,3 +157,31 @@ def test_ncf_learns_a_low_rank_matrix(orc):
                         for j in range(prob.n)])
     base = np.sqrt(np.mean((colmean[prob.heldout_cols] - prob.heldout_truth) ** 2))
     assert rmse < 0.6 * base, (rmse, base)
+
+
+def test_predictor_training_matches_torch_adam(orc):
+    """The offline performance predictor: 7 inputs -> 128 -> 64 SELU -> 1."""
+    rng = np.random.default_rng(9)
+    runs = synth.make_counters(seed=1, n_apps=6, n_cpu=2, n_gpu=4)
+    X, y = runs.X, runs.y
+    params = synth.pred_init(rng, 7, out_scale=1.0) + 0.05 * rng.standard_normal(9345)
+    perms = synth.ncf_perms(rng, len(y), 2)
+    theta, losses = orc.pred_train(X, y, params, 7, perms, 16, 3e-3)
+    W = [torch.tensor(p, dtype=torch.float64, requires_grad=True)
+         for p in orc.pred_unpack(params, 7)]
+    opt = torch.optim.Adam(W, lr=3e-3, betas=(0.9, 0.999), eps=1e-8)
+    tl = []
+    Xt, yt = torch.tensor(X), torch.tensor(y)
+    for perm in perms:
+        for b0 in range(0, len(y), 16):
+            sel = torch.as_tensor(perm[b0:b0 + 16], dtype=torch.long)
+            opt.zero_grad()
+            h = torch.nn.functional.selu(Xt[sel] @ W[0] + W[1])
+            h = torch.nn.functional.selu(h @ W[2] + W[3])
+            L = torch.nn.functional.mse_loss((h @ W[4] + W[5])[:, 0], yt[sel])
+            L.backward()
+            opt.step()
+            tl.append(L.item())
+    assert np.abs(losses - np.array(tl)).max() <= 1e-12
+    ref = np.concatenate([w.detach().numpy().ravel() for w in W])
+    assert np.abs(theta - ref).max() <= 1e-12
