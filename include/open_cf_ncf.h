@@ -17,10 +17,12 @@
  * rules as open_cf_predict / open_cf_select).
  *
  * Precision.  Parameters, gradients and Adam moments are FP32.  Products run
- * on BF16 tensor cores with FP32 accumulation (training: mma.sync GEMMs with
- * fused epilogues; completion: tcgen05 with TMEM accumulators).  The first
- * layer of the completion is evaluated in FP32 as Ea_i W1[0:32] + b1 plus
- * Es_j W1[32:64] (the same value as the concatenated product up to rounding).
+ * on tensor cores with FP32 accumulation: training on BF16 operands (mma.sync,
+ * forward and backward of 64 batch rows per CTA in one kernel); completion on
+ * FP16 operands (tcgen05, TMEM accumulators), its hidden activations formed in
+ * packed FP16 pairs.  The first layer of the completion is evaluated in FP32
+ * as Ea_i W1[0:32] + b1 plus Es_j W1[32:64] (the same value as the
+ * concatenated product up to rounding).
  *
  * Conventions (as in open_cf.h): array arguments are DEVICE pointers on the
  * handle's device unless the name ends in _host; the caller owns them; calls
@@ -103,6 +105,41 @@ int open_cf_ncf_predict(open_cf_ncf_t *h, float *T_out, float gamma, int32_t bas
  * wait (its tiles are then NaN), else OPEN_CF_OK. */
 int open_cf_ncf_skipped(open_cf_ncf_t *h, int64_t *count_host);
 int open_cf_ncf_check(open_cf_ncf_t *h);
+
+/* ------------------------------------------------------------------------
+ * Offline performance predictor (Sec. "Performance Prediction Model"): an MLP
+ * from n_features per-run inputs (the paper's seven: CPU cap, GPU cap, memory
+ * throughput, IPS, SM clock, DRAM active, FP active, each scaled by the caller)
+ * to the run's normalised performance, the same network shape as the NCF
+ * model's MLP (inputs zero padded to 64, 128 -> 64 SELU units, one linear
+ * output), trained with the same kernels on the mean squared error.  Its
+ * predictions for an application's online-profiled runs are the observed
+ * entries of the sparse row the completion fills in (Sec. "Online Performance
+ * Prediction").
+ *
+ * Parameters (float), n_features * 128 + 8449 entries in this order:
+ * W1[n_features][128], b1[128], W2[128][64], b2[64], w3[64], b3[1]. */
+typedef struct open_cf_pred open_cf_pred_t;
+
+/* n_features in [1, 64]; batch a multiple of 64 in [64, 65536]. */
+int open_cf_pred_create(int32_t n_features, int32_t batch, int device, open_cf_pred_t **out);
+void open_cf_pred_destroy(open_cf_pred_t *h);
+const char *open_cf_pred_last_error(const open_cf_pred_t *h);
+/* Resets Adam. */
+int open_cf_pred_set_params(open_cf_pred_t *h, const float *params, void *stream);
+int open_cf_pred_get_params(open_cf_pred_t *h, float *params, void *stream);
+/* N samples: X [N][n_features] (float), y [N] (float); epochs of mini-batch
+ * Adam as open_cf_ncf_train (perms [epochs][N] int32; loss_out
+ * double[epochs * ceil(N / batch)] or NULL). */
+int open_cf_pred_train(open_cf_pred_t *h, int64_t N, const float *X, const float *y,
+                       int32_t epochs, const int32_t *perms, float lr, double *loss_out,
+                       void *stream);
+/* Gradient of one batch of B <= batch samples, no update (g_params in the
+ * parameter layout above; either output may be NULL). */
+int open_cf_pred_grad(open_cf_pred_t *h, int64_t B, const float *X, const float *y,
+                      double *loss_out, float *g_params, void *stream);
+/* y_out[N] = the predicted normalised performance of every sample. */
+int open_cf_pred_infer(open_cf_pred_t *h, int64_t N, const float *X, float *y_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -82,6 +82,14 @@ _SIGNATURES = {
     "open_cf_ncf_predict": (ctypes.c_int, [_V, _V, _F, _I32, _V, _V, _V]),
     "open_cf_ncf_skipped": (ctypes.c_int, [_V, ctypes.POINTER(_I64)]),
     "open_cf_ncf_check": (ctypes.c_int, [_V]),
+    "open_cf_pred_create": (ctypes.c_int, [_I32, _I32, ctypes.c_int, ctypes.POINTER(_V)]),
+    "open_cf_pred_destroy": (None, [_V]),
+    "open_cf_pred_last_error": (ctypes.c_char_p, [_V]),
+    "open_cf_pred_set_params": (ctypes.c_int, [_V, _V, _V]),
+    "open_cf_pred_get_params": (ctypes.c_int, [_V, _V, _V]),
+    "open_cf_pred_train": (ctypes.c_int, [_V, _I64, _V, _V, _I32, _V, _F, _V, _V]),
+    "open_cf_pred_grad": (ctypes.c_int, [_V, _I64, _V, _V, _V, _V, _V]),
+    "open_cf_pred_infer": (ctypes.c_int, [_V, _I64, _V, _V, _V]),
 }
 
 MLP_PARAMS = 86560   # OPEN_CF_MLP_PARAMS
@@ -499,3 +507,90 @@ class NCF:
     def check(self):
         with torch.cuda.device(self.device):
             self._check(lib().open_cf_ncf_check(self._h))
+
+
+class Predictor:
+    """Offline performance predictor (open_cf_pred_*): n_features dense inputs
+    -> 128 -> 64 SELU units -> one output, trained on the mean squared error."""
+
+    def __init__(self, n_features: int = 7, batch: int = 1024, device: int = 0):
+        self._h = ctypes.c_void_p(0)
+        self.nf, self.batch = int(n_features), int(batch)
+        self.device = torch.device("cuda", device)
+        self.n_params = self.nf * NCF_H1 + (NCF_NET - 2 * NCF_D * NCF_H1)
+        h = ctypes.c_void_p(0)
+        rc = lib().open_cf_pred_create(self.nf, self.batch, device, ctypes.byref(h))
+        if rc != OK:
+            raise OpenCFError(rc, "open_cf_pred_create failed")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().open_cf_pred_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = lib().open_cf_pred_last_error(self._h)
+            raise OpenCFError(rc, msg.decode() if msg else "")
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _t(self, t, dtype, numel, name):
+        if t.dtype != dtype or t.device != self.device or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor on {self.device}")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"{name} must have {numel} elements")
+        return t
+
+    def set_params(self, params):
+        self._t(params, torch.float32, self.n_params, "params")
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_pred_set_params(self._h, _ptr(params), self._stream()))
+
+    def get_params(self):
+        p = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_pred_get_params(self._h, _ptr(p), self._stream()))
+        return p
+
+    def _xy(self, X, y):
+        N = y.numel()
+        self._t(X, torch.float32, N * self.nf, "X")
+        self._t(y, torch.float32, N, "y")
+        return N
+
+    def train(self, X, y, perms, lr: float, losses: bool = False):
+        N = self._xy(X, y)
+        epochs = perms.shape[0] if perms.dim() == 2 else 0
+        self._t(perms, torch.int32, epochs * N, "perms")
+        L = torch.empty(epochs * ((N + self.batch - 1) // self.batch), dtype=torch.float64,
+                        device=self.device) if losses else None
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_pred_train(self._h, N, _ptr(X), _ptr(y), epochs,
+                                                 _ptr(perms), float(lr), _ptr(L), self._stream()))
+        return L
+
+    def grad(self, X, y):
+        B = self._xy(X, y)
+        loss = torch.empty(1, dtype=torch.float64, device=self.device)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_pred_grad(self._h, B, _ptr(X), _ptr(y), _ptr(loss), _ptr(g),
+                                                self._stream()))
+        return loss, g
+
+    def infer(self, X):
+        N = X.numel() // self.nf
+        self._t(X, torch.float32, N * self.nf, "X")
+        y = torch.empty(N, dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_pred_infer(self._h, N, _ptr(X), _ptr(y), self._stream()))
+        return y

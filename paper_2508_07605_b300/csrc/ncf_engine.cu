@@ -53,6 +53,15 @@ struct open_cf_ncf {
     std::string msg;
 };
 
+struct open_cf_pred {
+    int device = 0, nfeat = 0, B = 0;
+    bool params_set = false;
+    NBuf theta, grad, m1, m2, bf, adam, ctl, loss1, part, lpart;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<StepGraph> graphs;
+    std::string msg;
+};
+
 namespace {
 
 struct Guard {
@@ -68,7 +77,7 @@ struct Guard {
     }
 };
 
-int nfail(open_cf_ncf_t *h, int code, const char *fmt, ...) {
+template <typename H> int nfail(H *h, int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -78,7 +87,7 @@ int nfail(open_cf_ncf_t *h, int code, const char *fmt, ...) {
     return code;
 }
 
-int ncuda(open_cf_ncf_t *h, cudaError_t e, const char *where) {
+template <typename H> int ncuda(H *h, cudaError_t e, const char *where) {
     cudaGetLastError();
     return nfail(h, e == cudaErrorMemoryAllocation ? OPEN_CF_OUT_OF_MEMORY : OPEN_CF_CUDA_ERROR,
                  "%s: %s", where, cudaGetErrorString(e));
@@ -393,6 +402,221 @@ int open_cf_ncf_check(open_cf_ncf_t *h) {
         NCK(h, cudaMemset(h->err.p, 0, 16));
         return nfail(h, OPEN_CF_TIMEOUT, "a completion kernel gave up on a tensor-core wait");
     }
+    return OPEN_CF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- predictor
+// The offline performance predictor (Sec. "Performance Prediction Model"):
+// the same network on n_features dense inputs (zero padded to 64), trained
+// and evaluated by the NCF training kernel in its dense-feature mode.
+namespace {
+
+int64_t pred_count(int nf) { return (int64_t)nf * NCF_H1 + (NCF_NET - NCF_OFF_B1); }
+
+cudaError_t pred_step(open_cf_pred_t *h, int64_t N, int64_t spe, const float *X, const float *y,
+                      const int32_t *perms, double *loss_hist, bool update, cudaStream_t st) {
+    float *th = F(h->theta), *g = F(h->grad);
+    NcfCtl *ctl = reinterpret_cast<NcfCtl *>(h->ctl.p);
+    NcfTrainArgs t{};
+    t.ctl = ctl;
+    t.adam = update ? reinterpret_cast<AdamState *>(h->adam.p) : nullptr;
+    t.nnz = N; t.spe = spe; t.m = 0; t.n = 0; t.B = h->B;
+    t.perms = perms; t.val = y;
+    t.feat = X; t.nfeat = h->nfeat;
+    t.W1b = h->bf.p; t.W2b = reinterpret_cast<const char *>(h->bf.p) + 2 * NCF_OFF_B1;
+    t.b1 = th + NCF_OFF_B1; t.b2 = th + NCF_OFF_B2; t.w3 = th + NCF_OFF_W3; t.b3 = th + NCF_OFF_B3;
+    t.part = F(h->part); t.part_stride = NET_PAD; t.lpart = F(h->lpart);
+    NcfAdamArgs u{};
+    u.ctl = ctl;
+    u.adam = reinterpret_cast<const AdamState *>(h->adam.p);
+    u.update = update;
+    u.parts = h->B / 64; u.part = F(h->part); u.part_stride = NET_PAD; u.lpart = F(h->lpart);
+    u.th = th; u.grad = g; u.m1 = F(h->m1); u.m2 = F(h->m2);
+    u.net_pad = NET_PAD; u.n_emb = 0;
+    u.bf = h->bf.p;
+    u.loss_hist = loss_hist; u.loss_last = (double *)h->loss1.p;
+    return launch_ncf_train_step(t, u, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int open_cf_pred_create(int32_t n_features, int32_t batch, int device, open_cf_pred_t **out) {
+    if (!out) return OPEN_CF_INVALID_ARG;
+    *out = nullptr;
+    if (n_features < 1 || n_features > 2 * NCF_D) return OPEN_CF_INVALID_ARG;
+    if (batch < 64 || batch > 65536 || batch % 64) return OPEN_CF_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return OPEN_CF_INVALID_ARG;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return OPEN_CF_CUDA_ERROR;
+    if (!(prop.major == 10 && prop.minor == 3)) return OPEN_CF_UNSUPPORTED;
+    open_cf_pred_t *h = new open_cf_pred();
+    h->device = device;
+    h->nfeat = n_features;
+    h->B = batch;
+    Guard gd(device);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](NBuf &b, size_t bytes) {
+        if (e == cudaSuccess) e = alloc(b, bytes);
+    };
+    A(h->theta, sizeof(float) * NET_PAD); A(h->grad, sizeof(float) * NET_PAD);
+    A(h->m1, sizeof(float) * NET_PAD); A(h->m2, sizeof(float) * NET_PAD);
+    A(h->bf, 2 * 2 * NCF_OFF_B1);
+    A(h->adam, 16); A(h->ctl, sizeof(NcfCtl)); A(h->loss1, sizeof(double));
+    A(h->part, sizeof(float) * (batch / 64) * NET_PAD); A(h->lpart, sizeof(float) * (batch / 64));
+    if (e == cudaSuccess) e = cudaMemset(h->ctl.p, 0, sizeof(NcfCtl));
+    if (e == cudaSuccess) e = prepare_ncf_train();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        open_cf_pred_destroy(h);
+        return e == cudaErrorMemoryAllocation ? OPEN_CF_OUT_OF_MEMORY : OPEN_CF_CUDA_ERROR;
+    }
+    *out = h;
+    return OPEN_CF_OK;
+}
+
+void open_cf_pred_destroy(open_cf_pred_t *h) {
+    if (!h) return;
+    {
+        Guard gd(h->device);
+        cudaDeviceSynchronize();
+        for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+        for (NBuf *b : {&h->theta, &h->grad, &h->m1, &h->m2, &h->bf, &h->adam, &h->ctl, &h->loss1,
+                        &h->part, &h->lpart})
+            release(*b);
+    }
+    delete h;
+}
+
+const char *open_cf_pred_last_error(const open_cf_pred_t *h) { return h ? h->msg.c_str() : ""; }
+
+int open_cf_pred_set_params(open_cf_pred_t *h, const float *params, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!params) return nfail(h, OPEN_CF_INVALID_ARG, "params is NULL");
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    float *th = F(h->theta);
+    const int64_t w1 = (int64_t)h->nfeat * NCF_H1;
+    NCK(h, cudaMemsetAsync(th, 0, sizeof(float) * NET_PAD, st));
+    NCK(h, cudaMemcpyAsync(th, params, sizeof(float) * w1, cudaMemcpyDeviceToDevice, st));
+    NCK(h, cudaMemcpyAsync(th + NCF_OFF_B1, params + w1, sizeof(float) * (NCF_NET - NCF_OFF_B1),
+                           cudaMemcpyDeviceToDevice, st));
+    NCK(h, cudaMemsetAsync(h->m1.p, 0, sizeof(float) * NET_PAD, st));
+    NCK(h, cudaMemsetAsync(h->m2.p, 0, sizeof(float) * NET_PAD, st));
+    NCK(h, cudaMemsetAsync(h->adam.p, 0, 16, st));
+    NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(NcfCtl), st));
+    NCK(h, launch_ncf_refresh_bf(th, h->bf.p, st));
+    h->params_set = true;
+    return OPEN_CF_OK;
+}
+
+int open_cf_pred_get_params(open_cf_pred_t *h, float *params, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
+    if (!params) return nfail(h, OPEN_CF_INVALID_ARG, "params is NULL");
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    const float *th = F(h->theta);
+    const int64_t w1 = (int64_t)h->nfeat * NCF_H1;
+    NCK(h, cudaMemcpyAsync(params, th, sizeof(float) * w1, cudaMemcpyDeviceToDevice, st));
+    NCK(h, cudaMemcpyAsync(params + w1, th + NCF_OFF_B1, sizeof(float) * (NCF_NET - NCF_OFF_B1),
+                           cudaMemcpyDeviceToDevice, st));
+    return OPEN_CF_OK;
+}
+
+int open_cf_pred_train(open_cf_pred_t *h, int64_t N, const float *X, const float *y,
+                       int32_t epochs, const int32_t *perms, float lr, double *loss_out,
+                       void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
+    if (N < 1 || N > INT32_MAX || epochs < 0 || !X || !y || (epochs > 0 && !perms))
+        return nfail(h, OPEN_CF_INVALID_ARG, "bad N, epochs or array");
+    if (!(lr >= 0.0f) || !std::isfinite(lr)) return nfail(h, OPEN_CF_INVALID_ARG, "bad lr");
+    if (epochs == 0) return OPEN_CF_OK;
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    const int64_t spe = (N + h->B - 1) / h->B, steps = spe * epochs;
+    NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(int64_t), st));
+    NCK(h, launch_adam_set_lr(h->adam.p, lr, st));
+    std::vector<int64_t> key{N, spe, (int64_t)X, (int64_t)y, (int64_t)perms, (int64_t)loss_out};
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : h->graphs)
+        if (g.key == key) exec = g.exec;
+    if (!exec) {
+        NCK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = pred_step(h, N, spe, X, y, perms, loss_out, true, h->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return ncuda(h, e, "training step capture");
+        }
+        if (e2 != cudaSuccess) return ncuda(h, e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return ncuda(h, e, "cudaGraphInstantiate");
+        if (h->graphs.size() >= 8) {
+            cudaGraphExecDestroy(h->graphs.front().exec);
+            h->graphs.erase(h->graphs.begin());
+        }
+        h->graphs.push_back(StepGraph{key, exec});
+    }
+    for (int64_t s = 0; s < steps; ++s) NCK(h, cudaGraphLaunch(exec, st));
+    return OPEN_CF_OK;
+}
+
+int open_cf_pred_grad(open_cf_pred_t *h, int64_t B, const float *X, const float *y,
+                      double *loss_out, float *g_params, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
+    if (B < 1 || B > h->B || !X || !y)
+        return nfail(h, OPEN_CF_INVALID_ARG, "B must be in [1, batch] and the arrays given");
+    Guard gd(h->device);
+    cudaStream_t st = SS(stream);
+    NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(int64_t), st));
+    NCK(h, pred_step(h, B, 1, X, y, nullptr, nullptr, false, st));
+    const float *g = F(h->grad);
+    const int64_t w1 = (int64_t)h->nfeat * NCF_H1;
+    if (loss_out)
+        NCK(h, cudaMemcpyAsync(loss_out, h->loss1.p, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (g_params) {
+        NCK(h, cudaMemcpyAsync(g_params, g, sizeof(float) * w1, cudaMemcpyDeviceToDevice, st));
+        NCK(h, cudaMemcpyAsync(g_params + w1, g + NCF_OFF_B1,
+                               sizeof(float) * (NCF_NET - NCF_OFF_B1), cudaMemcpyDeviceToDevice,
+                               st));
+    }
+    return OPEN_CF_OK;
+}
+
+int open_cf_pred_infer(open_cf_pred_t *h, int64_t N, const float *X, float *y_out, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
+    if (N < 0 || N > INT32_MAX - 64 || (N > 0 && (!X || !y_out)))
+        return nfail(h, OPEN_CF_INVALID_ARG, "bad N or array");
+    if (N == 0) return OPEN_CF_OK;
+    Guard gd(h->device);
+    float *th = F(h->theta);
+    NcfTrainArgs t{};
+    t.ctl = reinterpret_cast<NcfCtl *>(h->ctl.p);
+    t.nnz = N; t.spe = 1; t.B = (int)((N + 63) / 64 * 64);
+    t.feat = X; t.nfeat = h->nfeat; t.y_out = y_out; t.forward_only = true;
+    t.W1b = h->bf.p; t.W2b = reinterpret_cast<const char *>(h->bf.p) + 2 * NCF_OFF_B1;
+    t.b1 = th + NCF_OFF_B1; t.b2 = th + NCF_OFF_B2; t.w3 = th + NCF_OFF_W3; t.b3 = th + NCF_OFF_B3;
+    NCK(h, launch_ncf_forward(t, SS(stream)));
     return OPEN_CF_OK;
 }
 

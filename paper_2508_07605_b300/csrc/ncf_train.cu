@@ -134,11 +134,11 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     const int gid = lane >> 2, t4 = lane & 3;
 
     // batch position of this step
-    const int64_t s = a.ctl->step;
+    const int64_t s = a.forward_only ? 0 : a.ctl->step;
     const int64_t epoch = s / a.spe, off = (s % a.spe) * (int64_t)a.B;
     const int64_t left = a.nnz - off;
     const int beff = (int)(left < a.B ? left : a.B);
-    if (blockIdx.x == 0 && tid == 0) {
+    if (blockIdx.x == 0 && tid == 0 && !a.forward_only) {
         a.ctl->beff = beff;
         if (a.adam) a.adam->t += 1;   // the update kernel of this step reads it
     }
@@ -165,16 +165,26 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
         if (ok) {
             e = a.perms ? (int64_t)__ldg(a.perms + epoch * a.nnz + off + b) : off + b;
             ok = e >= 0 && e < a.nnz;
-            if (ok) {
+            if (ok && !a.feat) {
                 i = __ldg(a.app + e);
                 j = __ldg(a.set + e);
                 ok = i >= 0 && (int64_t)i < a.m && j >= 0 && (int64_t)j < a.n;
             }
+            if (ok && a.feat) i = 0;   // a live row (no embedding rows to update)
             if (!ok && q == 0)
                 atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->skipped), 1ull);
         }
         uint4 pk = make_uint4(0, 0, 0, 0);
-        if (ok) {
+        if (ok && a.feat) {   // dense features, zero padded to 64 columns
+            float x[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                x[t] = 8 * q + t < a.nfeat ? __ldg(a.feat + e * a.nfeat + 8 * q + t) : 0.f;
+            __nv_bfloat162 p0 = __floats2bfloat162_rn(x[0], x[1]), p1 = __floats2bfloat162_rn(x[2], x[3]);
+            __nv_bfloat162 p2 = __floats2bfloat162_rn(x[4], x[5]), p3 = __floats2bfloat162_rn(x[6], x[7]);
+            pk = make_uint4(*reinterpret_cast<uint32_t *>(&p0), *reinterpret_cast<uint32_t *>(&p1),
+                            *reinterpret_cast<uint32_t *>(&p2), *reinterpret_cast<uint32_t *>(&p3));
+        } else if (ok) {
             const float *src = q < 4 ? a.Ea + (int64_t)i * NCF_D + 8 * q
                                      : a.Es + (int64_t)j * NCF_D + 8 * (q - 4);
             const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src));
@@ -186,7 +196,7 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
         }
         *reinterpret_cast<uint4 *>(Xs + rr * SX + 8 * q) = pk;
         if (q == 0) {
-            Rs[rr] = ok ? __ldg(a.val + e) : 0.f;
+            Rs[rr] = (ok && a.val) ? __ldg(a.val + e) : 0.f;   // no targets when only predicting
             RI[rr] = ok ? i : -1;
             RJ[rr] = ok ? j : -1;
         }
@@ -241,6 +251,11 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(FULL, y, o);
             y += b3;
+            if (a.forward_only) {
+                const int64_t b = (int64_t)blockIdx.x * TB + r;
+                if (lane == 0 && b < beff) a.y_out[b] = RI[r] >= 0 ? y : __int_as_float(0x7fc00000);
+                continue;
+            }
             const float e = RI[r] >= 0 ? y - Rs[r] : 0.f;
             const float dy = scale * e;
             const float d0 = dy * w0 * dselu_t(__low2float(zz));
@@ -261,6 +276,7 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
             rw[2 * NCF_H2 + 1] = sse;
         }
     }
+    if (a.forward_only) return;   // uniform across the CTA
     __syncthreads();
     float *part = a.part + (int64_t)blockIdx.x * a.part_stride;
     for (int c = tid; c < HEADP; c += NTH) {
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
         part[NCF_OFF_B1 + tid] = v;
     }
     // ---- dx = dz1 W1^T (64 x 64, K = 128) into the embedding gradients
-    {
+    if (a.gE) {
         const int m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
         float acc[4][4];
         warp_mma<false, true, 4>(acc, D1s, S1, W1s, S1, m0, n0, NCF_H1, lane);
@@ -413,6 +429,12 @@ cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, c
     int64_t blocks = (u.net_pad + u.n_emb + 255) / 256;
     if (blocks > NUM_SMS_HINT * 8) blocks = NUM_SMS_HINT * 8;
     k_ncf_reduce_adam<<<(unsigned)blocks, 256, 0, st>>>(u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ncf_forward(const NcfTrainArgs &t, cudaStream_t st) {
+    if (t.B % TB || t.B <= 0 || !t.forward_only || !t.y_out) return cudaErrorInvalidValue;
+    k_ncf_train_tile<<<(unsigned)(t.B / TB), NTH, TRAIN_SMEM, st>>>(t);
     return cudaGetLastError();
 }
 
