@@ -1316,6 +1316,171 @@ def run_gpu_stream(args):
     return 0
 
 
+WORKLOAD_ONLINE = "online phase: predictor (7 inputs -> 128 -> 64 SELU -> 1) trained offline (20 " \
+                  "epochs, batch 1024, Adam 2e-3) on all " \
+                  "1024 settings (16x64 caps) of 1024 synthetic apps, V fitted (k=16) on their " \
+                  "dense matrix; per step 65,536 new apps, each profiled under 16 settings: " \
+                  "predictor on the 1,048,576 runs -> sparse rows -> ALS fold-in -> " \
+                  "reconstruction + Algorithm 2 (gamma=0.05) over all 1024 settings"
+
+
+def run_gpu_online(args):
+    """The whole online phase on the GPU: counters -> predictor -> fold-in -> selection."""
+    import torch
+
+    import paper_2508_07605_b300 as ocf
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n_cpu, n_gpu, k, lam = 16, 64, 16, 0.05
+    cpu, gpu = synth.cap_grid(n_cpu, n_gpu)
+    n = n_cpu * n_gpu
+    f32 = torch.float32
+    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
+    # ---- offline phase (not timed): predictor training and V
+    off = synth.make_counters(seed=0, n_apps=1024, n_cpu=n_cpu, n_gpu=n_gpu)
+    rng = np.random.default_rng(0)
+    pred = ocf.Predictor(7, batch=1024)
+    pred.set_params(to(synth.pred_init(rng, 7), f32))
+    Xo, yo = to(off.X, f32), to(off.y, f32)
+    epochs = 20
+    perms = to(np.stack(synth.ncf_perms(rng, len(off.y), epochs)), torch.int32)
+    t0 = time.perf_counter()
+    pred.train(Xo, yo, perms, 2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    h = ocf.OpenCF(k=k, lam=lam, sweeps=15, cpu_caps=cpu, gpu_caps=gpu)
+    h.set_V(to(synth.init_factor(rng, n, k), f32))
+    h.fit_offline(to(off.y.reshape(1024, n), f32))
+    # ---- the new applications' online profile (16 settings each)
+    m_new, runs = 65536, 16
+    new = synth.make_counters(seed=1, n_apps=m_new, n_cpu=n_cpu, n_gpu=n_gpu, runs=runs)
+    Xn = to(new.X, f32)
+    ptr = to(np.arange(0, m_new * runs + 1, runs, dtype=np.int64), torch.int64)
+    col = to(new.setting, torch.int32)
+
+    def step():
+        y = pred.infer(Xn)
+        U, _ = h.complete_rows(ptr, col, y)
+        _, best, sav = h.predict(U, gamma=GAMMA, want_T=False)
+        return y, U, best, sav
+
+    W = max(args.warmup, 3)
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_online.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                          else "/tmp/clocks_bench_online.csv")
+    with clocks:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            y, U, best, sav = step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    t_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps / 1e3
+    clk = clocks.summary(0)
+    # the predictor alone (the dominant kernel), back to back
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    e0.record(stream)
+    for _ in range(10):
+        pred.infer(Xn)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pred = e0.elapsed_time(e1) / 10 / 1e3
+    flops = 2.0 * (7 * 128 + 128 * 64 + 64) * m_new * runs   # the network's own products
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16_peak = float(peaks.get("bf16_tflops", 1800.0))
+
+    # ---- quality on the first 2048 new apps: completed rows and decisions against truth
+    import oracle as orc
+    orc.build()
+    ev_apps = 2048
+    rng_t = np.random.default_rng(1)
+    traits = synth.make_traits(rng_t, m_new)
+    full = synth.counter_runs(traits, np.repeat(np.arange(ev_apps), n), np.tile(np.arange(n),
+                              ev_apps), n_cpu, n_gpu)
+    Ttrue = full.y.reshape(ev_apps, n)
+    Ug = U[:ev_apps].double().cpu().numpy()
+    Vg = h.get_V().double().cpu().numpy()
+    That = Ug @ Vg.T
+    rmse = float(np.sqrt(np.mean((That - Ttrue) ** 2)))
+    bg = best[:ev_apps].cpu().numpy()
+    bt, st = orc.select_f64(Ttrue, cpu, gpu, GAMMA)
+    base = int(orc.baseline_index(cpu, gpu))
+    cg = cpu[np.arange(n) // n_gpu] + gpu[np.arange(n) % n_gpu]
+    Eb = cpu[-1] + gpu[-1]
+    ok = bg >= 0
+    true_loss = 1.0 - Ttrue[np.arange(ev_apps), base] / Ttrue[np.arange(ev_apps), np.maximum(bg, 0)]
+    true_save = (Eb - cg[np.maximum(bg, 0)] * Ttrue[np.arange(ev_apps), np.maximum(bg, 0)] /
+                 Ttrue[np.arange(ev_apps), base]) / Eb
+    yh = y.double().cpu().numpy()
+    pred_rmse = float(np.sqrt(np.mean((yh - new.y) ** 2)))
+
+    # ---- CPU baseline: the oracle's predictor, fold-in and selection on 256 apps
+    samp = 256
+    params = pred.get_params().double().cpu().numpy()
+    t0 = time.perf_counter()
+    yo_s = orc.pred_forward(new.X[:samp * runs], params, 7)
+    Uo, _ = orc.half_step(np.arange(0, samp * runs + 1, runs), new.setting[:samp * runs], yo_s,
+                          Vg, lam)
+    To = orc.predict(Uo, Vg)
+    orc.select_f64(To, cpu, gpu, GAMMA)
+    t_orc = (time.perf_counter() - t0) / samp
+
+    # ---- end to end: host counters in, decisions out
+    hX = torch.as_tensor(new.X.astype(np.float32)).pin_memory()
+    o_best = torch.empty(m_new, dtype=torch.int32).pin_memory()
+    dX = torch.empty_like(Xn)
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ee[i][0].record(stream)
+        dX.copy_(hX, non_blocking=True)
+        yy = pred.infer(dX)
+        UU, _ = h.complete_rows(ptr, col, yy)
+        _, bb, _ = h.predict(UU, gamma=GAMMA, want_T=False)
+        o_best.copy_(bb, non_blocking=True)
+        ee[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e = m_new * args.steps / (sum(a.elapsed_time(b) for a, b in ee) / 1e3)
+    line = {
+        "metric": "online apps/s (predictor + fold-in + Algorithm 2)", "value": m_new / t_step,
+        "unit": "apps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_ONLINE, "apps": m_new, "runs_per_app": runs, "n": n,
+                   "k": k, "parallelism": "replicas1",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "parts": {"predictor_ms": t_pred * 1e3, "offline_training_s": t_train},
+        "quality": {"predictor_rmse_on_profiled_runs": pred_rmse,
+                    "completed_rows_rmse_vs_truth": rmse,
+                    "chosen_within_true_loss_bound": float(np.mean(true_loss[ok] <= GAMMA + 1e-9)),
+                    "mean_true_saving_chosen": float(np.mean(true_save[ok])),
+                    "mean_true_saving_best_possible": float(np.mean(st[bt >= 0]))},
+        "roofline": {"kernel": "k_pred_forward (predictor)", "bound": "tensor",
+                     "achieved": flops / t_pred / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": flops / t_pred / 1e12 / bf16_peak, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
+        "cpu_baseline": {"value": 1.0 / t_orc, "unit": "apps/s", "cores": orc.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{samp} apps: predictor on their runs, fold-in, "
+                                   "reconstruction and Algorithm 2 (FP64)"},
+        "e2e": {"value": e2e, "unit": "apps/s", "h2d_bytes_per_step": int(4 * new.X.size),
+                "d2h_bytes_per_step": int(4 * m_new)},
+        "gpu_launches": 8 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1323,7 +1488,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c4", "c5", "phase", "ncf", "stream"],
+                    choices=["c1", "c2", "c3", "c4", "c5", "phase", "ncf", "stream", "online"],
                     help="c1: 64x120 FP64 joint fit; "
                          "c2: 4096x1024 fit (default, the headline line); "
                          "c3: 10,000 uneven problems in one batched launch; "
@@ -1331,7 +1496,8 @@ def main():
                          "c5: 1M x 4096 BF16-Gram fold-in + selection; "
                          "phase: Algorithm 1 over 2^17 power traces; "
                          "ncf: the paper's NCF model, one epoch + completion; "
-                         "stream: streaming refit, one batch of 8192 new apps per step")
+                         "stream: streaming refit, one batch of 8192 new apps per step; "
+                         "online: predictor -> fold-in -> Algorithm 2 for 65,536 new apps")
     ap.add_argument("--train-steps", type=int, default=30000,
                     help="c4 only: training steps (batch 4096) before the timed completions")
     ap.add_argument("--pool", type=int, default=1 << 20, help="c4 only: training apps")
@@ -1356,6 +1522,8 @@ def main():
         return run_gpu_ncf(args)
     if args.workload == "stream":
         return run_gpu_stream(args)
+    if args.workload == "online":
+        return run_gpu_online(args)
     return run_gpu(args)
 
 

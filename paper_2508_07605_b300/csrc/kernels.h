@@ -294,11 +294,10 @@ struct NcfTrainArgs {            // k_ncf_train_tile: forward + backward of one 
     int64_t s_off;
     // Dense-feature mode (the offline performance predictor): row e of the
     // input is feat[e][0 .. nfeat) padded with zeros to 64 (app, set, Ea, Es
-    // unused); forward_only writes y (NaN for a skipped entry) and stops.
+    // unused).  y_out: the predictions of launch_pred_forward.
     const float *feat = nullptr;
     int nfeat = 0;
     float *y_out = nullptr;
-    bool forward_only = false;
 };
 struct NcfAdamArgs {            // k_ncf_reduce_adam: partials -> gradient -> Adam
     NcfCtl *ctl;
@@ -325,8 +324,9 @@ struct NcfPredArgs {
 cudaError_t prepare_ncf_train();
 cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, cudaStream_t st);
 cudaError_t launch_ncf_refresh_bf(const float *theta, void *bf, cudaStream_t st);
-// Forward pass only (t.forward_only) over t.B rows (t.B a multiple of 64, any size).
-cudaError_t launch_ncf_forward(const NcfTrainArgs &t, cudaStream_t st);
+// Predictions of the dense-feature network for t.nnz rows of t.feat into t.y_out
+// (persistent: weights loaded once per CTA).
+cudaError_t launch_pred_forward(const NcfTrainArgs &t, int num_sms, cudaStream_t st);
 cudaError_t launch_ncf_first_layer(int64_t rows, const float *E, const float *W, const float *bias,
                                    float *out, cudaStream_t st);
 cudaError_t launch_ncf_w2_image(const float *W2, void *img, cudaStream_t st);

@@ -54,7 +54,7 @@ struct open_cf_ncf {
 };
 
 struct open_cf_pred {
-    int device = 0, nfeat = 0, B = 0;
+    int device = 0, nfeat = 0, B = 0, num_sms = 0;
     bool params_set = false;
     NBuf theta, grad, m1, m2, bf, adam, ctl, loss1, part, lpart;
     cudaStream_t cap_stream = nullptr;
@@ -473,6 +473,7 @@ int open_cf_pred_create(int32_t n_features, int32_t batch, int device, open_cf_p
     A(h->part, sizeof(float) * (batch / 64) * NET_PAD); A(h->lpart, sizeof(float) * (batch / 64));
     if (e == cudaSuccess) e = cudaMemset(h->ctl.p, 0, sizeof(NcfCtl));
     if (e == cudaSuccess) e = prepare_ncf_train();
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -605,18 +606,17 @@ int open_cf_pred_infer(open_cf_pred_t *h, int64_t N, const float *X, float *y_ou
     if (!h) return OPEN_CF_INVALID_ARG;
     h->msg.clear();
     if (!h->params_set) return nfail(h, OPEN_CF_NOT_FITTED, "set the parameters first");
-    if (N < 0 || N > INT32_MAX - 64 || (N > 0 && (!X || !y_out)))
+    if (N < 0 || (N > 0 && (!X || !y_out)))
         return nfail(h, OPEN_CF_INVALID_ARG, "bad N or array");
     if (N == 0) return OPEN_CF_OK;
     Guard gd(h->device);
     float *th = F(h->theta);
     NcfTrainArgs t{};
-    t.ctl = reinterpret_cast<NcfCtl *>(h->ctl.p);
-    t.nnz = N; t.spe = 1; t.B = (int)((N + 63) / 64 * 64);
-    t.feat = X; t.nfeat = h->nfeat; t.y_out = y_out; t.forward_only = true;
+    t.nnz = N;
+    t.feat = X; t.nfeat = h->nfeat; t.y_out = y_out;
     t.W1b = h->bf.p; t.W2b = reinterpret_cast<const char *>(h->bf.p) + 2 * NCF_OFF_B1;
     t.b1 = th + NCF_OFF_B1; t.b2 = th + NCF_OFF_B2; t.w3 = th + NCF_OFF_W3; t.b3 = th + NCF_OFF_B3;
-    NCK(h, launch_ncf_forward(t, SS(stream)));
+    NCK(h, launch_pred_forward(t, h->num_sms, SS(stream)));
     return OPEN_CF_OK;
 }
 

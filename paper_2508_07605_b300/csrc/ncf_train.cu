@@ -134,11 +134,11 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     const int gid = lane >> 2, t4 = lane & 3;
 
     // batch position of this step
-    const int64_t s = a.forward_only ? 0 : a.ctl->step;
+    const int64_t s = a.ctl->step;
     const int64_t epoch = s / a.spe, off = (s % a.spe) * (int64_t)a.B;
     const int64_t left = a.nnz - off;
     const int beff = (int)(left < a.B ? left : a.B);
-    if (blockIdx.x == 0 && tid == 0 && !a.forward_only) {
+    if (blockIdx.x == 0 && tid == 0) {
         a.ctl->beff = beff;
         if (a.adam) a.adam->t += 1;   // the update kernel of this step reads it
     }
@@ -251,11 +251,6 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(FULL, y, o);
             y += b3;
-            if (a.forward_only) {
-                const int64_t b = (int64_t)blockIdx.x * TB + r;
-                if (lane == 0 && b < beff) a.y_out[b] = RI[r] >= 0 ? y : __int_as_float(0x7fc00000);
-                continue;
-            }
             const float e = RI[r] >= 0 ? y - Rs[r] : 0.f;
             const float dy = scale * e;
             const float d0 = dy * w0 * dselu_t(__low2float(zz));
@@ -276,7 +271,6 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
             rw[2 * NCF_H2 + 1] = sse;
         }
     }
-    if (a.forward_only) return;   // uniform across the CTA
     __syncthreads();
     float *part = a.part + (int64_t)blockIdx.x * a.part_stride;
     for (int c = tid; c < HEADP; c += NTH) {
@@ -414,11 +408,102 @@ __global__ void k_ncf_refresh_bf(const float *__restrict__ th, bf16 *__restrict_
         bf[e] = __float2bfloat16_rn(e < NCF_OFF_B1 ? th[e] : th[NCF_OFF_W2 + e - NCF_OFF_B1]);
 }
 
+// Prediction with the dense-feature network (the offline performance
+// predictor): a persistent kernel that loads W1 (only the K1 = nfeat rounded
+// up to 16 rows that meet non-zero inputs) and W2 once per CTA and walks
+// 64-row tiles: gather -> z1 (K = K1) -> SELU -> z2 -> SELU -> y, the output
+// dot product folded into the second layer's epilogue.
+constexpr uint32_t P_OFF_W1 = 0;                                  // W1 [64][S1] (K1 rows used)
+constexpr uint32_t P_OFF_W2 = P_OFF_W1 + 2 * NCF_D * S1 * 2;      // W2 [128][S2]
+constexpr uint32_t P_OFF_X = P_OFF_W2 + NCF_H1 * S2 * 2;          // x  [64][SX]
+constexpr uint32_t P_OFF_H1 = P_OFF_X + TB * SX * 2;              // h1 [64][S1]
+constexpr uint32_t P_OFF_Y = P_OFF_H1 + TB * S1 * 2;              // [2][64] partial y
+constexpr uint32_t PRED_SMEM = P_OFF_Y + 2 * TB * 4;
+
+__global__ void __launch_bounds__(NTH) k_pred_forward(NcfTrainArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    bf16 *W1s = reinterpret_cast<bf16 *>(sm + P_OFF_W1), *W2s = reinterpret_cast<bf16 *>(sm + P_OFF_W2);
+    bf16 *Xs = reinterpret_cast<bf16 *>(sm + P_OFF_X), *H1s = reinterpret_cast<bf16 *>(sm + P_OFF_H1);
+    float *yp = reinterpret_cast<float *>(sm + P_OFF_Y);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gid = lane >> 2, t4 = lane & 3;
+    const int K1 = (a.nfeat + 15) / 16 * 16;
+    const bf16 *W1g = reinterpret_cast<const bf16 *>(a.W1b);
+    const bf16 *W2g = reinterpret_cast<const bf16 *>(a.W2b);
+    for (int v = tid; v < K1 * (NCF_H1 / 8); v += NTH) {
+        const int r = v / (NCF_H1 / 8), c8 = (v % (NCF_H1 / 8)) * 8;
+        *reinterpret_cast<uint4 *>(W1s + r * S1 + c8) =
+            __ldg(reinterpret_cast<const uint4 *>(W1g + r * NCF_H1 + c8));
+    }
+    for (int v = tid; v < NCF_H1 * (NCF_H2 / 8); v += NTH) {
+        const int r = v / (NCF_H2 / 8), c8 = (v % (NCF_H2 / 8)) * 8;
+        *reinterpret_cast<uint4 *>(W2s + r * S2 + c8) =
+            __ldg(reinterpret_cast<const uint4 *>(W2g + r * NCF_H2 + c8));
+    }
+    const float b3 = a.b3[0];
+    const int64_t tiles = (a.nnz + TB - 1) / TB;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t r0 = tile * TB;
+        // x tile: K1 columns (features, then zeros)
+        for (int v = tid; v < TB * (K1 / 8); v += NTH) {
+            const int rr = v / (K1 / 8), q = v % (K1 / 8);
+            const int64_t e = r0 + rr;
+            float x[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                x[t] = (e < a.nnz && 8 * q + t < a.nfeat) ? __ldg(a.feat + e * a.nfeat + 8 * q + t)
+                                                          : 0.f;
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) st_pair(Xs + rr * SX + 8 * q + t, x[t], x[t + 1]);
+        }
+        __syncthreads();
+        {   // h1 = SELU(x W1 + b1)
+            const int m0 = 16 * (warp & 3), n0 = 64 * (warp >> 2);
+            float acc[8][4];
+            warp_mma<false, false, 8>(acc, Xs, SX, W1s, S1, m0, n0, K1, lane);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
+                    st_pair(H1s + r * S1 + c, selu_t(acc[j][2 * h] + a.b1[c]),
+                            selu_t(acc[j][2 * h + 1] + a.b1[c + 1]));
+                }
+        }
+        __syncthreads();
+        {   // z2 = h1 W2 + b2; this warp's share of y = SELU(z2) . w3
+            const int m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
+            float acc[4][4];
+            warp_mma<false, false, 4>(acc, H1s, S1, W2s, S2, m0, n0, NCF_H1, lane);
+            float p[2] = {0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = n0 + 8 * j + 2 * t4 + (e & 1);
+                    p[e >> 1] = fmaf(a.w3[c], selu_t(acc[j][e] + a.b2[c]), p[e >> 1]);
+                }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {   // the four lanes of a row hold its columns
+                p[h] += __shfl_xor_sync(FULL, p[h], 1);
+                p[h] += __shfl_xor_sync(FULL, p[h], 2);
+                if (t4 == 0) yp[(warp >> 2) * TB + m0 + gid + 8 * h] = p[h];
+            }
+        }
+        __syncthreads();
+        if (tid < TB && r0 + tid < a.nnz) a.y_out[r0 + tid] = (yp[tid] + yp[TB + tid]) + b3;
+    }
+}
+
 }  // namespace
 
 cudaError_t prepare_ncf_train() {
-    return cudaFuncSetAttribute(k_ncf_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TRAIN_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_ncf_train_tile,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TRAIN_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_pred_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PRED_SMEM);
 }
 
 cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, cudaStream_t st) {
@@ -432,9 +517,11 @@ cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_ncf_forward(const NcfTrainArgs &t, cudaStream_t st) {
-    if (t.B % TB || t.B <= 0 || !t.forward_only || !t.y_out) return cudaErrorInvalidValue;
-    k_ncf_train_tile<<<(unsigned)(t.B / TB), NTH, TRAIN_SMEM, st>>>(t);
+cudaError_t launch_pred_forward(const NcfTrainArgs &t, int num_sms, cudaStream_t st) {
+    if (!t.feat || !t.y_out || t.nfeat < 1 || t.nfeat > 2 * NCF_D) return cudaErrorInvalidValue;
+    if (t.nnz <= 0) return cudaSuccess;
+    const int64_t tiles = (t.nnz + TB - 1) / TB, cap = 4 * (int64_t)num_sms;
+    k_pred_forward<<<(unsigned)(tiles < cap ? tiles : cap), NTH, PRED_SMEM, st>>>(t);
     return cudaGetLastError();
 }
 

@@ -568,52 +568,73 @@ def make_stream(seed: int = 0, n_batches: int = 16, batch: int = 8192, obs: int 
 # has a CPU share of its baseline runtime and how memory-bound its CPU and GPU
 # parts are; a run under caps (c, g) yields the paper's seven inputs (CPU cap,
 # GPU cap, memory throughput, IPS, SM clock, DRAM active, FP active) and the
-# normalised performance (baseline runtime / runtime, 1 at the largest caps).
+# normalised performance in the matrix's unit: runtime / baseline runtime
+# (1 at the largest caps, larger under tighter caps).
 @dataclasses.dataclass
 class CounterRuns:
     X: np.ndarray      # [N, 7] inputs, each scaled to about [0, 1]
-    y: np.ndarray      # [N] normalised performance
+    y: np.ndarray      # [N] normalised runtime (runtime / runtime at the largest caps)
     app: np.ndarray    # [N] application index
     setting: np.ndarray  # [N] setting index (CPU-major)
 
 
+@dataclasses.dataclass
+class AppTraits:
+    cpu_share: np.ndarray
+    mem_c: np.ndarray
+    mem_g: np.ndarray
+    flop: np.ndarray
+    ips0: np.ndarray
+
+
+def counter_runs(traits: AppTraits, app: np.ndarray, setting: np.ndarray, n_cpu: int,
+                 n_gpu: int, rng: Optional[np.random.Generator] = None,
+                 noise: float = 0.02) -> CounterRuns:
+    """Runs (app[r], setting[r]) of the synthetic applications: the seven inputs
+    (with multiplicative noise when rng is given) and the normalised runtime."""
+    cpu, gpu = cap_grid(n_cpu, n_gpu)
+    c = cpu[setting // n_gpu] / cpu[-1]
+    g = gpu[setting % n_gpu] / gpu[-1]
+    a = app
+    s_cpu = c ** (0.3 + 0.5 * (1.0 - traits.mem_c[a]))           # CPU speed under its cap
+    clk = np.minimum(1.0, 1.1 * g ** 0.6)                         # SM clock / max clock
+    s_gpu = traits.mem_g[a] * (1.0 - 0.2 * (1.0 - g)) + (1.0 - traits.mem_g[a]) * clk
+    y = traits.cpu_share[a] / s_cpu + (1.0 - traits.cpu_share[a]) / s_gpu
+    mult = (lambda: np.exp(rng.normal(0.0, noise, len(a)))) if rng is not None else (lambda: 1.0)
+    X = np.stack([
+        (cpu[setting // n_gpu] - cpu[0]) / (cpu[-1] - cpu[0]),
+        (gpu[setting % n_gpu] - gpu[0]) / (gpu[-1] - gpu[0]),
+        traits.mem_c[a] * s_cpu ** 0.5 * mult(),                   # memory throughput
+        traits.ips0[a] * s_cpu * (1.0 - 0.5 * traits.mem_c[a]) * mult(),   # IPS
+        clk * mult(),                                              # SM clock
+        traits.mem_g[a] * (1.0 - 0.2 * (1.0 - g)) / (s_gpu + 1e-9) * 0.8 * mult(),   # DRAM active
+        traits.flop[a] * clk * (1.0 - 0.5 * traits.mem_g[a]) * mult(),   # FP active
+    ], axis=1)
+    return CounterRuns(X.astype(np.float64), y.astype(np.float64), app.astype(np.int32),
+                       setting.astype(np.int32))
+
+
+def make_traits(rng: np.random.Generator, n_apps: int) -> AppTraits:
+    return AppTraits(rng.uniform(0.05, 0.6, n_apps), rng.uniform(0.0, 1.0, n_apps),
+                     rng.uniform(0.0, 1.0, n_apps), rng.uniform(0.2, 1.0, n_apps),
+                     rng.uniform(0.5, 1.0, n_apps))
+
+
 def make_counters(seed: int = 0, n_apps: int = 512, n_cpu: int = 16, n_gpu: int = 64,
                   runs: Optional[int] = None, noise: float = 0.02) -> CounterRuns:
-    """All settings of every application (runs None) or `runs` random settings each."""
+    """All settings of every application (runs None) or `runs` random settings
+    each (in increasing setting order per application)."""
     rng = np.random.default_rng(seed)
-    cpu, gpu = cap_grid(n_cpu, n_gpu)
     n = n_cpu * n_gpu
-    cpu_share = rng.uniform(0.05, 0.6, n_apps)
-    mem_c = rng.uniform(0.0, 1.0, n_apps)
-    mem_g = rng.uniform(0.0, 1.0, n_apps)
-    flop = rng.uniform(0.2, 1.0, n_apps)
-    ips0 = rng.uniform(0.5, 1.0, n_apps)
+    traits = make_traits(rng, n_apps)
     if runs is None:
         app = np.repeat(np.arange(n_apps), n)
         setting = np.tile(np.arange(n), n_apps)
     else:
         app = np.repeat(np.arange(n_apps), runs)
-        setting = np.concatenate([rng.choice(n, runs, replace=False) for _ in range(n_apps)])
-    c = cpu[setting // n_gpu] / cpu[-1]
-    g = gpu[setting % n_gpu] / gpu[-1]
-    a = app
-    s_cpu = c ** (0.3 + 0.5 * (1.0 - mem_c[a]))                  # CPU speed under its cap
-    clk = np.minimum(1.0, 1.1 * g ** 0.6)                         # SM clock / max clock
-    s_gpu = mem_g[a] * (1.0 - 0.2 * (1.0 - g)) + (1.0 - mem_g[a]) * clk
-    t = cpu_share[a] / s_cpu + (1.0 - cpu_share[a]) / s_gpu       # runtime / baseline runtime
-    y = 1.0 / t
-    mult = lambda: np.exp(rng.normal(0.0, noise, len(a)))
-    X = np.stack([
-        (cpu[setting // n_gpu] - cpu[0]) / (cpu[-1] - cpu[0]),
-        (gpu[setting % n_gpu] - gpu[0]) / (gpu[-1] - gpu[0]),
-        mem_c[a] * s_cpu ** 0.5 * mult(),                          # memory throughput
-        ips0[a] * s_cpu * (1.0 - 0.5 * mem_c[a]) * mult(),         # IPS
-        clk * mult(),                                              # SM clock
-        mem_g[a] * (1.0 - 0.2 * (1.0 - g)) / (s_gpu + 1e-9) * 0.8 * mult(),   # DRAM active
-        flop[a] * clk * (1.0 - 0.5 * mem_g[a]) * mult(),           # FP active
-    ], axis=1)
-    return CounterRuns(X.astype(np.float64), y.astype(np.float64), app.astype(np.int32),
-                       setting.astype(np.int32))
+        keys = rng.random((n_apps, n))
+        setting = np.sort(np.argpartition(keys, runs - 1, axis=1)[:, :runs], axis=1).ravel()
+    return counter_runs(traits, app, setting, n_cpu, n_gpu, rng, noise)
 
 
 def pred_init(rng: np.random.Generator, n_features: int = 7, out_scale: float = 0.1):
