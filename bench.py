@@ -1141,7 +1141,9 @@ def run_gpu_ncf(args):
                                  best.cpu().numpy(), b32))},
         "roofline": {"kernel": "k_ncf_predict_tc (completion call: first layer + pairs)",
                      "bound": "alu", "achieved": gexp, "peak": mufu, "unit": "Gexp/s",
-                     "frac": gexp / mufu, "traffic": profiled_ncf_traffic(m * n),
+                     "frac": gexp / mufu, "traffic": profiled_traffic_per_unit(
+                         os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "ncf.cu"),
+                         os.path.join(ROOT, "profiles", "ncf_predict_tc.md"), m * n),
                      "peak_source": "148 SMs x 16 ex2 per clock x median SM clock (derived: "
                                     "one FP32-rate exponential per SELU)",
                      "note": f"{EXP_PER_PAIR} SELU exponentials per entry, evaluated as packed "
@@ -1164,23 +1166,22 @@ def run_gpu_ncf(args):
 NCF_MMA_MACS = 128 * 64   # h1 W2 per completed entry
 
 
-def profiled_ncf_traffic(entries):
-    """DRAM bytes of one completion launch at `entries` entries, scaled from the
-    committed ncu summary's smaller capture (traffic grows with the entries
-    written), or None when the kernel changed since."""
+def profiled_traffic_per_unit(kernel_src, profile_md, units):
+    """DRAM bytes of one launch at `units` units of work, from the committed ncu
+    summary (its capture covers the same launch configuration), or None when
+    the kernel source changed since the counters were taken."""
     import hashlib
     import re
     try:
-        src = os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "ncf.cu")
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        text = open(os.path.join(ROOT, "profiles", "ncf_predict_tc.md")).read()
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        text = open(profile_md).read()
     except OSError:
         return None
     m = re.search(r"sha256 \(first 16 hex\): ([0-9a-f]{16})", text)
-    b = re.search(r"\| dram_bytes_per_launch \| (\d+) \| (\d+) entries \|", text)
+    b = re.search(r"\| dram_bytes_per_launch \| (\d+) \| (\d+) \w+ \|", text)
     if not m or not b or m.group(1) != h:
         return None
-    return int(b.group(1)) * entries / int(b.group(2))
+    return int(b.group(1)) * units / int(b.group(2))
 
 
 WORKLOAD_STREAM = "streaming refit: workload 2's matrix as the offline block (fit, 15 sweeps), " \
@@ -1466,7 +1467,10 @@ def run_gpu_online(args):
                     "mean_true_saving_best_possible": float(np.mean(st[bt >= 0]))},
         "roofline": {"kernel": "k_pred_forward (predictor)", "bound": "tensor",
                      "achieved": flops / t_pred / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
-                     "frac": flops / t_pred / 1e12 / bf16_peak, "traffic": None,
+                     "frac": flops / t_pred / 1e12 / bf16_peak,
+                     "traffic": profiled_traffic_per_unit(
+                         os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "ncf_train.cu"),
+                         os.path.join(ROOT, "profiles", "pred_forward_online.md"), m_new * runs),
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
         "cpu_baseline": {"value": 1.0 / t_orc, "unit": "apps/s", "cores": orc.num_threads(),
                          "kind": "oracle",
