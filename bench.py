@@ -115,6 +115,13 @@ class ClockSampler:
         return out
 
 
+def clocks_path(name):
+    """Where the nvidia-smi samples of the timed region go: $OPEN_CF_CLOCKS_DIR
+    (kept for inspection) or the temporary directory."""
+    import tempfile
+    return os.path.join(os.environ.get("OPEN_CF_CLOCKS_DIR", tempfile.gettempdir()), name)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -222,9 +229,7 @@ def run_gpu(args):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_bench_r{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else f"/tmp/clocks_bench_r{rank}.csv")
+    clocks = ClockSampler(clocks_path(f"clocks_bench_r{rank}.csv"))
     with clocks:
         torch.cuda.synchronize()
         for i in range(args.steps):
@@ -410,9 +415,7 @@ def run_gpu_large(args):
     if ws > 1:
         dist.barrier()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_bench_c5_r{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else f"/tmp/clocks_bench_c5_r{rank}.csv")
+    clocks = ClockSampler(clocks_path(f"clocks_bench_c5_r{rank}.csv"))
     with clocks:
         torch.cuda.synchronize()
         for i in range(args.steps):
@@ -674,9 +677,7 @@ def run_gpu_batched(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_c3.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else "/tmp/clocks_bench_c3.csv")
+    clocks = ClockSampler(clocks_path("clocks_bench_c3.csv"))
     with clocks:
         for i in range(args.steps):
             V.copy_(V0)
@@ -891,9 +892,7 @@ def run_gpu_learned(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev) / reps / 1e3, out
 
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_c4.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else "/tmp/clocks_bench_c4.csv")
+    clocks = ClockSampler(clocks_path("clocks_bench_c4.csv"))
     with clocks:
         t_learned, (U, st) = timed(learned, args.steps)
         t_mlp, (Um, _) = timed(mlp_only, args.steps)
@@ -1030,9 +1029,7 @@ def run_gpu_ncf(args):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_ncf.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else "/tmp/clocks_bench_ncf.csv")
+    clocks = ClockSampler(clocks_path("clocks_bench_ncf.csv"))
     with clocks:
         torch.cuda.synchronize()
         for i in range(args.steps):
@@ -1227,9 +1224,7 @@ def run_gpu_stream(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_stream.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else "/tmp/clocks_bench_stream.csv")
+    clocks = ClockSampler(clocks_path("clocks_bench_stream.csv"))
     U_new = []
     with clocks:
         for i in range(steps):
@@ -1373,9 +1368,7 @@ def run_gpu_online(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench_online.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                          else "/tmp/clocks_bench_online.csv")
+    clocks = ClockSampler(clocks_path("clocks_bench_online.csv"))
     with clocks:
         for i in range(args.steps):
             flush.zero_()
