@@ -59,8 +59,21 @@ def profiled_traffic(kernel_src, profile_md):
 
 
 def fp32_alu_peak_tflops(sm_mhz):
-    # 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock
+    # 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock (the nominal figure)
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+_ALU_PEAK = {}
+ALU_PEAK_SOURCE = "FMA-loop microbenchmark (open_cf_fma_peak) measured on this GPU"
+
+
+def alu_peak_tflops(fp64=False, device=0):
+    """Measured FMA throughput (TFLOP/s) of the device, once per process."""
+    key = (bool(fp64), device)
+    if key not in _ALU_PEAK:
+        import paper_2508_07605_b300 as ocf
+        _ALU_PEAK[key] = ocf.fma_peak(fp64, device)
+    return _ALU_PEAK[key]
 
 
 class ClockSampler:
@@ -281,7 +294,7 @@ def run_gpu(args):
     fl = algorithmic_flops_half(nnz, m, k) + algorithmic_flops_half(nnz, n, k)
     achieved = fl / (t_u + t_v) / 1e12
     clk = clocks.summary(local)
-    peak = fp32_alu_peak_tflops(2032.0)
+    peak = alu_peak_tflops(False, local)
 
     # ---- end to end through the C ABI with host buffers
     pin = lambda a: torch.as_tensor(a).pin_memory()
@@ -353,7 +366,7 @@ def run_gpu(args):
                          os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "row_solve_tc.cu"),
                          os.path.join(ROOT, "profiles", "rowsolve_tc_c2.md")),
                      "traffic_unit": "DRAM bytes per launch (mean of U- and V-half, ncu)",
-                     "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (derived)",
+                     "peak_source": ALU_PEAK_SOURCE,
                      "launch_us": {"u_half": t_u * 1e6, "v_half": t_v * 1e6}},
         "cpu_baseline": {"value": units / t_orc, "unit": "row-solves/s",
                          "cores": orc.num_threads(), "kind": "oracle",
@@ -473,8 +486,9 @@ def run_gpu_large(args):
         "roofline": {"kernel": "k_row_solve_tc<32,%s,1,bf16> (fold-in)" %
                                ("double" if chol64 else "float"),
                      "bound": "tensor+alu", "achieved": fl / t_fold / 1e12,
-                     "peak": fp32_alu_peak_tflops(2032.0), "unit": "TFLOP/s",
-                     "frac": fl / t_fold / 1e12 / fp32_alu_peak_tflops(2032.0),
+                     "peak": alu_peak_tflops(False, local), "unit": "TFLOP/s",
+                     "frac": fl / t_fold / 1e12 / alu_peak_tflops(False, local),
+                     "peak_source": ALU_PEAK_SOURCE,
                      "hbm_bytes_algorithmic": int((e1 - e0) * 8 + (r1 - r0 + 1) * 8 + (r1 - r0) * k * 4),
                      "hbm_gbs_achieved": ((e1 - e0) * 8 + (r1 - r0 + 1) * 8 + (r1 - r0) * k * 4) / t_fold / 1e9},
         "predict_roofline": {"kernel": "k_predict_select_tc (split-BF16 U V^T on tcgen05 + "
@@ -746,7 +760,7 @@ def run_gpu_batched(args):
         gaps.append(rmse(Ug, Vg) - rmse(fit[0], fit[1]))
     fl = sum(15 * (algorithmic_flops_half(q.nnz, q.m, q.k) + algorithmic_flops_half(q.nnz, q.n, q.k))
              for q in bp.problems)
-    peak = fp32_alu_peak_tflops(2032.0)
+    peak = alu_peak_tflops(False, 0)
     orc_units = 15 * sum(bp.problems[i].m + bp.problems[i].n for i in osamp)
     line = {
         "metric": "ALS row-solves/s", "value": units / t_step, "unit": "row-solves/s",
@@ -768,7 +782,7 @@ def run_gpu_batched(args):
         "roofline": {"kernel": "k_batched_als (all sweeps of all problems)", "bound": "alu",
                      "achieved": fl / t_step / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": fl / t_step / 1e12 / peak, "traffic": None,
-                     "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (derived)"},
+                     "peak_source": ALU_PEAK_SOURCE},
         "cpu_baseline": {"value": orc_units / t_orc, "unit": "row-solves/s",
                          "cores": orc.num_threads(), "kind": "oracle",
                          "sample": f"FP64 ALS fits of {len(osamp)} sampled problems"},
@@ -1284,7 +1298,7 @@ def run_gpu_stream(args):
     fl = algorithmic_flops_half(nnz_b, w.batch, k) + algorithmic_flops_half(nnz_b, n, k) + \
         n * k * k   # + adding the stored sums
     achieved = fl / t_step / 1e12
-    peak = fp32_alu_peak_tflops(clk["sm_mhz"] or 2032.0)
+    peak = alu_peak_tflops(False, 0)
     line = {
         "metric": "streamed apps/s (fold-in + incremental refit of V)",
         "value": w.batch / t_step, "unit": "apps/s", "n_gpus": 1, "steps": steps,
@@ -1298,7 +1312,7 @@ def run_gpu_stream(args):
         "roofline": {"kernel": "stream ingest (fold-in + V-half with stored sums)",
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "peak_source": "148 SMs x 128 FP32 lanes x 2 x median SM clock (derived)"},
+                     "peak_source": ALU_PEAK_SOURCE},
         "cpu_baseline": {"value": w.batch / t_orc, "unit": "apps/s",
                          "cores": orc.num_threads(), "kind": "oracle",
                          "sample": f"the same {steps} batches in FP64"},

@@ -302,6 +302,14 @@ int open_cf_stream_ingest(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
                           const int32_t *col, const void *val, void *U_out, int32_t *status,
                           void *stream);
 
+/* FMA-loop microbenchmark (a measurement service, no counterpart in the
+ * paper): the FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add
+ * throughput of `device` in TFLOP/s (2 FLOP per FMA), measured with CUDA
+ * events over one launch of independent FMA chains on every SM; the
+ * denominator of the ALU rooflines.  Synchronous; runs on the legacy default
+ * stream of `device`. */
+int open_cf_fma_peak(int32_t fp64, int32_t device, double *tflops_host);
+
 /* Allocation-free CSR -> CSC (no counterpart in the paper; a service of this
  * library).  Some callers cannot allocate device memory: their host framework
  * owns every device allocation through its own pool and forbids direct

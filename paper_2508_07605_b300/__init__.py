@@ -69,6 +69,7 @@ _SIGNATURES = {
     "open_cf_mlp_train_step": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _F, _V, _V, _V]),
     "open_cf_mlp_infer": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
     "open_cf_phase_detect": (ctypes.c_int, [_V, _I64, _I64, _I64, _F, _I32, _V, _V]),
+    "open_cf_fma_peak": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_D)]),
     "open_cf_stream_begin": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V]),
     "open_cf_stream_ingest": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V]),
     "open_cf_ncf_create": (ctypes.c_int, [_I64, _I32, _V, _I32, _V, _I32, ctypes.c_int,
@@ -137,6 +138,15 @@ def phase_detect(power, p_th: float = 60.0, window: int = 25):
     if rc != OK:
         raise OpenCFError(rc, "open_cf_phase_detect failed")
     return out
+
+
+def fma_peak(fp64: bool = False, device: int = 0) -> float:
+    """Measured FP32 (or FP64) FMA throughput of the device, TFLOP/s."""
+    out = _D(0.0)
+    rc = lib().open_cf_fma_peak(int(fp64), int(device), ctypes.byref(out))
+    if rc != OK:
+        raise OpenCFError(rc, "open_cf_fma_peak failed")
+    return float(out.value)
 
 
 def _ptr(t):
