@@ -243,3 +243,29 @@ def test_ncf_argument_errors():
         h.grad(big, big, torch.zeros(65, device=DEV))   # more than one batch
     assert e.value.code == ocf.INVALID_ARG
     h.close()
+
+
+def test_ncf_single_partial_batch_and_no_epochs(orc):
+    # nnz < batch: one shorter batch per epoch; epochs = 0 leaves the parameters
+    m, ncpu, ngpu = 30, 2, 16
+    n = ncpu * ngpu
+    params = _params(21, m, n)
+    rng = np.random.default_rng(22)
+    nnz = 100
+    ai = rng.integers(0, m, nnz).astype(np.int32)
+    sj = rng.integers(0, n, nnz).astype(np.int32)
+    r = _f32(rng.random(nnz))
+    h, _, _ = _handle(m, ncpu, ngpu, 256, params)
+    args = (dev(ai, torch.int32), dev(sj, torch.int32), dev(r, torch.float32))
+    h.train(*args, torch.zeros((0, nnz), dtype=torch.int32, device=DEV), 1e-3)
+    net0, _, _ = h.get_params()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(net0), params[0].astype(np.float32))
+    perms = synth.ncf_perms(rng, nnz, 2)
+    L = h.train(*args, dev(np.stack(perms), torch.int32), 1e-3, losses=True)
+    torch.cuda.synchronize()
+    _, _, _, L_o = orc.ncf_train(ai, sj, r, params[1], params[2], params[0], H1, H2, perms, 256,
+                                 1e-3)
+    assert len(host(L)) == 2 == len(L_o)
+    assert abs(host(L)[0] - L_o[0]) <= 1e-2 * L_o[0]
+    h.close()

@@ -120,3 +120,12 @@ def test_pred_argument_errors():
         h.infer(x)                                # parameters not set
     assert e.value.code == ocf.NOT_FITTED
     h.close()
+
+
+def test_pred_empty_inference():
+    h = ocf.Predictor(NF, batch=64)
+    h.set_params(dev(_params(2), torch.float32))
+    y = h.infer(torch.zeros((0, NF), dtype=torch.float32, device=DEV))
+    torch.cuda.synchronize()
+    assert y.shape == (0,)
+    h.close()

@@ -93,3 +93,20 @@ def test_stream_untouched_settings_and_errors(orc):
     with pytest.raises(ocf.OpenCFError) as e:
         hb.stream_begin(*csr_dev(*off, torch.float32), dev(np.zeros((300, 32)), torch.float32))
     assert e.value.code == ocf.UNSUPPORTED
+
+
+def test_stream_empty_batch_keeps_V(orc):
+    rng = np.random.default_rng(9)
+    n, k, lam = 96, 16, 0.05
+    off = _block(rng, 400, n, 0.3, torch.float32)
+    U_off = rounded(rng.standard_normal((400, k)) / 4, torch.float32)
+    h = ocf.OpenCF(k=k, lam=lam)
+    h.set_V(dev(np.zeros((n, k)), torch.float32))
+    h.stream_begin(*csr_dev(*off, torch.float32), dev(U_off, torch.float32))
+    V0 = host(h.get_V()).copy()
+    empty = (np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    U, st = h.stream_ingest(*csr_dev(*empty, torch.float32))
+    V1 = host(h.get_V())
+    torch.cuda.synchronize()
+    assert U.shape == (0, k) and st.shape == (0,)
+    assert row_rel_err(V1, V0).max() <= 1e-6     # re-solved from the same sums
