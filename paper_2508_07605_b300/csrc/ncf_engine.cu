@@ -24,6 +24,7 @@ using namespace ocf;
 namespace {
 
 constexpr int64_t NET_PAD = (NCF_NET + 3) / 4 * 4;   // embeddings start 16-byte aligned
+constexpr int STEPS_PER_GRAPH = 16;                   // training steps per graph launch
 static_assert(NCF_NET == OPEN_CF_NCF_NET, "network size");
 
 struct NBuf {
@@ -142,6 +143,45 @@ cudaError_t enqueue_step(open_cf_ncf_t *h, int64_t nnz, int64_t spe, const int32
     u.bf = h->bf.p;
     u.loss_hist = loss_hist; u.loss_last = (double *)h->loss1.p;
     return launch_ncf_train_step(t, u, st);
+}
+
+// Replays `steps` training steps: one graph of STEPS_PER_GRAPH consecutive
+// steps as often as it fits, then single-step graphs (the steps read their
+// position from the device counter, so every replay advances the run).  The
+// graphs are cached by `key` and rebuilt when the arguments change.
+template <typename H, typename F>
+int run_steps(H *h, std::vector<int64_t> key, int64_t steps, cudaStream_t st, F &&enqueue) {
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    for (int r = 0; r < 2; ++r) {
+        const int reps = r == 0 ? 1 : STEPS_PER_GRAPH;
+        std::vector<int64_t> k = key;
+        k.push_back(reps);
+        for (auto &g : h->graphs)
+            if (g.key == k) exec[r] = g.exec;
+        if (exec[r] || (r == 1 && steps < STEPS_PER_GRAPH)) continue;
+        NCK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int t = 0; t < reps && e == cudaSuccess; ++t) e = enqueue(h->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return ncuda(h, e, "training step capture");
+        }
+        if (e2 != cudaSuccess) return ncuda(h, e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec[r], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return ncuda(h, e, "cudaGraphInstantiate");
+        if (h->graphs.size() >= 8) {
+            cudaGraphExecDestroy(h->graphs.front().exec);
+            h->graphs.erase(h->graphs.begin());
+        }
+        h->graphs.push_back(StepGraph{k, exec[r]});
+    }
+    int64_t s = 0;
+    for (; s + STEPS_PER_GRAPH <= steps; s += STEPS_PER_GRAPH) NCK(h, cudaGraphLaunch(exec[1], st));
+    for (; s < steps; ++s) NCK(h, cudaGraphLaunch(exec[0], st));
+    return OPEN_CF_OK;
 }
 
 }  // namespace
@@ -288,33 +328,12 @@ int open_cf_ncf_train(open_cf_ncf_t *h, int64_t nnz, const int32_t *app, const i
     NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(int64_t), st));   // step = 0
     NCK(h, cudaMemsetAsync(F(h->grad) + NET_PAD, 0, sizeof(float) * n_emb(h), st));
     NCK(h, launch_adam_set_lr(h->adam.p, lr, st));
-    std::vector<int64_t> key{nnz, spe, (int64_t)app, (int64_t)setting, (int64_t)val,
-                             (int64_t)perms, (int64_t)loss_out};
-    cudaGraphExec_t exec = nullptr;
-    for (auto &g : h->graphs)
-        if (g.key == key) exec = g.exec;
-    if (!exec) {
-        NCK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = enqueue_step(h, nnz, spe, app, setting, val, perms, loss_out, true,
-                                     h->cap_stream);
-        cudaGraph_t graph = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
-        if (e != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return ncuda(h, e, "training step capture");
-        }
-        if (e2 != cudaSuccess) return ncuda(h, e2, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return ncuda(h, e, "cudaGraphInstantiate");
-        if (h->graphs.size() >= 8) {
-            cudaGraphExecDestroy(h->graphs.front().exec);
-            h->graphs.erase(h->graphs.begin());
-        }
-        h->graphs.push_back(StepGraph{key, exec});
-    }
-    for (int64_t s = 0; s < steps; ++s) NCK(h, cudaGraphLaunch(exec, st));
-    return OPEN_CF_OK;
+    return run_steps(h, {nnz, spe, (int64_t)app, (int64_t)setting, (int64_t)val, (int64_t)perms,
+                         (int64_t)loss_out},
+                     steps, st, [&](cudaStream_t cs) {
+                         return enqueue_step(h, nnz, spe, app, setting, val, perms, loss_out, true,
+                                             cs);
+                     });
 }
 
 int open_cf_ncf_grad(open_cf_ncf_t *h, int64_t B, const int32_t *app, const int32_t *setting,
@@ -551,31 +570,10 @@ int open_cf_pred_train(open_cf_pred_t *h, int64_t N, const float *X, const float
     const int64_t spe = (N + h->B - 1) / h->B, steps = spe * epochs;
     NCK(h, cudaMemsetAsync(h->ctl.p, 0, sizeof(int64_t), st));
     NCK(h, launch_adam_set_lr(h->adam.p, lr, st));
-    std::vector<int64_t> key{N, spe, (int64_t)X, (int64_t)y, (int64_t)perms, (int64_t)loss_out};
-    cudaGraphExec_t exec = nullptr;
-    for (auto &g : h->graphs)
-        if (g.key == key) exec = g.exec;
-    if (!exec) {
-        NCK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = pred_step(h, N, spe, X, y, perms, loss_out, true, h->cap_stream);
-        cudaGraph_t graph = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
-        if (e != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return ncuda(h, e, "training step capture");
-        }
-        if (e2 != cudaSuccess) return ncuda(h, e2, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return ncuda(h, e, "cudaGraphInstantiate");
-        if (h->graphs.size() >= 8) {
-            cudaGraphExecDestroy(h->graphs.front().exec);
-            h->graphs.erase(h->graphs.begin());
-        }
-        h->graphs.push_back(StepGraph{key, exec});
-    }
-    for (int64_t s = 0; s < steps; ++s) NCK(h, cudaGraphLaunch(exec, st));
-    return OPEN_CF_OK;
+    return run_steps(h, {N, spe, (int64_t)X, (int64_t)y, (int64_t)perms, (int64_t)loss_out}, steps,
+                     st, [&](cudaStream_t cs) {
+                         return pred_step(h, N, spe, X, y, perms, loss_out, true, cs);
+                     });
 }
 
 int open_cf_pred_grad(open_cf_pred_t *h, int64_t B, const float *X, const float *y,

@@ -94,6 +94,15 @@ __device__ __forceinline__ void warp_mma(float (&acc)[NT][4], const bf16 *A, int
     }
 }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void st_pair(bf16 *p, float a, float b) {
     *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
 }
@@ -117,7 +126,8 @@ constexpr uint32_t O_RED = O_DZ2 + TB * S2 * 2;                // [8][HEADP] flo
 constexpr uint32_t O_R = O_RED + 8 * HEADP * 4;
 constexpr uint32_t O_RI = O_R + TB * 4;
 constexpr uint32_t O_RJ = O_RI + TB * 4;
-constexpr uint32_t TRAIN_SMEM = O_RJ + TB * 4;
+constexpr uint32_t O_CB = O_RJ + TB * 4;                         // [4][128] db1 partials
+constexpr uint32_t TRAIN_SMEM = O_CB + 4 * NCF_H1 * 4;
 
 __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -130,6 +140,7 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     float *red = reinterpret_cast<float *>(sm + O_RED);
     float *Rs = reinterpret_cast<float *>(sm + O_R);
     int32_t *RI = reinterpret_cast<int32_t *>(sm + O_RI), *RJ = reinterpret_cast<int32_t *>(sm + O_RJ);
+    float *colp = reinterpret_cast<float *>(sm + O_CB);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gid = lane >> 2, t4 = lane & 3;
 
@@ -143,64 +154,93 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
         if (a.adam) a.adam->t += 1;   // the update kernel of this step reads it
     }
 
-    // ---- weights (BF16 copies, row-major) and the gathered inputs
+    // ---- weights (BF16 copies, row-major): asynchronous copies into the padded
+    // tiles, in flight while the inputs are gathered
     const bf16 *W1g = reinterpret_cast<const bf16 *>(a.W1b);
     const bf16 *W2g = reinterpret_cast<const bf16 *>(a.W2b);
     for (int v = tid; v < 2 * NCF_D * (NCF_H1 / 8); v += NTH) {
         const int r = v / (NCF_H1 / 8), c8 = (v % (NCF_H1 / 8)) * 8;
-        *reinterpret_cast<uint4 *>(W1s + r * S1 + c8) =
-            __ldg(reinterpret_cast<const uint4 *>(W1g + r * NCF_H1 + c8));
+        cp_async16(W1s + r * S1 + c8, W1g + r * NCF_H1 + c8);
     }
     for (int v = tid; v < NCF_H1 * (NCF_H2 / 8); v += NTH) {
         const int r = v / (NCF_H2 / 8), c8 = (v % (NCF_H2 / 8)) * 8;
-        *reinterpret_cast<uint4 *>(W2s + r * S2 + c8) =
-            __ldg(reinterpret_cast<const uint4 *>(W2g + r * NCF_H2 + c8));
+        cp_async16(W2s + r * S2 + c8, W2g + r * NCF_H2 + c8);
     }
-    for (int v = tid; v < TB * 8; v += NTH) {
-        const int rr = v >> 3, q = v & 7;
-        const int b = blockIdx.x * TB + rr;
-        bool ok = b < beff;
-        int32_t i = -1, j = -1;
-        int64_t e = 0;
-        if (ok) {
-            e = a.perms ? (int64_t)__ldg(a.perms + epoch * a.nnz + off + b) : off + b;
-            ok = e >= 0 && e < a.nnz;
-            if (ok && !a.feat) {
-                i = __ldg(a.app + e);
-                j = __ldg(a.set + e);
-                ok = i >= 0 && (int64_t)i < a.m && j >= 0 && (int64_t)j < a.n;
-            }
-            if (ok && a.feat) i = 0;   // a live row (no embedding rows to update)
-            if (!ok && q == 0)
-                atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->skipped), 1ull);
+    cp_async_commit();
+    // ---- gathered inputs: thread (row rr, chunk q) takes rows rr and rr + 32,
+    // the two dependent load chains (position -> indices -> embedding rows)
+    // in flight together
+    {
+        const int q = tid & 7;
+        int rr[2], b[2];
+        bool ok[2];
+        int64_t e[2];
+        int32_t i[2], j[2];
+        float rv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            rr[h] = (tid >> 3) + 32 * h;
+            b[h] = blockIdx.x * TB + rr[h];
+            ok[h] = b[h] < beff;
+            e[h] = off + b[h];
         }
-        uint4 pk = make_uint4(0, 0, 0, 0);
-        if (ok && a.feat) {   // dense features, zero padded to 64 columns
+        if (a.perms) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (ok[h]) e[h] = (int64_t)__ldg(a.perms + epoch * a.nnz + off + b[h]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            ok[h] = ok[h] && e[h] >= 0 && e[h] < a.nnz;
+            i[h] = -1;
+            j[h] = -1;
+            rv[h] = 0.f;
+            if (ok[h] && !a.feat) {
+                i[h] = __ldg(a.app + e[h]);
+                j[h] = __ldg(a.set + e[h]);
+            }
+            if (ok[h] && a.val) rv[h] = __ldg(a.val + e[h]);   // no targets when only predicting
+        }
+        uint4 pk[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const bool live = b[h] < beff;
+            if (ok[h] && !a.feat)
+                ok[h] = i[h] >= 0 && (int64_t)i[h] < a.m && j[h] >= 0 && (int64_t)j[h] < a.n;
+            if (ok[h] && a.feat) i[h] = 0;   // a live row (no embedding rows to update)
+            if (live && !ok[h] && q == 0)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->skipped), 1ull);
             float x[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
-                x[t] = 8 * q + t < a.nfeat ? __ldg(a.feat + e * a.nfeat + 8 * q + t) : 0.f;
+            for (int t = 0; t < 8; ++t) x[t] = 0.f;
+            if (ok[h] && a.feat) {   // dense features, zero padded to 64 columns
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (8 * q + t < a.nfeat) x[t] = __ldg(a.feat + e[h] * a.nfeat + 8 * q + t);
+            } else if (ok[h]) {
+                const float *src = q < 4 ? a.Ea + (int64_t)i[h] * NCF_D + 8 * q
+                                         : a.Es + (int64_t)j[h] * NCF_D + 8 * (q - 4);
+                const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src));
+                const float4 x1 = __ldg(reinterpret_cast<const float4 *>(src) + 1);
+                x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
+                x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+            }
             __nv_bfloat162 p0 = __floats2bfloat162_rn(x[0], x[1]), p1 = __floats2bfloat162_rn(x[2], x[3]);
             __nv_bfloat162 p2 = __floats2bfloat162_rn(x[4], x[5]), p3 = __floats2bfloat162_rn(x[6], x[7]);
-            pk = make_uint4(*reinterpret_cast<uint32_t *>(&p0), *reinterpret_cast<uint32_t *>(&p1),
-                            *reinterpret_cast<uint32_t *>(&p2), *reinterpret_cast<uint32_t *>(&p3));
-        } else if (ok) {
-            const float *src = q < 4 ? a.Ea + (int64_t)i * NCF_D + 8 * q
-                                     : a.Es + (int64_t)j * NCF_D + 8 * (q - 4);
-            const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src));
-            const float4 x1 = __ldg(reinterpret_cast<const float4 *>(src) + 1);
-            __nv_bfloat162 p0 = __floats2bfloat162_rn(x0.x, x0.y), p1 = __floats2bfloat162_rn(x0.z, x0.w);
-            __nv_bfloat162 p2 = __floats2bfloat162_rn(x1.x, x1.y), p3 = __floats2bfloat162_rn(x1.z, x1.w);
-            pk = make_uint4(*reinterpret_cast<uint32_t *>(&p0), *reinterpret_cast<uint32_t *>(&p1),
-                            *reinterpret_cast<uint32_t *>(&p2), *reinterpret_cast<uint32_t *>(&p3));
+            pk[h] = make_uint4(*reinterpret_cast<uint32_t *>(&p0), *reinterpret_cast<uint32_t *>(&p1),
+                               *reinterpret_cast<uint32_t *>(&p2), *reinterpret_cast<uint32_t *>(&p3));
         }
-        *reinterpret_cast<uint4 *>(Xs + rr * SX + 8 * q) = pk;
-        if (q == 0) {
-            Rs[rr] = (ok && a.val) ? __ldg(a.val + e) : 0.f;   // no targets when only predicting
-            RI[rr] = ok ? i : -1;
-            RJ[rr] = ok ? j : -1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            *reinterpret_cast<uint4 *>(Xs + rr[h] * SX + 8 * q) = pk[h];
+            if (q == 0) {
+                Rs[rr[h]] = ok[h] ? rv[h] : 0.f;
+                RI[rr[h]] = ok[h] ? i[h] : -1;
+                RJ[rr[h]] = ok[h] ? j[h] : -1;
+            }
         }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // ---- z1 = x W1 + b1 (64 x 128, K = 64)
@@ -286,14 +326,28 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
         float acc[8][4];
         warp_mma<false, true, 8>(acc, D2s, S2, W2s, S2, m0, n0, NCF_H2, lane);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < 8; ++j) {
+            float cs0 = 0.f, cs1 = 0.f;   // this lane's two columns over its two rows
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
                 const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162 *>(Z1s + r * S1 + c);
-                st_pair(D1s + r * S1 + c, acc[j][2 * h] * dselu_t(__low2float(zz)),
-                        acc[j][2 * h + 1] * dselu_t(__high2float(zz)));
+                const float d0 = acc[j][2 * h] * dselu_t(__low2float(zz));
+                const float d1 = acc[j][2 * h + 1] * dselu_t(__high2float(zz));
+                st_pair(D1s + r * S1 + c, d0, d1);
+                cs0 += d0;
+                cs1 += d1;
             }
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {   // over the eight row pairs of the slab
+                cs0 += __shfl_xor_sync(FULL, cs0, o);
+                cs1 += __shfl_xor_sync(FULL, cs1, o);
+            }
+            if (gid == 0) {
+                colp[(warp & 3) * NCF_H1 + n0 + 8 * j + 2 * t4] = cs0;
+                colp[(warp & 3) * NCF_H1 + n0 + 8 * j + 2 * t4 + 1] = cs1;
+            }
+        }
     }
     {
         const int m0 = 16 * warp;
@@ -324,11 +378,9 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
                     make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
             }
     }
-    if (tid < NCF_H1) {
-        float v = 0.f;
-        for (int r = 0; r < TB; ++r) v += __bfloat162float(D1s[r * S1 + tid]);
-        part[NCF_OFF_B1 + tid] = v;
-    }
+    if (tid < NCF_H1)   // the four 16-row slabs in order
+        part[NCF_OFF_B1 + tid] = ((colp[tid] + colp[NCF_H1 + tid]) + colp[2 * NCF_H1 + tid]) +
+                                 colp[3 * NCF_H1 + tid];
     // ---- dx = dz1 W1^T (64 x 64, K = 128) into the embedding gradients
     if (a.gE) {
         const int m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
@@ -369,9 +421,17 @@ __global__ void __launch_bounds__(256) k_ncf_reduce_adam(NcfAdamArgs a) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         float g;
-        if (e < NCF_NET) {
+        if (e < NCF_NET) {   // eight partials in flight at a time, summed in CTA order
             g = 0.f;
-            for (int c = 0; c < a.parts; ++c) g += a.part[(int64_t)c * a.part_stride + e];
+            int c = 0;
+            for (; c + 8 <= a.parts; c += 8) {
+                float v[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) v[t] = a.part[(int64_t)(c + t) * a.part_stride + e];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) g += v[t];
+            }
+            for (; c < a.parts; ++c) g += a.part[(int64_t)c * a.part_stride + e];
             a.grad[e] = g;
         } else if (e < a.net_pad) {
             continue;
