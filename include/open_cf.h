@@ -301,6 +301,15 @@ int open_cf_stream_begin(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ro
 int open_cf_stream_ingest(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_t *row_ptr,
                           const int32_t *col, const void *val, void *U_out, int32_t *status,
                           void *stream);
+/* The sums themselves, for a refit sharded over several processes (each adds
+ * its rows' terms, the processes sum their increments, each installs the
+ * totals): open_cf_stream_sums copies G (n x KP x KP real, row-major per
+ * setting), b (n x KP real) and the counts (n int64) out (any output may be
+ * NULL); open_cf_stream_set_sums installs such sums and re-solves every v_j
+ * from them.  NOT_FITTED before open_cf_stream_begin. */
+int open_cf_stream_sums(open_cf_t *h, void *G_out, void *b_out, int64_t *n_out, void *stream);
+int open_cf_stream_set_sums(open_cf_t *h, const void *G, const void *b, const int64_t *n_obs,
+                            void *stream);
 
 /* FMA-loop microbenchmark (a measurement service, no counterpart in the
  * paper): the FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add

@@ -432,6 +432,10 @@ class StreamState:
         lib().orc_stream_accumulate(len(row_ptr) - 1, _p(row_ptr, _i64), _p(col, _i32),
                                     _p(val, _d), _p(U, _d), self.k, _p(self.G, _d),
                                     _p(self.b, _d), _p(self.cnt, _i64))
+        return self.solve()
+
+    def solve(self):
+        """V from the current sums (after they were changed from outside)."""
         lib().orc_stream_solve(self.n, self.k, _p(self.G, _d), _p(self.b, _d),
                                _p(self.cnt, _i64), self.lam, int(self.weighted), _p(self.V, _d),
                                _p(self.status, _i32))

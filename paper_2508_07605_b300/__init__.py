@@ -72,6 +72,8 @@ _SIGNATURES = {
     "open_cf_fma_peak": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_D)]),
     "open_cf_stream_begin": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V]),
     "open_cf_stream_ingest": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V]),
+    "open_cf_stream_sums": (ctypes.c_int, [_V, _V, _V, _V, _V]),
+    "open_cf_stream_set_sums": (ctypes.c_int, [_V, _V, _V, _V, _V]),
     "open_cf_ncf_create": (ctypes.c_int, [_I64, _I32, _V, _I32, _V, _I32, ctypes.c_int,
                                           ctypes.POINTER(_V)]),
     "open_cf_ncf_destroy": (None, [_V]),
@@ -300,6 +302,26 @@ class OpenCF:
         self._check(lib().open_cf_stream_ingest(self._h, m, nnz, _ptr(row_ptr), _ptr(col),
                                                 _ptr(val), _ptr(U), _ptr(st), self._stream()))
         return U, st
+
+    def stream_sums(self):
+        """(G [n, KP, KP], b [n, KP], counts [n]) of the streaming refit."""
+        n = self.get_V().shape[0]
+        kp = 8 if self.k <= 8 else (16 if self.k <= 16 else 32)
+        G = self._empty(n, kp, kp)
+        b = self._empty(n, kp)
+        cnt = torch.empty(n, dtype=torch.int64, device=self.device)
+        self._check(lib().open_cf_stream_sums(self._h, _ptr(G), _ptr(b), _ptr(cnt),
+                                              self._stream()))
+        return G, b, cnt
+
+    def stream_set_sums(self, G, b, cnt):
+        """Install sums (e.g. totals over several processes) and re-solve V."""
+        for t, nm in ((G, "G"), (b, "b")):
+            self._real(t, nm)
+        if cnt.dtype != torch.int64 or cnt.device != self.device or not cnt.is_contiguous():
+            raise ValueError("counts must be a contiguous int64 tensor on the device")
+        self._check(lib().open_cf_stream_set_sums(self._h, _ptr(G), _ptr(b), _ptr(cnt),
+                                                  self._stream()))
 
     def objective(self, row_ptr, col, val, U, row_rmse: bool = False):
         m, nnz = self._csr(row_ptr, col, val)

@@ -938,6 +938,43 @@ int open_cf_stream_ingest(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
                                            (float *)U_out, status, st);
 }
 
+int open_cf_stream_sums(open_cf_t *h, void *G_out, void *b_out, int64_t *n_out, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!h->stream_on) return fail(h, OPEN_CF_NOT_FITTED, "call open_cf_stream_begin first");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const int64_t n = h->n, KP = h->KP;
+    if (G_out)
+        CK(h, cudaMemcpyAsync(G_out, h->sg.p, h->esz * n * KP * KP, cudaMemcpyDeviceToDevice, st));
+    if (b_out)
+        CK(h, cudaMemcpyAsync(b_out, h->sb.p, h->esz * n * KP, cudaMemcpyDeviceToDevice, st));
+    if (n_out)
+        CK(h, cudaMemcpyAsync(n_out, h->sn.p, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st));
+    return OPEN_CF_OK;
+}
+
+int open_cf_stream_set_sums(open_cf_t *h, const void *G, const void *b, const int64_t *n_obs,
+                            void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!h->stream_on) return fail(h, OPEN_CF_NOT_FITTED, "call open_cf_stream_begin first");
+    if (!G || !b || !n_obs) return fail(h, OPEN_CF_INVALID_ARG, "G, b and n_obs are required");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const int64_t n = h->n, KP = h->KP;
+    CK(h, cudaMemcpyAsync(h->sg.p, G, h->esz * n * KP * KP, cudaMemcpyDeviceToDevice, st));
+    CK(h, cudaMemcpyAsync(h->sb.p, b, h->esz * n * KP, cudaMemcpyDeviceToDevice, st));
+    CK(h, cudaMemcpyAsync(h->sn.p, n_obs, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st));
+    // every setting re-solved from the sums alone (a batch of no rows)
+    CK(h, ensure(h, h->U_w, h->esz * KP));
+    CK(h, ensure(h, h->j_ptr, sizeof(int64_t)));
+    CK(h, cudaMemsetAsync(h->j_ptr.p, 0, sizeof(int64_t), st));
+    const int64_t *p0 = (const int64_t *)h->j_ptr.p;
+    return h->f64 ? stream_vhalf<double>(h, 0, 0, p0, nullptr, nullptr, (const double *)h->U_w.p, st)
+                  : stream_vhalf<float>(h, 0, 0, p0, nullptr, nullptr, (const float *)h->U_w.p, st);
+}
+
 int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t *best,
                     float *saving, float gamma, int32_t baseline_setting, void *stream) {
     if (!h) return OPEN_CF_INVALID_ARG;

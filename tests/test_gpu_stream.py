@@ -110,3 +110,49 @@ def test_stream_empty_batch_keeps_V(orc):
     torch.cuda.synchronize()
     assert U.shape == (0, k) and st.shape == (0,)
     assert row_rel_err(V1, V0).max() <= 1e-6     # re-solved from the same sums
+
+
+def test_stream_sums_exchange_emulated_on_one_gpu(orc):
+    """Two handles stand for two ranks: each adds its shard's terms, the
+    increments are summed (what the all-reduce of paper_2508_07605_b300.shard
+    does across processes) and installed in both; V then equals that of one
+    handle that ingested every row."""
+    rng = np.random.default_rng(13)
+    n, k, lam = 96, 16, 0.05
+    dt = torch.float32
+    off = _block(rng, 500, n, 0.3, dt)
+    U_off = rounded(rng.standard_normal((500, k)) / 4, dt)
+    new = _block(rng, 300, n, 0.08, dt)
+
+    def rows(blk, r0, r1):
+        p, c, v = blk
+        return p[r0:r1 + 1] - p[r0], c[p[r0]:p[r1]], v[p[r0]:p[r1]]
+
+    one = ocf.OpenCF(k=k, lam=lam)
+    one.set_V(dev(np.zeros((n, k)), dt))
+    one.stream_begin(*csr_dev(*off, dt), dev(U_off, dt))
+    U_one, _ = one.stream_ingest(*csr_dev(*new, dt))
+    ranks = [ocf.OpenCF(k=k, lam=lam) for _ in range(2)]
+    cuts = [(0, 250), (250, 500)]
+    for h, (r0, r1) in zip(ranks, cuts):
+        h.set_V(dev(np.zeros((n, k)), dt))
+        h.stream_begin(*csr_dev(*rows(off, r0, r1), dt), dev(U_off[r0:r1], dt))
+    tot = [sum(x) for x in zip(*[h.stream_sums() for h in ranks])]
+    for h in ranks:
+        h.stream_set_sums(*tot)
+    base = [t.clone() for t in tot]
+    Us = []
+    for h, (r0, r1) in zip(ranks, [(0, 120), (120, 300)]):
+        U, _ = h.stream_ingest(*csr_dev(*rows(new, r0, r1), dt))
+        Us.append(U)
+    incs = [[c - b for c, b in zip(h.stream_sums(), base)] for h in ranks]
+    tot = [b + i0 + i1 for b, i0, i1 in zip(base, *incs)]
+    for h in ranks:
+        h.stream_set_sums(*tot)
+    torch.cuda.synchronize()
+    Vone = host(one.get_V()).astype(np.float64)
+    for h in ranks:
+        assert row_rel_err(host(h.get_V()), Vone).max() <= 1e-4
+    assert row_rel_err(host(torch.cat(Us)), host(U_one)).max() <= 1e-5
+    # the counts are exact
+    assert torch.equal(tot[2], one.stream_sums()[2])
