@@ -1228,10 +1228,11 @@ def run_gpu_stream(args):
         h.set_V(V_fit)
         h.stream_begin(*o_csr, U_off)
 
-    # warm-up on a restarted stream, then the timed stream from the start
+    # warm-up: every batch once on a restarted stream (each batch's ingest graph
+    # is captured here, at least W steps in all), then the timed stream from the start
     restart()
-    for b in range(min(W, nb)):
-        h.stream_ingest(*d_batches[b])
+    for b in range(max(W, steps)):
+        h.stream_ingest(*d_batches[b % nb])
     torch.cuda.synchronize()
     restart()
     torch.cuda.synchronize()

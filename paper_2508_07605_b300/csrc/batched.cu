@@ -39,7 +39,7 @@ __device__ void solve_range(const SolveArgs<float> &a, int wig, int W, unsigned 
     using WS = WarpSmem<float, float, KP>;
     // each warp's area starts at warp * sizeof(WS32); solve_system indexes smem[warp]
     WS *mine = reinterpret_cast<WS *>(wsbase + (size_t)warp * sizeof(WS32));
-    for (int64_t i = wig; i < a.m; i += W) solve_system<float, float, KP, 1>(a, i, mine, 0, lane);
+    for (int64_t i = wig; i < a.m; i += W) solve_system<float, float, KP, 1, false>(a, i, mine, 0, lane);
 }
 
 __device__ void run_half(const SolveArgs<float> &a, int KP, int wig, int W, unsigned char *wsbase,
@@ -49,7 +49,7 @@ __device__ void run_half(const SolveArgs<float> &a, int KP, int wig, int W, unsi
     else solve_range<32>(a, wig, W, wsbase, warp, lane);
 }
 
-__global__ void __launch_bounds__(BW * 32) k_batched_als(BatchArgs b) {
+__global__ void __launch_bounds__(BW * 32, 2) k_batched_als(BatchArgs b) {   // two CTAs per SM
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int32_t qslot[BW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -843,9 +843,10 @@ namespace {
 
 // Streaming refit: CSC of a batch of rows with (padded) factors Uw, then the
 // V-half-step with the stored sums added and kept (every setting re-solved).
+// stream_vhalf_ws sizes the workspaces (not capturable: it may allocate);
+// stream_vhalf_enqueue only launches kernels.
 template <typename TV>
-int stream_vhalf(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
-                 const TV *val, const TV *Uw, cudaStream_t st) {
+int stream_vhalf_ws(open_cf_t *h, int64_t m, int64_t nnz) {
     const int64_t n = h->n;
     const CscPlan plan = csc_plan(m, n, nnz, 0);
     CK(h, ensure(h, h->csc_ptr, sizeof(int64_t) * (n + 1)));
@@ -853,10 +854,19 @@ int stream_vhalf(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const
     CK(h, ensure(h, h->csc_val, sizeof(TV) * std::max<int64_t>(nnz, 1)));
     CK(h, ensure(h, h->cnt, sizeof(int32_t) * n * plan.nb));
     CK(h, ensure(h, h->tot, sizeof(int64_t) * n));
+    return OPEN_CF_OK;
+}
+
+template <typename TV>
+cudaError_t stream_vhalf_enqueue(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr,
+                                 const int32_t *idx, const TV *val, const TV *Uw, cudaStream_t st) {
+    const int64_t n = h->n;
+    const CscPlan plan = csc_plan(m, n, nnz, 0);
     int64_t *cptr = (int64_t *)h->csc_ptr.p;
-    CK(h, launch_csr_to_csc<TV>(m, n, nnz, ptr, idx, val, cptr, (int32_t *)h->csc_idx.p,
-                                (TV *)h->csc_val.p, (int32_t *)h->cnt.p, (int64_t *)h->tot.p, plan,
-                                st));
+    cudaError_t e = launch_csr_to_csc<TV>(m, n, nnz, ptr, idx, val, cptr, (int32_t *)h->csc_idx.p,
+                                          (TV *)h->csc_val.p, (int32_t *)h->cnt.p,
+                                          (int64_t *)h->tot.p, plan, st);
+    if (e != cudaSuccess) return e;
     SolveArgs<TV> va{n, nnz, cptr, (const int32_t *)h->csc_idx.p, (const TV *)h->csc_val.p, Uw,
                      m, (TV *)h->V.p, h->KP, h->KP, nullptr, h->cfg.lambda};
     va.wr = h->cfg.weighted_lambda != 0;
@@ -864,7 +874,15 @@ int stream_vhalf(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const
     va.gram_b = (TV *)h->sb.p;
     va.gram_n = (int64_t *)h->sn.p;
     va.gram_keep = true;
-    CK(h, half_step<TV>(h, va, st));
+    return half_step<TV>(h, va, st);
+}
+
+template <typename TV>
+int stream_vhalf(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
+                 const TV *val, const TV *Uw, cudaStream_t st) {
+    int rc = stream_vhalf_ws<TV>(h, m, nnz);
+    if (rc) return rc;
+    CK(h, stream_vhalf_enqueue<TV>(h, m, nnz, ptr, idx, val, Uw, st));
     return OPEN_CF_OK;
 }
 
@@ -883,13 +901,24 @@ int stream_ingest_t(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, co
                     const TV *val, TV *U_out, int32_t *status, cudaStream_t st) {
     const int KP = h->KP;
     CK(h, ensure(h, h->U_w, sizeof(TV) * std::max<int64_t>(m, 1) * KP));
+    int rc = stream_vhalf_ws<TV>(h, m, nnz);
+    if (rc) return rc;
     TV *Uw = (TV *)h->U_w.p;
-    SolveArgs<TV> ua{m, nnz, ptr, idx, val, (const TV *)h->V.p, h->n, Uw, KP, KP, status,
-                     h->cfg.lambda};
-    ua.wr = h->cfg.weighted_lambda != 0;
-    CK(h, half_step<TV>(h, ua, st));   // fold-in against the current V
-    if (m > 0) CK(h, launch_unpack_rows<TV>(Uw, m, KP, h->k, U_out, st));
-    return stream_vhalf<TV>(h, m, nnz, ptr, idx, val, Uw, st);
+    // fold-in against the current V, the factors out, the V-half with the
+    // stored sums: one captured graph per argument set, replayed
+    auto enqueue = [&](cudaStream_t cs) -> cudaError_t {
+        SolveArgs<TV> ua{m, nnz, ptr, idx, val, (const TV *)h->V.p, h->n, Uw, KP, KP, status,
+                         h->cfg.lambda};
+        ua.wr = h->cfg.weighted_lambda != 0;
+        cudaError_t e = half_step<TV>(h, ua, cs);
+        if (e != cudaSuccess) return e;
+        if (m > 0 && (e = launch_unpack_rows<TV>(Uw, m, KP, h->k, U_out, cs)) != cudaSuccess)
+            return e;
+        return stream_vhalf_enqueue<TV>(h, m, nnz, ptr, idx, val, Uw, cs);
+    };
+    std::vector<int64_t> key = {6, m, nnz, (int64_t)ptr, (int64_t)idx, (int64_t)val,
+                                (int64_t)U_out, (int64_t)status};
+    return run_graph(h, key, st, enqueue);
 }
 
 }  // namespace

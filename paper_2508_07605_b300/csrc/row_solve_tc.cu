@@ -475,7 +475,7 @@ k_row_solve_tc(SolveArgs<float> a) {
                     if (q == 0) a.gram_n[i] = s;
                 }
             }
-            const TC lam = a.wr ? TC(a.lambda * (double)s) : TC(a.lambda);   // weighted: lambda s_i
+            const TC lam = TC(a.lambda) * (a.wr ? TC(s) : TC(1));   // weighted: lambda s_i
 #pragma unroll
             for (int e = 0; e < KP; ++e)
                 if (e == q) A[e] += lam;

@@ -24,7 +24,9 @@ __device__ __forceinline__ double my_rsqrt(double x) { return rsqrt(x); }
 
 // Solve system i.  WPS = 1: the calling warp alone (lanes in G = 32/KP groups);
 // WPS > 1: the WPS warps of the CTA together (every warp of the CTA calls it).
-template <typename TV, typename TC, int KP, int WPS>
+// SUMS: the build supports the stored sums of the streaming refit (the
+// batched kernel, which never uses them, leaves them out to save registers).
+template <typename TV, typename TC, int KP, int WPS, bool SUMS = true>
 __device__ __forceinline__ void solve_system(const SolveArgs<TV> &a, int64_t i,
                                              WarpSmem<TV, TC, KP> *smem, int warp, int lane) {
     constexpr int G = 32 / KP;
@@ -111,7 +113,7 @@ __device__ __forceinline__ void solve_system(const SolveArgs<TV> &a, int64_t i,
             for (int e = 0; e < KP; ++e) A[e] = TC(acc[e]);
             bt = TC(bq);
         }
-        if (a.gram && !bad && (WPS == 1 || warp == 0)) {   // streaming: stored sums of earlier rows
+        if (SUMS && a.gram && !bad && (WPS == 1 || warp == 0)) {   // streaming: stored sums
             TV *gq = a.gram + (i * KP + q) * KP;
 #pragma unroll
             for (int e = 0; e < KP; ++e) A[e] += TC(gq[e]);
@@ -124,7 +126,7 @@ __device__ __forceinline__ void solve_system(const SolveArgs<TV> &a, int64_t i,
                 if (q == 0) a.gram_n[i] = s;
             }
         }
-        const TC lam = a.wr ? TC(a.lambda * (double)s) : TC(a.lambda);   // weighted: lambda s_i
+        const TC lam = TC(a.lambda) * (a.wr ? TC(s) : TC(1));   // weighted: lambda s_i
 #pragma unroll
         for (int e = 0; e < KP; ++e)
             if (e == q) A[e] += lam;
