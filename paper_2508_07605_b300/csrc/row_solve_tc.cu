@@ -142,7 +142,9 @@ template <int KP> struct Blocks {
     __device__ static constexpr int nb_of(int t) { return KP == 16 ? t : (t < 2 ? t : t - 2); }
 };
 
-template <int KP, typename TC, int WPS, bool BF>
+// SUMS: this build adds the streaming refit's stored sums (kept out of the
+// other builds, where the extra registers cost occupancy).
+template <int KP, typename TC, int WPS, bool BF, bool SUMS = false>
 __global__ void __launch_bounds__(WPS == 1 ? (sizeof(TC) == 8 && KP == 32 ? 128 : 256) : 32 * WPS)
 k_row_solve_tc(SolveArgs<float> a) {
     constexpr int WARPS = (WPS == 1) ? ((sizeof(TC) == 8 && KP == 32) ? 4 : 8) : WPS;
@@ -461,7 +463,7 @@ k_row_solve_tc(SolveArgs<float> a) {
                 for (int e = 0; e < KP; ++e) A[e] = TC(S.G[q][e]);
                 bt = TC(S.b[q]);
             }
-            if (a.gram && !bad && base + slot < M) {   // streaming: stored sums of earlier rows
+            if (SUMS && !bad && base + slot < M) {   // streaming: stored sums of earlier rows
                 const int64_t i = a.row_map ? a.row_map[base + slot] : base + slot;
                 float *gq = a.gram + (i * KP + q) * KP;
 #pragma unroll
@@ -570,7 +572,11 @@ template <int KP, typename TC, int WPS, bool BF> static size_t tc_smem_bytes() {
 }
 
 template <int KP, typename TC, int WPS, bool BF> static cudaError_t tc_attr() {
-    return cudaFuncSetAttribute(k_row_solve_tc<KP, TC, WPS, BF>,
+    cudaError_t e = cudaFuncSetAttribute(k_row_solve_tc<KP, TC, WPS, BF, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes<KP, TC, WPS, BF>());
+    if (e != cudaSuccess || BF) return e;
+    return cudaFuncSetAttribute(k_row_solve_tc<KP, TC, WPS, false, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tc_smem_bytes<KP, TC, WPS, BF>());
 }
@@ -611,29 +617,31 @@ static cudaError_t launch_pdl(K kernel, unsigned grid, unsigned block, size_t sm
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
-template <int KP, typename TC, bool BF>
+template <int KP, typename TC, bool BF, bool SUMS>
 static cudaError_t launch_tc_kp(const SolveArgs<float> &a, cudaStream_t st) {
     if (a.nnz >= LONG_ROW_TC * a.m) {
         int64_t blocks = a.m;
         if (blocks > NUM_SMS_HINT * 64) blocks = NUM_SMS_HINT * 64;
-        return launch_pdl(k_row_solve_tc<KP, TC, 4, BF>, (unsigned)blocks, 128,
+        return launch_pdl(k_row_solve_tc<KP, TC, 4, BF, SUMS>, (unsigned)blocks, 128,
                           tc_smem_bytes<KP, TC, 4, BF>(), st, a);
     }
     constexpr int WARPS = (sizeof(TC) == 8 && KP == 32) ? 4 : 8;
     const int64_t per = (int64_t)WARPS * (32 / KP);
     int64_t blocks = (a.m + per - 1) / per;
     if (blocks > NUM_SMS_HINT * 32) blocks = NUM_SMS_HINT * 32;
-    return launch_pdl(k_row_solve_tc<KP, TC, 1, BF>, (unsigned)blocks, WARPS * 32,
+    return launch_pdl(k_row_solve_tc<KP, TC, 1, BF, SUMS>, (unsigned)blocks, WARPS * 32,
                       tc_smem_bytes<KP, TC, 1, BF>(), st, a);
 }
 
-template <bool BF>
+template <bool BF, bool SUMS>
 static cudaError_t launch_tc_bf(const SolveArgs<float> &a, int KP, bool chol_fp64,
                                 cudaStream_t st) {
     if (KP == 16)
-        return chol_fp64 ? launch_tc_kp<16, double, BF>(a, st) : launch_tc_kp<16, float, BF>(a, st);
+        return chol_fp64 ? launch_tc_kp<16, double, BF, SUMS>(a, st)
+                         : launch_tc_kp<16, float, BF, SUMS>(a, st);
     if (KP == 32)
-        return chol_fp64 ? launch_tc_kp<32, double, BF>(a, st) : launch_tc_kp<32, float, BF>(a, st);
+        return chol_fp64 ? launch_tc_kp<32, double, BF, SUMS>(a, st)
+                         : launch_tc_kp<32, float, BF, SUMS>(a, st);
     return cudaErrorInvalidValue;
 }
 
@@ -641,8 +649,10 @@ cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp6
                                 cudaStream_t st) {
     if (a.m <= 0) return cudaSuccess;
     if (bf16 && !a.Fb) return cudaErrorInvalidValue;
-    return bf16 ? launch_tc_bf<true>(a, KP, chol_fp64, st)
-                : launch_tc_bf<false>(a, KP, chol_fp64, st);
+    if (bf16 && a.gram) return cudaErrorInvalidValue;   // the streaming refit is FP32 / FP64 only
+    if (bf16) return launch_tc_bf<true, false>(a, KP, chol_fp64, st);
+    return a.gram ? launch_tc_bf<false, true>(a, KP, chol_fp64, st)
+                  : launch_tc_bf<false, false>(a, KP, chol_fp64, st);
 }
 
 }  // namespace ocf
