@@ -294,11 +294,15 @@ class OpenCF:
         self._check(lib().open_cf_stream_begin(self._h, m, nnz, _ptr(row_ptr), _ptr(col),
                                                _ptr(val), _ptr(U), self._stream()))
 
-    def stream_ingest(self, row_ptr, col, val):
-        """A batch of new applications: (U_new, status); V is refitted in place."""
+    def stream_ingest(self, row_ptr, col, val, out=None, status=None):
+        """A batch of new applications: (U_new, status); V is refitted in place.
+        `out` (m x k) and `status` (int32 m) may be given to reuse buffers."""
         m, nnz = self._csr(row_ptr, col, val)
-        U = self._empty(m, self.k)
-        st = self._empty(m, dtype=torch.int32)
+        U = out if out is not None else self._empty(m, self.k)
+        st = status if status is not None else self._empty(m, dtype=torch.int32)
+        self._real(U, "out")
+        if U.shape != (m, self.k) or st.shape != (m,) or st.dtype != torch.int32:
+            raise ValueError("out must be m x k and status int32 of length m")
         self._check(lib().open_cf_stream_ingest(self._h, m, nnz, _ptr(row_ptr), _ptr(col),
                                                 _ptr(val), _ptr(U), _ptr(st), self._stream()))
         return U, st

@@ -292,10 +292,10 @@ __global__ void k_adam(int64_t count, float *__restrict__ th, const float *__res
                        const int64_t *__restrict__ bf_map, bf16 *__restrict__ thb,
                        const int64_t *__restrict__ img_map, bf16 *__restrict__ img) {
     __shared__ float corr[3];   // bias corrections of step t (after the tick), once per CTA
-    if (threadIdx.x == 0) {   // 1 - beta^t as 1 - 2^(t log2 beta), in FP32
-        const float tt = (float)as->t;
-        corr[0] = 1.f - exp2f(tt * log2f(b1));
-        corr[1] = 1.f - exp2f(tt * log2f(b2));
+    if (threadIdx.x == 0) {
+        const double tt = (double)as->t;
+        corr[0] = (float)(1.0 - pow((double)b1, tt));
+        corr[1] = (float)(1.0 - pow((double)b2, tt));
         corr[2] = as->lr;
     }
     __syncthreads();
