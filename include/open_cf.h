@@ -37,6 +37,11 @@
  *    errors are detected synchronously on the host and leave the handle
  *    unchanged.
  *  - A handle may be used by one host thread at a time.
+ *  - Calls that run many kernels (fits, joint refits, streaming ingests, the
+ *    learned path's training step) capture them once into a CUDA graph kept
+ *    per argument set (sizes and array addresses; up to 16 per handle) and
+ *    replay it: repeated calls on the same buffers cost one graph launch,
+ *    new buffers a new capture.
  *  - There is no CPU fallback: every computation runs in this library's CUDA
  *    kernels for sm_103a.
  */
