@@ -270,6 +270,7 @@ constexpr int64_t NCF_OFF_B2 = NCF_OFF_W2 + NCF_H1 * NCF_H2;
 constexpr int64_t NCF_OFF_W3 = NCF_OFF_B2 + NCF_H2;
 constexpr int64_t NCF_OFF_B3 = NCF_OFF_W3 + NCF_H2;
 constexpr int64_t NCF_NET = NCF_OFF_B3 + 1;                            // 16641
+constexpr int NCF_TT = 32;   // batch rows per CTA of the training kernel (partials per step: B / 32)
 struct NcfCtl {                 // device-side position of a training run
     int64_t step;               // steps done (epoch = step / steps_per_epoch)
     unsigned long long skipped; // batch entries skipped for out-of-range indices
@@ -287,9 +288,9 @@ struct NcfTrainArgs {            // k_ncf_train_tile: forward + backward of one 
     const float *Ea, *Es;       // FP32 embedding tables [m][32], [n][32]
     const void *W1b, *W2b;      // BF16 copies of W1 [64][128] and W2 [128][64]
     const float *b1, *b2, *w3, *b3;   // FP32 parameters
-    float *part;                // [B/64][part_stride] network-gradient partials (packed order)
+    float *part;                // [B/32][part_stride] network-gradient partials (packed order)
     int64_t part_stride;
-    float *lpart;               // [B/64] sums of squared residuals
+    float *lpart;               // [B/32] sums of squared residuals
     float *gE;                  // embedding gradients: Ea rows, then Es rows at s_off (NULL: none)
     int64_t s_off;
     // Dense-feature mode (the offline performance predictor): row e of the

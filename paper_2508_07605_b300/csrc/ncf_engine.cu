@@ -137,7 +137,7 @@ cudaError_t enqueue_step(open_cf_ncf_t *h, int64_t nnz, int64_t spe, const int32
     u.ctl = ctl;
     u.adam = reinterpret_cast<const AdamState *>(h->adam.p);
     u.update = update;
-    u.parts = h->B / 64; u.part = F(h->part); u.part_stride = NET_PAD; u.lpart = F(h->lpart);
+    u.parts = h->B / NCF_TT; u.part = F(h->part); u.part_stride = NET_PAD; u.lpart = F(h->lpart);
     u.th = th; u.grad = g; u.m1 = F(h->m1); u.m2 = F(h->m2);
     u.net_pad = NET_PAD; u.n_emb = n_emb(h);
     u.bf = h->bf.p;
@@ -232,7 +232,7 @@ int open_cf_ncf_create(int64_t m, int32_t n_cpu, const double *cpu_caps_w_host, 
     A(h->m1, sizeof(float) * P); A(h->m2, sizeof(float) * P);
     A(h->bf, 2 * 2 * NCF_OFF_B1);
     A(h->adam, 16); A(h->ctl, sizeof(NcfCtl)); A(h->loss1, sizeof(double));
-    A(h->part, sizeof(float) * (batch / 64) * NET_PAD); A(h->lpart, sizeof(float) * (batch / 64));
+    A(h->part, sizeof(float) * (batch / NCF_TT) * NET_PAD); A(h->lpart, sizeof(float) * (batch / NCF_TT));
     A(h->A, sizeof(float) * m * NCF_H1); A(h->S, sizeof(float) * h->n * NCF_H1);
     A(h->w2img, 2 * NCF_H1 * NCF_H2); A(h->cg, sizeof(float) * h->n); A(h->err, 16);
     if (e == cudaSuccess) e = cudaMemcpy(h->cg.p, cg.data(), sizeof(float) * h->n,
@@ -451,7 +451,7 @@ cudaError_t pred_step(open_cf_pred_t *h, int64_t N, int64_t spe, const float *X,
     u.ctl = ctl;
     u.adam = reinterpret_cast<const AdamState *>(h->adam.p);
     u.update = update;
-    u.parts = h->B / 64; u.part = F(h->part); u.part_stride = NET_PAD; u.lpart = F(h->lpart);
+    u.parts = h->B / NCF_TT; u.part = F(h->part); u.part_stride = NET_PAD; u.lpart = F(h->lpart);
     u.th = th; u.grad = g; u.m1 = F(h->m1); u.m2 = F(h->m2);
     u.net_pad = NET_PAD; u.n_emb = 0;
     u.bf = h->bf.p;
@@ -489,7 +489,7 @@ int open_cf_pred_create(int32_t n_features, int32_t batch, int device, open_cf_p
     A(h->m1, sizeof(float) * NET_PAD); A(h->m2, sizeof(float) * NET_PAD);
     A(h->bf, 2 * 2 * NCF_OFF_B1);
     A(h->adam, 16); A(h->ctl, sizeof(NcfCtl)); A(h->loss1, sizeof(double));
-    A(h->part, sizeof(float) * (batch / 64) * NET_PAD); A(h->lpart, sizeof(float) * (batch / 64));
+    A(h->part, sizeof(float) * (batch / NCF_TT) * NET_PAD); A(h->lpart, sizeof(float) * (batch / NCF_TT));
     if (e == cudaSuccess) e = cudaMemset(h->ctl.p, 0, sizeof(NcfCtl));
     if (e == cudaSuccess) e = prepare_ncf_train();
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);

@@ -2,12 +2,12 @@
 // Model"; mean squared error over a mini-batch of observed entries, Adam) in
 // two kernels.
 //
-// k_ncf_train_tile: one CTA per 64 batch rows runs the whole forward and
+// k_ncf_train_tile: one CTA per 32 batch rows runs the whole forward and
 // backward pass of its rows on the SM, with the BF16 weights and every
 // activation in shared memory:
-//   gather   x = [Ea_i, Es_j]                        (64 x 64, BF16)
-//   forward  z1 = x W1 + b1, h1 = SELU(z1)            (64 x 128)
-//            z2 = h1 W2 + b2, h2 = SELU(z2)           (64 x 64)
+//   gather   x = [Ea_i, Es_j]                        (32 x 64, BF16)
+//   forward  z1 = x W1 + b1, h1 = SELU(z1)            (32 x 128)
+//            z2 = h1 W2 + b2, h2 = SELU(z2)           (32 x 64)
 //   head     y = h2 . w3 + b3, dy = 2 (y - r) / B, dz2 = dy w3 SELU'(z2)
 //   backward dz1 = (dz2 W2^T) SELU'(z1),  dW2 += h1^T dz2,  dW1 += x^T dz1,
 //            db1 += colsum dz1,  dx = dz1 W1^T -> the two embedding rows
@@ -107,27 +107,31 @@ __device__ __forceinline__ void st_pair(bf16 *p, float a, float b) {
     *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
 }
 
-constexpr int TB = 64;                  // batch rows per CTA
+constexpr int TB = 64;                  // rows per tile of the prediction kernel
+constexpr int TT = NCF_TT;              // batch rows per CTA of the training kernel
+constexpr int MT = TT / 16;             // its 16-row slabs (MMA m-tiles)
+constexpr int WPM = 8 / MT;             // warps sharing one slab
 constexpr int NTH = 256;
+constexpr int RPT = TT * 8 / NTH;       // gathered rows per thread
 constexpr int SX = 2 * NCF_D + 8;       // row strides (elements) of the padded tiles
 constexpr int S1 = NCF_H1 + 8;
 constexpr int S2 = NCF_H2 + 8;
 constexpr uint32_t O_W1 = 0;                                   // W1  [64][S1]
 constexpr uint32_t O_W2 = O_W1 + 2 * NCF_D * S1 * 2;           // W2  [128][S2]
 constexpr uint32_t O_X = O_W2 + NCF_H1 * S2 * 2;               // x   [64][SX]
-constexpr uint32_t O_Z1 = O_X + TB * SX * 2;                   // z1, h1, dz1 [64][S1]
-constexpr uint32_t O_H1 = O_Z1 + TB * S1 * 2;
-constexpr uint32_t O_DZ1 = O_H1 + TB * S1 * 2;
-constexpr uint32_t O_Z2 = O_DZ1 + TB * S1 * 2;                 // z2, h2, dz2 [64][S2]
-constexpr uint32_t O_H2 = O_Z2 + TB * S2 * 2;
-constexpr uint32_t O_DZ2 = O_H2 + TB * S2 * 2;
+constexpr uint32_t O_Z1 = O_X + TT * SX * 2;                   // z1, h1, dz1 [TT][S1]
+constexpr uint32_t O_H1 = O_Z1 + TT * S1 * 2;
+constexpr uint32_t O_DZ1 = O_H1 + TT * S1 * 2;
+constexpr uint32_t O_Z2 = O_DZ1 + TT * S1 * 2;                 // z2, h2, dz2 [TT][S2]
+constexpr uint32_t O_H2 = O_Z2 + TT * S2 * 2;
+constexpr uint32_t O_DZ2 = O_H2 + TT * S2 * 2;
 constexpr int HEADP = 2 * NCF_H2 + 2;                          // gb2 | gw3 | gb3 | sse
-constexpr uint32_t O_RED = O_DZ2 + TB * S2 * 2;                // [8][HEADP] floats
+constexpr uint32_t O_RED = O_DZ2 + TT * S2 * 2;                // [8][HEADP] floats
 constexpr uint32_t O_R = O_RED + 8 * HEADP * 4;
-constexpr uint32_t O_RI = O_R + TB * 4;
-constexpr uint32_t O_RJ = O_RI + TB * 4;
-constexpr uint32_t O_CB = O_RJ + TB * 4;                         // [4][128] db1 partials
-constexpr uint32_t TRAIN_SMEM = O_CB + 4 * NCF_H1 * 4;
+constexpr uint32_t O_RI = O_R + TT * 4;
+constexpr uint32_t O_RJ = O_RI + TT * 4;
+constexpr uint32_t O_CB = O_RJ + TT * 4;                         // [MT][128] db1 partials
+constexpr uint32_t TRAIN_SMEM = O_CB + MT * NCF_H1 * 4;
 
 __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -167,30 +171,30 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
         cp_async16(W2s + r * S2 + c8, W2g + r * NCF_H2 + c8);
     }
     cp_async_commit();
-    // ---- gathered inputs: thread (row rr, chunk q) takes rows rr and rr + 32,
-    // the two dependent load chains (position -> indices -> embedding rows)
-    // in flight together
+    // ---- gathered inputs: thread (row rr, chunk q) takes rows rr, rr + 32, ...
+    // (RPT of them), their dependent load chains (position -> indices ->
+    // embedding rows) in flight together
     {
         const int q = tid & 7;
-        int rr[2], b[2];
-        bool ok[2];
-        int64_t e[2];
-        int32_t i[2], j[2];
-        float rv[2];
+        int rr[RPT], b[RPT];
+        bool ok[RPT];
+        int64_t e[RPT];
+        int32_t i[RPT], j[RPT];
+        float rv[RPT];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < RPT; ++h) {
             rr[h] = (tid >> 3) + 32 * h;
-            b[h] = blockIdx.x * TB + rr[h];
+            b[h] = blockIdx.x * TT + rr[h];
             ok[h] = b[h] < beff;
             e[h] = off + b[h];
         }
         if (a.perms) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < RPT; ++h)
                 if (ok[h]) e[h] = (int64_t)__ldg(a.perms + epoch * a.nnz + off + b[h]);
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < RPT; ++h) {
             ok[h] = ok[h] && e[h] >= 0 && e[h] < a.nnz;
             i[h] = -1;
             j[h] = -1;
@@ -201,9 +205,9 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
             }
             if (ok[h] && a.val) rv[h] = __ldg(a.val + e[h]);   // no targets when only predicting
         }
-        uint4 pk[2];
+        uint4 pk[RPT];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < RPT; ++h) {
             const bool live = b[h] < beff;
             if (ok[h] && !a.feat)
                 ok[h] = i[h] >= 0 && (int64_t)i[h] < a.m && j[h] >= 0 && (int64_t)j[h] < a.n;
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
                                *reinterpret_cast<uint32_t *>(&p2), *reinterpret_cast<uint32_t *>(&p3));
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < RPT; ++h) {
             *reinterpret_cast<uint4 *>(Xs + rr[h] * SX + 8 * q) = pk[h];
             if (q == 0) {
                 Rs[rr[h]] = ok[h] ? rv[h] : 0.f;
@@ -243,13 +247,14 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     cp_async_wait_all();
     __syncthreads();
 
-    // ---- z1 = x W1 + b1 (64 x 128, K = 64)
+    // ---- z1 = x W1 + b1 (TT x 128, K = 64)
     {
-        const int m0 = 16 * (warp & 3), n0 = 64 * (warp >> 2);
-        float acc[8][4];
-        warp_mma<false, false, 8>(acc, Xs, SX, W1s, S1, m0, n0, 2 * NCF_D, lane);
+        constexpr int NT = NCF_H1 / WPM / 8;
+        const int m0 = 16 * (warp % MT), n0 = (NCF_H1 / WPM) * (warp / MT);
+        float acc[NT][4];
+        warp_mma<false, false, NT>(acc, Xs, SX, W1s, S1, m0, n0, 2 * NCF_D, lane);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < NT; ++j)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
@@ -260,13 +265,14 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     }
     __syncthreads();
 
-    // ---- z2 = h1 W2 + b2 (64 x 64, K = 128)
+    // ---- z2 = h1 W2 + b2 (TT x 64, K = 128)
     {
-        const int m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
-        float acc[4][4];
-        warp_mma<false, false, 4>(acc, H1s, S1, W2s, S2, m0, n0, NCF_H1, lane);
+        constexpr int NT = NCF_H2 / WPM / 8;
+        const int m0 = 16 * (warp % MT), n0 = (NCF_H2 / WPM) * (warp / MT);
+        float acc[NT][4];
+        warp_mma<false, false, NT>(acc, H1s, S1, W2s, S2, m0, n0, NCF_H1, lane);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < NT; ++j)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
@@ -277,13 +283,13 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     }
     __syncthreads();
 
-    // ---- head: warp w takes rows 8w .. 8w + 7, lane l hidden columns 2l, 2l + 1
+    // ---- head: warp w takes rows (TT/8) w .. + TT/8 - 1, lane l hidden columns 2l, 2l + 1
     {
         const float scale = beff > 0 ? 2.f / (float)beff : 0.f;
         const float w0 = a.w3[2 * lane], w1 = a.w3[2 * lane + 1], b3 = a.b3[0];
         float gb2_0 = 0.f, gb2_1 = 0.f, gw3_0 = 0.f, gw3_1 = 0.f, gb3 = 0.f, sse = 0.f;
-        for (int u = 0; u < 8; ++u) {
-            const int r = 8 * warp + u;
+        for (int u = 0; u < TT / 8; ++u) {
+            const int r = (TT / 8) * warp + u;
             const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162 *>(H2s + r * S2 + 2 * lane);
             const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162 *>(Z2s + r * S2 + 2 * lane);
             const float h0 = __low2float(hh), h1 = __high2float(hh);
@@ -320,13 +326,14 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
         else a.lpart[blockIdx.x] = v;
     }
 
-    // ---- dz1 = (dz2 W2^T) SELU'(z1) (64 x 128, K = 64), and dW2 = h1^T dz2 (128 x 64, K = 64)
+    // ---- dz1 = (dz2 W2^T) SELU'(z1) (TT x 128, K = 64), and dW2 = h1^T dz2 (128 x 64, K = TT)
     {
-        const int m0 = 16 * (warp & 3), n0 = 64 * (warp >> 2);
-        float acc[8][4];
-        warp_mma<false, true, 8>(acc, D2s, S2, W2s, S2, m0, n0, NCF_H2, lane);
+        constexpr int NT = NCF_H1 / WPM / 8;
+        const int m0 = 16 * (warp % MT), n0 = (NCF_H1 / WPM) * (warp / MT);
+        float acc[NT][4];
+        warp_mma<false, true, NT>(acc, D2s, S2, W2s, S2, m0, n0, NCF_H2, lane);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < NT; ++j) {
             float cs0 = 0.f, cs1 = 0.f;   // this lane's two columns over its two rows
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -344,15 +351,15 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
                 cs1 += __shfl_xor_sync(FULL, cs1, o);
             }
             if (gid == 0) {
-                colp[(warp & 3) * NCF_H1 + n0 + 8 * j + 2 * t4] = cs0;
-                colp[(warp & 3) * NCF_H1 + n0 + 8 * j + 2 * t4 + 1] = cs1;
+                colp[(warp % MT) * NCF_H1 + n0 + 8 * j + 2 * t4] = cs0;
+                colp[(warp % MT) * NCF_H1 + n0 + 8 * j + 2 * t4 + 1] = cs1;
             }
         }
     }
     {
         const int m0 = 16 * warp;
         float acc[8][4];
-        warp_mma<true, false, 8>(acc, H1s, S1, D2s, S2, m0, 0, TB, lane);
+        warp_mma<true, false, 8>(acc, H1s, S1, D2s, S2, m0, 0, TT, lane);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
 #pragma unroll
@@ -364,11 +371,11 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
     }
     __syncthreads();
 
-    // ---- dW1 = x^T dz1 (64 x 128, K = 64), db1 = column sums of dz1
+    // ---- dW1 = x^T dz1 (64 x 128, K = TT), db1 = column sums of dz1
     {
         const int m0 = 16 * (warp & 3), n0 = 64 * (warp >> 2);
         float acc[8][4];
-        warp_mma<true, false, 8>(acc, Xs, SX, D1s, S1, m0, n0, TB, lane);
+        warp_mma<true, false, 8>(acc, Xs, SX, D1s, S1, m0, n0, TT, lane);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
 #pragma unroll
@@ -378,16 +385,20 @@ __global__ void __launch_bounds__(NTH, 1) k_ncf_train_tile(NcfTrainArgs a) {
                     make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
             }
     }
-    if (tid < NCF_H1)   // the four 16-row slabs in order
-        part[NCF_OFF_B1 + tid] = ((colp[tid] + colp[NCF_H1 + tid]) + colp[2 * NCF_H1 + tid]) +
-                                 colp[3 * NCF_H1 + tid];
-    // ---- dx = dz1 W1^T (64 x 64, K = 128) into the embedding gradients
-    if (a.gE) {
-        const int m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
-        float acc[4][4];
-        warp_mma<false, true, 4>(acc, D1s, S1, W1s, S1, m0, n0, NCF_H1, lane);
+    if (tid < NCF_H1) {   // the 16-row slabs in order
+        float v = colp[tid];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int t = 1; t < MT; ++t) v += colp[t * NCF_H1 + tid];
+        part[NCF_OFF_B1 + tid] = v;
+    }
+    // ---- dx = dz1 W1^T (TT x 64, K = 128) into the embedding gradients
+    if (a.gE) {
+        constexpr int NT = 2 * NCF_D / WPM / 8;
+        const int m0 = 16 * (warp % MT), n0 = (2 * NCF_D / WPM) * (warp / MT);
+        float acc[NT][4];
+        warp_mma<false, true, NT>(acc, D1s, S1, W1s, S1, m0, n0, NCF_H1, lane);
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int r = m0 + gid + 8 * (e >> 1), c = n0 + 8 * j + 2 * t4 + (e & 1);
@@ -567,8 +578,8 @@ cudaError_t prepare_ncf_train() {
 }
 
 cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, cudaStream_t st) {
-    if (t.B % TB || t.B <= 0) return cudaErrorInvalidValue;
-    k_ncf_train_tile<<<t.B / TB, NTH, TRAIN_SMEM, st>>>(t);
+    if (t.B % TT || t.B <= 0 || u.parts != t.B / TT) return cudaErrorInvalidValue;
+    k_ncf_train_tile<<<t.B / TT, NTH, TRAIN_SMEM, st>>>(t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int64_t blocks = (u.net_pad + u.n_emb + 255) / 256;
