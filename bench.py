@@ -135,6 +135,42 @@ def clocks_path(name):
     return os.path.join(os.environ.get("OPEN_CF_CLOCKS_DIR", tempfile.gettempdir()), name)
 
 
+def measure_e2e(steps, stream, host_in, dev_in, run, flush=None):
+    """End to end through the public API: every step copies the pinned host
+    inputs `host_in` into `dev_in`, calls run() (returns the step's device
+    outputs) and reads the outputs back into pinned host buffers, all inside
+    the CUDA-event-timed region.  Returns (seconds per step, H2D bytes, D2H bytes)."""
+    import torch
+    for h_, d_ in zip(host_in, dev_in):
+        d_.copy_(h_, non_blocking=True)
+    outs = run()
+    outs_host = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    for oh, o in zip(outs_host, outs):
+        oh.copy_(o, non_blocking=True)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()
+        ev[i][0].record(stream)
+        for h_, d_ in zip(host_in, dev_in):
+            d_.copy_(h_, non_blocking=True)
+        outs = run()
+        for oh, o in zip(outs_host, outs):
+            oh.copy_(o, non_blocking=True)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ev) / steps / 1e3
+    nbytes = lambda ts: int(sum(x.numel() * x.element_size() for x in ts))
+    return t, nbytes(host_in), nbytes(outs_host)
+
+
+def pinned(*arrays):
+    import torch
+    return [torch.as_tensor(np.ascontiguousarray(a)).pin_memory() for a in arrays]
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -441,10 +477,22 @@ def run_gpu_large(args):
     t_fold = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps / 1e3
     t_pred = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps / 1e3
     step_s = t_fold + t_pred
+    # end to end: this rank's CSR shard from pinned host memory, the choice back
+    U_keep = U.clone()
+    d_in = [torch.empty_like(x) for x in (s_ptr, s_col, s_val)]
+
+    def e2e_run():
+        Ue, _ = h.complete_rows(d_in[0], d_in[1], d_in[2])
+        _, b_, s_ = h.predict(Ue, gamma=GAMMA, want_T=False)
+        return [b_, s_]
+
+    t_e2e, h2d, d2h = measure_e2e(args.steps, stream,
+                                  pinned(s_ptr.cpu(), s_col.cpu(), s_val.cpu()), d_in, e2e_run)
+    U = U_keep
     if ws > 1:
-        t = torch.tensor([t_fold, t_pred, step_s], dtype=torch.float64, device=dev)
+        t = torch.tensor([t_fold, t_pred, step_s, t_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_fold, t_pred, step_s = (float(x) for x in t.tolist())
+        t_fold, t_pred, step_s, t_e2e = (float(x) for x in t.tolist())
         if rank != 0:
             return 0
     # error against the FP64 oracle on a 10k-row sample (same V, same observations)
@@ -502,6 +550,8 @@ def run_gpu_large(args):
         "cpu_baseline": {"value": len(rows) / t_orc, "unit": "row-solves/s",
                          "cores": orc.num_threads(), "kind": "oracle",
                          "sample": "FP64 fold-in of the 10k sampled rows"},
+        "e2e": {"value": prob.m / t_e2e, "unit": "row-solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "per_rank": "h2d/d2h bytes of rank 0's shard"},
         "clocks": clocks.summary(0),
     }
     print(json.dumps(line), flush=True)
@@ -553,7 +603,18 @@ def run_gpu_small(args):
     t_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps / 1e3
     units = jp.sweeps * (m + n)
     Ug = U.cpu().numpy()
-    Vg = h.get_V().cpu().numpy()
+    Vg_fit = h.get_V().cpu().numpy()
+    d_in = [torch.empty_like(x) for x in (rp, col, val, V0)]
+
+    def e2e_run():
+        h.set_V(d_in[3])
+        Ue = h.fit_csr(d_in[0], d_in[1], d_in[2], n)
+        _, b_, s_ = h.predict(Ue[m_off:].contiguous(), gamma=GAMMA, want_T=False)
+        return [b_, s_]
+
+    t_e2e, h2d, d2h = measure_e2e(args.steps, stream,
+                                  pinned(jp.row_ptr, jp.col, jp.val, jp.V0), d_in, e2e_run)
+    Vg = Vg_fit
     import oracle as orc
     orc.build()
     t0 = time.perf_counter()
@@ -585,6 +646,8 @@ def run_gpu_small(args):
                          "cores": orc.num_threads(), "kind": "oracle",
                          "sample": "the whole workload: FP64 joint fit + Algorithm 2 on the "
                                    "16 new rows"},
+        "e2e": {"value": units / t_e2e, "unit": "row-solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -620,6 +683,9 @@ def run_gpu_phase(args):
     torch.cuda.synchronize()
     t = sum(a_.elapsed_time(b_) for a_, b_ in ev) / args.steps / 1e3
     f = first.cpu().numpy()
+    d_in = [torch.empty_like(Pd)]
+    t_e2e, h2d, d2h = measure_e2e(args.steps, stream, pinned(P), d_in,
+                                  lambda: [ocf.phase_detect(d_in[0])])
     # algorithmic bytes: every reading up to the report (or the whole trace), and the outputs
     read = np.where(f >= 0, f + 1, L)
     bytes_alg = float(np.sum(read) * 4 + 8 * n)
@@ -649,6 +715,8 @@ def run_gpu_phase(args):
         "cpu_baseline": {"value": len(samp) / t_orc, "unit": "traces/s",
                          "cores": 1, "kind": "oracle",
                          "sample": f"{len(samp)} traces, the oracle's sequential loop"},
+        "e2e": {"value": n / t_e2e, "unit": "traces/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -701,6 +769,19 @@ def run_gpu_batched(args):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     t_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps / 1e3
+    U = U.clone()
+    # end to end: the concatenated problems from pinned host memory, factors back
+    d_in = [torch.empty_like(x) for x in (rp, col, val, V0)]
+    Ve = torch.empty_like(V0)
+
+    def e2e_run():
+        Ve.copy_(d_in[3])
+        Ue = h.batched_fit(c["m"], c["n"], c["k"], nnz_p, d_in[0], d_in[1], d_in[2], Ve)
+        return [Ue, Ve]
+
+    t_e2e, h2d, d2h = measure_e2e(args.steps, stream,
+                                  pinned(c["row_ptr"], c["col"], c["val"].astype(np.float32),
+                                         c["V0"].astype(np.float32)), d_in, e2e_run, flush)
     # plain GPU ALS: the same fits issued problem by problem (sample of problems)
     sample = list(range(0, len(bp), max(1, len(bp) // 200)))
     hs = {}
@@ -786,6 +867,8 @@ def run_gpu_batched(args):
         "cpu_baseline": {"value": orc_units / t_orc, "unit": "row-solves/s",
                          "cores": orc.num_threads(), "kind": "oracle",
                          "sample": f"FP64 ALS fits of {len(osamp)} sampled problems"},
+        "e2e": {"value": units / t_e2e, "unit": "row-solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
         "clocks": clocks.summary(0),
     }
     print(json.dumps(line), flush=True)
@@ -911,6 +994,13 @@ def run_gpu_learned(args):
         t_learned, (U, st) = timed(learned, args.steps)
         t_mlp, (Um, _) = timed(mlp_only, args.steps)
         t_plain, (Uf, stf) = timed(plain, args.steps)
+    U, st = U.clone(), st.clone()
+    # end to end: the new apps' observations from pinned host memory, factors
+    # and per-row status back
+    d_in = [torch.empty_like(x) for x in (row_ptr, col, val)]
+    t_e2e, h2d, d2h = measure_e2e(args.steps, stream,
+                                  pinned(row_ptr.cpu(), col.cpu(), val.cpu()), d_in,
+                                  lambda: list(h.mlp_infer(d_in[0], d_in[1], d_in[2])))
     E = clean_eval.shape[0]
 
     def rmse(Ux):
@@ -984,6 +1074,8 @@ def run_gpu_learned(args):
                          "cores": orc.num_threads(), "kind": "oracle",
                          "sample": "FP64 features + MLP forward + residual + fold-in of the "
                                    "fallback rows, 10k sampled new apps"},
+        "e2e": {"value": M / t_e2e, "unit": "rows/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
         "clocks": clocks.summary(0),
     }
     print(json.dumps(line), flush=True)

@@ -18,7 +18,7 @@
  *
  * Precision.  Parameters, gradients and Adam moments are FP32.  Products run
  * on tensor cores with FP32 accumulation: training on BF16 operands (mma.sync,
- * forward and backward of 64 batch rows per CTA in one kernel); completion on
+ * forward and backward of 32 batch rows per CTA in one kernel); completion on
  * FP16 operands (tcgen05, TMEM accumulators), its hidden activations formed in
  * packed FP16 pairs.  The first layer of the completion is evaluated in FP32
  * as Ea_i W1[0:32] + b1 plus Es_j W1[32:64] (the same value as the
