@@ -25,6 +25,7 @@
 // A step reads its batch position from a device-side counter, so one CUDA
 // graph of the two kernels serves every step of a training run.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -54,6 +55,14 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                              uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 __device__ __forceinline__ void ld_x4(uint32_t (&r)[4], const bf16 *p) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(p);
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -68,8 +77,9 @@ __device__ __forceinline__ void ld_x4_t(uint32_t (&r)[4], const bf16 *p) {
 // Warp tile of a shared-memory product: acc[j] += op(A)[m0 .. m0 + 16, :] op(B)[:, n0 + 8 j ..]
 // over K.  A is [M][K] (row stride lda), or [K][M] when AT; B is [K][N], or
 // [N][K] when BT.  acc[j][e]: row m0 + lane / 4 + 8 (e / 2), column
-// n0 + 8 j + 2 (lane % 4) + e % 2.
-template <bool AT, bool BT, int NT>
+// n0 + 8 j + 2 (lane % 4) + e % 2.  F16: the tiles hold FP16, not BF16, values
+// (same 16-bit layout; only the MMA's operand type differs).
+template <bool AT, bool BT, int NT, bool F16 = false>
 __device__ __forceinline__ void warp_mma(float (&acc)[NT][4], const bf16 *A, int lda,
                                          const bf16 *B, int ldb, int m0, int n0, int K,
                                          int lane) {
@@ -88,8 +98,13 @@ __device__ __forceinline__ void warp_mma(float (&acc)[NT][4], const bf16 *A, int
             uint32_t t[4];
             if (!BT) ld_x4_t(t, B + (k0 + (mi & 1) * 8 + rr) * ldb + nb + (mi >> 1) * 8);
             else ld_x4(t, B + (nb + (mi >> 1) * 8 + rr) * ldb + k0 + (mi & 1) * 8);
-            mma_bf16_16816(acc[j], af, t[0], t[1]);
-            mma_bf16_16816(acc[j + 1], af, t[2], t[3]);
+            if constexpr (F16) {
+                mma_f16_16816(acc[j], af, t[0], t[1]);
+                mma_f16_16816(acc[j + 1], af, t[2], t[3]);
+            } else {
+                mma_bf16_16816(acc[j], af, t[0], t[1]);
+                mma_bf16_16816(acc[j + 1], af, t[2], t[3]);
+            }
         }
     }
 }
@@ -483,18 +498,39 @@ __global__ void k_ncf_refresh_bf(const float *__restrict__ th, bf16 *__restrict_
 // predictor): a persistent kernel that loads W1 (only the K1 = nfeat rounded
 // up to 16 rows that meet non-zero inputs) and W2 once per CTA and walks
 // 64-row tiles: gather -> z1 (K = K1) -> SELU -> z2 -> SELU -> y, the output
-// dot product folded into the second layer's epilogue.
-constexpr uint32_t P_OFF_W1 = 0;                                  // W1 [64][S1] (K1 rows used)
-constexpr uint32_t P_OFF_W2 = P_OFF_W1 + 2 * NCF_D * S1 * 2;      // W2 [128][S2]
-constexpr uint32_t P_OFF_X = P_OFF_W2 + NCF_H1 * S2 * 2;          // x  [64][SX]
-constexpr uint32_t P_OFF_H1 = P_OFF_X + TB * SX * 2;              // h1 [64][S1]
+// dot product folded into the second layer's epilogue.  The first layer runs
+// on BF16 operands like training; the hidden activations are formed in packed
+// FP16 pairs (a branch-free SELU on two values per instruction: lambda
+// max(z, 0) + lambda alpha (2^(log2(e) min(z, 0)) - 1)) and the second layer
+// multiplies them, on FP16 operands, with W2 converted from its BF16 copy
+// (exact for |w| >= 2^-14; FP16 keeps three more mantissa bits than BF16 for
+// the activations).  Biases and output weights sit in registers.
+constexpr uint32_t P_OFF_W1 = 0;                                  // W1 [64][S1] BF16 (K1 rows used)
+constexpr uint32_t P_OFF_W2 = P_OFF_W1 + 2 * NCF_D * S1 * 2;      // W2 [128][S2] FP16
+constexpr uint32_t P_OFF_X = P_OFF_W2 + NCF_H1 * S2 * 2;          // x  [64][SX] BF16
+constexpr uint32_t P_OFF_H1 = P_OFF_X + TB * SX * 2;              // h1 [64][S1] FP16
 constexpr uint32_t P_OFF_Y = P_OFF_H1 + TB * S1 * 2;              // [2][64] partial y
 constexpr uint32_t PRED_SMEM = P_OFF_Y + 2 * TB * 4;
 
-__global__ void __launch_bounds__(NTH) k_pred_forward(NcfTrainArgs a) {
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
+__device__ __forceinline__ __half2 bits_h2(uint32_t u) { return *reinterpret_cast<__half2 *>(&u); }
+
+__device__ __forceinline__ __half2 selu_h2(__half2 z) {
+    const __half2 zero = __float2half2_rn(0.f);
+    const __half2 t = __hmul2(__hmin2(z, zero), __float2half2_rn(1.4426950408889634f));
+    uint32_t e;
+    asm("ex2.approx.f16x2 %0, %1;" : "=r"(e) : "r"(h2_bits(t)));
+    const __half2 la = __float2half2_rn(SELU_L * SELU_A);
+    const __half2 neg = __hfma2(bits_h2(e), la, __hneg2(la));
+    return __hfma2(__hmax2(z, zero), __float2half2_rn(SELU_L), neg);
+}
+
+__global__ void __launch_bounds__(NTH, 3) k_pred_forward(NcfTrainArgs a) {
     extern __shared__ __align__(16) unsigned char sm[];
-    bf16 *W1s = reinterpret_cast<bf16 *>(sm + P_OFF_W1), *W2s = reinterpret_cast<bf16 *>(sm + P_OFF_W2);
-    bf16 *Xs = reinterpret_cast<bf16 *>(sm + P_OFF_X), *H1s = reinterpret_cast<bf16 *>(sm + P_OFF_H1);
+    bf16 *W1s = reinterpret_cast<bf16 *>(sm + P_OFF_W1);
+    __half *W2s = reinterpret_cast<__half *>(sm + P_OFF_W2);
+    bf16 *Xs = reinterpret_cast<bf16 *>(sm + P_OFF_X);
+    __half *H1s = reinterpret_cast<__half *>(sm + P_OFF_H1);
     float *yp = reinterpret_cast<float *>(sm + P_OFF_Y);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gid = lane >> 2, t4 = lane & 3;
@@ -508,8 +544,32 @@ __global__ void __launch_bounds__(NTH) k_pred_forward(NcfTrainArgs a) {
     }
     for (int v = tid; v < NCF_H1 * (NCF_H2 / 8); v += NTH) {
         const int r = v / (NCF_H2 / 8), c8 = (v % (NCF_H2 / 8)) * 8;
-        *reinterpret_cast<uint4 *>(W2s + r * S2 + c8) =
-            __ldg(reinterpret_cast<const uint4 *>(W2g + r * NCF_H2 + c8));
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(W2g + r * NCF_H2 + c8));
+        const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+        uint32_t hv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&wv[q]));
+            hv[q] = h2_bits(__floats2half2_rn(f.x, f.y));
+        }
+        *reinterpret_cast<uint4 *>(W2s + r * S2 + c8) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    }
+    // this thread's columns of both epilogues: layer 1 n0 + 8 j + 2 t4 (+1),
+    // layer 2 likewise with its own n0
+    const int m0 = 16 * (warp & 3), n1 = 64 * (warp >> 2), n2 = 32 * (warp >> 2);
+    __half2 b1h[8], b2h[4];
+    float w3v[4][2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = n1 + 8 * j + 2 * t4;
+        b1h[j] = __floats2half2_rn(a.b1[c], a.b1[c + 1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = n2 + 8 * j + 2 * t4;
+        b2h[j] = __floats2half2_rn(a.b2[c], a.b2[c + 1]);
+        w3v[j][0] = a.w3[c];
+        w3v[j][1] = a.w3[c + 1];
     }
     const float b3 = a.b3[0];
     const int64_t tiles = (a.nnz + TB - 1) / TB;
@@ -528,31 +588,35 @@ __global__ void __launch_bounds__(NTH) k_pred_forward(NcfTrainArgs a) {
             for (int t = 0; t < 8; t += 2) st_pair(Xs + rr * SX + 8 * q + t, x[t], x[t + 1]);
         }
         __syncthreads();
-        {   // h1 = SELU(x W1 + b1)
-            const int m0 = 16 * (warp & 3), n0 = 64 * (warp >> 2);
+        {   // h1 = SELU(x W1 + b1), FP16 pairs
             float acc[8][4];
-            warp_mma<false, false, 8>(acc, Xs, SX, W1s, S1, m0, n0, K1, lane);
+            warp_mma<false, false, 8>(acc, Xs, SX, W1s, S1, m0, n1, K1, lane);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int r = m0 + gid + 8 * h, c = n0 + 8 * j + 2 * t4;
-                    st_pair(H1s + r * S1 + c, selu_t(acc[j][2 * h] + a.b1[c]),
-                            selu_t(acc[j][2 * h + 1] + a.b1[c + 1]));
+                    const int r = m0 + gid + 8 * h, c = n1 + 8 * j + 2 * t4;
+                    const __half2 z =
+                        __hadd2(__floats2half2_rn(acc[j][2 * h], acc[j][2 * h + 1]), b1h[j]);
+                    *reinterpret_cast<__half2 *>(H1s + r * S1 + c) = selu_h2(z);
                 }
         }
         __syncthreads();
         {   // z2 = h1 W2 + b2; this warp's share of y = SELU(z2) . w3
-            const int m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
             float acc[4][4];
-            warp_mma<false, false, 4>(acc, H1s, S1, W2s, S2, m0, n0, NCF_H1, lane);
+            warp_mma<false, false, 4, true>(acc, reinterpret_cast<const bf16 *>(H1s), S1,
+                                            reinterpret_cast<const bf16 *>(W2s), S2, m0, n2,
+                                            NCF_H1, lane);
             float p[2] = {0.f, 0.f};
 #pragma unroll
             for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int c = n0 + 8 * j + 2 * t4 + (e & 1);
-                    p[e >> 1] = fmaf(a.w3[c], selu_t(acc[j][e] + a.b2[c]), p[e >> 1]);
+                for (int h = 0; h < 2; ++h) {
+                    const __half2 z =
+                        __hadd2(__floats2half2_rn(acc[j][2 * h], acc[j][2 * h + 1]), b2h[j]);
+                    const float2 hv = __half22float2(selu_h2(z));
+                    p[h] = fmaf(w3v[j][0], hv.x, p[h]);
+                    p[h] = fmaf(w3v[j][1], hv.y, p[h]);
                 }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {   // the four lanes of a row hold its columns
@@ -591,7 +655,7 @@ cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, c
 cudaError_t launch_pred_forward(const NcfTrainArgs &t, int num_sms, cudaStream_t st) {
     if (!t.feat || !t.y_out || t.nfeat < 1 || t.nfeat > 2 * NCF_D) return cudaErrorInvalidValue;
     if (t.nnz <= 0) return cudaSuccess;
-    const int64_t tiles = (t.nnz + TB - 1) / TB, cap = 4 * (int64_t)num_sms;
+    const int64_t tiles = (t.nnz + TB - 1) / TB, cap = 3 * (int64_t)num_sms;   // 3 CTAs per SM
     k_pred_forward<<<(unsigned)(tiles < cap ? tiles : cap), NTH, PRED_SMEM, st>>>(t);
     return cudaGetLastError();
 }
