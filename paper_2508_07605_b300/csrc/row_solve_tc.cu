@@ -23,6 +23,20 @@
 // partial Grams in a fixed order through shared memory, and warp 0 solves.
 // Staging: lane t loads observation t's factor row (16-byte loads) into a
 // padded tile (stride KP+8 floats: the fragment loads are conflict-free).
+//
+// FP64 factorisation at KP = 32 (packed): the B300's FP64 pipe spends the
+// same time on a warp instruction whatever the number of active lanes, so
+// the cost is the count of FP64 warp instructions, and lane-per-row spends
+// two thirds of its update FMAs on the upper triangle.  There a warp forms
+// two systems' Grams and factorises both at once, 16 lanes per system, lane i
+// holding rows i and 31 - i of the lower triangle in 33 slots (slot e <= i:
+// row i, column e; slot e > i: row 31 - i, column 32 - e), so column p of
+// either row sits in a slot that does not depend on the lane (p and 32 - p).
+// Step p then costs 31 - p FMA instructions for the two systems instead of
+// 31 - p for one.  The forward substitution rides along with the
+// factorisation (y_p is formed on the pivot step and broadcast with column
+// p); the operations and their order are those of the lane-per-row path, so
+// both give the same bits.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -105,8 +119,7 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 // rows) are dead once the warp's Gram is in registers, so the Gram / factor
 // area of the solve phase overlays them: a warp needs max(staging, solve),
 // not the sum, which keeps 16 warps per SM resident for KP = 32.
-template <int KP, typename TC, bool BF, int NST> struct alignas(16) TcSmem {
-    static constexpr int SPW = 32 / KP;
+template <int KP, typename TC, bool BF, int NST, int SPW> struct alignas(16) TcSmem {
     // Staged rows padded to KP+8 elements (conflict-free fragment loads,
     // 16-byte aligned rows).  FP32: one tile of 32 rows per buffer.  BF16: the
     // hi and lo halves of each split row go to two tiles of 32 BF16 rows.
@@ -121,7 +134,8 @@ template <int KP, typename TC, bool BF, int NST> struct alignas(16) TcSmem {
             TC L[KP][KP + 1];      // the Cholesky factor of the same system
         };
         float b[KP];
-        TC col[2][KP];
+        TC col[2][KP + 4];   // column p of L (double-buffered); [KP]: y_p (packed path)
+        TC dinv[KP];         // inverse pivots (packed path)
     };
     union {
         Stage ld;
@@ -133,6 +147,14 @@ template <int KP, typename TC, bool BF, int NST> struct alignas(16) TcSmem {
 // stages do not shorten the U-half (its items wait on the tensor-core chain,
 // not on the copies) and cost occupancy, so every configuration uses 2.
 template <int KP, int WPS> constexpr int tc_stages() { return 2; }
+
+// The packed FP64 layout (two systems per warp) and systems per warp.
+template <int KP, typename TC, int WPS, bool SUMS> constexpr bool tc_pack() {
+    return KP == 32 && sizeof(TC) == 8 && WPS == 1 && !SUMS;
+}
+template <int KP, typename TC, int WPS, bool SUMS> constexpr int tc_spw() {
+    return WPS == 1 ? (tc_pack<KP, TC, WPS, SUMS>() ? 2 : 32 / KP) : 1;
+}
 
 template <int KP> struct Blocks {
     static constexpr int MB = KP / 16;
@@ -148,11 +170,12 @@ template <int KP, typename TC, int WPS, bool BF, bool SUMS = false>
 __global__ void __launch_bounds__(WPS == 1 ? (sizeof(TC) == 8 && KP == 32 ? 128 : 256) : 32 * WPS)
 k_row_solve_tc(SolveArgs<float> a) {
     constexpr int WARPS = (WPS == 1) ? ((sizeof(TC) == 8 && KP == 32) ? 4 : 8) : WPS;
-    constexpr int SPW = (WPS == 1) ? 32 / KP : 1;   // systems per warp
+    constexpr bool PACK = tc_pack<KP, TC, WPS, SUMS>();
+    constexpr int SPW = tc_spw<KP, TC, WPS, SUMS>();   // systems per warp
     constexpr int MB = Blocks<KP>::MB;
     constexpr int NBLK = Blocks<KP>::NBLK;
     constexpr int NST = tc_stages<KP, WPS>();
-    using WS = TcSmem<KP, TC, BF, NST>;
+    using WS = TcSmem<KP, TC, BF, NST, SPW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WS *smem = reinterpret_cast<WS *>(smem_raw);
 
@@ -434,6 +457,115 @@ k_row_solve_tc(SolveArgs<float> a) {
             __syncwarp();
         }
 
+        if constexpr (PACK) {
+            // ------------- solve phase, packed: 16 lanes per system ------------
+            const int sp = lane >> 4;   // system of this half-warp
+            const int i = lane & 15;    // its rows i and 31 - i
+            const int r2 = 31 - i;
+            auto &S = W.seg[sp];
+            bool bad = false;
+            int64_t s = 0;
+#pragma unroll
+            for (int si = 0; si < SPW; ++si)
+                if (si == sp) {
+                    bad = bad_s[si];
+                    s = s_s[si];
+                }
+            const double lam = double(a.lambda) * (a.wr ? double(s) : 1.0);   // weighted: lambda s_i
+            const double d1 = double(S.G[i][i]) + lam, d2 = double(S.G[r2][r2]) + lam;
+            double A[33];
+#pragma unroll
+            for (int e = 0; e < 33; ++e) {
+                const bool first = e <= i;
+                const double g = double(S.G[first ? i : r2][first ? e : 32 - e]);
+                A[e] = (e == i) ? d1 : (e == i + 1) ? d2 : g;   // the two diagonals
+            }
+            double y1 = double(S.b[i]), y2 = double(S.b[r2]);
+            __syncwarp();   // every lane has read G before L overwrites it
+#pragma unroll
+            for (int p = 0; p < 32; ++p) {
+                // pivot: row p, on lane p (first row) or lane 31 - p (second row)
+                const double piv = __shfl_sync(FULL, p <= 15 ? A[p] : A[32 - p], p <= 15 ? p : 31 - p, 16);
+                const double inv = rsq(piv);
+                const bool on1 = p <= 15 && i >= p;   // row i reaches column p
+                const bool on2 = i <= 31 - p;         // row 31 - i reaches column p
+                if (on1) A[p] = A[p] * inv;
+                if (on2) A[32 - p] = A[32 - p] * inv;
+                double *cb = S.col[p & 1];
+                if (on1) cb[i] = A[p];
+                if (on2) cb[r2] = A[32 - p];
+                if (p <= 15) {
+                    if (i == p) { y1 = y1 * inv; cb[32] = y1; }
+                } else {
+                    if (i == 31 - p) { y2 = y2 * inv; cb[32] = y2; }
+                }
+                if (i == 0) S.dinv[p] = inv;
+                __syncwarp();
+                const double f1 = p <= 15 ? A[p] : 0.0, f2 = A[32 - p];
+                const double yp = cb[32];
+                if (p <= 15 && i > p) y1 = fma(-f1, yp, y1);
+                if (r2 > p) y2 = fma(-f2, yp, y2);
+#pragma unroll
+                for (int e = 1; e < 33; ++e) {
+                    const bool up1 = e > p;        // first-row slot e: column e
+                    const bool up2 = e < 32 - p;   // second-row slot e: column 32 - e
+                    if (up1 && up2) {
+                        const bool first = e <= i;
+                        A[e] = fma(-(first ? f1 : f2), cb[first ? e : 32 - e], A[e]);
+                    } else if (up2) {
+                        if (e > i) A[e] = fma(-f2, cb[32 - e], A[e]);
+                    } else if (up1) {
+                        if (e <= i) A[e] = fma(-f1, cb[e], A[e]);
+                    }
+                }
+            }
+            // L to shared memory (row-major) for the back substitution
+#pragma unroll
+            for (int e = 0; e < 33; ++e) {
+                const bool first = e <= i;
+                S.L[first ? i : r2][first ? e : 32 - e] = A[e];
+            }
+            __syncwarp();
+            // back substitution L^T x = y
+            double x1 = y1, x2 = y2;
+#pragma unroll
+            for (int p = 31; p >= 0; --p) {
+                const double xp = __shfl_sync(FULL, p <= 15 ? x1 : x2, p <= 15 ? p : 31 - p, 16) *
+                                  S.dinv[p];
+                if (i < p) x1 = fma(-S.L[p][i], xp, x1);
+                if (r2 < p) x2 = fma(-S.L[p][r2], xp, x2);
+            }
+            x1 = x1 * S.dinv[i];
+            x2 = x2 * S.dinv[r2];
+            bool fail = !isfinite(x1) || !isfinite(x2);
+#pragma unroll
+            for (int off = 1; off < 16; off <<= 1)
+                fail |= __shfl_xor_sync(FULL, (int)fail, off) != 0;
+            const int64_t is = base + sp;
+            if (is < M) {
+                const int64_t io = a.row_map ? a.row_map[is] : is;
+                int32_t st = ST_OK;
+                if (bad) st = ST_BAD;
+                else if (s == 0) st = ST_EMPTY;
+                else if (fail) st = ST_NOT_SPD;
+                if (st != ST_OK) x1 = x2 = 0.0;
+                if (i < a.kout) a.out[io * a.ldo + i] = (float)x1;
+                if (r2 < a.kout) a.out[io * a.ldo + r2] = (float)x2;
+                if (a.outb) {   // split BF16 copy [hi | lo] of the output row
+                    __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.outb) + io * 2 * KP;
+                    const float xf1 = (float)x1, xf2 = (float)x2;
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(xf1), h2 = __float2bfloat16_rn(xf2);
+                    ob[i] = h1;
+                    ob[KP + i] = __float2bfloat16_rn(xf1 - __bfloat162float(h1));
+                    ob[r2] = h2;
+                    ob[KP + r2] = __float2bfloat16_rn(xf2 - __bfloat162float(h2));
+                }
+                if (a.status && i == 0) a.status[io] = st;
+            }
+            __syncwarp();
+            continue;
+        }
+
         // ---------------- solve phase: one KP-lane segment per system --------
         const int slot = (WPS == 1) ? g : 0;
         bool bad = false;
@@ -566,19 +698,19 @@ k_row_solve_tc(SolveArgs<float> a) {
     }
 }
 
-template <int KP, typename TC, int WPS, bool BF> static size_t tc_smem_bytes() {
+template <int KP, typename TC, int WPS, bool BF, bool SUMS> static size_t tc_smem_bytes() {
     constexpr int WARPS = (WPS == 1) ? ((sizeof(TC) == 8 && KP == 32) ? 4 : 8) : WPS;
-    return sizeof(TcSmem<KP, TC, BF, tc_stages<KP, WPS>()>) * WARPS;
+    return sizeof(TcSmem<KP, TC, BF, tc_stages<KP, WPS>(), tc_spw<KP, TC, WPS, SUMS>()>) * WARPS;
 }
 
 template <int KP, typename TC, int WPS, bool BF> static cudaError_t tc_attr() {
     cudaError_t e = cudaFuncSetAttribute(k_row_solve_tc<KP, TC, WPS, BF, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem_bytes<KP, TC, WPS, BF>());
+                                         (int)tc_smem_bytes<KP, TC, WPS, BF, false>());
     if (e != cudaSuccess || BF) return e;
     return cudaFuncSetAttribute(k_row_solve_tc<KP, TC, WPS, false, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tc_smem_bytes<KP, TC, WPS, BF>());
+                                (int)tc_smem_bytes<KP, TC, WPS, BF, true>());
 }
 
 template <bool BF> static cudaError_t tc_attrs() {
@@ -623,14 +755,14 @@ static cudaError_t launch_tc_kp(const SolveArgs<float> &a, cudaStream_t st) {
         int64_t blocks = a.m;
         if (blocks > NUM_SMS_HINT * 64) blocks = NUM_SMS_HINT * 64;
         return launch_pdl(k_row_solve_tc<KP, TC, 4, BF, SUMS>, (unsigned)blocks, 128,
-                          tc_smem_bytes<KP, TC, 4, BF>(), st, a);
+                          tc_smem_bytes<KP, TC, 4, BF, SUMS>(), st, a);
     }
     constexpr int WARPS = (sizeof(TC) == 8 && KP == 32) ? 4 : 8;
-    const int64_t per = (int64_t)WARPS * (32 / KP);
+    const int64_t per = (int64_t)WARPS * tc_spw<KP, TC, 1, SUMS>();
     int64_t blocks = (a.m + per - 1) / per;
     if (blocks > NUM_SMS_HINT * 32) blocks = NUM_SMS_HINT * 32;
     return launch_pdl(k_row_solve_tc<KP, TC, 1, BF, SUMS>, (unsigned)blocks, WARPS * 32,
-                      tc_smem_bytes<KP, TC, 1, BF>(), st, a);
+                      tc_smem_bytes<KP, TC, 1, BF, SUMS>(), st, a);
 }
 
 template <bool BF, bool SUMS>

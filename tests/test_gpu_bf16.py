@@ -27,7 +27,8 @@ def _pred_err(U_gpu, U_ref, V):
     return np.linalg.norm(Tg - Tr, axis=1) / np.maximum(np.linalg.norm(Tr, axis=1), 1e-30)
 
 
-@pytest.mark.parametrize("k,chol64", [(32, True), (32, False), (16, False), (8, True)])
+@pytest.mark.parametrize("k,chol64", [(32, True), (32, False), (16, False), (8, True), (24, True),
+                                       (17, True)])
 def test_bf16_foldin_matches_oracle(orc, k, chol64):
     """Fold-in of new rows against a fixed V at the shape of the large
     workload (4096 settings, ~1 % observed), scaled down in rows."""

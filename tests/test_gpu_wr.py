@@ -40,6 +40,7 @@ def _ragged(rng, m, n, k):
 
 @pytest.mark.parametrize("precision,k,chol64", [("fp32", 3, False), ("fp32", 16, False),
                                                 ("fp32", 32, False), ("fp32", 16, True),
+                                                ("fp32", 32, True), ("fp32", 20, True),
                                                 ("fp64", 8, False), ("fp64", 32, False)])
 def test_wr_foldin_ragged(orc, precision, k, chol64):
     rng = np.random.default_rng(700 + k)
