@@ -717,7 +717,10 @@ def run_gpu_phase(args):
                              "equal": bool(np.array_equal(f[samp], fo))},
         "roofline": {"kernel": "k_phase_detect", "bound": "hbm",
                      "achieved": bytes_alg / t / 1e9, "peak": hbm, "unit": "GB/s",
-                     "frac": bytes_alg / t / 1e9 / hbm, "traffic": None,
+                     "frac": bytes_alg / t / 1e9 / hbm,
+                     "traffic": profiled_traffic_per_unit(
+                         os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "phase.cu"),
+                         os.path.join(ROOT, "profiles", "phase_detect_2e17x3000.md"), n),
                      "note": "algorithmic bytes: the readings up to each trace's report "
                              "(the whole trace when none) plus the outputs"},
         "cpu_baseline": {"value": len(samp) / t_orc, "unit": "traces/s",
