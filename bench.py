@@ -92,7 +92,18 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
+        # nvidia-smi's start-up (its NVML initialisation) stalls the GPU for a few
+        # milliseconds; wait for its second sample so that the stall falls before
+        # the timed region, not inside it (a short region would absorb it whole)
+        t_end = time.time() + 5.0
+        while self.proc is not None and time.time() < t_end:
+            try:
+                if len(open(self.path).read().strip().splitlines()) >= 3:   # header + 2 samples
+                    break
+            except OSError:
+                pass
+            time.sleep(0.05)
+        time.sleep(0.05)
         return self
 
     def __exit__(self, *a):
@@ -270,16 +281,17 @@ def run_gpu(args):
         _, best, sav = h.predict(U, gamma=GAMMA, want_T=False)
         return U, best, sav
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    # the clock sampler starts before the warm-up, so that its start-up (and the
+    # idle wait for its first samples) falls before the timed steps
     clocks = ClockSampler(clocks_path(f"clocks_bench_r{rank}.csv"))
     with clocks:
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         for i in range(args.steps):
             flush.zero_()
@@ -458,14 +470,14 @@ def run_gpu_large(args):
         _, best, sav = h.predict(U, gamma=GAMMA, want_T=False)
         return U, best
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     clocks = ClockSampler(clocks_path(f"clocks_bench_c5_r{rank}.csv"))
-    with clocks:
+    with clocks:   # started before the warm-up (its start-up stays out of the timed steps)
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         for i in range(args.steps):
             ev[i][0].record(stream)
@@ -763,15 +775,15 @@ def run_gpu_batched(args):
     W = h.batched_tune(c["m"], c["n"], c["k"], nnz_p, rp, col, val, Vs)
     t_tune = time.perf_counter() - t0
     V = V0.clone()
-    for _ in range(max(args.warmup, 3)):
-        V.copy_(V0)
-        h.batched_fit(c["m"], c["n"], c["k"], nnz_p, rp, col, val, V)
-    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     clocks = ClockSampler(clocks_path("clocks_bench_c3.csv"))
-    with clocks:
+    with clocks:   # started before the warm-up (its start-up stays out of the timed steps)
+        for _ in range(max(args.warmup, 3)):
+            V.copy_(V0)
+            h.batched_fit(c["m"], c["n"], c["k"], nnz_p, rp, col, val, V)
+        torch.cuda.synchronize()
         for i in range(args.steps):
             V.copy_(V0)
             flush.zero_()
@@ -1141,13 +1153,12 @@ def run_gpu_ncf(args):
         return h.predict(gamma=GAMMA, T=False)
 
     W = max(args.warmup, 3)
-    for e in range(W):
-        step(e)
-    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     clocks = ClockSampler(clocks_path("clocks_bench_ncf.csv"))
-    with clocks:
+    with clocks:   # started before the warm-up (its start-up stays out of the timed steps)
+        for e in range(W):
+            step(e)
         torch.cuda.synchronize()
         for i in range(args.steps):
             flush.zero_()
@@ -1337,18 +1348,18 @@ def run_gpu_stream(args):
     # is captured here, at least W steps in all), then the timed stream from the start
     U_buf = torch.empty(w.batch, off.k, dtype=f32, device=dev)   # outputs reused every step
     S_buf = torch.empty(w.batch, dtype=torch.int32, device=dev)
-    restart()
-    for b in range(max(W, steps)):
-        h.stream_ingest(*d_batches[b % nb], out=U_buf, status=S_buf)
-    torch.cuda.synchronize()
-    restart()
-    torch.cuda.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     clocks = ClockSampler(clocks_path("clocks_bench_stream.csv"))
     U_first = torch.empty_like(U_buf)
-    with clocks:
+    with clocks:   # started before the warm-up (its start-up stays out of the timed steps)
+        restart()
+        for b in range(max(W, steps)):
+            h.stream_ingest(*d_batches[b % nb], out=U_buf, status=S_buf)
+        torch.cuda.synchronize()
+        restart()
+        torch.cuda.synchronize()
         for i in range(steps):
             flush.zero_()
             ev[i][0].record(stream)
@@ -1485,14 +1496,14 @@ def run_gpu_online(args):
         return y, U, best, sav
 
     W = max(args.warmup, 3)
-    for _ in range(W):
-        step()
-    torch.cuda.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     clocks = ClockSampler(clocks_path("clocks_bench_online.csv"))
-    with clocks:
+    with clocks:   # started before the warm-up (its start-up stays out of the timed steps)
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
