@@ -63,8 +63,9 @@ cudaError_t prepare_row_solve_tc();
 
 // Batched ALS over independent problems (batched.cu).  Per-problem arrays are
 // indexed by problem id p; order[] lists problem ids in processing order;
-// classes are consecutive ranges of order[] with their own warps per problem.
-constexpr int BATCH_MAX_CLASSES = 4;
+// classes are consecutive ranges of order[] with their own warps per problem
+// (per padded rank, largest first: a "large" and a "small" class each).
+constexpr int BATCH_MAX_CLASSES = 6;
 constexpr int64_t BATCH_MAX_N = 1024;
 struct BatchArgs {
     int64_t P;

@@ -53,7 +53,9 @@ struct open_cf {
     Buf b_meta, b_Uw, b_Vw, b_cptr, b_cidx, b_cval, b_counter;
     std::vector<int64_t> b_key;       // host description of the planned batch
     int32_t b_W[2] = {8, 2};          // warps per problem: large class, small class
-    int32_t b_class_end[2] = {0, 0};
+    int32_t b_nclass = 0;             // classes of the planned batch
+    int32_t b_class_end[BATCH_MAX_CLASSES] = {};
+    int32_t b_class_W[BATCH_MAX_CLASSES] = {};
     int64_t b_Um = 0, b_Vn = 0;       // padded factor sizes (floats)
     // learned warm start: FP32 master parameters, Adam moments, BF16 weights, scratch
     Buf mlp_th, mlp_g, mlp_m1, mlp_m2, mlp_bf, mlp_map, mlp_t, mlp_cn, mlp_scr, mlp_G;
@@ -365,19 +367,38 @@ int batch_plan(open_cf_t *h, int64_t P, const int64_t *m, const int64_t *n, cons
     meta[L.o_fv + P] = fv;
     meta[L.o_tu + P] = tu;
     meta[L.o_tv + P] = tv;
+    // Order: padded rank first (32, 16, 8), then cost, largest first (LPT).
+    // Keeping one padded rank together keeps the warps of an SM in one unrolled
+    // solver at a time (mixing the three thrashed the instruction cache).  Per
+    // padded rank, class "large" holds the costliest problems that take about
+    // half of that rank's work, class "small" the rest.
     std::vector<int32_t> order(P);
     for (int64_t p = 0; p < P; ++p) order[p] = (int32_t)p;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        const int kx = padded_k(k[x]), ky = padded_k(k[y]);
+        if (kx != ky) return kx > ky;
+        return cost[x] > cost[y];
+    });
     for (int64_t p = 0; p < P; ++p) ord[p] = order[p];
-    // class 0: the costliest problems that together take ~half of the work
-    double total = 0.0;
-    for (double c : cost) total += c;
-    double acc = 0.0;
-    int32_t split = 0;
-    while (split < P && acc < 0.5 * total) acc += cost[order[split++]];
-    h->b_class_end[0] = split;
-    h->b_class_end[1] = (int32_t)P;
+    h->b_nclass = 0;
+    for (int64_t g0 = 0; g0 < P;) {
+        const int kp = padded_k(k[order[g0]]);
+        int64_t g1 = g0;
+        double total = 0.0;
+        while (g1 < P && padded_k(k[order[g1]]) == kp) total += cost[order[g1++]];
+        double acc = 0.0;
+        int64_t split = g0;
+        while (split < g1 && acc < 0.5 * total) acc += cost[order[split++]];
+        if (split > g0) {
+            h->b_class_end[h->b_nclass] = (int32_t)split;
+            h->b_class_W[h->b_nclass++] = h->b_W[0];
+        }
+        if (g1 > split) {
+            h->b_class_end[h->b_nclass] = (int32_t)g1;
+            h->b_class_W[h->b_nclass++] = h->b_W[1];
+        }
+        g0 = g1;
+    }
     h->b_Um = fu;
     h->b_Vn = fv;
     L.nnz = nnz;
@@ -425,11 +446,11 @@ BatchArgs batch_args(open_cf_t *h, const BatchPlan &L, const int64_t *row_ptr, c
     b.sweeps = sweeps;
     b.lambda = h->cfg.lambda;
     b.wr = h->cfg.weighted_lambda != 0;
-    b.n_classes = 2;
-    b.class_end[0] = h->b_class_end[0];
-    b.class_end[1] = h->b_class_end[1];
-    b.class_W[0] = h->b_W[0];
-    b.class_W[1] = h->b_W[1];
+    b.n_classes = h->b_nclass;
+    for (int c = 0; c < h->b_nclass; ++c) {
+        b.class_end[c] = h->b_class_end[c];
+        b.class_W[c] = h->b_class_W[c];
+    }
     return b;
 }
 
@@ -1179,8 +1200,11 @@ int open_cf_batched_fit(open_cf_t *h, int64_t P, const int64_t *m_host, const in
     const BatchArgs b = batch_args(h, L, row_ptr, col, val, h->cfg.sweeps);
     const int grid = batched_grid(h);
     std::vector<int64_t> key = {2, P, nnz, (int64_t)row_ptr, (int64_t)col, (int64_t)val,
-                                (int64_t)V_inout, (int64_t)U_out, h->b_W[0], h->b_W[1],
-                                h->b_class_end[0]};
+                                (int64_t)V_inout, (int64_t)U_out, h->b_nclass};
+    for (int c = 0; c < h->b_nclass; ++c) {   // the classes are baked into the graph
+        key.push_back(h->b_class_end[c]);
+        key.push_back(h->b_class_W[c]);
+    }
     return run_graph(h, key, S(stream), [&](cudaStream_t st) {
         return batch_enqueue(h, L, b, V_inout, U_out, grid, st);
     });
