@@ -113,3 +113,46 @@ def test_batched_rejects_bad_descriptions():
     with pytest.raises(ocf.OpenCFError) as e:
         h.batched_fit([1], [2], [2], [5], z64, z32, f, V)          # nnz_p > m*n
     assert e.value.code == ocf.INVALID_ARG
+
+
+def test_batched_full_size_sampled(orc):
+    """The batched workload at full size -- 10,000 problems, autotuned warps,
+    one persistent launch of 15 sweeps, as the benchmark runs it.  On sampled
+    problems (evenly spaced plus the costliest) the final V-half equals the
+    oracle's half-step from the GPU's final U, row by row, and the held-out
+    error meets the gate against the oracle's own 15-sweep fit."""
+    bp = synth.make_batched(seed=0, n_problems=10000, n_heldout=64)
+    c = bp.concat()
+    val = c["val"].astype(np.float32)
+    nnz_p = np.array([p.nnz for p in bp.problems])
+    rp, col, vd = dev(c["row_ptr"], torch.int64), dev(c["col"], torch.int32), dev(val, torch.float32)
+    V0 = dev(c["V0"].astype(np.float32), torch.float32)
+    h = ocf.OpenCF(k=4, lam=0.05, sweeps=15)
+    h.batched_tune(c["m"], c["n"], c["k"], nnz_p, rp, col, vd, V0.clone())
+    V = V0.clone()
+    U = host(h.batched_fit(c["m"], c["n"], c["k"], nnz_p, rp, col, vd, V)).astype(np.float64)
+    V = host(V).astype(np.float64)
+    us, vs = _slices(c, "u_off"), _slices(c, "v_off")
+    cost = [p.nnz * p.k * p.k + (p.m + p.n) * p.k ** 3 for p in bp.problems]
+    sample = sorted(set(range(0, 10000, 250)) | set(np.argsort(cost)[-4:].tolist()))
+    worst = 0.0
+    se_g = se_o = 0.0
+    cnt = 0
+    for t in sample:
+        p = bp.problems[t]
+        pv = val[int(c["nnz_off"][t]):int(c["nnz_off"][t + 1])].astype(np.float64)
+        Ug = U[us[t]].reshape(p.m, p.k)
+        Vg = V[vs[t]].reshape(p.n, p.k)
+        cp, ci, cv = orc.transpose(p.row_ptr, p.col, pv, p.n)
+        Vr, _ = orc.half_step(cp, ci, cv, Ug, p.lam)
+        worst = max(worst, solve_err(Vg, Vr, Ug, cp, ci, cv, p.lam).max(initial=0.0))
+        if t % 500 == 0 and len(p.heldout_rows):   # the held-out gate on a sub-sample
+            Ur, Vo, _, _, _ = orc.als(p.row_ptr, p.col, pv, p.n,
+                                      rounded(p.V0, torch.float32), p.lam, 15)
+            pg = np.einsum("tk,tk->t", Ug[p.heldout_rows], Vg[p.heldout_cols])
+            po = np.einsum("tk,tk->t", Ur[p.heldout_rows], Vo[p.heldout_cols])
+            se_g += np.sum((pg - p.heldout_truth) ** 2)
+            se_o += np.sum((po - p.heldout_truth) ** 2)
+            cnt += len(pg)
+    assert worst <= TOL_FP32, worst
+    assert np.sqrt(se_g / cnt) <= np.sqrt(se_o / cnt) + 1e-3

@@ -129,3 +129,56 @@ def test_pred_empty_inference():
     torch.cuda.synchronize()
     assert y.shape == (0,)
     h.close()
+
+
+def test_online_full_size_sampled(orc):
+    """The online workload at full size, as the benchmark runs it: the
+    predictor trained on 1024 apps' runs (20 epochs), V fitted on their dense
+    matrix, then 65,536 new apps x 16 profiled runs through predictor ->
+    fold-in -> reconstruction + Algorithm 2.  Sampled: predictions against
+    the oracle's forward pass with the GPU's trained parameters; fold-in rows
+    against the oracle's solves on the GPU's predictions; decisions against
+    the oracle's Algorithm 2 on the GPU's own T, bit for bit."""
+    from gpu_util import TOL_FP32, solve_err
+    n_cpu, n_gpu, k, lam = 16, 64, 16, 0.05
+    cpu, gpu = synth.cap_grid(n_cpu, n_gpu)
+    n = n_cpu * n_gpu
+    f32 = torch.float32
+    off = synth.make_counters(seed=0, n_apps=1024, n_cpu=n_cpu, n_gpu=n_gpu)
+    rng = np.random.default_rng(0)
+    pred = ocf.Predictor(NF, batch=1024)
+    pred.set_params(dev(synth.pred_init(rng, NF), f32))
+    perms = dev(np.stack(synth.ncf_perms(rng, len(off.y), 20)), torch.int32)
+    pred.train(dev(off.X, f32), dev(off.y, f32), perms, 2e-3)
+    h = ocf.OpenCF(k=k, lam=lam, sweeps=15, cpu_caps=cpu, gpu_caps=gpu)
+    h.set_V(dev(synth.init_factor(rng, n, k), f32))
+    h.fit_offline(dev(off.y.reshape(1024, n), f32))
+    m_new, runs = 65536, 16
+    new = synth.make_counters(seed=1, n_apps=m_new, n_cpu=n_cpu, n_gpu=n_gpu, runs=runs)
+    ptr = np.arange(0, m_new * runs + 1, runs, dtype=np.int64)
+    y = pred.infer(dev(new.X, f32))
+    U, st = h.complete_rows(dev(ptr, torch.int64), dev(new.setting, torch.int32), y)
+    _, best, sav = h.predict(U, gamma=0.05, want_T=False)
+    y, Ug = host(y).astype(np.float64), host(U).astype(np.float64)
+    best, V = host(best), host(h.get_V()).astype(np.float64)
+    params = host(pred.get_params()).astype(np.float64)
+    apps = np.sort(rng.choice(m_new, 512, replace=False))
+    runs_s = (apps[:, None] * runs + np.arange(runs)).ravel()
+    # predictions: the test's derived scale, as in the parity test above
+    layers = orc.pred_unpack(params, NF)
+    _, Z2, Y = orc.mlp_forward(_f32(new.X[runs_s]), layers)
+    h2 = np.where(Z2 > 0, SELU_L * Z2, SELU_L * SELU_A * np.expm1(np.minimum(Z2, 0)))
+    scale = np.abs(h2 * layers[4][:, 0]).sum(1) + abs(layers[5][0])
+    assert (np.abs(y[runs_s] - Y[:, 0]) / scale).max() <= 2e-2
+    # fold-in of the sampled apps on the GPU's predictions
+    sp = np.arange(0, len(apps) * runs + 1, runs, dtype=np.int64)
+    sc = new.setting[runs_s]
+    sv = _f32(y[runs_s])
+    Uref, sref = orc.half_step(sp, sc, sv, V, lam)
+    assert np.array_equal(host(st)[apps], sref)
+    assert solve_err(Ug[apps], Uref, V, sp, sc, sv, lam).max() <= TOL_FP32
+    # Algorithm 2 on the GPU's T for the sampled apps
+    T, b2, _ = h.predict(U[torch.as_tensor(apps, device=DEV)].contiguous(), gamma=0.05)
+    assert np.array_equal(host(b2), best[apps])
+    bo, _ = orc.select_f32(host(T), cpu, gpu, 0.05)
+    assert np.array_equal(host(b2), bo)

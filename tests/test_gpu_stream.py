@@ -9,7 +9,7 @@ import torch
 
 import synth
 
-from gpu_util import TOL_FP32, TOL_FP64, csr_dev, dev, host, rounded, row_rel_err
+from gpu_util import TOL_FP32, TOL_FP64, csr_dev, dev, host, rounded, row_rel_err, solve_err
 
 pytestmark = pytest.mark.gpu
 
@@ -156,3 +156,40 @@ def test_stream_sums_exchange_emulated_on_one_gpu(orc):
     assert row_rel_err(host(torch.cat(Us)), host(U_one)).max() <= 1e-5
     # the counts are exact
     assert torch.equal(tot[2], one.stream_sums()[2])
+
+
+def test_stream_full_size_stepwise_sampled(orc):
+    """The streaming workload at full size (offline fit of the 2048-app block,
+    then 16 batches of 8192 new apps, one graph launch each, as the benchmark
+    runs it), step by step: sampled new apps' factors against the oracle's
+    fold-in from the GPU's previous V, and every setting of V against the
+    oracle's sums re-solved over the same factors."""
+    w = synth.make_stream(seed=0)
+    off = w.offline
+    cpu, gpu = off.caps()
+    f32 = torch.float32
+    h = ocf.OpenCF(k=off.k, lam=off.lam, sweeps=off.sweeps, cpu_caps=cpu, gpu_caps=gpu)
+    o_csr = csr_dev(off.row_ptr, off.col, off.val, f32)
+    h.set_V(dev(off.V0, f32))
+    U_off = h.fit_csr(*o_csr, off.n)
+    h.stream_begin(*o_csr, U_off)
+    ref = orc.StreamState(off.n, off.k, off.lam)
+    ref.add(off.row_ptr, off.col, rounded(off.val, f32), host(U_off).astype(np.float64))
+    V = host(h.get_V()).astype(np.float64)
+    assert row_rel_err(V, ref.V).max() <= TOL_FP32
+    rng = np.random.default_rng(0)
+    for b, (p, c, v) in enumerate(w.batches):
+        U, st = h.stream_ingest(*csr_dev(p, c, v, f32))
+        Ug = host(U).astype(np.float64)
+        rows = np.sort(rng.choice(len(p) - 1, 256, replace=False))
+        sp = [0]; sc = []; sv = []
+        for i in rows:
+            sc.append(c[p[i]:p[i + 1]]); sv.append(rounded(v[p[i]:p[i + 1]], f32))
+            sp.append(sp[-1] + p[i + 1] - p[i])
+        sp = np.array(sp); sc = np.concatenate(sc); sv = np.concatenate(sv)
+        Uref, sref = orc.half_step(sp, sc, sv, V, off.lam)
+        assert np.array_equal(host(st)[rows], sref)
+        assert solve_err(Ug[rows], Uref, V, sp, sc, sv, off.lam).max() <= TOL_FP32, b
+        ref.add(p, c, rounded(v, f32), Ug)
+        V = host(h.get_V()).astype(np.float64)
+        assert row_rel_err(V, ref.V).max() <= TOL_FP32, (b, row_rel_err(V, ref.V).max())
