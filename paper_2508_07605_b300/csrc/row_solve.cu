@@ -34,7 +34,7 @@ namespace ocf {
 template <typename TV, typename TC, int KP, int WPS>
 __global__ void __launch_bounds__(WPS == 1 ? 256 : 32 * WPS)
 k_row_solve(SolveArgs<TV> a) {
-    constexpr int WARPS = (WPS == 1) ? 8 : WPS;
+    const int WARPS = (WPS == 1) ? (int)(blockDim.x >> 5) : WPS;   // WPS = 1: 1 .. 8 warps
     using WS = WarpSmem<TV, TC, KP>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WS *smem = reinterpret_cast<WS *>(smem_raw);
@@ -82,19 +82,32 @@ cudaError_t prepare_row_solve() {
 // Observations per system above which a system gets a CTA of 4 warps.
 constexpr int64_t LONG_ROW = 96;
 
+// Systems per launch up to which an FP64 factorisation gets a CTA of 4 warps
+// per system whatever its row length.
+constexpr int64_t SMALL_FP64 = 4 * NUM_SMS_HINT;
+
 template <typename TV, typename TC, int KP>
 static cudaError_t launch_kp(const SolveArgs<TV> &a, cudaStream_t st) {
-    const bool long_rows = a.nnz >= LONG_ROW * a.m;
+    // The B300's FP64 rate is low enough that one warp's FP64 Gram of a long-ish
+    // row is a long chain on one SM sub-partition; in a small FP64 batch each
+    // system's Gram is split over 4 warps (the 4 sub-partitions of an SM).
+    const bool small_fp64 = sizeof(TC) == 8 && a.m <= SMALL_FP64;
+    const bool long_rows = a.nnz >= LONG_ROW * a.m || small_fp64;
     if (long_rows) {
         int64_t blocks = a.m;
         if (blocks > NUM_SMS_HINT * 64) blocks = NUM_SMS_HINT * 64;
         k_row_solve<TV, TC, KP, 4>
             <<<(unsigned)blocks, 128, smem_bytes<TV, TC, KP, 4>(), st>>>(a);
     } else {
-        int64_t blocks = (a.m + 7) / 8;
+        // Small batches are spread over the SMs, fewer warps per CTA: 64 systems
+        // in 8-warp CTAs would load 8 SMs and leave the rest idle.
+        int wpc = 8;
+        const int64_t per_sm = (a.m + NUM_SMS_HINT - 1) / NUM_SMS_HINT;
+        if (per_sm < 8) wpc = (int)(per_sm < 1 ? 1 : per_sm);
+        int64_t blocks = (a.m + wpc - 1) / wpc;
         if (blocks > NUM_SMS_HINT * 32) blocks = NUM_SMS_HINT * 32;
-        k_row_solve<TV, TC, KP, 1>
-            <<<(unsigned)blocks, 256, smem_bytes<TV, TC, KP, 1>(), st>>>(a);
+        k_row_solve<TV, TC, KP, 1><<<(unsigned)blocks, 32 * wpc,
+                                     sizeof(WarpSmem<TV, TC, KP>) * wpc, st>>>(a);
     }
     return cudaGetLastError();
 }
