@@ -683,7 +683,8 @@ def run_gpu_small(args):
         "error_vs_fp64_oracle": {"factor_rel_err_max": float(rel.max()), "gate": 1e-9,
                                  "selection_equal": bool(np.array_equal(best.cpu().numpy(), bo))},
         "heldout_rmse": {"gpu": rmse(Ug, Vg), "oracle_fp64": rmse(Uo, Vo)},
-        "roofline": {"kernel": "k_row_solve<double,double,8,1>", "bound": "latency",
+        "roofline": {"kernel": "k_row_solve<double,double,8,4> (a 4-warp CTA per system)",
+                     "bound": "latency",
                      "note": "3,680 solves of 8 x 8 systems per step: a few microseconds of "
                              "arithmetic; the step is launch and dependency latency"},
         "cpu_baseline": {"value": units / t_orc, "unit": "row-solves/s",
