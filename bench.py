@@ -1138,6 +1138,7 @@ WORKLOAD_NCF = "NCF (the paper's CF model): 4096 apps x 1024 settings (16x64 cap
                "epoch of mini-batch Adam (batch 1024) + completion of all 4096 x 1024 entries " \
                "+ Algorithm 2 (gamma=0.05)"
 EXP_PER_PAIR = 128 + 64   # SELU exponentials per completed entry (both hidden layers)
+NCF_TRAIN_FLOP = 6 * 2 * 64 * 128   # per training sample: 6 products of 64 x 128 MACs (2 forward, 4 backward)
 
 
 def mufu_peak_gexp(sm_mhz):
@@ -1222,6 +1223,7 @@ def run_gpu_ncf(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     bf16_peak = float(peaks.get("bf16_tflops", 1800.0))
     tflops = 2.0 * NCF_MMA_MACS * pairs / t_pred / 1e12
+    train_tflops = NCF_TRAIN_FLOP * nnz / t_epoch / 1e12
 
     # ---- parity on sampled applications, decisions on the GPU's own T
     import oracle as orc
@@ -1296,7 +1298,16 @@ def run_gpu_ncf(args):
                              "max_abs_err": float(np.abs(Th[rows] - Tref).max()),
                              "decisions_equal_fp32_oracle": bool(np.array_equal(
                                  best.cpu().numpy(), b32))},
-        "roofline": {"kernel": "k_ncf_predict_tc (completion call: first layer + pairs)",
+        "roofline": {"kernel": "k_ncf_train_tile + k_ncf_reduce_adam (one Adam step of 1024 "
+                               "samples, 32 CTAs; the epoch is 205 of them)",
+                     "bound": "latency", "achieved": train_tflops, "peak": bf16_peak,
+                     "unit": "TFLOP/s", "frac": train_tflops / bf16_peak, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                     "algorithmic": "6 products of 64 x 128 per sample (forward z1, z2; "
+                                    "backward dz1, dW2, dW1, dx) = 98,304 FLOP on mma.sync BF16",
+                     "note": "the dominant kernel pair of the step: a 1024-sample step is a "
+                             "dependent chain over 32 CTAs, far from any pipe limit"},
+        "completion_roofline": {"kernel": "k_ncf_predict_tc (completion call: first layer + pairs)",
                      "bound": "alu", "achieved": gexp, "peak": mufu, "unit": "Gexp/s",
                      "frac": gexp / mufu, "traffic": profiled_traffic_per_unit(
                          os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "ncf.cu"),
