@@ -444,11 +444,16 @@ __global__ void __launch_bounds__(256) k_ncf_reduce_adam(NcfAdamArgs a) {
     __syncthreads();
     const float fc1 = corr[0], fc2 = corr[1], lr = corr[2];
     bf16 *bf = reinterpret_cast<bf16 *>(a.bf);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        float g;
-        if (e < NCF_NET) {   // eight partials in flight at a time, summed in CTA order
-            g = 0.f;
+    // Work items: the NCF_NET network parameters one by one, then the embedding
+    // table four entries at a time (it starts 16-byte aligned at net_pad; the
+    // padding between is never touched).  Only an update touches the embeddings.
+    const int64_t n4 = a.update ? a.n_emb / 4 : 0;
+    const int64_t items = NCF_NET + n4;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < items;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        if (w < NCF_NET) {   // eight partials in flight at a time, summed in CTA order
+            const int64_t e = w;
+            float g = 0.f;
             int c = 0;
             for (; c + 8 <= a.parts; c += 8) {
                 float v[8];
@@ -459,22 +464,38 @@ __global__ void __launch_bounds__(256) k_ncf_reduce_adam(NcfAdamArgs a) {
             }
             for (; c < a.parts; ++c) g += a.part[(int64_t)c * a.part_stride + e];
             a.grad[e] = g;
-        } else if (e < a.net_pad) {
-            continue;
-        } else {
-            if (!a.update) continue;   // the embedding gradient stays for the caller
-            g = a.grad[e];
-            a.grad[e] = 0.f;
+            if (!a.update) continue;
+            const float m1 = 0.9f * a.m1[e] + 0.1f * g;
+            const float m2 = 0.999f * a.m2[e] + 0.001f * g * g;
+            a.m1[e] = m1;
+            a.m2[e] = m2;
+            const float t = a.th[e] - lr * (m1 / fc1) / (sqrtf(m2 / fc2) + 1e-8f);
+            a.th[e] = t;
+            if (e < NCF_OFF_B1) bf[e] = __float2bfloat16_rn(t);
+            else if (e >= NCF_OFF_W2 && e < NCF_OFF_B2)
+                bf[NCF_OFF_B1 + (e - NCF_OFF_W2)] = __float2bfloat16_rn(t);
+        } else {   // embeddings: the same update on a float4, the gradient cleared
+            const int64_t e = a.net_pad + 4 * (w - NCF_NET);
+            float4 *gp = reinterpret_cast<float4 *>(a.grad + e);
+            float4 *m1p = reinterpret_cast<float4 *>(a.m1 + e);
+            float4 *m2p = reinterpret_cast<float4 *>(a.m2 + e);
+            float4 *thp = reinterpret_cast<float4 *>(a.th + e);
+            const float4 g4 = *gp, a1 = *m1p, a2 = *m2p, t4 = *thp;
+            *gp = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, v1[4] = {a1.x, a1.y, a1.z, a1.w};
+            const float v2[4] = {a2.x, a2.y, a2.z, a2.w}, vt[4] = {t4.x, t4.y, t4.z, t4.w};
+            float o1[4], o2[4], ot[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float g = gv[q];
+                o1[q] = 0.9f * v1[q] + 0.1f * g;
+                o2[q] = 0.999f * v2[q] + 0.001f * g * g;
+                ot[q] = vt[q] - lr * (o1[q] / fc1) / (sqrtf(o2[q] / fc2) + 1e-8f);
+            }
+            *m1p = make_float4(o1[0], o1[1], o1[2], o1[3]);
+            *m2p = make_float4(o2[0], o2[1], o2[2], o2[3]);
+            *thp = make_float4(ot[0], ot[1], ot[2], ot[3]);
         }
-        if (!a.update) continue;
-        const float m1 = 0.9f * a.m1[e] + 0.1f * g;
-        const float m2 = 0.999f * a.m2[e] + 0.001f * g * g;
-        a.m1[e] = m1;
-        a.m2[e] = m2;
-        const float t = a.th[e] - lr * (m1 / fc1) / (sqrtf(m2 / fc2) + 1e-8f);
-        a.th[e] = t;
-        if (e < NCF_OFF_B1) bf[e] = __float2bfloat16_rn(t);
-        else if (e >= NCF_OFF_W2 && e < NCF_OFF_B2) bf[NCF_OFF_B1 + (e - NCF_OFF_W2)] = __float2bfloat16_rn(t);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double sse = 0.0;
@@ -646,7 +667,8 @@ cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, c
     k_ncf_train_tile<<<t.B / TT, NTH, TRAIN_SMEM, st>>>(t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int64_t blocks = (u.net_pad + u.n_emb + 255) / 256;
+    if (u.net_pad % 4 || u.n_emb % 4) return cudaErrorInvalidValue;   // float4 embedding updates
+    int64_t blocks = (NCF_NET + u.n_emb / 4 + 255) / 256;
     if (blocks > NUM_SMS_HINT * 8) blocks = NUM_SMS_HINT * 8;
     k_ncf_reduce_adam<<<(unsigned)blocks, 256, 0, st>>>(u);
     return cudaGetLastError();
