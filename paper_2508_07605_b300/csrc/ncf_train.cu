@@ -444,25 +444,34 @@ __global__ void __launch_bounds__(256) k_ncf_reduce_adam(NcfAdamArgs a) {
     __syncthreads();
     const float fc1 = corr[0], fc2 = corr[1], lr = corr[2];
     bf16 *bf = reinterpret_cast<bf16 *>(a.bf);
-    // Work items: the NCF_NET network parameters one by one, then the embedding
-    // table four entries at a time (it starts 16-byte aligned at net_pad; the
-    // padding between is never touched).  Only an update touches the embeddings.
+    // Work items: four per network parameter (lane q of a group of four sums
+    // partials q, q + 4, q + 8, ... in order, and the four sums are combined in
+    // a fixed order: one round of loads instead of parts / 8 dependent ones),
+    // then the embedding table four entries at a time (it starts 16-byte
+    // aligned at net_pad; the padding between is never touched).  Only an
+    // update touches the embeddings.
     const int64_t n4 = a.update ? a.n_emb / 4 : 0;
-    const int64_t items = NCF_NET + n4;
+    const int64_t items = 4 * NCF_NET + n4;
+    const int lane = threadIdx.x & 31;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < items;
          w += (int64_t)gridDim.x * blockDim.x) {
-        if (w < NCF_NET) {   // eight partials in flight at a time, summed in CTA order
-            const int64_t e = w;
+        if (w < 4 * NCF_NET) {   // 4 NCF_NET is a multiple of 4: a group never straddles
+            const int64_t e = w >> 2;
+            const int q = (int)(w & 3);
+            const unsigned gm = 0xFu << (lane & ~3);
             float g = 0.f;
-            int c = 0;
-            for (; c + 8 <= a.parts; c += 8) {
+            int c = q;
+            for (; c + 28 < a.parts; c += 32) {   // eight partials in flight at a time
                 float v[8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) v[t] = a.part[(int64_t)(c + t) * a.part_stride + e];
+                for (int t = 0; t < 8; ++t) v[t] = a.part[(int64_t)(c + 4 * t) * a.part_stride + e];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) g += v[t];
             }
-            for (; c < a.parts; ++c) g += a.part[(int64_t)c * a.part_stride + e];
+            for (; c < a.parts; c += 4) g += a.part[(int64_t)c * a.part_stride + e];
+            g += __shfl_xor_sync(gm, g, 1);   // (s0 + s1) + (s2 + s3) on every lane
+            g += __shfl_xor_sync(gm, g, 2);
+            if (q != 0) continue;
             a.grad[e] = g;
             if (!a.update) continue;
             const float m1 = 0.9f * a.m1[e] + 0.1f * g;
@@ -475,7 +484,7 @@ __global__ void __launch_bounds__(256) k_ncf_reduce_adam(NcfAdamArgs a) {
             else if (e >= NCF_OFF_W2 && e < NCF_OFF_B2)
                 bf[NCF_OFF_B1 + (e - NCF_OFF_W2)] = __float2bfloat16_rn(t);
         } else {   // embeddings: the same update on a float4, the gradient cleared
-            const int64_t e = a.net_pad + 4 * (w - NCF_NET);
+            const int64_t e = a.net_pad + 4 * (w - 4 * NCF_NET);
             float4 *gp = reinterpret_cast<float4 *>(a.grad + e);
             float4 *m1p = reinterpret_cast<float4 *>(a.m1 + e);
             float4 *m2p = reinterpret_cast<float4 *>(a.m2 + e);
@@ -668,7 +677,7 @@ cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, c
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (u.net_pad % 4 || u.n_emb % 4) return cudaErrorInvalidValue;   // float4 embedding updates
-    int64_t blocks = (NCF_NET + u.n_emb / 4 + 255) / 256;
+    int64_t blocks = (4 * NCF_NET + u.n_emb / 4 + 255) / 256;
     if (blocks > NUM_SMS_HINT * 8) blocks = NUM_SMS_HINT * 8;
     k_ncf_reduce_adam<<<(unsigned)blocks, 256, 0, st>>>(u);
     return cudaGetLastError();
