@@ -151,6 +151,36 @@ int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
                           const int32_t *col, const void *val, void *U_out, int32_t *status,
                           int32_t joint, void *stream);
 
+/* Online fold-in with the final residual check (extension of
+ * open_cf_complete_rows with joint = 0; Sec. "Online Performance Prediction"
+ * completes the new rows, the check verifies each row's normal equations).
+ * For handles with 16 < k <= 32 in OPEN_CF_FP32 or OPEN_CF_BF16_GRAM precision
+ * and the FP32 k x k factorisation (cholesky_fp64 = 0); other handles return
+ * OPEN_CF_UNSUPPORTED.  U_out (m_new x k float) and status (may be NULL) as
+ * for open_cf_complete_rows.
+ *  resid (float[m_new], may be NULL): per row the relative residual of the
+ *    normal equations the library formed (A_i = its Gram + lambda I, b_i its
+ *    right-hand side, in the handle's Gram precision):
+ *        |A_i u_i - b_i| / (|A_i|_F |u_i| + |b_i|),
+ *    with b_i - A_i u_i evaluated in double-FP32 arithmetic (error-free
+ *    products and sums, ~2^-44 relative), -1 for rows whose status is not OK.
+ *  refine = 1: one step of iterative refinement: the correction A_i d = r_i
+ *    (r_i that residual) is solved with the same FP32 factor and u_i += d;
+ *    resid then reports the refined u_i.  refine = 0: no refinement. */
+int open_cf_complete_rows_checked(open_cf_t *h, int64_t m_new, int64_t nnz,
+                                  const int64_t *row_ptr, const int32_t *col, const float *val,
+                                  float *U_out, int32_t *status, float *resid, int32_t refine,
+                                  void *stream);
+
+/* The same relative normal-equation residual for given factors U (m x k float)
+ * of the CSR rows against the handle's V (the residual part of the a9
+ * objective/residual step): resid float[m], every row computed (an empty row
+ * gives |lambda u| / (lambda sqrt(k) |u|)).  Same handle requirements as
+ * open_cf_complete_rows_checked. */
+int open_cf_normal_residual(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                            const int32_t *col, const float *val, const float *U, float *resid,
+                            void *stream);
+
 /* Reconstruction and Algorithm 2 (energy-efficient power-cap selection) on
  * the predicted rows T = U V^T, U m x k real.  T_out (m x n real) may be NULL,
  * in which case the dense prediction never leaves the chip; best (int32[m])
@@ -337,20 +367,26 @@ int open_cf_fma_peak(int32_t fp64, int32_t device, double *tflops_host);
  * provides every input and output (device pointers on the current device):
  * row_ptr int64[m+1], col int32[nnz], val float[nnz]; col_ptr int64[n+1],
  * row_idx int32[nnz], cval float[nnz].
- *  - The first call on a device looks up the array's device address and sets
- *    the kernels' shared-memory limit; make that first call before any stream
- *    capture begins.
+ *  - Every call looks up the array's device address on the current device
+ *    and sets the sort kernels' shared-memory limit (host-side calls that
+ *    allocate nothing, repeated so that a device reset cannot leave a stale
+ *    address).  The first call on a device also loads this library's module
+ *    there: make that first call before any stream capture begins.
  *  - All calls share the one array, so calls whose work overlaps on the GPU
  *    (different streams, or different host threads) race and corrupt each
  *    other's results; serialise them.  Each call overwrites every counter it
  *    reads, so nothing has to be cleared between calls.
- *  - n > OPEN_CF_NOALLOC_MAX_COLUMNS returns OPEN_CF_UNSUPPORTED (the column
- *    totals plus one block of counters no longer fit the array); the outputs
- *    are then left untouched.  Bad sizes or NULL pointers return
+ *  - n > OPEN_CF_NOALLOC_MAX_COLUMNS returns OPEN_CF_UNSUPPORTED (the sort's
+ *    per-column shared-memory counters bound n, as for the handle path); the
+ *    outputs are then left untouched.
+ *  - Speed: rows are sorted in at most (4 MiB - 8n rounded up to 256 B) / 4n
+ *    row blocks of one CTA each (254 at n = 4096, 39 at n = 25,000), where
+ *    the handle path uses up to 4096; wide matrices with many rows therefore
+ *    sort more slowly through this call.  Bad sizes or NULL pointers return
  *    OPEN_CF_INVALID_ARG; a CUDA failure returns OPEN_CF_CUDA_ERROR.
  * Work is enqueued on `stream` (NULL = legacy default stream). */
-#define OPEN_CF_NOALLOC_SCRATCH_BYTES (256 * 1024)
-#define OPEN_CF_NOALLOC_MAX_COLUMNS 21824 /* largest n with 8n (rounded up to 256) + 4n <= 256 KiB */
+#define OPEN_CF_NOALLOC_SCRATCH_BYTES (4 * 1024 * 1024)
+#define OPEN_CF_NOALLOC_MAX_COLUMNS 25000 /* the transpose's shared-memory counter limit */
 int open_cf_csr_to_csc_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
                                const int32_t *col, const float *val, int64_t *col_ptr,
                                int32_t *row_idx, float *cval, void *stream);

@@ -53,6 +53,9 @@ _SIGNATURES = {
     "open_cf_fit_offline": (ctypes.c_int, [_V, _V, _I64, _I64, _I64, _V, _V, _V]),
     "open_cf_fit_csr": (ctypes.c_int, [_V, _I64, _I64, _I64, _V, _V, _V, _V, _V, _V, _V, _V]),
     "open_cf_complete_rows": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _I32, _V]),
+    "open_cf_complete_rows_checked": (ctypes.c_int,
+                                      [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _I32, _V]),
+    "open_cf_normal_residual": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V]),
     "open_cf_predict": (ctypes.c_int, [_V, _V, _I64, _V, _V, _V, _F, _I32, _V]),
     "open_cf_select": (ctypes.c_int, [_V, _V, _I64, _I64, _V, _V, _F, _I32, _V]),
     "open_cf_objective": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
@@ -264,6 +267,30 @@ class OpenCF:
                                                 _ptr(val), _ptr(U), _ptr(st), int(joint),
                                                 self._stream()))
         return U, st
+
+    def complete_rows_checked(self, row_ptr, col, val, refine: bool = False, U=None, st=None,
+                              resid=None):
+        """Fold-in with the per-row normal-equation residual (and optionally one
+        refinement step); returns (U, status, resid).  Output tensors may be
+        passed in to be reused."""
+        m, nnz = self._csr(row_ptr, col, val)
+        U = self._empty(m, self.k) if U is None else U
+        st = self._empty(m, dtype=torch.int32) if st is None else st
+        resid = self._empty(m, dtype=torch.float32) if resid is None else resid
+        self._check(lib().open_cf_complete_rows_checked(
+            self._h, m, nnz, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(U), _ptr(st),
+            _ptr(resid), int(bool(refine)), self._stream()))
+        return U, st, resid
+
+    def normal_residual(self, row_ptr, col, val, U):
+        """Per-row relative normal-equation residual of the given factors."""
+        m, nnz = self._csr(row_ptr, col, val)
+        self._real(U, "U")
+        resid = self._empty(m, dtype=torch.float32)
+        self._check(lib().open_cf_normal_residual(self._h, m, nnz, _ptr(row_ptr), _ptr(col),
+                                                  _ptr(val), _ptr(U), _ptr(resid),
+                                                  self._stream()))
+        return resid
 
     def predict(self, U, gamma: float = 0.05, baseline: int = -1, want_T: bool = True,
                 want_select: bool = True):

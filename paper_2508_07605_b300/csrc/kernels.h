@@ -34,6 +34,13 @@ template <typename TV> struct SolveArgs {
     TV *gram_b = nullptr;
     int64_t *gram_n = nullptr;
     bool gram_keep = false;
+    // Rank-32 FP32-Cholesky solver only (solve32_tc.cu): per-row relative
+    // normal-equation residual |A u - b| / (|A|_F |u| + |b|) (null: none), one
+    // refinement step, or the residual of a given u (rows of stride ldo) with
+    // nothing solved or written but the residual.
+    float *resid = nullptr;
+    bool refine = false;
+    const TV *u_given = nullptr;
 };
 
 template <typename TV, typename TC>
@@ -60,6 +67,10 @@ cudaError_t prepare_row_solve();
 cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp64, bool bf16,
                                 cudaStream_t st);
 cudaError_t prepare_row_solve_tc();
+// Padded rank 32, FP32 Cholesky, one system per warp (bf16: split-BF16 Gram,
+// else 3-pass TF32), with the optional residual / refinement of SolveArgs.
+cudaError_t launch_solve32_tc(const SolveArgs<float> &a, bool bf16, cudaStream_t st);
+cudaError_t prepare_solve32_tc();
 
 // Batched ALS over independent problems (batched.cu).  Per-problem arrays are
 // indexed by problem id p; order[] lists problem ids in processing order;

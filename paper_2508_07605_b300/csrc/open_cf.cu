@@ -649,7 +649,8 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
     }
     DeviceGuard g(h->device);
     if (prepare_csr_to_csc(CSC_MAX_N) != cudaSuccess || prepare_row_solve() != cudaSuccess ||
-        prepare_row_solve_tc() != cudaSuccess || prepare_batched() != cudaSuccess ||
+        prepare_row_solve_tc() != cudaSuccess || prepare_solve32_tc() != cudaSuccess ||
+        prepare_batched() != cudaSuccess ||
         prepare_mlp_forward_tc() != cudaSuccess || prepare_predict_tc() != cudaSuccess ||
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
             cudaSuccess) {
@@ -856,6 +857,57 @@ int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
                                   st);
     return fit_sweeps<float>(h, m, nz, jp, (int32_t *)h->j_idx.p, (float *)h->j_val.p,
                              (float *)U_out, h->m_off, m_new, nullptr, nullptr, nullptr, st);
+}
+
+int open_cf_complete_rows_checked(open_cf_t *h, int64_t m_new, int64_t nnz,
+                                  const int64_t *row_ptr, const int32_t *col, const float *val,
+                                  float *U_out, int32_t *status, float *resid, int32_t refine,
+                                  void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = check_csr_args(h, m_new, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (h->f64 || h->KP != 32 || h->cfg.cholesky_fp64)
+        return fail(h, OPEN_CF_UNSUPPORTED,
+                    "the residual check needs 16 < k <= 32, FP32 or BF16-Gram precision and the "
+                    "FP32 factorisation");
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: fit or set V first");
+    if (m_new > 0 && !U_out) return fail(h, OPEN_CF_INVALID_ARG, "U_out is NULL");
+    if (refine != 0 && refine != 1) return fail(h, OPEN_CF_INVALID_ARG, "refine must be 0 or 1");
+    DeviceGuard g(h->device);
+    SolveArgs<float> a{m_new, nnz, row_ptr, col, val, (float *)h->V.p, h->n, U_out, h->k, h->k,
+                       status, h->cfg.lambda};
+    a.wr = h->cfg.weighted_lambda != 0;
+    const bool bf = h->cfg.precision == OPEN_CF_BF16_GRAM;
+    if (bf) a.Fb = h->Vb16.p;
+    a.resid = resid;
+    a.refine = refine != 0;
+    CK(h, launch_solve32_tc(a, bf, S(stream)));
+    return OPEN_CF_OK;
+}
+
+int open_cf_normal_residual(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                            const int32_t *col, const float *val, const float *U, float *resid,
+                            void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
+    if (rc) return rc;
+    if (h->f64 || h->KP != 32)
+        return fail(h, OPEN_CF_UNSUPPORTED,
+                    "the residual needs 16 < k <= 32 and FP32 or BF16-Gram precision");
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: fit or set V first");
+    if (m > 0 && (!U || !resid)) return fail(h, OPEN_CF_INVALID_ARG, "U or resid is NULL");
+    DeviceGuard g(h->device);
+    SolveArgs<float> a{m, nnz, row_ptr, col, val, (float *)h->V.p, h->n, nullptr, h->k, h->k,
+                       nullptr, h->cfg.lambda};
+    a.wr = h->cfg.weighted_lambda != 0;
+    const bool bf = h->cfg.precision == OPEN_CF_BF16_GRAM;
+    if (bf) a.Fb = h->Vb16.p;
+    a.resid = resid;
+    a.u_given = U;
+    CK(h, launch_solve32_tc(a, bf, S(stream)));
+    return OPEN_CF_OK;
 }
 
 }  // extern "C"

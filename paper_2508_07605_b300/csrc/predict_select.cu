@@ -166,10 +166,10 @@ __global__ void __launch_bounds__(PT) k_predict_select(PredictArgs<TV> a) {
                     }
                     // 16-row tiles (a warp per row): the lanes of a row agree on the
                     // row's smallest estimate.  64-row tiles (16 lanes per row): each
-                    // thread screens with its own, a looser bound (more settings reach
-                    // the exact test, none is lost) that saves a cross-lane minimum per
-                    // tile; measured faster there (0.419 -> 0.404 ms on the online line)
-                    // and slower with 16-row tiles (0.423 -> 0.429 ms on the default line).
+                    // thread screens with its own, which saves a cross-lane minimum per
+                    // tile.  Sound: a thread's minimum is at least the row's, and
+                    // alg2_bound increases with its argument, so the bound only gets
+                    // looser and no setting that could win or tie is screened out.
                     if constexpr (TX >= 32) emin = group_min<32>(emin);
                     float bound = alg2_bound(emin, a.Ebase);
                     if (best[r].j >= 0) bound = fminf(bound, best[r].Ethr);

@@ -60,15 +60,13 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// 32 accumulator values of one row (settings j0 .. j0 + 31): the smallest
-// screening estimate, the exact evaluation of those the screen keeps, the
-// dense output.  Indices are compile-time after unrolling, so v stays in
-// registers.
-// The lanes of a warp hold different rows, so an exact evaluation taken by
-// one lane is paid by all: the screen therefore tracks the smallest estimate
-// of each group of GS settings together with its element, evaluates that
-// element exactly on every lane at once, and leaves to a divergent second pass
-// only the rare elements that come within the screening margin of it.
+// Per group of GS settings of a row (one TMEM load, indices compile-time after
+// unrolling, so the values stay in registers): the dense output if requested,
+// then a branch-free screen (validity and the smallest energy estimate, three
+// instructions per element) and, only when the group's smallest estimate can
+// still win or tie, the exact evaluation of the elements within the bound.
+// The lanes of a warp hold different rows, so an exact evaluation taken by one
+// lane is paid by all; once a row has a best, few groups pass its threshold.
 __device__ __forceinline__ void store16(const uint32_t (&v)[GS], float *trow, int64_t j0,
                                         int64_t n, bool vec) {
     if (vec && j0 + GS <= n) {
@@ -120,8 +118,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (cg_smem && a.select)   // padded with zeros to whole chunks
-        for (int64_t j = tid; j < (int64_t)nch * CN; j += NTHREADS) cg_s[j] = j < a.n ? a.cg[j] : 0.0f;
+    if (cg_smem && a.select)   // padded with +inf to whole chunks
+        for (int64_t j = tid; j < (int64_t)nch * CN; j += NTHREADS)
+            cg_s[j] = j < a.n ? a.cg[j] : __int_as_float(0x7f800000);
     if (warp == ISSUER) tc_alloc(smem_u32(tmem_slot), TMEM_COLS);
     tc_fence_before();
     __syncthreads();
@@ -239,10 +238,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                         if (lane == 0) mbar_arrive(aempty(ab));
                     }
                     const int64_t j0 = (int64_t)chunk * CN + CPW * cq + GS * hh;
-                    const int nv = (int)(a.n - j0 < GS ? a.n - j0 : GS);   // settings in range
                     if (a.T && i < a.m) store16(v, a.T + i * a.n, j0, a.n, a.t_vec);
                     if (a.select) {
-                        // c + g of the group's settings (padded with zeros past n)
+                        // c + g of the group's settings (+inf past n: never a minimum)
                         float cgv[GS];
                         const float4 *cg4 = reinterpret_cast<const float4 *>(
                             cg_smem ? (const float *)cg_s + j0 : a.cg_pad + j0);
@@ -254,44 +252,68 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                             cgv[4 * e4 + 2] = x.z;
                             cgv[4 * e4 + 3] = x.w;
                         }
-                        // pass 1 (branch-free): the smallest estimate with its element and
-                        // t, and the second smallest.  Validity 0 < t <= t* is one unsigned
-                        // compare on the bit patterns (positive floats order like their
-                        // bits; zero, negatives and NaN fall outside), tsb = 0 for a row
-                        // without a valid baseline.
+                        // Screen, branch-free: w_e = (c + g) t of each valid element
+                        // (0 < t <= t* is one unsigned compare on the bit patterns:
+                        // positive floats order like their bits, zero, negatives and
+                        // NaN fall outside; tsb = 0 for a row without a valid
+                        // baseline), +inf otherwise, and the group's smallest w.  The
+                        // energy estimate is w / t_b = fl(w * (1 / t_b)), monotone in
+                        // w, so the group's smallest estimate is fl(min w * (1 / t_b)).
                         const float inf = __int_as_float(0x7f800000);
                         const uint32_t tsb = rc.tstar > 0.0f ? __float_as_uint(rc.tstar) : 0u;
-                        float me = inf, me2 = inf, mt = 0.0f;
-                        int mi = -1;
+                        float w[GS];
+                        float wmin = inf;
 #pragma unroll
                         for (int e = 0; e < GS; ++e) {
-                            const uint32_t tb = e < nv ? v[e] : 0u;
-                            const bool ok = (tb - 1u) < tsb;
-                            const float t = __uint_as_float(tb);
-                            const float est = __fmul_rn(__fmul_rn(cgv[e], t), rc.rtb);
-                            const bool lt = ok && est < me;
-                            me2 = lt ? me : (ok ? fminf(me2, est) : me2);
-                            me = lt ? est : me;
-                            mt = lt ? t : mt;
-                            mi = lt ? e : mi;
+                            const bool ok = (v[e] - 1u) < tsb;
+                            w[e] = ok ? __fmul_rn(cgv[e], __uint_as_float(v[e])) : inf;
+                            wmin = fminf(wmin, w[e]);
                         }
-                        if (mi >= 0) {   // some valid setting in this group
-                            float bound = alg2_bound(me, a.Ebase);
-                            if (best.j >= 0) bound = fminf(bound, best.Ethr);
-                            if (me <= bound) {
-                                const float mc = cg_smem ? cg_s[j0 + mi] : a.cg_pad[j0 + mi];
-                                alg2_exact(best, rc, mt, mc, a.Ebase, (int32_t)(j0 + mi));
-                                bound = fminf(bound, best.Ethr);
-                            }
-                            // pass 2, only when another setting is within the margin (rare)
-                            if (me2 <= bound) {
+                        // Exact evaluation only where the screen cannot exclude: the
+                        // group's smallest estimate is at most the best's threshold (or no
+                        // best yet).  Warp-uniform, since the lanes hold different rows:
+                        // every lane recovers its group's arg-min (the first element
+                        // attaining the minimum), the rows that need it evaluate that
+                        // element exactly in one pass, and only if some other element
+                        // lies within the screening bound (rare) a divergent pass
+                        // evaluates those too.
+                        const float me = __fmul_rn(wmin, rc.rtb);
+                        const bool trig = wmin < inf && me <= (best.j >= 0 ? best.Ethr : inf);
+                        if (__any_sync(FULL, trig)) {
+                            int mi = 0;
+                            float mt = 0.0f, mc = 0.0f;
 #pragma unroll
+                            for (int e = GS - 1; e >= 0; --e) {
+                                const bool hit = w[e] == wmin;
+                                mi = hit ? e : mi;
+                                mt = hit ? __uint_as_float(v[e]) : mt;
+                                mc = hit ? cgv[e] : mc;
+                            }
+                            float bound = inf;
+                            if (trig) {
+                                alg2_exact(best, rc, mt, mc, a.Ebase, (int32_t)(j0 + mi));
+                                bound = fminf(alg2_bound(me, a.Ebase), best.Ethr);
+                            }
+                            int more = 0;
+#pragma unroll
+                            for (int e = 0; e < GS; ++e)
+                                more += (trig && e != mi && __fmul_rn(w[e], rc.rtb) <= bound) ? 1 : 0;
+                            if (__any_sync(FULL, more > 0) && more > 0) {
+#pragma unroll 1
                                 for (int e = 0; e < GS; ++e) {
-                                    const uint32_t tb = e < nv ? v[e] : 0u;
-                                    const float t = __uint_as_float(tb);
-                                    const float est = __fmul_rn(__fmul_rn(cgv[e], t), rc.rtb);
-                                    if ((tb - 1u) < tsb && est <= bound && e != mi)
-                                        exact_call(best, rc, t, cgv[e], a.Ebase, (int32_t)(j0 + e));
+                                    float we = w[0];
+#pragma unroll
+                                    for (int f = 1; f < GS; ++f) we = (f == e) ? w[f] : we;
+                                    if (e != mi && __fmul_rn(we, rc.rtb) <= bound) {
+                                        float te = __uint_as_float(v[0]), ce = cgv[0];
+#pragma unroll
+                                        for (int f = 1; f < GS; ++f) {
+                                            te = (f == e) ? __uint_as_float(v[f]) : te;
+                                            ce = (f == e) ? cgv[f] : ce;
+                                        }
+                                        exact_call(best, rc, te, ce, a.Ebase, (int32_t)(j0 + e));
+                                        bound = fminf(bound, best.Ethr);
+                                    }
                                 }
                             }
                         }

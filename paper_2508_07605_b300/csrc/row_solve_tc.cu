@@ -42,78 +42,11 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "mma_sync.cuh"
 
 namespace ocf {
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// cp.async with zero fill: copies src_bytes (0 or the full size) and zeroes the rest.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
-                 "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
-                 "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-// BF16 operands: m16n8k16 MMA with FP32 accumulation, fragments of the staged
-// row-major tile read transposed by ldmatrix.
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void *p) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(s));
-}
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-// Programmatic dependent launch: a half-step lets the next one launch as soon
-// as all of its CTAs are running, and waits for its predecessor only before
-// the first access to data a predecessor writes (the other factor, the
-// compacted row list).  The CSR / CSC arrays read before the wait are never
-// written by a preceding half-step.
-__device__ __forceinline__ void pdl_trigger() {
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+using namespace sm;
 
 // Per-warp shared memory.  The staging buffers (NST stages of 32 factor
 // rows) are dead once the warp's Gram is in registers, so the Gram / factor
@@ -757,6 +690,9 @@ static cudaError_t launch_tc_kp(const SolveArgs<float> &a, cudaStream_t st) {
         return launch_pdl(k_row_solve_tc<KP, TC, 4, BF, SUMS>, (unsigned)blocks, 128,
                           tc_smem_bytes<KP, TC, 4, BF, SUMS>(), st, a);
     }
+    // one system per warp at rank 32 with an FP32 factorisation: the packed
+    // FP32x2 solver of solve32_tc.cu
+    if constexpr (KP == 32 && sizeof(TC) == 4 && !SUMS) return launch_solve32_tc(a, BF, st);
     constexpr int WARPS = (sizeof(TC) == 8 && KP == 32) ? 4 : 8;
     const int64_t per = (int64_t)WARPS * tc_spw<KP, TC, 1, SUMS>();
     int64_t blocks = (a.m + per - 1) / per;
@@ -782,6 +718,10 @@ cudaError_t launch_row_solve_tc(const SolveArgs<float> &a, int KP, bool chol_fp6
     if (a.m <= 0) return cudaSuccess;
     if (bf16 && !a.Fb) return cudaErrorInvalidValue;
     if (bf16 && a.gram) return cudaErrorInvalidValue;   // the streaming refit is FP32 / FP64 only
+    if (a.resid || a.refine || a.u_given) {   // residual / refinement: rank-32 FP32 solver only
+        if (KP != 32 || chol_fp64) return cudaErrorInvalidValue;
+        return launch_solve32_tc(a, bf16, st);
+    }
     if (bf16) return launch_tc_bf<true, false>(a, KP, chol_fp64, st);
     return a.gram ? launch_tc_bf<false, true>(a, KP, chol_fp64, st)
                   : launch_tc_bf<false, false>(a, KP, chol_fp64, st);

@@ -13,7 +13,7 @@ it, with the shapes of the paper's problem: rows are applications, columns are
 the offline block is dense, and each new application contributes a handful of
 online-profiled entries.
 
-Readings of unstated details (also listed in the design doc):
+Readings of details the paper leaves unstated:
   * noise ``N(0, 0.01)`` is a standard deviation of 0.01, added after
     normalisation, never clipped;
   * the exp-transformed matrix is normalised by its global min and max;
