@@ -1,6 +1,7 @@
-// One ALS row solve per warp at padded rank 32, Gram on the tensor cores,
-// FP32 Cholesky on packed FP32x2 FMAs, with an optional extended-precision
-// normal-equation residual and one step of iterative refinement.
+// One ALS row solve per half-warp at padded rank 32 (two systems per warp),
+// Gram on the tensor cores, FP32 Cholesky on packed FP32x2 FMAs, with an
+// optional extended-precision normal-equation residual and one step of
+// iterative refinement.
 //
 // Per row i of a CSR matrix with F the fixed other factor (the ridge row solve
 // of ALS; Sec. "Collaborative Filtering Model", Sec. "Online Performance
@@ -8,32 +9,37 @@
 //     A_i = sum_{j in Omega_i} f_j f_j^T + lambda I,   b_i = sum_{j in Omega_i} R_ij f_j,
 //     A_i = L L^T,  L y = b_i,  L^T u_i = y.
 //
-// Gram phase: the row's observations 32 at a time, each lane staging one
-// observation's factor row with 16-byte cp.async (double-buffered, zero fill
-// past the row end); S^T S and S^T r on mma.sync, either split BF16
-// (m16n8k16: x = hi + lo, hi^T hi + hi^T lo + lo^T hi, FP32 accumulation) or
-// 3-pass TF32 (m16n8k8), lower-triangle 16x8 blocks only.  The fragments go to
-// shared memory as the full symmetric A (the off-diagonal block is written
-// twice), which stays there for the residual.
+// Work split: each warp owns a contiguous range of row pairs.  While it
+// solves one pair it already has the next pair's row bounds, column indices
+// and values (the first 64 observations of each row) in flight into
+// registers, so the Gram phase of the next pair starts without waiting on
+// DRAM.
 //
-// Solve phase, lane q owning row q:
-//  * right-looking Cholesky: step p broadcasts column p of L through shared
-//    memory (stored column-major, so all of L stays there), and the trailing
-//    update a[r] -= l_q * L[r][p], r > p, runs two elements per instruction
-//    (fma.rn.f32x2; each element rounds exactly like fmaf);
-//  * the forward substitution L y = b rides along: y_p is formed on the pivot
-//    step and broadcast with column p;
-//  * back substitution from column q of L held in registers.
-// The operations and their order per element are those of the lane-per-row
-// factorisation in row_solve_tc.cu.
+// Gram phase (whole warp): both rows' observations 32 at a time, each lane
+// staging one observation's factor row with 16-byte cp.async (double-buffered,
+// zero fill past the row end); S^T S and S^T r on mma.sync, either split BF16
+// (m16n8k16: x = hi + lo, hi^T hi + hi^T lo + lo^T hi, FP32 accumulation) or
+// 3-pass TF32 (m16n8k8), lower-triangle 16x8 blocks only.  The fragments go
+// to shared memory as the packed lower triangle of A (rows padded to 4
+// floats), which stays there for the residual.
+//
+// Solve phase: half h of the warp solves system h of the pair; lane i holds
+// rows i and i + 16 of the lower triangle (16 + 32 registers; row i never
+// needs a column >= 16).  Right-looking Cholesky: step p broadcasts column p
+// of L through shared memory (packed by columns, each column from row
+// 4 floor(p/4) on, so the 16-byte loads stay aligned), and the trailing
+// update of both rows runs two elements per instruction (fma.rn.f32x2; each
+// element rounds exactly like fmaf).  The forward substitution L y = b rides
+// along (y_p formed on the pivot step, broadcast by a shuffle); the back
+// substitution runs from columns i and i + 16 of L held in registers.
 //
 // Residual (optional): r = b - A u in double-FP32 arithmetic (each product
-// split exactly by an FMA, sums by error-free two-sums, two chains per
-// packed instruction), i.e. with ~2^-44 relative error instead of FP32's
-// ~k 2^-24: B300's FP64 pipe runs at ~1/75 of the FP32 rate, so this costs a
-// fraction of one FP64 matrix-vector product.  With refinement, the
-// correction A d = r is solved with the same FP32 factor, u += d, and the
-// residual of the refined u is the one reported, as
+// split exactly by an FMA, sums by error-free two-sums; the two rows of a lane
+// are the two halves of each packed instruction), i.e. with ~2^-44 relative
+// error instead of FP32's ~k 2^-24: B300's FP64 pipe runs at ~1/75 of the FP32
+// rate, so this costs a fraction of one FP64 matrix-vector product.  With
+// refinement, the correction A d = r is solved with the same FP32 factor,
+// u += d, and the residual of the refined u is the one reported, as
 // |A u - b| / (|A|_F |u| + |b|).  A residual-only mode takes u as input.
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -47,24 +53,44 @@ namespace {
 
 using namespace sm;
 
-constexpr int KP = 32, WARPS = 8, NST = 2, LDA = 36;
+constexpr int KP = 32, WARPS = 8, NPACK = 576;
 
+// Packed lower triangle by rows: row r (entries 0 .. r, padded to 4) at rowoff(r).
+__host__ __device__ constexpr int rowoff(int r) {
+    return 8 * (r >> 2) * ((r >> 2) + 1) + 4 * (r & 3) * ((r >> 2) + 1);
+}
+// Packed lower triangle by columns: column p holds rows colbase(p) .. 31 at coloff(p).
+__host__ __device__ constexpr int colbase(int p) { return 4 * (p >> 2); }
+__host__ __device__ constexpr int coloff(int p) {
+    return 128 * (p >> 2) - 8 * (p >> 2) * ((p >> 2) - 1) + (p & 3) * (32 - 4 * (p >> 2));
+}
+static_assert(rowoff(32) == NPACK && coloff(32) == NPACK, "packed triangle size");
+
+// Per warp: the staging buffers of the Gram phase overlay the solve area of
+// the pair (L of both rows, A and b of the second row, solution scratch); A
+// and b of the first row sit outside, because they are written while the
+// second row's observations still stream into the staging buffers.
 template <bool BF> struct alignas(16) Smem32 {
     static constexpr int ROWB = (BF ? 2 : 4) * (KP + 8);   // padded staged row (bytes)
     struct alignas(16) Stage {
-        alignas(16) unsigned char stage[NST][BF ? 2 : 1][32][ROWB];
-        float sr[NST][32];
+        alignas(16) unsigned char stage[2][BF ? 2 : 1][32][ROWB];
+        float sr[2][32];
     };
     struct alignas(16) Solve {
-        float G[KP][LDA];    // A = Gram + lambda I, both triangles
-        float Lc[KP][LDA];   // Lc[p][r] = L[r][p] for r >= p; Lc[p][32] = y_p
-        float b[KP];
-        float x[KP];
+        float A1[NPACK];      // A = Gram + lambda I of the second row, lower triangle by rows
+        float L[2][NPACK];    // the Cholesky factors by columns
+        float b1[KP];
+        float x[2][KP];
+        float inv[2][KP];     // 1 / L_pp
     };
     union {
         Stage ld;
         Solve sv;
     };
+    float A0[NPACK];          // A and b of the first row
+    float b0[KP];
+    __device__ float *A(int h) { return h ? sv.A1 : A0; }
+    __device__ float *b(int h) { return h ? sv.b1 : b0; }
 };
 
 // lower-triangle 16x8 blocks of the 32x32 Gram: (mb, nb) = (0,0) (0,1) (1,0..3)
@@ -78,13 +104,13 @@ __device__ __forceinline__ void fma2_sub(float &a0, float &a1, float l, float c0
     a1 = r.y;
 }
 
-// Error-free accumulation of s - g * x on two independent chains (the two
+// Error-free accumulation of S - g * x on two independent chains (the two
 // halves of a packed register): (S, C) is a double-FP32 value per chain.
 __device__ __forceinline__ void dot2_sub(float2 &S, float2 &C, float2 g, float2 x) {
     const float2 P = __fmul2_rn(g, x);
-    const float2 E = __ffma2_rn(g, x, make_float2(-P.x, -P.y));   // g x - P, exact
     const float2 nP = make_float2(-P.x, -P.y);
-    const float2 T = __fadd2_rn(S, nP);                              // two-sum(S, -P)
+    const float2 E = __ffma2_rn(g, x, nP);                  // g x - P, exact
+    const float2 T = __fadd2_rn(S, nP);                     // two-sum(S, -P)
     const float2 Z = __fadd2_rn(T, make_float2(-S.x, -S.y));
     const float2 TZ = __fadd2_rn(T, make_float2(-Z.x, -Z.y));
     const float2 e1 = __fadd2_rn(S, make_float2(-TZ.x, -TZ.y));
@@ -94,63 +120,74 @@ __device__ __forceinline__ void dot2_sub(float2 &S, float2 &C, float2 g, float2 
     S = T;
 }
 
-// r_q = b_q - sum_e A[q][e] x_e in double-FP32; also |A row q|^2 (FP32).
-template <typename WS>
-__device__ __forceinline__ float ext_residual(const WS &W, int q, float bq, float &aa) {
-    const float4 *g4 = reinterpret_cast<const float4 *>(W.sv.G[q]);
-    const float4 *x4 = reinterpret_cast<const float4 *>(W.sv.x);
-    float2 S0 = make_float2(bq, 0.f), C0 = make_float2(0.f, 0.f);
-    float2 S1 = make_float2(0.f, 0.f), C1 = make_float2(0.f, 0.f);
-    float2 A2 = make_float2(0.f, 0.f);
+// Sum over the 16 lanes of a half-warp.
+__device__ __forceinline__ float half_sum(float v) {
 #pragma unroll
-    for (int e4 = 0; e4 < KP / 4; ++e4) {
-        const float4 g = g4[e4], x = x4[e4];
-        dot2_sub(S0, C0, make_float2(g.x, g.y), make_float2(x.x, x.y));
-        dot2_sub(S1, C1, make_float2(g.z, g.w), make_float2(x.z, x.w));
-        A2 = __ffma2_rn(make_float2(g.x, g.y), make_float2(g.x, g.y), A2);
-        A2 = __ffma2_rn(make_float2(g.z, g.w), make_float2(g.z, g.w), A2);
-    }
-    aa = A2.x + A2.y;
-    // combine the four chains: hi parts by two-sums, lo parts plainly
-    float hi = S0.x, lo = C0.x + C0.y + C1.x + C1.y;
-    const float parts[3] = {S0.y, S1.x, S1.y};
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        const float T = hi + parts[t];
-        const float Z = T - hi;
-        lo += (hi - (T - Z)) + (parts[t] - Z);
-        hi = T;
-    }
-    return hi + lo;
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    for (int off = 8; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
     return v;
 }
 
-// L^T x = y for lane q's component: column q of L (L[r][q], r >= q) is loaded
-// into registers, then x_p is formed on lane p and broadcast, p = 31 .. 0.
-template <typename WS>
-__device__ __forceinline__ float back_subst(const WS &W, int q, float yq, float myinv) {
-    float c[KP];
-    const float4 *c4 = reinterpret_cast<const float4 *>(W.sv.Lc[q]);
+// Rows r0 = i and r1 = i + 16 of b - A x (A symmetric from its packed lower
+// triangle, x from shared memory) in double-FP32, as the two chains of packed
+// instructions; also |row|^2 of both rows.
+__device__ __forceinline__ float2 ext_residual(const float *A, const float *x, int i,
+                                               float2 bq, float2 &aa) {
+    const int r0 = i, r1 = i + 16;
+    const int o0 = rowoff(r0), o1 = rowoff(r1);
+    float2 S = bq, C = make_float2(0.f, 0.f), A2 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int e4 = 0; e4 < KP / 4; ++e4) {
-        const float4 v = c4[e4];
-        c[4 * e4] = v.x;
-        c[4 * e4 + 1] = v.y;
-        c[4 * e4 + 2] = v.z;
-        c[4 * e4 + 3] = v.w;
+    for (int e = 0; e < KP; ++e) {
+        const float g0 = A[e <= r0 ? o0 + e : rowoff(e) + r0];
+        const float g1 = A[e <= r1 ? o1 + e : rowoff(e) + r1];
+        const float xe = x[e];
+        const float2 g = make_float2(g0, g1);
+        dot2_sub(S, C, g, make_float2(xe, xe));
+        A2 = __ffma2_rn(g, g, A2);
     }
-    float x = yq;
+    aa = A2;
+    return make_float2(S.x + C.x, S.y + C.y);
+}
+
+// L^T x = y for the two components (i, i + 16) a lane holds: columns i and
+// i + 16 of L are loaded into registers, then x_p is formed on its lane and
+// broadcast within the half-warp, p = 31 .. 0.  y arrives divided by nothing;
+// the result is the solution.
+__device__ __forceinline__ float2 back_subst(const float *L, int i, float y0, float y1,
+                                             float inv0, float inv1) {
+    float c0[KP], c1[16];
+    {
+        const float4 *q0 = reinterpret_cast<const float4 *>(L + coloff(i) - colbase(i));
 #pragma unroll
-    for (int p = KP - 1; p >= 0; --p) {
-        const float xp = __shfl_sync(FULL, x * myinv, p);
-        if (q < p) x = fmaf(-c[p], xp, x);
+        for (int t = 0; t < KP / 4; ++t) {
+            const float4 v = q0[t];
+            c0[4 * t] = v.x;
+            c0[4 * t + 1] = v.y;
+            c0[4 * t + 2] = v.z;
+            c0[4 * t + 3] = v.w;
+        }
+        const float4 *q1 = reinterpret_cast<const float4 *>(L + coloff(i + 16) - colbase(i + 16));
+#pragma unroll
+        for (int t = 4; t < KP / 4; ++t) {
+            const float4 v = q1[t];
+            c1[4 * t - 16] = v.x;
+            c1[4 * t - 15] = v.y;
+            c1[4 * t - 14] = v.z;
+            c1[4 * t - 13] = v.w;
+        }
     }
-    return x * myinv;
+    float x0 = y0, x1 = y1;
+#pragma unroll
+    for (int p = KP - 1; p >= 16; --p) {
+        const float xp = __shfl_sync(FULL, x1 * inv1, p - 16, 16);
+        x0 = fmaf(-c0[p], xp, x0);
+        if (i + 16 < p) x1 = fmaf(-c1[p - 16], xp, x1);
+    }
+#pragma unroll
+    for (int p = 15; p >= 0; --p) {
+        const float xp = __shfl_sync(FULL, x0 * inv0, p, 16);
+        if (i < p) x0 = fmaf(-c0[p], xp, x0);
+    }
+    return make_float2(x0 * inv0, x1 * inv1);
 }
 
 template <bool BF>
@@ -236,228 +273,362 @@ __device__ __forceinline__ void gram_item(const Smem32<BF> &W, int buf, int cnt,
     }
 }
 
+// A row pair's CSR bounds and the first two 32-observation items of each
+// row (this lane's column index and value in each), loaded into registers one
+// pair ahead.
+struct PairFetch {
+    int64_t beg[2], s[2], row[2];   // row < 0: no system (odd row count)
+    bool bad[2];
+    int32_t j[4];                   // item order: row 0 item 0, item 1, row 1 item 0, item 1
+    float v[4];
+};
+
+__device__ __forceinline__ void fetch_pair(const SolveArgs<float> &a, int64_t k, int64_t M,
+                                           int lane, PairFetch &f) {
+#pragma unroll
+    for (int si = 0; si < 2; ++si) {
+        const int64_t is = 2 * k + si;
+        int64_t beg = 0, end = 0, row = -1;
+        bool bad = false;
+        if (is < M) {
+            row = a.row_map ? a.row_map[is] : is;
+            bad = !row_bounds(a.ptr, row, a.nnz, beg, end);
+        }
+        f.beg[si] = beg;
+        f.s[si] = end - beg;
+        f.row[si] = row;
+        f.bad[si] = bad;
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const int64_t t = 32 * it + lane;
+            int32_t j = 0;
+            float v = 0.f;
+            if (t < end - beg) {
+                j = __ldg(a.idx + beg + t);
+                v = __ldg(a.val + beg + t);
+            }
+            f.j[2 * si + it] = j;
+            f.v[2 * si + it] = v;
+        }
+    }
+}
+
 template <bool BF>
 __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a) {
     using WS = Smem32<BF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gid = lane >> 2, tid4 = lane & 3;
-    const int q = lane;
+    const int h = lane >> 4, i = lane & 15;   // solve phase: system h of the pair, rows i, i + 16
     WS &W = reinterpret_cast<WS *>(smem_raw)[warp];
     pdl_trigger();
     if (a.m_dev || a.row_map) pdl_wait();         // the list comes from the preceding kernel
     const int64_t M = a.m_dev ? *a.m_dev : a.m;
-    const int64_t stride = (int64_t)gridDim.x * WARPS;
+    const int64_t P = (M + 1) / 2;                // row pairs
+    const int64_t G = (int64_t)gridDim.x * WARPS, gw = (int64_t)blockIdx.x * WARPS + warp;
+    const int64_t k0 = P * gw / G, k1 = P * (gw + 1) / G;
+    PairFetch cur;
+    if (k0 < k1) fetch_pair(a, k0, M, lane, cur);
 
-    for (int64_t is = (int64_t)blockIdx.x * WARPS + warp; is < M; is += stride) {
-        const int64_t row = a.row_map ? a.row_map[is] : is;
-        int64_t beg = 0, end = 0;
-        bool bad = !row_bounds(a.ptr, row, a.nnz, beg, end);
-        const int64_t s = end - beg;
-        const int nitems = (int)((s + 31) / 32);
-        bool badf = false;
-
-        // ---------------- Gram phase --------------------------------------
-        auto load_idx = [&](int w) -> int32_t {
-            const int64_t t = (int64_t)w * 32 + lane;
-            int32_t j = 0;
-            if (t < s) {
-                j = __ldg(a.idx + beg + t);
-                if (j < 0 || (int64_t)j >= a.n_other) {
-                    badf = true;
-                    j = 0;
+    for (int64_t k = k0; k < k1; ++k) {
+        // ---------------- Gram phase: both rows' items, one after the other
+        const int n0 = (int)((cur.s[0] + 31) / 32), n1 = (int)((cur.s[1] + 31) / 32);
+        const int nit = n0 + n1;
+        bool badf0 = false, badf1 = false;
+        // column index and value of this lane's observation in item w
+        auto item_jv = [&](int w, int32_t &j, float &v, int &buf_si) {
+            const int si = w < n0 ? 0 : 1;
+            const int loc = w - (si ? n0 : 0);
+            buf_si = si;
+            const int64_t t = (int64_t)loc * 32 + lane;
+            const int64_t ss = si ? cur.s[1] : cur.s[0];
+            if (loc < 2) {
+                const int slot = 2 * si + loc;
+                j = slot == 0 ? cur.j[0] : slot == 1 ? cur.j[1] : slot == 2 ? cur.j[2] : cur.j[3];
+                v = slot == 0 ? cur.v[0] : slot == 1 ? cur.v[1] : slot == 2 ? cur.v[2] : cur.v[3];
+            } else {
+                j = 0;
+                v = 0.f;
+                if (t < ss) {
+                    const int64_t bg = si ? cur.beg[1] : cur.beg[0];
+                    j = __ldg(a.idx + bg + t);
+                    v = __ldg(a.val + bg + t);
                 }
             }
-            return j;
+            if (t < ss && (j < 0 || (int64_t)j >= a.n_other)) {
+                if (si) badf1 = true; else badf0 = true;
+                j = 0;
+                v = 0.f;
+            }
+            return t < ss;
         };
-        auto issue = [&](int w, int32_t j, int buf) {
-            const int64_t t = (int64_t)w * 32 + lane;
-            const bool v = t < s;
+        auto issue = [&](int w, int buf) {
+            int32_t j;
+            float v;
+            int si;
+            const bool ok = item_jv(w, j, v, si);
             if constexpr (BF) {
                 const unsigned char *src =
                     reinterpret_cast<const unsigned char *>(a.Fb) + (int64_t)j * KP * 4;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, v ? 16 : 0);
-                    cp_async16(&W.ld.stage[buf][1][lane][16 * e], src + 2 * KP + 16 * e, v ? 16 : 0);
+                    cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, ok ? 16 : 0);
+                    cp_async16(&W.ld.stage[buf][1][lane][16 * e], src + 2 * KP + 16 * e, ok ? 16 : 0);
                 }
             } else {
                 const unsigned char *src = reinterpret_cast<const unsigned char *>(a.F + (int64_t)j * KP);
 #pragma unroll
                 for (int e = 0; e < 8; ++e)
-                    cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, v ? 16 : 0);
+                    cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, ok ? 16 : 0);
             }
-            cp_async4(&W.ld.sr[buf][lane], v ? (const void *)(a.val + beg + t) : (const void *)a.val,
-                      v ? 4 : 0);
+            W.ld.sr[buf][lane] = ok ? v : 0.f;
         };
-        float d[6][4], dr[2][4];
-#pragma unroll
-        for (int t = 0; t < 6; ++t)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) d[t][e] = 0.f;
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
         pdl_wait();   // from here on the other factor is read
-        if (nitems > 0) {
-            issue(0, load_idx(0), 0);
-            cp_async_commit();
-            int32_t jn = nitems > 1 ? load_idx(1) : 0;
-            for (int w = 0; w < nitems; ++w) {
-                if (w + 1 < nitems) issue(w + 1, jn, (w + 1) & 1);
+        // fragments of one row -> its packed lower triangle of A, and b
+        auto write_sys = [&](float *Ap, float *bp, const float (&d)[6][4], const float (&dr)[2][4]) {
+#pragma unroll
+            for (int tb = 0; tb < 6; ++tb) {
+                const int mb = mb_of(tb), nb = nb_of(tb);
+                const int r0 = mb * 16 + gid, c = nb * 8 + 2 * tid4;
+                const bool diag = (mb == 0) || (nb >= 2);   // diagonal 16x16 block
+                const int o0 = rowoff(r0), o8 = rowoff(r0 + 8);
+                if (!diag || c <= r0) Ap[o0 + c] = d[tb][0];
+                if (!diag || c + 1 <= r0) Ap[o0 + c + 1] = d[tb][1];
+                if (!diag || c <= r0 + 8) Ap[o8 + c] = d[tb][2];
+                if (!diag || c + 1 <= r0 + 8) Ap[o8 + c + 1] = d[tb][3];
+            }
+            if (tid4 == 0) {
+#pragma unroll
+                for (int mb = 0; mb < 2; ++mb) {
+                    bp[mb * 16 + gid] = dr[mb][0];
+                    bp[mb * 16 + gid + 8] = dr[mb][2];
+                }
+            }
+        };
+        // items of one row, the next item (possibly the other row's first) staged
+        // while this one is on the tensor cores
+        auto run_items = [&](int w0, int w1, int64_t ss, float (&d)[6][4], float (&dr)[2][4]) {
+            for (int w = w0; w < w1; ++w) {
+                if (w + 1 < nit) issue(w + 1, (w + 1) & 1);
                 cp_async_commit();
-                jn = (w + 2 < nitems) ? load_idx(w + 2) : 0;
                 cp_async_wait<1>();
                 __syncwarp();
-                const int cnt = (int)min((int64_t)32, s - (int64_t)w * 32);
+                const int cnt = (int)min((int64_t)32, ss - (int64_t)(w - w0) * 32);
                 gram_item<BF>(W, w & 1, cnt, d, dr, lane);
                 __syncwarp();   // this buffer is refilled two items later
             }
+        };
+        if (nit > 0) {
+            issue(0, 0);
+            cp_async_commit();
         }
-        cp_async_wait<0>();   // nothing in flight before the solve area overlays the stages
-        __syncwarp();
-        // fragments -> A (both triangles) and b
-#pragma unroll
-        for (int tb = 0; tb < 6; ++tb) {
-            const int mb = mb_of(tb), nb = nb_of(tb);
-            const int r0 = mb * 16 + gid, c = nb * 8 + 2 * tid4;
-            W.sv.G[r0][c] = d[tb][0];
-            W.sv.G[r0][c + 1] = d[tb][1];
-            W.sv.G[r0 + 8][c] = d[tb][2];
-            W.sv.G[r0 + 8][c + 1] = d[tb][3];
-            if (mb == 1 && nb < 2) {
-                W.sv.G[c][r0] = d[tb][0];
-                W.sv.G[c + 1][r0] = d[tb][1];
-                W.sv.G[c][r0 + 8] = d[tb][2];
-                W.sv.G[c + 1][r0 + 8] = d[tb][3];
-            }
-        }
-        if (tid4 == 0) {
-#pragma unroll
-            for (int mb = 0; mb < 2; ++mb) {
-                W.sv.b[mb * 16 + gid] = dr[mb][0];
-                W.sv.b[mb * 16 + gid + 8] = dr[mb][2];
-            }
-        }
-        bad = bad || (__any_sync(FULL, badf) != 0);
-        __syncwarp();
-        const float lam = float(a.lambda) * (a.wr ? float(s) : 1.f);   // weighted: lambda s_i
-        W.sv.G[q][q] += lam;
-        __syncwarp();
-        float ar[KP];
         {
-            const float4 *g4 = reinterpret_cast<const float4 *>(W.sv.G[q]);
+            float d[6][4], dr[2][4];
 #pragma unroll
-            for (int e4 = 0; e4 < KP / 4; ++e4) {
-                const float4 v = g4[e4];
-                ar[4 * e4] = v.x;
-                ar[4 * e4 + 1] = v.y;
-                ar[4 * e4 + 2] = v.z;
-                ar[4 * e4 + 3] = v.w;
-            }
+            for (int t = 0; t < 6; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) d[t][e] = 0.f;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
+            run_items(0, n0, cur.s[0], d, dr);
+            write_sys(W.A0, W.b0, d, dr);   // outside the staging area
         }
-        const float bq = W.sv.b[q];
-
-        float xq, myinv = 0.f;
+        {
+            float d[6][4], dr[2][4];
+#pragma unroll
+            for (int t = 0; t < 6; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) d[t][e] = 0.f;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
+            run_items(n0, nit, cur.s[1], d, dr);
+            cp_async_wait<0>();   // nothing in flight before the solve area overlays the stages
+            __syncwarp();
+            write_sys(W.sv.A1, W.sv.b1, d, dr);
+        }
+        const PairFetch pf = cur;
+        const bool bad0 = pf.bad[0] || (__any_sync(FULL, badf0) != 0);
+        const bool bad1 = pf.bad[1] || (__any_sync(FULL, badf1) != 0);
+        __syncwarp();
+        // ---------------- solve phase: half h solves system h
+        float *SA = W.A(h), *SL = W.sv.L[h], *Sx = W.sv.x[h], *Sinv = W.sv.inv[h];
+        const int64_t s = h ? pf.s[1] : pf.s[0];
+        const int64_t row = h ? pf.row[1] : pf.row[0];
+        const bool bad = h ? bad1 : bad0;
+        const float lam = float(a.lambda) * (a.wr ? float(s) : 1.f);   // weighted: lambda s_i
+        SA[rowoff(i) + i] += lam;
+        SA[rowoff(i + 16) + i + 16] += lam;
+        __syncwarp();
+        const float2 bq = make_float2(W.b(h)[i], W.b(h)[i + 16]);
+        float x0, x1, inv0 = 0.f, inv1 = 0.f;
         if (!a.u_given) {
+            float a0[16], a1[KP];
+            {
+                const float4 *q0 = reinterpret_cast<const float4 *>(SA + rowoff(i));
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float4 v = q0[t];
+                    a0[4 * t] = v.x;
+                    a0[4 * t + 1] = v.y;
+                    a0[4 * t + 2] = v.z;
+                    a0[4 * t + 3] = v.w;
+                }
+                const float4 *q1 = reinterpret_cast<const float4 *>(SA + rowoff(i + 16));
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float4 v = q1[t];
+                    a1[4 * t] = v.x;
+                    a1[4 * t + 1] = v.y;
+                    a1[4 * t + 2] = v.z;
+                    a1[4 * t + 3] = v.w;
+                }
+            }
             // ---- Cholesky A = L L^T with the forward substitution L y = b
-            float y = bq;
+            float y0 = bq.x, y1 = bq.y;
 #pragma unroll
             for (int p = 0; p < KP; ++p) {
-                const float piv = __shfl_sync(FULL, ar[p], p);
+                const float piv = p < 16 ? __shfl_sync(FULL, a0[p & 15], p, 16)
+                                         : __shfl_sync(FULL, a1[p], p - 16, 16);
                 const float inv = rsqrtf(piv);
-                if (q == p) myinv = inv;
-                const float l = ar[p] * inv;
-                ar[p] = l;
-                float *cp = W.sv.Lc[p];
-                cp[q] = l;
-                if (q == p) cp[32] = y * inv;
+                float *Lc = SL + coloff(p) - colbase(p);   // Lc[r] = L[r][p]
+                float l0 = 0.f;
+                if (p < 16) {
+                    l0 = a0[p & 15] * inv;
+                    a0[p & 15] = l0;
+                    if (i >= colbase(p)) Lc[i] = l0;
+                }
+                const float l1 = a1[p] * inv;
+                a1[p] = l1;
+                if (colbase(p) <= 16 || i + 16 >= colbase(p)) Lc[i + 16] = l1;
+                if (i == 0) Sinv[p] = inv;
+                const float yp = (p < 16 ? __shfl_sync(FULL, y0, p, 16)
+                                         : __shfl_sync(FULL, y1, p - 16, 16)) * inv;
+                if (p < 16) {
+                    if (i > p) y0 = fmaf(-l0, yp, y0);
+                    y1 = fmaf(-l1, yp, y1);
+                } else {
+                    if (i + 16 > p) y1 = fmaf(-l1, yp, y1);
+                }
                 __syncwarp();
-                const float yp = cp[32];
-                if (q > p) y = fmaf(-l, yp, y);
-                // trailing update a[r] -= l * L[r][p], r > p, from 16-byte loads of column p
+                // trailing update: row i over columns (p, 16), row i + 16 over (p, 32)
 #pragma unroll
                 for (int r4 = ((p + 1) / 4) * 4; r4 < KP; r4 += 4) {
-                    const float4 c4 = *reinterpret_cast<const float4 *>(cp + r4);
+                    const float4 c4 = *reinterpret_cast<const float4 *>(Lc + r4);
                     const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-                    if (r4 > p) {
-                        fma2_sub(ar[r4], ar[r4 + 1], l, cv[0], cv[1]);
-                        fma2_sub(ar[r4 + 2], ar[r4 + 3], l, cv[2], cv[3]);
-                    } else {
 #pragma unroll
-                        for (int e = 0; e < 4; e += 2) {
-                            const int r = r4 + e;
-                            if (r > p) {
-                                fma2_sub(ar[r], ar[r + 1], l, cv[e], cv[e + 1]);
-                            } else if (r + 1 > p) {
-                                ar[r + 1] = fmaf(-l, cv[e + 1], ar[r + 1]);
-                            }
+                    for (int e = 0; e < 4; e += 2) {
+                        const int r = r4 + e;
+                        if (r > p) {
+                            fma2_sub(a1[r], a1[r + 1], l1, cv[e], cv[e + 1]);
+                            if (p < 16 && r < 16) fma2_sub(a0[r & 15], a0[(r + 1) & 15], l0, cv[e], cv[e + 1]);
+                        } else if (r + 1 > p) {
+                            a1[r + 1] = fmaf(-l1, cv[e + 1], a1[r + 1]);
+                            if (p < 16 && r + 1 < 16) a0[(r + 1) & 15] = fmaf(-l0, cv[e + 1], a0[(r + 1) & 15]);
                         }
                     }
                 }
             }
-            const float yq = y * myinv;
+            // the factor is done: fetch the next pair's bounds, indices and values
+            // while the substitutions and the residual run
+            if (k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);
+            inv0 = Sinv[i];
+            inv1 = Sinv[i + 16];
             // ---- back substitution L^T x = y
-            xq = back_subst(W, q, yq, myinv);
+            const float2 xx = back_subst(SL, i, y0 * inv0, y1 * inv1, inv0, inv1);
+            x0 = xx.x;
+            x1 = xx.y;
         } else {
-            xq = (q < a.kout) ? a.u_given[row * a.ldo + q] : 0.f;
+            if (k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);
+            x0 = (i < a.kout && row >= 0) ? a.u_given[row * a.ldo + i] : 0.f;
+            x1 = (i + 16 < a.kout && row >= 0) ? a.u_given[row * a.ldo + i + 16] : 0.f;
         }
-        bool fail = !isfinite(xq);
-        fail = __any_sync(FULL, fail) != 0;
+        const unsigned fb = __ballot_sync(FULL, !isfinite(x0) || !isfinite(x1));
+        const bool fail = ((fb >> (16 * h)) & 0xffffu) != 0u;
         int32_t st = ST_OK;
         if (bad) st = ST_BAD;
         else if (s == 0) st = ST_EMPTY;
         else if (fail && !a.u_given) st = ST_NOT_SPD;
-        if (st != ST_OK && !a.u_given) xq = 0.f;
+        if (st != ST_OK && !a.u_given) x0 = x1 = 0.f;
 
         // ---- residual |A u - b| / (|A|_F |u| + |b|), optional refinement
         float rel = -1.f;
-        if ((a.resid || a.refine) && (st == ST_OK || a.u_given)) {
-            W.sv.x[q] = xq;
+        const bool want = (a.resid || a.refine) && (st == ST_OK || a.u_given);
+        if (__any_sync(FULL, want)) {   // both halves run the same instructions
+            Sx[i] = x0;
+            Sx[i + 16] = x1;
             __syncwarp();
-            float aa;
-            float r = ext_residual(W, q, bq, aa);
+            float2 aa;
+            float2 r = ext_residual(SA, Sx, i, bq, aa);
             if (a.refine && !a.u_given) {
-                // A d = r with the FP32 factor: L z = r (L[q][p] = Lc[p][q]), L^T d = z
-                float z = r;
+                // A d = r with the FP32 factor: L z = r (L[q][p] = column p, row q), L^T d = z
+                // (both halves run it: the shuffles need the whole warp)
+                float z0 = r.x, z1 = r.y;
 #pragma unroll
                 for (int p = 0; p < KP; ++p) {
-                    const float zp = __shfl_sync(FULL, z * myinv, p);
-                    if (q > p) z = fmaf(-W.sv.Lc[p][q], zp, z);
+                    const float *Lc = SL + coloff(p) - colbase(p);
+                    if (p < 16) {
+                        const float zp = __shfl_sync(FULL, z0 * inv0, p, 16);
+                        if (i > p) z0 = fmaf(-Lc[i], zp, z0);
+                        z1 = fmaf(-Lc[i + 16], zp, z1);
+                    } else {
+                        const float zp = __shfl_sync(FULL, z1 * inv1, p - 16, 16);
+                        if (i + 16 > p) z1 = fmaf(-Lc[i + 16], zp, z1);
+                    }
                 }
-                xq = xq + back_subst(W, q, z * myinv, myinv);
+                const float2 dd = back_subst(SL, i, z0 * inv0, z1 * inv1, inv0, inv1);
+                if (want) {
+                    x0 += dd.x;
+                    x1 += dd.y;
+                }
+            }
+            if (a.refine && !a.u_given) {
                 __syncwarp();   // every lane has read x before it is rewritten
-                W.sv.x[q] = xq;
+                if (want) {
+                    Sx[i] = x0;
+                    Sx[i + 16] = x1;
+                }
                 __syncwarp();
-                r = ext_residual(W, q, bq, aa);
+                r = ext_residual(SA, Sx, i, bq, aa);
             }
-            // |A|_F over the k x k system: the padded rows (q >= k) hold only lambda
-            const float rr = warp_sum(r * r), na = warp_sum(q < a.kout ? aa : 0.f),
-                        nu = warp_sum(xq * xq), nb = warp_sum(bq * bq);
+            // |A|_F over the k x k system: padded rows (q >= k) hold only lambda
+            const float rr = half_sum(r.x * r.x + r.y * r.y);
+            const float na = half_sum((i < a.kout ? aa.x : 0.f) + (i + 16 < a.kout ? aa.y : 0.f));
+            const float nu = half_sum(x0 * x0 + x1 * x1);
+            const float nb = half_sum(bq.x * bq.x + bq.y * bq.y);
             const float den = sqrtf(na) * sqrtf(nu) + sqrtf(nb);
-            rel = den > 0.f ? sqrtf(rr) / den : 0.f;
+            if (want) rel = den > 0.f ? sqrtf(rr) / den : 0.f;
         }
-        if (!a.u_given) {
-            if (q < a.kout) a.out[row * a.ldo + q] = xq;
-            if (a.outb) {   // split BF16 copy [hi | lo] of the output row
-                const __nv_bfloat16 hi = __float2bfloat16_rn(xq);
-                __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.outb) + row * 2 * KP;
-                ob[q] = hi;
-                ob[KP + q] = __float2bfloat16_rn(xq - __bfloat162float(hi));
+        if (row >= 0) {
+            if (!a.u_given) {
+                if (i < a.kout) a.out[row * a.ldo + i] = x0;
+                if (i + 16 < a.kout) a.out[row * a.ldo + i + 16] = x1;
+                if (a.outb) {   // split BF16 copy [hi | lo] of the output row
+                    __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.outb) + row * 2 * KP;
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                    ob[i] = h0;
+                    ob[i + 16] = h1;
+                    ob[KP + i] = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                    ob[KP + i + 16] = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                }
+                if (a.status && i == 0) a.status[row] = st;
             }
-            if (a.status && q == 0) a.status[row] = st;
+            if (a.resid && i == 0) a.resid[row] = rel;
         }
-        if (a.resid && q == 0) a.resid[row] = rel;
-        __syncwarp();   // the shared area is restaged by the next system
+        __syncwarp();   // the shared area is restaged by the next pair
     }
 }
 
 template <bool BF> size_t smem_bytes() { return sizeof(Smem32<BF>) * WARPS; }
 
 template <bool BF> cudaError_t launch32(const SolveArgs<float> &a, cudaStream_t st) {
-    int64_t blocks = (a.m + WARPS - 1) / WARPS;
-    if (blocks > NUM_SMS_HINT * 32) blocks = NUM_SMS_HINT * 32;
+    // a persistent grid: at most two CTAs per SM, each warp a contiguous range of row pairs
+    const int64_t pairs = (a.m + 1) / 2;
+    int64_t blocks = (pairs + WARPS - 1) / WARPS;
+    if (blocks > NUM_SMS_HINT * 2) blocks = NUM_SMS_HINT * 2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3(32 * WARPS);
