@@ -76,12 +76,17 @@ template <bool BF> struct alignas(16) Smem32 {
         alignas(16) unsigned char stage[2][BF ? 2 : 1][32][ROWB];
         float sr[2][32];
     };
+    // The two halves of the warp touch the same offsets of their own row's
+    // arrays at once, so the second row's copy of each array starts 16 banks
+    // after the first row's (strides of 16 mod 32 words): conflict-free.
+    static constexpr int LS = NPACK + 16, XS = KP + 16;
     struct alignas(16) Solve {
-        float A1[NPACK];      // A = Gram + lambda I of the second row, lower triangle by rows
-        float L[2][NPACK];    // the Cholesky factors by columns
+        float L[2 * LS];      // the Cholesky factors by columns (second row's at LS)
+        float x[2 * XS];
+        float inv[2 * XS];    // 1 / L_pp
         float b1[KP];
-        float x[2][KP];
-        float inv[2][KP];     // 1 / L_pp
+        float pad[16];        // puts A1 16 banks from A0
+        float A1[NPACK];      // A = Gram + lambda I of the second row, lower triangle by rows
     };
     union {
         Stage ld;
@@ -91,6 +96,9 @@ template <bool BF> struct alignas(16) Smem32 {
     float b0[KP];
     __device__ float *A(int h) { return h ? sv.A1 : A0; }
     __device__ float *b(int h) { return h ? sv.b1 : b0; }
+    __device__ float *Lf(int h) { return sv.L + h * LS; }
+    __device__ float *xv(int h) { return sv.x + h * XS; }
+    __device__ float *iv(int h) { return sv.inv + h * XS; }
 };
 
 // lower-triangle 16x8 blocks of the 32x32 Gram: (mb, nb) = (0,0) (0,1) (1,0..3)
@@ -455,7 +463,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
         const bool bad1 = pf.bad[1] || (__any_sync(FULL, badf1) != 0);
         __syncwarp();
         // ---------------- solve phase: half h solves system h
-        float *SA = W.A(h), *SL = W.sv.L[h], *Sx = W.sv.x[h], *Sinv = W.sv.inv[h];
+        float *SA = W.A(h), *SL = W.Lf(h), *Sx = W.xv(h), *Sinv = W.iv(h);
         const int64_t s = h ? pf.s[1] : pf.s[0];
         const int64_t row = h ? pf.row[1] : pf.row[0];
         const bool bad = h ? bad1 : bad0;
