@@ -38,7 +38,7 @@ using namespace tc;
 
 constexpr int TM = 128, CN = 256, KPT = 32;
 constexpr int NEPI = 16;                       // epilogue warps
-constexpr int GS = 16;                         // settings per TMEM load and screening group
+constexpr int GS = 32;                         // settings per TMEM load and screening group
 constexpr int NCQ = NEPI / 4;                  // column groups (warps per TMEM lane quarter)
 constexpr int CPW = CN / NCQ;                  // settings per epilogue warp and chunk
 constexpr int PRODUCER = NEPI, ISSUER = NEPI + 1;
@@ -51,7 +51,9 @@ constexpr uint32_t OFF_UL = OFF_UH + TM * KPT * 2;         // U lo image
 constexpr uint32_t OFF_TB = OFF_UL + TM * KPT * 2;         // t_b per row
 constexpr uint32_t OFF_CAND = OFF_TB + TM * 4;             // [TM][4] candidates
 constexpr uint32_t OFF_BAR = OFF_CAND + TM * 4 * sizeof(Cand);
-constexpr uint32_t OFF_CG = OFF_BAR + 128;                 // c + g table (when it fits)
+constexpr int STASH_LD = GS + 4;                           // floats per lane: 144 B, conflict-free rows
+constexpr uint32_t OFF_STASH = OFF_BAR + 128;              // per lane: the group's runtimes
+constexpr uint32_t OFF_CG = OFF_STASH + NEPI * 32 * STASH_LD * 4;   // c + g table (when it fits)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int BAR_TILE = 1, BAR_EPI = 2;                    // named barriers
 
@@ -67,8 +69,8 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 // still win or tie, the exact evaluation of the elements within the bound.
 // The lanes of a warp hold different rows, so an exact evaluation taken by one
 // lane is paid by all; once a row has a best, few groups pass its threshold.
-__device__ __forceinline__ void store16(const uint32_t (&v)[GS], float *trow, int64_t j0,
-                                        int64_t n, bool vec) {
+__device__ __forceinline__ void store_group(const uint32_t (&v)[GS], float *trow, int64_t j0,
+                                            int64_t n, bool vec) {
     if (vec && j0 + GS <= n) {
 #pragma unroll
         for (int e = 0; e < GS; e += 4)
@@ -80,13 +82,6 @@ __device__ __forceinline__ void store16(const uint32_t (&v)[GS], float *trow, in
         for (int e = 0; e < GS; ++e)
             if (j0 + e < n) trow[j0 + e] = __uint_as_float(v[e]);
     }
-}
-
-// The rare second-pass evaluations go through a call, so that 32 inlined
-// copies of the exact evaluation do not crowd the instruction cache.
-__device__ __noinline__ void exact_call(Cand &best, const RowCtx &rc, float t, float c, float Eb,
-                                        int32_t j) {
-    alg2_exact(best, rc, t, c, Eb, j);
 }
 
 // chunk processed at position s of a tile: the baseline's chunk first
@@ -179,6 +174,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
         float *tb_s = reinterpret_cast<float *>(sm + OFF_TB);
         Cand *cand_s = reinterpret_cast<Cand *>(sm + OFF_CAND);
         const int col_b = (int)(a.base - (int64_t)cb * CN);
+        float *stash_s = reinterpret_cast<float *>(sm + OFF_STASH);
+        const float inf = __int_as_float(0x7f800000);
+        auto cg_of = [&](int64_t j) { return cg_smem ? cg_s[j] : a.cg_pad[j]; };
         int64_t g = 0;
         for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
             const int64_t row0 = tile * TM;
@@ -209,6 +207,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
 
             const int64_t i = row0 + r;
             RowCtx rc{0.0f, -1.0f, 0.0f};
+            uint32_t tsb = 0u;   // bit pattern of t*: valid runtimes are <= it
             Cand best{0.0f, 0.0f, -1, 0.0f};
             for (int s = 0; s < nch; ++s, ++g) {
                 const int ab = (int)(g & 1);
@@ -224,13 +223,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                         tb_s[r] = __uint_as_float(tb);
                     }
                     named_sync(BAR_EPI, NEPI * 32);
-                    if (a.select) rc = alg2_row(tb_s[r], a.gamma);
+                    if (a.select) {
+                        rc = alg2_row(tb_s[r], a.gamma);
+                        tsb = rc.tstar > 0.0f ? __float_as_uint(rc.tstar) : 0u;
+                    }
                 }
                 // groups of GS settings: one TMEM load in registers at a time
 #pragma unroll 1
                 for (int hh = 0; hh < CPW / GS; ++hh) {
                     uint32_t v[GS];
-                    tc_ld16(ta + (uint32_t)(GS * hh), v);
+                    tc_ld32(ta + (uint32_t)(GS * hh), v);
                     tc_wait_ld();
                     if (hh == CPW / GS - 1) {   // all read: the accumulator is free
                         tc_fence_before();
@@ -238,80 +240,63 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                         if (lane == 0) mbar_arrive(aempty(ab));
                     }
                     const int64_t j0 = (int64_t)chunk * CN + CPW * cq + GS * hh;
-                    if (a.T && i < a.m) store16(v, a.T + i * a.n, j0, a.n, a.t_vec);
+                    if (a.T && i < a.m) store_group(v, a.T + i * a.n, j0, a.n, a.t_vec);
                     if (a.select) {
-                        // c + g of the group's settings (+inf past n: never a minimum)
-                        float cgv[GS];
+                        // Screen, branch-free: w_e = (c + g) t of each element with
+                        // t <= t* (one unsigned compare on the bit patterns: positive
+                        // floats order like their bits; negatives and NaN fall outside;
+                        // tsb = 0 for a row without a valid baseline), +inf otherwise
+                        // (c + g is +inf past n), and the group's smallest w.  A zero t
+                        // passes the compare; the exact evaluation rejects it.  The
+                        // energy estimate is w / t_b = fl(w (1 / t_b)), monotone in w,
+                        // so the group's smallest estimate is fl(min w (1 / t_b)).
                         const float4 *cg4 = reinterpret_cast<const float4 *>(
                             cg_smem ? (const float *)cg_s + j0 : a.cg_pad + j0);
-#pragma unroll
-                        for (int e4 = 0; e4 < GS / 4; ++e4) {
-                            const float4 x = cg4[e4];
-                            cgv[4 * e4] = x.x;
-                            cgv[4 * e4 + 1] = x.y;
-                            cgv[4 * e4 + 2] = x.z;
-                            cgv[4 * e4 + 3] = x.w;
-                        }
-                        // Screen, branch-free: w_e = (c + g) t of each valid element
-                        // (0 < t <= t* is one unsigned compare on the bit patterns:
-                        // positive floats order like their bits, zero, negatives and
-                        // NaN fall outside; tsb = 0 for a row without a valid
-                        // baseline), +inf otherwise, and the group's smallest w.  The
-                        // energy estimate is w / t_b = fl(w * (1 / t_b)), monotone in
-                        // w, so the group's smallest estimate is fl(min w * (1 / t_b)).
-                        const float inf = __int_as_float(0x7f800000);
-                        const uint32_t tsb = rc.tstar > 0.0f ? __float_as_uint(rc.tstar) : 0u;
                         float w[GS];
                         float wmin = inf;
 #pragma unroll
-                        for (int e = 0; e < GS; ++e) {
-                            const bool ok = (v[e] - 1u) < tsb;
-                            w[e] = ok ? __fmul_rn(cgv[e], __uint_as_float(v[e])) : inf;
-                            wmin = fminf(wmin, w[e]);
+                        for (int e4 = 0; e4 < GS / 4; ++e4) {
+                            const float4 c = cg4[e4];
+                            const float2 p0 = __fmul2_rn(make_float2(c.x, c.y),
+                                                         make_float2(__uint_as_float(v[4 * e4]),
+                                                                     __uint_as_float(v[4 * e4 + 1])));
+                            const float2 p1 = __fmul2_rn(make_float2(c.z, c.w),
+                                                         make_float2(__uint_as_float(v[4 * e4 + 2]),
+                                                                     __uint_as_float(v[4 * e4 + 3])));
+                            const float pw[4] = {p0.x, p0.y, p1.x, p1.y};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                w[4 * e4 + e] = v[4 * e4 + e] <= tsb ? pw[e] : inf;
+                                wmin = fminf(wmin, w[4 * e4 + e]);
+                            }
                         }
                         // Exact evaluation only where the screen cannot exclude: the
-                        // group's smallest estimate is at most the best's threshold (or no
-                        // best yet).  Warp-uniform, since the lanes hold different rows:
-                        // every lane recovers its group's arg-min (the first element
-                        // attaining the minimum), the rows that need it evaluate that
-                        // element exactly in one pass, and only if some other element
-                        // lies within the screening bound (rare) a divergent pass
-                        // evaluates those too.
+                        // group's smallest estimate is at most the best's threshold
+                        // (or no best yet); then every element within the bound of that
+                        // minimum (usually the minimum alone) is evaluated exactly, in
+                        // a per-row loop over the candidates' bit mask, with the group's
+                        // runtimes stashed in shared memory for indexed access.
                         const float me = __fmul_rn(wmin, rc.rtb);
-                        const bool trig = wmin < inf && me <= (best.j >= 0 ? best.Ethr : inf);
+                        const float thr = best.j >= 0 ? best.Ethr : inf;
+                        const bool trig = wmin < inf && me <= thr;
                         if (__any_sync(FULL, trig)) {
-                            int mi = 0;
-                            float mt = 0.0f, mc = 0.0f;
+                            float *stash = stash_s + (warp * 32 + lane) * STASH_LD;
 #pragma unroll
-                            for (int e = GS - 1; e >= 0; --e) {
-                                const bool hit = w[e] == wmin;
-                                mi = hit ? e : mi;
-                                mt = hit ? __uint_as_float(v[e]) : mt;
-                                mc = hit ? cgv[e] : mc;
-                            }
-                            float bound = inf;
+                            for (int e = 0; e < GS; e += 4)
+                                *reinterpret_cast<uint4 *>(stash + e) =
+                                    make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
                             if (trig) {
-                                alg2_exact(best, rc, mt, mc, a.Ebase, (int32_t)(j0 + mi));
-                                bound = fminf(alg2_bound(me, a.Ebase), best.Ethr);
-                            }
-                            int more = 0;
+                                float bound = fminf(alg2_bound(me, a.Ebase), thr);
+                                uint32_t mask = 0u;
 #pragma unroll
-                            for (int e = 0; e < GS; ++e)
-                                more += (trig && e != mi && __fmul_rn(w[e], rc.rtb) <= bound) ? 1 : 0;
-                            if (__any_sync(FULL, more > 0) && more > 0) {
-#pragma unroll 1
-                                for (int e = 0; e < GS; ++e) {
-                                    float we = w[0];
-#pragma unroll
-                                    for (int f = 1; f < GS; ++f) we = (f == e) ? w[f] : we;
-                                    if (e != mi && __fmul_rn(we, rc.rtb) <= bound) {
-                                        float te = __uint_as_float(v[0]), ce = cgv[0];
-#pragma unroll
-                                        for (int f = 1; f < GS; ++f) {
-                                            te = (f == e) ? __uint_as_float(v[f]) : te;
-                                            ce = (f == e) ? cgv[f] : ce;
-                                        }
-                                        exact_call(best, rc, te, ce, a.Ebase, (int32_t)(j0 + e));
+                                for (int e = 0; e < GS; ++e)
+                                    mask |= (w[e] < inf && __fmul_rn(w[e], rc.rtb) <= bound ? 1u : 0u) << e;
+                                while (mask) {
+                                    const int e = __ffs(mask) - 1;
+                                    mask &= mask - 1u;
+                                    const float t = stash[e];
+                                    if (t > 0.0f && __fmul_rn(__fmul_rn(cg_of(j0 + e), t), rc.rtb) <= bound) {
+                                        alg2_exact(best, rc, t, cg_of(j0 + e), a.Ebase, (int32_t)(j0 + e));
                                         bound = fminf(bound, best.Ethr);
                                     }
                                 }
