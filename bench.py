@@ -1017,6 +1017,7 @@ def run_gpu_batched(args):
         "config": {"workload": WORKLOAD_C3, "problems": len(bp), "nnz": int(c["val"].size),
                    "row_solves_per_step": units, "tuned_warps_per_problem": {"large": W[0],
                                                                             "small": W[1]},
+                   "tuned_class_cut_pct": W[2], "tuned_ctas_per_sm": W[3],
                    "l2": "flushed (256 MB write) before every timed step"},
         "plain_gpu_per_problem": {"value": plain_units / t_plain, "unit": "row-solves/s",
                                   "sample_problems": len(sample),

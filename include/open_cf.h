@@ -245,10 +245,13 @@ int open_cf_batched_fit(open_cf_t *h, int64_t P, const int64_t *m_host, const in
                         const int64_t *row_ptr, const int32_t *col, const float *val,
                         float *V_inout, float *U_out, void *stream);
 
-/* Autotuner of the batched fit: times 2-sweep trial runs over the candidate
- * warps-per-problem of the large class {2, 4, 8} and of the small class
- * {1, 2, 4}, keeps the fastest pair in the handle for later
- * open_cf_batched_fit calls and writes it to W_out_host[2] (may be NULL).
+/* Autotuner of the batched fit: times 2-sweep trial runs in a coordinate
+ * search over the launch's tile shape -- warps per problem of the large class
+ * {2, 4, 8} and of the small class {1, 2, 4} (9 pairs), then the share of each
+ * padded rank's cost given to the large class {30, 50, 70} %, then the CTAs
+ * per SM {1, 2} -- keeps the fastest setting in the handle for later
+ * open_cf_batched_fit calls and writes it to W_out_host[4] = {warps large,
+ * warps small, cut %, CTAs per SM} (may be NULL).
  * V_scratch receives trial results (same layout as V_inout; pass a copy of
  * the initial V).  Synchronises `stream`. */
 int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const int64_t *n_host,

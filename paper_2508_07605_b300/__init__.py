@@ -394,12 +394,12 @@ class OpenCF:
         m = np.ascontiguousarray(m, dtype=np.int64); n = np.ascontiguousarray(n, dtype=np.int64)
         k = np.ascontiguousarray(k, dtype=np.int32)
         nz = np.ascontiguousarray(nnz_p, dtype=np.int64)
-        W = (ctypes.c_int32 * 2)()
+        W = (ctypes.c_int32 * 4)()
         self._check(lib().open_cf_batched_tune(
             self._h, len(m), m.ctypes.data, n.ctypes.data, k.ctypes.data, nz.ctypes.data,
             col.numel(), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(V_scratch), W,
             self._stream()))
-        return int(W[0]), int(W[1])
+        return tuple(int(w) for w in W)   # warps large, warps small, cut %, CTAs per SM
 
     # -- learned warm start ------------------------------------------------
     def _f32(self, t, name, numel=None):

@@ -53,6 +53,8 @@ struct open_cf {
     Buf b_meta, b_Uw, b_Vw, b_cptr, b_cidx, b_cval, b_counter;
     std::vector<int64_t> b_key;       // host description of the planned batch
     int32_t b_W[2] = {8, 2};          // warps per problem: large class, small class
+    int32_t b_cut = 50;               // % of a padded rank's cost in its large class
+    int32_t b_ctas = 2;               // CTAs per SM of the persistent launch
     int32_t b_nclass = 0;             // classes of the planned batch
     int32_t b_class_end[BATCH_MAX_CLASSES] = {};
     int32_t b_class_W[BATCH_MAX_CLASSES] = {};
@@ -330,6 +332,7 @@ int batch_plan(open_cf_t *h, int64_t P, const int64_t *m, const int64_t *n, cons
     key.push_back(nnz);
     key.push_back(h->b_W[0]);
     key.push_back(h->b_W[1]);
+    key.push_back(h->b_cut);
     for (int64_t p = 0; p < P; ++p) {
         key.push_back(m[p]);
         key.push_back(n[p]);
@@ -371,7 +374,7 @@ int batch_plan(open_cf_t *h, int64_t P, const int64_t *m, const int64_t *n, cons
     // Keeping one padded rank together keeps the warps of an SM in one unrolled
     // solver at a time (mixing the three thrashed the instruction cache).  Per
     // padded rank, class "large" holds the costliest problems that take about
-    // half of that rank's work, class "small" the rest.
+    // a share of that rank's work (b_cut %, tuned), class "small" the rest.
     std::vector<int32_t> order(P);
     for (int64_t p = 0; p < P; ++p) order[p] = (int32_t)p;
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
@@ -388,7 +391,7 @@ int batch_plan(open_cf_t *h, int64_t P, const int64_t *m, const int64_t *n, cons
         while (g1 < P && padded_k(k[order[g1]]) == kp) total += cost[order[g1++]];
         double acc = 0.0;
         int64_t split = g0;
-        while (split < g1 && acc < 0.5 * total) acc += cost[order[split++]];
+        while (split < g1 && acc < 0.01 * h->b_cut * total) acc += cost[order[split++]];
         if (split > g0) {
             h->b_class_end[h->b_nclass] = (int32_t)split;
             h->b_class_W[h->b_nclass++] = h->b_W[0];
@@ -462,6 +465,7 @@ int batched_grid(open_cf_t *h) {
     const size_t smem = batched_smem_bytes();
     int per_sm = (int)std::max<size_t>(1, (size_t)prop.sharedMemPerMultiprocessor / (smem + 1024));
     if (per_sm > 2) per_sm = 2;
+    if (per_sm > h->b_ctas) per_sm = h->b_ctas;
     return prop.multiProcessorCount * per_sm;
 }
 
@@ -1252,7 +1256,7 @@ int open_cf_batched_fit(open_cf_t *h, int64_t P, const int64_t *m_host, const in
     const BatchArgs b = batch_args(h, L, row_ptr, col, val, h->cfg.sweeps);
     const int grid = batched_grid(h);
     std::vector<int64_t> key = {2, P, nnz, (int64_t)row_ptr, (int64_t)col, (int64_t)val,
-                                (int64_t)V_inout, (int64_t)U_out, h->b_nclass};
+                                (int64_t)V_inout, (int64_t)U_out, h->b_nclass, grid};
     for (int c = 0; c < h->b_nclass; ++c) {   // the classes are baked into the graph
         key.push_back(h->b_class_end[c]);
         key.push_back(h->b_class_W[c]);
@@ -1274,45 +1278,75 @@ int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const i
         return fail(h, OPEN_CF_INVALID_ARG, "NULL array");
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
-    const int grid = batched_grid(h);
-    const int cand_large[3] = {2, 4, 8}, cand_small[3] = {1, 2, 4};
-    float best_ms = 0.0f;
-    int32_t bw0 = h->b_W[0], bw1 = h->b_W[1];
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
+    // one 2-sweep trial of the current setting (the first run warms caches)
+    auto trial = [&](float &ms) -> int {
+        BatchPlan L;
+        int rc = batch_plan(h, P, m_host, n_host, k_host, nnz_host, nnz, L);
+        if (rc) return rc;
+        const BatchArgs b = batch_args(h, L, row_ptr, col, val, 2);
+        const int grid = batched_grid(h);
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(h, cudaEventRecord(e0, st));
+            CK(h, batch_enqueue(h, L, b, V_scratch, nullptr, grid, st));
+            CK(h, cudaEventRecord(e1, st));
+            CK(h, cudaEventSynchronize(e1));
+            CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        }
+        return OPEN_CF_OK;
+    };
+    // coordinate search: warps per problem of both classes, then the class cut,
+    // then the CTAs per SM, each stage from the best of the previous one
+    float best_ms = 0.0f;
     bool first = true;
-    for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) {
+    int32_t best[4] = {h->b_W[0], h->b_W[1], h->b_cut, h->b_ctas};
+    auto consider = [&]() -> int {
+        float ms = 0.0f;
+        int rc = trial(ms);
+        if (rc) return rc;
+        if (first || ms < best_ms) {
+            best_ms = ms;
+            best[0] = h->b_W[0];
+            best[1] = h->b_W[1];
+            best[2] = h->b_cut;
+            best[3] = h->b_ctas;
+            first = false;
+        }
+        return OPEN_CF_OK;
+    };
+    auto restore = [&]() {
+        h->b_W[0] = best[0];
+        h->b_W[1] = best[1];
+        h->b_cut = best[2];
+        h->b_ctas = best[3];
+    };
+    const int cand_large[3] = {2, 4, 8}, cand_small[3] = {1, 2, 4};
+    const int cand_cut[3] = {30, 50, 70}, cand_ctas[2] = {1, 2};
+    int rc = OPEN_CF_OK;
+    for (int a = 0; a < 3 && !rc; ++a)
+        for (int c = 0; c < 3 && !rc; ++c) {
             h->b_W[0] = cand_large[a];
             h->b_W[1] = cand_small[c];
-            BatchPlan L;
-            int rc = batch_plan(h, P, m_host, n_host, k_host, nnz_host, nnz, L);
-            if (rc) return rc;
-            const BatchArgs b = batch_args(h, L, row_ptr, col, val, 2);   // 2 sweeps per trial
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {   // first run warms caches
-                CK(h, cudaEventRecord(e0, st));
-                CK(h, batch_enqueue(h, L, b, V_scratch, nullptr, grid, st));
-                CK(h, cudaEventRecord(e1, st));
-                CK(h, cudaEventSynchronize(e1));
-                CK(h, cudaEventElapsedTime(&ms, e0, e1));
-            }
-            if (first || ms < best_ms) {
-                best_ms = ms;
-                bw0 = h->b_W[0];
-                bw1 = h->b_W[1];
-                first = false;
-            }
+            rc = consider();
         }
+    restore();
+    for (int c = 0; c < 3 && !rc; ++c) {
+        h->b_cut = cand_cut[c];
+        rc = consider();
+    }
+    restore();
+    for (int c = 0; c < 2 && !rc; ++c) {
+        h->b_ctas = cand_ctas[c];
+        rc = consider();
+    }
+    restore();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->b_W[0] = bw0;
-    h->b_W[1] = bw1;
-    if (W_out_host) {
-        W_out_host[0] = bw0;
-        W_out_host[1] = bw1;
-    }
+    if (rc) return rc;
+    if (W_out_host)
+        for (int t = 0; t < 4; ++t) W_out_host[t] = best[t];
     return OPEN_CF_OK;
 }
 

@@ -53,46 +53,75 @@ namespace {
 
 using namespace sm;
 
-constexpr int KP = 32, WARPS = 8, NPACK = 576;
+constexpr int KP = 32, WARPS = 8;
 
-// Packed lower triangle by rows: row r (entries 0 .. r, padded to 4) at rowoff(r).
-__host__ __device__ constexpr int rowoff(int r) {
-    return 8 * (r >> 2) * ((r >> 2) + 1) + 4 * (r & 3) * ((r >> 2) + 1);
-}
-// Packed lower triangle by columns: column p holds rows colbase(p) .. 31 at coloff(p).
+// Packed lower triangles in shared memory.  By rows (A): row r holds entries
+// 0 .. r padded to 4 floats; by columns (L): column p holds rows 4 floor(p/4)
+// .. 31 (so 16-byte loads stay aligned).  Lanes of a quarter-warp load eight
+// consecutive rows (columns) at once, so within each block of 8 rows
+// (columns) every start sits in a different 4-bank group: a row (column) is
+// moved forward by whole 16-byte steps until its group is free.
+struct Tab {
+    int v[33];
+};
 __host__ __device__ constexpr int colbase(int p) { return 4 * (p >> 2); }
-__host__ __device__ constexpr int coloff(int p) {
-    return 128 * (p >> 2) - 8 * (p >> 2) * ((p >> 2) - 1) + (p & 3) * (32 - 4 * (p >> 2));
+__host__ __device__ constexpr Tab make_rows() {
+    Tab t{};
+    int cur = 0, used = 0;
+    for (int q = 0; q < 32; ++q) {
+        if ((q & 7) == 0) used = 0;
+        while (used & (1 << ((cur >> 2) & 7))) cur += 4;
+        t.v[q] = cur;
+        used |= 1 << ((cur >> 2) & 7);
+        cur += 4 * ((q + 4) >> 2);
+    }
+    t.v[32] = cur;
+    return t;
 }
-static_assert(rowoff(32) == NPACK && coloff(32) == NPACK, "packed triangle size");
+__host__ __device__ constexpr Tab make_cols() {
+    Tab t{};
+    int cur = 0, used = 0;
+    for (int q = 0; q < 32; ++q) {
+        if ((q & 7) == 0) used = 0;
+        while (used & (1 << (((cur - colbase(q)) >> 2) & 7))) cur += 4;
+        t.v[q] = cur;
+        used |= 1 << (((cur - colbase(q)) >> 2) & 7);
+        cur += 32 - colbase(q);
+    }
+    t.v[32] = cur;
+    return t;
+}
+constexpr int NROWP = make_rows().v[32], NCOLP = make_cols().v[32];
+static_assert(NROWP == 676 && NCOLP == 672, "packed triangle sizes");
+__device__ constexpr Tab ROWT = make_rows();
+__device__ constexpr Tab COLT = make_cols();
+// compile-time offsets (runtime, lane-dependent ones come from a shared table)
+__device__ __forceinline__ constexpr int rowoff(int r) { return ROWT.v[r]; }
+__device__ __forceinline__ constexpr int coloff(int p) { return COLT.v[p]; }
 
-// Per warp: the staging buffers of the Gram phase overlay the solve area of
-// the pair (L of both rows, A and b of the second row, solution scratch); A
-// and b of the first row sit outside, because they are written while the
-// second row's observations still stream into the staging buffers.
 template <bool BF> struct alignas(16) Smem32 {
     static constexpr int ROWB = (BF ? 2 : 4) * (KP + 8);   // padded staged row (bytes)
     struct alignas(16) Stage {
         alignas(16) unsigned char stage[2][BF ? 2 : 1][32][ROWB];
-        float sr[2][32];
+        float sr[2][32];   // values (TF32 path); BF16 path: [0..15] hi halves, [16..31] lo halves
     };
     // The two halves of the warp touch the same offsets of their own row's
     // arrays at once, so the second row's copy of each array starts 16 banks
     // after the first row's (strides of 16 mod 32 words): conflict-free.
-    static constexpr int LS = NPACK + 16, XS = KP + 16;
+    static constexpr int LS = NCOLP + 16, XS = KP + 16;
     struct alignas(16) Solve {
         float L[2 * LS];      // the Cholesky factors by columns (second row's at LS)
         float x[2 * XS];
         float inv[2 * XS];    // 1 / L_pp
         float b1[KP];
         float pad[16];        // puts A1 16 banks from A0
-        float A1[NPACK];      // A = Gram + lambda I of the second row, lower triangle by rows
+        float A1[NROWP];      // A = Gram + lambda I of the second row, lower triangle by rows
     };
     union {
         Stage ld;
         Solve sv;
     };
-    float A0[NPACK];          // A and b of the first row
+    float A0[NROWP];          // A and b of the first row
     float b0[KP];
     __device__ float *A(int h) { return h ? sv.A1 : A0; }
     __device__ float *b(int h) { return h ? sv.b1 : b0; }
@@ -135,36 +164,56 @@ __device__ __forceinline__ float half_sum(float v) {
     return v;
 }
 
-// Rows r0 = i and r1 = i + 16 of b - A x (A symmetric from its packed lower
-// triangle, x from shared memory) in double-FP32, as the two chains of packed
-// instructions; also |row|^2 of both rows.
-__device__ __forceinline__ float2 ext_residual(const float *A, const float *x, int i,
-                                               float2 bq, float2 &aa) {
-    const int r0 = i, r1 = i + 16;
-    const int o0 = rowoff(r0), o1 = rowoff(r1);
+// Rows i and i + 16 of b - A x (o0, o1: their offsets in the packed triangle) (A symmetric from its packed lower triangle,
+// x from shared memory) in double-FP32, the two rows as the two chains of
+// packed instructions; with norms, also |row|^2 of both rows.  Row i + 16's
+// entries below column 16 and every column-part entry of row i above it sit
+// at lane-independent offsets; only the crossings of the diagonal select.
+template <bool NORMS>
+__device__ __forceinline__ float2 ext_residual(const float *A, const float *x, int i, int o0,
+                                               int o1, float2 bq, float2 &aa) {
     float2 S = bq, C = make_float2(0.f, 0.f), A2 = make_float2(0.f, 0.f);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const float4 *r4 = reinterpret_cast<const float4 *>(A + o1);
 #pragma unroll
-    for (int e = 0; e < KP; ++e) {
-        const float g0 = A[e <= r0 ? o0 + e : rowoff(e) + r0];
-        const float g1 = A[e <= r1 ? o1 + e : rowoff(e) + r1];
-        const float xe = x[e];
-        const float2 g = make_float2(g0, g1);
-        dot2_sub(S, C, g, make_float2(xe, xe));
-        A2 = __ffma2_rn(g, g, A2);
+    for (int t = 0; t < KP / 4; ++t) {
+        const float4 xv = x4[t];
+        const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+        float g1v[4];
+        if (t < 4) {   // row i + 16, columns 0 .. 15: its own row segment
+            const float4 g = r4[t];
+            g1v[0] = g.x; g1v[1] = g.y; g1v[2] = g.z; g1v[3] = g.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = 4 * t + u;
+            float g0, g1;
+            if (e < 16) {
+                g0 = A[e <= i ? o0 + e : rowoff(e) + i];
+                g1 = g1v[u];
+            } else {
+                g0 = A[rowoff(e) + i];                              // column part of row i
+                g1 = A[e <= i + 16 ? o1 + e : rowoff(e) + i + 16];
+            }
+            const float2 g = make_float2(g0, g1);
+            dot2_sub(S, C, g, make_float2(xs[u], xs[u]));
+            if (NORMS) A2 = __ffma2_rn(g, g, A2);
+        }
     }
-    aa = A2;
+    if (NORMS) aa = A2;
     return make_float2(S.x + C.x, S.y + C.y);
 }
 
 // L^T x = y for the two components (i, i + 16) a lane holds: columns i and
 // i + 16 of L are loaded into registers, then x_p is formed on its lane and
-// broadcast within the half-warp, p = 31 .. 0.  y arrives divided by nothing;
+// broadcast within the half-warp, p = 31 .. 0 (c0off, c1off: the columns'
+// offsets, less their first stored row).  y arrives divided by nothing;
 // the result is the solution.
-__device__ __forceinline__ float2 back_subst(const float *L, int i, float y0, float y1,
-                                             float inv0, float inv1) {
+__device__ __forceinline__ float2 back_subst(const float *L, int i, int c0off, int c1off,
+                                             float y0, float y1, float inv0, float inv1) {
     float c0[KP], c1[16];
     {
-        const float4 *q0 = reinterpret_cast<const float4 *>(L + coloff(i) - colbase(i));
+        const float4 *q0 = reinterpret_cast<const float4 *>(L + c0off);
 #pragma unroll
         for (int t = 0; t < KP / 4; ++t) {
             const float4 v = q0[t];
@@ -173,7 +222,7 @@ __device__ __forceinline__ float2 back_subst(const float *L, int i, float y0, fl
             c0[4 * t + 2] = v.z;
             c0[4 * t + 3] = v.w;
         }
-        const float4 *q1 = reinterpret_cast<const float4 *>(L + coloff(i + 16) - colbase(i + 16));
+        const float4 *q1 = reinterpret_cast<const float4 *>(L + c1off);
 #pragma unroll
         for (int t = 4; t < KP / 4; ++t) {
             const float4 v = q1[t];
@@ -219,19 +268,17 @@ __device__ __forceinline__ void gram_item(const Smem32<BF> &W, int buf, int cnt,
                 ldsm_x4_trans(aH[mb], sH + off);
                 ldsm_x4_trans(aL[mb], sL + off);
             }
-            float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+            // the values' split halves, staged as BF16 (observation t: hi at
+            // element t, lo at element 32 + t of the row): B fragments of S^T r,
+            // column 0 only
+            uint32_t rh0 = 0u, rh1 = 0u, rl0 = 0u, rl1 = 0u;
             if (gid == 0) {
-                r0 = W.ld.sr[buf][k0 + 2 * tid4];
-                r1 = W.ld.sr[buf][k0 + 2 * tid4 + 1];
-                r2 = W.ld.sr[buf][k0 + 2 * tid4 + 8];
-                r3 = W.ld.sr[buf][k0 + 2 * tid4 + 9];
+                const uint32_t *hv = reinterpret_cast<const uint32_t *>(&W.ld.sr[buf][0]);
+                rh0 = hv[(k0 >> 1) + tid4];
+                rh1 = hv[(k0 >> 1) + tid4 + 4];
+                rl0 = hv[16 + (k0 >> 1) + tid4];
+                rl1 = hv[16 + (k0 >> 1) + tid4 + 4];
             }
-            const float h0 = __bfloat162float(__float2bfloat16_rn(r0));
-            const float h1 = __bfloat162float(__float2bfloat16_rn(r1));
-            const float h2 = __bfloat162float(__float2bfloat16_rn(r2));
-            const float h3 = __bfloat162float(__float2bfloat16_rn(r3));
-            const uint32_t rh0 = pack_bf16(h0, h1), rh1 = pack_bf16(h2, h3);
-            const uint32_t rl0 = pack_bf16(r0 - h0, r1 - h1), rl1 = pack_bf16(r2 - h2, r3 - h3);
 #pragma unroll
             for (int ps = 0; ps < 3; ++ps) {   // pass-major: consecutive MMAs on different accumulators
 #pragma unroll
@@ -329,6 +376,18 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
     const int gid = lane >> 2, tid4 = lane & 3;
     const int h = lane >> 4, i = lane & 15;   // solve phase: system h of the pair, rows i, i + 16
     WS &W = reinterpret_cast<WS *>(smem_raw)[warp];
+    // lane-dependent offsets into the packed triangles, from a shared table
+    __shared__ int s_row[33], s_col[33];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < 33; ++t) {
+            s_row[t] = rowoff(t);
+            s_col[t] = t < 32 ? coloff(t) - colbase(t) : 0;
+        }
+    }
+    __syncthreads();
+    const int ro_i = s_row[i], ro_i16 = s_row[i + 16];
+    const int co_i = s_col[i], co_i16 = s_col[i + 16];
     pdl_trigger();
     if (a.m_dev || a.row_map) pdl_wait();         // the list comes from the preceding kernel
     const int64_t M = a.m_dev ? *a.m_dev : a.m;
@@ -389,17 +448,60 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                 for (int e = 0; e < 8; ++e)
                     cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, ok ? 16 : 0);
             }
-            W.ld.sr[buf][lane] = ok ? v : 0.f;
+            if constexpr (BF) {
+                const float vv = ok ? v : 0.f;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(vv);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(vv - __bfloat162float(hi));
+                __nv_bfloat16 *sb = reinterpret_cast<__nv_bfloat16 *>(&W.ld.sr[buf][0]);
+                sb[lane] = hi;
+                sb[32 + lane] = lo;
+            } else {
+                W.ld.sr[buf][lane] = ok ? v : 0.f;
+            }
         };
         pdl_wait();   // from here on the other factor is read
-        // fragments of one row -> its packed lower triangle of A, and b
-        auto write_sys = [&](float *Ap, float *bp, const float (&d)[6][4], const float (&dr)[2][4]) {
+        if (nit > 0) {
+            issue(0, 0);
+            cp_async_commit();
+        }
+#pragma unroll
+        for (int si = 0; si < 2; ++si) {
+            // this row's items, the next item (possibly the other row's first)
+            // staged while this one is on the tensor cores
+            float d[6][4], dr[2][4];
+#pragma unroll
+            for (int t = 0; t < 6; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) d[t][e] = 0.f;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
+            const int w0 = si ? n0 : 0, w1 = si ? nit : n0;
+            const int64_t ss = si ? cur.s[1] : cur.s[0];
+            for (int w = w0; w < w1; ++w) {
+                if (w + 1 < nit) issue(w + 1, (w + 1) & 1);
+                cp_async_commit();
+                cp_async_wait<1>();
+                __syncwarp();
+                const int cnt = (int)min((int64_t)32, ss - (int64_t)(w - w0) * 32);
+                gram_item<BF>(W, w & 1, cnt, d, dr, lane);
+                __syncwarp();   // this buffer is refilled two items later
+            }
+            if (si == 1) {
+                cp_async_wait<0>();   // nothing in flight before the solve area overlays the stages
+                __syncwarp();
+            }
+            // fragments -> the row's packed lower triangle of A, and b (the first
+            // row's lie outside the staging area, the second's overlay it)
+            float *Ap = si ? W.sv.A1 : W.A0;
+            float *bp = si ? W.sv.b1 : W.b0;
 #pragma unroll
             for (int tb = 0; tb < 6; ++tb) {
                 const int mb = mb_of(tb), nb = nb_of(tb);
                 const int r0 = mb * 16 + gid, c = nb * 8 + 2 * tid4;
                 const bool diag = (mb == 0) || (nb >= 2);   // diagonal 16x16 block
-                const int o0 = rowoff(r0), o8 = rowoff(r0 + 8);
+                const int o0 = s_row[r0], o8 = s_row[r0 + 8];
                 if (!diag || c <= r0) Ap[o0 + c] = d[tb][0];
                 if (!diag || c + 1 <= r0) Ap[o0 + c + 1] = d[tb][1];
                 if (!diag || c <= r0 + 8) Ap[o8 + c] = d[tb][2];
@@ -412,51 +514,6 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                     bp[mb * 16 + gid + 8] = dr[mb][2];
                 }
             }
-        };
-        // items of one row, the next item (possibly the other row's first) staged
-        // while this one is on the tensor cores
-        auto run_items = [&](int w0, int w1, int64_t ss, float (&d)[6][4], float (&dr)[2][4]) {
-            for (int w = w0; w < w1; ++w) {
-                if (w + 1 < nit) issue(w + 1, (w + 1) & 1);
-                cp_async_commit();
-                cp_async_wait<1>();
-                __syncwarp();
-                const int cnt = (int)min((int64_t)32, ss - (int64_t)(w - w0) * 32);
-                gram_item<BF>(W, w & 1, cnt, d, dr, lane);
-                __syncwarp();   // this buffer is refilled two items later
-            }
-        };
-        if (nit > 0) {
-            issue(0, 0);
-            cp_async_commit();
-        }
-        {
-            float d[6][4], dr[2][4];
-#pragma unroll
-            for (int t = 0; t < 6; ++t)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) d[t][e] = 0.f;
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
-            run_items(0, n0, cur.s[0], d, dr);
-            write_sys(W.A0, W.b0, d, dr);   // outside the staging area
-        }
-        {
-            float d[6][4], dr[2][4];
-#pragma unroll
-            for (int t = 0; t < 6; ++t)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) d[t][e] = 0.f;
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
-            run_items(n0, nit, cur.s[1], d, dr);
-            cp_async_wait<0>();   // nothing in flight before the solve area overlays the stages
-            __syncwarp();
-            write_sys(W.sv.A1, W.sv.b1, d, dr);
         }
         const PairFetch pf = cur;
         const bool bad0 = pf.bad[0] || (__any_sync(FULL, badf0) != 0);
@@ -468,15 +525,15 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
         const int64_t row = h ? pf.row[1] : pf.row[0];
         const bool bad = h ? bad1 : bad0;
         const float lam = float(a.lambda) * (a.wr ? float(s) : 1.f);   // weighted: lambda s_i
-        SA[rowoff(i) + i] += lam;
-        SA[rowoff(i + 16) + i + 16] += lam;
+        SA[ro_i + i] += lam;
+        SA[ro_i16 + i + 16] += lam;
         __syncwarp();
         const float2 bq = make_float2(W.b(h)[i], W.b(h)[i + 16]);
         float x0, x1, inv0 = 0.f, inv1 = 0.f;
         if (!a.u_given) {
             float a0[16], a1[KP];
             {
-                const float4 *q0 = reinterpret_cast<const float4 *>(SA + rowoff(i));
+                const float4 *q0 = reinterpret_cast<const float4 *>(SA + ro_i);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const float4 v = q0[t];
@@ -485,7 +542,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                     a0[4 * t + 2] = v.z;
                     a0[4 * t + 3] = v.w;
                 }
-                const float4 *q1 = reinterpret_cast<const float4 *>(SA + rowoff(i + 16));
+                const float4 *q1 = reinterpret_cast<const float4 *>(SA + ro_i16);
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const float4 v = q1[t];
@@ -546,7 +603,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             inv0 = Sinv[i];
             inv1 = Sinv[i + 16];
             // ---- back substitution L^T x = y
-            const float2 xx = back_subst(SL, i, y0 * inv0, y1 * inv1, inv0, inv1);
+            const float2 xx = back_subst(SL, i, co_i, co_i16, y0 * inv0, y1 * inv1, inv0, inv1);
             x0 = xx.x;
             x1 = xx.y;
         } else {
@@ -570,7 +627,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             Sx[i + 16] = x1;
             __syncwarp();
             float2 aa;
-            float2 r = ext_residual(SA, Sx, i, bq, aa);
+            float2 r = ext_residual<true>(SA, Sx, i, ro_i, ro_i16, bq, aa);
             if (a.refine && !a.u_given) {
                 // A d = r with the FP32 factor: L z = r (L[q][p] = column p, row q), L^T d = z
                 // (both halves run it: the shuffles need the whole warp)
@@ -587,7 +644,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                         if (i + 16 > p) z1 = fmaf(-Lc[i + 16], zp, z1);
                     }
                 }
-                const float2 dd = back_subst(SL, i, z0 * inv0, z1 * inv1, inv0, inv1);
+                const float2 dd = back_subst(SL, i, co_i, co_i16, z0 * inv0, z1 * inv1, inv0, inv1);
                 if (want) {
                     x0 += dd.x;
                     x1 += dd.y;
@@ -600,7 +657,8 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                     Sx[i + 16] = x1;
                 }
                 __syncwarp();
-                r = ext_residual(SA, Sx, i, bq, aa);
+                float2 aa2;
+                r = ext_residual<false>(SA, Sx, i, ro_i, ro_i16, bq, aa2);
             }
             // |A|_F over the k x k system: padded rows (q >= k) hold only lambda
             const float rr = half_sum(r.x * r.x + r.y * r.y);
@@ -650,20 +708,25 @@ template <bool BF> cudaError_t launch32(const SolveArgs<float> &a, cudaStream_t 
     return cudaLaunchKernelEx(&cfg, k_solve32_tc<BF>, a);
 }
 
+template <bool BF> cudaError_t attr32() {
+    return cudaFuncSetAttribute(k_solve32_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<BF>());
+}
+
 }  // namespace
 
 cudaError_t prepare_solve32_tc() {
-    cudaError_t e = cudaFuncSetAttribute(k_solve32_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes<true>());
+    cudaError_t e = attr32<true>();
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_solve32_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<false>());
+    return attr32<false>();
 }
 
 cudaError_t launch_solve32_tc(const SolveArgs<float> &a, bool bf16, cudaStream_t st) {
     if (a.m <= 0) return cudaSuccess;
     if (bf16 && !a.Fb) return cudaErrorInvalidValue;
     if (a.gram) return cudaErrorInvalidValue;   // the streaming refit's sums are not supported here
+    // one build serves the plain fold-in too (a build without the residual
+    // paths spilled more registers and measured slower)
     return bf16 ? launch32<true>(a, st) : launch32<false>(a, st);
 }
 

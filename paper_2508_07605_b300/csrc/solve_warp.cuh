@@ -22,6 +22,18 @@ template <typename TV, typename TC, int KP> struct alignas(16) WarpSmem {
 __device__ __forceinline__ float my_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double my_rsqrt(double x) { return rsqrt(x); }
 
+// a0 += f * x0, a1 += f * x1: in FP32 one packed fma.rn.f32x2 (each element
+// rounds exactly like fmaf, so the results are those of two scalar FMAs).
+__device__ __forceinline__ void fma_pair(float &a0, float &a1, float f, float x0, float x1) {
+    const float2 r = __ffma2_rn(make_float2(f, f), make_float2(x0, x1), make_float2(a0, a1));
+    a0 = r.x;
+    a1 = r.y;
+}
+__device__ __forceinline__ void fma_pair(double &a0, double &a1, double f, double x0, double x1) {
+    a0 = fma(f, x0, a0);
+    a1 = fma(f, x1, a1);
+}
+
 // Solve system i.  WPS = 1: the calling warp alone (lanes in G = 32/KP groups);
 // WPS > 1: the WPS warps of the CTA together (every warp of the CTA calls it).
 // SUMS: the build supports the stored sums of the streaming refit (the
@@ -74,8 +86,9 @@ __device__ __forceinline__ void solve_system(const SolveArgs<TV> &a, int64_t i,
                 for (int e4 = 0; e4 < KP / VN; ++e4) {
                     const VT x = rv[e4];
 #pragma unroll
-                    for (int e = 0; e < VN; ++e)
-                        acc[e4 * VN + e] = my_fma(fq, vget(x, e), acc[e4 * VN + e]);
+                    for (int e = 0; e < VN; e += 2)
+                        fma_pair(acc[e4 * VN + e], acc[e4 * VN + e + 1], fq, vget(x, e),
+                                 vget(x, e + 1));
                 }
                 bq = my_fma(r, fq, bq);
             }
@@ -150,8 +163,11 @@ __device__ __forceinline__ void solve_system(const SolveArgs<TV> &a, int64_t i,
             if (g == 0) cb[q] = l;
             if (lane == 0) W.dinv[p] = inv;
             __syncwarp();
+            // trailing update A[r] -= l L[r][p], r > p, two elements per instruction
+            if (p + 1 < KP && ((p + 1) & 1)) A[p + 1] = my_fma(-l, cb[p + 1], A[p + 1]);
 #pragma unroll
-            for (int r = p + 1; r < KP; ++r) A[r] = my_fma(-l, cb[r], A[r]);
+            for (int r = ((p + 1) & 1) ? p + 2 : p + 1; r + 1 < KP; r += 2)
+                fma_pair(A[r], A[r + 1], -l, cb[r], cb[r + 1]);
         }
 
         // ---- forward substitution L y = b ---------------------------------

@@ -96,7 +96,7 @@ def test_batched_fit_heldout_rmse_and_tuning_invariance(orc):
     Vs = dev(rounded(cc["V0"], torch.float32), torch.float32)
     W = h.batched_tune(cc["m"], cc["n"], cc["k"], nnz_p, dev(cc["row_ptr"], torch.int64),
                        dev(cc["col"], torch.int32), dev(val, torch.float32), Vs)
-    assert W[0] in (2, 4, 8) and W[1] in (1, 2, 4)
+    assert W[0] in (2, 4, 8) and W[1] in (1, 2, 4) and W[2] in (30, 50, 70) and W[3] in (1, 2)
     _, _, U2, V2 = _run(h, bp)
     assert np.array_equal(U, U2) and np.array_equal(V, V2)
 
