@@ -18,6 +18,7 @@
 //     warp with the shared warp-level solve (solve_warp.cuh).
 #include "common.cuh"
 #include "kernels.h"
+#include "packed_tri.cuh"
 #include "solve_warp.cuh"
 
 namespace ocf {
@@ -33,6 +34,148 @@ __device__ __forceinline__ void group_sync(int id, int nthreads) {
 using WS32 = WarpSmem<float, float, 32>;
 static_assert(sizeof(WS32) >= 2 * 1024 * 4, "CSC scratch must fit one warp's area");
 
+// Rank-32 systems two per warp (the fold-in solver's layout): half h of the
+// warp solves system i0 + h, lane i accumulating rows i and i + 16 of its
+// Gram directly in registers (16 + 32 values: row i never needs a column >= 16)
+// from staged factor rows, 16 observations per half and round; lambda joins
+// the diagonal when the pivot is broadcast; right-looking Cholesky with the
+// column of L through shared memory (packed by columns), packed FP32x2 trailing
+// updates, forward substitution on the pivot steps, back substitution from
+// columns i and i + 16 in registers.
+struct alignas(16) PairSmem32 {
+    static constexpr int SROW = 36, SHALF = 16 * SROW + 16;   // half 1 starts 16 banks on
+    static constexpr int LS = pk::NCOLP + 16, XS = 48;
+    float stage[2 * SHALF];
+    float sr[32];
+    float L[2 * LS];
+    float inv[2 * XS];
+};
+static_assert(sizeof(PairSmem32) <= sizeof(WarpSmem<float, float, 32>), "pair area fits a warp's area");
+
+__device__ __forceinline__ void solve_pair32(const SolveArgs<float> &a, int64_t i0,
+                                             PairSmem32 &W, int lane, int co_i, int co_i16) {
+    using namespace pk;
+    const int h = lane >> 4, i = lane & 15;
+    const int64_t is = i0 + h;
+    int64_t beg = 0, end = 0;
+    bool bad = false;
+    if (is < a.m) bad = !row_bounds(a.ptr, is, a.nnz, beg, end);
+    const int64_t s = end - beg;
+    const int64_t smax = max(s, (int64_t)__shfl_xor_sync(FULL, (long long)s, 16));
+    float a0[16], a1[KP], b0 = 0.f, b1 = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) a0[e] = 0.f;
+#pragma unroll
+    for (int e = 0; e < KP; ++e) a1[e] = 0.f;
+    float *st = W.stage + h * PairSmem32::SHALF;
+    // ---- Gram + right-hand side, 16 observations of each system per round
+    for (int64_t c0 = 0; c0 < smax; c0 += 16) {
+        const int64_t t = c0 + i;
+        float4 *dst = reinterpret_cast<float4 *>(st + i * PairSmem32::SROW);
+        float r = 0.f;
+        if (t < s) {
+            int32_t j = __ldg(a.idx + beg + t);
+            r = __ldg(a.val + beg + t);
+            if (j < 0 || (int64_t)j >= a.n_other) {
+                bad = true;
+                j = 0;
+                r = 0.f;
+            }
+            const float4 *src = reinterpret_cast<const float4 *>(a.F + (int64_t)j * KP);
+#pragma unroll
+            for (int e4 = 0; e4 < KP / 4; ++e4) dst[e4] = __ldg(src + e4);
+        } else {
+#pragma unroll
+            for (int e4 = 0; e4 < KP / 4; ++e4) dst[e4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        W.sr[lane] = r;
+        __syncwarp();
+        const int cnt = (int)min((int64_t)16, smax - c0);
+        for (int tt = 0; tt < cnt; ++tt) {
+            const float *x = st + tt * PairSmem32::SROW;
+            const float fi = x[i], fi16 = x[i + 16], rr = W.sr[16 * h + tt];
+            const float4 *x4 = reinterpret_cast<const float4 *>(x);
+#pragma unroll
+            for (int e4 = 0; e4 < KP / 4; ++e4) {
+                const float4 v = x4[e4];
+                if (e4 < 4) {
+                    fma_pair(a0[4 * e4], a0[4 * e4 + 1], fi, v.x, v.y);
+                    fma_pair(a0[4 * e4 + 2], a0[4 * e4 + 3], fi, v.z, v.w);
+                }
+                fma_pair(a1[4 * e4], a1[4 * e4 + 1], fi16, v.x, v.y);
+                fma_pair(a1[4 * e4 + 2], a1[4 * e4 + 3], fi16, v.z, v.w);
+            }
+            b0 = fmaf(rr, fi, b0);
+            b1 = fmaf(rr, fi16, b1);
+        }
+        __syncwarp();   // the stage is rewritten next round
+    }
+    bad = (__ballot_sync(FULL, bad) >> (16 * h)) & 0xffffu;
+    // ---- Cholesky with the forward substitution (lambda added to each pivot)
+    const float lam = float(a.lambda) * (a.wr ? float(s) : 1.f);   // weighted: lambda s_i
+    float *SL = W.L + h * PairSmem32::LS;
+    float y0 = b0, y1 = b1;
+#pragma unroll
+    for (int p = 0; p < KP; ++p) {
+        const float piv = (p < 16 ? __shfl_sync(FULL, a0[p & 15], p, 16)
+                                  : __shfl_sync(FULL, a1[p], p - 16, 16)) + lam;
+        const float inv = rsqrtf(piv);
+        float *Lc = SL + coloff(p) - colbase(p);   // Lc[r] = L[r][p]
+        float l0 = 0.f;
+        if (p < 16) {
+            l0 = a0[p & 15] * inv;
+            a0[p & 15] = l0;
+            if (i >= colbase(p)) Lc[i] = l0;
+        }
+        const float l1 = a1[p] * inv;
+        a1[p] = l1;
+        if (colbase(p) <= 16 || i + 16 >= colbase(p)) Lc[i + 16] = l1;
+        if (i == 0) W.inv[h * PairSmem32::XS + p] = inv;
+        const float yp = (p < 16 ? __shfl_sync(FULL, y0, p, 16)
+                                 : __shfl_sync(FULL, y1, p - 16, 16)) * inv;
+        if (p < 16) {
+            if (i > p) y0 = fmaf(-l0, yp, y0);
+            y1 = fmaf(-l1, yp, y1);
+        } else {
+            if (i + 16 > p) y1 = fmaf(-l1, yp, y1);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r4 = ((p + 1) / 4) * 4; r4 < KP; r4 += 4) {
+            const float4 c4 = *reinterpret_cast<const float4 *>(Lc + r4);
+            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e += 2) {
+                const int r = r4 + e;
+                if (r > p) {
+                    fma2_sub(a1[r], a1[r + 1], l1, cv[e], cv[e + 1]);
+                    if (p < 16 && r < 16) fma2_sub(a0[r & 15], a0[(r + 1) & 15], l0, cv[e], cv[e + 1]);
+                } else if (r + 1 > p) {
+                    a1[r + 1] = fmaf(-l1, cv[e + 1], a1[r + 1]);
+                    if (p < 16 && r + 1 < 16) a0[(r + 1) & 15] = fmaf(-l0, cv[e + 1], a0[(r + 1) & 15]);
+                }
+            }
+        }
+    }
+    const float inv0 = W.inv[h * PairSmem32::XS + i], inv1 = W.inv[h * PairSmem32::XS + i + 16];
+    // ---- back substitution L^T x = y
+    const float2 xx = back_subst(SL, i, co_i, co_i16, y0 * inv0, y1 * inv1, inv0, inv1);
+    float x0 = xx.x, x1 = xx.y;
+    const unsigned fb = __ballot_sync(FULL, !isfinite(x0) || !isfinite(x1));
+    const bool fail = ((fb >> (16 * h)) & 0xffffu) != 0u;
+    if (is < a.m) {
+        int32_t stc = ST_OK;
+        if (bad) stc = ST_BAD;
+        else if (s == 0) stc = ST_EMPTY;
+        else if (fail) stc = ST_NOT_SPD;
+        if (stc != ST_OK) x0 = x1 = 0.f;
+        if (i < a.kout) a.out[is * a.ldo + i] = x0;
+        if (i + 16 < a.kout) a.out[is * a.ldo + i + 16] = x1;
+        if (a.status && i == 0) a.status[is] = stc;
+    }
+    __syncwarp();   // the pair area is reused by the next pair
+}
+
 template <int KP>
 __device__ void solve_range(const SolveArgs<float> &a, int wig, int W, unsigned char *wsbase,
                             int warp, int lane) {
@@ -43,16 +186,27 @@ __device__ void solve_range(const SolveArgs<float> &a, int wig, int W, unsigned 
 }
 
 __device__ void run_half(const SolveArgs<float> &a, int KP, int wig, int W, unsigned char *wsbase,
-                         int warp, int lane) {
+                         int warp, int lane, int co_i, int co_i16) {
     if (KP == 8) solve_range<8>(a, wig, W, wsbase, warp, lane);
     else if (KP == 16) solve_range<16>(a, wig, W, wsbase, warp, lane);
-    else solve_range<32>(a, wig, W, wsbase, warp, lane);
+    else {   // rank 32: two systems per warp
+        PairSmem32 *mine = reinterpret_cast<PairSmem32 *>(wsbase + (size_t)warp * sizeof(WS32));
+        for (int64_t i0 = 2 * (int64_t)wig; i0 < a.m; i0 += 2 * (int64_t)W)
+            solve_pair32(a, i0, *mine, lane, co_i, co_i16);
+    }
 }
 
 __global__ void __launch_bounds__(BW * 32, 2) k_batched_als(BatchArgs b) {   // two CTAs per SM
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int32_t qslot[BW];
+    __shared__ int32_t s_col[32];   // column offsets of the packed rank-32 factor, less their first row
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < 32; ++t) s_col[t] = pk::coloff(t) - pk::colbase(t);
+    }
+    __syncthreads();
+    const int co_i = s_col[lane & 15], co_i16 = s_col[(lane & 15) + 16];
 
     for (int c = 0; c < b.n_classes; ++c) {
         const int W = b.class_W[c];
@@ -142,9 +296,9 @@ __global__ void __launch_bounds__(BW * 32, 2) k_batched_als(BatchArgs b) {   // 
                                 nullptr, b.lambda};
             ua.wr = va.wr = b.wr;
             for (int s = 0; s < b.sweeps; ++s) {
-                run_half(ua, KP, wig, W, gbase, wig, lane);
+                run_half(ua, KP, wig, W, gbase, wig, lane, co_i, co_i16);
                 group_sync(bar, gthreads);
-                run_half(va, KP, wig, W, gbase, wig, lane);
+                run_half(va, KP, wig, W, gbase, wig, lane, co_i, co_i16);
                 group_sync(bar, gthreads);
             }
         }
