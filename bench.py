@@ -520,7 +520,7 @@ def run_gpu_large(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     factor = args.c5_factor
-    prob = synth.make_large_foldin(seed=rank, device=dev)
+    prob = synth.make_large_foldin(seed=rank, m=args.rows, device=dev)
     cpu, gpu = synth.cap_grid(prob.n_cpu, prob.n_gpu)
     m, n, k = prob.m, prob.n, prob.k
     h = ocf.OpenCF(k=k, lam=prob.lam, precision="bf16_gram", cholesky_fp64=(factor == "fp64"),
@@ -590,7 +590,7 @@ def run_gpu_large(args):
     # error against the FP64 oracle on a 10k-row sample (same V, same observations)
     import oracle as orc
     orc.build()
-    rows = np.sort(np.random.default_rng(0).choice(m, 10000, replace=False))
+    rows = np.sort(np.random.default_rng(0).choice(m, min(m, 10000), replace=False))
     sp, sc, sv = c5_sample(prob, rows)
     V = prob.V.double().cpu().numpy()
     t_orc = timed_oracle(lambda: oracle_c5_step(orc, sp, sc, sv, V, prob.lam, cpu, gpu))
@@ -1839,7 +1839,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=30000,
                     help="c4 only: training steps (batch 4096) before the timed completions")
     ap.add_argument("--pool", type=int, default=1 << 20, help="c4 only: training apps")
-    ap.add_argument("--rows", type=int, default=1 << 20, help="c4 only: new apps completed")
+    ap.add_argument("--rows", type=int, default=1 << 20,
+                    help="c4, c5: new apps completed (smaller values for profiling captures)")
     ap.add_argument("--problems", type=int, default=10000, help="c3 only: number of problems")
     ap.add_argument("--c5-factor", default="fp32-refine", choices=sorted(C5_FACTOR),
                     help="c5 only: the k x k factorisation (fp32-refine: FP32 Cholesky + one "

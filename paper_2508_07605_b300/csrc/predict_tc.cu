@@ -287,15 +287,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                                     make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
                             if (trig) {
                                 float bound = fminf(alg2_bound(me, a.Ebase), thr);
+                                // candidates by w alone: fl(w (1 / t_b)) <= bound implies
+                                // w <= bound t_b (1 + 2^-22), so bw below keeps a superset
+                                // (invalid elements carry w = inf); each is re-checked
+                                // exactly below
+                                const float bw = __fmul_rn(__fmul_rn(bound, rc.tb), 1.00000095367431640625f);
                                 uint32_t mask = 0u;
 #pragma unroll
-                                for (int e = 0; e < GS; ++e)
-                                    mask |= (w[e] < inf && __fmul_rn(w[e], rc.rtb) <= bound ? 1u : 0u) << e;
+                                for (int e = 0; e < GS; ++e) mask |= (w[e] <= bw ? 1u : 0u) << e;
                                 while (mask) {
                                     const int e = __ffs(mask) - 1;
                                     mask &= mask - 1u;
                                     const float t = stash[e];
-                                    if (t > 0.0f && __fmul_rn(__fmul_rn(cg_of(j0 + e), t), rc.rtb) <= bound) {
+                                    if (t > 0.0f && __float_as_uint(t) <= tsb &&
+                                        __fmul_rn(__fmul_rn(cg_of(j0 + e), t), rc.rtb) <= bound) {
                                         alg2_exact(best, rc, t, cg_of(j0 + e), a.Ebase, (int32_t)(j0 + e));
                                         bound = fminf(bound, best.Ethr);
                                     }

@@ -89,6 +89,13 @@ def test_foldin_ragged_rows_every_k(orc, precision, k):
     ok = np.diff(ptr) > 0
     assert err[ok].max() <= TOL[precision], (err[ok].max(), np.argmax(err))
     assert np.abs(host(U)[~ok]).max(initial=0.0) == 0.0
+    # the plain relative error |u - u_or| / |u_or| beside it: rows above the gate
+    # under that measure are those whose right-hand side cancels (solve_err)
+    plain = row_rel_err(host(U), Uref)[ok]
+    loose = int((plain > TOL[precision]).sum())
+    print(f"k={k} {precision}: plain relative error max {plain.max():.2e} median "
+          f"{np.median(plain):.2e}; {loose} of {ok.sum()} rows need the cancellation scale")
+    assert np.median(plain) <= TOL[precision]
 
 
 def test_foldin_bad_index_is_flagged_not_read(orc):
