@@ -110,52 +110,102 @@ cudaError_t launch_batched_pack(int64_t P, const int64_t *rows, const int32_t *k
                                 const int64_t *t_off, const int64_t *f_off, const float *src,
                                 float *dst, bool to_padded, cudaStream_t st);
 
-// MLP warm start (mlp.cu).
-constexpr int MLP_IN = 48, MLP_INP = 64, MLP_H = 256, MLP_SIN = 16;
-enum { EPI_BIAS_SELU = 0, EPI_BIAS = 1, EPI_DSELU = 2, EPI_PART = 3 };
-struct GemmArgs {
-    int M, N, K;
-    const void *A;            // bf16: [M,K] row-major, or [K,M] when transposed
-    int lda;
-    const void *B;            // bf16: [K,N] row-major, or [N,K] when transposed
-    int ldb;
-    const float *bias;        // [N]
-    const void *Zin;          // bf16 [M,N] pre-activations (EPI_DSELU)
-    void *out_bf;             // bf16 output
-    float *out_f;             // FP32 output / split-K partials
-    void *out_z;              // bf16 pre-activation output (EPI_BIAS_SELU)
-    int ldo;
-};
-cudaError_t launch_gemm(const GemmArgs &g, bool at, bool bt, int epi, int splits,
-                        cudaStream_t st);
-cudaError_t launch_mlp_features(int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
-                                const float *val, const float *cnorm, const float *gnorm,
-                                int64_t n, void *X, cudaStream_t st);
-cudaError_t launch_sum_parts(int64_t count, int splits, const float *part, float *out,
-                             cudaStream_t st);
-cudaError_t launch_colsum(int M, int N, const void *A, float *part, float *out, cudaStream_t st);
-cudaError_t launch_mlp_loss(int B, int k, const float *Y, const float *T, const float *G,
-                            void *dY, int ldd, float *part, double *loss, cudaStream_t st);
-cudaError_t launch_gram_v(int64_t n, int KP, int k, const float *V, float *part, float *G,
-                          cudaStream_t st);   // part: 64 * k * k floats
+// MLP warm start (mlp.cu, mlp_tc.cu, mlp_train_tc.cu).
+constexpr int MLP_IN = 48, MLP_INP = 64, MLP_H = 256, MLP_SIN = 16, MLP_K_OUT = 32;
+// Internal parameter layout (FP32 masters): W1[64][256] (input rows 48 .. 63
+// stay zero), b1[256], W2[256][256], b2[256], W3[256][32], b3[32]; W[in][out].
+constexpr int64_t MLP_OFF_W1 = 0, MLP_OFF_B1 = MLP_INP * MLP_H,
+                  MLP_OFF_W2 = MLP_OFF_B1 + MLP_H, MLP_OFF_B2 = MLP_OFF_W2 + MLP_H * MLP_H,
+                  MLP_OFF_W3 = MLP_OFF_B2 + MLP_H, MLP_OFF_B3 = MLP_OFF_W3 + MLP_H * MLP_K_OUT,
+                  MLP_P_INT = MLP_OFF_B3 + MLP_K_OUT;
+// BF16 weight images (element offsets; layouts in mlp_tc.cuh): W2 for the
+// forward product (4 chunks of 256 x 64), W1 (256 x 64), W3 forward (32 x 256),
+// W2 for the backward product (4 chunks of 256 x 64), W3 backward (256 x 32).
+constexpr int64_t MLP_IMG_W2F = 0, MLP_IMG_W1 = MLP_IMG_W2F + MLP_H * MLP_H,
+                  MLP_IMG_W3F = MLP_IMG_W1 + MLP_INP * MLP_H,
+                  MLP_IMG_W2B = MLP_IMG_W3F + MLP_H * MLP_K_OUT,
+                  MLP_IMG_W3B = MLP_IMG_W2B + MLP_H * MLP_H,
+                  MLP_IMG_TOTAL = MLP_IMG_W3B + MLP_H * MLP_K_OUT;
 // Adam step counter and step size in device memory (zero = before step 1).
 struct AdamState {
     int64_t t;
     float lr;
 };
 // state: 16 bytes of device memory holding an AdamState
-// BF16 copies of the parameters: entry e goes to thb[map[e]] and img[imap[e]]
-// (an index < 0 means no copy).
-cudaError_t launch_adam(int64_t count, float *th, const float *g, float *m1, float *m2, float b1,
-                        float b2, float eps, void *state, const int64_t *bf_map, void *thb,
-                        const int64_t *img_map, void *img, cudaStream_t st);
 cudaError_t launch_adam_set_lr(void *state, float lr, cudaStream_t st);
-cudaError_t launch_to_bf16_map(int64_t count, const float *th, const int64_t *bf_map, void *thb,
-                               const int64_t *img_map, void *img, cudaStream_t st);
-cudaError_t launch_fallback_rows(int64_t m, const float *rmse, float thr, int32_t *list,
-                                 int64_t *count, int32_t *status, cudaStream_t st);
 cudaError_t launch_fallback_mark(int64_t m, const int32_t *list, const int64_t *count,
                                  int32_t *status, cudaStream_t st);
+// img (MLP_IMG_TOTAL BF16) from the FP32 masters th (MLP_P_INT)
+cudaError_t launch_mlp_images(const float *th, void *img, cudaStream_t st);
+
+// One CTA's slot of partial sums of a training step (floats): dW2 [256][256],
+// dW1 [64][256], dW3 [256][32], db1 [4][256], db2 [4][256], db3 [4][32] (per
+// TMEM lane quarter), loss [16] (per warp).
+constexpr int64_t MLP_PART_W2 = 0, MLP_PART_W1 = MLP_PART_W2 + MLP_H * MLP_H,
+                  MLP_PART_W3 = MLP_PART_W1 + MLP_INP * MLP_H,
+                  MLP_PART_B1 = MLP_PART_W3 + MLP_H * MLP_K_OUT,
+                  MLP_PART_B2 = MLP_PART_B1 + 4 * MLP_H, MLP_PART_B3 = MLP_PART_B2 + 4 * MLP_H,
+                  MLP_PART_LOSS = MLP_PART_B3 + 4 * MLP_K_OUT, MLP_PART_STRIDE = 92416;
+constexpr int MLP_GRAM_PARTS = 32;   // slices of G = V^T V, added in order
+struct MlpTrainArgs {
+    int64_t m, nnz;                   // batch rows B and their observations
+    const int64_t *ptr;
+    const int32_t *idx;
+    const float *val;
+    const float *ccap, *gcap;         // normalised CPU caps [n_cpu], GPU caps [n_gpu]
+    int32_t n_gpu;                    // setting j = c * n_gpu + g
+    int64_t n;
+    const void *img;                  // BF16 weight images
+    const float *b1, *b2, *b3;        // FP32 biases
+    const float *T;                   // B x 32 targets, 16-byte aligned
+    const float *G;                   // 32 x 32, G = V^T V (launch_mlp_gram)
+    float scale;                      // 2 / B
+    float *part;                      // grid x MLP_PART_STRIDE
+    AdamState *adam;                  // advanced once (NULL: gradient only)
+    int *err;                         // err[1] set when a bounded wait ran out
+};
+size_t mlp_train_tc_part_floats(int64_t B, int num_sms);
+cudaError_t prepare_mlp_train_tc();
+cudaError_t launch_mlp_train_tc(const MlpTrainArgs &a, int num_sms, cudaStream_t st);
+// G = V^T V (32 x 32) via MLP_GRAM_PARTS slices; ticket: one zeroed word, left zero
+cudaError_t launch_mlp_gram(int64_t n, int KP, const float *V, float *Gpart, float *G,
+                            unsigned int *ticket, cudaStream_t st);
+struct MlpReduceArgs {
+    const float *part;                // slots of the training kernel
+    int ctas;
+    float *th, *m1, *m2;              // FP32 masters and moments (MLP_P_INT)
+    const AdamState *adam;            // NULL: gradient only
+    void *img;                        // BF16 images refreshed after the update
+    float *grads_out;                 // gradient-only mode: external layout
+    double *loss;                     // may be NULL
+    int64_t B;
+    const int *err;
+};
+cudaError_t launch_mlp_reduce_adam(const MlpReduceArgs &a, cudaStream_t st);
+
+// Fused tcgen05 forward pass (mlp_tc.cu) over the images above.
+struct MlpTcArgs {
+    int64_t m, nnz;
+    const int64_t *ptr;
+    const int32_t *idx;
+    const float *val;
+    const float *ccap, *gcap;     // normalised CPU caps [n_cpu], GPU caps [n_gpu]
+    int32_t n_gpu;                // setting j = c * n_gpu + g
+    int64_t n;
+    const void *img;              // BF16 weight images
+    const float *b1, *b2, *b3;
+    float *Y;                     // m x 32, 16-byte aligned
+    const float *V;               // n x 32 setting factors (observed-entry residual)
+    float threshold;              // fallback when the row's RMSE is above it (or not finite)
+    float *row_rmse;              // m, may be null
+    int32_t *status;              // m, may be null: OK or FALLBACK_USED
+    int32_t *list;                // fallback rows, appended at list[*count]
+    int64_t *count;
+    int *err;                     // set to 1 when a bounded wait ran out
+};
+size_t mlp_forward_tc_smem();
+cudaError_t prepare_mlp_forward_tc();
+cudaError_t launch_mlp_forward_tc(const MlpTcArgs &a, int num_sms, cudaStream_t st);
 
 // Reconstruction on the tensor cores fused with Algorithm 2 (predict_tc.cu):
 // BF16-Gram precision mode, KP = 32.  Vimg: split BF16 operand images of V in
@@ -187,35 +237,6 @@ cudaError_t launch_predict_select_tc(const PredictTcArgs &a, int num_sms, cudaSt
 cudaError_t launch_phase_detect(const float *power, int64_t n_traces, int64_t len, int64_t ld,
                                 float p_th, int32_t window, int64_t *first, cudaStream_t st);
 
-// Fused tcgen05 forward pass (mlp_tc.cu).  img holds the BF16 weight images
-// W2 | W1 | W3 (element offsets below), each an N x K K-major operand image:
-// element (n, k) at (n / 8) * 8K + (k / 8) * 64 + (n % 8) * 8 + k % 8.
-constexpr int MLP_K_OUT = 32;
-constexpr int64_t MLP_IMG_W2 = 0, MLP_IMG_W1 = MLP_H * MLP_H,
-                  MLP_IMG_W3 = MLP_IMG_W1 + MLP_INP * MLP_H,
-                  MLP_IMG_TOTAL = MLP_IMG_W3 + MLP_H * MLP_K_OUT;
-struct MlpTcArgs {
-    int64_t m, nnz;
-    const int64_t *ptr;
-    const int32_t *idx;
-    const float *val;
-    const float *ccap, *gcap;     // normalised CPU caps [n_cpu], GPU caps [n_gpu]
-    int32_t n_gpu;                // setting j = c * n_gpu + g
-    int64_t n;
-    const void *img;              // BF16 weight images
-    const float *b1, *b2, *b3;
-    float *Y;                     // m x 32, 16-byte aligned
-    const float *V;               // n x 32 setting factors (observed-entry residual)
-    float threshold;              // fallback when the row's RMSE is above it (or not finite)
-    float *row_rmse;              // m, may be null
-    int32_t *status;              // m, may be null: OK or FALLBACK_USED
-    int32_t *list;                // fallback rows, appended at list[*count]
-    int64_t *count;
-    int *err;                     // set to 1 when a bounded wait ran out
-};
-size_t mlp_forward_tc_smem();
-cudaError_t prepare_mlp_forward_tc();
-cudaError_t launch_mlp_forward_tc(const MlpTcArgs &a, int num_sms, cudaStream_t st);
 
 // Reconstruction T = U V^T fused with Algorithm 2.
 template <typename TV> struct PredictArgs {

@@ -20,12 +20,8 @@
 //     turns in a 32 KB stage buffer, fetched by bulk asynchronous copies
 //     (cp.async.bulk + mbarrier transaction counts) while the epilogues run.
 //
-// Operand images (no swizzle, K-major): an R x K BF16 matrix is stored as
-// 8 x 8 core matrices of 128 contiguous bytes; element (r, k) lives at byte
-//   (r / 8) * (16 K) + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
-// so the descriptor's leading-dimension offset (next core matrix along K)
-// is 128 B and its stride-dimension offset (next 8 rows) is 16 K bytes.
-// The engine keeps the weights' BF16 copies in exactly this form, so they
+// Operand images: see mlp_tc.cuh.  The engine keeps the weights' BF16 copies
+// in exactly that form (W2 as four 256 x 64 chunks along its inputs), so they
 // reach shared memory by plain bulk copies.
 //
 // Every wait is bounded.  A CTA whose wait runs out records the event in
@@ -37,121 +33,22 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "tc_util.cuh"
+#include "mlp_tc.cuh"
 
 namespace ocf {
 
 namespace {
 
 using namespace tc;
+using namespace mlp;
 typedef __nv_bfloat16 bf16;
 
-constexpr int TM = 128;   // rows per tile (UMMA M)
 constexpr int NTHREADS = 512;
 constexpr uint32_t OFF_W2 = 0, OFF_STAGE = 131072, OFF_ACT = 163840, OFF_BAR = 229376;
 constexpr uint32_t OFF_BIAS = OFF_BAR + 64;   // b1 | b2 | b3 (FP32)
 constexpr uint32_t SMEM_BYTES = OFF_BIAS + 4 * (2 * 256 + 32);
 constexpr uint32_t BYTES_W2 = 131072, BYTES_W1 = 32768, BYTES_W3 = 16384;
 constexpr uint32_t TMEM_COLS = 512;   // layer-1 / layer-3 accumulator at 0, layer-2 at 256
-
-constexpr float SELU_L = 1.0507009873554804934193349852946f;
-constexpr float SELU_A = 1.6732632423543772848170429916717f;
-
-__device__ __forceinline__ float selu_f(float z) {
-    const float e = __expf(fminf(z, 0.f)) - 1.f;
-    return z > 0.f ? SELU_L * z : (SELU_L * SELU_A) * e;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-// The tile's rows are shared by groups of four lanes (row r = tid / 4, lane
-// g = tid % 4), the same mapping the residual uses: lane g takes the row's
-// observation slots g, g + 4, g + 8, g + 12 (the first 16 in setting order),
-// keeps their indices and values in registers until the residual, and writes
-// their features (c_norm, g_norm, runtime) into the BF16 feature image (K = 64;
-// slot s -> features 3s .. 3s + 2; features 48 .. 63 stay zero).
-struct RowObs {
-    int64_t beg, end;
-    bool ok;
-    int32_t j[4];   // -1: no observation in the slot, or an index out of range
-    float v[4];
-};
-
-__device__ __forceinline__ void features_quad(const MlpTcArgs &a, int64_t i, int r, int g,
-                                              unsigned char *act, RowObs &o) {
-    o.beg = 0;
-    o.end = 0;
-    o.ok = i < a.m && row_bounds(a.ptr, i, a.nnz, o.beg, o.end);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int64_t t = o.beg + g + 4 * b;
-        o.j[b] = -1;
-        o.v[b] = 0.f;
-        if (o.ok && t < o.end) {
-            const int32_t jj = __ldg(a.idx + t);
-            o.v[b] = __ldg(a.val + t);
-            if (jj >= 0 && (int64_t)jj < a.n) o.j[b] = jj;
-        }
-    }
-    unsigned char *row = act + (r >> 3) * (MLP_INP * 16) + (r & 7) * 16;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int s = g + 4 * b;
-        float c = 0.f, gg = 0.f, v = 0.f;
-        if (o.j[b] >= 0) {
-            const int32_t ci = o.j[b] / a.n_gpu;
-            c = __ldg(a.ccap + ci);
-            gg = __ldg(a.gcap + (o.j[b] - ci * a.n_gpu));
-            v = o.v[b];
-        }
-        const float x[3] = {c, gg, v};
-#pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            const int f = 3 * s + e;
-            *reinterpret_cast<bf16 *>(row + (f >> 3) * 128 + (f & 7) * 2) = __float2bfloat16_rn(x[e]);
-        }
-    }
-    if (g < 2) *reinterpret_cast<uint4 *>(row + (6 + g) * 128) = make_uint4(0, 0, 0, 0);
-}
-
-// Hidden-layer epilogue: this warp's 32 rows, columns [c0, c0 + 64) of the
-// accumulator at TMEM column tacc: bias (from shared memory) + SELU -> BF16
-// image (K = 256).  Both TMEM loads are in flight before the first wait.
-__device__ __forceinline__ void epi_hidden(uint32_t tmem, uint32_t tacc, int q, int lane, int c0,
-                                           const float *bias_s, unsigned char *act) {
-    const int r = 32 * q + lane;
-    unsigned char *row = act + (r >> 3) * (MLP_H * 16) + (r & 7) * 16;
-    uint32_t v0[32], v1[32];
-    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + tacc + (uint32_t)c0;
-    tc_ld32(ta, v0);
-    tc_ld32(ta + 32, v1);
-    tc_wait_ld();
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        uint32_t pk[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int c = 8 * g + 2 * e;
-            pk[e] = pack_bf16(selu_f(__uint_as_float(v0[c]) + bias_s[c0 + c]),
-                              selu_f(__uint_as_float(v0[c + 1]) + bias_s[c0 + c + 1]));
-        }
-        *reinterpret_cast<uint4 *>(row + (c0 / 8 + g) * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    }
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        uint32_t pk[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int c = 8 * g + 2 * e;
-            pk[e] = pack_bf16(selu_f(__uint_as_float(v1[c]) + bias_s[c0 + 32 + c]),
-                              selu_f(__uint_as_float(v1[c + 1]) + bias_s[c0 + 32 + c + 1]));
-        }
-        *reinterpret_cast<uint4 *>(row + ((c0 + 32) / 8 + g) * 128) =
-            make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    }
-}
 
 // Observed-entry RMSE of the tile's 128 rows under u (shared memory, rows of
 // U_STRIDE floats), one group of four lanes per row: per observation the
@@ -303,7 +200,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
     if (tid == 0 && (int64_t)blockIdx.x < tiles) {
         mbar_expect_tx(bar_w2, BYTES_W2);
         for (uint32_t c = 0; c < BYTES_W2; c += 32768)
-            bulk_g2s(s0 + OFF_W2 + c, img + 2 * MLP_IMG_W2 + c, 32768, bar_w2);
+            bulk_g2s(s0 + OFF_W2 + c, img + 2 * MLP_IMG_W2F + c, 32768, bar_w2);
         mbar_expect_tx(bar_st, BYTES_W1);
         bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W1, BYTES_W1, bar_st);
         st_pending = true;
@@ -343,7 +240,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
             tc_fence_after();
             if (tid == 0) {   // W1 is free: fetch W3 while the epilogue runs
                 mbar_expect_tx(bar_st, BYTES_W3);
-                bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W3, BYTES_W3, bar_st);
+                bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W3F, BYTES_W3, bar_st);
                 st_pending = true;
             }
             epi_hidden(tmem, 0, q, lane, 64 * cq, bias_s, sm + OFF_ACT);
@@ -353,9 +250,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
             // ---- layer 2: ACT (128 x 256) x W2 (256 x 256)^T -> TMEM [256, 512)
             if (tid == 0) {
                 tc_fence_after();
-                for (int s = 0; s < MLP_H / 16; ++s)
+                for (int s = 0; s < MLP_H / 16; ++s)   // W2: four 256 x 64 chunks
                     tc_mma(tmem + 256, sdesc(s0 + OFF_ACT + s * 256, 128, MLP_H * 16),
-                           sdesc(s0 + OFF_W2 + s * 256, 128, MLP_H * 16), id256, s > 0);
+                           sdesc(s0 + OFF_W2 + (s >> 2) * 32768 + (s & 3) * 256, 128, 64 * 16),
+                           id256, s > 0);
                 tc_commit(bar_mma);
             }
             if (warp == 1 && has_next) prefetch_tile(a, row0 + (int64_t)gridDim.x * TM, lane);

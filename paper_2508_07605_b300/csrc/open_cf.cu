@@ -60,15 +60,14 @@ struct open_cf {
     int32_t b_class_W[BATCH_MAX_CLASSES] = {};
     int64_t b_Um = 0, b_Vn = 0;       // padded factor sizes (floats)
     // learned warm start: FP32 master parameters, Adam moments, BF16 weights, scratch
-    Buf mlp_th, mlp_g, mlp_m1, mlp_m2, mlp_bf, mlp_map, mlp_t, mlp_cn, mlp_scr, mlp_G;
-    Buf mlp_img, mlp_imap, mlp_err;   // tcgen05 weight images, their map, timeout flag
+    Buf mlp_th, mlp_m1, mlp_m2, mlp_t, mlp_cn, mlp_scr;   // masters, moments, Adam state, caps, step scratch
+    Buf mlp_img, mlp_err;   // tcgen05 weight images, timeout flags
     Buf vimg, pt_err;                 // split BF16 operand images of V, timeout flag (predict)
     Buf ccount;                       // observations per column (weighted-lambda objective)
     Buf sg, sb, sn;                   // streaming refit: per-setting Gram, RHS, count sums
     bool stream_on = false;
     int num_sms = 0;
     bool mlp_ready = false;
-    int64_t mlp_Bcap = 0;
     uint64_t generation = 0;  // bumps whenever a workspace moves
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
@@ -498,51 +497,11 @@ namespace {
 
 // Parameter layout.  External (the caller's, and the oracle's): W1[48][256],
 // b1[256], W2[256][256], b2[256], W3[256][32], b3[32] = 86,560 floats.
-// Internal: W1 padded to [64][256] (rows 48..63 stay zero), rest identical.
+// Internal (MLP_OFF_*): W1 padded to [64][256] (rows 48..63 stay zero), rest identical.
 constexpr int64_t MLP_K = 32;
 constexpr int64_t P_EXT = MLP_IN * MLP_H + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H * MLP_K + MLP_K;
-constexpr int64_t P_INT = P_EXT + (MLP_INP - MLP_IN) * MLP_H;
 static_assert(P_EXT == OPEN_CF_MLP_PARAMS, "parameter count of the C ABI");
-constexpr int64_t OFF_W1 = 0, OFF_B1 = MLP_INP * MLP_H, OFF_W2 = OFF_B1 + MLP_H,
-                  OFF_B2 = OFF_W2 + MLP_H * MLP_H, OFF_W3 = OFF_B2 + MLP_H,
-                  OFF_B3 = OFF_W3 + MLP_H * MLP_K;
-// BF16 weight copies: W1b [64][256], W2b [256][256], W3b [256][32]
-constexpr int64_t BF_W1 = 0, BF_W2 = MLP_INP * MLP_H, BF_W3 = BF_W2 + MLP_H * MLP_H,
-                  BF_TOTAL = BF_W3 + MLP_H * MLP_K;
-
-struct MlpScratch {   // per chunk of Bp rows (multiple of 64)
-    void *X, *Z1, *H1, *Z2, *H2, *dY, *dZ2, *dZ1;
-    float *Y, *part, *cpart, *lpart;
-};
-
-size_t mlp_scratch_bytes(int64_t Bp) {
-    return 2 * (size_t)Bp * MLP_INP + 2 * 7 * (size_t)Bp * MLP_H + 2 * (size_t)Bp * MLP_K +
-           4 * (size_t)Bp * MLP_K + 4 * (size_t)(1 << 20) + 4 * (size_t)(Bp / 128 + 1) * MLP_H +
-           4 * 1024 + 8 * 256;
-}
-
-MlpScratch mlp_scratch(open_cf_t *h, int64_t Bp) {
-    unsigned char *p = (unsigned char *)h->mlp_scr.p;
-    auto take = [&](size_t bytes) {
-        void *q = p;
-        p += (bytes + 255) / 256 * 256;
-        return q;
-    };
-    MlpScratch S;
-    S.X = take(2 * Bp * MLP_INP);
-    S.Z1 = take(2 * Bp * MLP_H);
-    S.H1 = take(2 * Bp * MLP_H);
-    S.Z2 = take(2 * Bp * MLP_H);
-    S.H2 = take(2 * Bp * MLP_H);
-    S.dY = take(2 * Bp * MLP_K);
-    S.dZ2 = take(2 * Bp * MLP_H);
-    S.dZ1 = take(2 * Bp * MLP_H);
-    S.Y = (float *)take(4 * Bp * MLP_K);
-    S.part = (float *)take(4 * (size_t)(1 << 20));
-    S.cpart = (float *)take(4 * (size_t)(Bp / 128 + 1) * MLP_H);
-    S.lpart = (float *)take(4 * 1024);
-    return S;
-}
+static_assert(MLP_P_INT == P_EXT + (MLP_INP - MLP_IN) * MLP_H, "internal parameter count");
 
 int mlp_check(open_cf_t *h) {
     if (h->k != MLP_K) return fail(h, OPEN_CF_UNSUPPORTED, "the learned warm start has k = 32");
@@ -553,52 +512,6 @@ int mlp_check(open_cf_t *h) {
         return fail(h, OPEN_CF_INVALID_ARG, "cap grid size differs from the settings of V");
     if (!h->mlp_ready) return fail(h, OPEN_CF_NOT_FITTED, "set the MLP parameters first");
     return OPEN_CF_OK;
-}
-
-int mlp_ensure_scratch(open_cf_t *h, int64_t Bp) {
-    if (Bp > h->mlp_Bcap) {
-        CK(h, ensure(h, h->mlp_scr, mlp_scratch_bytes(Bp) + 16 * 256));
-        h->mlp_Bcap = Bp;
-    }
-    return OPEN_CF_OK;
-}
-
-// Forward pass of Bp rows (features already in S.X).
-cudaError_t mlp_forward(open_cf_t *h, const MlpScratch &S, int Bp, cudaStream_t st) {
-    const float *th = (const float *)h->mlp_th.p;
-    const unsigned char *wb = (const unsigned char *)h->mlp_bf.p;
-    GemmArgs g{};
-    g.M = Bp; g.N = MLP_H; g.K = MLP_INP;
-    g.A = S.X; g.lda = MLP_INP; g.B = wb + 2 * BF_W1; g.ldb = MLP_H;
-    g.bias = th + OFF_B1; g.out_bf = S.H1; g.out_z = S.Z1; g.ldo = MLP_H;
-    cudaError_t e = launch_gemm(g, false, false, EPI_BIAS_SELU, 1, st);
-    if (e != cudaSuccess) return e;
-    g.K = MLP_H; g.A = S.H1; g.lda = MLP_H; g.B = wb + 2 * BF_W2; g.bias = th + OFF_B2;
-    g.out_bf = S.H2; g.out_z = S.Z2;
-    if ((e = launch_gemm(g, false, false, EPI_BIAS_SELU, 1, st)) != cudaSuccess) return e;
-    GemmArgs g3{};
-    g3.M = Bp; g3.N = MLP_K; g3.K = MLP_H; g3.A = S.H2; g3.lda = MLP_H; g3.B = wb + 2 * BF_W3;
-    g3.ldb = MLP_K; g3.bias = th + OFF_B3; g3.out_f = S.Y; g3.ldo = MLP_K;
-    return launch_gemm(g3, false, false, EPI_BIAS, 1, st);
-}
-
-int splits_for(int64_t Kdim, int want) {
-    int s = want;
-    while (s > 1 && (Kdim % (32LL * s) != 0)) s >>= 1;
-    return s;
-}
-
-// dW = A^T dZ over Bp rows (split-K, fixed-order sum) into grad region g_out.
-cudaError_t weight_grad(const MlpScratch &S, const void *A, int M, const void *dZ, int N, int Bp,
-                        float *g_out, cudaStream_t st) {
-    const int want = (int)std::max<int64_t>(1, 256 / (((M + 63) / 64) * ((N + 63) / 64)));
-    const int s = splits_for(Bp, std::min(want, (int)((1 << 20) / ((int64_t)M * N))));
-    GemmArgs g{};
-    g.M = M; g.N = N; g.K = Bp; g.A = A; g.lda = M; g.B = dZ; g.ldb = N; g.out_f = S.part;
-    g.ldo = N;
-    cudaError_t e = launch_gemm(g, true, false, EPI_PART, s, st);
-    if (e != cudaSuccess) return e;
-    return launch_sum_parts((int64_t)M * N, s, S.part, g_out, st);
 }
 
 }  // namespace
@@ -655,7 +568,8 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
     if (prepare_csr_to_csc(CSC_MAX_N) != cudaSuccess || prepare_row_solve() != cudaSuccess ||
         prepare_row_solve_tc() != cudaSuccess || prepare_solve32_tc() != cudaSuccess ||
         prepare_batched() != cudaSuccess ||
-        prepare_mlp_forward_tc() != cudaSuccess || prepare_predict_tc() != cudaSuccess ||
+        prepare_mlp_forward_tc() != cudaSuccess || prepare_mlp_train_tc() != cudaSuccess ||
+        prepare_predict_tc() != cudaSuccess ||
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
             cudaSuccess) {
         cudaGetLastError();
@@ -677,8 +591,7 @@ void open_cf_destroy(open_cf_t *h) {
                        &h->csc_ptr, &h->csc_idx, &h->csc_val, &h->cnt, &h->tot, &h->part,
                        &h->flag, &h->j_ptr, &h->j_idx, &h->j_val, &h->Ub16, &h->b_meta, &h->b_Uw,
                        &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter, &h->mlp_th,
-                       &h->mlp_g, &h->mlp_m1, &h->mlp_m2, &h->mlp_bf, &h->mlp_map, &h->mlp_t,
-                       &h->mlp_cn, &h->mlp_scr, &h->mlp_G, &h->mlp_img, &h->mlp_imap,
+                       &h->mlp_m1, &h->mlp_m2, &h->mlp_t, &h->mlp_cn, &h->mlp_scr, &h->mlp_img,
                        &h->mlp_err, &h->vimg, &h->pt_err, &h->ccount, &h->sg, &h->sb,
                        &h->sn})
             free_buf(*b);
@@ -1358,48 +1271,22 @@ int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
     if (!params) return fail(h, OPEN_CF_INVALID_ARG, "params is NULL");
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
-    CK(h, ensure(h, h->mlp_th, 4 * P_INT));
-    CK(h, ensure(h, h->mlp_g, 4 * P_INT));
-    CK(h, ensure(h, h->mlp_m1, 4 * P_INT));
-    CK(h, ensure(h, h->mlp_m2, 4 * P_INT));
-    CK(h, ensure(h, h->mlp_bf, 2 * BF_TOTAL));
-    CK(h, ensure(h, h->mlp_map, 8 * P_INT));
-    CK(h, ensure(h, h->mlp_imap, 8 * P_INT));
+    CK(h, ensure(h, h->mlp_th, 4 * MLP_P_INT));
+    CK(h, ensure(h, h->mlp_m1, 4 * MLP_P_INT));
+    CK(h, ensure(h, h->mlp_m2, 4 * MLP_P_INT));
     CK(h, ensure(h, h->mlp_img, 2 * MLP_IMG_TOTAL));
     CK(h, ensure(h, h->mlp_err, 16));
     CK(h, cudaMemsetAsync(h->mlp_err.p, 0, 16, st));
     CK(h, ensure(h, h->mlp_t, 16));
-    CK(h, ensure(h, h->mlp_G, 4 * MLP_K * MLP_K));
     float *th = (float *)h->mlp_th.p;
-    CK(h, cudaMemsetAsync(th, 0, 4 * P_INT, st));
+    CK(h, cudaMemsetAsync(th, 0, 4 * MLP_P_INT, st));
     CK(h, cudaMemcpyAsync(th, params, 4 * MLP_IN * MLP_H, cudaMemcpyDeviceToDevice, st));
-    CK(h, cudaMemcpyAsync(th + OFF_B1, params + MLP_IN * MLP_H, 4 * (P_EXT - MLP_IN * MLP_H),
+    CK(h, cudaMemcpyAsync(th + MLP_OFF_B1, params + MLP_IN * MLP_H, 4 * (P_EXT - MLP_IN * MLP_H),
                           cudaMemcpyDeviceToDevice, st));
-    CK(h, cudaMemsetAsync(h->mlp_m1.p, 0, 4 * P_INT, st));
-    CK(h, cudaMemsetAsync(h->mlp_m2.p, 0, 4 * P_INT, st));
+    CK(h, cudaMemsetAsync(h->mlp_m1.p, 0, 4 * MLP_P_INT, st));
+    CK(h, cudaMemsetAsync(h->mlp_m2.p, 0, 4 * MLP_P_INT, st));
     CK(h, cudaMemsetAsync(h->mlp_t.p, 0, 16, st));
-    std::vector<int64_t> map(P_INT, -1);
-    for (int64_t e = 0; e < MLP_INP * MLP_H; ++e) map[OFF_W1 + e] = BF_W1 + e;
-    for (int64_t e = 0; e < MLP_H * MLP_H; ++e) map[OFF_W2 + e] = BF_W2 + e;
-    for (int64_t e = 0; e < MLP_H * MLP_K; ++e) map[OFF_W3 + e] = BF_W3 + e;
-    CK(h, cudaMemcpy(h->mlp_map.p, map.data(), 8 * P_INT, cudaMemcpyHostToDevice));
-    // K-major operand images of the fused forward pass: W_l[in = k][out = n]
-    std::fill(map.begin(), map.end(), -1);
-    auto image = [](int64_t n, int64_t k, int64_t K) {
-        return (n / 8) * (8 * K) + (k / 8) * 64 + (n % 8) * 8 + k % 8;
-    };
-    for (int64_t k = 0; k < MLP_INP; ++k)
-        for (int64_t n = 0; n < MLP_H; ++n)
-            map[OFF_W1 + k * MLP_H + n] = MLP_IMG_W1 + image(n, k, MLP_INP);
-    for (int64_t k = 0; k < MLP_H; ++k)
-        for (int64_t n = 0; n < MLP_H; ++n)
-            map[OFF_W2 + k * MLP_H + n] = MLP_IMG_W2 + image(n, k, MLP_H);
-    for (int64_t k = 0; k < MLP_H; ++k)
-        for (int64_t n = 0; n < MLP_K; ++n)
-            map[OFF_W3 + k * MLP_K + n] = MLP_IMG_W3 + image(n, k, MLP_H);
-    CK(h, cudaMemcpy(h->mlp_imap.p, map.data(), 8 * P_INT, cudaMemcpyHostToDevice));
-    CK(h, launch_to_bf16_map(P_INT, th, (const int64_t *)h->mlp_map.p, h->mlp_bf.p,
-                             (const int64_t *)h->mlp_imap.p, h->mlp_img.p, st));
+    CK(h, launch_mlp_images(th, h->mlp_img.p, st));   // the tensor cores' BF16 operand images
     // normalised caps of every setting (features), FP32
     const int64_t ns = (int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size();
     if (ns > 0) {
@@ -1408,16 +1295,12 @@ int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
         const double gmin = *std::min_element(h->gpu_caps.begin(), h->gpu_caps.end());
         const double gmax = *std::max_element(h->gpu_caps.begin(), h->gpu_caps.end());
         const int nc = (int)h->cpu_caps.size(), ng = (int)h->gpu_caps.size();
-        // [c_norm per setting | g_norm per setting | c_norm per CPU cap | g_norm per GPU cap]
-        std::vector<float> cn(2 * ns + nc + ng);
+        // [c_norm per CPU cap | g_norm per GPU cap]
+        std::vector<float> cn(nc + ng);
         auto cnorm = [&](double c) { return (float)(cmax > cmin ? (c - cmin) / (cmax - cmin) : 0.0); };
         auto gnorm = [&](double g) { return (float)(gmax > gmin ? (g - gmin) / (gmax - gmin) : 0.0); };
-        for (int64_t j = 0; j < ns; ++j) {
-            cn[j] = cnorm(h->cpu_caps[j / ng]);
-            cn[ns + j] = gnorm(h->gpu_caps[j % ng]);
-        }
-        for (int c = 0; c < nc; ++c) cn[2 * ns + c] = cnorm(h->cpu_caps[c]);
-        for (int g = 0; g < ng; ++g) cn[2 * ns + nc + g] = gnorm(h->gpu_caps[g]);
+        for (int c = 0; c < nc; ++c) cn[c] = cnorm(h->cpu_caps[c]);
+        for (int g = 0; g < ng; ++g) cn[nc + g] = gnorm(h->gpu_caps[g]);
         CK(h, ensure(h, h->mlp_cn, 4 * cn.size()));
         CK(h, cudaMemcpy(h->mlp_cn.p, cn.data(), 4 * cn.size(), cudaMemcpyHostToDevice));
     }
@@ -1434,7 +1317,7 @@ int open_cf_mlp_get_params(open_cf_t *h, float *params_out, void *stream) {
     DeviceGuard g(h->device);
     const float *th = (const float *)h->mlp_th.p;
     CK(h, cudaMemcpyAsync(params_out, th, 4 * MLP_IN * MLP_H, cudaMemcpyDeviceToDevice, S(stream)));
-    CK(h, cudaMemcpyAsync(params_out + MLP_IN * MLP_H, th + OFF_B1, 4 * (P_EXT - MLP_IN * MLP_H),
+    CK(h, cudaMemcpyAsync(params_out + MLP_IN * MLP_H, th + MLP_OFF_B1, 4 * (P_EXT - MLP_IN * MLP_H),
                           cudaMemcpyDeviceToDevice, S(stream)));
     return OPEN_CF_OK;
 }
@@ -1451,56 +1334,44 @@ int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *
     if (B <= 0 || !U_target) return fail(h, OPEN_CF_INVALID_ARG, "empty batch or no targets");
     if (!(lr >= 0.0f) || !std::isfinite(lr)) return fail(h, OPEN_CF_INVALID_ARG, "bad lr");
     if (B > (1 << 20)) return fail(h, OPEN_CF_UNSUPPORTED, "batch above 2^20 rows");
+    if ((uintptr_t)U_target % 16) return fail(h, OPEN_CF_INVALID_ARG, "U_target not 16-byte aligned");
     DeviceGuard g(h->device);
-    const int Bp = (int)((B + 63) / 64 * 64);
-    rc = mlp_ensure_scratch(h, Bp);
-    if (rc) return rc;
-    const MlpScratch Sx = mlp_scratch(h, Bp);
-    const int64_t ns = h->n;
+    // scratch: the slices of G = V^T V, G, the slices' ticket (zero between
+    // launches), then one slot of partial sums per CTA
+    const size_t g_floats = (size_t)MLP_GRAM_PARTS * MLP_K * MLP_K + MLP_K * MLP_K + 64;
+    const size_t p_floats = mlp_train_tc_part_floats(B, h->num_sms);
+    const size_t cap0 = h->mlp_scr.bytes;
+    CK(h, ensure(h, h->mlp_scr, 4 * (g_floats + p_floats)));
+    float *Gpart = (float *)h->mlp_scr.p, *Gfin = Gpart + MLP_GRAM_PARTS * MLP_K * MLP_K;
+    unsigned int *ticket = (unsigned int *)(Gfin + MLP_K * MLP_K);
+    float *part = Gpart + g_floats;
+    if (h->mlp_scr.bytes != cap0) CK(h, cudaMemsetAsync(ticket, 0, 4, S(stream)));
     std::vector<int64_t> key = {3, B, nnz, (int64_t)row_ptr, (int64_t)col, (int64_t)val,
                                 (int64_t)U_target, (int64_t)loss_out, (int64_t)grads_out};
     if (!grads_out) CK(h, launch_adam_set_lr(h->mlp_t.p, lr, S(stream)));
     return run_graph(h, key, S(stream), [&](cudaStream_t st) -> cudaError_t {
-        float *th = (float *)h->mlp_th.p, *gr = (float *)h->mlp_g.p;
-        const float *cn = (const float *)h->mlp_cn.p;
-        cudaError_t e = cudaMemsetAsync(Sx.X, 0, 2 * (size_t)Bp * MLP_INP, st);
+        float *th = (float *)h->mlp_th.p;
+        cudaError_t e = launch_mlp_gram(h->n, h->KP, (const float *)h->V.p, Gpart, Gfin, ticket, st);
         if (e != cudaSuccess) return e;
-        if ((e = launch_mlp_features(B, nnz, row_ptr, col, val, cn, cn + ns, ns, Sx.X, st)))
-            return e;
-        if ((e = mlp_forward(h, Sx, Bp, st))) return e;
-        if ((e = launch_gram_v(ns, h->KP, MLP_K, (const float *)h->V.p, Sx.part,
-                               (float *)h->mlp_G.p, st)))
-            return e;
-        if ((e = cudaMemsetAsync(Sx.dY, 0, 2 * (size_t)Bp * MLP_K, st))) return e;
-        if ((e = launch_mlp_loss((int)B, MLP_K, Sx.Y, U_target, (const float *)h->mlp_G.p, Sx.dY,
-                                 MLP_K, Sx.lpart, loss_out, st)))
-            return e;
-        const unsigned char *wb = (const unsigned char *)h->mlp_bf.p;
-        // layer 3
-        if ((e = weight_grad(Sx, Sx.H2, MLP_H, Sx.dY, MLP_K, Bp, gr + OFF_W3, st))) return e;
-        if ((e = launch_colsum(Bp, MLP_K, Sx.dY, Sx.cpart, gr + OFF_B3, st))) return e;
-        GemmArgs gb{};
-        gb.M = Bp; gb.N = MLP_H; gb.K = MLP_K; gb.A = Sx.dY; gb.lda = MLP_K;
-        gb.B = wb + 2 * BF_W3; gb.ldb = MLP_K; gb.Zin = Sx.Z2; gb.out_bf = Sx.dZ2; gb.ldo = MLP_H;
-        if ((e = launch_gemm(gb, false, true, EPI_DSELU, 1, st))) return e;
-        // layer 2
-        if ((e = weight_grad(Sx, Sx.H1, MLP_H, Sx.dZ2, MLP_H, Bp, gr + OFF_W2, st))) return e;
-        if ((e = launch_colsum(Bp, MLP_H, Sx.dZ2, Sx.cpart, gr + OFF_B2, st))) return e;
-        gb.K = MLP_H; gb.A = Sx.dZ2; gb.lda = MLP_H; gb.B = wb + 2 * BF_W2; gb.ldb = MLP_H;
-        gb.Zin = Sx.Z1; gb.out_bf = Sx.dZ1;
-        if ((e = launch_gemm(gb, false, true, EPI_DSELU, 1, st))) return e;
-        // layer 1 (the padded input columns give zero gradients)
-        if ((e = weight_grad(Sx, Sx.X, MLP_INP, Sx.dZ1, MLP_H, Bp, gr + OFF_W1, st))) return e;
-        if ((e = launch_colsum(Bp, MLP_H, Sx.dZ1, Sx.cpart, gr + OFF_B1, st))) return e;
-        if (grads_out) {
-            if ((e = cudaMemcpyAsync(grads_out, gr, 4 * MLP_IN * MLP_H, cudaMemcpyDeviceToDevice, st)))
-                return e;
-            return cudaMemcpyAsync(grads_out + MLP_IN * MLP_H, gr + OFF_B1,
-                                   4 * (P_EXT - MLP_IN * MLP_H), cudaMemcpyDeviceToDevice, st);
-        }
-        return launch_adam(P_INT, th, gr, (float *)h->mlp_m1.p, (float *)h->mlp_m2.p, 0.9f,
-                           0.999f, 1e-8f, h->mlp_t.p, (const int64_t *)h->mlp_map.p, h->mlp_bf.p,
-                           (const int64_t *)h->mlp_imap.p, h->mlp_img.p, st);
+        MlpTrainArgs ta{};
+        ta.m = B; ta.nnz = nnz; ta.ptr = row_ptr; ta.idx = col; ta.val = val;
+        ta.ccap = (const float *)h->mlp_cn.p;
+        ta.gcap = ta.ccap + h->cpu_caps.size();
+        ta.n_gpu = (int32_t)h->gpu_caps.size();
+        ta.n = h->n;
+        ta.img = h->mlp_img.p;
+        ta.b1 = th + MLP_OFF_B1; ta.b2 = th + MLP_OFF_B2; ta.b3 = th + MLP_OFF_B3;
+        ta.T = U_target; ta.G = Gfin; ta.scale = 2.0f / (float)B; ta.part = part;
+        ta.adam = grads_out ? nullptr : (AdamState *)h->mlp_t.p;
+        ta.err = (int *)h->mlp_err.p;
+        if ((e = launch_mlp_train_tc(ta, h->num_sms, st)) != cudaSuccess) return e;
+        MlpReduceArgs ra{};
+        ra.part = part; ra.ctas = (int)(p_floats / MLP_PART_STRIDE);
+        ra.th = th; ra.m1 = (float *)h->mlp_m1.p; ra.m2 = (float *)h->mlp_m2.p;
+        ra.adam = grads_out ? nullptr : (const AdamState *)h->mlp_t.p;
+        ra.img = h->mlp_img.p; ra.grads_out = grads_out; ra.loss = loss_out; ra.B = B;
+        ra.err = (const int *)h->mlp_err.p;
+        return launch_mlp_reduce_adam(ra, st);
     });
 }
 
@@ -1524,13 +1395,13 @@ int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
     // fused forward pass on the tensor cores (tcgen05), straight into U_out
     MlpTcArgs ta{};
     ta.m = m; ta.nnz = nnz; ta.ptr = row_ptr; ta.idx = col; ta.val = val;
-    ta.ccap = (const float *)h->mlp_cn.p + 2 * h->n;
+    ta.ccap = (const float *)h->mlp_cn.p;
     ta.gcap = ta.ccap + h->cpu_caps.size();
     ta.n_gpu = (int32_t)h->gpu_caps.size();
     ta.n = h->n;
     ta.img = h->mlp_img.p;
     const float *th = (const float *)h->mlp_th.p;
-    ta.b1 = th + OFF_B1; ta.b2 = th + OFF_B2; ta.b3 = th + OFF_B3;
+    ta.b1 = th + MLP_OFF_B1; ta.b2 = th + MLP_OFF_B2; ta.b3 = th + MLP_OFF_B3;
     ta.Y = U_out; ta.err = (int *)h->mlp_err.p;
     // the kernel also evaluates each row's observed-entry RMSE and lists the
     // rows above the threshold; those are re-solved by the ridge fold-in

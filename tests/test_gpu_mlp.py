@@ -98,6 +98,29 @@ def test_mlp_loss_and_gradients_match_oracle(orc, seed):
     assert np.array_equal(host(h.mlp_get_params()), _flat(params))
 
 
+@pytest.mark.parametrize("m", [1, 148 * 128 + 300])
+def test_mlp_gradients_over_tiles_match_oracle(orc, m):
+    """The fused training step at one row, and with more 128-row tiles than
+    SMs (two CTAs add a second tile into their partial sums); the gradient is
+    bit-reproducible from call to call."""
+    ptr, col, val, V, cpu, gpu, params = _small(20 + m % 5, m=m)
+    rng = np.random.default_rng(200 + m)
+    Yt = (rng.standard_normal((m, K)) / 2).astype(np.float32).astype(np.float64)
+    h = _handle(V, cpu, gpu, params)
+    csr = csr_dev(ptr, col, val, torch.float32)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    g1 = h.mlp_train_step(*csr, dev(Yt, torch.float32), loss=loss, grads=True)
+    g2 = h.mlp_train_step(*csr, dev(Yt, torch.float32), grads=True)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+    X = orc.mlp_features(ptr, col, val, cpu, gpu)
+    L, gref = orc.mlp_loss_grad(X, params, Yt, V.T @ V)
+    assert abs(float(host(loss)[0]) - L) <= TOL_BF16 * abs(L)
+    for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), _split(host(g1).astype(np.float64)),
+                          gref):
+        assert _rel(a, b) <= TOL_BF16, (name, _rel(a, b))
+
+
 def test_mlp_forward_and_residual_match_oracle(orc):
     ptr, col, val, V, cpu, gpu, params = _small(2, m=333)
     h = _handle(V, cpu, gpu, params)
