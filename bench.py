@@ -1048,6 +1048,9 @@ WORKLOAD_C4 = "learned warm start: MLP 48->256->256->32 SELU (BF16 tensor cores,
               "15 sweeps); completes 2^20 new apps from 16 observed settings each, ALS fold-in " \
               "fallback where the observed-entry RMSE > 0.02"
 MLP_SIZES = (48, 256, 256, 32)
+# per training sample: forward 48*256 + 256*256 + 256*32 MACs; backward dH2, dW3 (256*32
+# each), dH1, dW2 (256*256 each), dW1 (48*256); 2 FLOP per MAC
+MLP_TRAIN_FLOP = 2 * (48 * 256 + 256 * 256 + 256 * 32 + 2 * 256 * 32 + 2 * 256 * 256 + 48 * 256)
 
 
 def _mlp_split(flat):
@@ -1092,30 +1095,31 @@ def run_gpu_learned(args):
     h.mlp_set_params(torch.tensor(flat0, device=dev))
     B, steps, lr0 = 4096, args.train_steps, 2e-3
     rp = torch.arange(0, (B + 1) * S, S, dtype=torch.int64, device=dev)
-    cb = torch.empty(B, S, dtype=torch.int32, device=dev)
-    vb = torch.empty(B, S, dtype=torch.float32, device=dev)
-    tb = torch.empty(B, K, dtype=torch.float32, device=dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(1)
-    pos = pool
+    # one shuffle of the pool per epoch; the steps of an epoch take consecutive
+    # batches of the shuffled copy (every pool row has S observations, so one
+    # row_ptr serves every batch).  Throughput is timed over bursts of 128
+    # consecutive steps inside an epoch (device time, CUDA events).
+    per_epoch = pool // B
     t_samples = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for step in range(steps):
-        if pos + B > pool:
-            perm = torch.randperm(pool, generator=gen, device=dev)
-            pos = 0
-        idx = perm[pos:pos + B]
-        pos += B
-        torch.index_select(pc, 0, idx, out=cb)
-        torch.index_select(pv, 0, idx, out=vb)
-        torch.index_select(pt, 0, idx, out=tb)
-        e0.record(stream)
-        h.mlp_train_step(rp, cb.view(-1), vb.view(-1), tb,
-                         lr=lr0 * 0.5 * (1 + math.cos(math.pi * step / steps)))
-        e1.record(stream)
-        if step >= 10 and step % 64 == 0:   # sampled: an event sync costs more than a step
-            e1.synchronize()
-            t_samples.append(e0.elapsed_time(e1) / 1e3)
+    step = 0
+    while step < steps:
+        perm = torch.randperm(pool, generator=gen, device=dev)
+        cs, vs, ts = pc[perm], pv[perm], pt[perm]
+        for b in range(min(per_epoch, steps - step)):
+            if b == 8:
+                e0.record(stream)
+            h.mlp_train_step(rp, cs[b * B:(b + 1) * B].view(-1), vs[b * B:(b + 1) * B].view(-1),
+                             ts[b * B:(b + 1) * B],
+                             lr=lr0 * 0.5 * (1 + math.cos(math.pi * step / steps)))
+            if b == 8 + 127:
+                e1.record(stream)
+                e1.synchronize()
+                t_samples.append(e0.elapsed_time(e1) / 1e3 / 128)
+            step += 1
+        del cs, vs, ts
     train_sps = B / statistics.mean(t_samples) if t_samples else None
     del pc, pv, pt
     # new apps (2^20 by default), 16 observed settings each; noiseless rows kept
@@ -1258,6 +1262,16 @@ def run_gpu_learned(args):
         "mlp_only": {"value": M / t_mlp, "unit": "rows/s", "ms": t_mlp * 1e3},
         "fallback_fraction": frac_fb,
         "train_samples_per_s": train_sps,
+        "training": {
+            "samples_per_s": train_sps, "batch": B,
+            "ms_per_step": (B / train_sps * 1e3) if train_sps else None,
+            "kernels": "k_mlp_gram + k_mlp_train_tc (fused forward/backward on tcgen05) + "
+                       "k_mlp_reduce_adam, chained by programmatic dependent launch",
+            "flop_per_sample": MLP_TRAIN_FLOP,
+            "tflops": (MLP_TRAIN_FLOP * train_sps / 1e12) if train_sps else None,
+            "frac_of_bf16_peak": (MLP_TRAIN_FLOP * train_sps / 1e12 / bf16_peak) if train_sps
+                                 else None,
+            "timing": "device time of bursts of 128 consecutive steps (CUDA events)"},
         "learned_vs_plain_at_equal_rmse": {
             "gate": "held-out RMSE <= FP64 oracle fold-in RMSE + 1e-3", "oracle_rmse": rmse_orc,
             "gate_value": gate, "plain_fold_in_rows_per_s": plain_rps,

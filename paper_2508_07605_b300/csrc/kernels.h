@@ -140,7 +140,7 @@ cudaError_t launch_mlp_images(const float *th, void *img, cudaStream_t st);
 
 // One CTA's slot of partial sums of a training step (floats): dW2 [256][256],
 // dW1 [64][256], dW3 [256][32], db1 [4][256], db2 [4][256], db3 [4][32] (per
-// TMEM lane quarter), loss [16] (per warp).
+// TMEM lane quarter), loss [32] (per warp of the two CTAs of a cluster pair).
 constexpr int64_t MLP_PART_W2 = 0, MLP_PART_W1 = MLP_PART_W2 + MLP_H * MLP_H,
                   MLP_PART_W3 = MLP_PART_W1 + MLP_INP * MLP_H,
                   MLP_PART_B1 = MLP_PART_W3 + MLP_H * MLP_K_OUT,
@@ -160,13 +160,18 @@ struct MlpTrainArgs {
     const float *T;                   // B x 32 targets, 16-byte aligned
     const float *G;                   // 32 x 32, G = V^T V (launch_mlp_gram)
     float scale;                      // 2 / B
-    float *part;                      // grid x MLP_PART_STRIDE
+    float *part;                      // slots x MLP_PART_STRIDE (mlp_train_tc_slots)
     AdamState *adam;                  // advanced once (NULL: gradient only)
     int *err;                         // err[1] set when a bounded wait ran out
 };
-size_t mlp_train_tc_part_floats(int64_t B, int num_sms);
+// slots of partial sums: one per cluster pair (at most num_sms / 2 tiles),
+// else one per CTA of the one-CTA-per-tile kernel (mlp_train_tc1.cu)
+int mlp_train_tc_slots(int64_t B, int num_sms);
 cudaError_t prepare_mlp_train_tc();
-cudaError_t launch_mlp_train_tc(const MlpTrainArgs &a, int num_sms, cudaStream_t st);
+cudaError_t prepare_mlp_train_tc1();
+// pdl: launched as a programmatic dependent of the preceding kernel
+cudaError_t launch_mlp_train_tc(const MlpTrainArgs &a, int num_sms, bool pdl, cudaStream_t st);
+cudaError_t launch_mlp_train_tc1(const MlpTrainArgs &a, int grid, bool pdl, cudaStream_t st);
 // G = V^T V (32 x 32) via MLP_GRAM_PARTS slices; ticket: one zeroed word, left zero
 cudaError_t launch_mlp_gram(int64_t n, int KP, const float *V, float *Gpart, float *G,
                             unsigned int *ticket, cudaStream_t st);

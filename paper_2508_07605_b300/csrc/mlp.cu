@@ -83,7 +83,7 @@ constexpr int RED_PARAMS = 64;   // parameters per CTA of the reduction; 4 slot 
 __global__ void __launch_bounds__(256) k_mlp_reduce_adam(MlpReduceArgs a) {
     __shared__ float corr[3];
     __shared__ float gs[4][RED_PARAMS];
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");   // the training kernel's partials
+    mlp::pdl_wait();   // the training kernel's partial sums
     const bool failed = a.err && a.err[1] != 0;
     const float nan = __int_as_float(0x7fc00000);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(256) k_mlp_reduce_adam(MlpReduceArgs a) {
     }
     if (blockIdx.x == 0 && warp == 0 && a.loss) {   // loss: warp 0, fixed order
         double s = 0.0;
-        for (int64_t x = lane; x < (int64_t)a.ctas * 16; x += 32)
-            s += __ldcg(a.part + (x >> 4) * MLP_PART_STRIDE + MLP_PART_LOSS + (x & 15));
+        for (int64_t x = lane; x < (int64_t)a.ctas * 32; x += 32)
+            s += __ldcg(a.part + (x >> 5) * MLP_PART_STRIDE + MLP_PART_LOSS + (x & 31));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
         if (lane == 0) *a.loss = failed ? (double)nan : s / (double)a.B;

@@ -160,5 +160,24 @@ __device__ __forceinline__ void epi_hidden(uint32_t tmem, uint32_t tacc, int q, 
     }
 }
 
+// Programmatic dependent launch within a training step: the training kernel
+// lets the reduction launch at once; the reduction waits for it before its
+// first read of the partial sums.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// Store (first tile of a slot's owner) or add (later tiles) one partial sum.
+__device__ __forceinline__ void acc_store(float *p, float v, bool first) {
+    *p = first ? v : *p + v;
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+    return x;
+}
+
 }  // namespace mlp
 }  // namespace ocf

@@ -62,6 +62,9 @@ struct open_cf {
     // learned warm start: FP32 master parameters, Adam moments, BF16 weights, scratch
     Buf mlp_th, mlp_m1, mlp_m2, mlp_t, mlp_cn, mlp_scr;   // masters, moments, Adam state, caps, step scratch
     Buf mlp_img, mlp_err;   // tcgen05 weight images, timeout flags
+    // V changes (set, fit, streaming refit) advance v_epoch; the MLP loss matrix
+    // G = V^T V in the step scratch is current while mlp_g_epoch == v_epoch
+    uint64_t v_epoch = 1, mlp_g_epoch = 0;
     Buf vimg, pt_err;                 // split BF16 operand images of V, timeout flag (predict)
     Buf ccount;                       // observations per column (weighted-lambda objective)
     Buf sg, sb, sn;                   // streaming refit: per-setting Gram, RHS, count sums
@@ -197,6 +200,7 @@ template <typename TV>
 int fit_sweeps(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
                const TV *val, TV *U_out, int64_t u_row0, int64_t u_rows, int32_t *row_status,
                int32_t *col_status, double *J_hist, cudaStream_t stream) {
+    h->v_epoch++;   // the sweeps rewrite V
     const int64_t n = h->n;
     const int KP = h->KP;
     const CscPlan plan = csc_plan(m, n, nnz, 0);
@@ -633,6 +637,7 @@ int open_cf_set_V(open_cf_t *h, const void *V, int64_t n, void *stream) {
     h->n = n;
     h->stream_on = false;   // a new V starts a new stream
     h->V_set = true;
+    h->v_epoch++;
     return OPEN_CF_OK;
 }
 
@@ -870,6 +875,7 @@ cudaError_t stream_vhalf_enqueue(open_cf_t *h, int64_t m, int64_t nnz, const int
 template <typename TV>
 int stream_vhalf(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
                  const TV *val, const TV *Uw, cudaStream_t st) {
+    h->v_epoch++;   // the refit rewrites V
     int rc = stream_vhalf_ws<TV>(h, m, nnz);
     if (rc) return rc;
     CK(h, stream_vhalf_enqueue<TV>(h, m, nnz, ptr, idx, val, Uw, st));
@@ -889,6 +895,7 @@ int stream_begin_t(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, con
 template <typename TV>
 int stream_ingest_t(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ptr, const int32_t *idx,
                     const TV *val, TV *U_out, int32_t *status, cudaStream_t st) {
+    h->v_epoch++;   // the refit rewrites V
     const int KP = h->KP;
     CK(h, ensure(h, h->U_w, sizeof(TV) * std::max<int64_t>(m, 1) * KP));
     int rc = stream_vhalf_ws<TV>(h, m, nnz);
@@ -1339,20 +1346,26 @@ int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *
     // scratch: the slices of G = V^T V, G, the slices' ticket (zero between
     // launches), then one slot of partial sums per CTA
     const size_t g_floats = (size_t)MLP_GRAM_PARTS * MLP_K * MLP_K + MLP_K * MLP_K + 64;
-    const size_t p_floats = mlp_train_tc_part_floats(B, h->num_sms);
+    const int slots = mlp_train_tc_slots(B, h->num_sms);
+    const size_t p_floats = (size_t)slots * MLP_PART_STRIDE;
     const size_t cap0 = h->mlp_scr.bytes;
     CK(h, ensure(h, h->mlp_scr, 4 * (g_floats + p_floats)));
     float *Gpart = (float *)h->mlp_scr.p, *Gfin = Gpart + MLP_GRAM_PARTS * MLP_K * MLP_K;
     unsigned int *ticket = (unsigned int *)(Gfin + MLP_K * MLP_K);
     float *part = Gpart + g_floats;
-    if (h->mlp_scr.bytes != cap0) CK(h, cudaMemsetAsync(ticket, 0, 4, S(stream)));
+    if (h->mlp_scr.bytes != cap0) {   // a new scratch: the ticket is zeroed, G recomputed
+        CK(h, cudaMemsetAsync(ticket, 0, 4, S(stream)));
+        h->mlp_g_epoch = 0;
+    }
+    if (h->mlp_g_epoch != h->v_epoch) {   // G = V^T V, once per V
+        CK(h, launch_mlp_gram(h->n, h->KP, (const float *)h->V.p, Gpart, Gfin, ticket, S(stream)));
+        h->mlp_g_epoch = h->v_epoch;
+    }
     std::vector<int64_t> key = {3, B, nnz, (int64_t)row_ptr, (int64_t)col, (int64_t)val,
                                 (int64_t)U_target, (int64_t)loss_out, (int64_t)grads_out};
     if (!grads_out) CK(h, launch_adam_set_lr(h->mlp_t.p, lr, S(stream)));
     return run_graph(h, key, S(stream), [&](cudaStream_t st) -> cudaError_t {
         float *th = (float *)h->mlp_th.p;
-        cudaError_t e = launch_mlp_gram(h->n, h->KP, (const float *)h->V.p, Gpart, Gfin, ticket, st);
-        if (e != cudaSuccess) return e;
         MlpTrainArgs ta{};
         ta.m = B; ta.nnz = nnz; ta.ptr = row_ptr; ta.idx = col; ta.val = val;
         ta.ccap = (const float *)h->mlp_cn.p;
@@ -1364,9 +1377,10 @@ int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *
         ta.T = U_target; ta.G = Gfin; ta.scale = 2.0f / (float)B; ta.part = part;
         ta.adam = grads_out ? nullptr : (AdamState *)h->mlp_t.p;
         ta.err = (int *)h->mlp_err.p;
-        if ((e = launch_mlp_train_tc(ta, h->num_sms, st)) != cudaSuccess) return e;
+        cudaError_t e = launch_mlp_train_tc(ta, h->num_sms, false, st);
+        if (e != cudaSuccess) return e;
         MlpReduceArgs ra{};
-        ra.part = part; ra.ctas = (int)(p_floats / MLP_PART_STRIDE);
+        ra.part = part; ra.ctas = slots;
         ra.th = th; ra.m1 = (float *)h->mlp_m1.p; ra.m2 = (float *)h->mlp_m2.p;
         ra.adam = grads_out ? nullptr : (const AdamState *)h->mlp_t.p;
         ra.img = h->mlp_img.p; ra.grads_out = grads_out; ra.loss = loss_out; ra.B = B;

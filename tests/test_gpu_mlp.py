@@ -98,11 +98,13 @@ def test_mlp_loss_and_gradients_match_oracle(orc, seed):
     assert np.array_equal(host(h.mlp_get_params()), _flat(params))
 
 
-@pytest.mark.parametrize("m", [1, 148 * 128 + 300])
+@pytest.mark.parametrize("m", [1, 74 * 128, 75 * 128 + 5, 148 * 128 + 300])
 def test_mlp_gradients_over_tiles_match_oracle(orc, m):
-    """The fused training step at one row, and with more 128-row tiles than
-    SMs (two CTAs add a second tile into their partial sums); the gradient is
-    bit-reproducible from call to call."""
+    """The fused training step at one row; at 74 tiles (the largest batch the
+    cluster-pair kernel takes: one pair of CTAs per tile); at 75 tiles (the
+    one-CTA-per-tile kernel); and with more tiles than SMs (CTAs add a second
+    tile into their partial sums).  The gradient is bit-reproducible from
+    call to call."""
     ptr, col, val, V, cpu, gpu, params = _small(20 + m % 5, m=m)
     rng = np.random.default_rng(200 + m)
     Yt = (rng.standard_normal((m, K)) / 2).astype(np.float32).astype(np.float64)
@@ -119,6 +121,28 @@ def test_mlp_gradients_over_tiles_match_oracle(orc, m):
     for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), _split(host(g1).astype(np.float64)),
                           gref):
         assert _rel(a, b) <= TOL_BF16, (name, _rel(a, b))
+
+
+def test_mlp_gradient_follows_V(orc):
+    """The loss matrix G = V^T V is kept between steps while V is unchanged;
+    a new V (set_V) gives the gradient of the new loss."""
+    ptr, col, val, V, cpu, gpu, params = _small(30, m=300)
+    m = len(ptr) - 1
+    Yt = (np.random.default_rng(31).standard_normal((m, K)) / 2).astype(np.float32).astype(np.float64)
+    h = _handle(V, cpu, gpu, params)
+    csr = csr_dev(ptr, col, val, torch.float32)
+    X = orc.mlp_features(ptr, col, val, cpu, gpu)
+    V2 = (np.random.default_rng(32).standard_normal(V.shape) / 2).astype(np.float32).astype(np.float64)
+    for Vk in (V, V2):
+        h.set_V(dev(Vk, torch.float32))
+        loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+        g = h.mlp_train_step(*csr, dev(Yt, torch.float32), loss=loss, grads=True)
+        torch.cuda.synchronize()
+        L, gref = orc.mlp_loss_grad(X, params, Yt, Vk.T @ Vk)
+        assert abs(float(host(loss)[0]) - L) <= TOL_BF16 * abs(L)
+        for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"),
+                              _split(host(g).astype(np.float64)), gref):
+            assert _rel(a, b) <= TOL_BF16, (name, _rel(a, b))
 
 
 def test_mlp_forward_and_residual_match_oracle(orc):
