@@ -45,6 +45,26 @@ __device__ __forceinline__ RowCtx alg2_row(float tb, float gamma) {
         r.tstar = __uint_as_float(0x7f800000u);   // every finite t > 0 is valid
         return r;
     }
+    // In real numbers the bound is t_b / (1 - gamma); the rounded comparison
+    // moves it by a few units in the last place, so a short walk from there
+    // usually finds the transition (ok(t*) and not ok(next float)).  ok is
+    // monotone, so that transition is the one the bisection finds; a walk that
+    // does not end within 8 steps falls through to the bisection.
+    const float g1 = __fsub_rn(1.0f, gamma);
+    if (g1 > 0.0f) {
+        uint32_t b = __float_as_uint(__fdiv_rn(tb, g1));
+        if (b > 0u && b < hi) {
+            if (ok(b)) {
+                int s = 0;
+                while (s < 8 && ok(b + 1u)) { ++b; ++s; }
+                if (s < 8) { r.tstar = __uint_as_float(b); return r; }
+            } else {
+                int s = 0;
+                while (s < 8 && b > 1u && !ok(b - 1u)) { --b; ++s; }
+                if (s < 8 && b > 1u) { r.tstar = __uint_as_float(b - 1u); return r; }
+            }
+        }
+    }
     while (hi - lo > 1u) {
         const uint32_t mid = lo + (hi - lo) / 2u;
         if (ok(mid)) lo = mid; else hi = mid;

@@ -53,7 +53,8 @@ constexpr uint32_t OFF_CAND = OFF_TB + TM * 4;             // [TM][4] candidates
 constexpr uint32_t OFF_BAR = OFF_CAND + TM * 4 * sizeof(Cand);
 constexpr int STASH_LD = GS + 4;                           // floats per lane: 144 B, conflict-free rows
 constexpr uint32_t OFF_STASH = OFF_BAR + 128;              // per lane: the group's runtimes
-constexpr uint32_t OFF_CG = OFF_STASH + NEPI * 32 * STASH_LD * 4;   // c + g table (when it fits)
+constexpr uint32_t OFF_THR = OFF_STASH + NEPI * 32 * STASH_LD * 4;  // [TM][4] screening thresholds
+constexpr uint32_t OFF_CG = OFF_THR + TM * 4 * 4;                   // c + g table (when it fits)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int BAR_TILE = 1, BAR_EPI = 2;                    // named barriers
 
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
         Cand *cand_s = reinterpret_cast<Cand *>(sm + OFF_CAND);
         const int col_b = (int)(a.base - (int64_t)cb * CN);
         float *stash_s = reinterpret_cast<float *>(sm + OFF_STASH);
+        volatile float *thr_s = reinterpret_cast<volatile float *>(sm + OFF_THR);
         const float inf = __int_as_float(0x7f800000);
         auto cg_of = [&](int64_t j) { return cg_smem ? cg_s[j] : a.cg_pad[j]; };
         int64_t g = 0;
@@ -202,6 +204,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                 *reinterpret_cast<uint4 *>(sm + OFF_UH + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 *reinterpret_cast<uint4 *>(sm + OFF_UL + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
+            // this row's screening threshold, shared by its four column quarters
+            thr_s[r * 4 + cq] = inf;
             fence_async_smem();
             named_sync(BAR_TILE, (NEPI + 1) * 32);
 
@@ -276,8 +280,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                         // minimum (usually the minimum alone) is evaluated exactly, in
                         // a per-row loop over the candidates' bit mask, with the group's
                         // runtimes stashed in shared memory for indexed access.
+                        // The threshold is the smallest of the four quarters' (each
+                        // derived from an exactly evaluated candidate of this row, so an
+                        // element above it can neither win nor tie the row's final best;
+                        // a quarter's value read before its latest update is only looser).
                         const float me = __fmul_rn(wmin, rc.rtb);
-                        const float thr = best.j >= 0 ? best.Ethr : inf;
+                        float4 tq;
+                        asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                                     : "=f"(tq.x), "=f"(tq.y), "=f"(tq.z), "=f"(tq.w)
+                                     : "r"(s0 + OFF_THR + (uint32_t)(16 * r)));
+                        const float thr = fminf(fminf(fminf(tq.x, tq.y), fminf(tq.z, tq.w)),
+                                                best.j >= 0 ? best.Ethr : inf);
                         const bool trig = wmin < inf && me <= thr;
                         if (__any_sync(FULL, trig)) {
                             float *stash = stash_s + (warp * 32 + lane) * STASH_LD;
@@ -305,6 +318,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
                                         bound = fminf(bound, best.Ethr);
                                     }
                                 }
+                                if (best.j >= 0) thr_s[r * 4 + cq] = best.Ethr;
                             }
                         }
                     }

@@ -339,6 +339,36 @@ def test_predict_and_select_parity(orc, precision, m, gamma):
         assert (Eb - cg / p) / Eb >= s64[i] - 1e-5
 
 
+@pytest.mark.parametrize("gamma", [0.0, 1e-30, 0.05, 0.1, 0.3, 0.9999, 1.0, 2.0, -0.05, -3.0])
+def test_select_loss_bound_edges(orc, gamma):
+    """Runtimes a few units in the last place on either side of the loss
+    bound t_b / (1 - gamma), for several baselines: the kernel's validity
+    test (a largest valid runtime per row) must pick exactly the settings the
+    oracle's per-element FP32 check keeps."""
+    cpu, gpu = synth.cap_grid(4, 8)
+    n = len(cpu) * len(gpu)
+    base = oracle.baseline_index(cpu, gpu)
+    rng = np.random.default_rng(11)
+    tbs = np.array([1.0, 0.37, 3.0e-3, 7.25, 1.0e5, 0.999999, 2.0 ** -20], np.float32)
+    rows = []
+    for tb in tbs:
+        g1 = np.float32(1.0) - np.float32(gamma)
+        t0 = np.float32(tb / g1) if g1 > 0 else np.float32(tb * 4)
+        for _ in range(3):
+            steps = rng.integers(-6, 7, size=n).astype(np.int64)
+            bits = np.int64(t0.view(np.int32)) + steps
+            t = np.clip(bits, 1, 0x7f7fffff).astype(np.int32).view(np.float32)
+            t[base] = tb
+            rows.append(t)
+    T = np.stack(rows).astype(np.float32)
+    h = _handle(1, 0.1, caps=(cpu, gpu))
+    b, s = h.select(dev(T, torch.float32), gamma=gamma)
+    torch.cuda.synchronize()
+    b_or, s_or = orc.select_f32(T, cpu, gpu, gamma)
+    assert np.array_equal(host(b), b_or)
+    assert np.array_equal(host(s), s_or)
+
+
 def test_predict_without_dense_output_matches():
     rng = np.random.default_rng(4)
     cpu, gpu = synth.cap_grid(8, 15)
