@@ -276,7 +276,137 @@ __device__ __forceinline__ void fetch_pair(const SolveArgs<float> &a, int64_t k,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Thin rows (s_i <= 16 observations, fewer than k = 32): the same ridge
+// solution from the s_i x s_i dual system.  With S the s_i x k matrix of the
+// observed factor rows,
+//     (S^T S + lambda I) u = S^T r   <=>   u = S^T w,  (S S^T + lambda I) w = r
+// (multiply the second by S^T: S^T S S^T w + lambda S^T w = S^T r).  The dual
+// matrix has the primal's nonzero eigenvalues, so its condition number is at
+// most the primal's, and its factorisation is 16 x 16 instead of 32 x 32.
+// Both rows of a pair must be thin (a warp-uniform choice); padded
+// observations are zero rows of S with r = 0, so they solve to w = 0.
+//
+// Layout: row h's 16 staged observations sit in stage buffer h; G_h = S S^T
+// goes to shared memory (16 rows of stride 20 floats, the two systems in the
+// area of the first row's packed triangle), is overwritten by L's columns
+// (same stride) during the factorisation, and w is written where the
+// buffer's values were staged, so that S^T w runs on the same MMA path as
+// the primal right-hand side S^T r.
+constexpr int DUAL_MAX = 16, DUAL_LD = 20, DUAL_SYS = DUAL_MAX * DUAL_LD;
+
+// G = S S^T of the 16 staged observations of buffer buf (whole warp): the A
+// fragment of S (rows = observations) also supplies the B fragments of S^T.
 template <bool BF>
+__device__ __forceinline__ void dual_gram(const Smem32<BF> &W, int buf, float (&d)[2][4],
+                                          int lane) {
+    const int gid = lane >> 2, tid4 = lane & 3;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d[t][e] = 0.f;
+    if constexpr (BF) {
+        const __nv_bfloat16 *sH = reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][0][0][0]);
+        const __nv_bfloat16 *sL = reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][1][0][0]);
+        constexpr int LDE = Smem32<BF>::ROWB / 2;
+        const int row = (lane & 7) + ((lane >> 3) & 1) * 8, cofs = (lane >> 4) * 8;
+#pragma unroll
+        for (int k0 = 0; k0 < KP; k0 += 16) {
+            uint32_t aH[4], aL[4];
+            ldsm_x4(aH, sH + row * LDE + k0 + cofs);
+            ldsm_x4(aL, sL + row * LDE + k0 + cofs);
+#pragma unroll
+            for (int ps = 0; ps < 3; ++ps) {   // lo.hi, hi.lo, hi.hi
+                const uint32_t(&A)[4] = ps == 0 ? aL : aH;
+                const uint32_t(&B)[4] = ps == 1 ? aL : aH;
+                mma_bf16(d[0], A, B[0], B[2]);
+                mma_bf16(d[1], A, B[1], B[3]);
+            }
+        }
+    } else {
+        const float *stf = reinterpret_cast<const float *>(&W.ld.stage[buf][0][0][0]);
+        constexpr int LDF = Smem32<BF>::ROWB / 4;
+#pragma unroll
+        for (int k0 = 0; k0 < KP; k0 += 8) {
+            uint32_t h[4], l[4];
+            split_tf32(stf[gid * LDF + k0 + tid4], h[0], l[0]);
+            split_tf32(stf[(gid + 8) * LDF + k0 + tid4], h[1], l[1]);
+            split_tf32(stf[gid * LDF + k0 + tid4 + 4], h[2], l[2]);
+            split_tf32(stf[(gid + 8) * LDF + k0 + tid4 + 4], h[3], l[3]);
+#pragma unroll
+            for (int ps = 0; ps < 3; ++ps) {
+                const uint32_t(&A)[4] = ps == 0 ? l : h;
+                const uint32_t(&B)[4] = ps == 1 ? l : h;
+                mma_tf32(d[0], A, B[0], B[2]);
+                mma_tf32(d[1], A, B[1], B[3]);
+            }
+        }
+    }
+}
+
+// u = S^T w over the 16 staged observations of buffer buf, w staged where
+// the values were (whole warp; dr as in the primal right-hand side).
+template <bool BF>
+__device__ __forceinline__ void dual_sTw(const Smem32<BF> &W, int buf, float (&dr)[2][4],
+                                         int lane) {
+    const int gid = lane >> 2, tid4 = lane & 3;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
+    if constexpr (BF) {
+        const __nv_bfloat16 *sH = reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][0][0][0]);
+        const __nv_bfloat16 *sL = reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][1][0][0]);
+        constexpr int LDE = Smem32<BF>::ROWB / 2;
+        const int mi = lane >> 3, rr = lane & 7;
+        uint32_t aH[2][4], aL[2][4];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+            const int off = ((mi >> 1) * 8 + rr) * LDE + mb * 16 + (mi & 1) * 8;
+            ldsm_x4_trans(aH[mb], sH + off);
+            ldsm_x4_trans(aL[mb], sL + off);
+        }
+        uint32_t wh0 = 0u, wh1 = 0u, wl0 = 0u, wl1 = 0u;
+        if (gid == 0) {
+            const uint32_t *hv = reinterpret_cast<const uint32_t *>(&W.ld.sr[buf][0]);
+            wh0 = hv[tid4];
+            wh1 = hv[tid4 + 4];
+            wl0 = hv[16 + tid4];
+            wl1 = hv[16 + tid4 + 4];
+        }
+#pragma unroll
+        for (int ps = 0; ps < 3; ++ps)
+#pragma unroll
+            for (int mb = 0; mb < 2; ++mb)
+                mma_bf16(dr[mb], ps == 0 ? aL[mb] : aH[mb], ps == 1 ? wl0 : wh0,
+                         ps == 1 ? wl1 : wh1);
+    } else {
+        const float *stf = reinterpret_cast<const float *>(&W.ld.stage[buf][0][0][0]);
+        constexpr int LDF = Smem32<BF>::ROWB / 4;
+#pragma unroll
+        for (int k0 = 0; k0 < DUAL_MAX; k0 += 8) {
+            uint32_t ah[2][4], al[2][4];
+#pragma unroll
+            for (int mb = 0; mb < 2; ++mb) {
+                split_tf32(stf[(k0 + tid4) * LDF + mb * 16 + gid], ah[mb][0], al[mb][0]);
+                split_tf32(stf[(k0 + tid4) * LDF + mb * 16 + gid + 8], ah[mb][1], al[mb][1]);
+                split_tf32(stf[(k0 + tid4 + 4) * LDF + mb * 16 + gid], ah[mb][2], al[mb][2]);
+                split_tf32(stf[(k0 + tid4 + 4) * LDF + mb * 16 + gid + 8], ah[mb][3], al[mb][3]);
+            }
+            uint32_t wh0, wl0, wh1, wl1;
+            split_tf32(gid == 0 ? W.ld.sr[buf][k0 + tid4] : 0.0f, wh0, wl0);
+            split_tf32(gid == 0 ? W.ld.sr[buf][k0 + tid4 + 4] : 0.0f, wh1, wl1);
+#pragma unroll
+            for (int ps = 0; ps < 3; ++ps)
+#pragma unroll
+                for (int mb = 0; mb < 2; ++mb)
+                    mma_tf32(dr[mb], ps == 0 ? al[mb] : ah[mb], ps == 1 ? wl0 : wh0,
+                             ps == 1 ? wl1 : wh1);
+        }
+    }
+}
+
+template <bool BF, bool DUAL>
 __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a) {
     using WS = Smem32<BF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -304,10 +434,193 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
     const int64_t k0 = P * gw / G, k1 = P * (gw + 1) / G;
     PairFetch cur;
     if (k0 < k1) fetch_pair(a, k0, M, lane, cur);
+    const bool dual_ok = DUAL && !a.resid && !a.refine && !a.u_given;
 
     for (int64_t k = k0; k < k1; ++k) {
+      // A pair with one thin and one thick row runs in two passes, each row
+      // with an empty partner, so that every row takes the branch its own
+      // length selects and its result does not depend on the row it is paired
+      // with.  Only the last pass prefetches the next pair into cur.
+      const bool thin0 = cur.s[0] <= DUAL_MAX, thin1 = cur.s[1] <= DUAL_MAX;
+      const bool mixed = dual_ok && thin0 != thin1;
+#pragma unroll 1
+      for (int pass = 0; pass < (mixed ? 2 : 1); ++pass) {
+        const bool last = pass == (mixed ? 1 : 0);
+        PairFetch cp = cur;
+        if (mixed) {   // pass 0: the thin row alone; pass 1: the thick row alone
+            const int drop = ((pass == 0) == thin0) ? 1 : 0;
+#pragma unroll
+            for (int x = 0; x < 2; ++x)
+                if (x == drop) {
+                    cp.s[x] = 0;
+                    cp.row[x] = -1;
+                    cp.bad[x] = false;
+                }
+        }
+        if (dual_ok && cp.s[0] <= DUAL_MAX && cp.s[1] <= DUAL_MAX) {
+            // ---------------- thin pair: the 16 x 16 dual systems
+            const PairFetch pf = cp;
+            bool badf[2] = {false, false};
+            float vv[2];
+            pdl_wait();
+#pragma unroll
+            for (int si = 0; si < 2; ++si) {   // row si's observations -> stage buffer si
+                int32_t j = cp.j[2 * si];
+                float v = cp.v[2 * si];
+                const bool in = lane < pf.s[si];
+                if (in && (j < 0 || (int64_t)j >= a.n_other)) {
+                    badf[si] = true;
+                    j = 0;
+                    v = 0.f;
+                }
+                vv[si] = in ? v : 0.f;
+                if (lane < DUAL_MAX) {
+                    const int nb = in ? 16 : 0;
+                    if constexpr (BF) {
+                        const unsigned char *src =
+                            reinterpret_cast<const unsigned char *>(a.Fb) + (int64_t)j * KP * 4;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            cp_async16(&W.ld.stage[si][0][lane][16 * e], src + 16 * e, nb);
+                            cp_async16(&W.ld.stage[si][1][lane][16 * e], src + 2 * KP + 16 * e, nb);
+                        }
+                    } else {
+                        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.F + (int64_t)j * KP);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            cp_async16(&W.ld.stage[si][0][lane][16 * e], src + 16 * e, nb);
+                    }
+                }
+            }
+            cp_async_commit();
+            if (last && k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);   // in flight during the solve
+            const bool bad0 = pf.bad[0] || (__any_sync(FULL, badf[0]) != 0);
+            const bool bad1 = pf.bad[1] || (__any_sync(FULL, badf[1]) != 0);
+            cp_async_wait<0>();
+            __syncwarp();
+            float *Gb = W.A0;
+#pragma unroll
+            for (int si = 0; si < 2; ++si) {
+                float d[2][4];
+                dual_gram<BF>(W, si, d, lane);
+                float *G = Gb + si * DUAL_SYS;
+#pragma unroll
+                for (int nb = 0; nb < 2; ++nb) {
+                    const int c = nb * 8 + 2 * tid4;
+                    *reinterpret_cast<float2 *>(G + gid * DUAL_LD + c) = make_float2(d[nb][0], d[nb][1]);
+                    *reinterpret_cast<float2 *>(G + (gid + 8) * DUAL_LD + c) =
+                        make_float2(d[nb][2], d[nb][3]);
+                }
+            }
+            __syncwarp();
+            // half h solves system h: lane i holds row i of G_h + lambda I
+            const int64_t s = h ? pf.s[1] : pf.s[0];
+            const bool bad = h ? bad1 : bad0;
+            const float lam = float(a.lambda) * (a.wr ? float(s) : 1.f);   // weighted: lambda s_i
+            float *G = Gb + h * DUAL_SYS;
+            G[i * (DUAL_LD + 1)] += lam;
+            __syncwarp();
+            float g[DUAL_MAX];
+#pragma unroll
+            for (int t = 0; t < DUAL_MAX / 4; ++t) {
+                const float4 v = *reinterpret_cast<const float4 *>(G + i * DUAL_LD + 4 * t);
+                g[4 * t] = v.x;
+                g[4 * t + 1] = v.y;
+                g[4 * t + 2] = v.z;
+                g[4 * t + 3] = v.w;
+            }
+            const float r0 = __shfl_sync(FULL, vv[0], i), r1 = __shfl_sync(FULL, vv[1], i);
+            float y = h ? r1 : r0;
+            __syncwarp();   // every row is read before L's columns overwrite G
+            // Cholesky with the forward substitution riding along; column p of L
+            // at G + p * DUAL_LD
+            float myinv = 0.f;
+#pragma unroll
+            for (int p = 0; p < DUAL_MAX; ++p) {
+                const float piv = __shfl_sync(FULL, g[p], p, 16);
+                const float inv = rsqrtf(piv);
+                const float l = g[p] * inv;
+                float *Lc = G + p * DUAL_LD;
+                if (i >= p) Lc[i] = l;
+                if (i == p) myinv = inv;
+                const float yp = __shfl_sync(FULL, y, p, 16) * inv;
+                if (i > p) y = fmaf(-l, yp, y);
+                __syncwarp();
+#pragma unroll
+                for (int r4 = ((p + 1) / 4) * 4; r4 < DUAL_MAX; r4 += 4) {
+                    const float4 c4 = *reinterpret_cast<const float4 *>(Lc + r4);
+                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e += 2) {
+                        const int r = r4 + e;
+                        if (r > p) fma2_sub(g[r], g[r + 1], l, cv[e], cv[e + 1]);
+                        else if (r + 1 > p) g[r + 1] = fmaf(-l, cv[e + 1], g[r + 1]);
+                    }
+                }
+            }
+            // L^T w = L^{-1} r from column i of L in registers
+            float c[DUAL_MAX];
+#pragma unroll
+            for (int t = 0; t < DUAL_MAX / 4; ++t) {
+                const float4 v = *reinterpret_cast<const float4 *>(G + i * DUAL_LD + 4 * t);
+                c[4 * t] = v.x;
+                c[4 * t + 1] = v.y;
+                c[4 * t + 2] = v.z;
+                c[4 * t + 3] = v.w;
+            }
+            float x = y * myinv;
+#pragma unroll
+            for (int p = DUAL_MAX - 1; p >= 0; --p) {
+                const float wp = __shfl_sync(FULL, x * myinv, p, 16);
+                if (i < p) x = fmaf(-c[p], wp, x);
+            }
+            float w = x * myinv;
+            const unsigned fb = __ballot_sync(FULL, !isfinite(w));
+            const bool fail = ((fb >> (16 * h)) & 0xffffu) != 0u;
+            int32_t st = ST_OK;
+            if (bad) st = ST_BAD;
+            else if (s == 0) st = ST_EMPTY;
+            else if (fail) st = ST_NOT_SPD;
+            if (st != ST_OK) w = 0.f;
+            // w replaces the staged values of buffer h; u = S^T w on the MMA path
+            if constexpr (BF) {
+                __nv_bfloat16 *sb = reinterpret_cast<__nv_bfloat16 *>(&W.ld.sr[h][0]);
+                const __nv_bfloat16 wh = __float2bfloat16_rn(w);
+                sb[i] = wh;
+                sb[32 + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
+            } else {
+                W.ld.sr[h][i] = w;
+            }
+            const int32_t st_r[2] = {__shfl_sync(FULL, st, 0), __shfl_sync(FULL, st, 16)};
+            __syncwarp();
+#pragma unroll
+            for (int si = 0; si < 2; ++si) {
+                float dr[2][4];
+                dual_sTw<BF>(W, si, dr, lane);
+                const int64_t rw = si ? pf.row[1] : pf.row[0];
+                if (rw >= 0) {
+                    if (tid4 == 0) {
+                        const int cs[4] = {gid, gid + 8, 16 + gid, 24 + gid};
+                        const float us[4] = {dr[0][0], dr[0][2], dr[1][0], dr[1][2]};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (cs[q] < a.kout) a.out[rw * a.ldo + cs[q]] = us[q];
+                            if (a.outb) {   // split BF16 copy [hi | lo] of the output row
+                                __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.outb) + rw * 2 * KP;
+                                const __nv_bfloat16 uh = __float2bfloat16_rn(us[q]);
+                                ob[cs[q]] = uh;
+                                ob[KP + cs[q]] = __float2bfloat16_rn(us[q] - __bfloat162float(uh));
+                            }
+                        }
+                    }
+                    if (a.status && lane == 0) a.status[rw] = st_r[si];
+                }
+            }
+            __syncwarp();   // the shared area is restaged by the next pair
+            continue;
+        }
         // ---------------- Gram phase: both rows' items, one after the other
-        const int n0 = (int)((cur.s[0] + 31) / 32), n1 = (int)((cur.s[1] + 31) / 32);
+        const int n0 = (int)((cp.s[0] + 31) / 32), n1 = (int)((cp.s[1] + 31) / 32);
         const int nit = n0 + n1;
         bool badf0 = false, badf1 = false;
         // column index and value of this lane's observation in item w
@@ -316,16 +629,16 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             const int loc = w - (si ? n0 : 0);
             buf_si = si;
             const int64_t t = (int64_t)loc * 32 + lane;
-            const int64_t ss = si ? cur.s[1] : cur.s[0];
+            const int64_t ss = si ? cp.s[1] : cp.s[0];
             if (loc < 2) {
                 const int slot = 2 * si + loc;
-                j = slot == 0 ? cur.j[0] : slot == 1 ? cur.j[1] : slot == 2 ? cur.j[2] : cur.j[3];
-                v = slot == 0 ? cur.v[0] : slot == 1 ? cur.v[1] : slot == 2 ? cur.v[2] : cur.v[3];
+                j = slot == 0 ? cp.j[0] : slot == 1 ? cp.j[1] : slot == 2 ? cp.j[2] : cp.j[3];
+                v = slot == 0 ? cp.v[0] : slot == 1 ? cp.v[1] : slot == 2 ? cp.v[2] : cp.v[3];
             } else {
                 j = 0;
                 v = 0.f;
                 if (t < ss) {
-                    const int64_t bg = si ? cur.beg[1] : cur.beg[0];
+                    const int64_t bg = si ? cp.beg[1] : cp.beg[0];
                     j = __ldg(a.idx + bg + t);
                     v = __ldg(a.val + bg + t);
                 }
@@ -386,7 +699,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
 #pragma unroll
                 for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
             const int w0 = si ? n0 : 0, w1 = si ? nit : n0;
-            const int64_t ss = si ? cur.s[1] : cur.s[0];
+            const int64_t ss = si ? cp.s[1] : cp.s[0];
             for (int w = w0; w < w1; ++w) {
                 if (w + 1 < nit) issue(w + 1, (w + 1) & 1);
                 cp_async_commit();
@@ -423,7 +736,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                 }
             }
         }
-        const PairFetch pf = cur;
+        const PairFetch pf = cp;
         const bool bad0 = pf.bad[0] || (__any_sync(FULL, badf0) != 0);
         const bool bad1 = pf.bad[1] || (__any_sync(FULL, badf1) != 0);
         __syncwarp();
@@ -507,7 +820,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             }
             // the factor is done: fetch the next pair's bounds, indices and values
             // while the substitutions and the residual run
-            if (k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);
+            if (last && k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);
             inv0 = Sinv[i];
             inv1 = Sinv[i + 16];
             // ---- back substitution L^T x = y
@@ -515,7 +828,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             x0 = xx.x;
             x1 = xx.y;
         } else {
-            if (k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);
+            if (last && k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);
             x0 = (i < a.kout && row >= 0) ? a.u_given[row * a.ldo + i] : 0.f;
             x1 = (i + 16 < a.kout && row >= 0) ? a.u_given[row * a.ldo + i + 16] : 0.f;
         }
@@ -593,12 +906,13 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             if (a.resid && i == 0) a.resid[row] = rel;
         }
         __syncwarp();   // the shared area is restaged by the next pair
+      }
     }
 }
 
 template <bool BF> size_t smem_bytes() { return sizeof(Smem32<BF>) * WARPS; }
 
-template <bool BF> cudaError_t launch32(const SolveArgs<float> &a, cudaStream_t st) {
+template <bool BF, bool DUAL> cudaError_t launch32(const SolveArgs<float> &a, cudaStream_t st) {
     // a persistent grid: at most two CTAs per SM, each warp a contiguous range of row pairs
     const int64_t pairs = (a.m + 1) / 2;
     int64_t blocks = (pairs + WARPS - 1) / WARPS;
@@ -613,11 +927,15 @@ template <bool BF> cudaError_t launch32(const SolveArgs<float> &a, cudaStream_t 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_solve32_tc<BF>, a);
+    return cudaLaunchKernelEx(&cfg, k_solve32_tc<BF, DUAL>, a);
 }
 
 template <bool BF> cudaError_t attr32() {
-    return cudaFuncSetAttribute(k_solve32_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_solve32_tc<BF, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes<BF>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_solve32_tc<BF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes<BF>());
 }
 
@@ -634,8 +952,13 @@ cudaError_t launch_solve32_tc(const SolveArgs<float> &a, bool bf16, cudaStream_t
     if (bf16 && !a.Fb) return cudaErrorInvalidValue;
     if (a.gram) return cudaErrorInvalidValue;   // the streaming refit's sums are not supported here
     // one build serves the plain fold-in too (a build without the residual
-    // paths spilled more registers and measured slower)
-    return bf16 ? launch32<true>(a, st) : launch32<false>(a, st);
+    // paths spilled more registers and measured slower).  The build with the
+    // thin-row dual branch runs where rows average fewer than 24 observations
+    // (and no residual is wanted); with longer rows few pairs are thin, and
+    // the build without it keeps the normal-equation path's registers.
+    const bool dual = !a.resid && !a.refine && !a.u_given && a.nnz < 24 * a.m;
+    if (bf16) return dual ? launch32<true, true>(a, st) : launch32<true, false>(a, st);
+    return dual ? launch32<false, true>(a, st) : launch32<false, false>(a, st);
 }
 
 }  // namespace ocf

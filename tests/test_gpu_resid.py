@@ -68,12 +68,16 @@ def test_checked_foldin_matches_oracle(orc, precision, k):
     U2, st2, r2 = h.complete_rows_checked(*csr, refine=True)
     torch.cuda.synchronize()
     Uref, sref = orc.half_step(ptr, col, val, V, lam)
-    # the check alone changes nothing; the plain fold-in runs the same solver
-    assert torch.equal(U0, U1) and torch.equal(st0, st1)
+    # the check alone changes nothing where the plain fold-in runs the same
+    # solver: rows of more than 16 observations (the plain fold-in solves
+    # thinner rows from the 16 x 16 dual system, the checked one from the
+    # normal equations it checks; both against the oracle below)
+    thick = torch.as_tensor(np.diff(ptr) > 16, device=DEV)
+    assert torch.equal(U0[thick], U1[thick]) and torch.equal(st0, st1)
     for st in (st1, st2):
         assert np.array_equal(host(st), sref)
     ok = sref == 0
-    for U in (U1, U2):
+    for U in (U0, U1, U2):
         if precision == "fp32":
             err = solve_err(host(U), Uref, V, ptr, col, val, lam)[ok]
             assert err.max() <= TOL_FP32, err.max()
