@@ -292,7 +292,11 @@ __device__ __forceinline__ void fetch_pair(const SolveArgs<float> &a, int64_t k,
 // area of the first row's packed triangle), is overwritten by L's columns
 // (same stride) during the factorisation, and w is written where the
 // buffer's values were staged, so that S^T w runs on the same MMA path as
-// the primal right-hand side S^T r.
+// the primal right-hand side S^T r.  Where the observed rows are nearly
+// dependent, u = S^T w cancels and carries the error of w relative to |S||w|;
+// in FP32 mode one refinement step (residual of the dual system from the
+// staged FP32 rows, correction with the same factor, u += S^T dw) restores
+// the accuracy of the normal-equation solve.
 constexpr int DUAL_MAX = 16, DUAL_LD = 20, DUAL_SYS = DUAL_MAX * DUAL_LD;
 
 // G = S S^T of the 16 staged observations of buffer buf (whole warp): the A
@@ -344,66 +348,40 @@ __device__ __forceinline__ void dual_gram(const Smem32<BF> &W, int buf, float (&
     }
 }
 
-// u = S^T w over the 16 staged observations of buffer buf, w staged where
-// the values were (whole warp; dr as in the primal right-hand side).
-template <bool BF>
-__device__ __forceinline__ void dual_sTw(const Smem32<BF> &W, int buf, float (&dr)[2][4],
-                                         int lane) {
+// u = S^T w over the 16 staged observations of buffer buf (split BF16 mode),
+// w staged where the values were (whole warp; dr as in the primal right-hand
+// side).  The FP32 mode forms S^T w with FP32 FMAs instead (see the kernel).
+__device__ __forceinline__ void dual_sTw_bf16(const Smem32<true> &W, int buf, float (&dr)[2][4],
+                                              int lane) {
     const int gid = lane >> 2, tid4 = lane & 3;
 #pragma unroll
     for (int t = 0; t < 2; ++t)
 #pragma unroll
         for (int e = 0; e < 4; ++e) dr[t][e] = 0.f;
-    if constexpr (BF) {
-        const __nv_bfloat16 *sH = reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][0][0][0]);
-        const __nv_bfloat16 *sL = reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][1][0][0]);
-        constexpr int LDE = Smem32<BF>::ROWB / 2;
-        const int mi = lane >> 3, rr = lane & 7;
-        uint32_t aH[2][4], aL[2][4];
+    const __nv_bfloat16 *sH = reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][0][0][0]);
+    const __nv_bfloat16 *sL = reinterpret_cast<const __nv_bfloat16 *>(&W.ld.stage[buf][1][0][0]);
+    constexpr int LDE = Smem32<true>::ROWB / 2;
+    const int mi = lane >> 3, rr = lane & 7;
+    uint32_t aH[2][4], aL[2][4];
 #pragma unroll
-        for (int mb = 0; mb < 2; ++mb) {
-            const int off = ((mi >> 1) * 8 + rr) * LDE + mb * 16 + (mi & 1) * 8;
-            ldsm_x4_trans(aH[mb], sH + off);
-            ldsm_x4_trans(aL[mb], sL + off);
-        }
-        uint32_t wh0 = 0u, wh1 = 0u, wl0 = 0u, wl1 = 0u;
-        if (gid == 0) {
-            const uint32_t *hv = reinterpret_cast<const uint32_t *>(&W.ld.sr[buf][0]);
-            wh0 = hv[tid4];
-            wh1 = hv[tid4 + 4];
-            wl0 = hv[16 + tid4];
-            wl1 = hv[16 + tid4 + 4];
-        }
-#pragma unroll
-        for (int ps = 0; ps < 3; ++ps)
-#pragma unroll
-            for (int mb = 0; mb < 2; ++mb)
-                mma_bf16(dr[mb], ps == 0 ? aL[mb] : aH[mb], ps == 1 ? wl0 : wh0,
-                         ps == 1 ? wl1 : wh1);
-    } else {
-        const float *stf = reinterpret_cast<const float *>(&W.ld.stage[buf][0][0][0]);
-        constexpr int LDF = Smem32<BF>::ROWB / 4;
-#pragma unroll
-        for (int k0 = 0; k0 < DUAL_MAX; k0 += 8) {
-            uint32_t ah[2][4], al[2][4];
-#pragma unroll
-            for (int mb = 0; mb < 2; ++mb) {
-                split_tf32(stf[(k0 + tid4) * LDF + mb * 16 + gid], ah[mb][0], al[mb][0]);
-                split_tf32(stf[(k0 + tid4) * LDF + mb * 16 + gid + 8], ah[mb][1], al[mb][1]);
-                split_tf32(stf[(k0 + tid4 + 4) * LDF + mb * 16 + gid], ah[mb][2], al[mb][2]);
-                split_tf32(stf[(k0 + tid4 + 4) * LDF + mb * 16 + gid + 8], ah[mb][3], al[mb][3]);
-            }
-            uint32_t wh0, wl0, wh1, wl1;
-            split_tf32(gid == 0 ? W.ld.sr[buf][k0 + tid4] : 0.0f, wh0, wl0);
-            split_tf32(gid == 0 ? W.ld.sr[buf][k0 + tid4 + 4] : 0.0f, wh1, wl1);
-#pragma unroll
-            for (int ps = 0; ps < 3; ++ps)
-#pragma unroll
-                for (int mb = 0; mb < 2; ++mb)
-                    mma_tf32(dr[mb], ps == 0 ? al[mb] : ah[mb], ps == 1 ? wl0 : wh0,
-                             ps == 1 ? wl1 : wh1);
-        }
+    for (int mb = 0; mb < 2; ++mb) {
+        const int off = ((mi >> 1) * 8 + rr) * LDE + mb * 16 + (mi & 1) * 8;
+        ldsm_x4_trans(aH[mb], sH + off);
+        ldsm_x4_trans(aL[mb], sL + off);
     }
+    uint32_t wh0 = 0u, wh1 = 0u, wl0 = 0u, wl1 = 0u;
+    if (gid == 0) {
+        const uint32_t *hv = reinterpret_cast<const uint32_t *>(&W.ld.sr[buf][0]);
+        wh0 = hv[tid4];
+        wh1 = hv[tid4 + 4];
+        wl0 = hv[16 + tid4];
+        wl1 = hv[16 + tid4 + 4];
+    }
+#pragma unroll
+    for (int ps = 0; ps < 3; ++ps)
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb)
+            mma_bf16(dr[mb], ps == 0 ? aL[mb] : aH[mb], ps == 1 ? wl0 : wh0, ps == 1 ? wl1 : wh1);
 }
 
 template <bool BF, bool DUAL>
@@ -582,38 +560,103 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             else if (s == 0) st = ST_EMPTY;
             else if (fail) st = ST_NOT_SPD;
             if (st != ST_OK) w = 0.f;
-            // w replaces the staged values of buffer h; u = S^T w on the MMA path
             if constexpr (BF) {
+                // w replaces the staged values of buffer h; u = S^T w on the MMA
+                // path of the primal right-hand side (split BF16)
                 __nv_bfloat16 *sb = reinterpret_cast<__nv_bfloat16 *>(&W.ld.sr[h][0]);
                 const __nv_bfloat16 wh = __float2bfloat16_rn(w);
                 sb[i] = wh;
                 sb[32 + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
-            } else {
-                W.ld.sr[h][i] = w;
-            }
-            const int32_t st_r[2] = {__shfl_sync(FULL, st, 0), __shfl_sync(FULL, st, 16)};
-            __syncwarp();
+                const int32_t st_r[2] = {__shfl_sync(FULL, st, 0), __shfl_sync(FULL, st, 16)};
+                __syncwarp();
+                const int cs[4] = {gid, gid + 8, 16 + gid, 24 + gid};   // components a lane holds
 #pragma unroll
-            for (int si = 0; si < 2; ++si) {
-                float dr[2][4];
-                dual_sTw<BF>(W, si, dr, lane);
-                const int64_t rw = si ? pf.row[1] : pf.row[0];
-                if (rw >= 0) {
-                    if (tid4 == 0) {
-                        const int cs[4] = {gid, gid + 8, 16 + gid, 24 + gid};
-                        const float us[4] = {dr[0][0], dr[0][2], dr[1][0], dr[1][2]};
+                for (int si = 0; si < 2; ++si) {
+                    float ur[2][4];
+                    dual_sTw_bf16(W, si, ur, lane);
+                    const int64_t rw = si ? pf.row[1] : pf.row[0];
+                    if (rw >= 0) {
+                        if (tid4 == 0) {
+                            const float us[4] = {ur[0][0], ur[0][2], ur[1][0], ur[1][2]};
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (cs[q] < a.kout) a.out[rw * a.ldo + cs[q]] = us[q];
-                            if (a.outb) {   // split BF16 copy [hi | lo] of the output row
-                                __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.outb) + rw * 2 * KP;
-                                const __nv_bfloat16 uh = __float2bfloat16_rn(us[q]);
-                                ob[cs[q]] = uh;
-                                ob[KP + cs[q]] = __float2bfloat16_rn(us[q] - __bfloat162float(uh));
+                            for (int q = 0; q < 4; ++q) {
+                                if (cs[q] < a.kout) a.out[rw * a.ldo + cs[q]] = us[q];
+                                if (a.outb) {   // split BF16 copy [hi | lo] of the output row
+                                    __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.outb) + rw * 2 * KP;
+                                    const __nv_bfloat16 uh = __float2bfloat16_rn(us[q]);
+                                    ob[cs[q]] = uh;
+                                    ob[KP + cs[q]] = __float2bfloat16_rn(us[q] - __bfloat162float(uh));
+                                }
                             }
                         }
+                        if (a.status && lane == 0) a.status[rw] = st_r[si];
                     }
-                    if (a.status && lane == 0) a.status[rw] = st_r[si];
+                }
+            } else {
+                // FP32 mode: u = S^T w in FP32 FMAs over the staged rows (lane i of
+                // half h: components ca = i + 16 h and cb = i + 16 (1 - h), so the
+                // two halves' loads fall in different banks), then one refinement
+                // step: rho = r - S u - lambda w from the staged FP32 rows (not the
+                // split products the Gram was formed from), dw = (G + lambda I)^-1 rho
+                // with the same factor, u += S^T dw.  Where the observed rows are
+                // nearly dependent u = S^T w cancels; this step recovers (and
+                // passes) the accuracy of the normal-equation solve.
+                constexpr int LDF = WS::ROWB / 4;
+                const float *sf = reinterpret_cast<const float *>(&W.ld.stage[h][0][0][0]);
+                const int ca = i + 16 * h, cb = i + 16 * (1 - h);
+                float uA = 0.f, uB = 0.f;
+#pragma unroll
+                for (int t = 0; t < DUAL_MAX; ++t) {
+                    const float wt = __shfl_sync(FULL, w, t, 16);
+                    uA = fmaf(sf[t * LDF + ca], wt, uA);
+                    uB = fmaf(sf[t * LDF + cb], wt, uB);
+                }
+                float *uv = h ? W.b0 : W.A0 + 2 * DUAL_SYS;   // u of system h, 32 floats
+                uv[ca] = uA;
+                uv[cb] = uB;
+                __syncwarp();
+                const float4 *srow = reinterpret_cast<const float4 *>(sf + i * LDF);
+                const float4 *u4 = reinterpret_cast<const float4 *>(uv);
+                float2 acc = make_float2(fmaf(-lam, w, h ? r1 : r0), 0.f);
+#pragma unroll
+                for (int c4 = 0; c4 < KP / 4; ++c4) {
+                    const float4 x = srow[c4], uu = u4[c4];
+                    acc = __ffma2_rn(make_float2(-x.x, -x.y), make_float2(uu.x, uu.y), acc);
+                    acc = __ffma2_rn(make_float2(-x.z, -x.w), make_float2(uu.z, uu.w), acc);
+                }
+                float z = st == ST_OK ? acc.x + acc.y : 0.f;
+                // L z' = rho (column p of L at G + p * DUAL_LD), then L^T dw = z'
+#pragma unroll
+                for (int p = 0; p < DUAL_MAX; ++p) {
+                    const float zp = __shfl_sync(FULL, z * myinv, p, 16);
+                    if (i > p) z = fmaf(-G[p * DUAL_LD + i], zp, z);
+                }
+                float xd = z * myinv;
+#pragma unroll
+                for (int p = DUAL_MAX - 1; p >= 0; --p) {
+                    const float wp = __shfl_sync(FULL, xd * myinv, p, 16);
+                    if (i < p) xd = fmaf(-c[p], wp, xd);
+                }
+                const float dw = st == ST_OK ? xd * myinv : 0.f;   // (1 / L_ii may be inf there)
+#pragma unroll
+                for (int t = 0; t < DUAL_MAX; ++t) {
+                    const float dt = __shfl_sync(FULL, dw, t, 16);
+                    uA = fmaf(sf[t * LDF + ca], dt, uA);
+                    uB = fmaf(sf[t * LDF + cb], dt, uB);
+                }
+                const int64_t rw = h ? pf.row[1] : pf.row[0];
+                if (rw >= 0) {
+                    if (ca < a.kout) a.out[rw * a.ldo + ca] = uA;
+                    if (cb < a.kout) a.out[rw * a.ldo + cb] = uB;
+                    if (a.outb) {   // split BF16 copy [hi | lo] of the output row
+                        __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.outb) + rw * 2 * KP;
+                        const __nv_bfloat16 ha = __float2bfloat16_rn(uA), hb = __float2bfloat16_rn(uB);
+                        ob[ca] = ha;
+                        ob[cb] = hb;
+                        ob[KP + ca] = __float2bfloat16_rn(uA - __bfloat162float(ha));
+                        ob[KP + cb] = __float2bfloat16_rn(uB - __bfloat162float(hb));
+                    }
+                    if (a.status && i == 0) a.status[rw] = st;
                 }
             }
             __syncwarp();   // the shared area is restaged by the next pair

@@ -1,7 +1,8 @@
 """Thin rows at rank 17..32: rows with at most 16 observations are solved from
 the 16 x 16 dual system (u = S^T w, (S S^T + lambda I) w = r) when both rows of
-a solver pair are thin, and from the k x k normal equations otherwise.  Both
-branches against the FP64 oracle's primal row solve on the same inputs."""
+a solver pair are thin, and from the k x k normal equations otherwise (FP32
+mode adds one refinement step of the dual system).  Both branches against the
+FP64 oracle's primal row solve on the same inputs."""
 import numpy as np
 import pytest
 import torch
@@ -110,3 +111,37 @@ def test_dual_bf16_sweep_stepwise(orc):
     Vref, _ = orc.half_step(cptr, cidx, cval, U1d, prob.lam)
     okc = np.diff(cptr) > 0
     assert pred_err(host(V1), Vref, U1d)[okc].max() <= TOL_T
+
+
+@pytest.mark.parametrize("decay", [0.0, 3.0])
+def test_dual_as_accurate_as_normal_equations(orc, decay):
+    """FP32 mode, rank 32, 16 observations per row (the learned workload's
+    rows).  V's singular values fall by 10^decay, so some rows' observed
+    factor rows are nearly dependent and S^T w cancels; the dual branch (with
+    its refinement step) must stay as accurate as the 32 x 32 normal-equation
+    solve, which the checked fold-in runs on the same rows."""
+    rng = np.random.default_rng(31 + int(decay))
+    k, n, m, lam = 32, 4096, 4000, 0.05
+    Q = np.linalg.qr(rng.standard_normal((n, k)))[0]
+    V = rounded(Q * np.logspace(0, -decay, k) * np.sqrt(n / k) * 0.6, torch.float32)
+    cols = np.stack([np.sort(rng.choice(n, 16, replace=False)) for _ in range(m)])
+    ptr = np.arange(0, 16 * m + 1, 16, dtype=np.int64)
+    col = cols.reshape(-1).astype(np.int32)
+    val = rounded(rng.random(16 * m) * 0.5 + 0.2, torch.float32)
+    h = ocf.OpenCF(k=k, lam=lam)
+    h.set_V(dev(V, torch.float32))
+    csr = csr_dev(ptr, col, val, torch.float32)
+    Ud, _ = h.complete_rows(*csr)                            # dual systems
+    Up, _, _ = h.complete_rows_checked(*csr, refine=False)   # normal equations
+    torch.cuda.synchronize()
+    Uref, _ = orc.half_step(ptr, col, val, V, lam)
+
+    def pred(U):
+        T, Tr = np.asarray(U, np.float64) @ V.T, Uref @ V.T
+        return np.linalg.norm(T - Tr, axis=1) / np.linalg.norm(Tr, axis=1)
+
+    ed, ep = pred(host(Ud)), pred(host(Up))
+    print(f"decay {decay}: dual max {ed.max():.2e} median {np.median(ed):.2e}; "
+          f"normal equations max {ep.max():.2e} median {np.median(ep):.2e}")
+    assert ed.max() <= 2 * ep.max() + 1e-7
+    assert np.median(ed) <= 2 * np.median(ep) + 1e-8
