@@ -571,15 +571,38 @@ def run_gpu_large(args):
     best_keep = best.clone()
     # end to end through the C ABI: the CSR from pinned host memory, each app's
     # chosen setting and saving back
-    d_in = [torch.empty_like(x) for x in (row_ptr, col, val)]
+    host_in = pinned(row_ptr.cpu(), col.cpu(), val.cpu())
+    e2e_api, e2e_same = None, None
+    if factor != "fp64":
+        # open_cf_complete_select_host: one call per step; the copies of each
+        # chunk of rows overlap the solves of the chunk before
+        check = 2 if factor == "fp32-refine" else 1
+        b_h = torch.empty(m, dtype=torch.int32).pin_memory()
+        s_h = torch.empty(m, dtype=torch.float32).pin_memory()
+        h.complete_select_host(*host_in, check=check, gamma=GAMMA, best=b_h, saving=s_h)
+        torch.cuda.synchronize()
+        e2e_same = bool(torch.equal(b_h, best_keep.cpu()))
+        eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for a_, b_ in eve:
+            a_.record(stream)
+            h.complete_select_host(*host_in, check=check, gamma=GAMMA, best=b_h, saving=s_h)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = sum(a_.elapsed_time(b_) for a_, b_ in eve) / args.steps / 1e3
+        h2d = int(sum(x.numel() * x.element_size() for x in host_in))
+        d2h = int(b_h.numel() * 4 + s_h.numel() * 4)
+        e2e_api = ("open_cf_complete_select_host (pinned host CSR in, decisions out; the copies "
+                   "of each chunk of rows overlap the solves of the chunk before)")
+    else:
+        d_in = [torch.empty_like(x) for x in (row_ptr, col, val)]
 
-    def e2e_run():
-        Ue = fold(d_in[0], d_in[1], d_in[2])
-        _, b_, s_ = h.predict(Ue, gamma=GAMMA, want_T=False)
-        return [b_, s_]
+        def e2e_run():
+            Ue = fold(d_in[0], d_in[1], d_in[2])
+            _, b_, s_ = h.predict(Ue, gamma=GAMMA, want_T=False)
+            return [b_, s_]
 
-    t_e2e, h2d, d2h = measure_e2e(args.steps, stream,
-                                  pinned(row_ptr.cpu(), col.cpu(), val.cpu()), d_in, e2e_run)
+        t_e2e, h2d, d2h = measure_e2e(args.steps, stream, host_in, d_in, e2e_run)
     if ws > 1:
         tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -624,7 +647,13 @@ def run_gpu_large(args):
                            "Cholesky on packed FP32x2, residual / refinement)"
                            if factor != "fp64" else "k_row_solve_tc<32,double,1,bf16> (fold-in)",
                  "bound": "alu", "achieved": fold_ach, "peak": fold_peak, "unit": "TFLOP/s",
-                 "frac": fold_ach / fold_peak, "traffic": None,
+                 "frac": fold_ach / fold_peak,
+                 "traffic": None if factor == "fp64" else profiled_traffic_per_unit(
+                     os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "solve32_tc.cu"),
+                     os.path.join(ROOT, "profiles", "solve32_c5_2e19.md"), m),
+                 "traffic_source": "DRAM read + write of one ncu capture of the same kernel at "
+                                   "2^19 rows (profiles/solve32_c5_2e19.md), scaled to this "
+                                   "launch's rows; null if the source changed since",
                  "peak_source": ALU_PEAK_SOURCE + (" (FP64 FMA loop)" if factor == "fp64" else
                                                    " (FP32 FMA loop)"),
                  "algorithmic": "per row k^3/3 + 2k^2 (factor, solves) + 2k^2 per residual "
@@ -634,7 +663,13 @@ def run_gpu_large(args):
     pred_roof = {"kernel": "k_predict_select_tc (split-BF16 U V^T on tcgen05 + Algorithm 2 "
                            "from TMEM)", "bound": "tensor", "achieved": pred_ach,
                  "peak": bf16_peak, "unit": "TFLOP/s", "frac": pred_ach / bf16_peak,
-                 "traffic": None, "peak_source": "bf16_tflops (burst) of measured",
+                 "traffic": profiled_traffic_per_unit(
+                     os.path.join(ROOT, "paper_2508_07605_b300", "csrc", "predict_tc.cu"),
+                     os.path.join(ROOT, "profiles", "predict_tc_c5.md"), m),
+                 "traffic_source": "DRAM read + write of one ncu capture of the same kernel at "
+                                   "2^19 rows (profiles/predict_tc_c5.md), scaled to this "
+                                   "launch's rows; null if the source changed since",
+                 "peak_source": "bf16_tflops (burst) of measured",
                  "algorithmic": "2 m n k (the split form issues 3x that on the tensor pipe)",
                  "ms": t_pred * 1e3}
     dominant, other = (fold_roof, pred_roof) if t_fold >= t_pred else (pred_roof, fold_roof)
@@ -662,7 +697,9 @@ def run_gpu_large(args):
                          "sample": "FP64 fold-in + normal-equation residual + reconstruction + "
                                    "Algorithm 2 of 10,000 sampled apps (one warm-up, median of 3)"},
         "e2e": {"value": ws * m / t_e2e, "unit": "row-solves/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3,
+                **({"api": e2e_api, "decisions_equal_device_calls": e2e_same}
+                   if e2e_api else {})},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks.summary(local),
     }

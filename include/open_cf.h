@@ -200,6 +200,40 @@ int open_cf_normal_residual(open_cf_t *h, int64_t m, int64_t nnz, const int64_t 
 int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t *best,
                     float *saving, float gamma, int32_t baseline_setting, void *stream);
 
+/* The online phase end to end from HOST memory (Sec. "Online Performance
+ * Prediction" then Sec. "Optimal Power setting Selection"): the fold-in of m new
+ * rows (open_cf_complete_rows with joint = 0, or open_cf_complete_rows_checked)
+ * followed by open_cf_predict's Algorithm 2, for a caller whose CSR lives in
+ * host memory and who wants the decisions back in host memory.  The rows are
+ * processed in chunks (chunk_rows rows, rounded up to a multiple of 256; 0 =
+ * about m / 16, at least 32,768, rounded up to 128 rows per SM): the
+ * host-to-device copies of chunk c + 1 run on a copy
+ * stream of the handle while chunk c is solved on `stream`, so the copies
+ * overlap the solves.  Every chunk is solved as its own CSR, giving the results
+ * separate calls on its rows would give.
+ *  row_ptr (int64[m + 1], host; row_ptr[0] = 0, row_ptr[m] = nnz,
+ *    non-decreasing), col (int32[nnz], host), val (float[nnz], host): the CSR.
+ *    Page-locked (pinned) host memory is needed for the copies to overlap
+ *    anything; pageable memory works but serialises them.
+ *  check = 0: plain fold-in; 1: with the residual check; 2: with the residual
+ *    check and one refinement step (check >= 1: same handle requirements as
+ *    open_cf_complete_rows_checked).
+ *  gamma, baseline_setting: as for open_cf_predict (a cap grid is required).
+ *  best (int32[m], host), saving (float[m], host): Algorithm 2's decisions;
+ *  status (int32[m], host, may be NULL), resid (float[m], host, may be NULL;
+ *    check >= 1 only): as for open_cf_complete_rows_checked.
+ * The host arrays must stay valid and unchanged, and the outputs unread, until
+ * `stream` has completed the call's work (the call only enqueues; row_ptr is
+ * read on the host at the chunk boundaries during the call).  The handle keeps
+ * device copies of the inputs and outputs (grown to the largest call) and the
+ * factors of the last call; calls on one handle must not overlap on different
+ * streams.  FP32 / BF16-Gram handles; FP64 handles return OPEN_CF_UNSUPPORTED. */
+int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                                 const int32_t *col, const float *val, int32_t check,
+                                 float gamma, int32_t baseline_setting, int32_t *best,
+                                 float *saving, int32_t *status, float *resid,
+                                 int64_t chunk_rows, void *stream);
+
 /* Algorithm 2 alone on a given dense matrix T (m x n float, ld >= n), as in
  * open_cf_predict. */
 int open_cf_select(open_cf_t *h, const float *T, int64_t m, int64_t ld, int32_t *best,

@@ -57,6 +57,8 @@ _SIGNATURES = {
                                       [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _I32, _V]),
     "open_cf_normal_residual": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V]),
     "open_cf_predict": (ctypes.c_int, [_V, _V, _I64, _V, _V, _V, _F, _I32, _V]),
+    "open_cf_complete_select_host": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _I32, _F, _I32,
+                                                    _V, _V, _V, _V, _I64, _V]),
     "open_cf_select": (ctypes.c_int, [_V, _V, _I64, _I64, _V, _V, _F, _I32, _V]),
     "open_cf_objective": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
     "open_cf_csr_to_csc": (ctypes.c_int, [_V, _I64, _I64, _I64, _V, _V, _V, _V, _V, _V, _V]),
@@ -281,6 +283,33 @@ class OpenCF:
             self._h, m, nnz, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(U), _ptr(st),
             _ptr(resid), int(bool(refine)), self._stream()))
         return U, st, resid
+
+    def complete_select_host(self, row_ptr, col, val, check: int = 2, gamma: float = 0.05,
+                             baseline: int = -1, best=None, saving=None, status=None,
+                             resid=None, chunk_rows: int = 0):
+        """Fold-in (check 0: plain, 1: residual check, 2: check + one refinement
+        step) and Algorithm 2 for a CSR in host memory, decisions back in host
+        memory; the copies of one chunk of rows overlap the solves of the one
+        before (pin the host tensors for that).  Returns (best, saving, status,
+        resid) host tensors (status / resid None unless passed in); the work is
+        queued on the current stream: synchronise it before reading them."""
+        if row_ptr.dtype != torch.int64 or col.dtype != torch.int32 or val.dtype != torch.float32:
+            raise ValueError("row_ptr int64, col int32, val float32")
+        for t, nm in ((row_ptr, "row_ptr"), (col, "col"), (val, "val")):
+            if t.device.type != "cpu" or not t.is_contiguous():
+                raise ValueError(f"{nm} must be a contiguous host tensor")
+        m, nnz = row_ptr.numel() - 1, col.numel()
+        best = torch.empty(m, dtype=torch.int32, pin_memory=True) if best is None else best
+        saving = torch.empty(m, dtype=torch.float32, pin_memory=True) if saving is None else saving
+        for t in (best, saving, status, resid):
+            if t is not None and (t.device.type != "cpu" or not t.is_contiguous() or
+                                  t.numel() != m):
+                raise ValueError("outputs must be contiguous host tensors of m elements")
+        self._check(lib().open_cf_complete_select_host(
+            self._h, m, nnz, _ptr(row_ptr), _ptr(col), _ptr(val), int(check), float(gamma),
+            int(baseline), _ptr(best), _ptr(saving), _ptr(status), _ptr(resid), int(chunk_rows),
+            self._stream()))
+        return best, saving, status, resid
 
     def normal_residual(self, row_ptr, col, val, U):
         """Per-row relative normal-equation residual of the given factors."""

@@ -74,6 +74,11 @@ struct open_cf {
     uint64_t generation = 0;  // bumps whenever a workspace moves
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
+    // host-buffer completion: device copies of the inputs and outputs, a copy
+    // stream and per-chunk events (created on first use)
+    Buf hs_ptr, hs_rptr, hs_col, hs_val, hs_U, hs_best, hs_sav, hs_st, hs_res;
+    cudaStream_t hs_copy = nullptr;
+    std::vector<cudaEvent_t> hs_ev;
     std::string err;
 };
 
@@ -591,13 +596,16 @@ void open_cf_destroy(open_cf_t *h) {
         cudaDeviceSynchronize();
         for (auto &ge : h->graphs) cudaGraphExecDestroy(ge.exec);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+        if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
+        for (cudaEvent_t e : h->hs_ev) cudaEventDestroy(e);
         for (Buf *b : {&h->V, &h->Vb16, &h->cg, &h->off_ptr, &h->off_idx, &h->off_val, &h->U_w,
                        &h->csc_ptr, &h->csc_idx, &h->csc_val, &h->cnt, &h->tot, &h->part,
                        &h->flag, &h->j_ptr, &h->j_idx, &h->j_val, &h->Ub16, &h->b_meta, &h->b_Uw,
                        &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter, &h->mlp_th,
                        &h->mlp_m1, &h->mlp_m2, &h->mlp_t, &h->mlp_cn, &h->mlp_scr, &h->mlp_img,
                        &h->mlp_err, &h->vimg, &h->pt_err, &h->ccount, &h->sg, &h->sb,
-                       &h->sn})
+                       &h->sn, &h->hs_ptr, &h->hs_rptr, &h->hs_col, &h->hs_val, &h->hs_U, &h->hs_best,
+                       &h->hs_sav, &h->hs_st, &h->hs_res})
             free_buf(*b);
     }
     delete h;
@@ -1049,6 +1057,123 @@ int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t
                              sel ? (float *)h->cg.p : nullptr, base, Eb, gamma, (float *)T_out,
                              best, saving};
         CK(h, launch_predict_select<float>(a, S(stream)));
+    }
+    return OPEN_CF_OK;
+}
+
+int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
+                                 const int32_t *col, const float *val, int32_t check,
+                                 float gamma, int32_t baseline_setting, int32_t *best,
+                                 float *saving, int32_t *status, float *resid,
+                                 int64_t chunk_rows, void *stream) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (m < 0 || nnz < 0) return fail(h, OPEN_CF_INVALID_ARG, "negative m or nnz");
+    if (m > 0 && (!row_ptr || !best || !saving))
+        return fail(h, OPEN_CF_INVALID_ARG, "row_ptr, best or saving is NULL");
+    if (nnz > 0 && (!col || !val)) return fail(h, OPEN_CF_INVALID_ARG, "col or val is NULL");
+    if (check < 0 || check > 2) return fail(h, OPEN_CF_INVALID_ARG, "check must be 0, 1 or 2");
+    if (check == 0 && resid) return fail(h, OPEN_CF_INVALID_ARG, "resid needs check >= 1");
+    if (h->f64) return fail(h, OPEN_CF_UNSUPPORTED, "host-buffer completion is FP32 / BF16-Gram only");
+    if (check > 0 && (h->KP != 32 || h->cfg.cholesky_fp64))
+        return fail(h, OPEN_CF_UNSUPPORTED,
+                    "the residual check needs 16 < k <= 32 and the FP32 factorisation");
+    if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: fit or set V first");
+    if (h->cpu_caps.empty()) return fail(h, OPEN_CF_INVALID_ARG, "selection needs a cap grid");
+    if (chunk_rows < 0) return fail(h, OPEN_CF_INVALID_ARG, "chunk_rows < 0");
+    if (m == 0) return OPEN_CF_OK;
+    if (row_ptr[0] != 0 || row_ptr[m] != nnz)
+        return fail(h, OPEN_CF_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[m] == nnz");
+    // chunks: about 16 per call, at least 32768 rows; by default a whole number
+    // of 128-row reconstruction tiles per SM, so each chunk's persistent
+    // reconstruction ends with every SM busy
+    int64_t rows;
+    if (chunk_rows > 0) {
+        rows = (chunk_rows + 255) / 256 * 256;
+    } else {
+        const int64_t unit = 128 * (int64_t)std::max(1, h->num_sms);
+        rows = std::max<int64_t>(32768, (m + 15) / 16);
+        rows = (rows + unit - 1) / unit * unit;
+    }
+    const int64_t nch = (m + rows - 1) / rows;
+    // chunk boundaries in the entry arrays, read on the host; a non-decreasing
+    // sequence inside [0, nnz] is required here.  Each chunk is solved as a CSR
+    // of its own (row pointers rebased to the chunk's first entry), so rows
+    // inside it are checked against its own entries, as a separate call would.
+    std::vector<int64_t> eb((size_t)nch + 1);
+    for (int64_t c = 0; c <= nch; ++c) eb[(size_t)c] = row_ptr[std::min(m, c * rows)];
+    for (int64_t c = 0; c < nch; ++c)
+        if (eb[(size_t)c] < 0 || eb[(size_t)c + 1] < eb[(size_t)c] || eb[(size_t)c + 1] > nnz)
+            return fail(h, OPEN_CF_INVALID_ARG, "row_ptr is not non-decreasing within [0, nnz]");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    CK(h, ensure(h, h->hs_ptr, sizeof(int64_t) * (m + 1)));
+    CK(h, ensure(h, h->hs_rptr, sizeof(int64_t) * (m + nch)));
+    CK(h, ensure(h, h->hs_col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    CK(h, ensure(h, h->hs_val, sizeof(float) * std::max<int64_t>(nnz, 1)));
+    CK(h, ensure(h, h->hs_U, sizeof(float) * m * h->k));
+    CK(h, ensure(h, h->hs_best, sizeof(int32_t) * m));
+    CK(h, ensure(h, h->hs_sav, sizeof(float) * m));
+    CK(h, ensure(h, h->hs_st, sizeof(int32_t) * m));
+    if (check > 0) CK(h, ensure(h, h->hs_res, sizeof(float) * m));
+    if (!h->hs_copy) CK(h, cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking));
+    while ((int64_t)h->hs_ev.size() < nch + 1) {
+        cudaEvent_t e;
+        CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->hs_ev.push_back(e);
+    }
+    // the copies may overwrite the device buffers only after the work queued
+    // before this call on the caller's stream (an earlier call's solves)
+    CK(h, cudaEventRecord(h->hs_ev[(size_t)nch], st));
+    CK(h, cudaStreamWaitEvent(h->hs_copy, h->hs_ev[(size_t)nch], 0));
+    int64_t *dptr = (int64_t *)h->hs_ptr.p, *drp = (int64_t *)h->hs_rptr.p;
+    int32_t *dcol = (int32_t *)h->hs_col.p;
+    float *dval = (float *)h->hs_val.p, *dU = (float *)h->hs_U.p;
+    int32_t *dbest = (int32_t *)h->hs_best.p, *dst = (int32_t *)h->hs_st.p;
+    float *dsav = (float *)h->hs_sav.p, *dres = (float *)h->hs_res.p;
+    for (int64_t c = 0; c < nch; ++c) {   // copies of every chunk, in order, on the copy stream
+        const int64_t r0 = c * rows, r1 = std::min(m, r0 + rows);
+        const int64_t e0 = eb[(size_t)c], e1 = eb[(size_t)c + 1];
+        CK(h, cudaMemcpyAsync(dptr + r0, row_ptr + r0, sizeof(int64_t) * (r1 - r0 + 1),
+                              cudaMemcpyHostToDevice, h->hs_copy));
+        if (e1 > e0) {
+            CK(h, cudaMemcpyAsync(dcol + e0, col + e0, sizeof(int32_t) * (e1 - e0),
+                                  cudaMemcpyHostToDevice, h->hs_copy));
+            CK(h, cudaMemcpyAsync(dval + e0, val + e0, sizeof(float) * (e1 - e0),
+                                  cudaMemcpyHostToDevice, h->hs_copy));
+        }
+        CK(h, cudaEventRecord(h->hs_ev[(size_t)c], h->hs_copy));
+    }
+    for (int64_t c = 0; c < nch; ++c) {   // chunk c's solves wait for its copies only
+        const int64_t r0 = c * rows, r1 = std::min(m, r0 + rows), mc = r1 - r0;
+        const int64_t e0 = eb[(size_t)c], e1 = eb[(size_t)c + 1];
+        CK(h, cudaStreamWaitEvent(st, h->hs_ev[(size_t)c], 0));
+        int64_t *rp = drp + r0 + c;   // this chunk's rebased row pointers (mc + 1)
+        k_offset_copy<<<(unsigned)std::min<int64_t>((mc + 256) / 256 + 1, 4096), 256, 0, st>>>(
+            dptr + r0, mc + 1, -e0, rp);
+        CK(h, cudaGetLastError());
+        int rc;
+        if (check > 0)
+            rc = open_cf_complete_rows_checked(h, mc, e1 - e0, rp, dcol + e0, dval + e0,
+                                               dU + r0 * h->k, dst + r0, dres + r0,
+                                               check == 2 ? 1 : 0, st);
+        else
+            rc = open_cf_complete_rows(h, mc, e1 - e0, rp, dcol + e0, dval + e0,
+                                       dU + r0 * h->k, dst + r0, 0, st);
+        if (rc) return rc;
+        rc = open_cf_predict(h, dU + r0 * h->k, mc, nullptr, dbest + r0, dsav + r0, gamma,
+                             baseline_setting, st);
+        if (rc) return rc;
+        CK(h, cudaMemcpyAsync(best + r0, dbest + r0, sizeof(int32_t) * mc,
+                              cudaMemcpyDeviceToHost, st));
+        CK(h, cudaMemcpyAsync(saving + r0, dsav + r0, sizeof(float) * mc,
+                              cudaMemcpyDeviceToHost, st));
+        if (status)
+            CK(h, cudaMemcpyAsync(status + r0, dst + r0, sizeof(int32_t) * mc,
+                                  cudaMemcpyDeviceToHost, st));
+        if (resid)
+            CK(h, cudaMemcpyAsync(resid + r0, dres + r0, sizeof(float) * mc,
+                                  cudaMemcpyDeviceToHost, st));
     }
     return OPEN_CF_OK;
 }
