@@ -574,6 +574,8 @@ def run_gpu_large(args):
     host_in = pinned(row_ptr.cpu(), col.cpu(), val.cpu())
     e2e_api, e2e_same = None, None
     if factor != "fp64":
+        # the setting indices (< 4096) travel as 16-bit values
+        host_in[1] = col.cpu().to(torch.uint16).pin_memory()
         # open_cf_complete_select_host: one call per step; the copies of each
         # chunk of rows overlap the solves of the chunk before
         check = 2 if factor == "fp32-refine" else 1
@@ -592,8 +594,9 @@ def run_gpu_large(args):
         t_e2e = sum(a_.elapsed_time(b_) for a_, b_ in eve) / args.steps / 1e3
         h2d = int(sum(x.numel() * x.element_size() for x in host_in))
         d2h = int(b_h.numel() * 4 + s_h.numel() * 4)
-        e2e_api = ("open_cf_complete_select_host (pinned host CSR in, decisions out; the copies "
-                   "of each chunk of rows overlap the solves of the chunk before)")
+        e2e_api = ("open_cf_complete_select_host (pinned host CSR in, 16-bit setting indices; "
+                   "decisions out; the copies of each chunk of rows overlap the solves of the "
+                   "chunk before)")
     else:
         d_in = [torch.empty_like(x) for x in (row_ptr, col, val)]
 

@@ -212,7 +212,9 @@ int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t
  * overlap the solves.  Every chunk is solved as its own CSR, giving the results
  * separate calls on its rows would give.
  *  row_ptr (int64[m + 1], host; row_ptr[0] = 0, row_ptr[m] = nnz,
- *    non-decreasing), col (int32[nnz], host), val (float[nnz], host): the CSR.
+ *    non-decreasing), col (host; col_bytes = 4: int32[nnz]; col_bytes = 2:
+ *    uint16[nnz], for up to 65,535 settings, a quarter fewer bytes over the host
+ *    link; widened on the device), val (float[nnz], host): the CSR.
  *    Page-locked (pinned) host memory is needed for the copies to overlap
  *    anything; pageable memory works but serialises them.
  *  check = 0: plain fold-in; 1: with the residual check; 2: with the residual
@@ -229,7 +231,8 @@ int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t
  * factors of the last call; calls on one handle must not overlap on different
  * streams.  FP32 / BF16-Gram handles; FP64 handles return OPEN_CF_UNSUPPORTED. */
 int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
-                                 const int32_t *col, const float *val, int32_t check,
+                                 const void *col, int32_t col_bytes, const float *val,
+                                 int32_t check,
                                  float gamma, int32_t baseline_setting, int32_t *best,
                                  float *saving, int32_t *status, float *resid,
                                  int64_t chunk_rows, void *stream);

@@ -112,7 +112,7 @@ __device__ __forceinline__ void solve_pair32(const SolveArgs<float> &a, int64_t 
     }
     bad = (__ballot_sync(FULL, bad) >> (16 * h)) & 0xffffu;
     // ---- Cholesky with the forward substitution (lambda added to each pivot)
-    const float lam = float(a.lambda) * (a.wr ? float(s) : 1.f);   // weighted: lambda s_i
+    const float lam = a.wr ? (float)a.lambda * (float)(int)s : (float)a.lambda;   // weighted: lambda s_i
     float *SL = W.L + h * PairSmem32::LS;
     float y0 = b0, y1 = b1;
 #pragma unroll

@@ -66,6 +66,8 @@ struct open_cf {
     // G = V^T V in the step scratch is current while mlp_g_epoch == v_epoch
     uint64_t v_epoch = 1, mlp_g_epoch = 0;
     Buf vimg, pt_err;                 // split BF16 operand images of V, timeout flag (predict)
+    uint64_t vimg_epoch = 0;          // the images are of V while vimg_epoch == v_epoch
+    void *vimg_at = nullptr;          // ... and they are still at this address
     Buf ccount;                       // observations per column (weighted-lambda objective)
     Buf sg, sb, sn;                   // streaming refit: per-setting Gram, RHS, count sums
     bool stream_on = false;
@@ -76,7 +78,7 @@ struct open_cf {
     std::vector<GraphEntry> graphs;
     // host-buffer completion: device copies of the inputs and outputs, a copy
     // stream and per-chunk events (created on first use)
-    Buf hs_ptr, hs_rptr, hs_col, hs_val, hs_U, hs_best, hs_sav, hs_st, hs_res;
+    Buf hs_ptr, hs_rptr, hs_col, hs_col16, hs_val, hs_U, hs_best, hs_sav, hs_st, hs_res;
     cudaStream_t hs_copy = nullptr;
     std::vector<cudaEvent_t> hs_ev;
     std::string err;
@@ -604,7 +606,7 @@ void open_cf_destroy(open_cf_t *h) {
                        &h->b_Vw, &h->b_cptr, &h->b_cidx, &h->b_cval, &h->b_counter, &h->mlp_th,
                        &h->mlp_m1, &h->mlp_m2, &h->mlp_t, &h->mlp_cn, &h->mlp_scr, &h->mlp_img,
                        &h->mlp_err, &h->vimg, &h->pt_err, &h->ccount, &h->sg, &h->sb,
-                       &h->sn, &h->hs_ptr, &h->hs_rptr, &h->hs_col, &h->hs_val, &h->hs_U, &h->hs_best,
+                       &h->sn, &h->hs_ptr, &h->hs_rptr, &h->hs_col, &h->hs_col16, &h->hs_val, &h->hs_U, &h->hs_best,
                        &h->hs_sav, &h->hs_st, &h->hs_res})
             free_buf(*b);
     }
@@ -1043,7 +1045,11 @@ int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t
             CK(h, cudaMemsetAsync(h->pt_err.p, 0, 16, st));
         }
         CK(h, ensure(h, h->vimg, predict_tc_image_bytes(h->n)));
-        CK(h, launch_v_image((const float *)h->V.p, h->n, h->vimg.p, st));
+        if (h->vimg_epoch != h->v_epoch || h->vimg_at != h->vimg.p) {   // V's images, once per V
+            CK(h, launch_v_image((const float *)h->V.p, h->n, h->vimg.p, st));
+            h->vimg_epoch = h->v_epoch;
+            h->vimg_at = h->vimg.p;
+        }
         PredictTcArgs a{};
         a.m = m; a.n = h->n; a.U = as<float>(U); a.ldu = h->k; a.k = h->k;
         a.Vimg = h->vimg.p; a.cg = sel ? (const float *)h->cg.p : nullptr;
@@ -1061,8 +1067,20 @@ int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t
     return OPEN_CF_OK;
 }
 
+namespace {
+// 16-bit setting indices of one chunk widened to the solvers' int32 (kept as
+// unsigned: up to 65,535 settings)
+__global__ void k_widen_u16(const uint16_t *__restrict__ src, int64_t count,
+                            int32_t *__restrict__ dst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (int32_t)src[e];
+}
+}  // namespace
+
 int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
-                                 const int32_t *col, const float *val, int32_t check,
+                                 const void *col, int32_t col_bytes, const float *val,
+                                 int32_t check,
                                  float gamma, int32_t baseline_setting, int32_t *best,
                                  float *saving, int32_t *status, float *resid,
                                  int64_t chunk_rows, void *stream) {
@@ -1073,6 +1091,8 @@ int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int
         return fail(h, OPEN_CF_INVALID_ARG, "row_ptr, best or saving is NULL");
     if (nnz > 0 && (!col || !val)) return fail(h, OPEN_CF_INVALID_ARG, "col or val is NULL");
     if (check < 0 || check > 2) return fail(h, OPEN_CF_INVALID_ARG, "check must be 0, 1 or 2");
+    if (col_bytes != 2 && col_bytes != 4)
+        return fail(h, OPEN_CF_INVALID_ARG, "col_bytes must be 2 or 4");
     if (check == 0 && resid) return fail(h, OPEN_CF_INVALID_ARG, "resid needs check >= 1");
     if (h->f64) return fail(h, OPEN_CF_UNSUPPORTED, "host-buffer completion is FP32 / BF16-Gram only");
     if (check > 0 && (h->KP != 32 || h->cfg.cholesky_fp64))
@@ -1110,6 +1130,7 @@ int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int
     CK(h, ensure(h, h->hs_ptr, sizeof(int64_t) * (m + 1)));
     CK(h, ensure(h, h->hs_rptr, sizeof(int64_t) * (m + nch)));
     CK(h, ensure(h, h->hs_col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    if (col_bytes == 2) CK(h, ensure(h, h->hs_col16, sizeof(uint16_t) * std::max<int64_t>(nnz, 1)));
     CK(h, ensure(h, h->hs_val, sizeof(float) * std::max<int64_t>(nnz, 1)));
     CK(h, ensure(h, h->hs_U, sizeof(float) * m * h->k));
     CK(h, ensure(h, h->hs_best, sizeof(int32_t) * m));
@@ -1117,7 +1138,7 @@ int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int
     CK(h, ensure(h, h->hs_st, sizeof(int32_t) * m));
     if (check > 0) CK(h, ensure(h, h->hs_res, sizeof(float) * m));
     if (!h->hs_copy) CK(h, cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking));
-    while ((int64_t)h->hs_ev.size() < nch + 1) {
+    while ((int64_t)h->hs_ev.size() < 2 * nch + 2) {   // copies, start, solves, end
         cudaEvent_t e;
         CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         h->hs_ev.push_back(e);
@@ -1131,27 +1152,41 @@ int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int
     float *dval = (float *)h->hs_val.p, *dU = (float *)h->hs_U.p;
     int32_t *dbest = (int32_t *)h->hs_best.p, *dst = (int32_t *)h->hs_st.p;
     float *dsav = (float *)h->hs_sav.p, *dres = (float *)h->hs_res.p;
-    for (int64_t c = 0; c < nch; ++c) {   // copies of every chunk, in order, on the copy stream
-        const int64_t r0 = c * rows, r1 = std::min(m, r0 + rows);
+    // copy stream: every chunk's copies in order, then its row pointers rebased
+    // to its first entry (and 16-bit indices widened), then an event
+    for (int64_t c = 0; c < nch; ++c) {
+        const int64_t r0 = c * rows, r1 = std::min(m, r0 + rows), mc = r1 - r0;
         const int64_t e0 = eb[(size_t)c], e1 = eb[(size_t)c + 1];
-        CK(h, cudaMemcpyAsync(dptr + r0, row_ptr + r0, sizeof(int64_t) * (r1 - r0 + 1),
+        CK(h, cudaMemcpyAsync(dptr + r0, row_ptr + r0, sizeof(int64_t) * (mc + 1),
                               cudaMemcpyHostToDevice, h->hs_copy));
         if (e1 > e0) {
-            CK(h, cudaMemcpyAsync(dcol + e0, col + e0, sizeof(int32_t) * (e1 - e0),
-                                  cudaMemcpyHostToDevice, h->hs_copy));
+            if (col_bytes == 2)
+                CK(h, cudaMemcpyAsync((uint16_t *)h->hs_col16.p + e0,
+                                      (const uint16_t *)col + e0, sizeof(uint16_t) * (e1 - e0),
+                                      cudaMemcpyHostToDevice, h->hs_copy));
+            else
+                CK(h, cudaMemcpyAsync(dcol + e0, (const int32_t *)col + e0,
+                                      sizeof(int32_t) * (e1 - e0), cudaMemcpyHostToDevice,
+                                      h->hs_copy));
             CK(h, cudaMemcpyAsync(dval + e0, val + e0, sizeof(float) * (e1 - e0),
                                   cudaMemcpyHostToDevice, h->hs_copy));
         }
+        k_offset_copy<<<(unsigned)std::min<int64_t>((mc + 256) / 256 + 1, 4096), 256, 0,
+                        h->hs_copy>>>(dptr + r0, mc + 1, -e0, drp + r0 + c);
+        CK(h, cudaGetLastError());
+        if (col_bytes == 2 && e1 > e0) {
+            k_widen_u16<<<(unsigned)std::min<int64_t>((e1 - e0 + 255) / 256, 4 * 148), 256, 0,
+                          h->hs_copy>>>((const uint16_t *)h->hs_col16.p + e0, e1 - e0, dcol + e0);
+            CK(h, cudaGetLastError());
+        }
         CK(h, cudaEventRecord(h->hs_ev[(size_t)c], h->hs_copy));
     }
-    for (int64_t c = 0; c < nch; ++c) {   // chunk c's solves wait for its copies only
+    // the caller's stream: chunk c's solves wait for its copies only, then an event
+    for (int64_t c = 0; c < nch; ++c) {
         const int64_t r0 = c * rows, r1 = std::min(m, r0 + rows), mc = r1 - r0;
         const int64_t e0 = eb[(size_t)c], e1 = eb[(size_t)c + 1];
         CK(h, cudaStreamWaitEvent(st, h->hs_ev[(size_t)c], 0));
         int64_t *rp = drp + r0 + c;   // this chunk's rebased row pointers (mc + 1)
-        k_offset_copy<<<(unsigned)std::min<int64_t>((mc + 256) / 256 + 1, 4096), 256, 0, st>>>(
-            dptr + r0, mc + 1, -e0, rp);
-        CK(h, cudaGetLastError());
         int rc;
         if (check > 0)
             rc = open_cf_complete_rows_checked(h, mc, e1 - e0, rp, dcol + e0, dval + e0,
@@ -1164,17 +1199,26 @@ int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int
         rc = open_cf_predict(h, dU + r0 * h->k, mc, nullptr, dbest + r0, dsav + r0, gamma,
                              baseline_setting, st);
         if (rc) return rc;
+        CK(h, cudaEventRecord(h->hs_ev[(size_t)(nch + 1 + c)], st));
+    }
+    // copy stream again (after all input copies): each chunk's decisions back
+    // once its solves are done, then the caller's stream waits for the last
+    for (int64_t c = 0; c < nch; ++c) {
+        const int64_t r0 = c * rows, mc = std::min(m, r0 + rows) - r0;
+        CK(h, cudaStreamWaitEvent(h->hs_copy, h->hs_ev[(size_t)(nch + 1 + c)], 0));
         CK(h, cudaMemcpyAsync(best + r0, dbest + r0, sizeof(int32_t) * mc,
-                              cudaMemcpyDeviceToHost, st));
+                              cudaMemcpyDeviceToHost, h->hs_copy));
         CK(h, cudaMemcpyAsync(saving + r0, dsav + r0, sizeof(float) * mc,
-                              cudaMemcpyDeviceToHost, st));
+                              cudaMemcpyDeviceToHost, h->hs_copy));
         if (status)
             CK(h, cudaMemcpyAsync(status + r0, dst + r0, sizeof(int32_t) * mc,
-                                  cudaMemcpyDeviceToHost, st));
+                                  cudaMemcpyDeviceToHost, h->hs_copy));
         if (resid)
             CK(h, cudaMemcpyAsync(resid + r0, dres + r0, sizeof(float) * mc,
-                                  cudaMemcpyDeviceToHost, st));
+                                  cudaMemcpyDeviceToHost, h->hs_copy));
     }
+    CK(h, cudaEventRecord(h->hs_ev[(size_t)(2 * nch + 1)], h->hs_copy));
+    CK(h, cudaStreamWaitEvent(st, h->hs_ev[(size_t)(2 * nch + 1)], 0));
     return OPEN_CF_OK;
 }
 

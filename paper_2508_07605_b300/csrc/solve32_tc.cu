@@ -413,6 +413,9 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
     PairFetch cur;
     if (k0 < k1) fetch_pair(a, k0, M, lane, cur);
     const bool dual_ok = DUAL && !a.resid && !a.refine && !a.u_given;
+    // lambda in FP32 once (a conversion from the double argument runs on the FP64
+    // pipe, which on this part is a small fraction of the FP32 rate)
+    const float lam0 = (float)a.lambda;
 
     for (int64_t k = k0; k < k1; ++k) {
       // A pair with one thin and one thick row runs in two passes, each row
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             // half h solves system h: lane i holds row i of G_h + lambda I
             const int64_t s = h ? pf.s[1] : pf.s[0];
             const bool bad = h ? bad1 : bad0;
-            const float lam = float(a.lambda) * (a.wr ? float(s) : 1.f);   // weighted: lambda s_i
+            const float lam = a.wr ? lam0 * (float)(int)s : lam0;   // weighted: lambda s_i
             float *G = Gb + h * DUAL_SYS;
             G[i * (DUAL_LD + 1)] += lam;
             __syncwarp();
@@ -788,7 +791,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
         const int64_t s = h ? pf.s[1] : pf.s[0];
         const int64_t row = h ? pf.row[1] : pf.row[0];
         const bool bad = h ? bad1 : bad0;
-        const float lam = float(a.lambda) * (a.wr ? float(s) : 1.f);   // weighted: lambda s_i
+        const float lam = a.wr ? lam0 * (float)(int)s : lam0;   // weighted: lambda s_i
         SA[ro_i + i] += lam;
         SA[ro_i16 + i + 16] += lam;
         __syncwarp();

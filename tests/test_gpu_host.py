@@ -32,12 +32,13 @@ def _pinned(t):
     return t.cpu().pin_memory()
 
 
-@pytest.mark.parametrize("precision,check,chunk", [
-    ("bf16_gram", 2, 4096),     # the default line's configuration, 13 chunks (ragged last)
-    ("bf16_gram", 1, 0),        # default chunking
-    ("fp32", 0, 2560),          # plain fold-in, FP32 mode
+@pytest.mark.parametrize("precision,check,chunk,col16", [
+    ("bf16_gram", 2, 4096, False),   # the default line's configuration, 13 chunks (ragged last)
+    ("bf16_gram", 2, 4096, True),    # the same with 16-bit setting indices
+    ("bf16_gram", 1, 0, False),      # default chunking
+    ("fp32", 0, 2560, True),         # plain fold-in, FP32 mode
 ])
-def test_host_pipeline_equals_device_calls(orc, precision, check, chunk):
+def test_host_pipeline_equals_device_calls(orc, precision, check, chunk, col16):
     m = 50_001
     prob, cpu, gpu = _problem(m, seed=3)
     h = ocf.OpenCF(k=prob.k, lam=prob.lam, precision=precision, cpu_caps=cpu, gpu_caps=gpu)
@@ -51,7 +52,8 @@ def test_host_pipeline_equals_device_calls(orc, precision, check, chunk):
     T, best, sav = h.predict(U, gamma=0.05)
     torch.cuda.synchronize()
     # the same from pinned host memory, in chunks
-    hp, hc, hv = _pinned(prob.row_ptr), _pinned(prob.col), _pinned(prob.val)
+    hp, hv = _pinned(prob.row_ptr), _pinned(prob.val)
+    hc = (prob.col.cpu().to(torch.uint16) if col16 else prob.col.cpu()).pin_memory()
     st_h = torch.empty(m, dtype=torch.int32).pin_memory()
     res_h = torch.empty(m, dtype=torch.float32).pin_memory() if check > 0 else None
     for _ in range(2):   # twice: the second call reuses the handle's device copies
