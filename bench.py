@@ -461,6 +461,15 @@ WORKLOAD_C5 = "mixed precision at scale: 1M apps x 4096 settings (64x64 caps), k
               "on tensor cores (split hi+lo, FP32 accumulation), {factor}, per-row normal-" \
               "equation residual check; + reconstruction U V^T fused with Algorithm 2 " \
               "(gamma=0.05) over all 4096 settings"
+def c5_config(factor, ws, m, n, k, nnz):
+    """The workload 5 config both arms report (the same workload; each arm's
+    own arithmetic is stated outside the config)."""
+    return {"workload": WORKLOAD_C5.format(factor=C5_FACTOR[factor]),
+            "parallelism": f"replicas{ws}: each GPU completes its own 1M apps",
+            "m": m, "n": n, "k": k, "nnz": nnz,
+            "l2": "inputs (~0.35 GB of CSR) exceed L2; V's 0.5 MB stays resident"}
+
+
 C5_FACTOR = {
     "fp32-refine": "FP32 k x k Cholesky + one refinement step (double-FP32 residual)",
     "fp32": "FP32 k x k Cholesky",
@@ -684,13 +693,10 @@ def run_gpu_large(args):
                            "max": max(step_ms)},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16+f32" if factor != "fp64" else "bf16+f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_C5.format(factor=C5_FACTOR[factor]),
-                   "parallelism": f"replicas{ws}: each GPU completes its own 1M apps",
-                   "m": m, "n": n, "k": k, "nnz": nnz,
-                   "l2": "inputs (~0.35 GB of CSR) exceed L2; V's 0.5 MB stays resident",
-                   "timing": "CUDA events on the launching stream around the fold-in and the "
-                             "reconstruction of each step; a 10 ms device spin before the first "
-                             "timed step lets the host queue ahead (e2e keeps host costs)"},
+        "config": c5_config(factor, ws, m, n, k, nnz),
+        "timing": "CUDA events on the launching stream around the fold-in and the "
+                  "reconstruction of each step; a 10 ms device spin before the first "
+                  "timed step lets the host queue ahead (e2e keeps host costs)",
         "parts_ms": {"fold_in": t_fold * 1e3, "predict_select": t_pred * 1e3},
         "error_vs_fp64_oracle": err,
         "roofline": dominant,
@@ -741,11 +747,12 @@ def run_reference_c5(args):
     value = per * args.steps / sum(times)
     line = {
         "impl": "reference", "metric": "ALS row-solves/s", "value": value,
-        "unit": "row-solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "unit": "row-solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_C5.format(factor="FP64 k x k Cholesky (the oracle)"),
-                   "m": prob.m, "n": prob.n, "k": prob.k, "nnz": int(prob.col.numel())},
+        "config": c5_config(args.c5_factor, ws, prob.m, prob.n, prob.k, int(prob.col.numel())),
+        "computed_as": "the FP64 oracle: FP64 Gram, FP64 k x k Cholesky, FP64 residual, "
+                       "reconstruction and Algorithm 2 of the sampled apps",
         "cpu_baseline": {"value": value, "unit": "row-solves/s", "cores": orc.num_threads(),
                          "kind": "oracle",
                          "sample": f"{per} sampled apps per step: FP64 fold-in + normal-equation "
