@@ -166,7 +166,9 @@ int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_
  *    products and sums, ~2^-44 relative), -1 for rows whose status is not OK.
  *  refine = 1: one step of iterative refinement: the correction A_i d = r_i
  *    (r_i that residual) is solved with the same FP32 factor and u_i += d;
- *    resid then reports the refined u_i.  refine = 0: no refinement. */
+ *    resid then reports the refined u_i, its residual formed as r_i - A_i D
+ *    (D the step actually taken, in FP32: an error of ~k kappa eps^2 |A_i||u_i|,
+ *    well below the residual of an FP32 u_i).  refine = 0: no refinement. */
 int open_cf_complete_rows_checked(open_cf_t *h, int64_t m_new, int64_t nnz,
                                   const int64_t *row_ptr, const int32_t *col, const float *val,
                                   float *U_out, int32_t *status, float *resid, int32_t refine,

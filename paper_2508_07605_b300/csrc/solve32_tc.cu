@@ -40,7 +40,9 @@
 // rate, so this costs a fraction of one FP64 matrix-vector product.  With
 // refinement, the correction A d = r is solved with the same FP32 factor,
 // u += d, and the residual of the refined u is the one reported, as
-// |A u - b| / (|A|_F |u| + |b|).  A residual-only mode takes u as input.
+// |A u - b| / (|A|_F |u| + |b|); it is formed as r - A D with D the step taken,
+// in FP32 (its error, ~k kappa eps^2 |A||u|, is far below the residual itself).
+// A residual-only mode takes u as input.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -153,6 +155,39 @@ __device__ __forceinline__ float2 ext_residual(const float *A, const float *x, i
     }
     if (NORMS) aa = A2;
     return make_float2(S.x + C.x, S.y + C.y);
+}
+
+// Rows i and i + 16 of r - A d in FP32 (A symmetric from its packed lower
+// triangle, d from shared memory; the access pattern of ext_residual).
+__device__ __forceinline__ float2 residual_update(const float *A, const float *d, int i, int o0,
+                                                  int o1, float2 r) {
+    float2 S = r;
+    const float4 *d4 = reinterpret_cast<const float4 *>(d);
+    const float4 *r4 = reinterpret_cast<const float4 *>(A + o1);
+#pragma unroll
+    for (int t = 0; t < KP / 4; ++t) {
+        const float4 dv = d4[t];
+        const float ds[4] = {dv.x, dv.y, dv.z, dv.w};
+        float g1v[4];
+        if (t < 4) {
+            const float4 g = r4[t];
+            g1v[0] = g.x; g1v[1] = g.y; g1v[2] = g.z; g1v[3] = g.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = 4 * t + u;
+            float g0, g1;
+            if (e < 16) {
+                g0 = A[e <= i ? o0 + e : rowoff(e) + i];
+                g1 = g1v[u];
+            } else {
+                g0 = A[rowoff(e) + i];
+                g1 = A[e <= i + 16 ? o1 + e : rowoff(e) + i + 16];
+            }
+            S = __ffma2_rn(make_float2(-g0, -g1), make_float2(ds[u], ds[u]), S);
+        }
+    }
+    return S;
 }
 
 template <bool BF>
@@ -912,20 +947,24 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                     }
                 }
                 const float2 dd = back_subst(SL, i, co_i, co_i16, z0 * inv0, z1 * inv1, inv0, inv1);
+                // The refined residual b - A x' = r - A D with D = x' - x, the step
+                // actually taken (exact in FP32 where the correction is small next
+                // to x).  |D| is ~kappa eps |x|, so A D in FP32 errs by ~k kappa eps^2
+                // |A||x|, far below the residual's own size (~eps |A||x| once x' is
+                // rounded to FP32): the extended-precision part is r, not A D.
+                float d0 = 0.f, d1 = 0.f;
                 if (want) {
-                    x0 += dd.x;
-                    x1 += dd.y;
+                    const float n0 = x0 + dd.x, n1 = x1 + dd.y;
+                    d0 = n0 - x0;
+                    d1 = n1 - x1;
+                    x0 = n0;
+                    x1 = n1;
                 }
-            }
-            if (a.refine && !a.u_given) {
                 __syncwarp();   // every lane has read x before it is rewritten
-                if (want) {
-                    Sx[i] = x0;
-                    Sx[i + 16] = x1;
-                }
+                Sx[i] = d0;
+                Sx[i + 16] = d1;
                 __syncwarp();
-                float2 aa2;
-                r = ext_residual<false>(SA, Sx, i, ro_i, ro_i16, bq, aa2);
+                r = residual_update(SA, Sx, i, ro_i, ro_i16, r);
             }
             // |A|_F over the k x k system: padded rows (q >= k) hold only lambda
             const float rr = half_sum(r.x * r.x + r.y * r.y);

@@ -88,9 +88,16 @@ def test_checked_foldin_matches_oracle(orc, precision, k):
         r = host(r)
         assert (r[~ok] == -1).all()
         assert (r[ok] >= 0).all() and r[ok].max() <= 1e-5, r[ok].max()
-    # the reported residual of the refined rows, recomputed for the refined U
+    # the reported residual of the refined rows (the first residual updated by the
+    # step taken) against the double-FP32 residual recomputed for the refined U:
+    # the update's FP32 error is ~k kappa eps^2 |A||u| against a residual of
+    # ~eps |A||u| (measured: within 1.2e-5 relative; gate 1e-3)
     rg = host(h.normal_residual(*csr, U2))
-    assert np.allclose(rg[ok], host(r2)[ok], rtol=0, atol=1e-7)
+    r2h = host(r2)
+    assert np.allclose(rg[ok], r2h[ok], rtol=0, atol=1e-7)
+    rel = np.abs(rg[ok] - r2h[ok]) / np.maximum(rg[ok], 1e-12)
+    print(f"refined residual vs recomputed: max rel diff {rel.max():.2e}, median {np.median(rel):.2e}")
+    assert (np.abs(rg[ok] - r2h[ok]) <= 1e-3 * rg[ok] + 1e-12).all()
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16_gram"])
