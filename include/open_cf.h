@@ -36,7 +36,10 @@
  *    stream).  A return of OPEN_CF_OK means the work is enqueued.  Argument
  *    errors are detected synchronously on the host and leave the handle
  *    unchanged.
- *  - A handle may be used by one host thread at a time.
+ *  - A handle may be used by one host thread at a time.  What a handle keeps
+ *    between calls (V and its BF16 copies and operand images, workspaces) is
+ *    written on the stream of the call that produces it; calls on different
+ *    streams must be ordered by the caller (events), as for any shared buffer.
  *  - Calls that run many kernels (fits, joint refits, streaming ingests, the
  *    learned path's training step) capture them once into a CUDA graph kept
  *    per argument set (sizes and array addresses; up to 16 per handle) and
@@ -207,8 +210,9 @@ int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t
  * rows (open_cf_complete_rows with joint = 0, or open_cf_complete_rows_checked)
  * followed by open_cf_predict's Algorithm 2, for a caller whose CSR lives in
  * host memory and who wants the decisions back in host memory.  The rows are
- * processed in chunks (chunk_rows rows, rounded up to a multiple of 256; 0 =
- * about m / 16, at least 32,768, rounded up to 128 rows per SM): the
+ * processed in chunks (chunk_rows rows, rounded up to a multiple of 256 and to
+ * at most 1024 chunks; 0 = about m / 16, at least 32,768, rounded up to 128 rows
+ * per SM): the
  * host-to-device copies of chunk c + 1 run on a copy
  * stream of the handle while chunk c is solved on `stream`, so the copies
  * overlap the solves.  Every chunk is solved as its own CSR, giving the results

@@ -1115,6 +1115,7 @@ int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int
         rows = std::max<int64_t>(32768, (m + 15) / 16);
         rows = (rows + unit - 1) / unit * unit;
     }
+    rows = std::max<int64_t>(rows, ((m + 1023) / 1024 + 255) / 256 * 256);   // at most 1024 chunks
     const int64_t nch = (m + rows - 1) / rows;
     // chunk boundaries in the entry arrays, read on the host; a non-decreasing
     // sequence inside [0, nnz] is required here.  Each chunk is solved as a CSR

@@ -84,6 +84,22 @@ def test_host_pipeline_pageable_and_errors():
     b_h, s_h, _, _ = h.complete_select_host(hp, hc, hv, check=2, gamma=0.1, chunk_rows=256)
     torch.cuda.synchronize()
     assert torch.equal(b_h, best.cpu()) and torch.equal(s_h, sav.cpu())
+    # rows with an out-of-range setting index: the same BAD_INPUT status and the same
+    # decisions as the device-memory calls, whichever chunk the row falls in
+    cb = hc.clone()
+    cb[int(hp[5])] = -3
+    cb[int(hp[2000])] = prob.n + 7
+    cbd = cb.to(DEV)
+    Ub, stb, _ = h.complete_rows_checked(prob.row_ptr, cbd, prob.val, refine=True)
+    _, bb, sb = h.predict(Ub, gamma=0.1, want_T=False)
+    torch.cuda.synchronize()
+    assert int(stb[5]) == ocf.ROW_BAD_INPUT and int(stb[2000]) == ocf.ROW_BAD_INPUT
+    st_h = torch.empty(m, dtype=torch.int32)
+    b_h, s_h, _, _ = h.complete_select_host(hp, cb, hv, check=2, gamma=0.1, status=st_h,
+                                            chunk_rows=512)
+    torch.cuda.synchronize()
+    assert torch.equal(st_h, stb.cpu())
+    assert torch.equal(b_h, bb.cpu()) and torch.equal(s_h, sb.cpu())
     # an empty batch does nothing
     e = torch.zeros(1, dtype=torch.int64)
     b0, _, _, _ = h.complete_select_host(e, hc[:0], hv[:0])
