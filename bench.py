@@ -709,7 +709,9 @@ def run_gpu_large(args):
                 "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3,
                 **({"api": e2e_api, "decisions_equal_device_calls": e2e_same}
                    if e2e_api else {})},
-        "gpu_launches": 3 * args.steps,
+        # per timed step: the fold-in and the reconstruction (V's operand images are
+        # built once per V, in the warm-up)
+        "gpu_launches": 2 * args.steps,
         "clocks": clocks.summary(local),
     }
     print(json.dumps(line), flush=True)
