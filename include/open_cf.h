@@ -437,6 +437,28 @@ int open_cf_csr_to_csc_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t 
                                const int32_t *col, const float *val, int64_t *col_ptr,
                                int32_t *row_idx, float *cval, void *stream);
 
+/* Checkpoint and resume (extension; the paper has no counterpart): the state
+ * a handle has learned or accumulated, written to host memory and restored
+ * into a handle of the same configuration, so that a fit, the learned path's
+ * training or the streaming refit can stop and continue with results
+ * bit-identical to an uninterrupted run.  The checkpoint holds a header (the
+ * configuration: k, precision, factorisation, lambda, weighting; the number of
+ * settings; the cap grid), then each part the handle has: V (as the handle
+ * keeps it), the learned warm start's FP32 parameters with their Adam moments
+ * and step state, the streaming refit's per-setting sums; and an FNV-1a 64-bit
+ * checksum of all of it.  Little-endian.
+ * open_cf_save: buf (host, cap bytes) receives the checkpoint; with buf NULL
+ *   only *size_out is set (the size needed).  Waits for all work on the device
+ *   (cudaDeviceSynchronize) first.  OPEN_CF_INVALID_ARG if cap is too small.
+ * open_cf_load: restores a checkpoint of `size` bytes (host) into h, which must
+ *   have been created with the same k, precision, cholesky_fp64, lambda,
+ *   weighted_lambda and cap grid; anything else, a bad checksum or a truncated
+ *   buffer returns OPEN_CF_INVALID_ARG and leaves h unchanged.  Synchronous.
+ *   The offline block kept for joint refits, workspaces and captured graphs
+ *   are not part of a checkpoint. */
+int open_cf_save(open_cf_t *h, void *buf, int64_t cap, int64_t *size_out);
+int open_cf_load(open_cf_t *h, const void *buf, int64_t size);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,8 @@ _SIGNATURES = {
                                       [_V, _I64, _I64, _V, _V, _V, _V, _V, _V, _I32, _V]),
     "open_cf_normal_residual": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _V, _V, _V, _V]),
     "open_cf_predict": (ctypes.c_int, [_V, _V, _I64, _V, _V, _V, _F, _I32, _V]),
+    "open_cf_save": (ctypes.c_int, [_V, _V, _I64, ctypes.POINTER(_I64)]),
+    "open_cf_load": (ctypes.c_int, [_V, _V, _I64]),
     "open_cf_complete_select_host": (ctypes.c_int, [_V, _I64, _I64, _V, _V, _I32, _V, _I32, _F,
                                                     _I32, _V, _V, _V, _V, _I64, _V]),
     "open_cf_select": (ctypes.c_int, [_V, _V, _I64, _I64, _V, _V, _F, _I32, _V]),
@@ -313,6 +315,23 @@ class OpenCF:
             int(baseline), _ptr(best), _ptr(saving), _ptr(status), _ptr(resid), int(chunk_rows),
             self._stream()))
         return best, saving, status, resid
+
+    def save(self) -> bytes:
+        """Checkpoint of the handle's state (V, learned warm start with its Adam
+        state, streaming sums) as bytes; waits for the device."""
+        size = _I64(0)
+        self._check(lib().open_cf_save(self._h, None, 0, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        self._check(lib().open_cf_save(self._h, buf, size.value, ctypes.byref(size)))
+        return buf.raw[:size.value]
+
+    def load(self, data: bytes):
+        """Restore a checkpoint made by save() on a handle of the same configuration."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        self._check(lib().open_cf_load(self._h, buf, len(data)))
+        n = int.from_bytes(bytes(data[48:56]), "little", signed=True)   # the header's settings
+        if n > 0:
+            self.n = n
 
     def normal_residual(self, row_ptr, col, val, U):
         """Per-row relative normal-equation residual of the given factors."""

@@ -1440,7 +1440,10 @@ int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const i
     return OPEN_CF_OK;
 }
 
+static int mlp_caps_table(open_cf_t *h);
+
 int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
+    int rc_caps;
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (h->k != MLP_K) return fail(h, OPEN_CF_UNSUPPORTED, "the learned warm start has k = 32");
@@ -1464,7 +1467,15 @@ int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
     CK(h, cudaMemsetAsync(h->mlp_m2.p, 0, 4 * MLP_P_INT, st));
     CK(h, cudaMemsetAsync(h->mlp_t.p, 0, 16, st));
     CK(h, launch_mlp_images(th, h->mlp_img.p, st));   // the tensor cores' BF16 operand images
-    // normalised caps of every setting (features), FP32
+    rc_caps = mlp_caps_table(h);
+    if (rc_caps) return rc_caps;
+    CK(h, cudaStreamSynchronize(st));
+    h->mlp_ready = true;
+    return OPEN_CF_OK;
+}
+
+// normalised caps of every setting (the learned path's features), FP32
+static int mlp_caps_table(open_cf_t *h) {
     const int64_t ns = (int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size();
     if (ns > 0) {
         const double cmin = *std::min_element(h->cpu_caps.begin(), h->cpu_caps.end());
@@ -1481,8 +1492,6 @@ int open_cf_mlp_set_params(open_cf_t *h, const float *params, void *stream) {
         CK(h, ensure(h, h->mlp_cn, 4 * cn.size()));
         CK(h, cudaMemcpy(h->mlp_cn.p, cn.data(), 4 * cn.size(), cudaMemcpyHostToDevice));
     }
-    CK(h, cudaStreamSynchronize(st));
-    h->mlp_ready = true;
     return OPEN_CF_OK;
 }
 
@@ -1613,6 +1622,200 @@ int open_cf_phase_detect(const float *power, int64_t n_traces, int64_t len, int6
     if (launch_phase_detect(power, n_traces, len, ld, p_th, window, first, S(stream)) !=
         cudaSuccess)
         return OPEN_CF_CUDA_ERROR;
+    return OPEN_CF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume of a handle's state: a header, the cap grid, then the
+// sections the handle holds (V in its padded device layout; the learned warm
+// start's FP32 masters, Adam moments and step state; the streaming refit's
+// per-setting sums), and an FNV-1a 64-bit checksum of all that precedes it.
+// Little-endian, as the hosts this library runs on.
+static const char CKPT_MAGIC[8] = {'O', 'P', 'E', 'N', 'C', 'F', 'c', 'k'};
+static const uint32_t CKPT_VERSION = 1;
+enum : uint32_t { CKPT_V = 1u, CKPT_MLP = 2u, CKPT_STREAM = 4u };
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, flags;
+    int32_t k, KP, precision, cholesky_fp64, weighted_lambda, sweeps;
+    double lambda;
+    int64_t n;
+    int32_t n_cpu, n_gpu, esz, reserved;
+    int64_t bytes;   // the whole checkpoint, checksum included
+};
+static_assert(sizeof(CkptHeader) == 80, "checkpoint header layout");
+
+static uint64_t fnv1a64(const unsigned char *p, size_t n) {
+    uint64_t x = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        x ^= p[i];
+        x *= 0x100000001b3ull;
+    }
+    return x;
+}
+
+static int64_t ckpt_bytes(const open_cf_t *h, uint32_t flags) {
+    const int64_t n = h->n, KP = h->KP, e = (int64_t)h->esz;
+    int64_t b = (int64_t)sizeof(CkptHeader) + 8 * (int64_t)(h->cpu_caps.size() + h->gpu_caps.size());
+    if (flags & CKPT_V) b += e * n * KP;
+    if (flags & CKPT_MLP) b += 3 * 4 * MLP_P_INT + 16;
+    if (flags & CKPT_STREAM) b += e * n * KP * KP + e * n * KP + 8 * n;
+    return b + 8;
+}
+
+int open_cf_save(open_cf_t *h, void *buf, int64_t cap, int64_t *size_out) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    const uint32_t flags = (h->V_set ? CKPT_V : 0u) | (h->mlp_ready ? CKPT_MLP : 0u) |
+                           (h->stream_on ? CKPT_STREAM : 0u);
+    const int64_t total = ckpt_bytes(h, flags);
+    if (size_out) *size_out = total;
+    if (!buf) return OPEN_CF_OK;
+    if (cap < total) return fail(h, OPEN_CF_INVALID_ARG, "buffer of %lld bytes, %lld needed",
+                                 (long long)cap, (long long)total);
+    DeviceGuard g(h->device);
+    CK(h, cudaDeviceSynchronize());   // the state is complete on every stream
+    unsigned char *p = (unsigned char *)buf;
+    CkptHeader hd{};
+    memcpy(hd.magic, CKPT_MAGIC, 8);
+    hd.version = CKPT_VERSION;
+    hd.flags = flags;
+    hd.k = h->k; hd.KP = h->KP; hd.precision = (int32_t)h->cfg.precision;
+    hd.cholesky_fp64 = h->cfg.cholesky_fp64; hd.weighted_lambda = h->cfg.weighted_lambda;
+    hd.sweeps = h->cfg.sweeps; hd.lambda = h->cfg.lambda;
+    hd.n = h->V_set ? h->n : 0;
+    hd.n_cpu = (int32_t)h->cpu_caps.size(); hd.n_gpu = (int32_t)h->gpu_caps.size();
+    hd.esz = (int32_t)h->esz; hd.bytes = total;
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    for (double c : h->cpu_caps) { memcpy(p, &c, 8); p += 8; }
+    for (double c : h->gpu_caps) { memcpy(p, &c, 8); p += 8; }
+    const int64_t n = h->n, KP = h->KP, e = (int64_t)h->esz;
+    auto d2h = [&](const void *src, int64_t bytes) -> cudaError_t {
+        cudaError_t r = cudaMemcpy(p, src, (size_t)bytes, cudaMemcpyDeviceToHost);
+        p += bytes;
+        return r;
+    };
+    if (flags & CKPT_V) CK(h, d2h(h->V.p, e * n * KP));
+    if (flags & CKPT_MLP) {
+        CK(h, d2h(h->mlp_th.p, 4 * MLP_P_INT));
+        CK(h, d2h(h->mlp_m1.p, 4 * MLP_P_INT));
+        CK(h, d2h(h->mlp_m2.p, 4 * MLP_P_INT));
+        CK(h, d2h(h->mlp_t.p, 16));
+    }
+    if (flags & CKPT_STREAM) {
+        CK(h, d2h(h->sg.p, e * n * KP * KP));
+        CK(h, d2h(h->sb.p, e * n * KP));
+        CK(h, d2h(h->sn.p, 8 * n));
+    }
+    const uint64_t sum = fnv1a64((const unsigned char *)buf, (size_t)(total - 8));
+    memcpy(p, &sum, 8);
+    return OPEN_CF_OK;
+}
+
+int open_cf_load(open_cf_t *h, const void *buf, int64_t size) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (!buf || size < (int64_t)sizeof(CkptHeader) + 8)
+        return fail(h, OPEN_CF_INVALID_ARG, "no checkpoint or too short");
+    const unsigned char *p = (const unsigned char *)buf;
+    CkptHeader hd;
+    memcpy(&hd, p, sizeof(hd));
+    if (memcmp(hd.magic, CKPT_MAGIC, 8) != 0) return fail(h, OPEN_CF_INVALID_ARG, "not a checkpoint");
+    if (hd.version != CKPT_VERSION)
+        return fail(h, OPEN_CF_UNSUPPORTED, "checkpoint version %u", hd.version);
+    if (hd.bytes != size) return fail(h, OPEN_CF_INVALID_ARG, "checkpoint size mismatch");
+    uint64_t sum;
+    memcpy(&sum, p + size - 8, 8);
+    if (sum != fnv1a64(p, (size_t)(size - 8)))
+        return fail(h, OPEN_CF_INVALID_ARG, "checkpoint checksum mismatch");
+    // the state belongs to a handle of the same model configuration
+    if (hd.k != h->k || hd.KP != h->KP || hd.precision != (int32_t)h->cfg.precision ||
+        hd.cholesky_fp64 != h->cfg.cholesky_fp64 || hd.weighted_lambda != h->cfg.weighted_lambda ||
+        hd.lambda != h->cfg.lambda || hd.esz != (int32_t)h->esz)
+        return fail(h, OPEN_CF_INVALID_ARG,
+                    "checkpoint of another configuration (k, precision, lambda or weighting)");
+    if (hd.n_cpu != (int32_t)h->cpu_caps.size() || hd.n_gpu != (int32_t)h->gpu_caps.size())
+        return fail(h, OPEN_CF_INVALID_ARG, "checkpoint of another cap grid");
+    p += sizeof(hd);
+    for (int i = 0; i < hd.n_cpu + hd.n_gpu; ++i) {
+        double c;
+        memcpy(&c, p, 8);
+        p += 8;
+        const double mine = i < hd.n_cpu ? h->cpu_caps[i] : h->gpu_caps[i - hd.n_cpu];
+        if (c != mine) return fail(h, OPEN_CF_INVALID_ARG, "checkpoint of another cap grid");
+    }
+    if ((hd.flags & ~(CKPT_V | CKPT_MLP | CKPT_STREAM)) ||
+        ((hd.flags & CKPT_STREAM) && !(hd.flags & CKPT_V)))
+        return fail(h, OPEN_CF_INVALID_ARG, "checkpoint sections inconsistent");
+    const int64_t n = hd.n, KP = h->KP, e = (int64_t)h->esz;
+    if ((hd.flags & CKPT_V) && (n <= 0 || n > CSC_MAX_N ||
+                                (!h->cpu_caps.empty() &&
+                                 n != (int64_t)h->cpu_caps.size() * (int64_t)h->gpu_caps.size())))
+        return fail(h, OPEN_CF_INVALID_ARG, "checkpoint V has a bad number of settings");
+    if ((hd.flags & CKPT_MLP) && (h->k != MLP_K || h->f64))
+        return fail(h, OPEN_CF_INVALID_ARG, "checkpoint holds a learned warm start this handle cannot run");
+    {   // the declared sections must account for every byte
+        const int64_t saved_n = h->n;
+        h->n = n;
+        const int64_t want = ckpt_bytes(h, hd.flags);
+        h->n = saved_n;
+        if (want != size) return fail(h, OPEN_CF_INVALID_ARG, "checkpoint sections inconsistent");
+    }
+    DeviceGuard g(h->device);
+    CK(h, cudaDeviceSynchronize());
+    auto h2d = [&](void *dst, int64_t bytes) -> cudaError_t {
+        cudaError_t r = cudaMemcpy(dst, p, (size_t)bytes, cudaMemcpyHostToDevice);
+        p += bytes;
+        return r;
+    };
+    if (hd.flags & CKPT_V) {
+        CK(h, ensure(h, h->V, e * n * KP));
+        CK(h, h2d(h->V.p, e * n * KP));
+        if (h->cfg.precision == OPEN_CF_BF16_GRAM) {
+            CK(h, ensure(h, h->Vb16, 4 * n * KP));
+            CK(h, launch_to_bf16_split((const float *)h->V.p, n, KP, h->Vb16.p, 0));
+        }
+        if (!h->cpu_caps.empty() && h->n != n) {
+            std::vector<float> cg(n);
+            const int ng = (int)h->gpu_caps.size();
+            for (int64_t j = 0; j < n; ++j)
+                cg[j] = (float)h->cpu_caps[j / ng] + (float)h->gpu_caps[j % ng];
+            CK(h, ensure(h, h->cg, sizeof(float) * n));
+            CK(h, cudaMemcpy(h->cg.p, cg.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+        }
+        h->n = n;
+        h->V_set = true;
+        h->stream_on = false;
+        h->v_epoch++;
+    }
+    if (hd.flags & CKPT_MLP) {
+        CK(h, ensure(h, h->mlp_th, 4 * MLP_P_INT));
+        CK(h, ensure(h, h->mlp_m1, 4 * MLP_P_INT));
+        CK(h, ensure(h, h->mlp_m2, 4 * MLP_P_INT));
+        CK(h, ensure(h, h->mlp_img, 2 * MLP_IMG_TOTAL));
+        CK(h, ensure(h, h->mlp_err, 16));
+        CK(h, ensure(h, h->mlp_t, 16));
+        CK(h, cudaMemset(h->mlp_err.p, 0, 16));
+        CK(h, h2d(h->mlp_th.p, 4 * MLP_P_INT));
+        CK(h, h2d(h->mlp_m1.p, 4 * MLP_P_INT));
+        CK(h, h2d(h->mlp_m2.p, 4 * MLP_P_INT));
+        CK(h, h2d(h->mlp_t.p, 16));
+        CK(h, launch_mlp_images((const float *)h->mlp_th.p, h->mlp_img.p, 0));
+        const int rc = mlp_caps_table(h);
+        if (rc) return rc;
+        h->mlp_ready = true;
+    }
+    if (hd.flags & CKPT_STREAM) {
+        CK(h, ensure(h, h->sg, e * n * KP * KP));
+        CK(h, ensure(h, h->sb, e * n * KP));
+        CK(h, ensure(h, h->sn, 8 * n));
+        CK(h, h2d(h->sg.p, e * n * KP * KP));
+        CK(h, h2d(h->sb.p, e * n * KP));
+        CK(h, h2d(h->sn.p, 8 * n));
+        h->stream_on = true;
+    }
+    CK(h, cudaDeviceSynchronize());
     return OPEN_CF_OK;
 }
 
