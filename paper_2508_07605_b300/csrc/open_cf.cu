@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "open_cf.h"
@@ -97,6 +99,14 @@ struct DeviceGuard {
         cudaGetDevice(&cur);
         if (prev >= 0 && cur != prev) cudaSetDevice(prev);
     }
+};
+
+// An NVTX range over each compute entry point (header-only NVTX: without an
+// attached tool the push and pop do nothing), so a timeline shows which call
+// enqueued which kernels.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
 };
 
 int fail(open_cf_t *h, int code, const char *fmt, ...) {
@@ -669,6 +679,7 @@ int open_cf_get_V(open_cf_t *h, void *V_out, void *stream) {
 int open_cf_fit_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
                     const int32_t *col, const void *val, void *U_out, int32_t *row_status,
                     int32_t *col_status, double *J_hist, void *stream) {
+    NvtxRange nvtx_("open_cf_fit_csr");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
@@ -686,6 +697,7 @@ int open_cf_fit_csr(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64
 
 int open_cf_fit_offline(open_cf_t *h, const void *P, int64_t m_off, int64_t n, int64_t ld,
                         void *U_out, double *J_hist, void *stream) {
+    NvtxRange nvtx_("open_cf_fit_offline");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (!P || m_off <= 0 || n <= 0 || ld < n)
@@ -736,6 +748,7 @@ __global__ void k_offset_copy(const int64_t *__restrict__ src, int64_t count, in
 int open_cf_complete_rows(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_t *row_ptr,
                           const int32_t *col, const void *val, void *U_out, int32_t *status,
                           int32_t joint, void *stream) {
+    NvtxRange nvtx_("open_cf_complete_rows");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     int rc = check_csr_args(h, m_new, nnz, row_ptr, col, val);
@@ -795,6 +808,7 @@ int open_cf_complete_rows_checked(open_cf_t *h, int64_t m_new, int64_t nnz,
                                   const int64_t *row_ptr, const int32_t *col, const float *val,
                                   float *U_out, int32_t *status, float *resid, int32_t refine,
                                   void *stream) {
+    NvtxRange nvtx_("open_cf_complete_rows_checked");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     int rc = check_csr_args(h, m_new, nnz, row_ptr, col, val);
@@ -821,6 +835,7 @@ int open_cf_complete_rows_checked(open_cf_t *h, int64_t m_new, int64_t nnz,
 int open_cf_normal_residual(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
                             const int32_t *col, const float *val, const float *U, float *resid,
                             void *stream) {
+    NvtxRange nvtx_("open_cf_normal_residual");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
@@ -934,6 +949,7 @@ extern "C" {
 
 int open_cf_stream_begin(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
                          const int32_t *col, const void *val, const void *U, void *stream) {
+    NvtxRange nvtx_("open_cf_stream_begin");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (h->cfg.precision == OPEN_CF_BF16_GRAM)
@@ -960,6 +976,7 @@ int open_cf_stream_begin(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *ro
 int open_cf_stream_ingest(open_cf_t *h, int64_t m_new, int64_t nnz, const int64_t *row_ptr,
                           const int32_t *col, const void *val, void *U_out, int32_t *status,
                           void *stream) {
+    NvtxRange nvtx_("open_cf_stream_ingest");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (!h->stream_on) return fail(h, OPEN_CF_NOT_FITTED, "call open_cf_stream_begin first");
@@ -1013,6 +1030,7 @@ int open_cf_stream_set_sums(open_cf_t *h, const void *G, const void *b, const in
 
 int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t *best,
                     float *saving, float gamma, int32_t baseline_setting, void *stream) {
+    NvtxRange nvtx_("open_cf_predict");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (!h->V_set) return fail(h, OPEN_CF_NOT_FITTED, "no V: fit or set V first");
@@ -1084,6 +1102,7 @@ int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int
                                  float gamma, int32_t baseline_setting, int32_t *best,
                                  float *saving, int32_t *status, float *resid,
                                  int64_t chunk_rows, void *stream) {
+    NvtxRange nvtx_("open_cf_complete_select_host");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (m < 0 || nnz < 0) return fail(h, OPEN_CF_INVALID_ARG, "negative m or nnz");
@@ -1225,6 +1244,7 @@ int open_cf_complete_select_host(open_cf_t *h, int64_t m, int64_t nnz, const int
 
 int open_cf_select(open_cf_t *h, const float *T, int64_t m, int64_t ld, int32_t *best,
                    float *saving, float gamma, int32_t baseline_setting, void *stream) {
+    NvtxRange nvtx_("open_cf_select");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (h->cpu_caps.empty()) return fail(h, OPEN_CF_INVALID_ARG, "selection needs a cap grid");
@@ -1252,6 +1272,7 @@ int open_cf_select(open_cf_t *h, const float *T, int64_t m, int64_t ld, int32_t 
 int open_cf_objective(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
                       const int32_t *col, const void *val, const void *U, double *J_out,
                       float *row_rmse, void *stream) {
+    NvtxRange nvtx_("open_cf_objective");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
@@ -1280,6 +1301,7 @@ int open_cf_objective(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
 int open_cf_csr_to_csc(open_cf_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
                        const int32_t *col, const void *val, int64_t *col_ptr, int32_t *row_idx,
                        void *cval, void *stream) {
+    NvtxRange nvtx_("open_cf_csr_to_csc");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     int rc = check_csr_args(h, m, nnz, row_ptr, col, val);
@@ -1333,6 +1355,7 @@ int open_cf_batched_fit(open_cf_t *h, int64_t P, const int64_t *m_host, const in
                         const int32_t *k_host, const int64_t *nnz_host, int64_t nnz,
                         const int64_t *row_ptr, const int32_t *col, const float *val,
                         float *V_inout, float *U_out, void *stream) {
+    NvtxRange nvtx_("open_cf_batched_fit");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (h->cfg.precision != OPEN_CF_FP32)
@@ -1360,6 +1383,7 @@ int open_cf_batched_tune(open_cf_t *h, int64_t P, const int64_t *m_host, const i
                          const int32_t *k_host, const int64_t *nnz_host, int64_t nnz,
                          const int64_t *row_ptr, const int32_t *col, const float *val,
                          float *V_scratch, int32_t *W_out_host, void *stream) {
+    NvtxRange nvtx_("open_cf_batched_tune");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (h->cfg.precision != OPEN_CF_FP32)
@@ -1511,6 +1535,7 @@ int open_cf_mlp_get_params(open_cf_t *h, float *params_out, void *stream) {
 int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *row_ptr,
                            const int32_t *col, const float *val, const float *U_target, float lr,
                            double *loss_out, float *grads_out, void *stream) {
+    NvtxRange nvtx_("open_cf_mlp_train_step");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     int rc = mlp_check(h);
@@ -1571,6 +1596,7 @@ int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *
 int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_ptr,
                       const int32_t *col, const float *val, float *U_out, int32_t *status,
                       float *row_rmse, void *stream) {
+    NvtxRange nvtx_("open_cf_mlp_infer");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     int rc = mlp_check(h);
@@ -1664,6 +1690,7 @@ static int64_t ckpt_bytes(const open_cf_t *h, uint32_t flags) {
 }
 
 int open_cf_save(open_cf_t *h, void *buf, int64_t cap, int64_t *size_out) {
+    NvtxRange nvtx_("open_cf_save");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     const uint32_t flags = (h->V_set ? CKPT_V : 0u) | (h->mlp_ready ? CKPT_MLP : 0u) |
@@ -1714,6 +1741,7 @@ int open_cf_save(open_cf_t *h, void *buf, int64_t cap, int64_t *size_out) {
 }
 
 int open_cf_load(open_cf_t *h, const void *buf, int64_t size) {
+    NvtxRange nvtx_("open_cf_load");
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
     if (!buf || size < (int64_t)sizeof(CkptHeader) + 8)
