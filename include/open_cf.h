@@ -74,6 +74,8 @@ extern "C" {
 #define OPEN_CF_ROW_BAD_INPUT 4      /* row_ptr / col out of range; u = 0 */
 
 #define OPEN_CF_MAX_K 32
+/* Default bound of a tensor-core pipeline wait, in polls of mbarrier.try_wait. */
+#define OPEN_CF_WAIT_POLLS_DEFAULT (1 << 22)
 
 typedef struct open_cf open_cf_t; /* opaque: owns V, workspaces, CUDA graphs */
 
@@ -116,6 +118,31 @@ void open_cf_destroy(open_cf_t *h);
 /* Text of the last error on this handle ("" if none).  Valid until the next
  * call on the handle. */
 const char *open_cf_last_error(const open_cf_t *h);
+
+/* Watchdog of the tensor-core pipelines (reconstruction/selection, the
+ * learned warm start's inference and training).  Every wait of those kernels
+ * on an mbarrier (a bulk copy landing, tensor-core products finishing, a
+ * buffer being released) is bounded; a wait that runs out sets a flag on the
+ * device, the kernel stops issuing work, waits (again with a bound) for the
+ * copies and products it already issued, frees its tensor memory and returns,
+ * so the context stays usable.  What the flag means for the outputs:
+ *   - open_cf_predict (tensor-core path): the rows of the CTAs that gave up
+ *     hold unspecified values;
+ *   - open_cf_mlp_infer: the rows of the tiles that gave up are solved by the
+ *     ALS fold-in instead (status OPEN_CF_ROW_FALLBACK_USED), so U is correct;
+ *   - open_cf_mlp_train_step: the step changes no parameter and reports NaN;
+ *     while the flag is set every later step does the same.
+ *
+ * open_cf_set_wait_limit: the bound of those waits, in polls (0: a wait gives
+ * up without polling, which makes every launch take its timeout path; -1: the
+ * default, OPEN_CF_WAIT_POLLS_DEFAULT).  Host state only; applies to launches
+ * enqueued after the call.  INVALID_ARG for polls < -1.
+ *
+ * open_cf_check: synchronises the device, then returns OPEN_CF_TIMEOUT (and
+ * clears the flags; the text of open_cf_last_error names the kernels) if a
+ * wait gave up since the last check, else OPEN_CF_OK. */
+int open_cf_set_wait_limit(open_cf_t *h, int32_t polls);
+int open_cf_check(open_cf_t *h);
 
 /* Set the handle's V (n x k real): the initial V of the next fit (the random
  * draw of ALS's initialisation is passed in), or the fixed V of a fold-in.

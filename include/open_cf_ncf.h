@@ -105,6 +105,10 @@ int open_cf_ncf_predict(open_cf_ncf_t *h, float *T_out, float gamma, int32_t bas
  * wait (its tiles are then NaN), else OPEN_CF_OK. */
 int open_cf_ncf_skipped(open_cf_ncf_t *h, int64_t *count_host);
 int open_cf_ncf_check(open_cf_ncf_t *h);
+/* Bound of the completion kernel's tensor-core waits, in polls (0: every wait
+ * gives up at once; -1: OPEN_CF_WAIT_POLLS_DEFAULT), as open_cf_set_wait_limit
+ * does for the ALS handle.  Host state only.  INVALID_ARG for polls < -1. */
+int open_cf_ncf_set_wait_limit(open_cf_ncf_t *h, int32_t polls);
 
 /* ------------------------------------------------------------------------
  * Offline performance predictor (Sec. "Performance Prediction Model"): an MLP

@@ -48,6 +48,8 @@ _SIGNATURES = {
     "open_cf_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(_V)]),
     "open_cf_destroy": (None, [_V]),
     "open_cf_last_error": (ctypes.c_char_p, [_V]),
+    "open_cf_set_wait_limit": (ctypes.c_int, [_V, _I32]),
+    "open_cf_check": (ctypes.c_int, [_V]),
     "open_cf_set_V": (ctypes.c_int, [_V, _V, _I64, _V]),
     "open_cf_get_V": (ctypes.c_int, [_V, _V, _V]),
     "open_cf_fit_offline": (ctypes.c_int, [_V, _V, _I64, _I64, _I64, _V, _V, _V]),
@@ -92,6 +94,7 @@ _SIGNATURES = {
     "open_cf_ncf_predict": (ctypes.c_int, [_V, _V, _F, _I32, _V, _V, _V]),
     "open_cf_ncf_skipped": (ctypes.c_int, [_V, ctypes.POINTER(_I64)]),
     "open_cf_ncf_check": (ctypes.c_int, [_V]),
+    "open_cf_ncf_set_wait_limit": (ctypes.c_int, [_V, _I32]),
     "open_cf_pred_create": (ctypes.c_int, [_I32, _I32, ctypes.c_int, ctypes.POINTER(_V)]),
     "open_cf_pred_destroy": (None, [_V]),
     "open_cf_pred_last_error": (ctypes.c_char_p, [_V]),
@@ -226,6 +229,17 @@ class OpenCF:
     # -- API ---------------------------------------------------------------
     def last_error(self) -> str:
         return lib().open_cf_last_error(self._h).decode()
+
+    def set_wait_limit(self, polls: int = -1):
+        """Bound of the tensor-core pipelines' waits in polls (0: give up at once,
+        -1: the default)."""
+        self._check(lib().open_cf_set_wait_limit(self._h, int(polls)))
+
+    def check(self):
+        """Raise OpenCFError(TIMEOUT) if a tensor-core pipeline wait gave up since
+        the last check (synchronises the device; clears the flags)."""
+        with torch.cuda.device(self.device):
+            self._check(lib().open_cf_check(self._h))
 
     def set_V(self, V):
         self._real(V, "V")
@@ -621,6 +635,9 @@ class NCF:
     def check(self):
         with torch.cuda.device(self.device):
             self._check(lib().open_cf_ncf_check(self._h))
+
+    def set_wait_limit(self, polls: int = -1):
+        self._check(lib().open_cf_ncf_set_wait_limit(self._h, int(polls)))
 
 
 class Predictor:

@@ -154,6 +154,7 @@ struct MlpTrainArgs {
     const float *val;
     const float *ccap, *gcap;         // normalised CPU caps [n_cpu], GPU caps [n_gpu]
     int32_t n_gpu;                    // setting j = c * n_gpu + g
+    int wait_limit;                   // polls of each pipeline wait before it gives up
     int64_t n;
     const void *img;                  // BF16 weight images
     const float *b1, *b2, *b3;        // FP32 biases
@@ -179,7 +180,7 @@ struct MlpReduceArgs {
     const float *part;                // slots of the training kernel
     int ctas;
     float *th, *m1, *m2;              // FP32 masters and moments (MLP_P_INT)
-    const AdamState *adam;            // NULL: gradient only
+    AdamState *adam;                  // NULL: gradient only (t moved back if the step failed)
     void *img;                        // BF16 images refreshed after the update
     float *grads_out;                 // gradient-only mode: external layout
     double *loss;                     // may be NULL
@@ -196,6 +197,7 @@ struct MlpTcArgs {
     const float *val;
     const float *ccap, *gcap;     // normalised CPU caps [n_cpu], GPU caps [n_gpu]
     int32_t n_gpu;                // setting j = c * n_gpu + g
+    int wait_limit;               // polls of each pipeline wait before it gives up
     int64_t n;
     const void *img;              // BF16 weight images
     const float *b1, *b2, *b3;
@@ -221,6 +223,9 @@ struct PredictTcArgs {
     const float *U;       // m rows of k floats, stride ldu
     int64_t ldu;
     int k;
+    int wait_limit;       // polls of each pipeline wait before it gives up (fills the
+                          // padding: the struct stays at 128 bytes, the size it was
+                          // timed at)
     const void *Vimg;
     const float *cg;      // n: c_j + g_j
     const float *cg_pad;  // the same, zero-padded to whole chunks of 256 (used when n > PREDICT_TC_CG_MAX)
@@ -359,6 +364,7 @@ struct NcfPredArgs {
     const float *b2, *w3, *b3;
     float *T;                       // [m][n]
     int *err;                       // set to 1 if a tensor-core wait ran out
+    int wait_limit;                 // polls of each pipeline wait before it gives up
 };
 cudaError_t prepare_ncf_train();
 cudaError_t launch_ncf_train_step(const NcfTrainArgs &t, const NcfAdamArgs &u, cudaStream_t st);

@@ -73,7 +73,8 @@ constexpr int RED_PARAMS = 64;   // parameters per CTA of the reduction; 4 slot 
 // refreshed, or the gradient written out in the external layout.  The step
 // counter was advanced by the training kernel; the step size was set ahead
 // of the step.  A step whose training kernel gave up (err[1]) changes
-// nothing and reports NaN (loss and, in gradient mode, the gradient).
+// nothing (the step counter is moved back) and reports NaN (loss and, in
+// gradient mode, the gradient).
 //
 // Fixed summation order: warp w of a CTA takes slot group g = w / 2 and
 // parameters 32 (w % 2) + lane; it adds the slots c = g, g + 4, g + 8, ...
@@ -92,6 +93,9 @@ __global__ void __launch_bounds__(256) k_mlp_reduce_adam(MlpReduceArgs a) {
         corr[0] = 1.f - exp2f(tt * -0.15200309344504997f);    // log2(0.9)
         corr[1] = 1.f - exp2f(tt * -0.0014434168696687186f);  // log2(0.999)
         corr[2] = a.adam->lr;
+        // a step that did not happen leaves the step counter as it was (the
+        // other blocks' copies of t are not used when the step failed)
+        if (failed && blockIdx.x == 0) a.adam->t -= 1;
     }
     if (blockIdx.x == 0 && warp == 0 && a.loss) {   // loss: warp 0, fixed order
         double s = 0.0;

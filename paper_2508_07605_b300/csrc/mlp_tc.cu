@@ -195,15 +195,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // bar_st completes alternately for W1 (parity 0) and W3 (parity 1)
-    bool st_pending = false;
+    // bar_st completes alternately for W1 (parity 0) and W3 (parity 1); the
+    // copies not yet waited for are drained if a wait runs out
+    bool st_pending = false, w2_pending = false;
+    uint32_t st_par = 0;   // parity of the pending bar_st phase
     if (tid == 0 && (int64_t)blockIdx.x < tiles) {
         mbar_expect_tx(bar_w2, BYTES_W2);
         for (uint32_t c = 0; c < BYTES_W2; c += 32768)
             bulk_g2s(s0 + OFF_W2 + c, img + 2 * MLP_IMG_W2F + c, 32768, bar_w2);
         mbar_expect_tx(bar_st, BYTES_W1);
         bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W1, BYTES_W1, bar_st);
-        st_pending = true;
+        st_pending = w2_pending = true;
     }
     const uint32_t id256 = idesc_bf16(TM, 256), id32 = idesc_bf16(TM, MLP_K_OUT);
     uint32_t mma_count = 0;   // completions of bar_mma so far (parity = count & 1)
@@ -221,8 +223,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
             // ---- layer 1: ACT (128 x 64) x W1 (256 x 64)^T -> TMEM [0, 256)
             bool okw = true;
             if (tid == 0) {
-                if (first) okw = mbar_wait(bar_w2, 0);
-                okw = okw && mbar_wait(bar_st, 0);
+                if (first) {
+                    okw = mbar_wait(bar_w2, 0, a.wait_limit);
+                    w2_pending = !okw;
+                }
+                okw = okw && mbar_wait(bar_st, 0, a.wait_limit);
                 st_pending = !okw;
                 tc_fence_after();
                 if (okw)
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
                 tc_commit(bar_mma);
             }
             first = false;
-            bool okm = mbar_wait(bar_mma, mma_count & 1);
+            bool okm = mbar_wait(bar_mma, mma_count & 1, a.wait_limit);
             ++mma_count;
             bad = __syncthreads_or(!okm || !okw);
         }
@@ -242,6 +247,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
                 mbar_expect_tx(bar_st, BYTES_W3);
                 bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W3F, BYTES_W3, bar_st);
                 st_pending = true;
+                st_par = 1;
             }
             epi_hidden(tmem, 0, q, lane, 64 * cq, bias_s, sm + OFF_ACT);
             fence_async_smem();
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
                 tc_commit(bar_mma);
             }
             if (warp == 1 && has_next) prefetch_tile(a, row0 + (int64_t)gridDim.x * TM, lane);
-            const bool okm = mbar_wait(bar_mma, mma_count & 1);
+            const bool okm = mbar_wait(bar_mma, mma_count & 1, a.wait_limit);
             ++mma_count;
             bad = __syncthreads_or(!okm);
         }
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
             // ---- layer 3: ACT (128 x 256) x W3 (32 x 256)^T -> TMEM [0, 32)
             bool okw = true;
             if (tid == 0) {
-                okw = mbar_wait(bar_st, 1);
+                okw = mbar_wait(bar_st, 1, a.wait_limit);
                 st_pending = !okw;
                 tc_fence_after();
                 if (okw)
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
                                sdesc(s0 + OFF_STAGE + s * 256, 128, MLP_H * 16), id32, s > 0);
                 tc_commit(bar_mma);
             }
-            const bool okm = mbar_wait(bar_mma, mma_count & 1);
+            const bool okm = mbar_wait(bar_mma, mma_count & 1, a.wait_limit);
             ++mma_count;
             bad = __syncthreads_or(!okm || !okw);
         }
@@ -289,6 +295,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
                 mbar_expect_tx(bar_st, BYTES_W1);
                 bulk_g2s(s0 + OFF_STAGE, img + 2 * MLP_IMG_W1, BYTES_W1, bar_st);
                 st_pending = true;
+                st_par = 0;
             }
             // u = acc + b3: columns [8 cq, 8 cq + 8) of this warp's rows -> Y and
             // shared memory (ACT is free: layer 3 is done)
@@ -331,11 +338,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_forward_tc(MlpTcArgs a) {
     }
     if (bad && tid == 0) {
         atomicExch(a.err, 1);
-        // drain: a weight copy may still be in flight (bounded)
-        if (st_pending) {
-            mbar_wait(bar_st, 0);
-            mbar_wait(bar_st, 1);
-        }
+        // drain (bounded): the weight copies not yet waited for, and the products
+        // of the last commit (which covers every earlier one; its phase is the
+        // barrier's latest, as each earlier one was waited for)
+        if (w2_pending) mbar_wait(bar_w2, 0);
+        if (st_pending) mbar_wait(bar_st, st_par);
+        if (mma_count > 0) mbar_wait(bar_mma, (mma_count - 1) & 1);
     }
     tc_fence_before();
     __syncthreads();

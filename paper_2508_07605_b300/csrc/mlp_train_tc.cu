@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc(MlpTrainArgs a) {
     const int64_t cluster = blockIdx.x >> 1;
     const uint32_t bar_full = s0 + OFF_BAR, bar_free = bar_full + 8 * NSLOT;
     const uint32_t bar_a = bar_free + 8 * NSLOT, bar_b = bar_a + 8;
+    const uint32_t bar_drain = bar_b + 16;   // after the TMEM slot
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + OFF_BAR + 8 * (2 * NSLOT + 2));
     float *G_s = reinterpret_cast<float *>(sm + OFF_G);
     float *bias_s = reinterpret_cast<float *>(sm + OFF_BIAS);   // b1 [0,256) b2 [256,512) b3
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc(MlpTrainArgs a) {
         }
         mbar_init(bar_a, 1);
         mbar_init(bar_b, 1);
+        mbar_init(bar_drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         if (blockIdx.x == 0 && a.adam) a.adam->t += 1;   // the reduction runs step t + 1
     }
@@ -249,7 +251,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc(MlpTrainArgs a) {
     uint32_t issued = 0, arrived = 0, released = 0, commits_b = 0;
     auto issue = [&](uint32_t g) -> bool {   // after the chunk four before it left the slot
         const uint32_t s = g % NSLOT;
-        if (g >= NSLOT && !mbar_wait(bar_free + 8 * s, ((g - NSLOT) / NSLOT) & 1)) return false;
+        if (g >= NSLOT && !mbar_wait(bar_free + 8 * s, ((g - NSLOT) / NSLOT) & 1, a.wait_limit))
+            return false;
         int64_t elem;
         uint32_t bytes;
         chunk_src((int)(g % CHUNKS), c, elem, bytes);
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc(MlpTrainArgs a) {
         return true;
     };
     auto ready = [&](uint32_t g) -> bool {
-        const bool ok = mbar_wait(bar_full + 8 * (g % NSLOT), (g / NSLOT) & 1);
+        const bool ok = mbar_wait(bar_full + 8 * (g % NSLOT), (g / NSLOT) & 1, a.wait_limit);
         if (ok) arrived = g + 1;
         tc_fence_after();
         return ok;
@@ -306,13 +309,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc(MlpTrainArgs a) {
     uint32_t na = 0, nb = 0;   // completions of bar_a / bar_b waited for by the epilogue warps
     bool bad = false;
     auto wait_a = [&]() -> bool {
-        const bool ok = mbar_wait(bar_a, na & 1);
+        const bool ok = mbar_wait(bar_a, na & 1, a.wait_limit);
         ++na;
         tc_fence_after();
         return ok;
     };
     auto wait_b = [&]() -> bool {
-        const bool ok = mbar_wait(bar_b, nb & 1);
+        const bool ok = mbar_wait(bar_b, nb & 1, a.wait_limit);
         ++nb;
         tc_fence_after();
         return ok;
@@ -561,8 +564,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc(MlpTrainArgs a) {
         atomicExch(a.err + 1, 1);
         for (uint32_t g = arrived; g < issued; ++g)   // copies still in flight (bounded)
             mbar_wait(bar_full + 8 * (g % NSLOT), (g / NSLOT) & 1);
-        tc_commit(bar_b);   // every product issued so far (bounded)
-        mbar_wait(bar_b, commits_b & 1);
+        // every product issued so far: a commit to a barrier of its own, whose
+        // first phase no earlier wait can alias (bounded)
+        tc_commit(bar_drain);
+        mbar_wait(bar_drain, 0);
     }
     // neither CTA leaves while its partner may still write into its shared memory
     cluster_barrier();

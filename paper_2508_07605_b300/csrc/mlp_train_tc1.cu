@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc1(MlpTrainArgs a) {
     uint32_t issued = 0, arrived = 0;
     auto issue = [&](uint32_t g) -> bool {   // after the chunk two before it left the slot
         const uint32_t s = g & 1;
-        if (g >= 2 && !mbar_wait(bar_free + 8 * s, ((g - 2) >> 1) & 1)) return false;
+        if (g >= 2 && !mbar_wait(bar_free + 8 * s, ((g - 2) >> 1) & 1, a.wait_limit)) return false;
         int64_t elem;
         uint32_t bytes;
         chunk_src((int)(g % CHUNKS), elem, bytes);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc1(MlpTrainArgs a) {
         return true;
     };
     auto ready = [&](uint32_t g) -> bool {
-        const bool ok = mbar_wait(bar_full + 8 * (g & 1), (g >> 1) & 1);
+        const bool ok = mbar_wait(bar_full + 8 * (g & 1), (g >> 1) & 1, a.wait_limit);
         if (ok) arrived = g + 1;
         tc_fence_after();
         return ok;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_mlp_train_tc1(MlpTrainArgs a) {
             ok = body();
             tc_commit(bar_mma);
         }
-        const bool okm = mbar_wait(bar_mma, mma_count & 1);
+        const bool okm = mbar_wait(bar_mma, mma_count & 1, a.wait_limit);
         ++mma_count;
         const bool fail = __syncthreads_or(!(ok && okm)) != 0;
         tc_fence_after();

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(NP_THREADS, 2) k_ncf_predict_tc(NcfPredArgs a)
             if (tid == 0) {
                 tc_fence_after();
                 if (k == 0) {
-                    ok = mbar_wait(bar_w2, 0);
+                    ok = mbar_wait(bar_w2, 0, a.wait_limit);
                     w2_pending = !ok;
                 }
             }
@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(NP_THREADS, 2) k_ncf_predict_tc(NcfPredArgs a)
             int64_t i, sb;
             w.tile(kp, i, sb);
             const int64_t j0 = sb * NP_TM;
-            const bool ok = mbar_wait(bar_mma0 + 8 * (uint32_t)(kp & 1), (uint32_t)((kp >> 1) & 1));
+            const bool ok = mbar_wait(bar_mma0 + 8 * (uint32_t)(kp & 1), (uint32_t)((kp >> 1) & 1),
+                                     a.wait_limit);
             tc_fence_after();
             const int q = warp & 3, cq = warp >> 2;   // TMEM lane quarter, column half
             uint32_t v[32];

@@ -49,6 +49,7 @@ struct open_cf_ncf {
     NBuf theta, grad, m1, m2, bf, adam, ctl, loss1;
     NBuf part, lpart;
     NBuf A, S, w2img, T, cg, err;
+    int wait_limit = OPEN_CF_WAIT_POLLS_DEFAULT;   // polls of a tensor-core pipeline wait
     cudaStream_t cap_stream = nullptr;
     std::vector<StepGraph> graphs;
     std::string msg;
@@ -391,7 +392,7 @@ int open_cf_ncf_predict(open_cf_ncf_t *h, float *T_out, float gamma, int32_t bas
     NCK(h, launch_ncf_first_layer(h->m, Ea, th, th + NCF_OFF_B1, F(h->A), st));
     NCK(h, launch_ncf_first_layer(h->n, Es, th + NCF_D * NCF_H1, nullptr, F(h->S), st));
     NcfPredArgs a{h->m, h->n, F(h->A), F(h->S), h->w2img.p, th + NCF_OFF_B2, th + NCF_OFF_W3,
-                  th + NCF_OFF_B3, T, (int *)h->err.p};
+                  th + NCF_OFF_B3, T, (int *)h->err.p, h->wait_limit};
     NCK(h, launch_ncf_predict_tc(a, h->num_sms, st));
     if (sel) {
         const int ng = (int)h->gpu.size();
@@ -408,6 +409,14 @@ int open_cf_ncf_skipped(open_cf_ncf_t *h, int64_t *count_host) {
     NCK(h, cudaDeviceSynchronize());
     NCK(h, cudaMemcpy(&c, h->ctl.p, sizeof(NcfCtl), cudaMemcpyDeviceToHost));
     *count_host = (int64_t)c.skipped;
+    return OPEN_CF_OK;
+}
+
+int open_cf_ncf_set_wait_limit(open_cf_ncf_t *h, int32_t polls) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->msg.clear();
+    if (polls < -1) return nfail(h, OPEN_CF_INVALID_ARG, "polls must be >= -1");
+    h->wait_limit = polls < 0 ? OPEN_CF_WAIT_POLLS_DEFAULT : polls;
     return OPEN_CF_OK;
 }
 

@@ -68,6 +68,7 @@ struct open_cf {
     // G = V^T V in the step scratch is current while mlp_g_epoch == v_epoch
     uint64_t v_epoch = 1, mlp_g_epoch = 0;
     Buf vimg, pt_err;                 // split BF16 operand images of V, timeout flag (predict)
+    int wait_limit = OPEN_CF_WAIT_POLLS_DEFAULT;   // polls of a tensor-core pipeline wait
     uint64_t vimg_epoch = 0;          // the images are of V while vimg_epoch == v_epoch
     void *vimg_at = nullptr;          // ... and they are still at this address
     Buf ccount;                       // observations per column (weighted-lambda objective)
@@ -625,6 +626,32 @@ void open_cf_destroy(open_cf_t *h) {
 
 const char *open_cf_last_error(const open_cf_t *h) { return h ? h->err.c_str() : ""; }
 
+int open_cf_set_wait_limit(open_cf_t *h, int32_t polls) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    if (polls < -1) return fail(h, OPEN_CF_INVALID_ARG, "polls must be >= -1");
+    h->wait_limit = polls < 0 ? OPEN_CF_WAIT_POLLS_DEFAULT : polls;
+    return OPEN_CF_OK;
+}
+
+int open_cf_check(open_cf_t *h) {
+    if (!h) return OPEN_CF_INVALID_ARG;
+    h->err.clear();
+    DeviceGuard g(h->device);
+    CK(h, cudaDeviceSynchronize());
+    int flags[8] = {};
+    if (h->pt_err.p) CK(h, cudaMemcpy(flags, h->pt_err.p, 16, cudaMemcpyDeviceToHost));
+    if (h->mlp_err.p) CK(h, cudaMemcpy(flags + 4, h->mlp_err.p, 16, cudaMemcpyDeviceToHost));
+    if (!(flags[0] | flags[4] | flags[5])) return OPEN_CF_OK;
+    if (h->pt_err.p) CK(h, cudaMemset(h->pt_err.p, 0, 16));
+    if (h->mlp_err.p) CK(h, cudaMemset(h->mlp_err.p, 0, 16));
+    std::string what;
+    if (flags[0]) what += " reconstruction";
+    if (flags[4]) what += " learned-inference";
+    if (flags[5]) what += " learned-training";
+    return fail(h, OPEN_CF_TIMEOUT, "a tensor-core pipeline wait gave up in:%s", what.c_str());
+}
+
 int open_cf_set_V(open_cf_t *h, const void *V, int64_t n, void *stream) {
     if (!h) return OPEN_CF_INVALID_ARG;
     h->err.clear();
@@ -1075,6 +1102,7 @@ int open_cf_predict(open_cf_t *h, const void *U, int64_t m, void *T_out, int32_t
         a.T = (float *)T_out;
         a.t_vec = T_out && (reinterpret_cast<uintptr_t>(T_out) % 16 == 0) && (h->n % 4 == 0);
         a.best = best; a.saving = saving; a.err = (int *)h->pt_err.p;
+        a.wait_limit = h->wait_limit;
         CK(h, launch_predict_select_tc(a, h->num_sms, st));
     } else {
         PredictArgs<float> a{m, h->n, h->KP, h->k, as<float>(U), h->k, (float *)h->V.p,
@@ -1566,7 +1594,8 @@ int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *
         h->mlp_g_epoch = h->v_epoch;
     }
     std::vector<int64_t> key = {3, B, nnz, (int64_t)row_ptr, (int64_t)col, (int64_t)val,
-                                (int64_t)U_target, (int64_t)loss_out, (int64_t)grads_out};
+                                (int64_t)U_target, (int64_t)loss_out, (int64_t)grads_out,
+                                h->wait_limit};
     if (!grads_out) CK(h, launch_adam_set_lr(h->mlp_t.p, lr, S(stream)));
     return run_graph(h, key, S(stream), [&](cudaStream_t st) -> cudaError_t {
         float *th = (float *)h->mlp_th.p;
@@ -1581,12 +1610,13 @@ int open_cf_mlp_train_step(open_cf_t *h, int64_t B, int64_t nnz, const int64_t *
         ta.T = U_target; ta.G = Gfin; ta.scale = 2.0f / (float)B; ta.part = part;
         ta.adam = grads_out ? nullptr : (AdamState *)h->mlp_t.p;
         ta.err = (int *)h->mlp_err.p;
+        ta.wait_limit = h->wait_limit;
         cudaError_t e = launch_mlp_train_tc(ta, h->num_sms, false, st);
         if (e != cudaSuccess) return e;
         MlpReduceArgs ra{};
         ra.part = part; ra.ctas = slots;
         ra.th = th; ra.m1 = (float *)h->mlp_m1.p; ra.m2 = (float *)h->mlp_m2.p;
-        ra.adam = grads_out ? nullptr : (const AdamState *)h->mlp_t.p;
+        ra.adam = grads_out ? nullptr : (AdamState *)h->mlp_t.p;
         ra.img = h->mlp_img.p; ra.grads_out = grads_out; ra.loss = loss_out; ra.B = B;
         ra.err = (const int *)h->mlp_err.p;
         return launch_mlp_reduce_adam(ra, st);
@@ -1621,7 +1651,7 @@ int open_cf_mlp_infer(open_cf_t *h, int64_t m, int64_t nnz, const int64_t *row_p
     ta.img = h->mlp_img.p;
     const float *th = (const float *)h->mlp_th.p;
     ta.b1 = th + MLP_OFF_B1; ta.b2 = th + MLP_OFF_B2; ta.b3 = th + MLP_OFF_B3;
-    ta.Y = U_out; ta.err = (int *)h->mlp_err.p;
+    ta.Y = U_out; ta.err = (int *)h->mlp_err.p; ta.wait_limit = h->wait_limit;
     // the kernel also evaluates each row's observed-entry RMSE and lists the
     // rows above the threshold; those are re-solved by the ridge fold-in
     int64_t *cnt = (int64_t *)h->flag.p;

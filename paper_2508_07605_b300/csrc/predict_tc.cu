@@ -23,8 +23,12 @@
 // Accumulator j of chunk g is reused by chunk g + 2, so the tensor cores fill
 // one accumulator while the epilogue drains the other.
 //
-// Every mbarrier wait is bounded; a wait that runs out sets *err and the
-// thread stops waiting (its results are then unspecified; *err says so).
+// Every mbarrier wait is bounded (a.wait_limit polls); a wait that runs out
+// sets *err, the thread stops waiting and the producer and MMA warps stop
+// issuing (the CTA's results are then unspecified; *err says so).  Before the
+// CTA frees its TMEM and exits, the producer waits for its last copy into each
+// buffer and the MMA warp for its last commit, again with a bound, so that no
+// copy or product is still in flight.
 #include "alg2.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t s0 = smem_u32(sm);
     const uint32_t bar = s0 + OFF_BAR;
-    // full[2] @0, empty[2] @16, afull[2] @32, aempty[2] @48, TMEM slot @64
+    // full[2] @0, empty[2] @16, afull[2] @32, aempty[2] @48, TMEM slot @64, drain @72
     auto full = [&](int b) { return bar + 8 * b; };
     auto empty = [&](int b) { return bar + 16 + 8 * b; };
     auto afull = [&](int b) { return bar + 32 + 8 * b; };
@@ -112,6 +116,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
             mbar_init(afull(b), 1);
             mbar_init(aempty(b), NEPI);
         }
+        mbar_init(bar + 72, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (cg_smem && a.select)   // padded with +inf to whole chunks
@@ -127,46 +132,65 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
     if (warp == PRODUCER) {
         if (lane == 0) {
             const unsigned char *img = reinterpret_cast<const unsigned char *>(a.Vimg);
-            int64_t g = 0;
-            for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x)
+            int64_t g = 0;   // copies issued
+            for (int64_t tile = blockIdx.x; tile < tiles && !bad; tile += gridDim.x)
                 for (int s = 0; s < nch; ++s, ++g) {
                     const int vb = (int)(g & 1);
                     const uint32_t ph = (uint32_t)((g >> 1) & 1);
-                    if (!bad && !mbar_wait(empty(vb), ph ^ 1u)) bad = true;
+                    if (!mbar_wait(empty(vb), ph ^ 1u, a.wait_limit)) {
+                        bad = true;
+                        break;
+                    }
                     mbar_expect_tx(full(vb), CHUNK_BYTES);
                     bulk_g2s(s0 + OFF_VB + vb * CHUNK_BYTES,
                              img + (int64_t)chunk_at(s, cb) * CHUNK_BYTES, CHUNK_BYTES, full(vb));
                 }
+            // drain: no copy may land after the CTA has gone; the last two copies
+            // (one per buffer) are the only ones that can be in flight (a no-op when
+            // the MMA warp consumed them all)
+            for (int64_t x = g >= 2 ? g - 2 : 0; x < g; ++x)
+                mbar_wait(full((int)(x & 1)), (uint32_t)((x >> 1) & 1));
         }
     } else if (warp == ISSUER) {
         const uint32_t idesc = idesc_bf16(TM, CN);
-        int64_t g = 0;
+        int64_t g = 0, last = -1;   // the last chunk whose products were committed
         for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
             named_sync(BAR_TILE, (NEPI + 1) * 32);   // this tile's U images are written
             for (int s = 0; s < nch; ++s, ++g) {
                 const int vb = (int)(g & 1), ab = (int)(g & 1);
                 const uint32_t ph = (uint32_t)((g >> 1) & 1);
                 if (lane == 0) {
-                    if (!bad && !mbar_wait(full(vb), ph)) bad = true;
-                    if (!bad && !mbar_wait(aempty(ab), ph ^ 1u)) bad = true;
-                    tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(ab * CN);
-                    const uint32_t vh = s0 + OFF_VB + vb * CHUNK_BYTES, vl = vh + HALF_BYTES;
+                    // once a wait gave up, nothing more is issued (the loops still run
+                    // for the tile barrier the epilogue warps take part in)
+                    if (!bad && !mbar_wait(full(vb), ph, a.wait_limit)) bad = true;
+                    if (!bad && !mbar_wait(aempty(ab), ph ^ 1u, a.wait_limit)) bad = true;
+                    if (!bad) {
+                        tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(ab * CN);
+                        const uint32_t vh = s0 + OFF_VB + vb * CHUNK_BYTES, vl = vh + HALF_BYTES;
 #pragma unroll
-                    for (int ks = 0; ks < KPT / 16; ++ks) {
-                        const uint64_t ah = sdesc(s0 + OFF_UH + ks * 256, 128, KPT * 16);
-                        const uint64_t al = sdesc(s0 + OFF_UL + ks * 256, 128, KPT * 16);
-                        const uint64_t bh = sdesc(vh + ks * 256, 128, KPT * 16);
-                        const uint64_t bl = sdesc(vl + ks * 256, 128, KPT * 16);
-                        tc_mma(d, ah, bh, idesc, ks > 0);
-                        tc_mma(d, ah, bl, idesc, 1);
-                        tc_mma(d, al, bh, idesc, 1);
+                        for (int ks = 0; ks < KPT / 16; ++ks) {
+                            const uint64_t ah = sdesc(s0 + OFF_UH + ks * 256, 128, KPT * 16);
+                            const uint64_t al = sdesc(s0 + OFF_UL + ks * 256, 128, KPT * 16);
+                            const uint64_t bh = sdesc(vh + ks * 256, 128, KPT * 16);
+                            const uint64_t bl = sdesc(vl + ks * 256, 128, KPT * 16);
+                            tc_mma(d, ah, bh, idesc, ks > 0);
+                            tc_mma(d, ah, bl, idesc, 1);
+                            tc_mma(d, al, bh, idesc, 1);
+                        }
+                        tc_commit(empty(vb));
+                        tc_commit(afull(ab));
+                        last = g;
                     }
-                    tc_commit(empty(vb));
-                    tc_commit(afull(ab));
                 }
                 __syncwarp();
             }
+        }
+        // drain: every product issued finishes before TMEM is freed (a commit to
+        // a barrier of its own, whose first phase no earlier wait can alias)
+        if (lane == 0 && last >= 0) {
+            tc_commit(bar + 72);
+            mbar_wait(bar + 72, 0);
         }
     } else {
         // ---------------- epilogue warps
@@ -216,7 +240,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_predict_select_tc(PredictTcArgs
             for (int s = 0; s < nch; ++s, ++g) {
                 const int ab = (int)(g & 1);
                 const uint32_t ph = (uint32_t)((g >> 1) & 1);
-                if (!bad && !mbar_wait(afull(ab), ph)) bad = true;
+                if (!bad && !mbar_wait(afull(ab), ph, a.wait_limit)) bad = true;
                 tc_fence_after();
                 const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * CN + CPW * cq);
                 const int chunk = chunk_at(s, cb);

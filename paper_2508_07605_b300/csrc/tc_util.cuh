@@ -13,7 +13,7 @@
 namespace ocf {
 namespace tc {
 
-constexpr int WAIT_LIMIT = 1 << 22;   // polls of a bounded mbarrier wait
+constexpr int WAIT_LIMIT = 1 << 22;   // default polls of a bounded mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -54,9 +54,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase of the given parity to complete; false when the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < WAIT_LIMIT; ++it)
+// Wait for the phase of the given parity to complete; false when the bound
+// (polls of try_wait; 0 gives up at once) ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = WAIT_LIMIT) {
+    for (int it = 0; it < limit; ++it)
         if (mbar_try(bar, parity)) return true;
     return false;
 }
