@@ -41,6 +41,10 @@ template <typename TV> struct SolveArgs {
     float *resid = nullptr;
     bool refine = false;
     const TV *u_given = nullptr;
+    // Rank-32 FP32-Cholesky solver only: a device word it may use as a pair
+    // counter (zeroed on the stream before each launch) to balance the warps'
+    // work; null: fixed ranges.
+    unsigned int *work = nullptr;
 };
 
 template <typename TV, typename TC>

@@ -69,6 +69,7 @@ struct open_cf {
     uint64_t v_epoch = 1, mlp_g_epoch = 0;
     Buf vimg, pt_err;                 // split BF16 operand images of V, timeout flag (predict)
     int wait_limit = OPEN_CF_WAIT_POLLS_DEFAULT;   // polls of a tensor-core pipeline wait
+    Buf work_ctr;                     // the rank-32 fold-in's pair counter (allocated at creation)
     uint64_t vimg_epoch = 0;          // the images are of V while vimg_epoch == v_epoch
     void *vimg_at = nullptr;          // ... and they are still at this address
     Buf ccount;                       // observations per column (weighted-lambda objective)
@@ -197,8 +198,11 @@ cudaError_t half_step(open_cf_t *h, const SolveArgs<TV> &a, cudaStream_t st) {
         return launch_row_solve<double, double>(a, h->KP, st);
     } else {
         const bool bf = h->cfg.precision == OPEN_CF_BF16_GRAM;
-        if (bf || h->KP >= 16)
-            return launch_row_solve_tc(a, h->KP, h->cfg.cholesky_fp64 != 0, bf, st);
+        if (bf || h->KP >= 16) {
+            SolveArgs<TV> b = a;
+            b.work = (unsigned int *)h->work_ctr.p;   // used by the rank-32 FP32 solver
+            return launch_row_solve_tc(b, h->KP, h->cfg.cholesky_fp64 != 0, bf, st);
+        }
         if (h->cfg.cholesky_fp64) return launch_row_solve<float, double>(a, h->KP, st);
         return launch_row_solve<float, float>(a, h->KP, st);
     }
@@ -593,7 +597,9 @@ int open_cf_create(const open_cf_config *cfg, open_cf_t **out) {
         prepare_mlp_forward_tc() != cudaSuccess || prepare_mlp_train_tc() != cudaSuccess ||
         prepare_predict_tc() != cudaSuccess ||
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        ensure(h, h->work_ctr, 16) != cudaSuccess) {
+        free_buf(h->work_ctr);
         cudaGetLastError();
         delete h;
         return OPEN_CF_CUDA_ERROR;
@@ -618,7 +624,7 @@ void open_cf_destroy(open_cf_t *h) {
                        &h->mlp_m1, &h->mlp_m2, &h->mlp_t, &h->mlp_cn, &h->mlp_scr, &h->mlp_img,
                        &h->mlp_err, &h->vimg, &h->pt_err, &h->ccount, &h->sg, &h->sb,
                        &h->sn, &h->hs_ptr, &h->hs_rptr, &h->hs_col, &h->hs_col16, &h->hs_val, &h->hs_U, &h->hs_best,
-                       &h->hs_sav, &h->hs_st, &h->hs_res})
+                       &h->hs_sav, &h->hs_st, &h->hs_res, &h->work_ctr})
             free_buf(*b);
     }
     delete h;
@@ -855,6 +861,7 @@ int open_cf_complete_rows_checked(open_cf_t *h, int64_t m_new, int64_t nnz,
     if (bf) a.Fb = h->Vb16.p;
     a.resid = resid;
     a.refine = refine != 0;
+    a.work = (unsigned int *)h->work_ctr.p;
     CK(h, launch_solve32_tc(a, bf, S(stream)));
     return OPEN_CF_OK;
 }
@@ -880,6 +887,7 @@ int open_cf_normal_residual(open_cf_t *h, int64_t m, int64_t nnz, const int64_t 
     if (bf) a.Fb = h->Vb16.p;
     a.resid = resid;
     a.u_given = U;
+    a.work = (unsigned int *)h->work_ctr.p;
     CK(h, launch_solve32_tc(a, bf, S(stream)));
     return OPEN_CF_OK;
 }

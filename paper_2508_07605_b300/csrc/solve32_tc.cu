@@ -54,6 +54,27 @@
 namespace ocf {
 namespace {
 
+// The kernel's arguments: the fields of SolveArgs<float> this solver reads,
+// packed (the 32-bit fields share one 16-byte block).
+struct Fold32Args {
+    int64_t m, nnz;
+    const int64_t *ptr;
+    const int32_t *idx;
+    const float *val;
+    const void *Fsrc;              // F (FP32 rows of KP) or Fb (split BF16 rows), by the build
+    float *out;
+    int32_t *status;
+    void *outb;
+    const int32_t *row_map;
+    const int64_t *m_dev;
+    float *resid;
+    const float *u_given;
+    unsigned int *work;            // pair counter, zeroed before the launch (null: static ranges)
+    int32_t n_other, ldo, kout;
+    float lambda;
+    bool wr, refine;
+};
+
 using namespace sm;
 using namespace pk;
 
@@ -281,7 +302,7 @@ struct PairFetch {
     float v[4];
 };
 
-__device__ __forceinline__ void fetch_pair(const SolveArgs<float> &a, int64_t k, int64_t M,
+__device__ __forceinline__ void fetch_pair(const Fold32Args &a, int64_t k, int64_t M,
                                            int lane, PairFetch &f) {
 #pragma unroll
     for (int si = 0; si < 2; ++si) {
@@ -420,7 +441,7 @@ __device__ __forceinline__ void dual_sTw_bf16(const Smem32<true> &W, int buf, fl
 }
 
 template <bool BF, bool DUAL>
-__global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a) {
+__global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(Fold32Args a) {
     using WS = Smem32<BF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -444,15 +465,49 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
     const int64_t M = a.m_dev ? *a.m_dev : a.m;
     const int64_t P = (M + 1) / 2;                // row pairs
     const int64_t G = (int64_t)gridDim.x * WARPS, gw = (int64_t)blockIdx.x * WARPS + warp;
-    const int64_t k0 = P * gw / G, k1 = P * (gw + 1) / G;
+    // Work.  Without a counter warp gw solves the pairs [P gw / G, P (gw + 1) / G).
+    // With one (a.work, zero at the launch) it first solves a contiguous range of
+    // Q = floor((P - P / 8) / G) pairs, then claims the remaining pairs one at a
+    // time (pair Q G + c for the counter's value c), so that row-length variance
+    // does not leave SMs idle at the end (the warps then finish within about one
+    // pair's time of each other).  A pair's result does not depend on the warp.
+    // (pair indices fit in 32 bits: the launcher refuses more than 2^31 - 1 pairs)
+    const bool dyn = a.work != nullptr;
+    const int32_t P32 = (int32_t)P, G32 = (int32_t)G, gw32 = (int32_t)gw;
+    const int32_t Q = dyn ? (P32 - P32 / 8) / G32 : 0;
+    auto claimed = [&](unsigned int c) -> int32_t { return Q * G32 + (int32_t)c; };
+    int32_t k = dyn ? Q * gw32 : (int32_t)(P * gw / G), kend = dyn ? Q * (gw32 + 1) : (int32_t)(P * (gw + 1) / G);
+    if (dyn && k == kend) {   // no contiguous share: claim the first pair
+        unsigned int c = 0;
+        if (lane == 0) c = atomicAdd(a.work, 1u);
+        k = claimed(__shfl_sync(FULL, c, 0));
+        kend = k < P32 ? k + 1 : k;
+    }
     PairFetch cur;
-    if (k0 < k1) fetch_pair(a, k0, M, lane, cur);
+    if (k < kend) fetch_pair(a, k, M, lane, cur);
     const bool dual_ok = DUAL && !a.resid && !a.refine && !a.u_given;
-    // lambda in FP32 once (a conversion from the double argument runs on the FP64
-    // pipe, which on this part is a small fraction of the FP32 rate)
-    const float lam0 = (float)a.lambda;
+    const float lam0 = a.lambda;
 
-    for (int64_t k = k0; k < k1; ++k) {
+    while (k < kend) {
+      // The pair after this one: the next of the range, else (with a counter)
+      // a claimed one, whose claim is issued here and read where the next pair
+      // is fetched (warp-uniform points; every path through the body has one).
+      const bool need = dyn && k + 1 == kend;
+      unsigned int claim = 0;
+      if (need && lane == 0) claim = atomicAdd(a.work, 1u);
+      int32_t kn = -1, knend = 0;
+      auto next = [&]() {
+          if (kn >= 0) return;
+          if (k + 1 < kend) {
+              kn = k + 1;
+              knend = kend;
+          } else if (need) {
+              kn = claimed(__shfl_sync(FULL, claim, 0));
+              knend = kn < P32 ? kn + 1 : kn;
+          } else {
+              kn = knend = kend;
+          }
+      };
       // A pair with one thin and one thick row runs in two passes, each row
       // with an empty partner, so that every row takes the branch its own
       // length selects and its result does not depend on the row it is paired
@@ -494,14 +549,14 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                     const int nb = in ? 16 : 0;
                     if constexpr (BF) {
                         const unsigned char *src =
-                            reinterpret_cast<const unsigned char *>(a.Fb) + (int64_t)j * KP * 4;
+                            reinterpret_cast<const unsigned char *>(a.Fsrc) + (int64_t)j * KP * 4;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             cp_async16(&W.ld.stage[si][0][lane][16 * e], src + 16 * e, nb);
                             cp_async16(&W.ld.stage[si][1][lane][16 * e], src + 2 * KP + 16 * e, nb);
                         }
                     } else {
-                        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.F + (int64_t)j * KP);
+                        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.Fsrc) + (int64_t)j * KP * 4;
 #pragma unroll
                         for (int e = 0; e < 8; ++e)
                             cp_async16(&W.ld.stage[si][0][lane][16 * e], src + 16 * e, nb);
@@ -509,7 +564,10 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
                 }
             }
             cp_async_commit();
-            if (last && k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);   // in flight during the solve
+            if (last) {   // in flight during the solve
+                next();
+                if (kn < knend) fetch_pair(a, kn, M, lane, cur);
+            }
             const bool bad0 = pf.bad[0] || (__any_sync(FULL, badf[0]) != 0);
             const bool bad1 = pf.bad[1] || (__any_sync(FULL, badf[1]) != 0);
             cp_async_wait<0>();
@@ -738,14 +796,14 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             const bool ok = item_jv(w, j, v, si);
             if constexpr (BF) {
                 const unsigned char *src =
-                    reinterpret_cast<const unsigned char *>(a.Fb) + (int64_t)j * KP * 4;
+                    reinterpret_cast<const unsigned char *>(a.Fsrc) + (int64_t)j * KP * 4;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, ok ? 16 : 0);
                     cp_async16(&W.ld.stage[buf][1][lane][16 * e], src + 2 * KP + 16 * e, ok ? 16 : 0);
                 }
             } else {
-                const unsigned char *src = reinterpret_cast<const unsigned char *>(a.F + (int64_t)j * KP);
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(a.Fsrc) + (int64_t)j * KP * 4;
 #pragma unroll
                 for (int e = 0; e < 8; ++e)
                     cp_async16(&W.ld.stage[buf][0][lane][16 * e], src + 16 * e, ok ? 16 : 0);
@@ -901,7 +959,10 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             }
             // the factor is done: fetch the next pair's bounds, indices and values
             // while the substitutions and the residual run
-            if (last && k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);
+            if (last) {
+                next();
+                if (kn < knend) fetch_pair(a, kn, M, lane, cur);
+            }
             inv0 = Sinv[i];
             inv1 = Sinv[i + 16];
             // ---- back substitution L^T x = y
@@ -909,7 +970,10 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
             x0 = xx.x;
             x1 = xx.y;
         } else {
-            if (last && k + 1 < k1) fetch_pair(a, k + 1, M, lane, cur);
+            if (last) {
+                next();
+                if (kn < knend) fetch_pair(a, kn, M, lane, cur);
+            }
             x0 = (i < a.kout && row >= 0) ? a.u_given[row * a.ldo + i] : 0.f;
             x1 = (i + 16 < a.kout && row >= 0) ? a.u_given[row * a.ldo + i + 16] : 0.f;
         }
@@ -992,6 +1056,9 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(SolveArgs<float> a
         }
         __syncwarp();   // the shared area is restaged by the next pair
       }
+      next();
+      k = kn;
+      kend = knend;
     }
 }
 
@@ -1012,7 +1079,20 @@ template <bool BF, bool DUAL> cudaError_t launch32(const SolveArgs<float> &a, cu
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_solve32_tc<BF, DUAL>, a);
+    Fold32Args f;
+    f.m = a.m; f.nnz = a.nnz; f.ptr = a.ptr; f.idx = a.idx; f.val = a.val;
+    f.Fsrc = BF ? a.Fb : (const void *)a.F;
+    f.out = a.out; f.status = a.status; f.outb = a.outb; f.row_map = a.row_map; f.m_dev = a.m_dev;
+    f.resid = a.resid; f.u_given = a.u_given;
+    // the counter only where the launch does not overlap its producer (a device
+    // row list or count comes from the preceding kernel)
+    f.work = (a.m_dev || a.row_map) ? nullptr : a.work;
+    f.n_other = (int32_t)a.n_other; f.ldo = (int32_t)a.ldo; f.kout = a.kout;
+    // lambda in FP32 once, on the host (a conversion from double on the device
+    // runs on the FP64 pipe, a small fraction of the FP32 rate on this part)
+    f.lambda = (float)a.lambda;
+    f.wr = a.wr; f.refine = a.refine;
+    return cudaLaunchKernelEx(&cfg, k_solve32_tc<BF, DUAL>, f);
 }
 
 template <bool BF> cudaError_t attr32() {
@@ -1036,12 +1116,19 @@ cudaError_t launch_solve32_tc(const SolveArgs<float> &a, bool bf16, cudaStream_t
     if (a.m <= 0) return cudaSuccess;
     if (bf16 && !a.Fb) return cudaErrorInvalidValue;
     if (a.gram) return cudaErrorInvalidValue;   // the streaming refit's sums are not supported here
+    // the packed arguments hold the setting count and the row stride in 32 bits
+    if (a.n_other > INT32_MAX || a.ldo > INT32_MAX) return cudaErrorInvalidValue;
     // one build serves the plain fold-in too (a build without the residual
     // paths spilled more registers and measured slower).  The build with the
     // thin-row dual branch runs where rows average fewer than 24 observations
     // (and no residual is wanted); with longer rows few pairs are thin, and
     // the build without it keeps the normal-equation path's registers.
     const bool dual = !a.resid && !a.refine && !a.u_given && a.nnz < 24 * a.m;
+    if ((a.m + 1) / 2 > INT32_MAX) return cudaErrorInvalidValue;   // pair indices are 32-bit
+    if (a.work && !a.m_dev && !a.row_map) {
+        cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+    }
     if (bf16) return dual ? launch32<true, true>(a, st) : launch32<true, false>(a, st);
     return dual ? launch32<false, true>(a, st) : launch32<false, false>(a, st);
 }
