@@ -152,6 +152,32 @@ def host_lead():
     torch.cuda._sleep(20_000_000)
 
 
+def host_link_bound(h2d_bytes, t_e2e, dev):
+    """The end-to-end figure's own bound: one pinned host-to-device copy of the
+    step's input bytes, timed with CUDA events (median of 5, after 2 untimed),
+    and the fraction of the end-to-end step it accounts for."""
+    import torch
+    hbuf = torch.empty(h2d_bytes, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(h2d_bytes, dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(dev)
+    ts = []
+    for i in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            dbuf.copy_(hbuf, non_blocking=True)
+            e1.record(s)
+        e1.synchronize()
+        if i >= 2:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    t = sorted(ts)[len(ts) // 2]
+    del hbuf, dbuf
+    return {"h2d_GBps": h2d_bytes / t / 1e9, "h2d_s_per_step": t,
+            "frac_of_e2e_step": t / t_e2e,
+            "note": "the step's input bytes in one pinned copy; the end-to-end step cannot be "
+                    "shorter than this"}
+
+
 def clocks_path(name):
     """Where the nvidia-smi samples of the timed region go: $OPEN_CF_CLOCKS_DIR
     (kept for inspection) or the temporary directory."""
@@ -581,7 +607,7 @@ def run_gpu_large(args):
     # end to end through the C ABI: the CSR from pinned host memory, each app's
     # chosen setting and saving back
     host_in = pinned(row_ptr.cpu(), col.cpu(), val.cpu())
-    e2e_api, e2e_same = None, None
+    e2e_api, e2e_same, e2e_link = None, None, None
     if factor != "fp64":
         # the setting indices (< 4096) travel as 16-bit values
         host_in[1] = col.cpu().to(torch.uint16).pin_memory()
@@ -606,6 +632,7 @@ def run_gpu_large(args):
         e2e_api = ("open_cf_complete_select_host (pinned host CSR in, 16-bit setting indices; "
                    "decisions out; the copies of each chunk of rows overlap the solves of the "
                    "chunk before)")
+        e2e_link = host_link_bound(h2d, t_e2e, dev)
     else:
         d_in = [torch.empty_like(x) for x in (row_ptr, col, val)]
 
@@ -708,7 +735,8 @@ def run_gpu_large(args):
         "e2e": {"value": ws * m / t_e2e, "unit": "row-solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3,
                 **({"api": e2e_api, "decisions_equal_device_calls": e2e_same}
-                   if e2e_api else {})},
+                   if e2e_api else {}),
+                **({"host_link": e2e_link} if e2e_link else {})},
         # per timed step: the fold-in and the reconstruction (V's operand images are
         # built once per V, in the warm-up)
         "gpu_launches": 2 * args.steps,

@@ -9,11 +9,13 @@
 //     A_i = sum_{j in Omega_i} f_j f_j^T + lambda I,   b_i = sum_{j in Omega_i} R_ij f_j,
 //     A_i = L L^T,  L y = b_i,  L^T u_i = y.
 //
-// Work split: each warp owns a contiguous range of row pairs.  While it
-// solves one pair it already has the next pair's row bounds, column indices
-// and values (the first 64 observations of each row) in flight into
-// registers, so the Gram phase of the next pair starts without waiting on
-// DRAM.
+// Work split: each warp owns a contiguous range of row pairs (7/8 of its fair
+// share when the caller passes a pair counter; the rest of the pairs are then
+// claimed one at a time, which evens out the row-length variance between
+// warps).  While it solves one pair it already has the next pair's row
+// bounds, column indices and values (the first 64 observations of each row)
+// in flight into registers, so the Gram phase of the next pair starts without
+// waiting on DRAM.
 //
 // Gram phase (whole warp): both rows' observations 32 at a time, each lane
 // staging one observation's factor row with 16-byte cp.async (double-buffered,
@@ -1065,7 +1067,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_solve32_tc(Fold32Args a) {
 template <bool BF> size_t smem_bytes() { return sizeof(Smem32<BF>) * WARPS; }
 
 template <bool BF, bool DUAL> cudaError_t launch32(const SolveArgs<float> &a, cudaStream_t st) {
-    // a persistent grid: at most two CTAs per SM, each warp a contiguous range of row pairs
+    // a persistent grid: at most two CTAs per SM
     const int64_t pairs = (a.m + 1) / 2;
     int64_t blocks = (pairs + WARPS - 1) / WARPS;
     if (blocks > NUM_SMS_HINT * 2) blocks = NUM_SMS_HINT * 2;
