@@ -37,9 +37,12 @@
  *    errors are detected synchronously on the host and leave the handle
  *    unchanged.
  *  - A handle may be used by one host thread at a time.  What a handle keeps
- *    between calls (V and its BF16 copies and operand images, workspaces) is
- *    written on the stream of the call that produces it; calls on different
- *    streams must be ordered by the caller (events), as for any shared buffer.
+ *    between calls (V and its BF16 copies and operand images, workspaces, the
+ *    rank-32 row solver's pair counter) is written on the stream of the call
+ *    that uses it; calls on different streams must be ordered by the caller
+ *    (events), as for any shared buffer -- two row solves of one handle
+ *    running at once on two streams would share that counter.  Use one handle
+ *    per stream for concurrent solves.
  *  - Calls that run many kernels (fits, joint refits, streaming ingests, the
  *    learned path's training step) capture them once into a CUDA graph kept
  *    per argument set (sizes and array addresses; up to 16 per handle) and
